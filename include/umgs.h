@@ -1,0 +1,163 @@
+/*
+ * umgs.h - C ABI of libumgs: single-pass anti-aliased rasterization of
+ * triangle meshes and 3D Gaussians, and Gaussian-centric proxy-mesh binding
+ * and deformation (UniMGS, arXiv 2601.19233), as hand-written CUDA kernels
+ * for GB300 (sm_103a).
+ *
+ * General rules
+ *  - Every array argument is a DEVICE pointer on the context's device, owned
+ *    by the caller, unless the comment says "host".  Output arrays are
+ *    allocated by the caller.  Structs describing cameras are host values.
+ *  - All float arrays are IEEE binary32, row-major, densely packed.
+ *  - Calls are asynchronous on the given CUDA stream (cudaStream_t passed as
+ *    void*; NULL = the legacy default stream) unless the comment says that
+ *    the call synchronises.
+ *  - No call aborts, traps or exits.  Every call returns a umgs_status; on
+ *    failure umgs_last_error(ctx) returns a message valid until the next call
+ *    on the same context.  A context must not be used by two host threads at
+ *    the same time.
+ *  - Workspace (projected records, keys, saved state) is owned by the context
+ *    or by a umgs_frame and grows on demand with cudaMalloc.
+ */
+#ifndef UMGS_H
+#define UMGS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    UMGS_OK = 0,
+    UMGS_ERR_INVALID_ARG = 1,     /* bad pointer, size, mode or camera */
+    UMGS_ERR_OUT_OF_MEMORY = 2,   /* workspace allocation failed */
+    UMGS_ERR_CAPACITY = 3,        /* a fixed-capacity device buffer overflowed */
+    UMGS_ERR_CUDA = 4,            /* a CUDA runtime call or kernel launch failed */
+    UMGS_ERR_TIMEOUT = 5,         /* a bounded device-side wait gave up */
+    UMGS_ERR_NOT_IMPLEMENTED = 6
+} umgs_status;
+
+/* blend modes (Sec. 3.2, Fig. 3 / Fig. 4) */
+enum {
+    UMGS_BLEND_FULL = 0,        /* depth-adjacent triangle entities with 4-sample t^j (Eq. 7-9) */
+    UMGS_BLEND_DIRECT = 1,      /* triangles as plain fragments, centre coverage (Fig. 3a) */
+    UMGS_BLEND_MSAA_ALL = 2,    /* Eq. 5-6: pixel-level T, O_i = mean coverage (Fig. 3b) */
+    UMGS_BLEND_ENTITY_ALL = 3   /* one entity across Gaussians: colour overflow (Fig. 3c) */
+};
+
+/* SH coefficient storage */
+enum { UMGS_F32 = 0, UMGS_BF16 = 1 };
+
+/* binding modes (Sec. 3.3) */
+enum { UMGS_BIND_BBX = 0, UMGS_BIND_CENTER = 1, UMGS_BIND_NEAREST = 2 };
+
+/* deformation modes (Eq. 13) */
+enum { UMGS_DEFORM_FRAME = 0, UMGS_DEFORM_LITERAL = 1 };
+
+typedef struct umgs_ctx umgs_ctx;
+typedef struct umgs_frame umgs_frame;
+
+/* Gaussians (Sec. 3.3: mean mu, covariance Sigma; colour from SH as in 3DGS). */
+typedef struct {
+    const float* means;      /* [n,3] */
+    const float* quats;      /* [n,4] (w,x,y,z); normalised inside; ignored when cov3d != NULL */
+    const float* scales;     /* [n,3] activated standard deviations; ignored when cov3d != NULL */
+    const float* opacities;  /* [n] activated opacity in [0,1] */
+    const void* sh;          /* [n,(sh_degree+1)^2,3] float32 or bfloat16 (sh_dtype) */
+    const float* cov3d;      /* nullable [n,6] (xx,xy,xz,yy,yz,zz), e.g. the output of umgs_deform */
+    int64_t n;
+    int32_t sh_degree;       /* 0..3 */
+    int32_t sh_dtype;        /* UMGS_F32 or UMGS_BF16 */
+} umgs_gaussians;
+
+/* A triangle mesh with per-vertex colour and alpha (Sec. 3.2: c_i, alpha_i). */
+typedef struct {
+    const float* verts;      /* [nv,3] world positions */
+    const int32_t* faces;    /* [nf,3] vertex indices in [0,nv) */
+    const float* vcolor;     /* [nv,3] linear RGB */
+    const float* valpha;     /* nullable [nv] per-vertex alpha, interpolated */
+    const float* falpha;     /* nullable [nf] per-face alpha, overrides valpha */
+    int64_t nv, nf;
+} umgs_mesh;
+
+/* Pinhole camera, world->camera [R|t], x right, y down, z forward;
+ * pixel (x,y) has its centre at (x+0.5, y+0.5); u = fx*X/Z + cx. */
+typedef struct {
+    float viewmat[12];       /* row-major 3x4 [R|t] */
+    float fx, fy, cx, cy;
+    int32_t width, height;
+    float near_z;            /* primitives with Z <= near_z are culled */
+} umgs_camera;
+
+typedef struct {
+    int32_t tile_size;       /* 8, 16 or 32 pixels; 0 = 16 */
+    int32_t blend_mode;      /* UMGS_BLEND_* */
+    float t_eps;             /* early termination: stop after T < t_eps; 0 = never (default 1e-4) */
+    float bg[3];             /* opaque background colour (Eq. 10-11) */
+    int32_t flags;           /* reserved, 0 */
+} umgs_render_opts;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  Synchronises. */
+umgs_status umgs_ctx_create(umgs_ctx** out, int device);
+/* Destroy a context and free its workspace.  Synchronises the device. */
+void umgs_ctx_destroy(umgs_ctx* ctx);
+/* Last error message of this context ("" after success). */
+const char* umgs_last_error(const umgs_ctx* ctx);
+/* Default render options (tile 16, FULL, t_eps 1e-4, black background). */
+void umgs_default_render_opts(umgs_render_opts* opts);
+
+/* A frame holds the projected records, sorted tile lists and per-pixel state
+ * of one umgs_render call, for umgs_render_backward and for inspection. */
+umgs_status umgs_frame_create(umgs_ctx* ctx, umgs_frame** out);
+void umgs_frame_destroy(umgs_frame* frame);
+
+/* ---- rendering (Sec. 3.2, Eq. 1-2 and 7-11) -------------------------------
+ *
+ * Renders ncams views of the Gaussians and nmeshes meshes in ONE pass per
+ * view: Gaussians are EWA-projected to 2D conics, triangles are set up with
+ * integer edge functions over 4 samples per pixel; every primitive is binned
+ * into the screen tiles its footprint touches with the key
+ * (camera*tiles + tile, depth bits, unified id), the keys are sorted, and
+ * each pixel composites its depth-ordered fragments front to back.  A run of
+ * depth-adjacent triangle fragments with no Gaussian between them forms one
+ * entity whose sub-pixel transmittances t^j give the continuous coverage
+ * O_i (Eq. 7-9); T after an entity is T_in * mean_j t^j.  Gaussian alpha is
+ * min(0.99, o*exp(-d^T conic d / 2)), fragments below 1/255 are skipped.
+ *
+ * gaussians  host pointer to a umgs_gaussians (n may be 0)
+ * meshes     host array of nmeshes umgs_mesh (may be NULL when nmeshes == 0)
+ * cams       host array of ncams cameras; all must have the same width/height
+ * opts       host pointer; NULL = defaults
+ * out_rgbt   [ncams,H,W,4] device float: RGB (background included) and the
+ *            final transmittance T
+ * frame      nullable; when given, the frame keeps everything
+ *            umgs_render_backward needs (and the call uses its buffers)
+ * Synchronises once per call on `stream` to read the number of keys.
+ * Errors: INVALID_ARG (NULL arrays with n > 0, ncams < 1, mixed image sizes,
+ * tile_size not 8/16/32, sh_degree > 3), OUT_OF_MEMORY, CUDA.
+ */
+umgs_status umgs_render(umgs_ctx* ctx, const umgs_gaussians* gaussians,
+                        const umgs_mesh* meshes, int32_t nmeshes,
+                        const umgs_camera* cams, int32_t ncams,
+                        const umgs_render_opts* opts, float* out_rgbt,
+                        umgs_frame* frame, void* stream);
+
+/* Number of keys (tile, primitive) pairs and tiles (all cameras) of the last
+ * render into `frame`.  Host outputs; synchronises nothing. */
+umgs_status umgs_frame_counts(const umgs_frame* frame, int64_t* num_keys, int64_t* num_tiles);
+
+/* Copy the sorted tile lists of the last render into caller buffers (device):
+ * tile_ptr [num_tiles+1] int64 (list of tile t is [tile_ptr[t], tile_ptr[t+1])),
+ * ids [num_keys] int32 unified primitive ids, dbits [num_keys] uint32 depth
+ * bits; each list in ascending (depth bits, id).  Asynchronous on stream. */
+umgs_status umgs_frame_lists(const umgs_frame* frame, int64_t* tile_ptr, int32_t* ids,
+                             uint32_t* dbits, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UMGS_H */

@@ -1,0 +1,148 @@
+// C ABI of libumgs: argument validation, contexts and frames.
+#include <cstring>
+#include <string>
+
+#include "internal.h"
+
+namespace umgs {
+
+umgs_status fail(umgs_ctx* ctx, umgs_status s, const std::string& msg) {
+    if (ctx) ctx->err = msg;
+    return s;
+}
+
+umgs_status cuda_fail(umgs_ctx* ctx, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(ctx, UMGS_ERR_CUDA, m);
+}
+
+}  // namespace umgs
+
+using namespace umgs;
+
+extern "C" {
+
+umgs_status umgs_ctx_create(umgs_ctx** out, int device) {
+    if (!out) return UMGS_ERR_INVALID_ARG;
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+        cudaGetLastError();
+        return UMGS_ERR_INVALID_ARG;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return UMGS_ERR_CUDA;
+    umgs_ctx* c = new umgs_ctx();
+    c->device = device;
+    if (cudaMallocHost(reinterpret_cast<void**>(&c->pinned), 64 * sizeof(int64_t)) != cudaSuccess) {
+        delete c;
+        return UMGS_ERR_OUT_OF_MEMORY;
+    }
+    cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    c->default_frame = new umgs_frame();
+    c->default_frame->ctx = c;
+    *out = c;
+    return UMGS_OK;
+}
+
+void umgs_ctx_destroy(umgs_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->default_frame) {
+        ctx->default_frame->release();
+        delete ctx->default_frame;
+    }
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    delete ctx;
+}
+
+const char* umgs_last_error(const umgs_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+void umgs_default_render_opts(umgs_render_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->tile_size = 16;
+    o->blend_mode = UMGS_BLEND_FULL;
+    o->t_eps = 1e-4f;
+}
+
+umgs_status umgs_frame_create(umgs_ctx* ctx, umgs_frame** out) {
+    if (!ctx || !out) return UMGS_ERR_INVALID_ARG;
+    umgs_frame* f = new umgs_frame();
+    f->ctx = ctx;
+    *out = f;
+    ctx->err.clear();
+    return UMGS_OK;
+}
+
+void umgs_frame_destroy(umgs_frame* frame) {
+    if (!frame) return;
+    cudaSetDevice(frame->ctx->device);
+    cudaDeviceSynchronize();
+    frame->release();
+    delete frame;
+}
+
+umgs_status umgs_render(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_mesh* meshes, int32_t nmeshes,
+                        const umgs_camera* cams, int32_t ncams, const umgs_render_opts* opts_in, float* out_rgbt,
+                        umgs_frame* frame, void* stream) {
+    if (!ctx) return UMGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, UMGS_ERR_CUDA, "cudaSetDevice");
+    umgs_render_opts opts;
+    umgs_default_render_opts(&opts);
+    if (opts_in) opts = *opts_in;
+    if (opts.tile_size == 0) opts.tile_size = 16;
+    if (opts.tile_size != 8 && opts.tile_size != 16 && opts.tile_size != 32)
+        return fail(ctx, UMGS_ERR_INVALID_ARG, "tile_size must be 8, 16 or 32");
+    if (opts.blend_mode < 0 || opts.blend_mode > 3) return fail(ctx, UMGS_ERR_INVALID_ARG, "unknown blend_mode");
+    if (!cams || ncams < 1) return fail(ctx, UMGS_ERR_INVALID_ARG, "need at least one camera");
+    if (!out_rgbt) return fail(ctx, UMGS_ERR_INVALID_ARG, "out_rgbt is NULL");
+    if (nmeshes < 0 || (nmeshes > 0 && !meshes)) return fail(ctx, UMGS_ERR_INVALID_ARG, "bad mesh array");
+    for (int c = 0; c < ncams; ++c) {
+        if (cams[c].width != cams[0].width || cams[c].height != cams[0].height)
+            return fail(ctx, UMGS_ERR_INVALID_ARG, "all cameras must share width and height");
+        if (cams[c].width < 1 || cams[c].height < 1 || cams[c].width > 32768 || cams[c].height > 32768)
+            return fail(ctx, UMGS_ERR_INVALID_ARG, "image size out of range (1..32768)");
+        if (!(cams[c].fx > 0.f) || !(cams[c].fy > 0.f) || !(cams[c].near_z > 0.f))
+            return fail(ctx, UMGS_ERR_INVALID_ARG, "fx, fy and near_z must be positive");
+    }
+    if (g && g->n > 0) {
+        if (!g->means || !g->opacities || !g->sh) return fail(ctx, UMGS_ERR_INVALID_ARG, "Gaussian array is NULL");
+        if (!g->cov3d && (!g->quats || !g->scales))
+            return fail(ctx, UMGS_ERR_INVALID_ARG, "need quats+scales or cov3d");
+        if (g->sh_degree < 0 || g->sh_degree > 3) return fail(ctx, UMGS_ERR_INVALID_ARG, "sh_degree must be 0..3");
+        if (g->sh_dtype != UMGS_F32 && g->sh_dtype != UMGS_BF16)
+            return fail(ctx, UMGS_ERR_INVALID_ARG, "sh_dtype must be UMGS_F32 or UMGS_BF16");
+    }
+    if (g && g->n < 0) return fail(ctx, UMGS_ERR_INVALID_ARG, "negative Gaussian count");
+    for (int m = 0; m < nmeshes; ++m) {
+        const umgs_mesh& me = meshes[m];
+        if (me.nf < 0 || me.nv < 0) return fail(ctx, UMGS_ERR_INVALID_ARG, "negative mesh size");
+        if (me.nf > 0 && (!me.verts || !me.faces || !me.vcolor || me.nv < 1))
+            return fail(ctx, UMGS_ERR_INVALID_ARG, "mesh array is NULL");
+    }
+    umgs_frame* fr = frame ? frame : ctx->default_frame;
+    if (fr->ctx != ctx) return fail(ctx, UMGS_ERR_INVALID_ARG, "frame belongs to another context");
+    umgs_gaussians empty;
+    std::memset(&empty, 0, sizeof(empty));
+    return render_forward(ctx, g ? g : &empty, meshes, nmeshes, cams, ncams, opts, out_rgbt, fr,
+                          static_cast<cudaStream_t>(stream));
+}
+
+umgs_status umgs_frame_counts(const umgs_frame* frame, int64_t* num_keys, int64_t* num_tiles) {
+    if (!frame || !num_keys || !num_tiles) return UMGS_ERR_INVALID_ARG;
+    if (!frame->valid) return UMGS_ERR_INVALID_ARG;
+    *num_keys = frame->num_keys;
+    *num_tiles = frame->num_tiles;
+    return UMGS_OK;
+}
+
+umgs_status umgs_frame_lists(const umgs_frame* frame, int64_t* tile_ptr, int32_t* ids, uint32_t* dbits,
+                             void* stream) {
+    if (!frame || !tile_ptr || !frame->valid) return UMGS_ERR_INVALID_ARG;
+    if (frame->num_keys > 0 && (!ids || !dbits)) return UMGS_ERR_INVALID_ARG;
+    return frame_lists(frame, tile_ptr, ids, dbits, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

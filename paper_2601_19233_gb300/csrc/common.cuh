@@ -1,0 +1,82 @@
+// Shared device definitions of libumgs (sm_103a).
+//
+// Canonical arithmetic: every float operation that decides WHICH fragments
+// exist or in WHICH ORDER they are blended (pixel footprints of Gaussians,
+// triangle snapping, depth keys, binding argmins) goes through the _rn
+// intrinsics below, one IEEE binary32 operation each, never contracted into
+// an FMA.  These decisions are therefore reproducible bit for bit by any
+// IEEE-754 implementation that evaluates the same expression tree.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace umgs {
+
+__device__ __forceinline__ float fm(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fa(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fdv(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float fsq(float a) { return __fsqrt_rn(a); }
+// ((a0*b0 + a1*b1) + a2*b2), each op rounded
+__device__ __forceinline__ float dot3c(float a0, float a1, float a2, float b0, float b1, float b2) {
+    return fa(fa(fm(a0, b0), fm(a1, b1)), fm(a2, b2));
+}
+
+// Camera as the kernels see it.
+struct DevCam {
+    float R[9];      // row-major rotation (world -> camera)
+    float t[3];
+    float fx, fy, cx, cy;
+    int32_t W, H;
+    float near_z;
+    float campos[3]; // camera centre (colour direction only; not a decision)
+    int32_t pad;
+};
+
+// Projected Gaussian record: 48 bytes, three 16-byte vectors.
+//  q0 = (u, v, ca, cb), q1 = (cc, opacity, r, g), q2 = (b, rect_x, rect_y, -)
+//  power2 = ca*dx^2 + cb*dx*dy + cc*dy^2 is the exponent in base 2:
+//  alpha = min(0.99, opacity * exp2(power2)); rect_x = x_lo | x_hi << 16.
+struct __align__(16) GRec {
+    float4 q0, q1, q2;
+};
+
+// Triangle record: 160 bytes, ten 16-byte vectors.
+//  edge k (opposite vertex k of the orientation-corrected triangle):
+//     E_k(sx, sy) = A_k*sx + B_k*sy + C_k in 1/256-px units, top-left bias
+//     folded into C_k, sample covered <=> all E_k >= 0
+//  u, v: unsnapped screen positions (ORIGINAL vertex order) for attributes
+//  iz: 1/Z per vertex, col: vertex colours, alpha: per-vertex alpha;
+//  const_alpha != 0 means alpha[0] is the face alpha (no interpolation).
+struct __align__(16) TRec {
+    int32_t A[3];
+    int32_t B[3];
+    int32_t const_alpha;
+    int32_t pad0;
+    long long C[3];
+    long long pad1;
+    float u[3], v[3];
+    float iz[3];
+    float col[9];
+    float alpha[3];
+    float pad2[3];
+};
+static_assert(sizeof(GRec) == 48, "GRec size");
+static_assert(sizeof(TRec) == 160, "TRec size");
+
+// Per (camera, primitive) binning info: pixel rect packed as lo | hi << 16,
+// depth bits; an empty rect (lo > hi) means culled.
+struct __align__(16) BinInfo {
+    uint32_t rx, ry, dbits, valid;
+};
+
+// 4 samples per pixel at the rotated-grid offsets (-2,-6), (6,-2), (-6,2),
+// (2,6) / 16 px, i.e. these offsets in 1/256 px from the pixel centre.
+__device__ __forceinline__ int sample_dx(int j) { return j == 0 ? -32 : j == 1 ? 96 : j == 2 ? -96 : 32; }
+__device__ __forceinline__ int sample_dy(int j) { return j == 0 ? -96 : j == 1 ? -32 : j == 2 ? 32 : 96; }
+
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.99f;
+constexpr float kLog2e = 1.4426950408889634f;
+
+}  // namespace umgs

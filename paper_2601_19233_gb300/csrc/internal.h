@@ -1,0 +1,75 @@
+// Host-side internals of libumgs: context, frames, workspace, launchers.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+#include <cuda_runtime.h>
+
+#include "../../include/umgs.h"
+#include "common.cuh"
+
+namespace umgs {
+
+// A device buffer that only grows.
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    cudaError_t reserve(size_t n) {
+        if (n <= bytes) return cudaSuccess;
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+        size_t want = n + n / 4 + 256;
+        cudaError_t e = cudaMalloc(&ptr, want);
+        if (e != cudaSuccess) { ptr = nullptr; return e; }
+        bytes = want;
+        return cudaSuccess;
+    }
+    void release() { if (ptr) cudaFree(ptr); ptr = nullptr; bytes = 0; }
+    template <class T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+}  // namespace umgs
+
+// Everything one umgs_render call produces and umgs_render_backward consumes.
+struct umgs_frame {
+    umgs_ctx* ctx = nullptr;
+    umgs::DevBuf cams, grec, trec, bin, tile_count, tile_off, tile_fill, keys, keys_tmp;
+    umgs::DevBuf last, status;
+    int64_t ng = 0, nt = 0;          // Gaussians, triangles (all meshes)
+    int32_t ncams = 0, W = 0, H = 0;
+    int32_t tile = 16, tiles_x = 0, tiles_y = 0;
+    int64_t num_keys = 0, num_tiles = 0;
+    int32_t blend_mode = 0;
+    float t_eps = 1e-4f;
+    float bg[3] = {0, 0, 0};
+    bool valid = false;
+    std::vector<int64_t> mesh_offset;  // unified id of each mesh's first face
+    void release() {
+        for (auto* b : {&cams, &grec, &trec, &bin, &tile_count, &tile_off, &tile_fill, &keys, &keys_tmp,
+                        &last, &status})
+            b->release();
+    }
+};
+
+struct umgs_ctx {
+    int device = 0;
+    std::string err;
+    umgs_frame* default_frame = nullptr;
+    int64_t* pinned = nullptr;  // small pinned host scratch
+    int num_sms = 0;
+};
+
+namespace umgs {
+
+umgs_status fail(umgs_ctx* ctx, umgs_status s, const std::string& msg);
+umgs_status cuda_fail(umgs_ctx* ctx, cudaError_t e, const char* where);
+
+umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_mesh* meshes, int32_t nmeshes,
+                           const umgs_camera* cams, int32_t ncams, const umgs_render_opts& opts,
+                           float* out_rgbt, umgs_frame* fr, cudaStream_t stream);
+
+umgs_status frame_lists(const umgs_frame* fr, int64_t* tile_ptr, int32_t* ids, uint32_t* dbits,
+                        cudaStream_t stream);
+
+}  // namespace umgs

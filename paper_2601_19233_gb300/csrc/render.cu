@@ -1,0 +1,816 @@
+// Forward single-pass rasterization of Gaussians and triangles (Sec. 3.2).
+//
+// Pipeline per umgs_render call (all cameras in one set of launches):
+//   1. project_gaussians / setup_triangles: one thread per primitive, looping
+//      over cameras; canonical fp32 footprint + depth key, a compact record
+//      for the compositor, and an atomic count per touched screen tile.
+//   2. scan_tiles: exclusive scan of the per-tile counts (single CTA).
+//   3. scatter_keys: every (primitive, tile) pair writes the 64-bit key
+//      (depth bits << 32 | unified id) into its tile's bucket (atomic slot).
+//      This is the outer, counting-sort layer of the onion sort: buckets are
+//      ordered by tile; inside a bucket the order is arbitrary.
+//   4. sort_tiles: one CTA per tile sorts its bucket by (depth bits, id) -
+//      bitonic in shared memory up to kSortCap keys, otherwise sorted chunks
+//      merged in global memory (inner layer of the onion sort).
+//   5. composite: one CTA per tile, one thread per pixel; records of the
+//      sorted list are staged through shared memory in batches; every pixel
+//      blends its fragments front to back (Eq. 1-2 for Gaussians, Eq. 7-9
+//      for entities of depth-adjacent triangles) and the CTA stops when
+//      every pixel has T < t_eps (block-wide vote).
+#include <cstdio>
+#include <cmath>
+#include <algorithm>
+
+#include "internal.h"
+
+namespace umgs {
+
+// ---------------------------------------------------------------------------
+// spherical harmonics (3DGS colour model), degree <= 3, fp32.
+// Real SH with the Condon-Shortley phase, index l*l + (m + l).
+__device__ __forceinline__ float sh_coef(const void* sh, int dtype, int64_t base, int c) {
+    if (dtype == UMGS_BF16) {
+        const unsigned short* p = static_cast<const unsigned short*>(sh);
+        return __uint_as_float(((unsigned int)p[base + c]) << 16);
+    }
+    return static_cast<const float*>(sh)[base + c];
+}
+
+__device__ void eval_sh(const void* sh, int dtype, int deg, int64_t i, float dx, float dy, float dz, float rgb[3]) {
+    const int K = (deg + 1) * (deg + 1);
+    const int64_t base = i * (int64_t)K * 3;
+    float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+    float x = dx * inv, y = dy * inv, z = dz * inv;
+    float Y[16];
+    Y[0] = 0.28209479177387814f;                    // 1/(2 sqrt(pi))
+    if (deg > 0) {
+        const float c1 = 0.4886025119029199f;       // sqrt(3/(4 pi))
+        Y[1] = -c1 * y;
+        Y[2] = c1 * z;
+        Y[3] = -c1 * x;
+    }
+    if (deg > 1) {
+        const float xx = x * x, yy = y * y, zz = z * z;
+        Y[4] = 1.0925484305920792f * x * y;           // sqrt(15/pi)/2
+        Y[5] = -1.0925484305920792f * y * z;
+        Y[6] = 0.31539156525252005f * (2.f * zz - xx - yy);  // sqrt(5/pi)/4
+        Y[7] = -1.0925484305920792f * x * z;
+        Y[8] = 0.5462742152960396f * (xx - yy);       // sqrt(15/pi)/4
+        if (deg > 2) {
+            Y[9] = -0.5900435899266435f * y * (3.f * xx - yy);          // sqrt(35/(2 pi))/4
+            Y[10] = 2.890611442640554f * x * y * z;                      // sqrt(105/pi)/2
+            Y[11] = -0.4570457994644658f * y * (4.f * zz - xx - yy);    // sqrt(21/(2 pi))/4
+            Y[12] = 0.3731763325901154f * z * (2.f * zz - 3.f * xx - 3.f * yy);  // sqrt(7/pi)/4
+            Y[13] = -0.4570457994644658f * x * (4.f * zz - xx - yy);
+            Y[14] = 1.445305721320277f * z * (xx - yy);                  // sqrt(105/pi)/4
+            Y[15] = -0.5900435899266435f * x * (xx - 3.f * yy);
+        }
+    }
+    for (int c = 0; c < 3; ++c) {
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (k < K) acc = fmaf(sh_coef(sh, dtype, base + 3 * k, c), Y[k], acc);
+        rgb[c] = fmaxf(acc + 0.5f, 0.f);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// canonical Gaussian covariance and projection
+
+__device__ void cov3d_canonical(float qw, float qx, float qy, float qz, float sx, float sy, float sz, float S[6]) {
+    float n = fsq(fa(fa(fa(fm(qw, qw), fm(qx, qx)), fm(qy, qy)), fm(qz, qz)));
+    float w, x, y, z;
+    if (n == 0.f) { w = 1.f; x = y = z = 0.f; }
+    else { w = fdv(qw, n); x = fdv(qx, n); y = fdv(qy, n); z = fdv(qz, n); }
+    float r[9];
+    r[0] = fs(1.f, fm(2.f, fa(fm(y, y), fm(z, z))));
+    r[1] = fm(2.f, fs(fm(x, y), fm(w, z)));
+    r[2] = fm(2.f, fa(fm(x, z), fm(w, y)));
+    r[3] = fm(2.f, fa(fm(x, y), fm(w, z)));
+    r[4] = fs(1.f, fm(2.f, fa(fm(x, x), fm(z, z))));
+    r[5] = fm(2.f, fs(fm(y, z), fm(w, x)));
+    r[6] = fm(2.f, fs(fm(x, z), fm(w, y)));
+    r[7] = fm(2.f, fa(fm(y, z), fm(w, x)));
+    r[8] = fs(1.f, fm(2.f, fa(fm(x, x), fm(y, y))));
+    float M[9];
+    const float s[3] = {sx, sy, sz};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) M[3 * i + j] = fm(r[3 * i + j], s[j]);
+    auto e = [&](int i, int j) { return dot3c(M[3 * i], M[3 * i + 1], M[3 * i + 2], M[3 * j], M[3 * j + 1], M[3 * j + 2]); };
+    S[0] = e(0, 0); S[1] = e(0, 1); S[2] = e(0, 2); S[3] = e(1, 1); S[4] = e(1, 2); S[5] = e(2, 2);
+}
+
+// fp64 2D covariance for near-singular cases (same formula, double precision)
+__device__ void cov2d_fp64(const DevCam& C, float mx, float my, float mz, const float* q, const float* s,
+                           const float* c6, double& a, double& b, double& c) {
+    const double R[9] = {C.R[0], C.R[1], C.R[2], C.R[3], C.R[4], C.R[5], C.R[6], C.R[7], C.R[8]};
+    double X = R[0] * mx + R[1] * my + R[2] * mz + C.t[0];
+    double Y = R[3] * mx + R[4] * my + R[5] * mz + C.t[1];
+    double Z = R[6] * mx + R[7] * my + R[8] * mz + C.t[2];
+    double S[3][3];
+    if (c6) {
+        S[0][0] = c6[0]; S[0][1] = S[1][0] = c6[1]; S[0][2] = S[2][0] = c6[2];
+        S[1][1] = c6[3]; S[1][2] = S[2][1] = c6[4]; S[2][2] = c6[5];
+    } else {
+        double w = q[0], x = q[1], y = q[2], z = q[3];
+        double n = sqrt(w * w + x * x + y * y + z * z);
+        if (n == 0.0) { w = 1; x = y = z = 0; } else { w /= n; x /= n; y /= n; z /= n; }
+        double r[3][3] = {{1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y)},
+                          {2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x)},
+                          {2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)}};
+        double M[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) M[i][j] = r[i][j] * (double)s[j];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) S[i][j] = M[i][0] * M[j][0] + M[i][1] * M[j][1] + M[i][2] * M[j][2];
+    }
+    double limx = 1.3 * ((double)C.W / (2.0 * C.fx)), limy = 1.3 * ((double)C.H / (2.0 * C.fy));
+    double xc = fmin(limx, fmax(-limx, X / Z)) * Z, yc = fmin(limy, fmax(-limy, Y / Z)) * Z;
+    double J[2][3] = {{C.fx / Z, 0.0, -C.fx * xc / (Z * Z)}, {0.0, C.fy / Z, -C.fy * yc / (Z * Z)}};
+    double T[2][3];
+    for (int i = 0; i < 2; ++i)
+        for (int k = 0; k < 3; ++k) T[i][k] = J[i][0] * R[k] + J[i][1] * R[3 + k] + J[i][2] * R[6 + k];
+    double U[2][3];
+    for (int i = 0; i < 2; ++i)
+        for (int k = 0; k < 3; ++k) U[i][k] = T[i][0] * S[0][k] + T[i][1] * S[1][k] + T[i][2] * S[2][k];
+    a = U[0][0] * T[0][0] + U[0][1] * T[0][1] + U[0][2] * T[0][2] + 0.3;
+    b = U[0][0] * T[1][0] + U[0][1] * T[1][1] + U[0][2] * T[1][2];
+    c = U[1][0] * T[1][0] + U[1][1] * T[1][1] + U[1][2] * T[1][2] + 0.3;
+}
+
+__global__ void __launch_bounds__(256) project_gaussians_kernel(
+    const float* __restrict__ means, const float* __restrict__ quats, const float* __restrict__ scales,
+    const float* __restrict__ opac, const void* __restrict__ sh, int sh_dtype, int sh_deg,
+    const float* __restrict__ cov3d, int64_t N, const DevCam* __restrict__ cams, int ncams,
+    int ts, int tiles_x, int tiles_per_cam, GRec* __restrict__ grec, BinInfo* __restrict__ bin, int64_t ntot_prims,
+    int32_t* __restrict__ tile_count) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
+    float q[4] = {0, 0, 0, 0}, s[3] = {0, 0, 0}, c6[6];
+    float S[6];
+    if (cov3d) {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) c6[k] = cov3d[6 * i + k];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) S[k] = c6[k];
+    } else {
+        q[0] = quats[4 * i]; q[1] = quats[4 * i + 1]; q[2] = quats[4 * i + 2]; q[3] = quats[4 * i + 3];
+        s[0] = scales[3 * i]; s[1] = scales[3 * i + 1]; s[2] = scales[3 * i + 2];
+        cov3d_canonical(q[0], q[1], q[2], q[3], s[0], s[1], s[2], S);
+    }
+    const float o = opac[i];
+    for (int cam = 0; cam < ncams; ++cam) {
+        const DevCam& C = cams[cam];
+        const int64_t ri = (int64_t)cam * N + i;           // record index
+        const int64_t bidx = (int64_t)cam * ntot_prims + i;  // bin index
+        const float* R = C.R;
+        const float X = fa(dot3c(R[0], R[1], R[2], mx, my, mz), C.t[0]);
+        const float Y = fa(dot3c(R[3], R[4], R[5], mx, my, mz), C.t[1]);
+        const float Z = fa(dot3c(R[6], R[7], R[8], mx, my, mz), C.t[2]);
+        bool valid = Z > C.near_z;
+        const float u = fa(fdv(fm(C.fx, X), Z), C.cx);
+        const float v = fa(fdv(fm(C.fy, Y), Z), C.cy);
+        const float limx = fm(1.3f, fdv((float)C.W, fm(2.f, C.fx)));
+        const float limy = fm(1.3f, fdv((float)C.H, fm(2.f, C.fy)));
+        const float xc = fm(fminf(limx, fmaxf(-limx, fdv(X, Z))), Z);
+        const float yc = fm(fminf(limy, fmaxf(-limy, fdv(Y, Z))), Z);
+        const float z2 = fm(Z, Z);
+        const float j00 = fdv(C.fx, Z), j11 = fdv(C.fy, Z);
+        const float j02 = -fdv(fm(C.fx, xc), z2), j12 = -fdv(fm(C.fy, yc), z2);
+        float T0[3], T1[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            T0[k] = fa(fm(j00, R[k]), fm(j02, R[6 + k]));
+            T1[k] = fa(fm(j11, R[3 + k]), fm(j12, R[6 + k]));
+        }
+        // Sigma rows: [S0 S1 S2; S1 S3 S4; S2 S4 S5]
+        const float Sm[9] = {S[0], S[1], S[2], S[1], S[3], S[4], S[2], S[4], S[5]};
+        float U0[3], U1[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            U0[k] = dot3c(T0[0], T0[1], T0[2], Sm[k], Sm[3 + k], Sm[6 + k]);
+            U1[k] = dot3c(T1[0], T1[1], T1[2], Sm[k], Sm[3 + k], Sm[6 + k]);
+        }
+        float a = dot3c(U0[0], U0[1], U0[2], T0[0], T0[1], T0[2]);
+        const float b = dot3c(U0[0], U0[1], U0[2], T1[0], T1[1], T1[2]);
+        float c = dot3c(U1[0], U1[1], U1[2], T1[0], T1[1], T1[2]);
+        a = fa(a, 0.3f);
+        c = fa(c, 0.3f);
+        const float det = fs(fm(a, c), fm(b, b));
+        const float rx = fm(3.f, fsq(a)), ry = fm(3.f, fsq(c));
+        valid = valid && det > 0.f && isfinite(u) && isfinite(v) && isfinite(rx) && isfinite(ry);
+        const float xlo = fmaxf(ceilf(fs(fs(u, rx), 0.5f)), 0.f);
+        const float xhi = fminf(floorf(fs(fa(u, rx), 0.5f)), (float)(C.W - 1));
+        const float ylo = fmaxf(ceilf(fs(fs(v, ry), 0.5f)), 0.f);
+        const float yhi = fminf(floorf(fs(fa(v, ry), 0.5f)), (float)(C.H - 1));
+        valid = valid && xlo <= xhi && ylo <= yhi;
+        BinInfo bi;
+        bi.dbits = __float_as_uint(Z);
+        bi.valid = valid ? 1u : 0u;
+        if (!valid) {
+            bi.rx = 1u;  // lo = 1 > hi = 0 : empty
+            bi.ry = 1u;
+            bin[bidx] = bi;
+            continue;
+        }
+        const int ixlo = (int)xlo, ixhi = (int)xhi, iylo = (int)ylo, iyhi = (int)yhi;
+        bi.rx = (uint32_t)ixlo | ((uint32_t)ixhi << 16);
+        bi.ry = (uint32_t)iylo | ((uint32_t)iyhi << 16);
+        bin[bidx] = bi;
+        // conic (not a decision): fp32, or fp64 when the 2x2 determinant is
+        // small relative to a*c (cancellation would cost > 10 bits)
+        float ia, ib, ic;
+        if (det < 0.0009765625f * a * c) {
+            double A2, B2, C2;
+            cov2d_fp64(C, mx, my, mz, q, s, cov3d ? c6 : nullptr, A2, B2, C2);
+            const double d2 = A2 * C2 - B2 * B2;
+            ia = (float)(C2 / d2); ib = (float)(-B2 / d2); ic = (float)(A2 / d2);
+        } else {
+            const float id = 1.f / det;
+            ia = c * id; ib = -b * id; ic = a * id;
+        }
+        float rgb[3];
+        eval_sh(sh, sh_dtype, sh_deg, i, mx - C.campos[0], my - C.campos[1], mz - C.campos[2], rgb);
+        GRec g;
+        g.q0 = make_float4(u, v, -0.5f * kLog2e * ia, -kLog2e * ib);
+        g.q1 = make_float4(-0.5f * kLog2e * ic, o, rgb[0], rgb[1]);
+        g.q2 = make_float4(rgb[2], __uint_as_float(bi.rx), __uint_as_float(bi.ry), 0.f);
+        grec[ri] = g;
+        const int txlo = ixlo / ts, txhi = ixhi / ts, tylo = iylo / ts, tyhi = iyhi / ts;
+        for (int ty = tylo; ty <= tyhi; ++ty)
+            for (int tx = txlo; tx <= txhi; ++tx)
+                atomicAdd(&tile_count[cam * tiles_per_cam + ty * tiles_x + tx], 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// canonical triangle setup
+
+__device__ __forceinline__ long long floor_div256(long long a) { return a >> 8; }
+__device__ __forceinline__ long long ceil_div256(long long a) { return -((-a) >> 8); }
+
+__global__ void __launch_bounds__(256) setup_triangles_kernel(
+    const float* __restrict__ verts, const int32_t* __restrict__ faces, const float* __restrict__ vcolor,
+    const float* __restrict__ valpha, const float* __restrict__ falpha, int64_t nv, int64_t nf,
+    int64_t tri_base /* index of this mesh's first face among all triangles */, int64_t nt_total,
+    int64_t id_base /* unified id of this mesh's first face */, const DevCam* __restrict__ cams, int ncams,
+    int ts, int tiles_x, int tiles_per_cam, TRec* __restrict__ trec, BinInfo* __restrict__ bin,
+    int64_t ntot_prims, int32_t* __restrict__ tile_count, int32_t* __restrict__ status) {
+    const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    int vid[3] = {faces[3 * f], faces[3 * f + 1], faces[3 * f + 2]};
+    bool idx_ok = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        if (vid[k] < 0 || vid[k] >= nv) idx_ok = false;
+    if (!idx_ok) {
+        atomicOr(status, 1);
+        for (int cam = 0; cam < ncams; ++cam) {
+            BinInfo bi; bi.rx = 1u; bi.ry = 1u; bi.dbits = 0u; bi.valid = 0u;
+            bin[(int64_t)cam * ntot_prims + id_base + f] = bi;
+        }
+        return;
+    }
+    float P[3][3], col[9], al[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            P[k][d] = verts[3 * (int64_t)vid[k] + d];
+            col[3 * k + d] = vcolor[3 * (int64_t)vid[k] + d];
+        }
+    }
+    int const_alpha = 1;
+    if (falpha) { al[0] = al[1] = al[2] = falpha[f]; }
+    else if (valpha) { const_alpha = 0; al[0] = valpha[vid[0]]; al[1] = valpha[vid[1]]; al[2] = valpha[vid[2]]; }
+    else { al[0] = al[1] = al[2] = 1.f; }
+    for (int cam = 0; cam < ncams; ++cam) {
+        const DevCam& C = cams[cam];
+        const float* R = C.R;
+        float Zv[3], uv[3], vv[3];
+        long long sx[3], sy[3];
+        bool valid = true;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float X = fa(dot3c(R[0], R[1], R[2], P[k][0], P[k][1], P[k][2]), C.t[0]);
+            const float Y = fa(dot3c(R[3], R[4], R[5], P[k][0], P[k][1], P[k][2]), C.t[1]);
+            const float Z = fa(dot3c(R[6], R[7], R[8], P[k][0], P[k][1], P[k][2]), C.t[2]);
+            const float u = fa(fdv(fm(C.fx, X), Z), C.cx);
+            const float v = fa(fdv(fm(C.fy, Y), Z), C.cy);
+            const bool ok = Z > C.near_z && isfinite(u) && isfinite(v) && fabsf(u) <= 16384.f && fabsf(v) <= 16384.f;
+            valid = valid && ok;
+            Zv[k] = Z; uv[k] = u; vv[k] = v;
+            sx[k] = ok ? __float2ll_rn(fm(256.f, u)) : 0;
+            sy[k] = ok ? __float2ll_rn(fm(256.f, v)) : 0;
+        }
+        const long long area = (sx[1] - sx[0]) * (sy[2] - sy[0]) - (sx[2] - sx[0]) * (sy[1] - sy[0]);
+        valid = valid && area != 0;
+        long long ox[3] = {sx[0], sx[1], sx[2]}, oy[3] = {sy[0], sy[1], sy[2]};
+        if (area < 0) { ox[1] = sx[2]; ox[2] = sx[1]; oy[1] = sy[2]; oy[2] = sy[1]; }
+        const long long xmin = min(sx[0], min(sx[1], sx[2])), xmax = max(sx[0], max(sx[1], sx[2]));
+        const long long ymin = min(sy[0], min(sy[1], sy[2])), ymax = max(sy[0], max(sy[1], sy[2]));
+        const long long xlo = max(ceil_div256(xmin - 224), 0LL), xhi = min(floor_div256(xmax - 32), (long long)(C.W - 1));
+        const long long ylo = max(ceil_div256(ymin - 224), 0LL), yhi = min(floor_div256(ymax - 32), (long long)(C.H - 1));
+        valid = valid && xlo <= xhi && ylo <= yhi;
+        BinInfo bi;
+        bi.dbits = __float_as_uint(fdv(fa(fa(Zv[0], Zv[1]), Zv[2]), 3.f));
+        bi.valid = valid ? 1u : 0u;
+        const int64_t bidx = (int64_t)cam * ntot_prims + id_base + f;
+        if (!valid) { bi.rx = 1u; bi.ry = 1u; bin[bidx] = bi; continue; }
+        bi.rx = (uint32_t)xlo | ((uint32_t)xhi << 16);
+        bi.ry = (uint32_t)ylo | ((uint32_t)yhi << 16);
+        bin[bidx] = bi;
+        TRec t;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int a = (k + 1) % 3, b = (k + 2) % 3;
+            const long long A = oy[a] - oy[b];
+            const long long B = ox[b] - ox[a];
+            const long long Cc = ox[a] * oy[b] - oy[a] * ox[b];
+            const bool topleft = A > 0 || (A == 0 && B > 0);
+            t.A[k] = (int32_t)A;
+            t.B[k] = (int32_t)B;
+            t.C[k] = Cc - (topleft ? 0 : 1);
+            t.u[k] = uv[k];
+            t.v[k] = vv[k];
+            t.iz[k] = 1.f / Zv[k];
+            t.alpha[k] = al[k];
+        }
+#pragma unroll
+        for (int k = 0; k < 9; ++k) t.col[k] = col[k];
+        t.const_alpha = const_alpha;
+        t.pad0 = 0; t.pad1 = 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) t.pad2[k] = 0.f;
+        trec[(int64_t)cam * nt_total + tri_base + f] = t;
+        const int txlo = (int)xlo / ts, txhi = (int)xhi / ts, tylo = (int)ylo / ts, tyhi = (int)yhi / ts;
+        for (int ty = tylo; ty <= tyhi; ++ty)
+            for (int tx = txlo; tx <= txhi; ++tx)
+                atomicAdd(&tile_count[cam * tiles_per_cam + ty * tiles_x + tx], 1);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// exclusive scan of tile counts (one CTA of 1024 threads)
+
+__global__ void __launch_bounds__(1024) scan_tiles_kernel(const int32_t* __restrict__ cnt, int64_t M,
+                                                          int64_t* __restrict__ off) {
+    __shared__ long long warp_sums[32];
+    const int tid = threadIdx.x;
+    const int64_t per = (M + 1023) / 1024;
+    const int64_t b = min((int64_t)tid * per, M), e = min(b + per, M);
+    long long local = 0;
+    for (int64_t k = b; k < e; ++k) local += cnt[k];
+    // inclusive scan of `local` across the block
+    long long x = local;
+    const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        long long w = warp_sums[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            long long y = __shfl_up_sync(0xffffffffu, w, d);
+            if (lane >= d) w += y;
+        }
+        warp_sums[lane] = w;
+    }
+    __syncthreads();
+    long long run = x - local + (warp > 0 ? warp_sums[warp - 1] : 0);
+    for (int64_t k = b; k < e; ++k) { off[k] = run; run += cnt[k]; }
+    if (tid == 1023) off[M] = warp_sums[31];
+}
+
+// ---------------------------------------------------------------------------
+// key scatter into tile buckets (outer layer of the onion sort)
+
+__global__ void __launch_bounds__(256) scatter_keys_kernel(const BinInfo* __restrict__ bin, int64_t ntot, int ncams,
+                                                           int ts, int tiles_x, int tiles_per_cam,
+                                                           const int64_t* __restrict__ off,
+                                                           int32_t* __restrict__ fill, uint64_t* __restrict__ keys) {
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (gid >= ntot * ncams) return;
+    const int cam = (int)(gid / ntot);
+    const int64_t id = gid - (int64_t)cam * ntot;
+    const BinInfo bi = bin[gid];
+    if (!bi.valid) return;
+    const int xlo = bi.rx & 0xffff, xhi = bi.rx >> 16, ylo = bi.ry & 0xffff, yhi = bi.ry >> 16;
+    const uint64_t key = ((uint64_t)bi.dbits << 32) | (uint64_t)(uint32_t)id;
+    for (int ty = ylo / ts; ty <= yhi / ts; ++ty)
+        for (int tx = xlo / ts; tx <= xhi / ts; ++tx) {
+            const int t = cam * tiles_per_cam + ty * tiles_x + tx;
+            const int slot = atomicAdd(&fill[t], 1);
+            keys[off[t] + slot] = key;
+        }
+}
+
+// ---------------------------------------------------------------------------
+// per-tile sort (inner layer of the onion sort)
+
+constexpr int kSortThreads = 512;
+constexpr int kSortCap = 4096;  // keys sorted entirely in shared memory
+
+__device__ void bitonic_smem(uint64_t* s, int n2) {
+    for (int k = 2; k <= n2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n2 / 2; i += blockDim.x) {
+                // index of the lower element of the i-th compare pair at stride j
+                const int lo = 2 * i - (i & (j - 1));
+                const int hi = lo + j;
+                const bool up = (lo & k) == 0;
+                const uint64_t a = s[lo], b = s[hi];
+                if ((a > b) == up) { s[lo] = b; s[hi] = a; }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// merge path split: number of elements taken from A among the first `diag` outputs
+__device__ int merge_split(const uint64_t* A, int na, const uint64_t* B, int nb, int diag) {
+    int lo = max(0, diag - nb), hi = min(diag, na);
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (A[mid] < B[diag - 1 - mid]) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kSortThreads) sort_tiles_kernel(uint64_t* __restrict__ keys,
+                                                                   uint64_t* __restrict__ tmp,
+                                                                   const int64_t* __restrict__ off) {
+    extern __shared__ uint64_t s_keys[];
+    const int tile = blockIdx.x;
+    const int64_t beg = off[tile];
+    const int n = (int)(off[tile + 1] - beg);
+    if (n <= 1) return;
+    uint64_t* seg = keys + beg;
+    // sort chunks of kSortCap in shared memory
+    for (int c0 = 0; c0 < n; c0 += kSortCap) {
+        const int m = min(kSortCap, n - c0);
+        int n2 = 1;
+        while (n2 < m) n2 <<= 1;
+        for (int k = threadIdx.x; k < n2; k += blockDim.x) s_keys[k] = k < m ? seg[c0 + k] : ~0ull;
+        __syncthreads();
+        bitonic_smem(s_keys, n2);
+        for (int k = threadIdx.x; k < m; k += blockDim.x) seg[c0 + k] = s_keys[k];
+        __syncthreads();
+    }
+    if (n <= kSortCap) return;
+    // merge sorted runs pairwise in global memory (ping-pong with tmp)
+    uint64_t* src = seg;
+    uint64_t* dst = tmp + beg;
+    for (int run = kSortCap; run < n; run <<= 1) {
+        for (int s0 = 0; s0 < n; s0 += 2 * run) {
+            const int na = min(run, n - s0);
+            const int nb = min(run, n - s0 - na);
+            const uint64_t* A = src + s0;
+            const uint64_t* B = A + na;
+            const int total = na + nb;
+            const int per = (total + blockDim.x - 1) / blockDim.x;
+            const int d0 = min((int)threadIdx.x * per, total), d1 = min(d0 + per, total);
+            int ia = merge_split(A, na, B, nb, d0);
+            int ib = d0 - ia;
+            for (int d = d0; d < d1; ++d) {
+                const bool takeA = ib >= nb || (ia < na && A[ia] < B[ib]);
+                dst[s0 + d] = takeA ? A[ia++] : B[ib++];
+            }
+        }
+        __syncthreads();
+        uint64_t* t = src; src = dst; dst = t;
+    }
+    if (src != seg)
+        for (int k = threadIdx.x; k < n; k += blockDim.x) seg[k] = src[k];
+}
+
+// ---------------------------------------------------------------------------
+// compositor
+
+constexpr int kBatch = 256;
+
+struct PixelState {
+    float C[3];
+    float T;
+    float Tin;
+    float t[4];
+    float g_since;
+    bool in_ent;
+};
+
+template <int TS>
+__global__ void __launch_bounds__(TS * TS) composite_kernel(
+    const uint64_t* __restrict__ keys, const int64_t* __restrict__ off, const GRec* __restrict__ grec,
+    const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x, int tiles_per_cam, int W, int H,
+    float t_eps, float bg0, float bg1, float bg2, int mode, float4* __restrict__ out, int32_t* __restrict__ out_last) {
+    constexpr int NT = TS * TS;
+    __shared__ float4 s_rec[kBatch][10];
+    __shared__ uint32_t s_id[kBatch];
+    const int tile = blockIdx.x;
+    const int cam = tile / tiles_per_cam;
+    const int lt = tile - cam * tiles_per_cam;
+    const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
+    const int px = tx * TS + (threadIdx.x % TS), py = ty * TS + (threadIdx.x / TS);
+    const bool inside = px < W && py < H;
+    const int64_t beg = off[tile], end = off[tile + 1];
+    const GRec* G = grec + (int64_t)cam * Ng;
+    const TRec* TR = trec + (int64_t)cam * Nt;
+    const float qx = px + 0.5f, qy = py + 0.5f;
+    const long long scx = (long long)px * 256 + 128, scy = (long long)py * 256 + 128;
+
+    PixelState st;
+    st.C[0] = st.C[1] = st.C[2] = 0.f;
+    st.T = 1.f; st.Tin = 1.f; st.g_since = 1.f;
+    st.t[0] = st.t[1] = st.t[2] = st.t[3] = 1.f;
+    st.in_ent = false;
+    bool done = !inside;
+    int last = 0;
+
+    for (int64_t b0 = beg; b0 < end; b0 += kBatch) {
+        if (__syncthreads_count(done) == NT) break;
+        const int n = (int)min((int64_t)kBatch, end - b0);
+        for (int k = threadIdx.x; k < n; k += NT) {
+            const uint32_t id = (uint32_t)keys[b0 + k];
+            s_id[k] = id;
+            if (id < Ng) {
+                const float4* src = reinterpret_cast<const float4*>(G + id);
+                s_rec[k][0] = src[0]; s_rec[k][1] = src[1]; s_rec[k][2] = src[2];
+            } else {
+                const float4* src = reinterpret_cast<const float4*>(TR + (id - Ng));
+#pragma unroll
+                for (int q = 0; q < 10; ++q) s_rec[k][q] = src[q];
+            }
+        }
+        __syncthreads();
+        if (!done) {
+            for (int k = 0; k < n; ++k) {
+                const uint32_t id = s_id[k];
+                if (id < Ng) {
+                    const float4 q2 = s_rec[k][2];
+                    const uint32_t rx = __float_as_uint(q2.y), ry = __float_as_uint(q2.z);
+                    if (px < (int)(rx & 0xffff) || px > (int)(rx >> 16) || py < (int)(ry & 0xffff) || py > (int)(ry >> 16))
+                        continue;
+                    const float4 q0 = s_rec[k][0], q1 = s_rec[k][1];
+                    const float dx = qx - q0.x, dy = qy - q0.y;
+                    const float p2 = q0.z * dx * dx + q0.w * dx * dy + q1.x * dy * dy;
+                    const float alpha = fminf(kAlphaMax, q1.y * exp2f(p2));
+                    if (alpha < kAlphaMin) continue;
+                    const float w = alpha * st.T;
+                    st.C[0] += w * q1.z; st.C[1] += w * q1.w; st.C[2] += w * q2.x;
+                    st.T *= (1.f - alpha);
+                    if (mode == UMGS_BLEND_ENTITY_ALL) st.g_since *= (1.f - alpha);
+                    else st.in_ent = false;
+                } else {
+                    const TRec& t = *reinterpret_cast<const TRec*>(&s_rec[k][0]);
+                    long long E[3];
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) E[e] = (long long)t.A[e] * scx + (long long)t.B[e] * scy + t.C[e];
+                    int mask = 0;
+                    if (mode == UMGS_BLEND_DIRECT) {
+                        mask = (E[0] >= 0 && E[1] >= 0 && E[2] >= 0) ? 0xf : 0;
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int sdx = sample_dx(j), sdy = sample_dy(j);
+                            bool in = true;
+#pragma unroll
+                            for (int e = 0; e < 3; ++e) in = in && (E[e] + (long long)(t.A[e] * sdx + t.B[e] * sdy) >= 0);
+                            mask |= in ? (1 << j) : 0;
+                        }
+                    }
+                    if (mask == 0) continue;
+                    // attributes at the pixel centre: perspective-correct
+                    // barycentrics of the unsnapped triangle, clamped at 0
+                    float lam[3];
+#pragma unroll
+                    for (int e = 0; e < 3; ++e) {
+                        const int a = (e + 1) % 3, b = (e + 2) % 3;
+                        lam[e] = (t.u[a] - qx) * (t.v[b] - qy) - (t.u[b] - qx) * (t.v[a] - qy);
+                    }
+                    const float area = lam[0] + lam[1] + lam[2];
+                    float wv[3];
+                    if (area != 0.f) {
+                        const float ia = 1.f / area;
+#pragma unroll
+                        for (int e = 0; e < 3; ++e) wv[e] = fmaxf(lam[e] * ia, 0.f) * t.iz[e];
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 3; ++e) wv[e] = (1.f / 3.f) * t.iz[e];
+                    }
+                    const float ws = wv[0] + wv[1] + wv[2];
+                    if (ws > 0.f) { const float is = 1.f / ws; wv[0] *= is; wv[1] *= is; wv[2] *= is; }
+                    else { wv[0] = wv[1] = wv[2] = 1.f / 3.f; }
+                    float col[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) col[c] = wv[0] * t.col[c] + wv[1] * t.col[3 + c] + wv[2] * t.col[6 + c];
+                    float a = t.const_alpha ? t.alpha[0] : (wv[0] * t.alpha[0] + wv[1] * t.alpha[1] + wv[2] * t.alpha[2]);
+                    a = fminf(fmaxf(a, 0.f), 1.f);
+                    if (mode == UMGS_BLEND_DIRECT) {
+                        const float w = a * st.T;
+                        st.C[0] += w * col[0]; st.C[1] += w * col[1]; st.C[2] += w * col[2];
+                        st.T *= (1.f - a);
+                    } else if (mode == UMGS_BLEND_MSAA_ALL) {
+                        const float O = 0.25f * (float)__popc(mask);
+                        const float w = O * a * st.T;
+                        st.C[0] += w * col[0]; st.C[1] += w * col[1]; st.C[2] += w * col[2];
+                        st.T *= (1.f - O * a);
+                    } else {
+                        if (!st.in_ent) {
+                            st.Tin = st.T;
+                            st.t[0] = st.t[1] = st.t[2] = st.t[3] = 1.f;
+                            st.g_since = 1.f;
+                            st.in_ent = true;
+                        }
+                        float O = 0.f;
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) O += ((mask >> j) & 1) ? st.t[j] : 0.f;
+                        O *= 0.25f;
+                        const float w = st.Tin * O * a;
+                        st.C[0] += w * col[0]; st.C[1] += w * col[1]; st.C[2] += w * col[2];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+                            if ((mask >> j) & 1) st.t[j] *= (1.f - a);
+                        const float tm = 0.25f * ((st.t[0] + st.t[1]) + (st.t[2] + st.t[3]));
+                        st.T = (mode == UMGS_BLEND_ENTITY_ALL) ? st.Tin * tm * st.g_since : st.Tin * tm;
+                    }
+                }
+                last = (int)(b0 - beg) + k + 1;
+                if (st.T < t_eps) { done = true; break; }
+            }
+        }
+    }
+    if (inside) {
+        const int64_t pix = ((int64_t)cam * H + py) * W + px;
+        out[pix] = make_float4(st.C[0] + st.T * bg0, st.C[1] + st.T * bg1, st.C[2] + st.T * bg2, st.T);
+        if (out_last) out_last[pix] = last;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// frame inspection: split sorted keys into ids / depth bits
+
+__global__ void split_keys_kernel(const uint64_t* __restrict__ keys, int64_t n, int32_t* __restrict__ ids,
+                                  uint32_t* __restrict__ dbits) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint64_t k = keys[i];
+    ids[i] = (int32_t)(uint32_t)k;
+    dbits[i] = (uint32_t)(k >> 32);
+}
+
+// ---------------------------------------------------------------------------
+// host orchestration
+
+static inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
+
+umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_mesh* meshes, int32_t nmeshes,
+                           const umgs_camera* cams, int32_t ncams, const umgs_render_opts& opts, float* out_rgbt,
+                           umgs_frame* fr, cudaStream_t stream) {
+    const int ts = opts.tile_size;
+    const int W = cams[0].width, H = cams[0].height;
+    const int tiles_x = (W + ts - 1) / ts, tiles_y = (H + ts - 1) / ts;
+    const int tiles_per_cam = tiles_x * tiles_y;
+    const int64_t M = (int64_t)tiles_per_cam * ncams;
+    const int64_t Ng = g ? g->n : 0;
+    int64_t Nt = 0;
+    fr->mesh_offset.clear();
+    for (int m = 0; m < nmeshes; ++m) { fr->mesh_offset.push_back(Ng + Nt); Nt += meshes[m].nf; }
+    const int64_t Ntot = Ng + Nt;
+    if (Ntot >= (int64_t)0xffffffffLL) return fail(ctx, UMGS_ERR_INVALID_ARG, "too many primitives (ids are 32-bit)");
+    if (M >= (int64_t)1 << 31) return fail(ctx, UMGS_ERR_INVALID_ARG, "too many tiles");
+    fr->valid = false;
+    fr->ng = Ng; fr->nt = Nt; fr->ncams = ncams; fr->W = W; fr->H = H;
+    fr->tile = ts; fr->tiles_x = tiles_x; fr->tiles_y = tiles_y; fr->num_tiles = M;
+    fr->blend_mode = opts.blend_mode; fr->t_eps = opts.t_eps;
+    fr->bg[0] = opts.bg[0]; fr->bg[1] = opts.bg[1]; fr->bg[2] = opts.bg[2];
+
+    cudaError_t e;
+#define UMGS_TRY(x)                                                   \
+    do {                                                              \
+        e = (x);                                                      \
+        if (e == cudaErrorMemoryAllocation) {                         \
+            cudaGetLastError();                                       \
+            return fail(ctx, UMGS_ERR_OUT_OF_MEMORY, #x);             \
+        }                                                             \
+        if (e != cudaSuccess) return cuda_fail(ctx, e, #x);           \
+    } while (0)
+
+    UMGS_TRY(fr->cams.reserve(sizeof(DevCam) * ncams));
+    UMGS_TRY(fr->grec.reserve(sizeof(GRec) * std::max<int64_t>(1, Ng * ncams)));
+    UMGS_TRY(fr->trec.reserve(sizeof(TRec) * std::max<int64_t>(1, Nt * ncams)));
+    UMGS_TRY(fr->bin.reserve(sizeof(BinInfo) * std::max<int64_t>(1, Ntot * ncams)));
+    UMGS_TRY(fr->tile_count.reserve(sizeof(int32_t) * (M + 1)));
+    UMGS_TRY(fr->tile_fill.reserve(sizeof(int32_t) * (M + 1)));
+    UMGS_TRY(fr->tile_off.reserve(sizeof(int64_t) * (M + 1)));
+    UMGS_TRY(fr->status.reserve(sizeof(int32_t) * 4));
+
+    // cameras: host -> pinned staging -> device
+    std::vector<DevCam> dc(ncams);
+    for (int c = 0; c < ncams; ++c) {
+        const umgs_camera& cm = cams[c];
+        DevCam& d = dc[c];
+        for (int r = 0; r < 3; ++r) {
+            for (int k = 0; k < 3; ++k) d.R[3 * r + k] = cm.viewmat[4 * r + k];
+            d.t[r] = cm.viewmat[4 * r + 3];
+        }
+        d.fx = cm.fx; d.fy = cm.fy; d.cx = cm.cx; d.cy = cm.cy;
+        d.W = cm.width; d.H = cm.height; d.near_z = cm.near_z;
+        for (int k = 0; k < 3; ++k) {
+            double s = 0;
+            for (int r = 0; r < 3; ++r) s -= (double)cm.viewmat[4 * r + k] * (double)cm.viewmat[4 * r + 3];
+            d.campos[k] = (float)s;
+        }
+        d.pad = 0;
+    }
+    UMGS_TRY(cudaMemcpyAsync(fr->cams.ptr, dc.data(), sizeof(DevCam) * ncams, cudaMemcpyHostToDevice, stream));
+    UMGS_TRY(cudaMemsetAsync(fr->tile_count.ptr, 0, sizeof(int32_t) * (M + 1), stream));
+    UMGS_TRY(cudaMemsetAsync(fr->status.ptr, 0, sizeof(int32_t) * 4, stream));
+
+    const DevCam* dcams = fr->cams.as<DevCam>();
+    if (Ng > 0) {
+        project_gaussians_kernel<<<grid_for(Ng, 256), 256, 0, stream>>>(
+            g->means, g->quats, g->scales, g->opacities, g->sh, g->sh_dtype, g->sh_degree, g->cov3d, Ng, dcams,
+            ncams, ts, tiles_x, tiles_per_cam, fr->grec.as<GRec>(), fr->bin.as<BinInfo>(), Ntot,
+            fr->tile_count.as<int32_t>());
+        UMGS_TRY(cudaGetLastError());
+    }
+    int64_t tri_base = 0;
+    for (int m = 0; m < nmeshes; ++m) {
+        const umgs_mesh& me = meshes[m];
+        if (me.nf > 0) {
+            setup_triangles_kernel<<<grid_for(me.nf, 256), 256, 0, stream>>>(
+                me.verts, me.faces, me.vcolor, me.valpha, me.falpha, me.nv, me.nf, tri_base, Nt, Ng + tri_base,
+                dcams, ncams, ts, tiles_x, tiles_per_cam, fr->trec.as<TRec>(), fr->bin.as<BinInfo>(), Ntot,
+                fr->tile_count.as<int32_t>(), fr->status.as<int32_t>());
+            UMGS_TRY(cudaGetLastError());
+        }
+        tri_base += me.nf;
+    }
+    scan_tiles_kernel<<<1, 1024, 0, stream>>>(fr->tile_count.as<int32_t>(), M, fr->tile_off.as<int64_t>());
+    UMGS_TRY(cudaGetLastError());
+    // read back the key count (and the status word)
+    UMGS_TRY(cudaMemcpyAsync(ctx->pinned, fr->tile_off.as<int64_t>() + M, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                             stream));
+    UMGS_TRY(cudaMemcpyAsync(ctx->pinned + 1, fr->status.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+    UMGS_TRY(cudaStreamSynchronize(stream));
+    const int64_t K = ctx->pinned[0];
+    const int32_t st = (int32_t)(ctx->pinned[1] & 0xffffffff);
+    if (st & 1) return fail(ctx, UMGS_ERR_INVALID_ARG, "a face index is out of range");
+    fr->num_keys = K;
+    UMGS_TRY(fr->keys.reserve(sizeof(uint64_t) * std::max<int64_t>(1, K)));
+    UMGS_TRY(fr->keys_tmp.reserve(sizeof(uint64_t) * std::max<int64_t>(1, K)));
+    UMGS_TRY(cudaMemsetAsync(fr->tile_fill.ptr, 0, sizeof(int32_t) * (M + 1), stream));
+    if (Ntot > 0) {
+        scatter_keys_kernel<<<grid_for(Ntot * ncams, 256), 256, 0, stream>>>(
+            fr->bin.as<BinInfo>(), Ntot, ncams, ts, tiles_x, tiles_per_cam, fr->tile_off.as<int64_t>(),
+            fr->tile_fill.as<int32_t>(), fr->keys.as<uint64_t>());
+        UMGS_TRY(cudaGetLastError());
+    }
+    sort_tiles_kernel<<<(unsigned)M, kSortThreads, kSortCap * sizeof(uint64_t), stream>>>(
+        fr->keys.as<uint64_t>(), fr->keys_tmp.as<uint64_t>(), fr->tile_off.as<int64_t>());
+    UMGS_TRY(cudaGetLastError());
+    UMGS_TRY(fr->last.reserve(sizeof(int32_t) * (int64_t)ncams * W * H));
+    const float te = opts.t_eps > 0.f ? opts.t_eps : -1.f;
+    float4* out = reinterpret_cast<float4*>(out_rgbt);
+    int32_t* last = fr->last.as<int32_t>();
+    if (ts == 16)
+        composite_kernel<16><<<(unsigned)M, 256, 0, stream>>>(
+            fr->keys.as<uint64_t>(), fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->trec.as<TRec>(), Ng, Nt,
+            tiles_x, tiles_per_cam, W, H, te, opts.bg[0], opts.bg[1], opts.bg[2], opts.blend_mode, out, last);
+    else if (ts == 8)
+        composite_kernel<8><<<(unsigned)M, 64, 0, stream>>>(
+            fr->keys.as<uint64_t>(), fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->trec.as<TRec>(), Ng, Nt,
+            tiles_x, tiles_per_cam, W, H, te, opts.bg[0], opts.bg[1], opts.bg[2], opts.blend_mode, out, last);
+    else
+        composite_kernel<32><<<(unsigned)M, 1024, 0, stream>>>(
+            fr->keys.as<uint64_t>(), fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->trec.as<TRec>(), Ng, Nt,
+            tiles_x, tiles_per_cam, W, H, te, opts.bg[0], opts.bg[1], opts.bg[2], opts.blend_mode, out, last);
+    UMGS_TRY(cudaGetLastError());
+    fr->valid = true;
+#undef UMGS_TRY
+    return UMGS_OK;
+}
+
+umgs_status frame_lists(const umgs_frame* fr, int64_t* tile_ptr, int32_t* ids, uint32_t* dbits, cudaStream_t stream) {
+    cudaError_t e = cudaMemcpyAsync(tile_ptr, fr->tile_off.ptr, sizeof(int64_t) * (fr->num_tiles + 1),
+                                    cudaMemcpyDeviceToDevice, stream);
+    if (e != cudaSuccess) return cuda_fail(fr->ctx, e, "cudaMemcpyAsync(tile_ptr)");
+    if (fr->num_keys > 0) {
+        split_keys_kernel<<<grid_for(fr->num_keys, 256), 256, 0, stream>>>(fr->keys.as<uint64_t>(), fr->num_keys, ids,
+                                                                            dbits);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(fr->ctx, e, "split_keys_kernel");
+    }
+    return UMGS_OK;
+}
+
+}  // namespace umgs

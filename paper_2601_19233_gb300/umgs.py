@@ -1,0 +1,249 @@
+"""Thin Python binding of libumgs (ctypes).  Argument marshalling only: every
+step of rendering, binding and deformation runs in the CUDA library.
+
+PyTorch provides device memory and the current CUDA stream; tensors are
+passed as raw device pointers.  If the library is missing the import of the
+entry points raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libumgs.so")
+
+OK = 0
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CAPACITY", 4: "CUDA", 5: "TIMEOUT",
+          6: "NOT_IMPLEMENTED"}
+BLEND_FULL, BLEND_DIRECT, BLEND_MSAA_ALL, BLEND_ENTITY_ALL = 0, 1, 2, 3
+F32, BF16 = 0, 1
+BIND_BBX, BIND_CENTER, BIND_NEAREST = 0, 1, 2
+DEFORM_FRAME, DEFORM_LITERAL = 0, 1
+
+
+class UmgsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("umgs %s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class CGaussians(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("quats", ctypes.c_void_p), ("scales", ctypes.c_void_p),
+                ("opacities", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("cov3d", ctypes.c_void_p),
+                ("n", ctypes.c_int64), ("sh_degree", ctypes.c_int32), ("sh_dtype", ctypes.c_int32)]
+
+
+class CMesh(ctypes.Structure):
+    _fields_ = [("verts", ctypes.c_void_p), ("faces", ctypes.c_void_p), ("vcolor", ctypes.c_void_p),
+                ("valpha", ctypes.c_void_p), ("falpha", ctypes.c_void_p), ("nv", ctypes.c_int64),
+                ("nf", ctypes.c_int64)]
+
+
+class CCamera(ctypes.Structure):
+    _fields_ = [("viewmat", ctypes.c_float * 12), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
+                ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("near_z", ctypes.c_float)]
+
+
+class CRenderOpts(ctypes.Structure):
+    _fields_ = [("tile_size", ctypes.c_int32), ("blend_mode", ctypes.c_int32), ("t_eps", ctypes.c_float),
+                ("bg", ctypes.c_float * 3), ("flags", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libumgs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libumgs.so not found at %s: run __graft_entry__.build() "
+                               "(there is no CPU fallback)" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.umgs_ctx_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
+        L.umgs_ctx_destroy.argtypes = [vp]
+        L.umgs_last_error.argtypes = [vp]
+        L.umgs_last_error.restype = ctypes.c_char_p
+        L.umgs_default_render_opts.argtypes = [ctypes.POINTER(CRenderOpts)]
+        L.umgs_frame_create.argtypes = [vp, ctypes.POINTER(vp)]
+        L.umgs_frame_destroy.argtypes = [vp]
+        L.umgs_render.argtypes = [vp, ctypes.POINTER(CGaussians), ctypes.POINTER(CMesh), i32,
+                                  ctypes.POINTER(CCamera), i32, ctypes.POINTER(CRenderOpts), vp, vp, vp]
+        L.umgs_frame_counts.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        L.umgs_frame_lists.argtypes = [vp, vp, vp, vp, vp]
+        for name in ("umgs_ctx_create", "umgs_frame_create", "umgs_render", "umgs_frame_counts",
+                     "umgs_frame_lists"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "tensor must be a contiguous CUDA tensor"
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """A libumgs context on one device (owns workspace)."""
+
+    def __init__(self, device=0):
+        self._h = ctypes.c_void_p()
+        self.device = device
+        st = lib().umgs_ctx_create(ctypes.byref(self._h), int(device))
+        if st != OK:
+            raise UmgsError(st, "umgs_ctx_create(device=%d)" % device)
+
+    def check(self, st, what):
+        if st != OK:
+            msg = lib().umgs_last_error(self._h)
+            raise UmgsError(st, "%s: %s" % (what, msg.decode() if msg else ""))
+
+    def close(self):
+        if self._h:
+            lib().umgs_ctx_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Frame:
+    """Saved state of one render (sorted lists, records, per-pixel state)."""
+
+    def __init__(self, ctx: Context):
+        self.ctx = ctx
+        self._h = ctypes.c_void_p()
+        ctx.check(lib().umgs_frame_create(ctx._h, ctypes.byref(self._h)), "umgs_frame_create")
+
+    def counts(self):
+        k, t = ctypes.c_int64(), ctypes.c_int64()
+        self.ctx.check(lib().umgs_frame_counts(self._h, ctypes.byref(k), ctypes.byref(t)), "umgs_frame_counts")
+        return k.value, t.value
+
+    def lists(self):
+        """(tile_ptr int64 [T+1], ids int32 [K], dbits int32 [K] (uint32 bits)) on the device."""
+        k, t = self.counts()
+        dev = torch.device("cuda", self.ctx.device)
+        ptr = torch.empty(t + 1, dtype=torch.int64, device=dev)
+        ids = torch.empty(max(k, 1), dtype=torch.int32, device=dev)
+        db = torch.empty(max(k, 1), dtype=torch.int32, device=dev)
+        self.ctx.check(lib().umgs_frame_lists(self._h, _ptr(ptr), _ptr(ids), _ptr(db), _stream()),
+                       "umgs_frame_lists")
+        return ptr, ids[:k], db[:k]
+
+    def __del__(self):
+        try:
+            if self._h:
+                lib().umgs_frame_destroy(self._h)
+        except Exception:
+            pass
+
+
+# ----------------------------------------------------------------------------
+# device-side scene containers (plain tensors)
+
+@dataclass
+class DevGaussians:
+    means: torch.Tensor
+    quats: torch.Tensor
+    scales: torch.Tensor
+    opacities: torch.Tensor
+    sh: torch.Tensor
+    sh_degree: int
+    cov3d: torch.Tensor | None = None
+
+    @property
+    def n(self):
+        return int(self.means.shape[0])
+
+    def c(self):
+        dtype = BF16 if self.sh.dtype == torch.bfloat16 else F32
+        return CGaussians(_ptr(self.means), _ptr(self.quats), _ptr(self.scales), _ptr(self.opacities),
+                          _ptr(self.sh), _ptr(self.cov3d), self.n, int(self.sh_degree), dtype)
+
+
+@dataclass
+class DevMesh:
+    verts: torch.Tensor
+    faces: torch.Tensor
+    vcolor: torch.Tensor
+    valpha: torch.Tensor | None = None
+    falpha: torch.Tensor | None = None
+
+    def c(self):
+        return CMesh(_ptr(self.verts), _ptr(self.faces), _ptr(self.vcolor), _ptr(self.valpha), _ptr(self.falpha),
+                     int(self.verts.shape[0]), int(self.faces.shape[0]))
+
+
+def camera_struct(cam) -> CCamera:
+    c = CCamera()
+    vm = np.asarray(cam.viewmat, np.float32).reshape(12)
+    for k in range(12):
+        c.viewmat[k] = float(vm[k])
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height, c.near_z = int(cam.width), int(cam.height), float(cam.near)
+    return c
+
+
+def _t(a, device, dtype=None):
+    if a is None:
+        return None
+    t = torch.as_tensor(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.to(device).contiguous()
+
+
+def gaussians_to_device(g, device="cuda", sh_dtype=torch.float32) -> DevGaussians:
+    return DevGaussians(_t(g.means, device), _t(g.quats, device), _t(g.scales, device), _t(g.opacities, device),
+                        _t(g.sh, device, sh_dtype), g.sh_degree)
+
+
+def mesh_to_device(m, device="cuda") -> DevMesh:
+    return DevMesh(_t(m.verts, device), _t(m.faces.astype(np.int32), device), _t(m.vcolor, device),
+                   _t(m.valpha, device), _t(m.falpha, device))
+
+
+def render_opts(tile_size=16, blend_mode=BLEND_FULL, t_eps=1e-4, bg=(0.0, 0.0, 0.0)) -> CRenderOpts:
+    o = CRenderOpts()
+    lib().umgs_default_render_opts(ctypes.byref(o))
+    o.tile_size = int(tile_size)
+    o.blend_mode = int(blend_mode)
+    o.t_eps = float(t_eps)
+    for k in range(3):
+        o.bg[k] = float(bg[k])
+    return o
+
+
+def render(ctx: Context, gaussians: DevGaussians | None, meshes, cameras, opts: CRenderOpts | None = None,
+           out: torch.Tensor | None = None, frame: Frame | None = None, stream=None) -> torch.Tensor:
+    """umgs_render: returns [ncams, H, W, 4] float32 (RGB, T) on the device."""
+    cams = (CCamera * len(cameras))(*[camera_struct(c) for c in cameras])
+    H, W = int(cameras[0].height), int(cameras[0].width)
+    dev = torch.device("cuda", ctx.device)
+    if out is None:
+        out = torch.empty((len(cameras), H, W, 4), dtype=torch.float32, device=dev)
+    cm = (CMesh * max(1, len(meshes)))(*[m.c() for m in meshes]) if meshes else None
+    cg = gaussians.c() if gaussians is not None else None
+    st = lib().umgs_render(ctx._h, ctypes.byref(cg) if cg is not None else None, cm, len(meshes), cams,
+                           len(cameras), ctypes.byref(opts) if opts is not None else None, _ptr(out),
+                           frame._h if frame is not None else None, _stream(stream))
+    ctx.check(st, "umgs_render")
+    return out
