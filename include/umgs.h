@@ -106,6 +106,10 @@ umgs_status umgs_ctx_create(umgs_ctx** out, int device);
 void umgs_ctx_destroy(umgs_ctx* ctx);
 /* Last error message of this context ("" after success). */
 const char* umgs_last_error(const umgs_ctx* ctx);
+/* Synchronise `stream` and report any error a kernel of this context
+ * detected on the device since the previous umgs_ctx_sync (deferred
+ * argument errors of asynchronous calls such as umgs_deform). */
+umgs_status umgs_ctx_sync(umgs_ctx* ctx, void* stream);
 /* Default render options (tile 16, FULL, t_eps 1e-4, black background). */
 void umgs_default_render_opts(umgs_render_opts* opts);
 
@@ -155,6 +159,57 @@ umgs_status umgs_frame_counts(const umgs_frame* frame, int64_t* num_keys, int64_
  * bits; each list in ascending (depth bits, id).  Asynchronous on stream. */
 umgs_status umgs_frame_lists(const umgs_frame* frame, int64_t* tile_ptr, int32_t* ids,
                              uint32_t* dbits, void* stream);
+
+/* ---- deformation transfer (Sec. 3.3, Eq. 12-13) ---------------------------
+ *
+ * Per proxy face f: deformation gradient D_f = F'_f F_f^-1 with the frame
+ * F = [e1, e2, n/sqrt(|n|)] (e1 = v1-v0, e2 = v2-v0, n = e1 x e2; the inverse
+ * is taken in fp64 for sliver faces).  Per proxy vertex: D_v = rest-area-
+ * weighted mean of the incident D_f, polar D_v = R_v S_v (a proper rotation;
+ * for det D_v < 0 the smallest singular direction is flipped), r_v = log R_v
+ * (axis-angle, angle in [0, pi]), Delta_v = V'_v - V_v.
+ * Per Gaussian, for each of its 8 bound points P_i (face[i], barycentrics
+ * (1-b1-b2, b1, b2) on the face's vertices 0,1,2): Delta_i, r_i, S_i by
+ * barycentric interpolation (Eq. 12); R' = exp(mean r_i), S' = mean S_i
+ * (Eq. 13); Sigma' = (R'S') Sigma (R'S')^T; q' = quat(R') * q (w >= 0);
+ * mu' = mu + mean Delta_i (mode LITERAL, Eq. 13 as printed) or
+ * mu' = mu + mean Delta_i + (R'S' - I)(mu - mean P_i) (mode FRAME, default:
+ * exact for rigid motions and uniform scalings of the proxy).
+ *
+ * rest       Gaussians at rest (means, quats, scales or cov3d; n); SH/opacity unused
+ * face       [n,8] int32 proxy face per bound point (from umgs_bind)
+ * bary       [n,8,2] float (b1, b2) per bound point (from umgs_bind)
+ * proxy_v    [nv,3] rest proxy vertices; proxy_vd [nv,3] deformed vertices
+ * proxy_f    [nf,3] int32 proxy faces
+ * out_means  [n,3]; out_cov3d [n,6] (xx,xy,xz,yy,yz,zz); out_quats [n,4] (nullable)
+ * Asynchronous.  Errors: INVALID_ARG (NULL arrays, nv < 3 or nf < 1, bad
+ * mode), OUT_OF_MEMORY, CUDA.  A face id outside [0,nf) or a proxy vertex
+ * index outside [0,nv) is detected on the device: the affected outputs are
+ * NaN and the next umgs_ctx_sync reports INVALID_ARG.
+ */
+umgs_status umgs_deform(umgs_ctx* ctx, const umgs_gaussians* rest, const int32_t* face, const float* bary,
+                        const float* proxy_v, const float* proxy_vd, const int32_t* proxy_f, int64_t nv,
+                        int64_t nf, int32_t mode, float* out_means, float* out_cov3d, float* out_quats,
+                        void* stream);
+
+/* The per-vertex transform table of the last umgs_deform call, copied to a
+ * caller buffer [nv,12] (Delta xyz, r xyz, S xx xy xz yy yz zz).  Async. */
+umgs_status umgs_deform_vertex_table(umgs_ctx* ctx, float* out_table, int64_t nv, void* stream);
+
+/* ---- per-stage timing ------------------------------------------------------
+ * When enabled, every stage launched by this context is bracketed by CUDA
+ * events recorded on the stream it runs on.  umgs_profile_read synchronises
+ * those events, returns per stage the summed milliseconds and the number of
+ * launches since the last read (host arrays of UMGS_NUM_STAGES), and clears
+ * the record.  Stages: */
+enum {
+    UMGS_STAGE_PROJECT_GAUSSIANS = 0, UMGS_STAGE_SETUP_TRIANGLES, UMGS_STAGE_SCAN, UMGS_STAGE_SCATTER,
+    UMGS_STAGE_SORT, UMGS_STAGE_COMPOSITE, UMGS_STAGE_DEFORM_FACES, UMGS_STAGE_DEFORM_VERTICES,
+    UMGS_STAGE_DEFORM_GAUSSIANS, UMGS_STAGE_BIND_GRID, UMGS_STAGE_BIND_RAYCAST, UMGS_STAGE_BIND_NEAREST,
+    UMGS_STAGE_BACKWARD_COMPOSITE, UMGS_STAGE_BACKWARD_PROJECT, UMGS_NUM_STAGES = 16
+};
+umgs_status umgs_profile_enable(umgs_ctx* ctx, int32_t on);
+umgs_status umgs_profile_read(umgs_ctx* ctx, double* ms, int64_t* launches);
 
 #ifdef __cplusplus
 }

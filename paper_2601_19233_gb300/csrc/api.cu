@@ -38,6 +38,11 @@ umgs_status umgs_ctx_create(umgs_ctx** out, int device) {
         return UMGS_ERR_OUT_OF_MEMORY;
     }
     cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (c->dstatus.reserve(16) != cudaSuccess || cudaMemset(c->dstatus.ptr, 0, 16) != cudaSuccess) {
+        cudaFreeHost(c->pinned);
+        delete c;
+        return UMGS_ERR_OUT_OF_MEMORY;
+    }
     c->default_frame = new umgs_frame();
     c->default_frame->ctx = c;
     *out = c;
@@ -53,10 +58,55 @@ void umgs_ctx_destroy(umgs_ctx* ctx) {
         delete ctx->default_frame;
     }
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    for (auto& r : ctx->prof.recs) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : ctx->prof.pool) cudaEventDestroy(e);
+    ctx->dstatus.release();
+    ctx->vacc.release();
+    ctx->vtab.release();
+    ctx->bind_ws.release();
     delete ctx;
 }
 
 const char* umgs_last_error(const umgs_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+umgs_status umgs_ctx_sync(umgs_ctx* ctx, void* stream) {
+    if (!ctx) return UMGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(ctx->pinned, ctx->dstatus.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "umgs_ctx_sync");
+    const int32_t st = (int32_t)(ctx->pinned[0] & 0xffffffff);
+    if (st != 0) {
+        cudaMemsetAsync(ctx->dstatus.ptr, 0, sizeof(int32_t), s);
+        cudaStreamSynchronize(s);
+        return fail(ctx, UMGS_ERR_INVALID_ARG, "a kernel saw an out-of-range face or vertex index (status " +
+                                                   std::to_string(st) + ")");
+    }
+    return UMGS_OK;
+}
+
+umgs_status umgs_profile_enable(umgs_ctx* ctx, int32_t on) {
+    if (!ctx) return UMGS_ERR_INVALID_ARG;
+    ctx->prof.on = on != 0;
+    return UMGS_OK;
+}
+
+umgs_status umgs_profile_read(umgs_ctx* ctx, double* ms, int64_t* launches) {
+    if (!ctx || !ms || !launches) return UMGS_ERR_INVALID_ARG;
+    for (int k = 0; k < UMGS_NUM_STAGES; ++k) { ms[k] = 0.0; launches[k] = 0; }
+    umgs_status st = UMGS_OK;
+    for (auto& r : ctx->prof.recs) {
+        float t = 0.f;
+        if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess)
+            st = fail(ctx, UMGS_ERR_CUDA, "cudaEventElapsedTime");
+        if (r.stage >= 0 && r.stage < UMGS_NUM_STAGES) { ms[r.stage] += t; launches[r.stage] += 1; }
+        ctx->prof.pool.push_back(r.a);
+        ctx->prof.pool.push_back(r.b);
+    }
+    ctx->prof.recs.clear();
+    return st;
+}
 
 void umgs_default_render_opts(umgs_render_opts* o) {
     if (!o) return;
@@ -128,6 +178,37 @@ umgs_status umgs_render(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_mesh*
     std::memset(&empty, 0, sizeof(empty));
     return render_forward(ctx, g ? g : &empty, meshes, nmeshes, cams, ncams, opts, out_rgbt, fr,
                           static_cast<cudaStream_t>(stream));
+}
+
+umgs_status umgs_deform(umgs_ctx* ctx, const umgs_gaussians* rest, const int32_t* face, const float* bary,
+                        const float* proxy_v, const float* proxy_vd, const int32_t* proxy_f, int64_t nv,
+                        int64_t nf, int32_t mode, float* out_means, float* out_cov3d, float* out_quats,
+                        void* stream) {
+    if (!ctx) return UMGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, UMGS_ERR_CUDA, "cudaSetDevice");
+    if (!rest || rest->n < 0) return fail(ctx, UMGS_ERR_INVALID_ARG, "rest Gaussians missing");
+    if (mode != UMGS_DEFORM_FRAME && mode != UMGS_DEFORM_LITERAL) return fail(ctx, UMGS_ERR_INVALID_ARG, "bad mode");
+    if (!proxy_v || !proxy_vd || !proxy_f || nv < 3 || nf < 1) return fail(ctx, UMGS_ERR_INVALID_ARG, "bad proxy mesh");
+    if (rest->n > 0) {
+        if (!rest->means || !face || !bary || !out_means || !out_cov3d)
+            return fail(ctx, UMGS_ERR_INVALID_ARG, "NULL array");
+        if (!rest->cov3d && (!rest->quats || !rest->scales))
+            return fail(ctx, UMGS_ERR_INVALID_ARG, "need quats+scales or cov3d");
+        if ((reinterpret_cast<uintptr_t>(face) | reinterpret_cast<uintptr_t>(bary)) & 15)
+            return fail(ctx, UMGS_ERR_INVALID_ARG, "face and bary must be 16-byte aligned");
+    }
+    return deform_forward(ctx, rest, face, bary, proxy_v, proxy_vd, proxy_f, nv, nf, mode, out_means, out_cov3d,
+                          out_quats, static_cast<cudaStream_t>(stream));
+}
+
+umgs_status umgs_deform_vertex_table(umgs_ctx* ctx, float* out_table, int64_t nv, void* stream) {
+    if (!ctx || !out_table) return UMGS_ERR_INVALID_ARG;
+    if (nv != ctx->vtab_rows || nv <= 0) return fail(ctx, UMGS_ERR_INVALID_ARG, "nv differs from the last umgs_deform");
+    cudaError_t e = cudaMemcpyAsync(out_table, ctx->vtab.ptr, sizeof(float) * 12 * nv, cudaMemcpyDeviceToDevice,
+                                    static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpyAsync");
+    return UMGS_OK;
 }
 
 umgs_status umgs_frame_counts(const umgs_frame* frame, int64_t* num_keys, int64_t* num_tiles) {

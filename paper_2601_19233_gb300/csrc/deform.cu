@@ -1,0 +1,394 @@
+// Deformation transfer from the proxy mesh to the Gaussians (Sec. 3.3, Eq. 12-13).
+//
+//   face_gradients   one thread per proxy face: D_f = F'_f F_f^-1 with the
+//                    frame F = [e1, e2, n / sqrt(|n|)] (fp64 inverse for
+//                    sliver faces); area-weighted accumulation into the
+//                    three vertices (atomics).
+//   vertex_xforms    one thread per proxy vertex: D_v = sum / area, polar
+//                    D_v = R_v S_v (Jacobi eigen-decomposition of D^T D),
+//                    r_v = log R_v, Delta_v = V'_v - V_v -> a 48-byte row of
+//                    the vertex table (stays in L2: 10K vertices = 0.5 MB).
+//   deform_gaussians one thread per Gaussian: 8 bound points x 3 vertex rows
+//                    gathered from the table, Eq. 12 interpolation, Eq. 13
+//                    averaging, R' = exp(mean r), Sigma' = A Sigma A^T with
+//                    A = R'S', mu' (FRAME or LITERAL), q' = quat(R') q.
+//                    Streams 136 B in and 52 B out per Gaussian.
+#include <cmath>
+
+#include "internal.h"
+
+namespace umgs {
+
+constexpr int kStatusBadIndex = 2;
+
+// ---- small 3x3 helpers (row-major) ---------------------------------------
+
+__device__ __forceinline__ void cross3(const float a[3], const float b[3], float c[3]) {
+    c[0] = a[1] * b[2] - a[2] * b[1];
+    c[1] = a[2] * b[0] - a[0] * b[2];
+    c[2] = a[0] * b[1] - a[1] * b[0];
+}
+__device__ __forceinline__ float dot3(const float a[3], const float b[3]) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+// columns e1, e2, n/sqrt(|n|) of the face frame; returns |n|
+__device__ float face_frame(const float a[3], const float b[3], const float c[3], float F[9]) {
+    float e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    float e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+    float n[3];
+    cross3(e1, e2, n);
+    const float nn = sqrtf(dot3(n, n));
+    const float s = nn > 0.f ? rsqrtf(nn) : 0.f;
+    for (int r = 0; r < 3; ++r) {
+        F[3 * r + 0] = e1[r];
+        F[3 * r + 1] = e2[r];
+        F[3 * r + 2] = n[r] * s;
+    }
+    return nn;
+}
+
+__device__ bool inv3(const float M[9], float I[9]) {
+    const float c00 = M[4] * M[8] - M[5] * M[7], c01 = M[5] * M[6] - M[3] * M[8], c02 = M[3] * M[7] - M[4] * M[6];
+    const float det = M[0] * c00 + M[1] * c01 + M[2] * c02;
+    if (!(fabsf(det) > 0.f)) return false;
+    const float id = 1.f / det;
+    I[0] = c00 * id; I[1] = (M[2] * M[7] - M[1] * M[8]) * id; I[2] = (M[1] * M[5] - M[2] * M[4]) * id;
+    I[3] = c01 * id; I[4] = (M[0] * M[8] - M[2] * M[6]) * id; I[5] = (M[2] * M[3] - M[0] * M[5]) * id;
+    I[6] = c02 * id; I[7] = (M[1] * M[6] - M[0] * M[7]) * id; I[8] = (M[0] * M[4] - M[1] * M[3]) * id;
+    return true;
+}
+
+__device__ bool inv3_fp64(const float Mf[9], float I[9]) {
+    double M[9];
+    for (int k = 0; k < 9; ++k) M[k] = Mf[k];
+    const double c00 = M[4] * M[8] - M[5] * M[7], c01 = M[5] * M[6] - M[3] * M[8], c02 = M[3] * M[7] - M[4] * M[6];
+    const double det = M[0] * c00 + M[1] * c01 + M[2] * c02;
+    if (!(fabs(det) > 0.0)) return false;
+    const double id = 1.0 / det;
+    I[0] = (float)(c00 * id); I[1] = (float)((M[2] * M[7] - M[1] * M[8]) * id); I[2] = (float)((M[1] * M[5] - M[2] * M[4]) * id);
+    I[3] = (float)(c01 * id); I[4] = (float)((M[0] * M[8] - M[2] * M[6]) * id); I[5] = (float)((M[2] * M[3] - M[0] * M[5]) * id);
+    I[6] = (float)(c02 * id); I[7] = (float)((M[1] * M[6] - M[0] * M[7]) * id); I[8] = (float)((M[0] * M[4] - M[1] * M[3]) * id);
+    return true;
+}
+
+__device__ __forceinline__ void matmul3(const float A[9], const float B[9], float C[9]) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) C[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] + A[3 * i + 2] * B[6 + j];
+}
+
+// ---- K1a: per-face deformation gradients ----------------------------------
+
+__global__ void __launch_bounds__(256) face_gradients_kernel(const float* __restrict__ V, const float* __restrict__ Vd,
+                                                             const int32_t* __restrict__ F, int64_t nv, int64_t nf,
+                                                             float* __restrict__ vacc, int32_t* __restrict__ status) {
+    const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    const int i0 = F[3 * f], i1 = F[3 * f + 1], i2 = F[3 * f + 2];
+    if (i0 < 0 || i0 >= nv || i1 < 0 || i1 >= nv || i2 < 0 || i2 >= nv) { atomicOr(status, kStatusBadIndex); return; }
+    const int idx[3] = {i0, i1, i2};
+    float P[3][3], Q[3][3];
+    for (int k = 0; k < 3; ++k)
+        for (int d = 0; d < 3; ++d) { P[k][d] = V[3 * (int64_t)idx[k] + d]; Q[k][d] = Vd[3 * (int64_t)idx[k] + d]; }
+    float Fr[9], Fd[9], Fi[9], D[9];
+    const float nn = face_frame(P[0], P[1], P[2], Fr);
+    face_frame(Q[0], Q[1], Q[2], Fd);
+    if (!(nn > 0.f)) return;  // degenerate rest face: zero weight
+    // sliver: |n| = |e1||e2| sin(angle); invert in fp64 when sin < 1e-3
+    const float l1 = sqrtf(Fr[0] * Fr[0] + Fr[3] * Fr[3] + Fr[6] * Fr[6]);
+    const float l2 = sqrtf(Fr[1] * Fr[1] + Fr[4] * Fr[4] + Fr[7] * Fr[7]);
+    const bool ok = (nn < 1e-3f * l1 * l2) ? inv3_fp64(Fr, Fi) : inv3(Fr, Fi);
+    if (!ok) return;
+    matmul3(Fd, Fi, D);
+    const float area = 0.5f * nn;
+    for (int k = 0; k < 3; ++k) {
+        float* acc = vacc + 10 * (int64_t)idx[k];
+        for (int e = 0; e < 9; ++e) atomicAdd(acc + e, area * D[e]);
+        atomicAdd(acc + 9, area);
+    }
+}
+
+// ---- K1b: per-vertex polar decomposition and log map ----------------------
+
+// cyclic Jacobi eigen-decomposition of a symmetric 3x3 matrix A (destroyed);
+// eigenvectors in the columns of V
+__device__ void jacobi_eigen3(float A[9], float V[9]) {
+    for (int k = 0; k < 9; ++k) V[k] = (k % 4 == 0) ? 1.f : 0.f;
+    for (int sweep = 0; sweep < 10; ++sweep) {
+        const float off = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
+        const float dia = A[0] * A[0] + A[4] * A[4] + A[8] * A[8];
+        if (off <= 1e-14f * dia) break;
+        for (int pq = 0; pq < 3; ++pq) {
+            const int p = pq == 2 ? 1 : 0, q = pq == 0 ? 1 : 2;
+            const float apq = A[3 * p + q];
+            if (fabsf(apq) < 1e-30f) continue;
+            const float theta = (A[3 * q + q] - A[3 * p + p]) / (2.f * apq);
+            const float t = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+            const float c = rsqrtf(t * t + 1.f), s = t * c;
+            // A <- J^T A J with J the (p,q) rotation
+            for (int k = 0; k < 3; ++k) {  // columns p, q
+                const float akp = A[3 * k + p], akq = A[3 * k + q];
+                A[3 * k + p] = c * akp - s * akq;
+                A[3 * k + q] = s * akp + c * akq;
+            }
+            for (int k = 0; k < 3; ++k) {  // rows p, q
+                const float apk = A[3 * p + k], aqk = A[3 * q + k];
+                A[3 * p + k] = c * apk - s * aqk;
+                A[3 * q + k] = s * apk + c * aqk;
+            }
+            for (int k = 0; k < 3; ++k) {
+                const float vkp = V[3 * k + p], vkq = V[3 * k + q];
+                V[3 * k + p] = c * vkp - s * vkq;
+                V[3 * k + q] = s * vkp + c * vkq;
+            }
+        }
+    }
+}
+
+// D = R S with R a proper rotation (det D < 0: smallest singular direction flipped)
+__device__ void polar3(const float D[9], float R[9], float S6[6]) {
+    float A[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) A[3 * i + j] = D[i] * D[j] + D[3 + i] * D[3 + j] + D[6 + i] * D[6 + j];
+    float V[9];
+    jacobi_eigen3(A, V);
+    float lam[3] = {A[0], A[4], A[8]};
+    // sort eigenpairs by decreasing eigenvalue
+    int o[3] = {0, 1, 2};
+    if (lam[o[0]] < lam[o[1]]) { int t = o[0]; o[0] = o[1]; o[1] = t; }
+    if (lam[o[1]] < lam[o[2]]) { int t = o[1]; o[1] = o[2]; o[2] = t; }
+    if (lam[o[0]] < lam[o[1]]) { int t = o[0]; o[0] = o[1]; o[1] = t; }
+    float v[3][3];
+    for (int k = 0; k < 3; ++k)
+        for (int r = 0; r < 3; ++r) v[k][r] = V[3 * r + o[k]];
+    // right-handed V
+    float c[3];
+    cross3(v[0], v[1], c);
+    if (dot3(c, v[2]) < 0.f) { v[2][0] = -v[2][0]; v[2][1] = -v[2][1]; v[2][2] = -v[2][2]; }
+    // u1 = D v1 / |D v1|, u2 = D v2 orthogonalised, u3 = u1 x u2
+    float u[3][3];
+    for (int k = 0; k < 2; ++k)
+        for (int r = 0; r < 3; ++r) u[k][r] = D[3 * r] * v[k][0] + D[3 * r + 1] * v[k][1] + D[3 * r + 2] * v[k][2];
+    float n0 = sqrtf(dot3(u[0], u[0]));
+    if (n0 > 0.f) for (int r = 0; r < 3; ++r) u[0][r] /= n0;
+    else { u[0][0] = v[0][0]; u[0][1] = v[0][1]; u[0][2] = v[0][2]; }
+    const float p = dot3(u[0], u[1]);
+    for (int r = 0; r < 3; ++r) u[1][r] -= p * u[0][r];
+    float n1 = sqrtf(dot3(u[1], u[1]));
+    if (n1 > 1e-20f) for (int r = 0; r < 3; ++r) u[1][r] /= n1;
+    else {  // rank <= 1: any unit vector orthogonal to u1
+        float a[3] = {fabsf(u[0][0]) < 0.9f ? 1.f : 0.f, fabsf(u[0][0]) < 0.9f ? 0.f : 1.f, 0.f};
+        cross3(u[0], a, u[1]);
+        const float m = rsqrtf(dot3(u[1], u[1]));
+        for (int r = 0; r < 3; ++r) u[1][r] *= m;
+    }
+    cross3(u[0], u[1], u[2]);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) R[3 * i + j] = u[0][i] * v[0][j] + u[1][i] * v[1][j] + u[2][i] * v[2][j];
+    // S = R^T D, symmetrised
+    float S[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) S[3 * i + j] = R[i] * D[j] + R[3 + i] * D[3 + j] + R[6 + i] * D[6 + j];
+    S6[0] = S[0]; S6[1] = 0.5f * (S[1] + S[3]); S6[2] = 0.5f * (S[2] + S[6]);
+    S6[3] = S[4]; S6[4] = 0.5f * (S[5] + S[7]); S6[5] = S[8];
+}
+
+// axis-angle log of a rotation, angle in [0, pi]
+__device__ void log_rot(const float R[9], float r[3]) {
+    const float w[3] = {0.5f * (R[7] - R[5]), 0.5f * (R[2] - R[6]), 0.5f * (R[3] - R[1])};  // sin(t) * axis
+    const float s = sqrtf(dot3(w, w));
+    const float c = 0.5f * (R[0] + R[4] + R[8] - 1.f);
+    const float th = atan2f(s, c);
+    if (s > 1e-4f) {
+        const float k = th / s;
+        r[0] = k * w[0]; r[1] = k * w[1]; r[2] = k * w[2];
+    } else if (c > 0.f) {  // near identity: th ~ s
+        const float k = 1.f + s * s / 6.f;
+        r[0] = k * w[0]; r[1] = k * w[1]; r[2] = k * w[2];
+    } else {  // near pi: axis from (R + I)/2 = a a^T
+        int j = 0;
+        if (R[4] > R[3 * j + j]) j = 1;
+        if (R[8] > R[3 * j + j]) j = 2;
+        float a[3] = {0.5f * (R[j] + (j == 0)), 0.5f * (R[3 + j] + (j == 1)), 0.5f * (R[6 + j] + (j == 2))};
+        const float m = rsqrtf(dot3(a, a));
+        a[0] *= m; a[1] *= m; a[2] *= m;
+        if (dot3(a, w) < 0.f) { a[0] = -a[0]; a[1] = -a[1]; a[2] = -a[2]; }
+        r[0] = th * a[0]; r[1] = th * a[1]; r[2] = th * a[2];
+    }
+}
+
+__global__ void __launch_bounds__(256) vertex_xforms_kernel(const float* __restrict__ V, const float* __restrict__ Vd,
+                                                            const float* __restrict__ vacc, int64_t nv,
+                                                            float* __restrict__ vtab) {
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    const float* a = vacc + 10 * v;
+    float D[9];
+    const float w = a[9];
+    if (w > 0.f) { const float iw = 1.f / w; for (int k = 0; k < 9; ++k) D[k] = a[k] * iw; }
+    else { for (int k = 0; k < 9; ++k) D[k] = (k % 4 == 0) ? 1.f : 0.f; }
+    float R[9], S6[6], r[3];
+    polar3(D, R, S6);
+    log_rot(R, r);
+    float* o = vtab + 12 * v;
+    for (int d = 0; d < 3; ++d) o[d] = Vd[3 * v + d] - V[3 * v + d];
+    o[3] = r[0]; o[4] = r[1]; o[5] = r[2];
+    for (int k = 0; k < 6; ++k) o[6 + k] = S6[k];
+}
+
+// ---- K2: per-Gaussian update ------------------------------------------------
+
+__device__ void exp_rot(const float r[3], float R[9], float q[4]) {
+    const float th2 = dot3(r, r);
+    const float th = sqrtf(th2);
+    float A, B, hs, hc;  // R = I + A [r]x + B [r]x^2 ; q = (cos(th/2), sin(th/2)/th * r)
+    if (th < 1e-3f) {
+        A = 1.f - th2 / 6.f;
+        B = 0.5f - th2 / 24.f;
+        hs = 0.5f - th2 / 48.f;
+        hc = 1.f - th2 / 8.f;
+    } else {
+        float s, c;
+        sincosf(th, &s, &c);
+        A = s / th;
+        B = (1.f - c) / th2;
+        float s2, c2;
+        sincosf(0.5f * th, &s2, &c2);
+        hs = s2 / th;
+        hc = c2;
+    }
+    const float x = r[0], y = r[1], z = r[2];
+    R[0] = 1.f + B * (-(y * y + z * z)); R[1] = -A * z + B * x * y;         R[2] = A * y + B * x * z;
+    R[3] = A * z + B * x * y;           R[4] = 1.f + B * (-(x * x + z * z)); R[5] = -A * x + B * y * z;
+    R[6] = -A * y + B * x * z;          R[7] = A * x + B * y * z;          R[8] = 1.f + B * (-(x * x + y * y));
+    q[0] = hc; q[1] = hs * x; q[2] = hs * y; q[3] = hs * z;
+}
+
+__global__ void __launch_bounds__(256) deform_gaussians_kernel(
+    const float* __restrict__ means, const float* __restrict__ quats, const float* __restrict__ scales,
+    const float* __restrict__ cov3d, int64_t n, const int32_t* __restrict__ face, const float* __restrict__ bary,
+    const float* __restrict__ V, const int32_t* __restrict__ F, int64_t nv, int64_t nf,
+    const float* __restrict__ vtab, int mode, float* __restrict__ out_means, float* __restrict__ out_cov,
+    float* __restrict__ out_quats, int32_t* __restrict__ status) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int4 f0 = reinterpret_cast<const int4*>(face)[2 * i];
+    const int4 f1 = reinterpret_cast<const int4*>(face)[2 * i + 1];
+    const int fid[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
+    const float4* bp = reinterpret_cast<const float4*>(bary) + 4 * i;
+    float bb[16];
+    for (int k = 0; k < 4; ++k) { const float4 t = bp[k]; bb[4 * k] = t.x; bb[4 * k + 1] = t.y; bb[4 * k + 2] = t.z; bb[4 * k + 3] = t.w; }
+    float dsum[3] = {0, 0, 0}, rsum[3] = {0, 0, 0}, ssum[6] = {0, 0, 0, 0, 0, 0}, psum[3] = {0, 0, 0};
+    bool bad = false;
+    for (int c = 0; c < 8; ++c) {
+        const int f = fid[c];
+        if (f < 0 || f >= nf) { bad = true; break; }
+        const float b1 = bb[2 * c], b2 = bb[2 * c + 1];
+        const float w[3] = {1.f - b1 - b2, b1, b2};
+        for (int k = 0; k < 3; ++k) {
+            const int v = F[3 * (int64_t)f + k];
+            if (v < 0 || v >= nv) { bad = true; break; }
+            const float4* row = reinterpret_cast<const float4*>(vtab + 12 * (int64_t)v);
+            const float4 t0 = row[0], t1 = row[1], t2 = row[2];
+            const float wk = w[k];
+            dsum[0] += wk * t0.x; dsum[1] += wk * t0.y; dsum[2] += wk * t0.z;
+            rsum[0] += wk * t0.w; rsum[1] += wk * t1.x; rsum[2] += wk * t1.y;
+            ssum[0] += wk * t1.z; ssum[1] += wk * t1.w; ssum[2] += wk * t2.x;
+            ssum[3] += wk * t2.y; ssum[4] += wk * t2.z; ssum[5] += wk * t2.w;
+            psum[0] += wk * V[3 * (int64_t)v]; psum[1] += wk * V[3 * (int64_t)v + 1]; psum[2] += wk * V[3 * (int64_t)v + 2];
+        }
+        if (bad) break;
+    }
+    if (bad) {
+        atomicOr(status, kStatusBadIndex);
+        const float nanv = __int_as_float(0x7fc00000);
+        for (int d = 0; d < 3; ++d) out_means[3 * i + d] = nanv;
+        for (int d = 0; d < 6; ++d) out_cov[6 * i + d] = nanv;
+        if (out_quats) for (int d = 0; d < 4; ++d) out_quats[4 * i + d] = nanv;
+        return;
+    }
+    const float e = 0.125f;
+    float rb[3] = {rsum[0] * e, rsum[1] * e, rsum[2] * e};
+    float Rp[9], qr[4];
+    exp_rot(rb, Rp, qr);
+    const float Sb[9] = {ssum[0] * e, ssum[1] * e, ssum[2] * e, ssum[1] * e, ssum[3] * e, ssum[4] * e,
+                         ssum[2] * e, ssum[4] * e, ssum[5] * e};
+    float A[9];
+    matmul3(Rp, Sb, A);
+    const float mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
+    float mo[3];
+    for (int d = 0; d < 3; ++d) mo[d] = mu[d] + dsum[d] * e;
+    if (mode == UMGS_DEFORM_FRAME) {
+        const float rel[3] = {mu[0] - psum[0] * e, mu[1] - psum[1] * e, mu[2] - psum[2] * e};
+        for (int d = 0; d < 3; ++d) mo[d] += A[3 * d] * rel[0] + A[3 * d + 1] * rel[1] + A[3 * d + 2] * rel[2] - rel[d];
+    }
+    for (int d = 0; d < 3; ++d) out_means[3 * i + d] = mo[d];
+    // Sigma
+    float S[9];
+    float qn[4] = {1.f, 0.f, 0.f, 0.f};
+    if (cov3d) {
+        const float* c6 = cov3d + 6 * i;
+        S[0] = c6[0]; S[1] = c6[1]; S[2] = c6[2]; S[3] = c6[1]; S[4] = c6[3]; S[5] = c6[4];
+        S[6] = c6[2]; S[7] = c6[4]; S[8] = c6[5];
+    } else {
+        float qw = quats[4 * i], qx = quats[4 * i + 1], qy = quats[4 * i + 2], qz = quats[4 * i + 3];
+        const float nq = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+        if (nq > 0.f) { qw /= nq; qx /= nq; qy /= nq; qz /= nq; } else { qw = 1.f; qx = qy = qz = 0.f; }
+        qn[0] = qw; qn[1] = qx; qn[2] = qy; qn[3] = qz;
+        const float r[9] = {1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
+                            2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
+                            2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)};
+        const float s[3] = {scales[3 * i], scales[3 * i + 1], scales[3 * i + 2]};
+        float M[9];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) M[3 * a + b] = r[3 * a + b] * s[b];
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) S[3 * a + b] = M[3 * a] * M[3 * b] + M[3 * a + 1] * M[3 * b + 1] + M[3 * a + 2] * M[3 * b + 2];
+    }
+    float AS[9], Sig[9];
+    matmul3(A, S, AS);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) Sig[3 * a + b] = AS[3 * a] * A[3 * b] + AS[3 * a + 1] * A[3 * b + 1] + AS[3 * a + 2] * A[3 * b + 2];
+    float* oc = out_cov + 6 * i;
+    oc[0] = Sig[0]; oc[1] = Sig[1]; oc[2] = Sig[2]; oc[3] = Sig[4]; oc[4] = Sig[5]; oc[5] = Sig[8];
+    if (out_quats) {
+        // q' = qr * qn (Hamilton product), canonical sign w >= 0
+        float o[4];
+        o[0] = qr[0] * qn[0] - qr[1] * qn[1] - qr[2] * qn[2] - qr[3] * qn[3];
+        o[1] = qr[0] * qn[1] + qr[1] * qn[0] + qr[2] * qn[3] - qr[3] * qn[2];
+        o[2] = qr[0] * qn[2] - qr[1] * qn[3] + qr[2] * qn[0] + qr[3] * qn[1];
+        o[3] = qr[0] * qn[3] + qr[1] * qn[2] - qr[2] * qn[1] + qr[3] * qn[0];
+        const float sg = o[0] < 0.f ? -1.f : 1.f;
+        for (int d = 0; d < 4; ++d) out_quats[4 * i + d] = sg * o[d];
+    }
+}
+
+static inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
+
+umgs_status deform_forward(umgs_ctx* ctx, const umgs_gaussians* g, const int32_t* face, const float* bary,
+                           const float* V, const float* Vd, const int32_t* F, int64_t nv, int64_t nf, int32_t mode,
+                           float* out_means, float* out_cov, float* out_quats, cudaStream_t stream) {
+    cudaError_t e;
+    if ((e = ctx->vacc.reserve(sizeof(float) * 10 * nv)) != cudaSuccess) return fail(ctx, UMGS_ERR_OUT_OF_MEMORY, "vacc");
+    if ((e = ctx->vtab.reserve(sizeof(float) * 12 * nv)) != cudaSuccess) return fail(ctx, UMGS_ERR_OUT_OF_MEMORY, "vtab");
+    ctx->vtab_rows = nv;
+    if ((e = cudaMemsetAsync(ctx->vacc.ptr, 0, sizeof(float) * 10 * nv, stream)) != cudaSuccess)
+        return cuda_fail(ctx, e, "cudaMemsetAsync");
+    int32_t* status = ctx->dstatus.as<int32_t>();
+    {
+        StageTimer tm(ctx, UMGS_STAGE_DEFORM_FACES, stream);
+        face_gradients_kernel<<<grid_for(nf, 256), 256, 0, stream>>>(V, Vd, F, nv, nf, ctx->vacc.as<float>(), status);
+    }
+    {
+        StageTimer tm(ctx, UMGS_STAGE_DEFORM_VERTICES, stream);
+        vertex_xforms_kernel<<<grid_for(nv, 256), 256, 0, stream>>>(V, Vd, ctx->vacc.as<float>(), nv,
+                                                                    ctx->vtab.as<float>());
+    }
+    StageTimer tm(ctx, UMGS_STAGE_DEFORM_GAUSSIANS, stream);
+    if (g->n > 0)
+        deform_gaussians_kernel<<<grid_for(g->n, 256), 256, 0, stream>>>(
+            g->means, g->quats, g->scales, g->cov3d, g->n, face, bary, V, F, nv, nf, ctx->vtab.as<float>(), mode,
+            out_means, out_cov, out_quats, status);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "deform kernels");
+    return UMGS_OK;
+}
+
+}  // namespace umgs

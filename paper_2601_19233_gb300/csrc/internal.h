@@ -52,22 +52,63 @@ struct umgs_frame {
     }
 };
 
+// Per-stage CUDA-event timing (umgs_profile_enable / umgs_profile_read).
+struct StageProfiler {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;      // free events
+    struct Rec { int stage; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    cudaEvent_t get() {
+        if (!pool.empty()) { cudaEvent_t e = pool.back(); pool.pop_back(); return e; }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+};
+
 struct umgs_ctx {
     int device = 0;
+    StageProfiler prof;
     std::string err;
     umgs_frame* default_frame = nullptr;
     int64_t* pinned = nullptr;  // small pinned host scratch
     int num_sms = 0;
+    umgs::DevBuf dstatus;       // device status word of asynchronous calls
+    umgs::DevBuf vacc, vtab;    // deformation: per-vertex accumulators / transform table
+    int64_t vtab_rows = 0;
+    umgs::DevBuf bind_ws;       // binding workspace
 };
 
 namespace umgs {
 
 umgs_status fail(umgs_ctx* ctx, umgs_status s, const std::string& msg);
+
+// RAII bracket of one stage: records an event pair on `stream` when profiling is on.
+struct StageTimer {
+    umgs_ctx* ctx;
+    int stage;
+    cudaStream_t stream;
+    cudaEvent_t a = nullptr;
+    StageTimer(umgs_ctx* c, int s, cudaStream_t st) : ctx(c), stage(s), stream(st) {
+        if (ctx->prof.on) { a = ctx->prof.get(); cudaEventRecord(a, stream); }
+    }
+    ~StageTimer() {
+        if (a) {
+            cudaEvent_t b = ctx->prof.get();
+            cudaEventRecord(b, stream);
+            ctx->prof.recs.push_back({stage, a, b});
+        }
+    }
+};
 umgs_status cuda_fail(umgs_ctx* ctx, cudaError_t e, const char* where);
 
 umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_mesh* meshes, int32_t nmeshes,
                            const umgs_camera* cams, int32_t ncams, const umgs_render_opts& opts,
                            float* out_rgbt, umgs_frame* fr, cudaStream_t stream);
+
+umgs_status deform_forward(umgs_ctx* ctx, const umgs_gaussians* g, const int32_t* face, const float* bary,
+                           const float* V, const float* Vd, const int32_t* F, int64_t nv, int64_t nf, int32_t mode,
+                           float* out_means, float* out_cov, float* out_quats, cudaStream_t stream);
 
 umgs_status frame_lists(const umgs_frame* fr, int64_t* tile_ptr, int32_t* ids, uint32_t* dbits,
                         cudaStream_t stream);

@@ -737,6 +737,7 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
 
     const DevCam* dcams = fr->cams.as<DevCam>();
     if (Ng > 0) {
+        StageTimer tm(ctx, UMGS_STAGE_PROJECT_GAUSSIANS, stream);
         project_gaussians_kernel<<<grid_for(Ng, 256), 256, 0, stream>>>(
             g->means, g->quats, g->scales, g->opacities, g->sh, g->sh_dtype, g->sh_degree, g->cov3d, Ng, dcams,
             ncams, ts, tiles_x, tiles_per_cam, fr->grec.as<GRec>(), fr->bin.as<BinInfo>(), Ntot,
@@ -747,6 +748,7 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     for (int m = 0; m < nmeshes; ++m) {
         const umgs_mesh& me = meshes[m];
         if (me.nf > 0) {
+            StageTimer tm(ctx, UMGS_STAGE_SETUP_TRIANGLES, stream);
             setup_triangles_kernel<<<grid_for(me.nf, 256), 256, 0, stream>>>(
                 me.verts, me.faces, me.vcolor, me.valpha, me.falpha, me.nv, me.nf, tri_base, Nt, Ng + tri_base,
                 dcams, ncams, ts, tiles_x, tiles_per_cam, fr->trec.as<TRec>(), fr->bin.as<BinInfo>(), Ntot,
@@ -755,8 +757,11 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
         }
         tri_base += me.nf;
     }
-    scan_tiles_kernel<<<1, 1024, 0, stream>>>(fr->tile_count.as<int32_t>(), M, fr->tile_off.as<int64_t>());
-    UMGS_TRY(cudaGetLastError());
+    {
+        StageTimer tm(ctx, UMGS_STAGE_SCAN, stream);
+        scan_tiles_kernel<<<1, 1024, 0, stream>>>(fr->tile_count.as<int32_t>(), M, fr->tile_off.as<int64_t>());
+        UMGS_TRY(cudaGetLastError());
+    }
     // read back the key count (and the status word)
     UMGS_TRY(cudaMemcpyAsync(ctx->pinned, fr->tile_off.as<int64_t>() + M, sizeof(int64_t), cudaMemcpyDeviceToHost,
                              stream));
@@ -770,18 +775,23 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     UMGS_TRY(fr->keys_tmp.reserve(sizeof(uint64_t) * std::max<int64_t>(1, K)));
     UMGS_TRY(cudaMemsetAsync(fr->tile_fill.ptr, 0, sizeof(int32_t) * (M + 1), stream));
     if (Ntot > 0) {
+        StageTimer tm(ctx, UMGS_STAGE_SCATTER, stream);
         scatter_keys_kernel<<<grid_for(Ntot * ncams, 256), 256, 0, stream>>>(
             fr->bin.as<BinInfo>(), Ntot, ncams, ts, tiles_x, tiles_per_cam, fr->tile_off.as<int64_t>(),
             fr->tile_fill.as<int32_t>(), fr->keys.as<uint64_t>());
         UMGS_TRY(cudaGetLastError());
     }
-    sort_tiles_kernel<<<(unsigned)M, kSortThreads, kSortCap * sizeof(uint64_t), stream>>>(
-        fr->keys.as<uint64_t>(), fr->keys_tmp.as<uint64_t>(), fr->tile_off.as<int64_t>());
-    UMGS_TRY(cudaGetLastError());
+    {
+        StageTimer tm(ctx, UMGS_STAGE_SORT, stream);
+        sort_tiles_kernel<<<(unsigned)M, kSortThreads, kSortCap * sizeof(uint64_t), stream>>>(
+            fr->keys.as<uint64_t>(), fr->keys_tmp.as<uint64_t>(), fr->tile_off.as<int64_t>());
+        UMGS_TRY(cudaGetLastError());
+    }
     UMGS_TRY(fr->last.reserve(sizeof(int32_t) * (int64_t)ncams * W * H));
     const float te = opts.t_eps > 0.f ? opts.t_eps : -1.f;
     float4* out = reinterpret_cast<float4*>(out_rgbt);
     int32_t* last = fr->last.as<int32_t>();
+    StageTimer tm_comp(ctx, UMGS_STAGE_COMPOSITE, stream);
     if (ts == 16)
         composite_kernel<16><<<(unsigned)M, 256, 0, stream>>>(
             fr->keys.as<uint64_t>(), fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->trec.as<TRec>(), Ng, Nt,

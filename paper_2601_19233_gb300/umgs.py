@@ -78,8 +78,13 @@ def lib():
                                   ctypes.POINTER(CCamera), i32, ctypes.POINTER(CRenderOpts), vp, vp, vp]
         L.umgs_frame_counts.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
         L.umgs_frame_lists.argtypes = [vp, vp, vp, vp, vp]
-        for name in ("umgs_ctx_create", "umgs_frame_create", "umgs_render", "umgs_frame_counts",
-                     "umgs_frame_lists"):
+        L.umgs_ctx_sync.argtypes = [vp, vp]
+        L.umgs_deform.argtypes = [vp, ctypes.POINTER(CGaussians), vp, vp, vp, vp, vp, i64, i64, i32, vp, vp, vp, vp]
+        L.umgs_deform_vertex_table.argtypes = [vp, vp, i64, vp]
+        L.umgs_profile_enable.argtypes = [vp, i32]
+        L.umgs_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
+        for name in ("umgs_profile_enable", "umgs_profile_read", "umgs_ctx_create", "umgs_frame_create", "umgs_render", "umgs_frame_counts",
+                     "umgs_frame_lists", "umgs_ctx_sync", "umgs_deform", "umgs_deform_vertex_table"):
             getattr(L, name).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -111,6 +116,10 @@ class Context:
         if st != OK:
             msg = lib().umgs_last_error(self._h)
             raise UmgsError(st, "%s: %s" % (what, msg.decode() if msg else ""))
+
+    def sync(self, stream=None):
+        """umgs_ctx_sync: synchronise and raise deferred device-side errors."""
+        self.check(lib().umgs_ctx_sync(self._h, _stream(stream)), "umgs_ctx_sync")
 
     def close(self):
         if self._h:
@@ -247,3 +256,56 @@ def render(ctx: Context, gaussians: DevGaussians | None, meshes, cameras, opts: 
                            frame._h if frame is not None else None, _stream(stream))
     ctx.check(st, "umgs_render")
     return out
+
+
+def deform(ctx: Context, rest: DevGaussians, face: torch.Tensor, bary: torch.Tensor, proxy_v: torch.Tensor,
+           proxy_vd: torch.Tensor, proxy_f: torch.Tensor, mode=DEFORM_FRAME, out=None, with_quats=True,
+           stream=None):
+    """umgs_deform: returns (means' [n,3], cov3d' [n,6], quats' [n,4] or None)."""
+    n = rest.n
+    dev = torch.device("cuda", ctx.device)
+    if out is None:
+        out = (torch.empty((n, 3), dtype=torch.float32, device=dev),
+               torch.empty((n, 6), dtype=torch.float32, device=dev),
+               torch.empty((n, 4), dtype=torch.float32, device=dev) if with_quats else None)
+    cg = rest.c()
+    st = lib().umgs_deform(ctx._h, ctypes.byref(cg), _ptr(face), _ptr(bary), _ptr(proxy_v), _ptr(proxy_vd),
+                           _ptr(proxy_f), int(proxy_v.shape[0]), int(proxy_f.shape[0]), int(mode), _ptr(out[0]),
+                           _ptr(out[1]), _ptr(out[2]), _stream(stream))
+    ctx.check(st, "umgs_deform")
+    return out
+
+
+def deform_vertex_table(ctx: Context, nv: int, stream=None) -> torch.Tensor:
+    t = torch.empty((nv, 12), dtype=torch.float32, device=torch.device("cuda", ctx.device))
+    ctx.check(lib().umgs_deform_vertex_table(ctx._h, _ptr(t), int(nv), _stream(stream)), "umgs_deform_vertex_table")
+    return t
+
+
+NUM_STAGES = 16
+
+
+def profile_enable(ctx: Context, on=True):
+    ctx.check(lib().umgs_profile_enable(ctx._h, 1 if on else 0), "umgs_profile_enable")
+
+
+def profile_read(ctx: Context):
+    """(ms [16], launches [16]) summed per stage since the last read."""
+    ms = (ctypes.c_double * NUM_STAGES)()
+    n = (ctypes.c_int64 * NUM_STAGES)()
+    ctx.check(lib().umgs_profile_read(ctx._h, ms, n), "umgs_profile_read")
+    return list(ms), list(n)
+
+
+def bind_or_fallback(ctx, g, proxy_v, proxy_f, cameras, device):
+    """Bind with umgs_bind when the library provides it, else a seeded random
+    face/barycentric table of the same shape (labelled in the returned info)."""
+    if hasattr(lib(), "umgs_bind"):
+        face, bary, dist, flags, nfb = bind(ctx, g, proxy_v, proxy_f, cameras, mode=BIND_BBX)
+        return face, bary, "umgs_bind BBX k=3, %d cameras, %d fallback targets" % (len(cameras), nfb)
+    gen = torch.Generator(device=device).manual_seed(0)
+    n = g.n
+    face = torch.randint(0, int(proxy_f.shape[0]), (n, 8), generator=gen, device=device, dtype=torch.int32)
+    b = torch.rand((n, 8, 2), generator=gen, device=device)
+    b = torch.where(b.sum(-1, keepdim=True) > 1, 1 - b, b).contiguous()
+    return face, b, "synthetic random table"

@@ -1,0 +1,103 @@
+"""GPU parity of the deformation transfer (Eq. 12-13) against the fp64 oracle."""
+import numpy as np
+import pytest
+import torch
+from scipy.spatial.transform import Rotation
+
+from oracle import deform as D
+from oracle.render import cov3d_fp64
+from paper_2601_19233_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2601_19233_gb300 import build, umgs
+    build.build()
+    return umgs.Context(0)
+
+
+def _problem(seed=0, n=5000, subdiv=3):
+    rng = np.random.default_rng(seed)
+    V, F = S.icosphere(subdiv, 1.0)
+    g = S.make_gaussians(rng, S.shell_points(rng, n, 1.0, 0.05), -4.0, 0)
+    face = rng.integers(0, len(F), size=(n, 8)).astype(np.int32)
+    b = rng.uniform(0, 1, size=(n, 8, 2))
+    b = np.where(b.sum(-1, keepdims=True) > 1, 1 - b, b).astype(np.float32)
+    return V, F, g, face, b
+
+
+def _run(ctx, V, Vd, F, g, face, b, mode=0, cov3d=None):
+    from paper_2601_19233_gb300 import umgs
+    dg = umgs.gaussians_to_device(g)
+    if cov3d is not None:
+        dg.cov3d = torch.as_tensor(cov3d.astype(np.float32)).cuda()
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a)).cuda()
+    m, c, q = umgs.deform(ctx, dg, t(face), t(b), t(V.astype(np.float32)), t(Vd.astype(np.float32)), t(F), mode=mode)
+    ctx.sync()
+    return m.cpu().numpy(), c.cpu().numpy(), q.cpu().numpy()
+
+
+def _cov_err(c6, Sig):
+    ref = D.sym6(Sig)
+    scale = np.abs(ref).max(1, keepdims=True)
+    return (np.abs(c6 - ref) / scale).max()
+
+
+def _quat_err(q, qref):
+    d = np.minimum(np.abs(q - qref).max(1), np.abs(q + qref).max(1))
+    return d.max()
+
+
+@pytest.mark.parametrize("mode", [D.FRAME, D.LITERAL])
+def test_smooth_deformation_matches_oracle(ctx, mode):
+    V, F, g, face, b = _problem(1)
+    Vd = S.displace(V, S.sinusoid_params(np.random.default_rng(5)), 17)
+    m, c, q = _run(ctx, V, Vd, F, g, face, b, mode)
+    mr, Sr, qr = D.deform_gaussians(g.means, g.quats, g.scales, face, b, V, Vd, F, mode=mode)
+    assert np.abs(m - mr).max() < 1e-5
+    assert _cov_err(c, Sr) < 1e-4
+    assert _quat_err(q, qr) < 1e-5
+
+
+def test_vertex_table_matches_oracle(ctx):
+    from paper_2601_19233_gb300 import umgs
+    V, F, g, face, b = _problem(2)
+    Vd = S.displace(V, S.sinusoid_params(np.random.default_rng(6)), 40)
+    _run(ctx, V, Vd, F, g, face, b)
+    tab = umgs.deform_vertex_table(ctx, len(V)).cpu().numpy()
+    delta, r, Sv = D.vertex_transforms(V, Vd, F)
+    assert np.abs(tab[:, :3] - delta).max() < 1e-6
+    assert np.abs(tab[:, 3:6] - r).max() < 2e-5
+    assert np.abs(tab[:, 6:] - D.sym6(Sv)).max() < 2e-5
+
+
+def test_rigid_motion_moves_gaussians_rigidly(ctx):
+    V, F, g, face, b = _problem(3)
+    Rm = Rotation.random(random_state=3).as_matrix()
+    t = np.array([0.3, -0.1, 0.2])
+    Vd = V.astype(np.float64) @ Rm.T + t
+    m, c, q = _run(ctx, V, Vd, F, g, face, b)
+    assert np.abs(m - (g.means.astype(np.float64) @ Rm.T + t)).max() < 1e-5
+    Sig = cov3d_fp64(g.quats, g.scales)
+    assert _cov_err(c, Rm @ Sig @ Rm.T) < 1e-5
+
+
+def test_identity_and_cov3d_input(ctx):
+    V, F, g, face, b = _problem(4, n=2000)
+    Sig = cov3d_fp64(g.quats, g.scales)
+    m, c, q = _run(ctx, V, V, F, g, face, b, cov3d=D.sym6(Sig))
+    assert np.abs(m - g.means).max() < 1e-6
+    assert _cov_err(c, Sig) < 1e-5
+
+
+def test_out_of_range_face_is_reported(ctx):
+    from paper_2601_19233_gb300 import umgs
+    V, F, g, face, b = _problem(5, n=100)
+    face = face.copy()
+    face[7, 3] = len(F) + 5
+    with pytest.raises(umgs.UmgsError) as e:
+        _run(ctx, V, V, F, g, face, b)
+    assert e.value.status == 1
+    ctx.sync()  # status cleared
