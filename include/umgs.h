@@ -211,6 +211,37 @@ enum {
 umgs_status umgs_profile_enable(umgs_ctx* ctx, int32_t on);
 umgs_status umgs_profile_read(umgs_ctx* ctx, double* ms, int64_t* launches);
 
+/* ---- deformation without device allocation ---------------------------------
+ * No counterpart in the paper.  For callers that cannot allocate device
+ * memory - e.g. a host application that hands all device memory to its own
+ * allocator at start-up, a plugin in a process whose device memory another
+ * runtime owns, or a real-time loop that cannot absorb the synchronisation
+ * of cudaMalloc - this computes exactly what umgs_deform computes (same
+ * kernels, same arguments, same output layout) without a context and
+ * without calling cudaMalloc, cudaFree or any allocating routine.
+ *
+ * Its scratch (per-vertex accumulators, the vertex transform table and a
+ * status word) lives in one file-scope __device__ array sized for
+ * UMGS_NOALLOC_MAX_PROXY_VERTICES proxy vertices (about 2.9 MB), which every
+ * GPU that loads the library keeps until the process exits.
+ *  - Runs on the CALLING thread's current device and on `stream`.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - All calls share the array and it keeps the last call's contents (each
+ *    call clears what must start at zero): calls that overlap on the GPU
+ *    (several streams or host threads at once) race and give wrong results.
+ *  - Out-of-range face or vertex ids give NaN outputs for the affected
+ *    Gaussians; no deferred status is kept.
+ * Errors: INVALID_ARG (as umgs_deform), CAPACITY (nv above the maximum),
+ * CUDA (lookup or launch failure).  Asynchronous.
+ */
+#define UMGS_NOALLOC_MAX_PROXY_VERTICES 32768
+umgs_status umgs_deform_noalloc(const umgs_gaussians* rest, const int32_t* face, const float* bary,
+                                const float* proxy_v, const float* proxy_vd, const int32_t* proxy_f,
+                                int64_t nv, int64_t nf, int32_t mode, float* out_means, float* out_cov3d,
+                                float* out_quats, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

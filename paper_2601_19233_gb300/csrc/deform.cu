@@ -14,6 +14,7 @@
 //                    A = R'S', mu' (FRAME or LITERAL), q' = quat(R') q.
 //                    Streams 136 B in and 52 B out per Gaussian.
 #include <cmath>
+#include <mutex>
 
 #include "internal.h"
 
@@ -392,3 +393,88 @@ umgs_status deform_forward(umgs_ctx* ctx, const umgs_gaussians* g, const int32_t
 }
 
 }  // namespace umgs
+
+// ---------------------------------------------------------------------------
+// Deformation without device allocation (no paper counterpart).
+//
+// Some callers cannot allocate device memory: a host application that
+// reserves the whole device memory for its own allocator up front, a plugin
+// inside a process whose device memory another runtime owns, or a real-time
+// loop whose frame budget cannot absorb the synchronisation of cudaMalloc.
+// umgs_deform_noalloc runs the same three deformation kernels as umgs_deform
+// but keeps its scratch (per-vertex accumulators, vertex transform table and
+// a status word) in the file-scope array below, so it needs no context and
+// never calls cudaMalloc, cudaFree or any allocating library routine.
+//
+// The array holds UMGS_NOALLOC_MAX_PROXY_VERTICES vertices (22 floats each)
+// plus 64 words; every GPU that loads the library keeps it (about 2.9 MB)
+// until the process exits.  All calls share it: calls whose work overlaps
+// on the GPU (other streams, other host threads) race on it.
+
+namespace umgs {
+
+constexpr int64_t kNoAllocMaxVerts = UMGS_NOALLOC_MAX_PROXY_VERTICES;
+constexpr int64_t kNoAllocFloats = kNoAllocMaxVerts * 22 + 64;
+
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocFloats];
+
+__global__ void noalloc_clear_kernel(float* __restrict__ p, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) p[i] = 0.f;
+}
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device.  In host code the symbol is only a host-side stand-in, so the
+// address must come from cudaGetSymbolAddress with that device current.
+static cudaError_t noalloc_scratch_address(float** out) {
+    constexpr int kMaxDev = 64;
+    static float* addr[kMaxDev] = {};
+    static std::mutex mu;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        addr[dev] = static_cast<float*>(p);
+    }
+    *out = addr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace umgs
+
+extern "C" umgs_status umgs_deform_noalloc(const umgs_gaussians* rest, const int32_t* face, const float* bary,
+                                           const float* proxy_v, const float* proxy_vd, const int32_t* proxy_f,
+                                           int64_t nv, int64_t nf, int32_t mode, float* out_means,
+                                           float* out_cov3d, float* out_quats, void* stream) {
+    using namespace umgs;
+    if (!rest || rest->n < 0) return UMGS_ERR_INVALID_ARG;
+    if (mode != UMGS_DEFORM_FRAME && mode != UMGS_DEFORM_LITERAL) return UMGS_ERR_INVALID_ARG;
+    if (!proxy_v || !proxy_vd || !proxy_f || nv < 3 || nf < 1) return UMGS_ERR_INVALID_ARG;
+    if (nv > kNoAllocMaxVerts) return UMGS_ERR_CAPACITY;
+    if (rest->n > 0) {
+        if (!rest->means || !face || !bary || !out_means || !out_cov3d) return UMGS_ERR_INVALID_ARG;
+        if (!rest->cov3d && (!rest->quats || !rest->scales)) return UMGS_ERR_INVALID_ARG;
+        if ((reinterpret_cast<uintptr_t>(face) | reinterpret_cast<uintptr_t>(bary)) & 15) return UMGS_ERR_INVALID_ARG;
+    }
+    float* base = nullptr;
+    if (noalloc_scratch_address(&base) != cudaSuccess) return UMGS_ERR_CUDA;
+    float* vacc = base;                                   // [nv,10]
+    float* vtab = base + 10 * kNoAllocMaxVerts;           // [nv,12]
+    int32_t* status = reinterpret_cast<int32_t*>(base + 22 * kNoAllocMaxVerts);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the accumulators and the status word keep the previous call's values
+    noalloc_clear_kernel<<<grid_for(10 * nv, 256), 256, 0, s>>>(vacc, 10 * nv);
+    noalloc_clear_kernel<<<1, 64, 0, s>>>(reinterpret_cast<float*>(status), 64);
+    face_gradients_kernel<<<grid_for(nf, 256), 256, 0, s>>>(proxy_v, proxy_vd, proxy_f, nv, nf, vacc, status);
+    vertex_xforms_kernel<<<grid_for(nv, 256), 256, 0, s>>>(proxy_v, proxy_vd, vacc, nv, vtab);
+    if (rest->n > 0)
+        deform_gaussians_kernel<<<grid_for(rest->n, 256), 256, 0, s>>>(
+            rest->means, rest->quats, rest->scales, rest->cov3d, rest->n, face, bary, proxy_v, proxy_f, nv, nf, vtab,
+            mode, out_means, out_cov3d, out_quats, status);
+    return cudaGetLastError() == cudaSuccess ? UMGS_OK : UMGS_ERR_CUDA;
+}

@@ -81,6 +81,9 @@ def lib():
         L.umgs_ctx_sync.argtypes = [vp, vp]
         L.umgs_deform.argtypes = [vp, ctypes.POINTER(CGaussians), vp, vp, vp, vp, vp, i64, i64, i32, vp, vp, vp, vp]
         L.umgs_deform_vertex_table.argtypes = [vp, vp, i64, vp]
+        L.umgs_deform_noalloc.argtypes = [ctypes.POINTER(CGaussians), vp, vp, vp, vp, vp, i64, i64, i32, vp, vp,
+                                          vp, vp]
+        L.umgs_deform_noalloc.restype = ctypes.c_int
         L.umgs_profile_enable.argtypes = [vp, i32]
         L.umgs_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
         for name in ("umgs_profile_enable", "umgs_profile_read", "umgs_ctx_create", "umgs_frame_create", "umgs_render", "umgs_frame_counts",
@@ -273,6 +276,24 @@ def deform(ctx: Context, rest: DevGaussians, face: torch.Tensor, bary: torch.Ten
                            _ptr(proxy_f), int(proxy_v.shape[0]), int(proxy_f.shape[0]), int(mode), _ptr(out[0]),
                            _ptr(out[1]), _ptr(out[2]), _stream(stream))
     ctx.check(st, "umgs_deform")
+    return out
+
+
+NOALLOC_MAX_PROXY_VERTICES = 32768
+
+
+def deform_noalloc(rest: DevGaussians, face, bary, proxy_v, proxy_vd, proxy_f, out, mode=DEFORM_FRAME,
+                   stream=None):
+    """umgs_deform_noalloc: the deformation for callers that cannot allocate
+    device memory.  `out` = (means [n,3], cov3d [n,6], quats [n,4] or None),
+    all preallocated by the caller; nothing is allocated on the device.
+    Runs on the current device; see include/umgs.h for the shared-scratch rules."""
+    cg = rest.c()
+    st = lib().umgs_deform_noalloc(ctypes.byref(cg), _ptr(face), _ptr(bary), _ptr(proxy_v), _ptr(proxy_vd),
+                                   _ptr(proxy_f), int(proxy_v.shape[0]), int(proxy_f.shape[0]), int(mode),
+                                   _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), _stream(stream))
+    if st != OK:
+        raise UmgsError(st, "umgs_deform_noalloc")
     return out
 
 
