@@ -160,6 +160,38 @@ umgs_status umgs_frame_counts(const umgs_frame* frame, int64_t* num_keys, int64_
 umgs_status umgs_frame_lists(const umgs_frame* frame, int64_t* tile_ptr, int32_t* ids,
                              uint32_t* dbits, void* stream);
 
+/* ---- Gaussian-centric binding (Sec. 3.3, "Binding Gaussians to Mesh") -------
+ *
+ * For every Gaussian, one target (mode CENTER: the mean; the paper's
+ * UniMGS*) or 8 targets (mode BBX: the corners mu + R_q (+-k s_x, +-k s_y,
+ * +-k s_z), corner c taking the + sign on axis j when bit j of c is set; the
+ * paper's UniMGS).  From every camera centre o a ray o + t (p - o), t > 0, is
+ * cast through the target p; every proxy face it hits is a candidate and the
+ * target binds to the hit nearest to p (distance |t - 1| |p - o|; ties:
+ * lower camera index, then lower face index).  A target that no ray hits,
+ * and every target in mode NEAREST, binds to the closest point of the proxy
+ * mesh (ties: lower face index).  The ray/triangle test (Moller-Trumbore)
+ * and the closest-point evaluation use canonical float32 operations, so the
+ * result equals a brute-force search over all faces and cameras bit for bit.
+ *
+ * g          Gaussians (means; quats and scales in mode BBX)
+ * proxy_v    [nv,3], proxy_f [nf,3] int32
+ * cams       host array of ncams cameras (only the pose is used; ignored in NEAREST)
+ * k_sigma    box half-size in standard deviations (the paper's BBX; 3)
+ * out_face   [n,8] int32 bound face per target (CENTER/NEAREST: 8 copies)
+ * out_bary   [n,8,2] (b1, b2): the bound point is (1-b1-b2) v0 + b1 v1 + b2 v2
+ * out_dist   [n,8] distance from the target to the bound point
+ * out_flags  [n,8] uint8: 1 = ray hit, 2 = closest-point fallback / NEAREST
+ * out_num_fallback  host; number of [n,8] slots with flag 2 (nullable)
+ * Synchronises (reads the grid size and the fallback count).  Errors:
+ * INVALID_ARG (sizes, NULL arrays, out-of-range proxy face ids), CAPACITY
+ * (a ray exceeded the cell-visit budget), OUT_OF_MEMORY, CUDA.
+ */
+umgs_status umgs_bind(umgs_ctx* ctx, const umgs_gaussians* g, const float* proxy_v, const int32_t* proxy_f,
+                      int64_t nv, int64_t nf, const umgs_camera* cams, int32_t ncams, int32_t mode, float k_sigma,
+                      int32_t* out_face, float* out_bary, float* out_dist, uint8_t* out_flags,
+                      int64_t* out_num_fallback, void* stream);
+
 /* ---- deformation transfer (Sec. 3.3, Eq. 12-13) ---------------------------
  *
  * Per proxy face f: deformation gradient D_f = F'_f F_f^-1 with the frame

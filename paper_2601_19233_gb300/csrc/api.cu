@@ -64,6 +64,8 @@ void umgs_ctx_destroy(umgs_ctx* ctx) {
     ctx->vacc.release();
     ctx->vtab.release();
     ctx->bind_ws.release();
+    ctx->bind_cams.release();
+    ctx->bind_cnt.release();
     delete ctx;
 }
 
@@ -200,6 +202,31 @@ umgs_status umgs_deform(umgs_ctx* ctx, const umgs_gaussians* rest, const int32_t
     }
     return deform_forward(ctx, rest, face, bary, proxy_v, proxy_vd, proxy_f, nv, nf, mode, out_means, out_cov3d,
                           out_quats, static_cast<cudaStream_t>(stream));
+}
+
+umgs_status umgs_bind(umgs_ctx* ctx, const umgs_gaussians* g, const float* proxy_v, const int32_t* proxy_f,
+                      int64_t nv, int64_t nf, const umgs_camera* cams, int32_t ncams, int32_t mode, float k_sigma,
+                      int32_t* out_face, float* out_bary, float* out_dist, uint8_t* out_flags,
+                      int64_t* out_num_fallback, void* stream) {
+    if (!ctx) return UMGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, UMGS_ERR_CUDA, "cudaSetDevice");
+    if (!g || g->n < 0) return fail(ctx, UMGS_ERR_INVALID_ARG, "Gaussians missing");
+    if (mode != UMGS_BIND_BBX && mode != UMGS_BIND_CENTER && mode != UMGS_BIND_NEAREST)
+        return fail(ctx, UMGS_ERR_INVALID_ARG, "bad bind mode");
+    if (!proxy_v || !proxy_f || nv < 3 || nf < 1) return fail(ctx, UMGS_ERR_INVALID_ARG, "bad proxy mesh");
+    if (nf >= (1LL << 31)) return fail(ctx, UMGS_ERR_INVALID_ARG, "too many proxy faces");
+    if (mode != UMGS_BIND_NEAREST && (!cams || ncams < 1))
+        return fail(ctx, UMGS_ERR_INVALID_ARG, "ray-cast binding needs at least one camera");
+    if (g->n > 0) {
+        if (!g->means || !out_face || !out_bary || !out_dist || !out_flags)
+            return fail(ctx, UMGS_ERR_INVALID_ARG, "NULL array");
+        if (mode == UMGS_BIND_BBX && (!g->quats || !g->scales))
+            return fail(ctx, UMGS_ERR_INVALID_ARG, "BBX binding needs quats and scales");
+        if (!(k_sigma > 0.f)) return fail(ctx, UMGS_ERR_INVALID_ARG, "k_sigma must be positive");
+    }
+    return bind_forward(ctx, g, proxy_v, proxy_f, nv, nf, cams, mode == UMGS_BIND_NEAREST ? 0 : ncams, mode, k_sigma,
+                        out_face, out_bary, out_dist, out_flags, out_num_fallback, static_cast<cudaStream_t>(stream));
 }
 
 umgs_status umgs_deform_vertex_table(umgs_ctx* ctx, float* out_table, int64_t nv, void* stream) {

@@ -76,7 +76,8 @@ struct umgs_ctx {
     umgs::DevBuf dstatus;       // device status word of asynchronous calls
     umgs::DevBuf vacc, vtab;    // deformation: per-vertex accumulators / transform table
     int64_t vtab_rows = 0;
-    umgs::DevBuf bind_ws;       // binding workspace
+    umgs::DevBuf bind_ws;       // binding workspace (grid header + cell entries)
+    umgs::DevBuf bind_cams, bind_cnt;
 };
 
 namespace umgs {
@@ -109,6 +110,11 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
 umgs_status deform_forward(umgs_ctx* ctx, const umgs_gaussians* g, const int32_t* face, const float* bary,
                            const float* V, const float* Vd, const int32_t* F, int64_t nv, int64_t nf, int32_t mode,
                            float* out_means, float* out_cov, float* out_quats, cudaStream_t stream);
+
+umgs_status bind_forward(umgs_ctx* ctx, const umgs_gaussians* g, const float* V, const int32_t* F, int64_t nv,
+                         int64_t nf, const umgs_camera* cams, int32_t ncams, int32_t mode, float k_sigma,
+                         int32_t* out_face, float* out_bary, float* out_dist, uint8_t* out_flags,
+                         int64_t* out_num_fallback, cudaStream_t stream);
 
 umgs_status frame_lists(const umgs_frame* fr, int64_t* tile_ptr, int32_t* ids, uint32_t* dbits,
                         cudaStream_t stream);

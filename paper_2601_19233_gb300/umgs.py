@@ -81,6 +81,9 @@ def lib():
         L.umgs_ctx_sync.argtypes = [vp, vp]
         L.umgs_deform.argtypes = [vp, ctypes.POINTER(CGaussians), vp, vp, vp, vp, vp, i64, i64, i32, vp, vp, vp, vp]
         L.umgs_deform_vertex_table.argtypes = [vp, vp, i64, vp]
+        L.umgs_bind.argtypes = [vp, ctypes.POINTER(CGaussians), vp, vp, i64, i64, ctypes.POINTER(CCamera), i32, i32,
+                                ctypes.c_float, vp, vp, vp, vp, ctypes.POINTER(i64), vp]
+        L.umgs_bind.restype = ctypes.c_int
         L.umgs_deform_noalloc.argtypes = [ctypes.POINTER(CGaussians), vp, vp, vp, vp, vp, i64, i64, i32, vp, vp,
                                           vp, vp]
         L.umgs_deform_noalloc.restype = ctypes.c_int
@@ -316,6 +319,25 @@ def profile_read(ctx: Context):
     n = (ctypes.c_int64 * NUM_STAGES)()
     ctx.check(lib().umgs_profile_read(ctx._h, ms, n), "umgs_profile_read")
     return list(ms), list(n)
+
+
+def bind(ctx: Context, g: DevGaussians, proxy_v: torch.Tensor, proxy_f: torch.Tensor, cameras, mode=BIND_BBX,
+         k_sigma=3.0, stream=None):
+    """umgs_bind: returns (face [n,8] i32, bary [n,8,2], dist [n,8], flags [n,8] u8, num_fallback)."""
+    n = g.n
+    dev = torch.device("cuda", ctx.device)
+    face = torch.empty((n, 8), dtype=torch.int32, device=dev)
+    bary = torch.empty((n, 8, 2), dtype=torch.float32, device=dev)
+    dist = torch.empty((n, 8), dtype=torch.float32, device=dev)
+    flags = torch.empty((n, 8), dtype=torch.uint8, device=dev)
+    cams = (CCamera * max(1, len(cameras)))(*[camera_struct(c) for c in cameras])
+    nfb = ctypes.c_int64(0)
+    cg = g.c()
+    st = lib().umgs_bind(ctx._h, ctypes.byref(cg), _ptr(proxy_v), _ptr(proxy_f), int(proxy_v.shape[0]),
+                         int(proxy_f.shape[0]), cams, len(cameras), int(mode), float(k_sigma), _ptr(face), _ptr(bary),
+                         _ptr(dist), _ptr(flags), ctypes.byref(nfb), _stream(stream))
+    ctx.check(st, "umgs_bind")
+    return face, bary, dist, flags, nfb.value
 
 
 def bind_or_fallback(ctx, g, proxy_v, proxy_f, cameras, device):
