@@ -338,6 +338,7 @@ def render_image(scene, cam_index=0, mode=FULL, t_eps=T_EPS, t_product=False,
     out_tie = np.zeros(H * W, bool)
     out_ws = np.zeros(H * W)
     out_n = np.zeros(H * W, np.int64)
+    sig = []
     bgv = np.asarray(bg, np.float64)
     out_rgb[:] = bgv
     bounds = np.nonzero(np.diff(np.concatenate([[-1], pix, [-2]])))[0]
@@ -350,5 +351,7 @@ def render_image(scene, cam_index=0, mode=FULL, t_eps=T_EPS, t_product=False,
         out_tie[p] = res["tie"]
         out_ws[p] = sum(x for _, x in res["weights"])
         out_n[p] = len(frags)
+        sig.append((p, res["n"], tuple(i for i, _ in res["weights"]),
+                    tuple(f.get("mask", -1) for f in frags[:res["n"]])))
     return dict(rgb=out_rgb.reshape(H, W, 3), T=out_T.reshape(H, W), tie=out_tie.reshape(H, W),
-                wsum=out_ws.reshape(H, W), nfrag=out_n.reshape(H, W))
+                wsum=out_ws.reshape(H, W), nfrag=out_n.reshape(H, W), sig=hash(tuple(sig)))
