@@ -184,6 +184,38 @@ def run_umgs(args, rank, world, local_rank):
     value = K * world / (ms_total / 1e3)
     nkeys, ntiles = frame.counts()
 
+    # forward + backward: the render keeps its backward state and the gradient
+    # of a fixed synthetic upstream dL/d(rgb, T) is propagated to the deformed
+    # Gaussians (means, cov3d, opacity, SH) and the mesh (vertices, colours, alpha)
+    opts_s = umgs.render_opts(16, save=True)
+    gen = torch.Generator(device=dev).manual_seed(1)
+    dl = torch.randn((1, H, W, 4), generator=gen, device=dev) * 1e-3
+
+    def step_fb(f):
+        step_deform(f)
+        umgs.render(ctx, gdef, [mesh], [cam], opts_s, out=out, frame=frame)
+        return umgs.render_backward(ctx, frame, gdef, [mesh], dl)
+
+    def step_deform(f):
+        umgs.deform(ctx, g, face, bary, PV, Vd_all[f % nframes], PF, out=(mu2, cov2, None))
+
+    for f in range(max(2, Wm)):
+        step_fb(f)
+    torch.cuda.synchronize()
+    umgs.profile_read(ctx)
+    umgs.profile_enable(ctx, True)
+    Kb = max(5, K // 2)
+    b0 = torch.cuda.Event(enable_timing=True)
+    b1 = torch.cuda.Event(enable_timing=True)
+    b0.record()
+    for f in range(Kb):
+        step_fb(f)
+    b1.record()
+    torch.cuda.synchronize()
+    fb_ms = b0.elapsed_time(b1) / Kb
+    fb_stage_ms, fb_stage_n = umgs.profile_read(ctx)
+    umgs.profile_enable(ctx, False)
+
     # end to end: per-step proxy upload from pinned host memory and image readback
     host_vd = torch.as_tensor(disp).pin_memory()
     host_out = torch.empty((1, H, W, 4), dtype=torch.float32).pin_memory()
@@ -223,6 +255,9 @@ def run_umgs(args, rank, world, local_rank):
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": int(sum(stage_n)) // 1,
         "stages_ms": {k: round(v["ms_per_launch"], 4) for k, v in stages.items()},
+        "fwd_bwd": {"value": round(1e3 / fb_ms * world, 3), "unit": "frames/s", "ms_per_step": round(fb_ms, 4),
+                    "steps": Kb, "backward_stages_ms": {names[k]: round(fb_stage_ms[k] / fb_stage_n[k], 4)
+                                                        for k in (12, 13) if fb_stage_n[k] > 0}},
         "bind_s": round(bind_s, 3),
         "roofline": roof,
         "clocks": clk,

@@ -90,13 +90,34 @@ typedef struct {
     float near_z;            /* primitives with Z <= near_z are culled */
 } umgs_camera;
 
+/* umgs_render_opts.flags */
+enum { UMGS_RENDER_SAVE_BACKWARD = 1 };  /* keep per-pixel state for umgs_render_backward (FULL mode) */
+
 typedef struct {
     int32_t tile_size;       /* 8, 16 or 32 pixels; 0 = 16 */
     int32_t blend_mode;      /* UMGS_BLEND_* */
     float t_eps;             /* early termination: stop after T < t_eps; 0 = never (default 1e-4) */
     float bg[3];             /* opaque background colour (Eq. 10-11) */
-    int32_t flags;           /* reserved, 0 */
+    int32_t flags;           /* UMGS_RENDER_* bits */
 } umgs_render_opts;
+
+/* Gradient outputs of umgs_render_backward; every pointer is nullable (not
+ * computed).  Shapes follow the inputs; all float32. */
+typedef struct {
+    float* means;      /* [n,3] */
+    float* quats;      /* [n,4]  (when the render used quats/scales) */
+    float* scales;     /* [n,3] */
+    float* opacities;  /* [n] */
+    float* sh;         /* [n,(deg+1)^2,3] */
+    float* cov3d;      /* [n,6]  (when the render used cov3d) */
+} umgs_gaussian_grads;
+
+typedef struct {
+    float* verts;      /* [nv,3] (through attribute interpolation; coverage is piecewise constant) */
+    float* vcolor;     /* [nv,3] */
+    float* valpha;     /* [nv]   (when the mesh has valpha and no falpha) */
+    float* falpha;     /* [nf]   (when the mesh has falpha) */
+} umgs_mesh_grads;
 
 /* ---- context ------------------------------------------------------------ */
 
@@ -159,6 +180,34 @@ umgs_status umgs_frame_counts(const umgs_frame* frame, int64_t* num_keys, int64_
  * bits; each list in ascending (depth bits, id).  Asynchronous on stream. */
 umgs_status umgs_frame_lists(const umgs_frame* frame, int64_t* tile_ptr, int32_t* ids,
                              uint32_t* dbits, void* stream);
+
+/* ---- backward (gradient of the composite) ----------------------------------
+ *
+ * Given dL/d(out_rgbt) of a umgs_render call that used a frame and the flag
+ * UMGS_RENDER_SAVE_BACKWARD (blend mode FULL), computes dL/d of the inputs:
+ * Gaussian means, quats, scales (or cov3d), opacities, SH; mesh vertex
+ * positions (through the perspective-correct attribute interpolation), vertex
+ * colours and alphas.  The sorted lists of the frame are replayed back to
+ * front per pixel; Gaussian transmittance is recovered by division
+ * (alpha <= 0.99), triangle entities use the per-pixel stack of sub-sample
+ * transmittances saved by the forward, so opaque triangles need no division.
+ * The derivative is that of the function the forward computed (early
+ * termination included); clamps (alpha max 0.99, alpha to [0,1], colour >= 0,
+ * barycentrics >= 0) pass the gradient at their boundary.
+ *
+ * frame      the frame of the forward call (same ctx)
+ * g, meshes  the SAME inputs as the forward call
+ * dL_drgbt   [ncams,H,W,4] device float: dL/dR, dL/dG, dL/dB, dL/dT
+ * gg, mg     host structs of device output pointers (mg: nmeshes entries);
+ *            outputs are overwritten (zero-filled first)
+ * Synchronises once (checks the saved-state capacity; if a pixel had more
+ * triangle fragments than the stack held, the forward composite is re-run
+ * with a larger stack first).  Errors: INVALID_ARG (no saved frame, sizes),
+ * NOT_IMPLEMENTED (blend modes other than FULL), OUT_OF_MEMORY, CUDA.
+ */
+umgs_status umgs_render_backward(umgs_ctx* ctx, umgs_frame* frame, const umgs_gaussians* g,
+                                 const umgs_mesh* meshes, int32_t nmeshes, const float* dL_drgbt,
+                                 const umgs_gaussian_grads* gg, const umgs_mesh_grads* mg, void* stream);
 
 /* ---- Gaussian-centric binding (Sec. 3.3, "Binding Gaussians to Mesh") -------
  *

@@ -172,13 +172,17 @@ def composite_torch(scene, p, fr, pixels, table, bg=(0.0, 0.0, 0.0)):
     py = torch.tensor([y + 0.5 for _, y in pixels], dtype=DT)[:, None].expand(P, L)
     kind_t = torch.as_tensor(kind)
     # Gaussian alpha and colour per (pixel, slot)
-    gi = torch.as_tensor(np.where(kind == 1, gid, 0))
-    dx = px - u[gi]
-    dy = py - v[gi]
-    A, B, C = conic[gi, 0], conic[gi, 1], conic[gi, 2]
-    power = -0.5 * (A * dx * dx + C * dy * dy) - B * dx * dy
-    ga = torch.clamp(opac[gi] * torch.exp(power), max=R.ALPHA_MAX)
-    gc = rgb[gi]
+    if ng > 0:
+        gi = torch.as_tensor(np.where(kind == 1, gid, 0))
+        dx = px - u[gi]
+        dy = py - v[gi]
+        A, B, C = conic[gi, 0], conic[gi, 1], conic[gi, 2]
+        power = -0.5 * (A * dx * dx + C * dy * dy) - B * dx * dy
+        ga = torch.clamp(opac[gi] * torch.exp(power), max=R.ALPHA_MAX)
+        gc = rgb[gi]
+    else:  # no Gaussians: no slot is a Gaussian slot
+        ga = torch.zeros((P, L), dtype=DT)
+        gc = torch.zeros((P, L, 3), dtype=DT)
     # triangle alpha and colour per (pixel, slot)
     ta = torch.zeros((P, L), dtype=DT)
     tc = torch.zeros((P, L, 3), dtype=DT)

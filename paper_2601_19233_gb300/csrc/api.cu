@@ -182,6 +182,30 @@ umgs_status umgs_render(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_mesh*
                           static_cast<cudaStream_t>(stream));
 }
 
+umgs_status umgs_render_backward(umgs_ctx* ctx, umgs_frame* frame, const umgs_gaussians* g,
+                                 const umgs_mesh* meshes, int32_t nmeshes, const float* dL_drgbt,
+                                 const umgs_gaussian_grads* gg, const umgs_mesh_grads* mg, void* stream) {
+    if (!ctx) return UMGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, UMGS_ERR_CUDA, "cudaSetDevice");
+    if (!frame || frame->ctx != ctx || !frame->valid) return fail(ctx, UMGS_ERR_INVALID_ARG, "no rendered frame");
+    if (frame->blend_mode != UMGS_BLEND_FULL)
+        return fail(ctx, UMGS_ERR_NOT_IMPLEMENTED, "backward is implemented for blend mode FULL");
+    if (!frame->saved) return fail(ctx, UMGS_ERR_INVALID_ARG, "render without UMGS_RENDER_SAVE_BACKWARD");
+    if (!dL_drgbt) return fail(ctx, UMGS_ERR_INVALID_ARG, "dL_drgbt is NULL");
+    const int64_t ng = g ? g->n : 0;
+    if (ng != frame->ng) return fail(ctx, UMGS_ERR_INVALID_ARG, "Gaussian count differs from the forward call");
+    if (nmeshes != (int32_t)frame->mesh_offset.size() || (nmeshes > 0 && !meshes))
+        return fail(ctx, UMGS_ERR_INVALID_ARG, "mesh count differs from the forward call");
+    int64_t nt = 0;
+    for (int m = 0; m < nmeshes; ++m) nt += meshes[m].nf;
+    if (nt != frame->nt) return fail(ctx, UMGS_ERR_INVALID_ARG, "triangle count differs from the forward call");
+    umgs_gaussians empty;
+    std::memset(&empty, 0, sizeof(empty));
+    return render_backward(ctx, frame, g ? g : &empty, meshes, nmeshes, dL_drgbt, gg, mg,
+                           static_cast<cudaStream_t>(stream));
+}
+
 umgs_status umgs_deform(umgs_ctx* ctx, const umgs_gaussians* rest, const int32_t* face, const float* bary,
                         const float* proxy_v, const float* proxy_vd, const int32_t* proxy_f, int64_t nv,
                         int64_t nf, int32_t mode, float* out_means, float* out_cov3d, float* out_quats,

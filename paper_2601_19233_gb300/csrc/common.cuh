@@ -75,6 +75,13 @@ struct __align__(16) BinInfo {
 __device__ __forceinline__ int sample_dx(int j) { return j == 0 ? -32 : j == 1 ? 96 : j == 2 ? -96 : 32; }
 __device__ __forceinline__ int sample_dy(int j) { return j == 0 ? -96 : j == 1 ? -32 : j == 2 ? 32 : 96; }
 
+// Gaussian alpha at offset (dx, dy) from the projected mean, with a fixed
+// operation sequence so the forward and the backward replay agree bit for bit:
+// power2 = ca dx^2 + cb dx dy + cc dy^2 (base-2 exponent), alpha = o 2^power2.
+__device__ __forceinline__ float gauss_power2(float ca, float cb, float cc, float dx, float dy) {
+    return __fmaf_rn(cc, __fmul_rn(dy, dy), __fmaf_rn(cb, __fmul_rn(dx, dy), __fmul_rn(ca, __fmul_rn(dx, dx))));
+}
+
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kLog2e = 1.4426950408889634f;

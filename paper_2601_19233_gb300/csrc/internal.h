@@ -36,6 +36,11 @@ struct umgs_frame {
     umgs_ctx* ctx = nullptr;
     umgs::DevBuf cams, grec, trec, bin, tile_count, tile_off, tile_fill, keys, keys_tmp;
     umgs::DevBuf last, status;
+    umgs::DevBuf tfin, ntri, stack;   // backward state (saved renders only)
+    umgs::DevBuf ggrad, tgrad, rerun_out;
+    int32_t stack_cap = 8;
+    bool saved = false;
+    umgs_render_opts opts{};
     int64_t ng = 0, nt = 0;          // Gaussians, triangles (all meshes)
     int32_t ncams = 0, W = 0, H = 0;
     int32_t tile = 16, tiles_x = 0, tiles_y = 0;
@@ -47,7 +52,7 @@ struct umgs_frame {
     std::vector<int64_t> mesh_offset;  // unified id of each mesh's first face
     void release() {
         for (auto* b : {&cams, &grec, &trec, &bin, &tile_count, &tile_off, &tile_fill, &keys, &keys_tmp,
-                        &last, &status})
+                        &last, &status, &tfin, &ntri, &stack, &ggrad, &tgrad, &rerun_out})
             b->release();
     }
 };
@@ -115,6 +120,12 @@ umgs_status bind_forward(umgs_ctx* ctx, const umgs_gaussians* g, const float* V,
                          int64_t nf, const umgs_camera* cams, int32_t ncams, int32_t mode, float k_sigma,
                          int32_t* out_face, float* out_bary, float* out_dist, uint8_t* out_flags,
                          int64_t* out_num_fallback, cudaStream_t stream);
+
+cudaError_t launch_composite(umgs_frame* fr, const umgs_render_opts& opts, float* out_rgbt, cudaStream_t stream);
+
+umgs_status render_backward(umgs_ctx* ctx, umgs_frame* fr, const umgs_gaussians* g, const umgs_mesh* meshes,
+                            int32_t nmeshes, const float* dL_drgbt, const umgs_gaussian_grads* gg,
+                            const umgs_mesh_grads* mg, cudaStream_t stream);
 
 umgs_status frame_lists(const umgs_frame* fr, int64_t* tile_ptr, int32_t* ids, uint32_t* dbits,
                         cudaStream_t stream);

@@ -284,10 +284,10 @@ __global__ void __launch_bounds__(256) setup_triangles_kernel(
             col[3 * k + d] = vcolor[3 * (int64_t)vid[k] + d];
         }
     }
-    int const_alpha = 1;
+    int const_alpha = 1;  // 0: interpolated vertex alpha, 1: face alpha, 2: no alpha (1)
     if (falpha) { al[0] = al[1] = al[2] = falpha[f]; }
     else if (valpha) { const_alpha = 0; al[0] = valpha[vid[0]]; al[1] = valpha[vid[1]]; al[2] = valpha[vid[2]]; }
-    else { al[0] = al[1] = al[2] = 1.f; }
+    else { const_alpha = 2; al[0] = al[1] = al[2] = 1.f; }
     for (int cam = 0; cam < ncams; ++cam) {
         const DevCam& C = cams[cam];
         const float* R = C.R;
@@ -507,11 +507,17 @@ struct PixelState {
     bool in_ent;
 };
 
-template <int TS>
+// SAVE: also keep what the backward pass needs: per pixel the final T and
+// the number of covering triangle fragments, and per covering triangle
+// fragment the four sub-sample transmittances before it (scaled by T_in/4)
+// in a per-pixel stack of capacity `cap` (`need` records the largest count).
+template <int TS, bool SAVE>
 __global__ void __launch_bounds__(TS * TS) composite_kernel(
     const uint64_t* __restrict__ keys, const int64_t* __restrict__ off, const GRec* __restrict__ grec,
     const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x, int tiles_per_cam, int W, int H,
-    float t_eps, float bg0, float bg1, float bg2, int mode, float4* __restrict__ out, int32_t* __restrict__ out_last) {
+    float t_eps, float bg0, float bg1, float bg2, int mode, float4* __restrict__ out, int32_t* __restrict__ out_last,
+    float* __restrict__ out_tfin, int32_t* __restrict__ out_ntri, float4* __restrict__ stack, int cap,
+    int64_t npix, int32_t* __restrict__ need) {
     constexpr int NT = TS * TS;
     __shared__ float4 s_rec[kBatch][10];
     __shared__ uint32_t s_id[kBatch];
@@ -534,6 +540,8 @@ __global__ void __launch_bounds__(TS * TS) composite_kernel(
     st.in_ent = false;
     bool done = !inside;
     int last = 0;
+    int sp = 0;
+    const int64_t pix = ((int64_t)cam * H + py) * W + px;
 
     for (int64_t b0 = beg; b0 < end; b0 += kBatch) {
         if (__syncthreads_count(done) == NT) break;
@@ -560,9 +568,9 @@ __global__ void __launch_bounds__(TS * TS) composite_kernel(
                     if (px < (int)(rx & 0xffff) || px > (int)(rx >> 16) || py < (int)(ry & 0xffff) || py > (int)(ry >> 16))
                         continue;
                     const float4 q0 = s_rec[k][0], q1 = s_rec[k][1];
-                    const float dx = qx - q0.x, dy = qy - q0.y;
-                    const float p2 = q0.z * dx * dx + q0.w * dx * dy + q1.x * dy * dy;
-                    const float alpha = fminf(kAlphaMax, q1.y * exp2f(p2));
+                    const float dx = __fsub_rn(qx, q0.x), dy = __fsub_rn(qy, q0.y);
+                    const float p2 = gauss_power2(q0.z, q0.w, q1.x, dx, dy);
+                    const float alpha = fminf(kAlphaMax, __fmul_rn(q1.y, exp2f(p2)));
                     if (alpha < kAlphaMin) continue;
                     const float w = alpha * st.T;
                     st.C[0] += w * q1.z; st.C[1] += w * q1.w; st.C[2] += w * q2.x;
@@ -630,6 +638,13 @@ __global__ void __launch_bounds__(TS * TS) composite_kernel(
                             st.g_since = 1.f;
                             st.in_ent = true;
                         }
+                        if (SAVE && mode == UMGS_BLEND_FULL) {
+                            if (sp < cap) {
+                                const float q = 0.25f * st.Tin;
+                                stack[(int64_t)sp * npix + pix] = make_float4(q * st.t[0], q * st.t[1], q * st.t[2], q * st.t[3]);
+                            }
+                            ++sp;
+                        }
                         float O = 0.f;
 #pragma unroll
                         for (int j = 0; j < 4; ++j) O += ((mask >> j) & 1) ? st.t[j] : 0.f;
@@ -649,9 +664,13 @@ __global__ void __launch_bounds__(TS * TS) composite_kernel(
         }
     }
     if (inside) {
-        const int64_t pix = ((int64_t)cam * H + py) * W + px;
         out[pix] = make_float4(st.C[0] + st.T * bg0, st.C[1] + st.T * bg1, st.C[2] + st.T * bg2, st.T);
         if (out_last) out_last[pix] = last;
+        if (SAVE) {
+            out_tfin[pix] = st.T;
+            out_ntri[pix] = sp;
+            if (sp > cap) atomicMax(need, sp);
+        }
     }
 }
 
@@ -665,6 +684,29 @@ __global__ void split_keys_kernel(const uint64_t* __restrict__ keys, int64_t n, 
     const uint64_t k = keys[i];
     ids[i] = (int32_t)(uint32_t)k;
     dbits[i] = (uint32_t)(k >> 32);
+}
+
+
+cudaError_t launch_composite(umgs_frame* fr, const umgs_render_opts& opts, float* out_rgbt, cudaStream_t stream) {
+    const float te = opts.t_eps > 0.f ? opts.t_eps : -1.f;
+    float4* out = reinterpret_cast<float4*>(out_rgbt);
+    const int ts = fr->tile;
+    const unsigned M = (unsigned)fr->num_tiles;
+    const int tpc = fr->tiles_x * fr->tiles_y;
+    const int64_t npix = (int64_t)fr->ncams * fr->W * fr->H;
+    const bool save = fr->saved;
+    if (save) cudaMemsetAsync(fr->status.as<int32_t>() + 2, 0, sizeof(int32_t), stream);
+#define UMGS_LAUNCH(TSV, SV)                                                                                    \
+    composite_kernel<TSV, SV><<<M, TSV * TSV, 0, stream>>>(                                                     \
+        fr->keys.as<uint64_t>(), fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->trec.as<TRec>(), fr->ng,  \
+        fr->nt, fr->tiles_x, tpc, fr->W, fr->H, te, opts.bg[0], opts.bg[1], opts.bg[2], opts.blend_mode, out,     \
+        fr->last.as<int32_t>(), save ? fr->tfin.as<float>() : nullptr, save ? fr->ntri.as<int32_t>() : nullptr,   \
+        save ? fr->stack.as<float4>() : nullptr, fr->stack_cap, npix, fr->status.as<int32_t>() + 2)
+    if (ts == 16) { if (save) UMGS_LAUNCH(16, true); else UMGS_LAUNCH(16, false); }
+    else if (ts == 8) { if (save) UMGS_LAUNCH(8, true); else UMGS_LAUNCH(8, false); }
+    else { if (save) UMGS_LAUNCH(32, true); else UMGS_LAUNCH(32, false); }
+#undef UMGS_LAUNCH
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -691,6 +733,7 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     fr->ng = Ng; fr->nt = Nt; fr->ncams = ncams; fr->W = W; fr->H = H;
     fr->tile = ts; fr->tiles_x = tiles_x; fr->tiles_y = tiles_y; fr->num_tiles = M;
     fr->blend_mode = opts.blend_mode; fr->t_eps = opts.t_eps;
+    fr->opts = opts;
     fr->bg[0] = opts.bg[0]; fr->bg[1] = opts.bg[1]; fr->bg[2] = opts.bg[2];
 
     cudaError_t e;
@@ -788,23 +831,17 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
         UMGS_TRY(cudaGetLastError());
     }
     UMGS_TRY(fr->last.reserve(sizeof(int32_t) * (int64_t)ncams * W * H));
-    const float te = opts.t_eps > 0.f ? opts.t_eps : -1.f;
-    float4* out = reinterpret_cast<float4*>(out_rgbt);
-    int32_t* last = fr->last.as<int32_t>();
-    StageTimer tm_comp(ctx, UMGS_STAGE_COMPOSITE, stream);
-    if (ts == 16)
-        composite_kernel<16><<<(unsigned)M, 256, 0, stream>>>(
-            fr->keys.as<uint64_t>(), fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->trec.as<TRec>(), Ng, Nt,
-            tiles_x, tiles_per_cam, W, H, te, opts.bg[0], opts.bg[1], opts.bg[2], opts.blend_mode, out, last);
-    else if (ts == 8)
-        composite_kernel<8><<<(unsigned)M, 64, 0, stream>>>(
-            fr->keys.as<uint64_t>(), fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->trec.as<TRec>(), Ng, Nt,
-            tiles_x, tiles_per_cam, W, H, te, opts.bg[0], opts.bg[1], opts.bg[2], opts.blend_mode, out, last);
-    else
-        composite_kernel<32><<<(unsigned)M, 1024, 0, stream>>>(
-            fr->keys.as<uint64_t>(), fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->trec.as<TRec>(), Ng, Nt,
-            tiles_x, tiles_per_cam, W, H, te, opts.bg[0], opts.bg[1], opts.bg[2], opts.blend_mode, out, last);
-    UMGS_TRY(cudaGetLastError());
+    fr->saved = (opts.flags & UMGS_RENDER_SAVE_BACKWARD) != 0 && opts.blend_mode == UMGS_BLEND_FULL;
+    if (fr->saved) {
+        const int64_t npix = (int64_t)ncams * W * H;
+        UMGS_TRY(fr->tfin.reserve(sizeof(float) * npix));
+        UMGS_TRY(fr->ntri.reserve(sizeof(int32_t) * npix));
+        UMGS_TRY(fr->stack.reserve(sizeof(float4) * npix * fr->stack_cap));
+    }
+    {
+        StageTimer tm_comp(ctx, UMGS_STAGE_COMPOSITE, stream);
+        UMGS_TRY(launch_composite(fr, opts, out_rgbt, stream));
+    }
     fr->valid = true;
 #undef UMGS_TRY
     return UMGS_OK;

@@ -23,6 +23,7 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "OUT_OF_MEMORY", 3: "CAPACITY", 4: "CUDA
 BLEND_FULL, BLEND_DIRECT, BLEND_MSAA_ALL, BLEND_ENTITY_ALL = 0, 1, 2, 3
 F32, BF16 = 0, 1
 BIND_BBX, BIND_CENTER, BIND_NEAREST = 0, 1, 2
+RENDER_SAVE_BACKWARD = 1
 DEFORM_FRAME, DEFORM_LITERAL = 0, 1
 
 
@@ -48,6 +49,16 @@ class CCamera(ctypes.Structure):
     _fields_ = [("viewmat", ctypes.c_float * 12), ("fx", ctypes.c_float), ("fy", ctypes.c_float),
                 ("cx", ctypes.c_float), ("cy", ctypes.c_float), ("width", ctypes.c_int32),
                 ("height", ctypes.c_int32), ("near_z", ctypes.c_float)]
+
+
+class CGaussianGrads(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("quats", ctypes.c_void_p), ("scales", ctypes.c_void_p),
+                ("opacities", ctypes.c_void_p), ("sh", ctypes.c_void_p), ("cov3d", ctypes.c_void_p)]
+
+
+class CMeshGrads(ctypes.Structure):
+    _fields_ = [("verts", ctypes.c_void_p), ("vcolor", ctypes.c_void_p), ("valpha", ctypes.c_void_p),
+                ("falpha", ctypes.c_void_p)]
 
 
 class CRenderOpts(ctypes.Structure):
@@ -84,6 +95,9 @@ def lib():
         L.umgs_bind.argtypes = [vp, ctypes.POINTER(CGaussians), vp, vp, i64, i64, ctypes.POINTER(CCamera), i32, i32,
                                 ctypes.c_float, vp, vp, vp, vp, ctypes.POINTER(i64), vp]
         L.umgs_bind.restype = ctypes.c_int
+        L.umgs_render_backward.argtypes = [vp, vp, ctypes.POINTER(CGaussians), ctypes.POINTER(CMesh), i32, vp,
+                                           ctypes.POINTER(CGaussianGrads), ctypes.POINTER(CMeshGrads), vp]
+        L.umgs_render_backward.restype = ctypes.c_int
         L.umgs_deform_noalloc.argtypes = [ctypes.POINTER(CGaussians), vp, vp, vp, vp, vp, i64, i64, i32, vp, vp,
                                           vp, vp]
         L.umgs_deform_noalloc.restype = ctypes.c_int
@@ -236,9 +250,10 @@ def mesh_to_device(m, device="cuda") -> DevMesh:
                    _t(m.valpha, device), _t(m.falpha, device))
 
 
-def render_opts(tile_size=16, blend_mode=BLEND_FULL, t_eps=1e-4, bg=(0.0, 0.0, 0.0)) -> CRenderOpts:
+def render_opts(tile_size=16, blend_mode=BLEND_FULL, t_eps=1e-4, bg=(0.0, 0.0, 0.0), save=False) -> CRenderOpts:
     o = CRenderOpts()
     lib().umgs_default_render_opts(ctypes.byref(o))
+    o.flags = RENDER_SAVE_BACKWARD if save else 0
     o.tile_size = int(tile_size)
     o.blend_mode = int(blend_mode)
     o.t_eps = float(t_eps)
@@ -352,3 +367,41 @@ def bind_or_fallback(ctx, g, proxy_v, proxy_f, cameras, device):
     b = torch.rand((n, 8, 2), generator=gen, device=device)
     b = torch.where(b.sum(-1, keepdim=True) > 1, 1 - b, b).contiguous()
     return face, b, "synthetic random table"
+
+
+def render_backward(ctx: Context, frame: Frame, gaussians: DevGaussians | None, meshes, dL_drgbt: torch.Tensor,
+                    stream=None):
+    """umgs_render_backward: returns dict of gradient tensors (Gaussian and per-mesh)."""
+    dev = torch.device("cuda", ctx.device)
+    out = {}
+    cg = None
+    gg = CGaussianGrads()
+    if gaussians is not None and gaussians.n > 0:
+        n = gaussians.n
+        out["means"] = torch.empty((n, 3), device=dev)
+        out["opacities"] = torch.empty((n,), device=dev)
+        out["sh"] = torch.empty(tuple(gaussians.sh.shape), device=dev, dtype=torch.float32)
+        if gaussians.cov3d is not None:
+            out["cov3d"] = torch.empty((n, 6), device=dev)
+        else:
+            out["quats"] = torch.empty((n, 4), device=dev)
+            out["scales"] = torch.empty((n, 3), device=dev)
+        gg = CGaussianGrads(_ptr(out["means"]), _ptr(out.get("quats")), _ptr(out.get("scales")),
+                            _ptr(out["opacities"]), _ptr(out["sh"]), _ptr(out.get("cov3d")))
+        cg = gaussians.c()
+    mgs = []
+    for mi, m in enumerate(meshes):
+        out["verts%d" % mi] = torch.empty_like(m.verts)
+        out["vcolor%d" % mi] = torch.empty_like(m.vcolor)
+        fa = va = None
+        if m.falpha is not None:
+            fa = out["falpha%d" % mi] = torch.empty_like(m.falpha)
+        elif m.valpha is not None:
+            va = out["valpha%d" % mi] = torch.empty_like(m.valpha)
+        mgs.append(CMeshGrads(_ptr(out["verts%d" % mi]), _ptr(out["vcolor%d" % mi]), _ptr(va), _ptr(fa)))
+    cm = (CMesh * max(1, len(meshes)))(*[m.c() for m in meshes]) if meshes else None
+    cmg = (CMeshGrads * max(1, len(mgs)))(*mgs) if mgs else None
+    st = lib().umgs_render_backward(ctx._h, frame._h, ctypes.byref(cg) if cg is not None else None, cm, len(meshes),
+                                    _ptr(dL_drgbt.contiguous()), ctypes.byref(gg), cmg, _stream(stream))
+    ctx.check(st, "umgs_render_backward")
+    return out

@@ -1,0 +1,92 @@
+"""GPU backward (umgs_render_backward) against the fp64 autograd oracle.
+
+Tolerance per parameter group: |g - g_ref| <= 1e-3 max|g_ref| + 1e-6 (fp32
+accumulation with atomics against fp64).  Upstream gradients are zeroed on
+tie pixels (a decision within rounding of a threshold)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import grad as OG
+from oracle import render as R
+from paper_2601_19233_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2601_19233_gb300 import build, umgs
+    build.build()
+    return umgs.Context(0)
+
+
+def _run(ctx, sc, seed, tile=None, use_cov3d=False):
+    from paper_2601_19233_gb300 import umgs
+    cam = sc.cameras[0]
+    H, W = cam.height, cam.width
+    rng = np.random.default_rng(seed)
+    ref_img = R.render_image(sc)
+    gC = rng.normal(size=(H, W, 3))
+    gT = rng.normal(size=(H, W))
+    gC[ref_img["tie"]] = 0
+    gT[ref_img["tie"]] = 0
+    cov = None
+    if use_cov3d:
+        from oracle.deform import sym6
+        from oracle.render import cov3d_fp64
+        cov = sym6(cov3d_fp64(sc.gaussians.quats, sc.gaussians.scales)).astype(np.float32)
+    ref, rgb, T = OG.image_grad(sc, gC, gT, cov3d=cov)
+    g = umgs.gaussians_to_device(sc.gaussians)
+    if use_cov3d:
+        g.cov3d = torch.as_tensor(cov).cuda()
+    ms = [umgs.mesh_to_device(m) for m in sc.meshes]
+    fr = umgs.Frame(ctx)
+    out = umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(tile or sc.tile, save=True), frame=fr)
+    dl = torch.as_tensor(np.concatenate([gC, gT[..., None]], -1)[None].astype(np.float32)).cuda()
+    grads = umgs.render_backward(ctx, fr, g, ms, dl)
+    torch.cuda.synchronize()
+    return ref, {k: v.cpu().numpy() for k, v in grads.items()}, out.cpu().numpy(), rgb
+
+
+def _compare(ref, got, names):
+    for k in names:
+        r = ref[k]
+        gk = got[k].reshape(r.shape)
+        scale = np.abs(r).max()
+        err = np.abs(gk - r).max()
+        assert err <= 1e-3 * scale + 1e-6, (k, err, scale)
+
+
+def test_config0_gradients(ctx):
+    sc = S.config0()
+    ref, got, out, rgb = _run(ctx, sc, 0)
+    _compare(ref, got, ["means", "quats", "scales", "opacities", "sh", "verts0", "vcolor0", "falpha0"])
+
+
+@pytest.mark.parametrize("seed,W,H,n,deg,valpha", [(71, 45, 37, 500, 3, True), (72, 40, 52, 700, 1, False)])
+def test_small_scene_gradients(ctx, seed, W, H, n, deg, valpha):
+    sc = S.small_scene(seed, W, H, n, mesh_subdiv=2, sh_degree=deg, with_valpha=valpha)
+    ref, got, out, rgb = _run(ctx, sc, seed, tile=16)
+    names = ["means", "quats", "scales", "opacities", "sh", "verts0", "vcolor0"]
+    names.append("valpha0" if valpha else "falpha0")
+    _compare(ref, got, names)
+
+
+def test_cov3d_input_gradients(ctx):
+    sc = S.small_scene(81, 33, 29, 300, mesh_subdiv=1, sh_degree=0)
+    ref, got, out, rgb = _run(ctx, sc, 81, tile=8, use_cov3d=True)
+    _compare(ref, got, ["means", "cov3d", "opacities", "sh", "verts0", "vcolor0", "falpha0"])
+
+
+def test_opaque_stack_overflow_rerun(ctx):
+    # 12 full-screen opaque-ish quads stacked: more triangle fragments per pixel
+    # than the initial saved-state capacity, exercising the re-run path
+    from tests import helpers as Hh
+    c = Hh.cam(20, 16)
+    qs = [Hh.screen_quad(c, z, 0.3, (0.1 * i, 0.5, 1 - 0.05 * i)) for i, z in enumerate(np.linspace(-1.5, 0.8, 12))]
+    m = S.Mesh(np.concatenate([q.verts for q in qs]), np.concatenate([q.faces + 4 * i for i, q in enumerate(qs)]),
+               np.concatenate([q.vcolor for q in qs]), None, np.concatenate([q.falpha for q in qs]))
+    sc = Hh.scene(Hh.no_gaussians(), [m], c)
+    ref, got, out, rgb = _run(ctx, sc, 5, tile=8)
+    _compare(ref, got, ["verts0", "vcolor0", "falpha0"])
