@@ -108,7 +108,7 @@ def build_workload(n_gauss, frames):
 def stage_names():
     return ["project_gaussians", "setup_triangles", "scan", "scatter", "sort", "composite", "deform_faces",
             "deform_vertices", "deform_gaussians", "bind_grid", "bind_raycast", "bind_nearest",
-            "backward_composite", "backward_project", "s14", "s15"]
+            "backward_composite", "backward_project", "shade_gaussians", "s15"]
 
 
 def run_umgs(args, rank, world, local_rank):

@@ -287,7 +287,8 @@ enum {
     UMGS_STAGE_PROJECT_GAUSSIANS = 0, UMGS_STAGE_SETUP_TRIANGLES, UMGS_STAGE_SCAN, UMGS_STAGE_SCATTER,
     UMGS_STAGE_SORT, UMGS_STAGE_COMPOSITE, UMGS_STAGE_DEFORM_FACES, UMGS_STAGE_DEFORM_VERTICES,
     UMGS_STAGE_DEFORM_GAUSSIANS, UMGS_STAGE_BIND_GRID, UMGS_STAGE_BIND_RAYCAST, UMGS_STAGE_BIND_NEAREST,
-    UMGS_STAGE_BACKWARD_COMPOSITE, UMGS_STAGE_BACKWARD_PROJECT, UMGS_NUM_STAGES = 16
+    UMGS_STAGE_BACKWARD_COMPOSITE, UMGS_STAGE_BACKWARD_PROJECT, UMGS_STAGE_SHADE_GAUSSIANS,
+    UMGS_NUM_STAGES = 16
 };
 umgs_status umgs_profile_enable(umgs_ctx* ctx, int32_t on);
 umgs_status umgs_profile_read(umgs_ctx* ctx, double* ms, int64_t* launches);

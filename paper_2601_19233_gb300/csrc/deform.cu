@@ -8,10 +8,11 @@
 //                    D_v = R_v S_v (Jacobi eigen-decomposition of D^T D),
 //                    r_v = log R_v, Delta_v = V'_v - V_v -> a 48-byte row of
 //                    the vertex table (stays in L2: 10K vertices = 0.5 MB).
-//   deform_gaussians one thread per Gaussian: 8 bound points x 3 vertex rows
-//                    gathered from the table, Eq. 12 interpolation, Eq. 13
-//                    averaging, R' = exp(mean r), Sigma' = A Sigma A^T with
-//                    A = R'S', mu' (FRAME or LITERAL), q' = quat(R') q.
+//   deform_gaussians eight threads per Gaussian (one per bound point): 3 vertex
+//                    rows gathered from the table each, Eq. 12 interpolation,
+//                    shuffle-reduced over the 8 points, Eq. 13 averaging,
+//                    R' = exp(mean r), Sigma' = A Sigma A^T with A = R'S',
+//                    mu' (FRAME or LITERAL), q' = quat(R') q.
 //                    Streams 136 B in and 52 B out per Gaussian.
 #include <cmath>
 #include <mutex>
@@ -263,68 +264,84 @@ __device__ void exp_rot(const float r[3], float R[9], float q[4]) {
     q[0] = hc; q[1] = hs * x; q[2] = hs * y; q[3] = hs * z;
 }
 
+// One thread per (Gaussian, bound point): 8 consecutive lanes gather the
+// Eq. 12 interpolants of one Gaussian's 8 points (independent loads, and a
+// single broadcast when points share a face), reduce them with shuffles and
+// then all 8 lanes evaluate Eq. 13; lanes 0-2 write mu', Sigma', q'.
 __global__ void __launch_bounds__(256) deform_gaussians_kernel(
     const float* __restrict__ means, const float* __restrict__ quats, const float* __restrict__ scales,
     const float* __restrict__ cov3d, int64_t n, const int32_t* __restrict__ face, const float* __restrict__ bary,
     const float* __restrict__ V, const int32_t* __restrict__ F, int64_t nv, int64_t nf,
     const float* __restrict__ vtab, int mode, float* __restrict__ out_means, float* __restrict__ out_cov,
     float* __restrict__ out_quats, int32_t* __restrict__ status) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const int4 f0 = reinterpret_cast<const int4*>(face)[2 * i];
-    const int4 f1 = reinterpret_cast<const int4*>(face)[2 * i + 1];
-    const int fid[8] = {f0.x, f0.y, f0.z, f0.w, f1.x, f1.y, f1.z, f1.w};
-    const float4* bp = reinterpret_cast<const float4*>(bary) + 4 * i;
-    float bb[16];
-    for (int k = 0; k < 4; ++k) { const float4 t = bp[k]; bb[4 * k] = t.x; bb[4 * k + 1] = t.y; bb[4 * k + 2] = t.z; bb[4 * k + 3] = t.w; }
-    float dsum[3] = {0, 0, 0}, rsum[3] = {0, 0, 0}, ssum[6] = {0, 0, 0, 0, 0, 0}, psum[3] = {0, 0, 0};
-    bool bad = false;
-    for (int c = 0; c < 8; ++c) {
-        const int f = fid[c];
-        if (f < 0 || f >= nf) { bad = true; break; }
-        const float b1 = bb[2 * c], b2 = bb[2 * c + 1];
-        const float w[3] = {1.f - b1 - b2, b1, b2};
-        for (int k = 0; k < 3; ++k) {
-            const int v = F[3 * (int64_t)f + k];
-            if (v < 0 || v >= nv) { bad = true; break; }
-            const float4* row = reinterpret_cast<const float4*>(vtab + 12 * (int64_t)v);
-            const float4 t0 = row[0], t1 = row[1], t2 = row[2];
-            const float wk = w[k];
-            dsum[0] += wk * t0.x; dsum[1] += wk * t0.y; dsum[2] += wk * t0.z;
-            rsum[0] += wk * t0.w; rsum[1] += wk * t1.x; rsum[2] += wk * t1.y;
-            ssum[0] += wk * t1.z; ssum[1] += wk * t1.w; ssum[2] += wk * t2.x;
-            ssum[3] += wk * t2.y; ssum[4] += wk * t2.z; ssum[5] += wk * t2.w;
-            psum[0] += wk * V[3 * (int64_t)v]; psum[1] += wk * V[3 * (int64_t)v + 1]; psum[2] += wk * V[3 * (int64_t)v + 2];
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = tid >> 3;
+    const int corner = (int)(tid & 7);
+    const bool live = i < n;
+    float acc[15];
+#pragma unroll
+    for (int e = 0; e < 15; ++e) acc[e] = 0.f;
+    int bad = 0;
+    if (live) {
+        const int f = face[8 * i + corner];
+        const float2 b = reinterpret_cast<const float2*>(bary)[8 * i + corner];
+        if (f < 0 || f >= nf) {
+            bad = 1;
+        } else {
+            const float w[3] = {1.f - b.x - b.y, b.x, b.y};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int v = F[3 * (int64_t)f + k];
+                if (v < 0 || v >= nv) { bad = 1; continue; }
+                const float4* row = reinterpret_cast<const float4*>(vtab + 12 * (int64_t)v);
+                const float4 t0 = row[0], t1 = row[1], t2 = row[2];
+                const float px = V[3 * (int64_t)v], py = V[3 * (int64_t)v + 1], pz = V[3 * (int64_t)v + 2];
+                const float wk = w[k];
+                acc[0] += wk * t0.x; acc[1] += wk * t0.y; acc[2] += wk * t0.z;     // Delta
+                acc[3] += wk * t0.w; acc[4] += wk * t1.x; acc[5] += wk * t1.y;     // log R
+                acc[6] += wk * t1.z; acc[7] += wk * t1.w; acc[8] += wk * t2.x;     // S
+                acc[9] += wk * t2.y; acc[10] += wk * t2.z; acc[11] += wk * t2.w;
+                acc[12] += wk * px; acc[13] += wk * py; acc[14] += wk * pz;         // P
+            }
         }
-        if (bad) break;
     }
+    // sum over the 8 lanes of this Gaussian
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+#pragma unroll
+        for (int e = 0; e < 15; ++e) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if (!live || corner > 2) return;
     if (bad) {
-        atomicOr(status, kStatusBadIndex);
+        if (corner == 0) atomicOr(status, kStatusBadIndex);
         const float nanv = __int_as_float(0x7fc00000);
-        for (int d = 0; d < 3; ++d) out_means[3 * i + d] = nanv;
-        for (int d = 0; d < 6; ++d) out_cov[6 * i + d] = nanv;
-        if (out_quats) for (int d = 0; d < 4; ++d) out_quats[4 * i + d] = nanv;
+        if (corner == 0) for (int d = 0; d < 3; ++d) out_means[3 * i + d] = nanv;
+        if (corner == 1) for (int d = 0; d < 6; ++d) out_cov[6 * i + d] = nanv;
+        if (corner == 2 && out_quats) for (int d = 0; d < 4; ++d) out_quats[4 * i + d] = nanv;
         return;
     }
     const float e = 0.125f;
-    float rb[3] = {rsum[0] * e, rsum[1] * e, rsum[2] * e};
+    float rb[3] = {acc[3] * e, acc[4] * e, acc[5] * e};
     float Rp[9], qr[4];
     exp_rot(rb, Rp, qr);
-    const float Sb[9] = {ssum[0] * e, ssum[1] * e, ssum[2] * e, ssum[1] * e, ssum[3] * e, ssum[4] * e,
-                         ssum[2] * e, ssum[4] * e, ssum[5] * e};
+    const float Sb[9] = {acc[6] * e, acc[7] * e, acc[8] * e, acc[7] * e, acc[9] * e, acc[10] * e,
+                         acc[8] * e, acc[10] * e, acc[11] * e};
     float A[9];
     matmul3(Rp, Sb, A);
-    const float mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
-    float mo[3];
-    for (int d = 0; d < 3; ++d) mo[d] = mu[d] + dsum[d] * e;
-    if (mode == UMGS_DEFORM_FRAME) {
-        const float rel[3] = {mu[0] - psum[0] * e, mu[1] - psum[1] * e, mu[2] - psum[2] * e};
-        for (int d = 0; d < 3; ++d) mo[d] += A[3 * d] * rel[0] + A[3 * d + 1] * rel[1] + A[3 * d + 2] * rel[2] - rel[d];
+    if (corner == 0) {
+        const float mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
+        float mo[3];
+        for (int d = 0; d < 3; ++d) mo[d] = mu[d] + acc[d] * e;
+        if (mode == UMGS_DEFORM_FRAME) {
+            const float rel[3] = {mu[0] - acc[12] * e, mu[1] - acc[13] * e, mu[2] - acc[14] * e};
+            for (int d = 0; d < 3; ++d) mo[d] += A[3 * d] * rel[0] + A[3 * d + 1] * rel[1] + A[3 * d + 2] * rel[2] - rel[d];
+        }
+        for (int d = 0; d < 3; ++d) out_means[3 * i + d] = mo[d];
+        return;
     }
-    for (int d = 0; d < 3; ++d) out_means[3 * i + d] = mo[d];
-    // Sigma
-    float S[9];
     float qn[4] = {1.f, 0.f, 0.f, 0.f};
+    float S[9];
     if (cov3d) {
         const float* c6 = cov3d + 6 * i;
         S[0] = c6[0]; S[1] = c6[1]; S[2] = c6[2]; S[3] = c6[1]; S[4] = c6[3]; S[5] = c6[4];
@@ -334,22 +351,29 @@ __global__ void __launch_bounds__(256) deform_gaussians_kernel(
         const float nq = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
         if (nq > 0.f) { qw /= nq; qx /= nq; qy /= nq; qz /= nq; } else { qw = 1.f; qx = qy = qz = 0.f; }
         qn[0] = qw; qn[1] = qx; qn[2] = qy; qn[3] = qz;
-        const float r[9] = {1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
-                            2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
-                            2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)};
-        const float s[3] = {scales[3 * i], scales[3 * i + 1], scales[3 * i + 2]};
-        float M[9];
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) M[3 * a + b] = r[3 * a + b] * s[b];
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) S[3 * a + b] = M[3 * a] * M[3 * b] + M[3 * a + 1] * M[3 * b + 1] + M[3 * a + 2] * M[3 * b + 2];
+        if (corner == 1) {
+            const float r[9] = {1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
+                                2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
+                                2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)};
+            const float s[3] = {scales[3 * i], scales[3 * i + 1], scales[3 * i + 2]};
+            float M[9];
+            for (int a = 0; a < 3; ++a)
+                for (int bb = 0; bb < 3; ++bb) M[3 * a + bb] = r[3 * a + bb] * s[bb];
+            for (int a = 0; a < 3; ++a)
+                for (int bb = 0; bb < 3; ++bb)
+                    S[3 * a + bb] = M[3 * a] * M[3 * bb] + M[3 * a + 1] * M[3 * bb + 1] + M[3 * a + 2] * M[3 * bb + 2];
+        }
     }
-    float AS[9], Sig[9];
-    matmul3(A, S, AS);
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) Sig[3 * a + b] = AS[3 * a] * A[3 * b] + AS[3 * a + 1] * A[3 * b + 1] + AS[3 * a + 2] * A[3 * b + 2];
-    float* oc = out_cov + 6 * i;
-    oc[0] = Sig[0]; oc[1] = Sig[1]; oc[2] = Sig[2]; oc[3] = Sig[4]; oc[4] = Sig[5]; oc[5] = Sig[8];
+    if (corner == 1) {
+        float AS[9], Sig[9];
+        matmul3(A, S, AS);
+        for (int a = 0; a < 3; ++a)
+            for (int bb = 0; bb < 3; ++bb)
+                Sig[3 * a + bb] = AS[3 * a] * A[3 * bb] + AS[3 * a + 1] * A[3 * bb + 1] + AS[3 * a + 2] * A[3 * bb + 2];
+        float* oc = out_cov + 6 * i;
+        oc[0] = Sig[0]; oc[1] = Sig[1]; oc[2] = Sig[2]; oc[3] = Sig[4]; oc[4] = Sig[5]; oc[5] = Sig[8];
+        return;
+    }
     if (out_quats) {
         // q' = qr * qn (Hamilton product), canonical sign w >= 0
         float o[4];
@@ -385,7 +409,7 @@ umgs_status deform_forward(umgs_ctx* ctx, const umgs_gaussians* g, const int32_t
     }
     StageTimer tm(ctx, UMGS_STAGE_DEFORM_GAUSSIANS, stream);
     if (g->n > 0)
-        deform_gaussians_kernel<<<grid_for(g->n, 256), 256, 0, stream>>>(
+        deform_gaussians_kernel<<<grid_for(8 * g->n, 256), 256, 0, stream>>>(
             g->means, g->quats, g->scales, g->cov3d, g->n, face, bary, V, F, nv, nf, ctx->vtab.as<float>(), mode,
             out_means, out_cov, out_quats, status);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "deform kernels");
@@ -473,7 +497,7 @@ extern "C" umgs_status umgs_deform_noalloc(const umgs_gaussians* rest, const int
     face_gradients_kernel<<<grid_for(nf, 256), 256, 0, s>>>(proxy_v, proxy_vd, proxy_f, nv, nf, vacc, status);
     vertex_xforms_kernel<<<grid_for(nv, 256), 256, 0, s>>>(proxy_v, proxy_vd, vacc, nv, vtab);
     if (rest->n > 0)
-        deform_gaussians_kernel<<<grid_for(rest->n, 256), 256, 0, s>>>(
+        deform_gaussians_kernel<<<grid_for(8 * rest->n, 256), 256, 0, s>>>(
             rest->means, rest->quats, rest->scales, rest->cov3d, rest->n, face, bary, proxy_v, proxy_f, nv, nf, vtab,
             mode, out_means, out_cov3d, out_quats, status);
     return cudaGetLastError() == cudaSuccess ? UMGS_OK : UMGS_ERR_CUDA;

@@ -38,6 +38,7 @@ struct umgs_frame {
     umgs::DevBuf last, status;
     umgs::DevBuf tfin, ntri, stack;   // backward state (saved renders only)
     umgs::DevBuf ggrad, tgrad, rerun_out;
+    umgs::DevBuf fix_list;            // (camera, Gaussian) records whose conic is refined in fp64
     int32_t stack_cap = 8;
     bool saved = false;
     umgs_render_opts opts{};
@@ -52,7 +53,7 @@ struct umgs_frame {
     std::vector<int64_t> mesh_offset;  // unified id of each mesh's first face
     void release() {
         for (auto* b : {&cams, &grec, &trec, &bin, &tile_count, &tile_off, &tile_fill, &keys, &keys_tmp,
-                        &last, &status, &tfin, &ntri, &stack, &ggrad, &tgrad, &rerun_out})
+                        &last, &status, &tfin, &ntri, &stack, &ggrad, &tgrad, &rerun_out, &fix_list})
             b->release();
     }
 };

@@ -26,54 +26,8 @@
 namespace umgs {
 
 // ---------------------------------------------------------------------------
-// spherical harmonics (3DGS colour model), degree <= 3, fp32.
-// Real SH with the Condon-Shortley phase, index l*l + (m + l).
-__device__ __forceinline__ float sh_coef(const void* sh, int dtype, int64_t base, int c) {
-    if (dtype == UMGS_BF16) {
-        const unsigned short* p = static_cast<const unsigned short*>(sh);
-        return __uint_as_float(((unsigned int)p[base + c]) << 16);
-    }
-    return static_cast<const float*>(sh)[base + c];
-}
-
-__device__ void eval_sh(const void* sh, int dtype, int deg, int64_t i, float dx, float dy, float dz, float rgb[3]) {
-    const int K = (deg + 1) * (deg + 1);
-    const int64_t base = i * (int64_t)K * 3;
-    float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
-    float x = dx * inv, y = dy * inv, z = dz * inv;
-    float Y[16];
-    Y[0] = 0.28209479177387814f;                    // 1/(2 sqrt(pi))
-    if (deg > 0) {
-        const float c1 = 0.4886025119029199f;       // sqrt(3/(4 pi))
-        Y[1] = -c1 * y;
-        Y[2] = c1 * z;
-        Y[3] = -c1 * x;
-    }
-    if (deg > 1) {
-        const float xx = x * x, yy = y * y, zz = z * z;
-        Y[4] = 1.0925484305920792f * x * y;           // sqrt(15/pi)/2
-        Y[5] = -1.0925484305920792f * y * z;
-        Y[6] = 0.31539156525252005f * (2.f * zz - xx - yy);  // sqrt(5/pi)/4
-        Y[7] = -1.0925484305920792f * x * z;
-        Y[8] = 0.5462742152960396f * (xx - yy);       // sqrt(15/pi)/4
-        if (deg > 2) {
-            Y[9] = -0.5900435899266435f * y * (3.f * xx - yy);          // sqrt(35/(2 pi))/4
-            Y[10] = 2.890611442640554f * x * y * z;                      // sqrt(105/pi)/2
-            Y[11] = -0.4570457994644658f * y * (4.f * zz - xx - yy);    // sqrt(21/(2 pi))/4
-            Y[12] = 0.3731763325901154f * z * (2.f * zz - 3.f * xx - 3.f * yy);  // sqrt(7/pi)/4
-            Y[13] = -0.4570457994644658f * x * (4.f * zz - xx - yy);
-            Y[14] = 1.445305721320277f * z * (xx - yy);                  // sqrt(105/pi)/4
-            Y[15] = -0.5900435899266435f * x * (xx - 3.f * yy);
-        }
-    }
-    for (int c = 0; c < 3; ++c) {
-        float acc = 0.f;
-#pragma unroll
-        for (int k = 0; k < 16; ++k)
-            if (k < K) acc = fmaf(sh_coef(sh, dtype, base + 3 * k, c), Y[k], acc);
-        rgb[c] = fmaxf(acc + 0.5f, 0.f);
-    }
-}
+// spherical harmonics (3DGS colour model), degree <= 3, fp32: real SH with
+// the Condon-Shortley phase, index l*l + (m + l), see shade_gaussians_kernel.
 
 // ---------------------------------------------------------------------------
 // canonical Gaussian covariance and projection
@@ -141,26 +95,67 @@ __device__ void cov2d_fp64(const DevCam& C, float mx, float my, float mz, const 
     c = U[1][0] * T[1][0] + U[1][1] * T[1][1] + U[1][2] * T[1][2] + 0.3;
 }
 
-__global__ void __launch_bounds__(256) project_gaussians_kernel(
+// Conic of a near-singular projected covariance, in fp64 (rare; kept out of
+// line so the common path does not pay for its registers).
+__device__ __noinline__ void conic_fp64(const DevCam& C, float mx, float my, float mz,
+                                        const float* __restrict__ quats, const float* __restrict__ scales,
+                                        const float* __restrict__ cov3d, int64_t i, float* out) {
+    float q[4] = {0, 0, 0, 0}, s[3] = {0, 0, 0}, c6[6];
+    if (cov3d) {
+        for (int k = 0; k < 6; ++k) c6[k] = cov3d[6 * i + k];
+    } else {
+        for (int k = 0; k < 4; ++k) q[k] = quats[4 * i + k];
+        for (int k = 0; k < 3; ++k) s[k] = scales[3 * i + k];
+    }
+    double A2, B2, C2;
+    cov2d_fp64(C, mx, my, mz, q, s, cov3d ? c6 : nullptr, A2, B2, C2);
+    const double d2 = A2 * C2 - B2 * B2;
+    out[0] = (float)(C2 / d2);
+    out[1] = (float)(-B2 / d2);
+    out[2] = (float)(A2 / d2);
+}
+
+// fp64 conics of the (camera, Gaussian) records listed by project_gaussians;
+// when the list overflowed every record is re-tested.
+__global__ void refine_conics_kernel(const float* __restrict__ means, const float* __restrict__ quats,
+                                     const float* __restrict__ scales, const float* __restrict__ cov3d, int64_t N,
+                                     const DevCam* __restrict__ cams, int ncams, const BinInfo* __restrict__ bin,
+                                     int64_t ntot, const unsigned* __restrict__ fix_count,
+                                     const int64_t* __restrict__ fix_list, unsigned fix_cap, GRec* __restrict__ grec) {
+    const unsigned cnt = *fix_count;
+    const bool overflow = cnt > fix_cap;
+    const int64_t total = overflow ? N * ncams : (int64_t)cnt;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t ri = overflow ? k : fix_list[k];
+        const int cam = (int)(ri / N);
+        const int64_t i = ri - (int64_t)cam * N;
+        if (!bin[(int64_t)cam * ntot + i].valid) continue;
+        float* g = reinterpret_cast<float*>(grec + ri);
+        float cq[3];  // on overflow every visible record is refined (fp64 is never less accurate)
+        conic_fp64(cams[cam], means[3 * i], means[3 * i + 1], means[3 * i + 2], quats, scales, cov3d, i, cq);
+        g[2] = -0.5f * kLog2e * cq[0];
+        g[3] = -kLog2e * cq[1];
+        g[4] = -0.5f * kLog2e * cq[2];
+    }
+}
+
+__global__ void __launch_bounds__(256, 2) project_gaussians_kernel(
     const float* __restrict__ means, const float* __restrict__ quats, const float* __restrict__ scales,
     const float* __restrict__ opac, const void* __restrict__ sh, int sh_dtype, int sh_deg,
     const float* __restrict__ cov3d, int64_t N, const DevCam* __restrict__ cams, int ncams,
     int ts, int tiles_x, int tiles_per_cam, GRec* __restrict__ grec, BinInfo* __restrict__ bin, int64_t ntot_prims,
-    int32_t* __restrict__ tile_count) {
+    int32_t* __restrict__ tile_count, unsigned* __restrict__ fix_count, int64_t* __restrict__ fix_list,
+    unsigned fix_cap) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N) return;
     const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
-    float q[4] = {0, 0, 0, 0}, s[3] = {0, 0, 0}, c6[6];
     float S[6];
     if (cov3d) {
 #pragma unroll
-        for (int k = 0; k < 6; ++k) c6[k] = cov3d[6 * i + k];
-#pragma unroll
-        for (int k = 0; k < 6; ++k) S[k] = c6[k];
+        for (int k = 0; k < 6; ++k) S[k] = cov3d[6 * i + k];
     } else {
-        q[0] = quats[4 * i]; q[1] = quats[4 * i + 1]; q[2] = quats[4 * i + 2]; q[3] = quats[4 * i + 3];
-        s[0] = scales[3 * i]; s[1] = scales[3 * i + 1]; s[2] = scales[3 * i + 2];
-        cov3d_canonical(q[0], q[1], q[2], q[3], s[0], s[1], s[2], S);
+        cov3d_canonical(quats[4 * i], quats[4 * i + 1], quats[4 * i + 2], quats[4 * i + 3], scales[3 * i],
+                        scales[3 * i + 1], scales[3 * i + 2], S);
     }
     const float o = opac[i];
     for (int cam = 0; cam < ncams; ++cam) {
@@ -224,26 +219,95 @@ __global__ void __launch_bounds__(256) project_gaussians_kernel(
         // conic (not a decision): fp32, or fp64 when the 2x2 determinant is
         // small relative to a*c (cancellation would cost > 10 bits)
         float ia, ib, ic;
-        if (det < 0.0009765625f * a * c) {
-            double A2, B2, C2;
-            cov2d_fp64(C, mx, my, mz, q, s, cov3d ? c6 : nullptr, A2, B2, C2);
-            const double d2 = A2 * C2 - B2 * B2;
-            ia = (float)(C2 / d2); ib = (float)(-B2 / d2); ic = (float)(A2 / d2);
-        } else {
+        {
             const float id = 1.f / det;
             ia = c * id; ib = -b * id; ic = a * id;
         }
-        float rgb[3];
-        eval_sh(sh, sh_dtype, sh_deg, i, mx - C.campos[0], my - C.campos[1], mz - C.campos[2], rgb);
-        GRec g;
-        g.q0 = make_float4(u, v, -0.5f * kLog2e * ia, -kLog2e * ib);
-        g.q1 = make_float4(-0.5f * kLog2e * ic, o, rgb[0], rgb[1]);
-        g.q2 = make_float4(rgb[2], __uint_as_float(bi.rx), __uint_as_float(bi.ry), 0.f);
-        grec[ri] = g;
+        if (det < 0.0009765625f * a * c) {  // near-singular: refined in fp64 by refine_conics_kernel
+            const unsigned slot = atomicAdd(fix_count, 1u);
+            if (slot < fix_cap) fix_list[slot] = ri;
+        }
+        // colour (q1.zw, q2.x) is written by shade_gaussians_kernel
+        float4* gp = reinterpret_cast<float4*>(grec + ri);
+        gp[0] = make_float4(u, v, -0.5f * kLog2e * ia, -kLog2e * ib);
+        reinterpret_cast<float2*>(gp + 1)[0] = make_float2(-0.5f * kLog2e * ic, o);
+        reinterpret_cast<float2*>(gp + 2)[0] = make_float2(0.f, __uint_as_float(bi.rx));
+        reinterpret_cast<float*>(gp + 2)[2] = __uint_as_float(bi.ry);
         const int txlo = ixlo / ts, txhi = ixhi / ts, tylo = iylo / ts, tyhi = iyhi / ts;
         for (int ty = tylo; ty <= tyhi; ++ty)
             for (int tx = txlo; tx <= txhi; ++tx)
                 atomicAdd(&tile_count[cam * tiles_per_cam + ty * tiles_x + tx], 1);
+    }
+}
+
+// View-dependent colour of every visible (camera, Gaussian): one thread per
+// Gaussian keeps its SH coefficients in registers across the cameras.
+template <int DEG>
+__global__ void __launch_bounds__(256) shade_gaussians_kernel(const float* __restrict__ means, const void* __restrict__ sh,
+                                                              int sh_dtype, int64_t N, const DevCam* __restrict__ cams,
+                                                              int ncams, const BinInfo* __restrict__ bin, int64_t ntot,
+                                                              GRec* __restrict__ grec) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    float c[3 * K];
+    if (sh_dtype == UMGS_BF16) {
+        const unsigned short* p = static_cast<const unsigned short*>(sh) + i * 3 * K;
+#pragma unroll
+        for (int k = 0; k < 3 * K; ++k) c[k] = __uint_as_float(((unsigned int)p[k]) << 16);
+    } else if ((3 * K) % 4 == 0) {
+        const float4* p = reinterpret_cast<const float4*>(static_cast<const float*>(sh) + i * 3 * K);
+#pragma unroll
+        for (int k = 0; k < 3 * K / 4; ++k) {
+            const float4 t = p[k];
+            c[4 * k] = t.x; c[4 * k + 1] = t.y; c[4 * k + 2] = t.z; c[4 * k + 3] = t.w;
+        }
+    } else {
+        const float* p = static_cast<const float*>(sh) + i * 3 * K;
+#pragma unroll
+        for (int k = 0; k < 3 * K; ++k) c[k] = p[k];
+    }
+    const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
+    for (int cam = 0; cam < ncams; ++cam) {
+        if (!bin[(int64_t)cam * ntot + i].valid) continue;
+        const DevCam& C = cams[cam];
+        const float dx = mx - C.campos[0], dy = my - C.campos[1], dz = mz - C.campos[2];
+        const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+        const float x = dx * inv, y = dy * inv, z = dz * inv;
+        float Y[K];
+        Y[0] = 0.28209479177387814f;                                   // 1/(2 sqrt(pi))
+        if (DEG > 0) {
+            const float c1 = 0.4886025119029199f;                      // sqrt(3/(4 pi))
+            Y[1] = -c1 * y; Y[2] = c1 * z; Y[3] = -c1 * x;
+        }
+        if (DEG > 1) {
+            const float xx = x * x, yy = y * y, zz = z * z;
+            Y[4] = 1.0925484305920792f * x * y;                        // sqrt(15/pi)/2
+            Y[5] = -1.0925484305920792f * y * z;
+            Y[6] = 0.31539156525252005f * (2.f * zz - xx - yy);       // sqrt(5/pi)/4
+            Y[7] = -1.0925484305920792f * x * z;
+            Y[8] = 0.5462742152960396f * (xx - yy);                    // sqrt(15/pi)/4
+            if (DEG > 2) {
+                Y[9] = -0.5900435899266435f * y * (3.f * xx - yy);    // sqrt(35/(2 pi))/4
+                Y[10] = 2.890611442640554f * x * y * z;                // sqrt(105/pi)/2
+                Y[11] = -0.4570457994644658f * y * (4.f * zz - xx - yy);  // sqrt(21/(2 pi))/4
+                Y[12] = 0.3731763325901154f * z * (2.f * zz - 3.f * xx - 3.f * yy);  // sqrt(7/pi)/4
+                Y[13] = -0.4570457994644658f * x * (4.f * zz - xx - yy);
+                Y[14] = 1.445305721320277f * z * (xx - yy);            // sqrt(105/pi)/4
+                Y[15] = -0.5900435899266435f * x * (xx - 3.f * yy);
+            }
+        }
+        float rgb[3];
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc = fmaf(c[3 * k + ch], Y[k], acc);
+            rgb[ch] = fmaxf(acc + 0.5f, 0.f);
+        }
+        float4* gp = reinterpret_cast<float4*>(grec + (int64_t)cam * N + i);
+        reinterpret_cast<float2*>(gp + 1)[1] = make_float2(rgb[0], rgb[1]);
+        reinterpret_cast<float*>(gp + 2)[0] = rgb[2];
     }
 }
 
@@ -417,20 +481,70 @@ __global__ void __launch_bounds__(256) scatter_keys_kernel(const BinInfo* __rest
 // per-tile sort (inner layer of the onion sort)
 
 constexpr int kSortThreads = 512;
-constexpr int kSortCap = 4096;  // keys sorted entirely in shared memory
+constexpr int kSortE = 8;                          // keys per thread in registers
+constexpr int kSortCap = kSortThreads * kSortE;    // keys sorted in one pass (4096)
 
-__device__ void bitonic_smem(uint64_t* s, int n2) {
+__device__ __forceinline__ uint64_t shfl_xor64(uint64_t v, int m) {
+    const unsigned lo = __shfl_xor_sync(0xffffffffu, (unsigned)v, m);
+    const unsigned hi = __shfl_xor_sync(0xffffffffu, (unsigned)(v >> 32), m);
+    return ((uint64_t)hi << 32) | lo;
+}
+
+// Bitonic sort of n2 (power of two, 256..kSortCap) keys held as kSortE
+// consecutive keys per thread (key g = thread*kSortE + e).  Strides below
+// kSortE are register swaps, strides below 32*kSortE warp shuffles, larger
+// strides go through shared memory.  All threads of the block must call it.
+__device__ void bitonic_regs(uint64_t (&a)[kSortE], int n2, uint64_t* s) {
+    const int t = threadIdx.x;
+    const int lane = t & 31;
+    const bool act = t * kSortE < n2;
     for (int k = 2; k <= n2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < n2 / 2; i += blockDim.x) {
-                // index of the lower element of the i-th compare pair at stride j
-                const int lo = 2 * i - (i & (j - 1));
-                const int hi = lo + j;
-                const bool up = (lo & k) == 0;
-                const uint64_t a = s[lo], b = s[hi];
-                if ((a > b) == up) { s[lo] = b; s[hi] = a; }
-            }
+        int j = k >> 1;
+        if (j >= 32 * kSortE) {
+            // large strides through shared memory
+            if (act)
+#pragma unroll
+                for (int e = 0; e < kSortE; ++e) s[t * kSortE + e] = a[e];
             __syncthreads();
+            for (; j >= 32 * kSortE; j >>= 1) {
+                for (int i = t; i < n2 / 2; i += blockDim.x) {
+                    const int lo = 2 * i - (i & (j - 1));
+                    const int hi = lo + j;
+                    const bool up = (lo & k) == 0;
+                    const uint64_t x = s[lo], y = s[hi];
+                    if ((x > y) == up) { s[lo] = y; s[hi] = x; }
+                }
+                __syncthreads();
+            }
+            if (act)
+#pragma unroll
+                for (int e = 0; e < kSortE; ++e) a[e] = s[t * kSortE + e];
+            __syncthreads();
+        }
+        // strides kSortE .. 32*kSortE/2: partner thread in the same warp
+        for (; j >= kSortE; j >>= 1) {
+            const int m = j / kSortE;
+            const bool lower = (lane & m) == 0;
+            const bool up = ((t * kSortE) & k) == 0;
+            const bool keep_min = lower == up;
+#pragma unroll
+            for (int e = 0; e < kSortE; ++e) {
+                const uint64_t o = shfl_xor64(a[e], m);
+                a[e] = keep_min ? (a[e] < o ? a[e] : o) : (a[e] > o ? a[e] : o);
+            }
+        }
+        // strides below kSortE: inside the thread
+#pragma unroll
+        for (int jj = kSortE / 2; jj > 0; jj >>= 1) {
+            if (jj > j) continue;
+#pragma unroll
+            for (int e = 0; e < kSortE; ++e) {
+                const int p = e ^ jj;
+                if (p > e) {
+                    const bool up = ((t * kSortE + e) & k) == 0;
+                    if ((a[e] > a[p]) == up) { const uint64_t x = a[e]; a[e] = a[p]; a[p] = x; }
+                }
+            }
         }
     }
 }
@@ -449,21 +563,30 @@ __device__ int merge_split(const uint64_t* A, int na, const uint64_t* B, int nb,
 __global__ void __launch_bounds__(kSortThreads) sort_tiles_kernel(uint64_t* __restrict__ keys,
                                                                    uint64_t* __restrict__ tmp,
                                                                    const int64_t* __restrict__ off) {
-    extern __shared__ uint64_t s_keys[];
+    __shared__ uint64_t s_keys[kSortCap];
     const int tile = blockIdx.x;
     const int64_t beg = off[tile];
     const int n = (int)(off[tile + 1] - beg);
     if (n <= 1) return;
     uint64_t* seg = keys + beg;
-    // sort chunks of kSortCap in shared memory
+    // sort chunks of kSortCap keys in registers
     for (int c0 = 0; c0 < n; c0 += kSortCap) {
         const int m = min(kSortCap, n - c0);
-        int n2 = 1;
+        int n2 = 32 * kSortE;
         while (n2 < m) n2 <<= 1;
-        for (int k = threadIdx.x; k < n2; k += blockDim.x) s_keys[k] = k < m ? seg[c0 + k] : ~0ull;
-        __syncthreads();
-        bitonic_smem(s_keys, n2);
-        for (int k = threadIdx.x; k < m; k += blockDim.x) seg[c0 + k] = s_keys[k];
+        uint64_t a[kSortE];
+        const int t = threadIdx.x;
+#pragma unroll
+        for (int e = 0; e < kSortE; ++e) {
+            const int g = t * kSortE + e;
+            a[e] = g < m ? seg[c0 + g] : ~0ull;
+        }
+        bitonic_regs(a, n2, s_keys);
+#pragma unroll
+        for (int e = 0; e < kSortE; ++e) {
+            const int g = t * kSortE + e;
+            if (g < m) seg[c0 + g] = a[e];
+        }
         __syncthreads();
     }
     if (n <= kSortCap) return;
@@ -779,12 +902,31 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     UMGS_TRY(cudaMemsetAsync(fr->status.ptr, 0, sizeof(int32_t) * 4, stream));
 
     const DevCam* dcams = fr->cams.as<DevCam>();
+    const unsigned fix_cap = (unsigned)std::min<int64_t>(std::max<int64_t>(1, Ng * ncams), 1 << 22);
+    UMGS_TRY(fr->fix_list.reserve(sizeof(int64_t) * fix_cap));
     if (Ng > 0) {
         StageTimer tm(ctx, UMGS_STAGE_PROJECT_GAUSSIANS, stream);
         project_gaussians_kernel<<<grid_for(Ng, 256), 256, 0, stream>>>(
             g->means, g->quats, g->scales, g->opacities, g->sh, g->sh_dtype, g->sh_degree, g->cov3d, Ng, dcams,
             ncams, ts, tiles_x, tiles_per_cam, fr->grec.as<GRec>(), fr->bin.as<BinInfo>(), Ntot,
-            fr->tile_count.as<int32_t>());
+            fr->tile_count.as<int32_t>(), reinterpret_cast<unsigned*>(fr->status.as<int32_t>() + 3),
+            fr->fix_list.as<int64_t>(), fix_cap);
+        UMGS_TRY(cudaGetLastError());
+        refine_conics_kernel<<<4 * ctx->num_sms, 128, 0, stream>>>(
+            g->means, g->quats, g->scales, g->cov3d, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot,
+            reinterpret_cast<unsigned*>(fr->status.as<int32_t>() + 3), fr->fix_list.as<int64_t>(), fix_cap,
+            fr->grec.as<GRec>());
+        UMGS_TRY(cudaGetLastError());
+    }
+    if (Ng > 0) {
+        StageTimer tm(ctx, UMGS_STAGE_SHADE_GAUSSIANS, stream);
+        const unsigned gb = grid_for(Ng, 256);
+        switch (g->sh_degree) {
+            case 0: shade_gaussians_kernel<0><<<gb, 256, 0, stream>>>(g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>()); break;
+            case 1: shade_gaussians_kernel<1><<<gb, 256, 0, stream>>>(g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>()); break;
+            case 2: shade_gaussians_kernel<2><<<gb, 256, 0, stream>>>(g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>()); break;
+            default: shade_gaussians_kernel<3><<<gb, 256, 0, stream>>>(g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>()); break;
+        }
         UMGS_TRY(cudaGetLastError());
     }
     int64_t tri_base = 0;
@@ -826,7 +968,7 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     }
     {
         StageTimer tm(ctx, UMGS_STAGE_SORT, stream);
-        sort_tiles_kernel<<<(unsigned)M, kSortThreads, kSortCap * sizeof(uint64_t), stream>>>(
+        sort_tiles_kernel<<<(unsigned)M, kSortThreads, 0, stream>>>(
             fr->keys.as<uint64_t>(), fr->keys_tmp.as<uint64_t>(), fr->tile_off.as<int64_t>());
         UMGS_TRY(cudaGetLastError());
     }
