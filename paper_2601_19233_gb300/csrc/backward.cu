@@ -42,7 +42,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 template <int TS>
 __global__ void __launch_bounds__(TS * TS) composite_bwd_kernel(
-    const uint64_t* __restrict__ keys, const int64_t* __restrict__ off, const GRec* __restrict__ grec,
+    const uint32_t* __restrict__ ids, const int64_t* __restrict__ off, const GRec* __restrict__ grec,
     const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x, int tiles_per_cam, int W, int H, float bg0,
     float bg1, float bg2, const float4* __restrict__ dout, const int32_t* __restrict__ last,
     const float* __restrict__ tfin, const int32_t* __restrict__ ntri, const float4* __restrict__ stack, int64_t npix,
@@ -88,7 +88,7 @@ __global__ void __launch_bounds__(TS * TS) composite_bwd_kernel(
         const int n = bend - b0;
         __syncthreads();
         for (int k = threadIdx.x; k < n; k += NT) {
-            const uint32_t id = (uint32_t)keys[beg + b0 + k];
+            const uint32_t id = ids[beg + b0 + k];
             s_id[k] = id;
             if (id < Ng) {
                 const float4* src = reinterpret_cast<const float4*>(G + id);
@@ -551,7 +551,7 @@ umgs_status render_backward(umgs_ctx* ctx, umgs_frame* fr, const umgs_gaussians*
         const float4* dout = reinterpret_cast<const float4*>(dL_drgbt);
 #define UMGS_LAUNCH(TSV)                                                                                         \
         composite_bwd_kernel<TSV><<<M, TSV * TSV, 0, stream>>>(                                                  \
-            fr->keys.as<uint64_t>(), fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->trec.as<TRec>(), Ng, Nt, \
+            fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->trec.as<TRec>(), Ng, Nt,               \
             fr->tiles_x, tpc, fr->W, fr->H, fr->bg[0], fr->bg[1], fr->bg[2], dout, fr->last.as<int32_t>(),         \
             fr->tfin.as<float>(), fr->ntri.as<int32_t>(), fr->stack.as<float4>(), npix, fr->ggrad.as<float>(),     \
             fr->tgrad.as<float>())

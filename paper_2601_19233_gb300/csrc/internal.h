@@ -34,7 +34,12 @@ struct DevBuf {
 // Everything one umgs_render call produces and umgs_render_backward consumes.
 struct umgs_frame {
     umgs_ctx* ctx = nullptr;
-    umgs::DevBuf cams, grec, trec, bin, tile_count, tile_off, tile_fill, keys, keys_tmp;
+    umgs::DevBuf cams, grec, trec, bin, tile_off;
+    // binning: record depth keys/values (+ ping-pong), per-record tile counts
+    // and offsets, (tile, id) pairs (+ ping-pong), radix histograms, scan sums
+    umgs::DevBuf pk, pv, pk2, pv2, pcnt, poff, tk, tv, tk2, tv2, rs_hist, rs_hist2, rs_bsum;
+    uint32_t* ids = nullptr;    // sorted unified ids (into tv or tv2)
+    uint32_t* tkeys = nullptr;  // sorted tile keys
     umgs::DevBuf last, status;
     umgs::DevBuf tfin, ntri, stack;   // backward state (saved renders only)
     umgs::DevBuf ggrad, tgrad, rerun_out;
@@ -52,7 +57,8 @@ struct umgs_frame {
     bool valid = false;
     std::vector<int64_t> mesh_offset;  // unified id of each mesh's first face
     void release() {
-        for (auto* b : {&cams, &grec, &trec, &bin, &tile_count, &tile_off, &tile_fill, &keys, &keys_tmp,
+        for (auto* b : {&cams, &grec, &trec, &bin, &tile_off, &pk, &pv, &pk2, &pv2, &pcnt, &poff, &tk, &tv, &tk2, &tv2,
+                        &rs_hist, &rs_hist2, &rs_bsum,
                         &last, &status, &tfin, &ntri, &stack, &ggrad, &tgrad, &rerun_out, &fix_list})
             b->release();
     }

@@ -2,17 +2,18 @@
 //
 // Pipeline per umgs_render call (all cameras in one set of launches):
 //   1. project_gaussians / setup_triangles: one thread per primitive, looping
-//      over cameras; canonical fp32 footprint + depth key, a compact record
-//      for the compositor, and an atomic count per touched screen tile.
-//   2. scan_tiles: exclusive scan of the per-tile counts (single CTA).
-//   3. scatter_keys: every (primitive, tile) pair writes the 64-bit key
-//      (depth bits << 32 | unified id) into its tile's bucket (atomic slot).
-//      This is the outer, counting-sort layer of the onion sort: buckets are
-//      ordered by tile; inside a bucket the order is arbitrary.
-//   4. sort_tiles: one CTA per tile sorts its bucket by (depth bits, id) -
-//      bitonic in shared memory up to kSortCap keys, otherwise sorted chunks
-//      merged in global memory (inner layer of the onion sort).
-//   5. composite: one CTA per tile, one thread per pixel; records of the
+//      over cameras; canonical fp32 footprint (pixel rect) + depth key and a
+//      compact record for the compositor; refine_conics_kernel recomputes the
+//      few near-singular conics in fp64; shade_gaussians_kernel evaluates SH.
+//   2. binning, a two-level stable radix sort (the onion sort):
+//      a. every (camera, primitive) record sorted by its depth bits
+//         (4 x 8-bit passes, stable, so equal depths stay in id order);
+//      b. in that order every record emits one (tile, id) pair per tile its
+//         rect touches (offsets from an exclusive scan of the tile counts);
+//      c. the pairs are sorted stably by tile (8-bit passes over the tile
+//         bits): each tile's list is then in (depth bits, id) order;
+//      d. tile_ranges: per tile, the first index of its list (binary search).
+//   3. composite: one CTA per tile, one thread per pixel; records of the
 //      sorted list are staged through shared memory in batches; every pixel
 //      blends its fragments front to back (Eq. 1-2 for Gaussians, Eq. 7-9
 //      for entities of depth-adjacent triangles) and the CTA stops when
@@ -22,6 +23,7 @@
 #include <algorithm>
 
 #include "internal.h"
+#include "radix.cuh"
 
 namespace umgs {
 
@@ -144,7 +146,7 @@ __global__ void __launch_bounds__(256, 2) project_gaussians_kernel(
     const float* __restrict__ opac, const void* __restrict__ sh, int sh_dtype, int sh_deg,
     const float* __restrict__ cov3d, int64_t N, const DevCam* __restrict__ cams, int ncams,
     int ts, int tiles_x, int tiles_per_cam, GRec* __restrict__ grec, BinInfo* __restrict__ bin, int64_t ntot_prims,
-    int32_t* __restrict__ tile_count, unsigned* __restrict__ fix_count, int64_t* __restrict__ fix_list,
+    unsigned* __restrict__ fix_count, int64_t* __restrict__ fix_list,
     unsigned fix_cap) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -233,10 +235,6 @@ __global__ void __launch_bounds__(256, 2) project_gaussians_kernel(
         reinterpret_cast<float2*>(gp + 1)[0] = make_float2(-0.5f * kLog2e * ic, o);
         reinterpret_cast<float2*>(gp + 2)[0] = make_float2(0.f, __uint_as_float(bi.rx));
         reinterpret_cast<float*>(gp + 2)[2] = __uint_as_float(bi.ry);
-        const int txlo = ixlo / ts, txhi = ixhi / ts, tylo = iylo / ts, tyhi = iyhi / ts;
-        for (int ty = tylo; ty <= tyhi; ++ty)
-            for (int tx = txlo; tx <= txhi; ++tx)
-                atomicAdd(&tile_count[cam * tiles_per_cam + ty * tiles_x + tx], 1);
     }
 }
 
@@ -323,7 +321,7 @@ __global__ void __launch_bounds__(256) setup_triangles_kernel(
     int64_t tri_base /* index of this mesh's first face among all triangles */, int64_t nt_total,
     int64_t id_base /* unified id of this mesh's first face */, const DevCam* __restrict__ cams, int ncams,
     int ts, int tiles_x, int tiles_per_cam, TRec* __restrict__ trec, BinInfo* __restrict__ bin,
-    int64_t ntot_prims, int32_t* __restrict__ tile_count, int32_t* __restrict__ status) {
+    int64_t ntot_prims, int32_t* __restrict__ status) {
     const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (f >= nf) return;
     int vid[3] = {faces[3 * f], faces[3 * f + 1], faces[3 * f + 2]};
@@ -411,209 +409,69 @@ __global__ void __launch_bounds__(256) setup_triangles_kernel(
 #pragma unroll
         for (int k = 0; k < 3; ++k) t.pad2[k] = 0.f;
         trec[(int64_t)cam * nt_total + tri_base + f] = t;
-        const int txlo = (int)xlo / ts, txhi = (int)xhi / ts, tylo = (int)ylo / ts, tyhi = (int)yhi / ts;
-        for (int ty = tylo; ty <= tyhi; ++ty)
-            for (int tx = txlo; tx <= txhi; ++tx)
-                atomicAdd(&tile_count[cam * tiles_per_cam + ty * tiles_x + tx], 1);
     }
 }
 
 // ---------------------------------------------------------------------------
-// exclusive scan of tile counts (one CTA of 1024 threads)
+// binning: a two-level stable radix sort (the "onion"): all (camera,
+// primitive) records by depth bits, then the emitted (tile, primitive) pairs
+// by tile.  Stability makes each tile's list come out in (depth bits, id)
+// order without a per-tile sort.
 
-__global__ void __launch_bounds__(1024) scan_tiles_kernel(const int32_t* __restrict__ cnt, int64_t M,
-                                                          int64_t* __restrict__ off) {
-    __shared__ long long warp_sums[32];
-    const int tid = threadIdx.x;
-    const int64_t per = (M + 1023) / 1024;
-    const int64_t b = min((int64_t)tid * per, M), e = min(b + per, M);
-    long long local = 0;
-    for (int64_t k = b; k < e; ++k) local += cnt[k];
-    // inclusive scan of `local` across the block
-    long long x = local;
-    const int lane = tid & 31, warp = tid >> 5;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        long long y = __shfl_up_sync(0xffffffffu, x, d);
-        if (lane >= d) x += y;
-    }
-    if (lane == 31) warp_sums[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-        long long w = warp_sums[lane];
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            long long y = __shfl_up_sync(0xffffffffu, w, d);
-            if (lane >= d) w += y;
-        }
-        warp_sums[lane] = w;
-    }
-    __syncthreads();
-    long long run = x - local + (warp > 0 ? warp_sums[warp - 1] : 0);
-    for (int64_t k = b; k < e; ++k) { off[k] = run; run += cnt[k]; }
-    if (tid == 1023) off[M] = warp_sums[31];
+__global__ void prim_keys_kernel(const BinInfo* __restrict__ bin, int64_t n, uint32_t* __restrict__ pk,
+                                 uint32_t* __restrict__ pv) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const BinInfo b = bin[i];
+    pk[i] = b.valid ? b.dbits : 0xffffffffu;
+    pv[i] = (uint32_t)i;
 }
 
-// ---------------------------------------------------------------------------
-// key scatter into tile buckets (outer layer of the onion sort)
+__device__ __forceinline__ uint32_t tiles_of(const BinInfo& b, int ts) {
+    if (!b.valid) return 0u;
+    const int xlo = b.rx & 0xffff, xhi = b.rx >> 16, ylo = b.ry & 0xffff, yhi = b.ry >> 16;
+    return (uint32_t)((xhi / ts - xlo / ts + 1) * (yhi / ts - ylo / ts + 1));
+}
 
-__global__ void __launch_bounds__(256) scatter_keys_kernel(const BinInfo* __restrict__ bin, int64_t ntot, int ncams,
-                                                           int ts, int tiles_x, int tiles_per_cam,
-                                                           const int64_t* __restrict__ off,
-                                                           int32_t* __restrict__ fill, uint64_t* __restrict__ keys) {
-    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (gid >= ntot * ncams) return;
-    const int cam = (int)(gid / ntot);
-    const int64_t id = gid - (int64_t)cam * ntot;
-    const BinInfo bi = bin[gid];
-    if (!bi.valid) return;
-    const int xlo = bi.rx & 0xffff, xhi = bi.rx >> 16, ylo = bi.ry & 0xffff, yhi = bi.ry >> 16;
-    const uint64_t key = ((uint64_t)bi.dbits << 32) | (uint64_t)(uint32_t)id;
-    for (int ty = ylo / ts; ty <= yhi / ts; ++ty)
-        for (int tx = xlo / ts; tx <= xhi / ts; ++tx) {
-            const int t = cam * tiles_per_cam + ty * tiles_x + tx;
-            const int slot = atomicAdd(&fill[t], 1);
-            keys[off[t] + slot] = key;
+__global__ void tile_counts_kernel(const BinInfo* __restrict__ bin, const uint32_t* __restrict__ pv, int64_t n, int ts,
+                                   uint32_t* __restrict__ cnt) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    cnt[i] = tiles_of(bin[pv[i]], ts);
+}
+
+__global__ void emit_pairs_kernel(const BinInfo* __restrict__ bin, const uint32_t* __restrict__ pv,
+                                  const uint32_t* __restrict__ off, int64_t n, int64_t ntot, int ts, int tiles_x,
+                                  int tiles_per_cam, uint32_t* __restrict__ tk, uint32_t* __restrict__ tv) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t rec = pv[i];
+    const BinInfo b = bin[rec];
+    if (!b.valid) return;
+    const int cam = (int)(rec / ntot);
+    const uint32_t id = (uint32_t)(rec - (int64_t)cam * ntot);
+    const int xlo = (b.rx & 0xffff) / ts, xhi = (b.rx >> 16) / ts, ylo = (b.ry & 0xffff) / ts, yhi = (b.ry >> 16) / ts;
+    uint32_t o = off[i];
+    for (int ty = ylo; ty <= yhi; ++ty)
+        for (int tx = xlo; tx <= xhi; ++tx) {
+            tk[o] = (uint32_t)(cam * tiles_per_cam + ty * tiles_x + tx);
+            tv[o] = id;
+            ++o;
         }
 }
 
-// ---------------------------------------------------------------------------
-// per-tile sort (inner layer of the onion sort)
-
-constexpr int kSortThreads = 512;
-constexpr int kSortE = 8;                          // keys per thread in registers
-constexpr int kSortCap = kSortThreads * kSortE;    // keys sorted in one pass (4096)
-
-__device__ __forceinline__ uint64_t shfl_xor64(uint64_t v, int m) {
-    const unsigned lo = __shfl_xor_sync(0xffffffffu, (unsigned)v, m);
-    const unsigned hi = __shfl_xor_sync(0xffffffffu, (unsigned)(v >> 32), m);
-    return ((uint64_t)hi << 32) | lo;
-}
-
-// Bitonic sort of n2 (power of two, 256..kSortCap) keys held as kSortE
-// consecutive keys per thread (key g = thread*kSortE + e).  Strides below
-// kSortE are register swaps, strides below 32*kSortE warp shuffles, larger
-// strides go through shared memory.  All threads of the block must call it.
-__device__ void bitonic_regs(uint64_t (&a)[kSortE], int n2, uint64_t* s) {
-    const int t = threadIdx.x;
-    const int lane = t & 31;
-    const bool act = t * kSortE < n2;
-    for (int k = 2; k <= n2; k <<= 1) {
-        int j = k >> 1;
-        if (j >= 32 * kSortE) {
-            // large strides through shared memory
-            if (act)
-#pragma unroll
-                for (int e = 0; e < kSortE; ++e) s[t * kSortE + e] = a[e];
-            __syncthreads();
-            for (; j >= 32 * kSortE; j >>= 1) {
-                for (int i = t; i < n2 / 2; i += blockDim.x) {
-                    const int lo = 2 * i - (i & (j - 1));
-                    const int hi = lo + j;
-                    const bool up = (lo & k) == 0;
-                    const uint64_t x = s[lo], y = s[hi];
-                    if ((x > y) == up) { s[lo] = y; s[hi] = x; }
-                }
-                __syncthreads();
-            }
-            if (act)
-#pragma unroll
-                for (int e = 0; e < kSortE; ++e) a[e] = s[t * kSortE + e];
-            __syncthreads();
-        }
-        // strides kSortE .. 32*kSortE/2: partner thread in the same warp
-        for (; j >= kSortE; j >>= 1) {
-            const int m = j / kSortE;
-            const bool lower = (lane & m) == 0;
-            const bool up = ((t * kSortE) & k) == 0;
-            const bool keep_min = lower == up;
-#pragma unroll
-            for (int e = 0; e < kSortE; ++e) {
-                const uint64_t o = shfl_xor64(a[e], m);
-                a[e] = keep_min ? (a[e] < o ? a[e] : o) : (a[e] > o ? a[e] : o);
-            }
-        }
-        // strides below kSortE: inside the thread
-#pragma unroll
-        for (int jj = kSortE / 2; jj > 0; jj >>= 1) {
-            if (jj > j) continue;
-#pragma unroll
-            for (int e = 0; e < kSortE; ++e) {
-                const int p = e ^ jj;
-                if (p > e) {
-                    const bool up = ((t * kSortE + e) & k) == 0;
-                    if ((a[e] > a[p]) == up) { const uint64_t x = a[e]; a[e] = a[p]; a[p] = x; }
-                }
-            }
-        }
-    }
-}
-
-// merge path split: number of elements taken from A among the first `diag` outputs
-__device__ int merge_split(const uint64_t* A, int na, const uint64_t* B, int nb, int diag) {
-    int lo = max(0, diag - nb), hi = min(diag, na);
+// tile_off[t] = first index of tile t in the sorted keys (lower bound)
+__global__ void tile_ranges_kernel(const uint32_t* __restrict__ tk, int64_t K, int64_t M, int64_t* __restrict__ off) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t > M) return;
+    if (t == M) { off[M] = K; return; }
+    int64_t lo = 0, hi = K;
     while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (A[mid] < B[diag - 1 - mid]) lo = mid + 1;
+        const int64_t mid = (lo + hi) >> 1;
+        if (tk[mid] < (uint32_t)t) lo = mid + 1;
         else hi = mid;
     }
-    return lo;
-}
-
-__global__ void __launch_bounds__(kSortThreads) sort_tiles_kernel(uint64_t* __restrict__ keys,
-                                                                   uint64_t* __restrict__ tmp,
-                                                                   const int64_t* __restrict__ off) {
-    __shared__ uint64_t s_keys[kSortCap];
-    const int tile = blockIdx.x;
-    const int64_t beg = off[tile];
-    const int n = (int)(off[tile + 1] - beg);
-    if (n <= 1) return;
-    uint64_t* seg = keys + beg;
-    // sort chunks of kSortCap keys in registers
-    for (int c0 = 0; c0 < n; c0 += kSortCap) {
-        const int m = min(kSortCap, n - c0);
-        int n2 = 32 * kSortE;
-        while (n2 < m) n2 <<= 1;
-        uint64_t a[kSortE];
-        const int t = threadIdx.x;
-#pragma unroll
-        for (int e = 0; e < kSortE; ++e) {
-            const int g = t * kSortE + e;
-            a[e] = g < m ? seg[c0 + g] : ~0ull;
-        }
-        bitonic_regs(a, n2, s_keys);
-#pragma unroll
-        for (int e = 0; e < kSortE; ++e) {
-            const int g = t * kSortE + e;
-            if (g < m) seg[c0 + g] = a[e];
-        }
-        __syncthreads();
-    }
-    if (n <= kSortCap) return;
-    // merge sorted runs pairwise in global memory (ping-pong with tmp)
-    uint64_t* src = seg;
-    uint64_t* dst = tmp + beg;
-    for (int run = kSortCap; run < n; run <<= 1) {
-        for (int s0 = 0; s0 < n; s0 += 2 * run) {
-            const int na = min(run, n - s0);
-            const int nb = min(run, n - s0 - na);
-            const uint64_t* A = src + s0;
-            const uint64_t* B = A + na;
-            const int total = na + nb;
-            const int per = (total + blockDim.x - 1) / blockDim.x;
-            const int d0 = min((int)threadIdx.x * per, total), d1 = min(d0 + per, total);
-            int ia = merge_split(A, na, B, nb, d0);
-            int ib = d0 - ia;
-            for (int d = d0; d < d1; ++d) {
-                const bool takeA = ib >= nb || (ia < na && A[ia] < B[ib]);
-                dst[s0 + d] = takeA ? A[ia++] : B[ib++];
-            }
-        }
-        __syncthreads();
-        uint64_t* t = src; src = dst; dst = t;
-    }
-    if (src != seg)
-        for (int k = threadIdx.x; k < n; k += blockDim.x) seg[k] = src[k];
+    off[t] = lo;
 }
 
 // ---------------------------------------------------------------------------
@@ -636,7 +494,7 @@ struct PixelState {
 // in a per-pixel stack of capacity `cap` (`need` records the largest count).
 template <int TS, bool SAVE>
 __global__ void __launch_bounds__(TS * TS) composite_kernel(
-    const uint64_t* __restrict__ keys, const int64_t* __restrict__ off, const GRec* __restrict__ grec,
+    const uint32_t* __restrict__ ids, const int64_t* __restrict__ off, const GRec* __restrict__ grec,
     const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x, int tiles_per_cam, int W, int H,
     float t_eps, float bg0, float bg1, float bg2, int mode, float4* __restrict__ out, int32_t* __restrict__ out_last,
     float* __restrict__ out_tfin, int32_t* __restrict__ out_ntri, float4* __restrict__ stack, int cap,
@@ -670,7 +528,7 @@ __global__ void __launch_bounds__(TS * TS) composite_kernel(
         if (__syncthreads_count(done) == NT) break;
         const int n = (int)min((int64_t)kBatch, end - b0);
         for (int k = threadIdx.x; k < n; k += NT) {
-            const uint32_t id = (uint32_t)keys[b0 + k];
+            const uint32_t id = ids[b0 + k];
             s_id[k] = id;
             if (id < Ng) {
                 const float4* src = reinterpret_cast<const float4*>(G + id);
@@ -800,13 +658,15 @@ __global__ void __launch_bounds__(TS * TS) composite_kernel(
 // ---------------------------------------------------------------------------
 // frame inspection: split sorted keys into ids / depth bits
 
-__global__ void split_keys_kernel(const uint64_t* __restrict__ keys, int64_t n, int32_t* __restrict__ ids,
-                                  uint32_t* __restrict__ dbits) {
+__global__ void lists_kernel(const uint32_t* __restrict__ tk, const uint32_t* __restrict__ tv, int64_t n,
+                             const BinInfo* __restrict__ bin, int64_t ntot, int tiles_per_cam,
+                             int32_t* __restrict__ ids, uint32_t* __restrict__ dbits) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const uint64_t k = keys[i];
-    ids[i] = (int32_t)(uint32_t)k;
-    dbits[i] = (uint32_t)(k >> 32);
+    const uint32_t id = tv[i];
+    const int cam = (int)(tk[i] / (uint32_t)tiles_per_cam);
+    ids[i] = (int32_t)id;
+    dbits[i] = bin[(int64_t)cam * ntot + id].dbits;
 }
 
 
@@ -821,7 +681,7 @@ cudaError_t launch_composite(umgs_frame* fr, const umgs_render_opts& opts, float
     if (save) cudaMemsetAsync(fr->status.as<int32_t>() + 2, 0, sizeof(int32_t), stream);
 #define UMGS_LAUNCH(TSV, SV)                                                                                    \
     composite_kernel<TSV, SV><<<M, TSV * TSV, 0, stream>>>(                                                     \
-        fr->keys.as<uint64_t>(), fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->trec.as<TRec>(), fr->ng,  \
+        fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->trec.as<TRec>(), fr->ng,                  \
         fr->nt, fr->tiles_x, tpc, fr->W, fr->H, te, opts.bg[0], opts.bg[1], opts.bg[2], opts.blend_mode, out,     \
         fr->last.as<int32_t>(), save ? fr->tfin.as<float>() : nullptr, save ? fr->ntri.as<int32_t>() : nullptr,   \
         save ? fr->stack.as<float4>() : nullptr, fr->stack_cap, npix, fr->status.as<int32_t>() + 2)
@@ -830,6 +690,45 @@ cudaError_t launch_composite(umgs_frame* fr, const umgs_render_opts& opts, float
     else { if (save) UMGS_LAUNCH(32, true); else UMGS_LAUNCH(32, false); }
 #undef UMGS_LAUNCH
     return cudaGetLastError();
+}
+
+
+// exclusive scan of n uint32 counts into out; the grand total goes to *total (device)
+cudaError_t scan_u32(umgs_frame* fr, const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total, cudaStream_t s) {
+    const int64_t nb = (n + kRsTile - 1) / kRsTile;
+    cudaError_t e = fr->rs_bsum.reserve(sizeof(uint32_t) * std::max<int64_t>(1, nb));
+    if (e != cudaSuccess) return e;
+    if (nb > (1 << 22)) return cudaErrorInvalidValue;
+    scan_reduce_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(in, n, fr->rs_bsum.as<uint32_t>());
+    scan_blocks_kernel<<<1, 1024, 0, s>>>(fr->rs_bsum.as<uint32_t>(), (int)nb, total);
+    scan_apply_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(in, n, fr->rs_bsum.as<uint32_t>(), out);
+    return cudaGetLastError();
+}
+
+// stable LSD radix sort of (k, v) on the low `bits` bits; ping-pongs with
+// (k2, v2) and returns where the result ended
+cudaError_t radix_sort_pairs(umgs_frame* fr, uint32_t* k, uint32_t* v, uint32_t* k2, uint32_t* v2, int64_t n, int bits,
+                             uint32_t** rk, uint32_t** rv, cudaStream_t s) {
+    const int64_t nb = (n + kRsTile - 1) / kRsTile;
+    const int64_t nh = 256 * nb;
+    cudaError_t e = fr->rs_hist.reserve(sizeof(uint32_t) * nh);
+    if (e != cudaSuccess) return e;
+    e = fr->rs_hist2.reserve(sizeof(uint32_t) * 256);
+    if (e != cudaSuccess) return e;
+    uint32_t* hist = fr->rs_hist.as<uint32_t>();
+    uint32_t* dtotal = fr->rs_hist2.as<uint32_t>();
+    for (int shift = 0; shift < bits; shift += 8) {
+        radix_upsweep_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(k, n, shift, (int)nb, hist);
+        radix_hist_scan_kernel<<<256, kRsThreads, 0, s>>>(hist, (int)nb, dtotal);
+        radix_downsweep_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(k, v, n, shift, (int)nb, hist, dtotal, k2, v2);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        uint32_t* t = k; k = k2; k2 = t;
+        t = v; v = v2; v2 = t;
+    }
+    *rk = k;
+    *rv = v;
+    return cudaSuccess;
 }
 
 // ---------------------------------------------------------------------------
@@ -874,10 +773,8 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     UMGS_TRY(fr->grec.reserve(sizeof(GRec) * std::max<int64_t>(1, Ng * ncams)));
     UMGS_TRY(fr->trec.reserve(sizeof(TRec) * std::max<int64_t>(1, Nt * ncams)));
     UMGS_TRY(fr->bin.reserve(sizeof(BinInfo) * std::max<int64_t>(1, Ntot * ncams)));
-    UMGS_TRY(fr->tile_count.reserve(sizeof(int32_t) * (M + 1)));
-    UMGS_TRY(fr->tile_fill.reserve(sizeof(int32_t) * (M + 1)));
     UMGS_TRY(fr->tile_off.reserve(sizeof(int64_t) * (M + 1)));
-    UMGS_TRY(fr->status.reserve(sizeof(int32_t) * 4));
+    UMGS_TRY(fr->status.reserve(sizeof(int32_t) * 8));
 
     // cameras: host -> pinned staging -> device
     std::vector<DevCam> dc(ncams);
@@ -898,8 +795,7 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
         d.pad = 0;
     }
     UMGS_TRY(cudaMemcpyAsync(fr->cams.ptr, dc.data(), sizeof(DevCam) * ncams, cudaMemcpyHostToDevice, stream));
-    UMGS_TRY(cudaMemsetAsync(fr->tile_count.ptr, 0, sizeof(int32_t) * (M + 1), stream));
-    UMGS_TRY(cudaMemsetAsync(fr->status.ptr, 0, sizeof(int32_t) * 4, stream));
+    UMGS_TRY(cudaMemsetAsync(fr->status.ptr, 0, sizeof(int32_t) * 8, stream));
 
     const DevCam* dcams = fr->cams.as<DevCam>();
     const unsigned fix_cap = (unsigned)std::min<int64_t>(std::max<int64_t>(1, Ng * ncams), 1 << 22);
@@ -909,7 +805,7 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
         project_gaussians_kernel<<<grid_for(Ng, 256), 256, 0, stream>>>(
             g->means, g->quats, g->scales, g->opacities, g->sh, g->sh_dtype, g->sh_degree, g->cov3d, Ng, dcams,
             ncams, ts, tiles_x, tiles_per_cam, fr->grec.as<GRec>(), fr->bin.as<BinInfo>(), Ntot,
-            fr->tile_count.as<int32_t>(), reinterpret_cast<unsigned*>(fr->status.as<int32_t>() + 3),
+            reinterpret_cast<unsigned*>(fr->status.as<int32_t>() + 3),
             fr->fix_list.as<int64_t>(), fix_cap);
         UMGS_TRY(cudaGetLastError());
         refine_conics_kernel<<<4 * ctx->num_sms, 128, 0, stream>>>(
@@ -937,39 +833,68 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
             setup_triangles_kernel<<<grid_for(me.nf, 256), 256, 0, stream>>>(
                 me.verts, me.faces, me.vcolor, me.valpha, me.falpha, me.nv, me.nf, tri_base, Nt, Ng + tri_base,
                 dcams, ncams, ts, tiles_x, tiles_per_cam, fr->trec.as<TRec>(), fr->bin.as<BinInfo>(), Ntot,
-                fr->tile_count.as<int32_t>(), fr->status.as<int32_t>());
+                fr->status.as<int32_t>());
             UMGS_TRY(cudaGetLastError());
         }
         tri_base += me.nf;
     }
-    {
+    // ---- binning: depth sort of all records, pair emission, stable tile sort
+    const int64_t NR = Ntot * ncams;  // (camera, primitive) records
+    UMGS_TRY(fr->pk.reserve(sizeof(uint32_t) * std::max<int64_t>(1, NR)));
+    UMGS_TRY(fr->pv.reserve(sizeof(uint32_t) * std::max<int64_t>(1, NR)));
+    UMGS_TRY(fr->pk2.reserve(sizeof(uint32_t) * std::max<int64_t>(1, NR)));
+    UMGS_TRY(fr->pv2.reserve(sizeof(uint32_t) * std::max<int64_t>(1, NR)));
+    UMGS_TRY(fr->pcnt.reserve(sizeof(uint32_t) * std::max<int64_t>(1, NR)));
+    UMGS_TRY(fr->poff.reserve(sizeof(uint32_t) * std::max<int64_t>(1, NR)));
+    uint32_t* pk = fr->pk.as<uint32_t>();
+    uint32_t* pv = fr->pv.as<uint32_t>();
+    if (NR > 0) {
         StageTimer tm(ctx, UMGS_STAGE_SCAN, stream);
-        scan_tiles_kernel<<<1, 1024, 0, stream>>>(fr->tile_count.as<int32_t>(), M, fr->tile_off.as<int64_t>());
+        prim_keys_kernel<<<grid_for(NR, 256), 256, 0, stream>>>(fr->bin.as<BinInfo>(), NR, pk, pv);
         UMGS_TRY(cudaGetLastError());
+        uint32_t* rk = nullptr;
+        uint32_t* rv = nullptr;
+        UMGS_TRY(radix_sort_pairs(fr, pk, pv, fr->pk2.as<uint32_t>(), fr->pv2.as<uint32_t>(), NR, 32, &rk, &rv, stream));
+        pk = rk;
+        pv = rv;
+        tile_counts_kernel<<<grid_for(NR, 256), 256, 0, stream>>>(fr->bin.as<BinInfo>(), pv, NR, ts,
+                                                                  fr->pcnt.as<uint32_t>());
+        UMGS_TRY(scan_u32(fr, fr->pcnt.as<uint32_t>(), fr->poff.as<uint32_t>(), NR,
+                          reinterpret_cast<uint32_t*>(fr->status.as<int32_t>() + 1), stream));
     }
-    // read back the key count (and the status word)
-    UMGS_TRY(cudaMemcpyAsync(ctx->pinned, fr->tile_off.as<int64_t>() + M, sizeof(int64_t), cudaMemcpyDeviceToHost,
-                             stream));
-    UMGS_TRY(cudaMemcpyAsync(ctx->pinned + 1, fr->status.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+    // read back the number of pairs (and the status word)
+    UMGS_TRY(cudaMemcpyAsync(ctx->pinned, fr->status.ptr, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
     UMGS_TRY(cudaStreamSynchronize(stream));
-    const int64_t K = ctx->pinned[0];
-    const int32_t st = (int32_t)(ctx->pinned[1] & 0xffffffff);
+    const int32_t st = (int32_t)(ctx->pinned[0] & 0xffffffff);
+    const int64_t K = NR > 0 ? (int64_t)(uint32_t)(ctx->pinned[0] >> 32) : 0;
     if (st & 1) return fail(ctx, UMGS_ERR_INVALID_ARG, "a face index is out of range");
     fr->num_keys = K;
-    UMGS_TRY(fr->keys.reserve(sizeof(uint64_t) * std::max<int64_t>(1, K)));
-    UMGS_TRY(fr->keys_tmp.reserve(sizeof(uint64_t) * std::max<int64_t>(1, K)));
-    UMGS_TRY(cudaMemsetAsync(fr->tile_fill.ptr, 0, sizeof(int32_t) * (M + 1), stream));
-    if (Ntot > 0) {
+    UMGS_TRY(fr->tk.reserve(sizeof(uint32_t) * std::max<int64_t>(1, K)));
+    UMGS_TRY(fr->tv.reserve(sizeof(uint32_t) * std::max<int64_t>(1, K)));
+    UMGS_TRY(fr->tk2.reserve(sizeof(uint32_t) * std::max<int64_t>(1, K)));
+    UMGS_TRY(fr->tv2.reserve(sizeof(uint32_t) * std::max<int64_t>(1, K)));
+    fr->ids = fr->tv.as<uint32_t>();
+    fr->tkeys = fr->tk.as<uint32_t>();
+    if (K > 0) {
         StageTimer tm(ctx, UMGS_STAGE_SCATTER, stream);
-        scatter_keys_kernel<<<grid_for(Ntot * ncams, 256), 256, 0, stream>>>(
-            fr->bin.as<BinInfo>(), Ntot, ncams, ts, tiles_x, tiles_per_cam, fr->tile_off.as<int64_t>(),
-            fr->tile_fill.as<int32_t>(), fr->keys.as<uint64_t>());
+        emit_pairs_kernel<<<grid_for(NR, 256), 256, 0, stream>>>(fr->bin.as<BinInfo>(), pv, fr->poff.as<uint32_t>(), NR,
+                                                                 Ntot, ts, tiles_x, tiles_per_cam, fr->tk.as<uint32_t>(),
+                                                                 fr->tv.as<uint32_t>());
         UMGS_TRY(cudaGetLastError());
     }
     {
         StageTimer tm(ctx, UMGS_STAGE_SORT, stream);
-        sort_tiles_kernel<<<(unsigned)M, kSortThreads, 0, stream>>>(
-            fr->keys.as<uint64_t>(), fr->keys_tmp.as<uint64_t>(), fr->tile_off.as<int64_t>());
+        if (K > 0) {
+            int bits = 1;
+            while (((int64_t)1 << bits) < M) ++bits;
+            uint32_t* rk = nullptr;
+            uint32_t* rv = nullptr;
+            UMGS_TRY(radix_sort_pairs(fr, fr->tk.as<uint32_t>(), fr->tv.as<uint32_t>(), fr->tk2.as<uint32_t>(),
+                                      fr->tv2.as<uint32_t>(), K, bits, &rk, &rv, stream));
+            fr->tkeys = rk;
+            fr->ids = rv;
+        }
+        tile_ranges_kernel<<<grid_for(M + 1, 256), 256, 0, stream>>>(fr->tkeys, K, M, fr->tile_off.as<int64_t>());
         UMGS_TRY(cudaGetLastError());
     }
     UMGS_TRY(fr->last.reserve(sizeof(int32_t) * (int64_t)ncams * W * H));
@@ -994,10 +919,11 @@ umgs_status frame_lists(const umgs_frame* fr, int64_t* tile_ptr, int32_t* ids, u
                                     cudaMemcpyDeviceToDevice, stream);
     if (e != cudaSuccess) return cuda_fail(fr->ctx, e, "cudaMemcpyAsync(tile_ptr)");
     if (fr->num_keys > 0) {
-        split_keys_kernel<<<grid_for(fr->num_keys, 256), 256, 0, stream>>>(fr->keys.as<uint64_t>(), fr->num_keys, ids,
-                                                                            dbits);
+        lists_kernel<<<grid_for(fr->num_keys, 256), 256, 0, stream>>>(
+            fr->tkeys, fr->ids, fr->num_keys, fr->bin.as<BinInfo>(), fr->ng + fr->nt, fr->tiles_x * fr->tiles_y, ids,
+            dbits);
         e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(fr->ctx, e, "split_keys_kernel");
+        if (e != cudaSuccess) return cuda_fail(fr->ctx, e, "lists_kernel");
     }
     return UMGS_OK;
 }
