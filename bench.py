@@ -242,7 +242,7 @@ def run_umgs(args, rank, world, local_rank):
     names = stage_names()
     stages = {names[k]: {"ms_per_launch": stage_ms[k] / stage_n[k], "launches": int(stage_n[k])}
               for k in range(16) if stage_n[k] > 0}
-    roof = roofline(stages, nkeys, n, sc, clk)
+    roof = roofline(stages, nkeys, n, sc, clk, frame.evaluations())
     res = {
         "metric": METRIC, "value": round(value, 3), "unit": "frames/s", "n_gpus": world, "steps": K,
         "warmup": Wm, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
@@ -270,34 +270,50 @@ def run_umgs(args, rank, world, local_rank):
         torch.distributed.destroy_process_group()
 
 
-def roofline(stages, nkeys, n, sc, clk):
-    """Roofline of the dominant stage (see the design doc for the byte/flop counts)."""
+def roofline(stages, nkeys, n, sc, clk, evals):
+    """Roofline of the dominant stage, plus HBM figures of the streaming stages.
+
+    composite: ALU-bound; algorithmic work = 12 FP32 operations per
+    (pixel, fragment) evaluation (N_alg counted on the device), peak = the
+    FP32 FMA rate 2 x 128 lanes x 152 SMs at the sampled SM clock.
+    Streaming stages: algorithmic bytes per Gaussian / triangle / key against
+    the measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs).
+    """
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
-    src = "measured" if "hbm_gbs" in peaks else "fallback"
+    hsrc = "measured hbm_gbs" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
+    ng, nt = n, sc.meshes[0].nf
+    alg = {  # algorithmic bytes per launch
+        "project_gaussians": ng * (12 + 28 + 4 + 36 + 16),
+        "shade_gaussians": ng * (192 + 12 + 16 + 12),
+        "setup_triangles": nt * (12 + 16 + 160 + 16) + sc.meshes[0].nv * 28,
+        "deform_gaussians": ng * (96 + 40 + 36),
+        "scatter": nkeys * 8,
+    }
+    hbm_stages = {}
+    for k, b in alg.items():
+        if k in stages:
+            t = stages[k]["ms_per_launch"] * 1e-3
+            hbm_stages[k] = {"achieved_gbs": round(b / t / 1e9, 1), "frac": round(b / t / 1e9 / hbm, 4)}
     dom = max(stages, key=lambda k: stages[k]["ms_per_launch"])
     t = stages[dom]["ms_per_launch"] * 1e-3
-    # algorithmic bytes per launch of each HBM-streaming stage
-    ng, nt = n, sc.meshes[0].nf
-    alg = {
-        "project_gaussians": ng * (236 + 48 + 16),
-        "setup_triangles": nt * (12 + 16 + 160 + 16) + sc.meshes[0].nv * 28,
-        "scatter": ng * 16 + nkeys * 8,
-        "sort": nkeys * 16,
-        "composite": nkeys * 8 + 1920 * 1080 * 16,
-        "deform_gaussians": ng * (96 + 40 + 36),
-    }
-    bytes_ = alg.get(dom)
-    if bytes_ is None:
-        return {"bound": "hbm", "stage": dom, "achieved": None, "peak": hbm, "unit": "GB/s", "frac": None,
-                "traffic": None, "peak_source": src}
-    ach = bytes_ / t / 1e9
-    return {"bound": "hbm", "stage": dom, "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
-            "frac": round(ach / hbm, 4), "traffic": None, "peak_source": src + " hbm_gbs"}
+    if dom == "composite":
+        mhz = clk.get("sm_mhz") or 2070.0
+        peak = 2 * 128 * 152 * mhz * 1e6 / 1e12
+        ach = 12.0 * evals / t / 1e12
+        return {"bound": "alu", "stage": dom, "achieved": round(ach, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+                "frac": round(ach / peak, 4), "traffic": None, "evaluations": int(evals),
+                "work": "12 FP32 ops per (pixel, fragment) evaluation",
+                "peak_source": "FP32 FMA rate 2x128 lanes x 152 SMs at %.0f MHz (sampled)" % mhz,
+                "hbm_stages": hbm_stages, "hbm_peak_gbs": hbm, "hbm_peak_source": hsrc}
+    b = alg.get(dom)
+    ach = b / t / 1e9 if b else None
+    return {"bound": "hbm", "stage": dom, "achieved": ach and round(ach, 1), "peak": hbm, "unit": "GB/s",
+            "frac": ach and round(ach / hbm, 4), "traffic": None, "peak_source": hsrc, "hbm_stages": hbm_stages}
 
 
 # ----------------------------------------------------------------------------

@@ -91,7 +91,12 @@ typedef struct {
 } umgs_camera;
 
 /* umgs_render_opts.flags */
-enum { UMGS_RENDER_SAVE_BACKWARD = 1 };  /* keep per-pixel state for umgs_render_backward (FULL mode) */
+enum {
+    UMGS_RENDER_SAVE_BACKWARD = 1,  /* keep per-pixel state for umgs_render_backward (FULL mode) */
+    UMGS_RENDER_MIXED = 2           /* Gaussian fragment records in fp16 (screen position fp32), fp32
+                                       blending; pair with bf16 SH for the mixed-precision form.  Keys,
+                                       footprints and order are unchanged (still exact); no backward. */
+};
 
 typedef struct {
     int32_t tile_size;       /* 8, 16 or 32 pixels; 0 = 16 */
@@ -99,6 +104,8 @@ typedef struct {
     float t_eps;             /* early termination: stop after T < t_eps; 0 = never (default 1e-4) */
     float bg[3];             /* opaque background colour (Eq. 10-11) */
     int32_t flags;           /* UMGS_RENDER_* bits */
+    int32_t sched;           /* compositor schedule: 0 = one CTA per tile; k > 0 = persistent launch with
+                                k CTAs per SM taking tiles in decreasing order of list length */
 } umgs_render_opts;
 
 /* Gradient outputs of umgs_render_backward; every pointer is nullable (not
@@ -173,6 +180,13 @@ umgs_status umgs_render(umgs_ctx* ctx, const umgs_gaussians* gaussians,
 /* Number of keys (tile, primitive) pairs and tiles (all cameras) of the last
  * render into `frame`.  Host outputs; synchronises nothing. */
 umgs_status umgs_frame_counts(const umgs_frame* frame, int64_t* num_keys, int64_t* num_tiles);
+
+/* Number of (pixel, fragment) evaluations of the last render into `frame`:
+ * for every pixel, the entries of its tile list whose footprint (Gaussian
+ * pixel rect, triangle pixel rect) holds the pixel, up to and including the
+ * one after which T < t_eps.  The algorithmic work unit of the compositor.
+ * Host output; synchronises `stream`. */
+umgs_status umgs_frame_evaluations(const umgs_frame* frame, int64_t* evals, void* stream);
 
 /* Copy the sorted tile lists of the last render into caller buffers (device):
  * tile_ptr [num_tiles+1] int64 (list of tile t is [tile_ptr[t], tile_ptr[t+1])),
@@ -276,6 +290,40 @@ umgs_status umgs_deform(umgs_ctx* ctx, const umgs_gaussians* rest, const int32_t
 /* The per-vertex transform table of the last umgs_deform call, copied to a
  * caller buffer [nv,12] (Delta xyz, r xyz, S xx xy xz yy yz zz).  Async. */
 umgs_status umgs_deform_vertex_table(umgs_ctx* ctx, float* out_table, int64_t nv, void* stream);
+
+/* ---- multi-view form: CUDA graph and autotuning -----------------------------
+ *
+ * umgs_render_graph_create renders once (an ordinary umgs_render into
+ * `frame`, which sizes every buffer and uploads the cameras), then captures
+ * the same render into a CUDA graph on a private stream.  The captured render
+ * has no host read-back: the (tile, primitive) pair buffers hold
+ * key_headroom (>= 1; default 1.25) times the pairs of the sizing render,
+ * and a larger count is flagged on the device instead of being written.
+ * umgs_graph_launch replays it asynchronously on `stream` with the SAME
+ * input and output device pointers and the cameras of the creation call
+ * (their contents may change between launches, the cameras may not);
+ * umgs_graph_check synchronises `stream` and reports CAPACITY if a launch
+ * needed more pairs (re-create the graph), INVALID_ARG for bad face indices.
+ * The frame belongs to the graph until umgs_graph_destroy.
+ */
+typedef struct umgs_graph umgs_graph;
+umgs_status umgs_render_graph_create(umgs_ctx* ctx, umgs_frame* frame, const umgs_gaussians* gaussians,
+                                     const umgs_mesh* meshes, int32_t nmeshes, const umgs_camera* cams,
+                                     int32_t ncams, const umgs_render_opts* opts, float* out_rgbt,
+                                     float key_headroom, umgs_graph** out, void* stream);
+umgs_status umgs_graph_launch(umgs_graph* graph, void* stream);
+umgs_status umgs_graph_check(umgs_graph* graph, void* stream);
+void umgs_graph_destroy(umgs_graph* graph);
+
+/* Autotuner: renders the given workload with every tile size (8, 16, 32)
+ * and compositor schedule (one CTA per tile; persistent with 1, 2 or 4 CTAs
+ * per SM), 1 warm-up + 3 timed renders each (CUDA events on `stream`), and
+ * writes the fastest tile_size and sched into *inout (other fields kept) and
+ * its time in ms per render into *best_ms (nullable).  out_rgbt receives the
+ * renders ([ncams,H,W,4]).  Synchronises. */
+umgs_status umgs_autotune(umgs_ctx* ctx, const umgs_gaussians* gaussians, const umgs_mesh* meshes,
+                          int32_t nmeshes, const umgs_camera* cams, int32_t ncams, umgs_render_opts* inout,
+                          float* out_rgbt, double* best_ms, void* stream);
 
 /* ---- per-stage timing ------------------------------------------------------
  * When enabled, every stage launched by this context is bracketed by CUDA

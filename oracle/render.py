@@ -355,3 +355,32 @@ def render_image(scene, cam_index=0, mode=FULL, t_eps=T_EPS, t_product=False,
                     tuple(f.get("mask", -1) for f in frags[:res["n"]])))
     return dict(rgb=out_rgb.reshape(H, W, 3), T=out_T.reshape(H, W), tie=out_tie.reshape(H, W),
                 wsum=out_ws.reshape(H, W), nfrag=out_n.reshape(H, W), sig=hash(tuple(sig)))
+
+
+def evaluation_count(scene, cam_index=0, mode=FULL, t_eps=T_EPS, frame=None):
+    """Algorithmic work of the compositor: for every pixel, the number of
+    entries of its depth-ordered candidate list (Gaussians whose pixel rect
+    holds the pixel, triangles whose pixel rect holds it) up to and including
+    the fragment after which T < t_eps (all of them when it never drops).
+    Returns (total, per-pixel counts [H,W])."""
+    fr = frame or Frame(scene, cam_index)
+    P = fr.P
+    W, H = fr.cam.width, fr.cam.height
+    counts = np.zeros((H, W), np.int64)
+    r = P.rect
+    for y in range(H):
+        for x in range(W):
+            cand = np.nonzero(P.valid & (r[:, 0] <= x) & (r[:, 1] >= x) & (r[:, 2] <= y) & (r[:, 3] >= y))[0]
+            if len(cand) == 0:
+                continue
+            order = np.lexsort((cand, P.dbits[cand]))
+            cand = cand[order]
+            frags = {f["id"]: f for f in fr.fragments_at(x, y, candidates=cand)}
+            res = composite([frags[i] for i in cand if i in frags], mode, t_eps)
+            # position (in the candidate list) of the last consumed fragment
+            consumed = [f for f in cand if f in frags][:res["n"]]
+            if res["T"] < t_eps and consumed:
+                counts[y, x] = int(np.nonzero(cand == consumed[-1])[0][0]) + 1
+            else:
+                counts[y, x] = len(cand)
+    return int(counts.sum()), counts

@@ -192,6 +192,7 @@ umgs_status umgs_render_backward(umgs_ctx* ctx, umgs_frame* frame, const umgs_ga
     if (frame->blend_mode != UMGS_BLEND_FULL)
         return fail(ctx, UMGS_ERR_NOT_IMPLEMENTED, "backward is implemented for blend mode FULL");
     if (!frame->saved) return fail(ctx, UMGS_ERR_INVALID_ARG, "render without UMGS_RENDER_SAVE_BACKWARD");
+    if (frame->mixed) return fail(ctx, UMGS_ERR_NOT_IMPLEMENTED, "backward of a mixed-precision render");
     if (!dL_drgbt) return fail(ctx, UMGS_ERR_INVALID_ARG, "dL_drgbt is NULL");
     const int64_t ng = g ? g->n : 0;
     if (ng != frame->ng) return fail(ctx, UMGS_ERR_INVALID_ARG, "Gaussian count differs from the forward call");
@@ -267,6 +268,17 @@ umgs_status umgs_frame_counts(const umgs_frame* frame, int64_t* num_keys, int64_
     if (!frame->valid) return UMGS_ERR_INVALID_ARG;
     *num_keys = frame->num_keys;
     *num_tiles = frame->num_tiles;
+    return UMGS_OK;
+}
+
+umgs_status umgs_frame_evaluations(const umgs_frame* frame, int64_t* evals, void* stream) {
+    if (!frame || !evals || !frame->valid) return UMGS_ERR_INVALID_ARG;
+    unsigned long long v = 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(&v, frame->status.as<int32_t>() + 6, sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return UMGS_ERR_CUDA;
+    *evals = (int64_t)v;
     return UMGS_OK;
 }
 

@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(TS * TS) composite_bwd_kernel(
                                     py <= (int)(ry >> 16);
                 const float dx = __fsub_rn(qx, q0.x), dy = __fsub_rn(qy, q0.y);
                 const float p2 = gauss_power2(q0.z, q0.w, q1.x, dx, dy);
-                const float Gv = exp2f(p2);
+                const float Gv = fast_exp2(p2);
                 const float ag = __fmul_rn(q1.y, Gv);
                 const float alpha = fminf(kAlphaMax, ag);
                 const bool contrib = active && inrect && alpha >= kAlphaMin;

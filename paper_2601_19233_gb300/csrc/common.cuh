@@ -8,6 +8,7 @@
 // IEEE-754 implementation that evaluates the same expression tree.
 #pragma once
 #include <cstdint>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace umgs {
@@ -41,6 +42,21 @@ struct __align__(16) GRec {
     float4 q0, q1, q2;
 };
 
+// Mixed-precision Gaussian record: 32 bytes, two 16-byte vectors.  The
+// screen position stays fp32 (fp16 loses sub-pixel precision above 2048 px);
+// conic, opacity and colour are fp16; the rect is exact.
+//  v0 = (u, v, half2(ca, cb), half2(cc, opacity)), v1 = (half2(r, g), half2(b, 0), rect_x, rect_y)
+struct __align__(16) GRec16 {
+    uint4 v0, v1;
+};
+
+__device__ __forceinline__ uint32_t pack_half2(float a, float b) {
+    const __half ha = __float2half_rn(a), hb = __float2half_rn(b);
+    return (uint32_t)__half_as_ushort(ha) | ((uint32_t)__half_as_ushort(hb) << 16);
+}
+__device__ __forceinline__ float half_lo(uint32_t p) { return __half2float(__ushort_as_half((unsigned short)(p & 0xffffu))); }
+__device__ __forceinline__ float half_hi(uint32_t p) { return __half2float(__ushort_as_half((unsigned short)(p >> 16))); }
+
 // Triangle record: 160 bytes, ten 16-byte vectors.
 //  edge k (opposite vertex k of the orientation-corrected triangle):
 //     E_k(sx, sy) = A_k*sx + B_k*sy + C_k in 1/256-px units, top-left bias
@@ -59,9 +75,11 @@ struct __align__(16) TRec {
     float iz[3];
     float col[9];
     float alpha[3];
-    float pad2[3];
+    uint32_t rx, ry;  // pixel rect, lo | hi << 16 (as in BinInfo)
+    float pad2;
 };
 static_assert(sizeof(GRec) == 48, "GRec size");
+static_assert(sizeof(GRec16) == 32, "GRec16 size");
 static_assert(sizeof(TRec) == 160, "TRec size");
 
 // Per (camera, primitive) binning info: pixel rect packed as lo | hi << 16,
@@ -74,6 +92,15 @@ struct __align__(16) BinInfo {
 // (2,6) / 16 px, i.e. these offsets in 1/256 px from the pixel centre.
 __device__ __forceinline__ int sample_dx(int j) { return j == 0 ? -32 : j == 1 ? 96 : j == 2 ? -96 : 32; }
 __device__ __forceinline__ int sample_dy(int j) { return j == 0 ? -96 : j == 1 ? -32 : j == 2 ? 32 : 96; }
+
+// 2^x by the hardware approximation (ex2.approx.ftz: relative error ~2^-22,
+// flushes results below 2^-126 to 0); used by the forward and the backward
+// replay alike, so both take the same alpha decisions.
+__device__ __forceinline__ float fast_exp2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 
 // Gaussian alpha at offset (dx, dy) from the projected mean, with a fixed
 // operation sequence so the forward and the backward replay agree bit for bit:

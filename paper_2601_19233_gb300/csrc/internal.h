@@ -44,8 +44,12 @@ struct umgs_frame {
     umgs::DevBuf tfin, ntri, stack;   // backward state (saved renders only)
     umgs::DevBuf ggrad, tgrad, rerun_out;
     umgs::DevBuf fix_list;            // (camera, Gaussian) records whose conic is refined in fp64
+    umgs::DevBuf ord_k, ord_v, ord_k2, ord_v2;  // tile order of the persistent compositor
     int32_t stack_cap = 8;
     bool saved = false;
+    bool mixed = false;               // Gaussian records in fp16 (GRec16)
+    bool nosync = false;              // capture-safe mode: no host read-back inside umgs_render
+    int64_t key_capacity = 0;         // pair capacity in capture-safe mode
     umgs_render_opts opts{};
     int64_t ng = 0, nt = 0;          // Gaussians, triangles (all meshes)
     int32_t ncams = 0, W = 0, H = 0;
@@ -59,7 +63,8 @@ struct umgs_frame {
     void release() {
         for (auto* b : {&cams, &grec, &trec, &bin, &tile_off, &pk, &pv, &pk2, &pv2, &pcnt, &poff, &tk, &tv, &tk2, &tv2,
                         &rs_hist, &rs_hist2, &rs_bsum,
-                        &last, &status, &tfin, &ntri, &stack, &ggrad, &tgrad, &rerun_out, &fix_list})
+                        &last, &status, &tfin, &ntri, &stack, &ggrad, &tgrad, &rerun_out, &fix_list, &ord_k, &ord_v,
+                        &ord_k2, &ord_v2})
             b->release();
     }
 };

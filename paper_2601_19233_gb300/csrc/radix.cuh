@@ -116,10 +116,12 @@ static __global__ void __launch_bounds__(kRsThreads) scan_apply_kernel(const uin
 
 // ---- stable LSD radix sort, 8 bits per pass -----------------------------------
 
-static __global__ void __launch_bounds__(kRsThreads) radix_upsweep_kernel(const uint32_t* __restrict__ keys, int64_t n,
-                                                                          int shift, int nblocks,
+static __global__ void __launch_bounds__(kRsThreads) radix_upsweep_kernel(const uint32_t* __restrict__ keys,
+                                                                          const uint32_t* __restrict__ n_dev,
+                                                                          int64_t n_cap, int shift, int nblocks,
                                                                           uint32_t* __restrict__ hist) {
     __shared__ uint32_t cnt[256];
+    const int64_t n = min((int64_t)*n_dev, n_cap);
     cnt[threadIdx.x] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * kRsTile;
@@ -156,9 +158,10 @@ static __global__ void __launch_bounds__(kRsThreads) radix_hist_scan_kernel(uint
 // as contiguous runs per digit (coalesced).  Input order is preserved for
 // equal digits.
 static __global__ void __launch_bounds__(kRsThreads) radix_downsweep_kernel(
-    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, int64_t n, int shift, int nblocks,
-    const uint32_t* __restrict__ hist, const uint32_t* __restrict__ dtotal, uint32_t* __restrict__ kout,
-    uint32_t* __restrict__ vout) {
+    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, const uint32_t* __restrict__ n_dev,
+    int64_t n_cap, int shift, int nblocks, const uint32_t* __restrict__ hist, const uint32_t* __restrict__ dtotal,
+    uint32_t* __restrict__ kout, uint32_t* __restrict__ vout) {
+    const int64_t n = min((int64_t)*n_dev, n_cap);
     constexpr int NW = kRsThreads / 32;
     __shared__ uint32_t wcnt[NW][256];
     __shared__ uint32_t s_warp[32];

@@ -123,7 +123,8 @@ __global__ void refine_conics_kernel(const float* __restrict__ means, const floa
                                      const float* __restrict__ scales, const float* __restrict__ cov3d, int64_t N,
                                      const DevCam* __restrict__ cams, int ncams, const BinInfo* __restrict__ bin,
                                      int64_t ntot, const unsigned* __restrict__ fix_count,
-                                     const int64_t* __restrict__ fix_list, unsigned fix_cap, GRec* __restrict__ grec) {
+                                     const int64_t* __restrict__ fix_list, unsigned fix_cap, GRec* __restrict__ grec,
+                                     GRec16* __restrict__ grec16) {
     const unsigned cnt = *fix_count;
     const bool overflow = cnt > fix_cap;
     const int64_t total = overflow ? N * ncams : (int64_t)cnt;
@@ -132,12 +133,19 @@ __global__ void refine_conics_kernel(const float* __restrict__ means, const floa
         const int cam = (int)(ri / N);
         const int64_t i = ri - (int64_t)cam * N;
         if (!bin[(int64_t)cam * ntot + i].valid) continue;
-        float* g = reinterpret_cast<float*>(grec + ri);
         float cq[3];  // on overflow every visible record is refined (fp64 is never less accurate)
         conic_fp64(cams[cam], means[3 * i], means[3 * i + 1], means[3 * i + 2], quats, scales, cov3d, i, cq);
-        g[2] = -0.5f * kLog2e * cq[0];
-        g[3] = -kLog2e * cq[1];
-        g[4] = -0.5f * kLog2e * cq[2];
+        if (grec16) {
+            uint32_t* h = reinterpret_cast<uint32_t*>(grec16 + ri);
+            const float o = half_hi(h[3]);
+            h[2] = pack_half2(-0.5f * kLog2e * cq[0], -kLog2e * cq[1]);
+            h[3] = pack_half2(-0.5f * kLog2e * cq[2], o);
+        } else {
+            float* g = reinterpret_cast<float*>(grec + ri);
+            g[2] = -0.5f * kLog2e * cq[0];
+            g[3] = -kLog2e * cq[1];
+            g[4] = -0.5f * kLog2e * cq[2];
+        }
     }
 }
 
@@ -145,8 +153,8 @@ __global__ void __launch_bounds__(256, 2) project_gaussians_kernel(
     const float* __restrict__ means, const float* __restrict__ quats, const float* __restrict__ scales,
     const float* __restrict__ opac, const void* __restrict__ sh, int sh_dtype, int sh_deg,
     const float* __restrict__ cov3d, int64_t N, const DevCam* __restrict__ cams, int ncams,
-    int ts, int tiles_x, int tiles_per_cam, GRec* __restrict__ grec, BinInfo* __restrict__ bin, int64_t ntot_prims,
-    unsigned* __restrict__ fix_count, int64_t* __restrict__ fix_list,
+    int ts, int tiles_x, int tiles_per_cam, GRec* __restrict__ grec, GRec16* __restrict__ grec16,
+    BinInfo* __restrict__ bin, int64_t ntot_prims, unsigned* __restrict__ fix_count, int64_t* __restrict__ fix_list,
     unsigned fix_cap) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -229,12 +237,19 @@ __global__ void __launch_bounds__(256, 2) project_gaussians_kernel(
             const unsigned slot = atomicAdd(fix_count, 1u);
             if (slot < fix_cap) fix_list[slot] = ri;
         }
-        // colour (q1.zw, q2.x) is written by shade_gaussians_kernel
-        float4* gp = reinterpret_cast<float4*>(grec + ri);
-        gp[0] = make_float4(u, v, -0.5f * kLog2e * ia, -kLog2e * ib);
-        reinterpret_cast<float2*>(gp + 1)[0] = make_float2(-0.5f * kLog2e * ic, o);
-        reinterpret_cast<float2*>(gp + 2)[0] = make_float2(0.f, __uint_as_float(bi.rx));
-        reinterpret_cast<float*>(gp + 2)[2] = __uint_as_float(bi.ry);
+        // colour is written by shade_gaussians_kernel
+        if (grec16) {
+            GRec16* hp = grec16 + ri;
+            hp->v0 = make_uint4(__float_as_uint(u), __float_as_uint(v),
+                                pack_half2(-0.5f * kLog2e * ia, -kLog2e * ib), pack_half2(-0.5f * kLog2e * ic, o));
+            reinterpret_cast<uint2*>(&hp->v1)[1] = make_uint2(bi.rx, bi.ry);
+        } else {
+            float4* gp = reinterpret_cast<float4*>(grec + ri);
+            gp[0] = make_float4(u, v, -0.5f * kLog2e * ia, -kLog2e * ib);
+            reinterpret_cast<float2*>(gp + 1)[0] = make_float2(-0.5f * kLog2e * ic, o);
+            reinterpret_cast<float2*>(gp + 2)[0] = make_float2(0.f, __uint_as_float(bi.rx));
+            reinterpret_cast<float*>(gp + 2)[2] = __uint_as_float(bi.ry);
+        }
     }
 }
 
@@ -244,7 +259,7 @@ template <int DEG>
 __global__ void __launch_bounds__(256) shade_gaussians_kernel(const float* __restrict__ means, const void* __restrict__ sh,
                                                               int sh_dtype, int64_t N, const DevCam* __restrict__ cams,
                                                               int ncams, const BinInfo* __restrict__ bin, int64_t ntot,
-                                                              GRec* __restrict__ grec) {
+                                                              GRec* __restrict__ grec, GRec16* __restrict__ grec16) {
     constexpr int K = (DEG + 1) * (DEG + 1);
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -303,9 +318,14 @@ __global__ void __launch_bounds__(256) shade_gaussians_kernel(const float* __res
             for (int k = 0; k < K; ++k) acc = fmaf(c[3 * k + ch], Y[k], acc);
             rgb[ch] = fmaxf(acc + 0.5f, 0.f);
         }
-        float4* gp = reinterpret_cast<float4*>(grec + (int64_t)cam * N + i);
-        reinterpret_cast<float2*>(gp + 1)[1] = make_float2(rgb[0], rgb[1]);
-        reinterpret_cast<float*>(gp + 2)[0] = rgb[2];
+        if (grec16) {
+            reinterpret_cast<uint2*>(&grec16[(int64_t)cam * N + i].v1)[0] =
+                make_uint2(pack_half2(rgb[0], rgb[1]), pack_half2(rgb[2], 0.f));
+        } else {
+            float4* gp = reinterpret_cast<float4*>(grec + (int64_t)cam * N + i);
+            reinterpret_cast<float2*>(gp + 1)[1] = make_float2(rgb[0], rgb[1]);
+            reinterpret_cast<float*>(gp + 2)[0] = rgb[2];
+        }
     }
 }
 
@@ -407,7 +427,9 @@ __global__ void __launch_bounds__(256) setup_triangles_kernel(
         t.const_alpha = const_alpha;
         t.pad0 = 0; t.pad1 = 0;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) t.pad2[k] = 0.f;
+        t.rx = bi.rx;
+        t.ry = bi.ry;
+        t.pad2 = 0.f;
         trec[(int64_t)cam * nt_total + tri_base + f] = t;
     }
 }
@@ -419,8 +441,9 @@ __global__ void __launch_bounds__(256) setup_triangles_kernel(
 // order without a per-tile sort.
 
 __global__ void prim_keys_kernel(const BinInfo* __restrict__ bin, int64_t n, uint32_t* __restrict__ pk,
-                                 uint32_t* __restrict__ pv) {
+                                 uint32_t* __restrict__ pv, uint32_t* __restrict__ n_dev) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i == 0) *n_dev = (uint32_t)n;
     if (i >= n) return;
     const BinInfo b = bin[i];
     pk[i] = b.valid ? b.dbits : 0xffffffffu;
@@ -442,7 +465,8 @@ __global__ void tile_counts_kernel(const BinInfo* __restrict__ bin, const uint32
 
 __global__ void emit_pairs_kernel(const BinInfo* __restrict__ bin, const uint32_t* __restrict__ pv,
                                   const uint32_t* __restrict__ off, int64_t n, int64_t ntot, int ts, int tiles_x,
-                                  int tiles_per_cam, uint32_t* __restrict__ tk, uint32_t* __restrict__ tv) {
+                                  int tiles_per_cam, uint32_t* __restrict__ tk, uint32_t* __restrict__ tv, int64_t cap,
+                                  int32_t* __restrict__ status) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const uint32_t rec = pv[i];
@@ -451,7 +475,8 @@ __global__ void emit_pairs_kernel(const BinInfo* __restrict__ bin, const uint32_
     const int cam = (int)(rec / ntot);
     const uint32_t id = (uint32_t)(rec - (int64_t)cam * ntot);
     const int xlo = (b.rx & 0xffff) / ts, xhi = (b.rx >> 16) / ts, ylo = (b.ry & 0xffff) / ts, yhi = (b.ry >> 16) / ts;
-    uint32_t o = off[i];
+    int64_t o = off[i];
+    if (o + (int64_t)(yhi - ylo + 1) * (xhi - xlo + 1) > cap) { atomicOr(status, 4); return; }  // capacity overflow
     for (int ty = ylo; ty <= yhi; ++ty)
         for (int tx = xlo; tx <= xhi; ++tx) {
             tk[o] = (uint32_t)(cam * tiles_per_cam + ty * tiles_x + tx);
@@ -461,9 +486,11 @@ __global__ void emit_pairs_kernel(const BinInfo* __restrict__ bin, const uint32_
 }
 
 // tile_off[t] = first index of tile t in the sorted keys (lower bound)
-__global__ void tile_ranges_kernel(const uint32_t* __restrict__ tk, int64_t K, int64_t M, int64_t* __restrict__ off) {
+__global__ void tile_ranges_kernel(const uint32_t* __restrict__ tk, const uint32_t* __restrict__ K_dev, int64_t Kcap,
+                                   int64_t M, int64_t* __restrict__ off) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t > M) return;
+    const int64_t K = min((int64_t)*K_dev, Kcap);
     if (t == M) { off[M] = K; return; }
     int64_t lo = 0, hi = K;
     while (lo < hi) {
@@ -493,16 +520,14 @@ struct PixelState {
 // fragment the four sub-sample transmittances before it (scaled by T_in/4)
 // in a per-pixel stack of capacity `cap` (`need` records the largest count).
 template <int TS, bool SAVE>
-__global__ void __launch_bounds__(TS * TS) composite_kernel(
+__device__ __forceinline__ void composite_tile(
+    int tile, float4 (*__restrict__ s_rec)[10], uint32_t* __restrict__ s_id, uint32_t* __restrict__ s_wmask,
     const uint32_t* __restrict__ ids, const int64_t* __restrict__ off, const GRec* __restrict__ grec,
-    const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x, int tiles_per_cam, int W, int H,
-    float t_eps, float bg0, float bg1, float bg2, int mode, float4* __restrict__ out, int32_t* __restrict__ out_last,
+    const GRec16* __restrict__ grec16, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
+    int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, int mode, float4* __restrict__ out, int32_t* __restrict__ out_last,
     float* __restrict__ out_tfin, int32_t* __restrict__ out_ntri, float4* __restrict__ stack, int cap,
-    int64_t npix, int32_t* __restrict__ need) {
+    int64_t npix, int32_t* __restrict__ need, unsigned long long* __restrict__ eval_count) {
     constexpr int NT = TS * TS;
-    __shared__ float4 s_rec[kBatch][10];
-    __shared__ uint32_t s_id[kBatch];
-    const int tile = blockIdx.x;
     const int cam = tile / tiles_per_cam;
     const int lt = tile - cam * tiles_per_cam;
     const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
@@ -510,6 +535,7 @@ __global__ void __launch_bounds__(TS * TS) composite_kernel(
     const bool inside = px < W && py < H;
     const int64_t beg = off[tile], end = off[tile + 1];
     const GRec* G = grec + (int64_t)cam * Ng;
+    const GRec16* G16 = grec16 ? grec16 + (int64_t)cam * Ng : nullptr;
     const TRec* TR = trec + (int64_t)cam * Nt;
     const float qx = px + 0.5f, qy = py + 0.5f;
     const long long scx = (long long)px * 256 + 128, scy = (long long)py * 256 + 128;
@@ -522,44 +548,82 @@ __global__ void __launch_bounds__(TS * TS) composite_kernel(
     bool done = !inside;
     int last = 0;
     int sp = 0;
+    unsigned nevals = 0;  // (pixel, fragment) pairs whose footprint holds the pixel, up to termination
     const int64_t pix = ((int64_t)cam * H + py) * W + px;
 
+    // warp w covers the tile rows [w*32/TS, (w+1)*32/TS); a record whose rect
+    // misses those rows is skipped by the whole warp with one test
+    constexpr int ROWS_PER_WARP = 32 / TS > 0 ? 32 / TS : 1;
+    const int warp = threadIdx.x >> 5;
+    const int tile_y0 = ty * TS;
+    const float pxf = (float)px, pyf = (float)py;
     for (int64_t b0 = beg; b0 < end; b0 += kBatch) {
         if (__syncthreads_count(done) == NT) break;
         const int n = (int)min((int64_t)kBatch, end - b0);
         for (int k = threadIdx.x; k < n; k += NT) {
             const uint32_t id = ids[b0 + k];
             s_id[k] = id;
+            uint32_t rx, ry;
             if (id < Ng) {
-                const float4* src = reinterpret_cast<const float4*>(G + id);
-                s_rec[k][0] = src[0]; s_rec[k][1] = src[1]; s_rec[k][2] = src[2];
+                float4 a, b, c;
+                if (G16) {  // fp16 record: widen to the fp32 layout
+                    const uint4 h0 = G16[id].v0, h1 = G16[id].v1;
+                    a = make_float4(__uint_as_float(h0.x), __uint_as_float(h0.y), half_lo(h0.z), half_hi(h0.z));
+                    b = make_float4(half_lo(h0.w), half_hi(h0.w), half_lo(h1.x), half_hi(h1.x));
+                    c = make_float4(half_lo(h1.y), __uint_as_float(h1.z), __uint_as_float(h1.w), 0.f);
+                } else {
+                    const float4* src = reinterpret_cast<const float4*>(G + id);
+                    a = src[0]; b = src[1]; c = src[2];
+                }
+                rx = __float_as_uint(c.y);
+                ry = __float_as_uint(c.z);
+                s_rec[k][0] = a;
+                s_rec[k][1] = make_float4(b.x, b.y, (float)(rx & 0xffff), (float)(rx >> 16));
+                s_rec[k][2] = make_float4((float)(ry & 0xffff), (float)(ry >> 16), b.z, b.w);
+                s_rec[k][3] = make_float4(c.x, 0.f, 0.f, 0.f);
             } else {
                 const float4* src = reinterpret_cast<const float4*>(TR + (id - Ng));
 #pragma unroll
                 for (int q = 0; q < 10; ++q) s_rec[k][q] = src[q];
+                const TRec& tr = *reinterpret_cast<const TRec*>(&s_rec[k][0]);
+                rx = tr.rx;
+                ry = tr.ry;
             }
+            // warps whose rows intersect the record's rows
+            const int r0 = max((int)(ry & 0xffff) - tile_y0, 0), r1 = min((int)(ry >> 16) - tile_y0, TS - 1);
+            uint32_t wm = 0;
+            if (r0 <= r1) {
+                const int w0 = (r0 * TS) >> 5, w1 = (r1 * TS + TS - 1) >> 5;
+                wm = ((2u << w1) - 1u) & ~((1u << w0) - 1u);
+            }
+            s_wmask[k] = wm;
         }
         __syncthreads();
-        if (!done) {
+        if (__any_sync(0xffffffffu, !done)) {
             for (int k = 0; k < n; ++k) {
+                if (!((s_wmask[k] >> warp) & 1u)) continue;  // uniform across the warp
+                if (done) continue;
                 const uint32_t id = s_id[k];
                 if (id < Ng) {
-                    const float4 q2 = s_rec[k][2];
-                    const uint32_t rx = __float_as_uint(q2.y), ry = __float_as_uint(q2.z);
-                    if (px < (int)(rx & 0xffff) || px > (int)(rx >> 16) || py < (int)(ry & 0xffff) || py > (int)(ry >> 16))
-                        continue;
-                    const float4 q0 = s_rec[k][0], q1 = s_rec[k][1];
+                    const float4 q1 = s_rec[k][1], q2 = s_rec[k][2];
+                    if (pxf < q1.z || pxf > q1.w || pyf < q2.x || pyf > q2.y) continue;
+                    ++nevals;
+                    const float4 q0 = s_rec[k][0];
                     const float dx = __fsub_rn(qx, q0.x), dy = __fsub_rn(qy, q0.y);
                     const float p2 = gauss_power2(q0.z, q0.w, q1.x, dx, dy);
-                    const float alpha = fminf(kAlphaMax, __fmul_rn(q1.y, exp2f(p2)));
+                    const float alpha = fminf(kAlphaMax, __fmul_rn(q1.y, fast_exp2(p2)));
                     if (alpha < kAlphaMin) continue;
                     const float w = alpha * st.T;
-                    st.C[0] += w * q1.z; st.C[1] += w * q1.w; st.C[2] += w * q2.x;
+                    st.C[0] += w * q2.z; st.C[1] += w * q2.w; st.C[2] += w * s_rec[k][3].x;
                     st.T *= (1.f - alpha);
                     if (mode == UMGS_BLEND_ENTITY_ALL) st.g_since *= (1.f - alpha);
                     else st.in_ent = false;
                 } else {
                     const TRec& t = *reinterpret_cast<const TRec*>(&s_rec[k][0]);
+                    if (px < (int)(t.rx & 0xffff) || px > (int)(t.rx >> 16) || py < (int)(t.ry & 0xffff) ||
+                        py > (int)(t.ry >> 16))
+                        continue;
+                    ++nevals;
                     long long E[3];
 #pragma unroll
                     for (int e = 0; e < 3; ++e) E[e] = (long long)t.A[e] * scx + (long long)t.B[e] * scy + t.C[e];
@@ -640,9 +704,15 @@ __global__ void __launch_bounds__(TS * TS) composite_kernel(
                     }
                 }
                 last = (int)(b0 - beg) + k + 1;
-                if (st.T < t_eps) { done = true; break; }
+                if (st.T < t_eps) done = true;
             }
         }
+    }
+    {
+        unsigned s = nevals;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0 && s) atomicAdd(eval_count, (unsigned long long)s);
     }
     if (inside) {
         out[pix] = make_float4(st.C[0] + st.T * bg0, st.C[1] + st.T * bg1, st.C[2] + st.T * bg2, st.T);
@@ -653,6 +723,57 @@ __global__ void __launch_bounds__(TS * TS) composite_kernel(
             if (sp > cap) atomicMax(need, sp);
         }
     }
+}
+
+
+// one CTA per tile (grid launch)
+template <int TS, bool SAVE>
+__global__ void __launch_bounds__(TS * TS) composite_kernel(
+    const uint32_t* __restrict__ ids, const int64_t* __restrict__ off, const GRec* __restrict__ grec,
+    const GRec16* __restrict__ grec16, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
+    int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, int mode, float4* __restrict__ out, int32_t* __restrict__ out_last,
+    float* __restrict__ out_tfin, int32_t* __restrict__ out_ntri, float4* __restrict__ stack, int cap,
+    int64_t npix, int32_t* __restrict__ need, unsigned long long* __restrict__ eval_count) {
+    __shared__ float4 s_rec[kBatch][10];
+    __shared__ uint32_t s_id[kBatch];
+    __shared__ uint32_t s_wmask[kBatch];
+    composite_tile<TS, SAVE>(blockIdx.x, s_rec, s_id, s_wmask, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, mode, out, out_last, out_tfin, out_ntri, stack, cap, npix, need, eval_count);
+}
+
+// persistent launch: resident CTAs take tiles from an atomic queue in the
+// order `order` (decreasing list length: the heaviest tiles start first)
+template <int TS, bool SAVE>
+__global__ void __launch_bounds__(TS * TS) composite_persistent_kernel(
+    const uint32_t* __restrict__ order, unsigned* __restrict__ work, int64_t M,
+    const uint32_t* __restrict__ ids, const int64_t* __restrict__ off, const GRec* __restrict__ grec,
+    const GRec16* __restrict__ grec16, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
+    int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, int mode, float4* __restrict__ out, int32_t* __restrict__ out_last,
+    float* __restrict__ out_tfin, int32_t* __restrict__ out_ntri, float4* __restrict__ stack, int cap,
+    int64_t npix, int32_t* __restrict__ need, unsigned long long* __restrict__ eval_count) {
+    __shared__ float4 s_rec[kBatch][10];
+    __shared__ uint32_t s_id[kBatch];
+    __shared__ uint32_t s_wmask[kBatch];
+    __shared__ unsigned s_next;
+    while (true) {
+        if (threadIdx.x == 0) s_next = atomicAdd(work, 1u);
+        __syncthreads();
+        const unsigned k = s_next;
+        __syncthreads();
+        if ((int64_t)k >= M) break;
+        composite_tile<TS, SAVE>((int)order[k], s_rec, s_id, s_wmask, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, mode, out, out_last, out_tfin, out_ntri, stack, cap, npix, need, eval_count);
+        __syncthreads();
+    }
+}
+
+// tile order for the persistent launch: key = 0xffff - min(list length, 0xffff)
+__global__ void tile_order_keys_kernel(const int64_t* __restrict__ off, int64_t M, uint32_t* __restrict__ k,
+                                       uint32_t* __restrict__ v, uint32_t* __restrict__ m_dev) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t == 0) *m_dev = (uint32_t)M;
+    if (t >= M) return;
+    const int64_t c = off[t + 1] - off[t];
+    k[t] = 0xffffu - (uint32_t)min(c, (int64_t)0xffff);
+    v[t] = (uint32_t)t;
 }
 
 // ---------------------------------------------------------------------------
@@ -670,6 +791,10 @@ __global__ void lists_kernel(const uint32_t* __restrict__ tk, const uint32_t* __
 }
 
 
+cudaError_t radix_sort_pairs(umgs_frame* fr, uint32_t* k, uint32_t* v, uint32_t* k2, uint32_t* v2,
+                             const uint32_t* n_dev, int64_t n_cap, int bits, uint32_t** rk, uint32_t** rv,
+                             cudaStream_t s);
+
 cudaError_t launch_composite(umgs_frame* fr, const umgs_render_opts& opts, float* out_rgbt, cudaStream_t stream) {
     const float te = opts.t_eps > 0.f ? opts.t_eps : -1.f;
     float4* out = reinterpret_cast<float4*>(out_rgbt);
@@ -679,12 +804,45 @@ cudaError_t launch_composite(umgs_frame* fr, const umgs_render_opts& opts, float
     const int64_t npix = (int64_t)fr->ncams * fr->W * fr->H;
     const bool save = fr->saved;
     if (save) cudaMemsetAsync(fr->status.as<int32_t>() + 2, 0, sizeof(int32_t), stream);
+    const bool persist = opts.sched > 0;
+    const uint32_t* order = nullptr;
+    unsigned* work = nullptr;
+    int nblk = 0;
+    if (persist) {
+        // tiles in decreasing order of list length (stable radix sort of 16-bit keys)
+        cudaError_t e;
+        if ((e = fr->ord_k.reserve(sizeof(uint32_t) * M)) != cudaSuccess) return e;
+        if ((e = fr->ord_v.reserve(sizeof(uint32_t) * M)) != cudaSuccess) return e;
+        if ((e = fr->ord_k2.reserve(sizeof(uint32_t) * M)) != cudaSuccess) return e;
+        if ((e = fr->ord_v2.reserve(sizeof(uint32_t) * M)) != cudaSuccess) return e;
+        uint32_t* mdev = reinterpret_cast<uint32_t*>(fr->status.as<int32_t>() + 4);
+        work = reinterpret_cast<unsigned*>(fr->status.as<int32_t>() + 8);
+        tile_order_keys_kernel<<<(M + 255) / 256, 256, 0, stream>>>(fr->tile_off.as<int64_t>(), M, fr->ord_k.as<uint32_t>(),
+                                                                     fr->ord_v.as<uint32_t>(), mdev);
+        uint32_t* rk = nullptr;
+        uint32_t* rv = nullptr;
+        if ((e = radix_sort_pairs(fr, fr->ord_k.as<uint32_t>(), fr->ord_v.as<uint32_t>(), fr->ord_k2.as<uint32_t>(),
+                                  fr->ord_v2.as<uint32_t>(), mdev, M, 16, &rk, &rv, stream)) != cudaSuccess)
+            return e;
+        order = rv;
+        cudaMemsetAsync(work, 0, sizeof(unsigned), stream);
+        nblk = opts.sched * fr->ctx->num_sms;
+    }
 #define UMGS_LAUNCH(TSV, SV)                                                                                    \
-    composite_kernel<TSV, SV><<<M, TSV * TSV, 0, stream>>>(                                                     \
-        fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->trec.as<TRec>(), fr->ng,                  \
+    if (persist) composite_persistent_kernel<TSV, SV><<<nblk, TSV * TSV, 0, stream>>>(order, work, M,          \
+        fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->mixed ? fr->grec.as<GRec16>() : nullptr,  \
+        fr->trec.as<TRec>(), fr->ng,                                                                            \
         fr->nt, fr->tiles_x, tpc, fr->W, fr->H, te, opts.bg[0], opts.bg[1], opts.bg[2], opts.blend_mode, out,     \
         fr->last.as<int32_t>(), save ? fr->tfin.as<float>() : nullptr, save ? fr->ntri.as<int32_t>() : nullptr,   \
-        save ? fr->stack.as<float4>() : nullptr, fr->stack_cap, npix, fr->status.as<int32_t>() + 2)
+        save ? fr->stack.as<float4>() : nullptr, fr->stack_cap, npix, fr->status.as<int32_t>() + 2,             \
+        reinterpret_cast<unsigned long long*>(fr->status.as<int32_t>() + 6));                                   \
+    else composite_kernel<TSV, SV><<<M, TSV * TSV, 0, stream>>>(                                                \
+        fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->mixed ? fr->grec.as<GRec16>() : nullptr,  \
+        fr->trec.as<TRec>(), fr->ng,                                                                            \
+        fr->nt, fr->tiles_x, tpc, fr->W, fr->H, te, opts.bg[0], opts.bg[1], opts.bg[2], opts.blend_mode, out,     \
+        fr->last.as<int32_t>(), save ? fr->tfin.as<float>() : nullptr, save ? fr->ntri.as<int32_t>() : nullptr,   \
+        save ? fr->stack.as<float4>() : nullptr, fr->stack_cap, npix, fr->status.as<int32_t>() + 2,             \
+        reinterpret_cast<unsigned long long*>(fr->status.as<int32_t>() + 6))
     if (ts == 16) { if (save) UMGS_LAUNCH(16, true); else UMGS_LAUNCH(16, false); }
     else if (ts == 8) { if (save) UMGS_LAUNCH(8, true); else UMGS_LAUNCH(8, false); }
     else { if (save) UMGS_LAUNCH(32, true); else UMGS_LAUNCH(32, false); }
@@ -705,11 +863,14 @@ cudaError_t scan_u32(umgs_frame* fr, const uint32_t* in, uint32_t* out, int64_t 
     return cudaGetLastError();
 }
 
-// stable LSD radix sort of (k, v) on the low `bits` bits; ping-pongs with
-// (k2, v2) and returns where the result ended
-cudaError_t radix_sort_pairs(umgs_frame* fr, uint32_t* k, uint32_t* v, uint32_t* k2, uint32_t* v2, int64_t n, int bits,
-                             uint32_t** rk, uint32_t** rv, cudaStream_t s) {
-    const int64_t nb = (n + kRsTile - 1) / kRsTile;
+// stable LSD radix sort of (k, v) on the low `bits` bits; the element count
+// is read from device memory (n_dev, at most n_cap, which sizes the grids);
+// ping-pongs with (k2, v2) and returns where the result ended
+cudaError_t radix_sort_pairs(umgs_frame* fr, uint32_t* k, uint32_t* v, uint32_t* k2, uint32_t* v2,
+                             const uint32_t* n_dev, int64_t n_cap, int bits, uint32_t** rk, uint32_t** rv,
+                             cudaStream_t s) {
+    const int64_t n = n_cap;
+    const int64_t nb = std::max<int64_t>(1, (n + kRsTile - 1) / kRsTile);
     const int64_t nh = 256 * nb;
     cudaError_t e = fr->rs_hist.reserve(sizeof(uint32_t) * nh);
     if (e != cudaSuccess) return e;
@@ -718,9 +879,10 @@ cudaError_t radix_sort_pairs(umgs_frame* fr, uint32_t* k, uint32_t* v, uint32_t*
     uint32_t* hist = fr->rs_hist.as<uint32_t>();
     uint32_t* dtotal = fr->rs_hist2.as<uint32_t>();
     for (int shift = 0; shift < bits; shift += 8) {
-        radix_upsweep_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(k, n, shift, (int)nb, hist);
+        radix_upsweep_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(k, n_dev, n_cap, shift, (int)nb, hist);
         radix_hist_scan_kernel<<<256, kRsThreads, 0, s>>>(hist, (int)nb, dtotal);
-        radix_downsweep_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(k, v, n, shift, (int)nb, hist, dtotal, k2, v2);
+        radix_downsweep_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(k, v, n_dev, n_cap, shift, (int)nb, hist, dtotal,
+                                                                   k2, v2);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         uint32_t* t = k; k = k2; k2 = t;
@@ -770,11 +932,17 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     } while (0)
 
     UMGS_TRY(fr->cams.reserve(sizeof(DevCam) * ncams));
-    UMGS_TRY(fr->grec.reserve(sizeof(GRec) * std::max<int64_t>(1, Ng * ncams)));
+    const bool mixed = (opts.flags & UMGS_RENDER_MIXED) != 0;
+    fr->mixed = mixed;
+    UMGS_TRY(fr->grec.reserve((mixed ? sizeof(GRec16) : sizeof(GRec)) * std::max<int64_t>(1, Ng * ncams)));
     UMGS_TRY(fr->trec.reserve(sizeof(TRec) * std::max<int64_t>(1, Nt * ncams)));
     UMGS_TRY(fr->bin.reserve(sizeof(BinInfo) * std::max<int64_t>(1, Ntot * ncams)));
     UMGS_TRY(fr->tile_off.reserve(sizeof(int64_t) * (M + 1)));
-    UMGS_TRY(fr->status.reserve(sizeof(int32_t) * 8));
+    // status words: [0] error bits, [1] number of (tile, id) pairs, [2] largest
+    // saved-stack need, [3] fp64 conic list length, [4] tile count for the
+    // tile-order sort, [5] record count for the depth sort, [6..7] evaluation
+    // count (u64), [8] persistent work counter
+    UMGS_TRY(fr->status.reserve(sizeof(int32_t) * 16));
 
     // cameras: host -> pinned staging -> device
     std::vector<DevCam> dc(ncams);
@@ -794,8 +962,10 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
         }
         d.pad = 0;
     }
-    UMGS_TRY(cudaMemcpyAsync(fr->cams.ptr, dc.data(), sizeof(DevCam) * ncams, cudaMemcpyHostToDevice, stream));
-    UMGS_TRY(cudaMemsetAsync(fr->status.ptr, 0, sizeof(int32_t) * 8, stream));
+    // (capture-safe mode: the cameras were uploaded by the sizing render)
+    if (!fr->nosync)
+        UMGS_TRY(cudaMemcpyAsync(fr->cams.ptr, dc.data(), sizeof(DevCam) * ncams, cudaMemcpyHostToDevice, stream));
+    UMGS_TRY(cudaMemsetAsync(fr->status.ptr, 0, sizeof(int32_t) * 16, stream));
 
     const DevCam* dcams = fr->cams.as<DevCam>();
     const unsigned fix_cap = (unsigned)std::min<int64_t>(std::max<int64_t>(1, Ng * ncams), 1 << 22);
@@ -804,24 +974,25 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
         StageTimer tm(ctx, UMGS_STAGE_PROJECT_GAUSSIANS, stream);
         project_gaussians_kernel<<<grid_for(Ng, 256), 256, 0, stream>>>(
             g->means, g->quats, g->scales, g->opacities, g->sh, g->sh_dtype, g->sh_degree, g->cov3d, Ng, dcams,
-            ncams, ts, tiles_x, tiles_per_cam, fr->grec.as<GRec>(), fr->bin.as<BinInfo>(), Ntot,
-            reinterpret_cast<unsigned*>(fr->status.as<int32_t>() + 3),
+            ncams, ts, tiles_x, tiles_per_cam, fr->grec.as<GRec>(), mixed ? fr->grec.as<GRec16>() : nullptr,
+            fr->bin.as<BinInfo>(), Ntot, reinterpret_cast<unsigned*>(fr->status.as<int32_t>() + 3),
             fr->fix_list.as<int64_t>(), fix_cap);
         UMGS_TRY(cudaGetLastError());
         refine_conics_kernel<<<4 * ctx->num_sms, 128, 0, stream>>>(
             g->means, g->quats, g->scales, g->cov3d, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot,
             reinterpret_cast<unsigned*>(fr->status.as<int32_t>() + 3), fr->fix_list.as<int64_t>(), fix_cap,
-            fr->grec.as<GRec>());
+            fr->grec.as<GRec>(), mixed ? fr->grec.as<GRec16>() : nullptr);
         UMGS_TRY(cudaGetLastError());
     }
     if (Ng > 0) {
         StageTimer tm(ctx, UMGS_STAGE_SHADE_GAUSSIANS, stream);
         const unsigned gb = grid_for(Ng, 256);
+        GRec16* g16 = mixed ? fr->grec.as<GRec16>() : nullptr;
         switch (g->sh_degree) {
-            case 0: shade_gaussians_kernel<0><<<gb, 256, 0, stream>>>(g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>()); break;
-            case 1: shade_gaussians_kernel<1><<<gb, 256, 0, stream>>>(g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>()); break;
-            case 2: shade_gaussians_kernel<2><<<gb, 256, 0, stream>>>(g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>()); break;
-            default: shade_gaussians_kernel<3><<<gb, 256, 0, stream>>>(g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>()); break;
+            case 0: shade_gaussians_kernel<0><<<gb, 256, 0, stream>>>(g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16); break;
+            case 1: shade_gaussians_kernel<1><<<gb, 256, 0, stream>>>(g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16); break;
+            case 2: shade_gaussians_kernel<2><<<gb, 256, 0, stream>>>(g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16); break;
+            default: shade_gaussians_kernel<3><<<gb, 256, 0, stream>>>(g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16); break;
         }
         UMGS_TRY(cudaGetLastError());
     }
@@ -848,53 +1019,64 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     UMGS_TRY(fr->poff.reserve(sizeof(uint32_t) * std::max<int64_t>(1, NR)));
     uint32_t* pk = fr->pk.as<uint32_t>();
     uint32_t* pv = fr->pv.as<uint32_t>();
+    uint32_t* status_u = reinterpret_cast<uint32_t*>(fr->status.as<int32_t>());
     if (NR > 0) {
         StageTimer tm(ctx, UMGS_STAGE_SCAN, stream);
-        prim_keys_kernel<<<grid_for(NR, 256), 256, 0, stream>>>(fr->bin.as<BinInfo>(), NR, pk, pv);
+        prim_keys_kernel<<<grid_for(NR, 256), 256, 0, stream>>>(fr->bin.as<BinInfo>(), NR, pk, pv, status_u + 5);
         UMGS_TRY(cudaGetLastError());
         uint32_t* rk = nullptr;
         uint32_t* rv = nullptr;
-        UMGS_TRY(radix_sort_pairs(fr, pk, pv, fr->pk2.as<uint32_t>(), fr->pv2.as<uint32_t>(), NR, 32, &rk, &rv, stream));
+        UMGS_TRY(radix_sort_pairs(fr, pk, pv, fr->pk2.as<uint32_t>(), fr->pv2.as<uint32_t>(), status_u + 5, NR, 32, &rk,
+                                  &rv, stream));
         pk = rk;
         pv = rv;
         tile_counts_kernel<<<grid_for(NR, 256), 256, 0, stream>>>(fr->bin.as<BinInfo>(), pv, NR, ts,
                                                                   fr->pcnt.as<uint32_t>());
-        UMGS_TRY(scan_u32(fr, fr->pcnt.as<uint32_t>(), fr->poff.as<uint32_t>(), NR,
-                          reinterpret_cast<uint32_t*>(fr->status.as<int32_t>() + 1), stream));
+        UMGS_TRY(scan_u32(fr, fr->pcnt.as<uint32_t>(), fr->poff.as<uint32_t>(), NR, status_u + 1, stream));
     }
-    // read back the number of pairs (and the status word)
-    UMGS_TRY(cudaMemcpyAsync(ctx->pinned, fr->status.ptr, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
-    UMGS_TRY(cudaStreamSynchronize(stream));
-    const int32_t st = (int32_t)(ctx->pinned[0] & 0xffffffff);
-    const int64_t K = NR > 0 ? (int64_t)(uint32_t)(ctx->pinned[0] >> 32) : 0;
-    if (st & 1) return fail(ctx, UMGS_ERR_INVALID_ARG, "a face index is out of range");
-    fr->num_keys = K;
-    UMGS_TRY(fr->tk.reserve(sizeof(uint32_t) * std::max<int64_t>(1, K)));
-    UMGS_TRY(fr->tv.reserve(sizeof(uint32_t) * std::max<int64_t>(1, K)));
-    UMGS_TRY(fr->tk2.reserve(sizeof(uint32_t) * std::max<int64_t>(1, K)));
-    UMGS_TRY(fr->tv2.reserve(sizeof(uint32_t) * std::max<int64_t>(1, K)));
+    int64_t Kcap;
+    if (!fr->nosync) {
+        // read back the number of pairs (and the status word)
+        UMGS_TRY(cudaMemcpyAsync(ctx->pinned, fr->status.ptr, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+        UMGS_TRY(cudaStreamSynchronize(stream));
+        const int32_t st = (int32_t)(ctx->pinned[0] & 0xffffffff);
+        const int64_t K = NR > 0 ? (int64_t)(uint32_t)(ctx->pinned[0] >> 32) : 0;
+        if (st & 1) return fail(ctx, UMGS_ERR_INVALID_ARG, "a face index is out of range");
+        fr->num_keys = K;
+        Kcap = K;
+        UMGS_TRY(fr->tk.reserve(sizeof(uint32_t) * std::max<int64_t>(1, K)));
+        UMGS_TRY(fr->tv.reserve(sizeof(uint32_t) * std::max<int64_t>(1, K)));
+        UMGS_TRY(fr->tk2.reserve(sizeof(uint32_t) * std::max<int64_t>(1, K)));
+        UMGS_TRY(fr->tv2.reserve(sizeof(uint32_t) * std::max<int64_t>(1, K)));
+    } else {
+        // capture-safe: no host read-back; buffers were sized beforehand and an
+        // overflow is flagged in the status word (bit 2)
+        Kcap = fr->key_capacity;
+        fr->num_keys = -1;
+    }
     fr->ids = fr->tv.as<uint32_t>();
     fr->tkeys = fr->tk.as<uint32_t>();
-    if (K > 0) {
+    if (NR > 0) {
         StageTimer tm(ctx, UMGS_STAGE_SCATTER, stream);
         emit_pairs_kernel<<<grid_for(NR, 256), 256, 0, stream>>>(fr->bin.as<BinInfo>(), pv, fr->poff.as<uint32_t>(), NR,
                                                                  Ntot, ts, tiles_x, tiles_per_cam, fr->tk.as<uint32_t>(),
-                                                                 fr->tv.as<uint32_t>());
+                                                                 fr->tv.as<uint32_t>(), Kcap, fr->status.as<int32_t>());
         UMGS_TRY(cudaGetLastError());
     }
     {
         StageTimer tm(ctx, UMGS_STAGE_SORT, stream);
-        if (K > 0) {
+        if (Kcap > 0) {
             int bits = 1;
             while (((int64_t)1 << bits) < M) ++bits;
             uint32_t* rk = nullptr;
             uint32_t* rv = nullptr;
             UMGS_TRY(radix_sort_pairs(fr, fr->tk.as<uint32_t>(), fr->tv.as<uint32_t>(), fr->tk2.as<uint32_t>(),
-                                      fr->tv2.as<uint32_t>(), K, bits, &rk, &rv, stream));
+                                      fr->tv2.as<uint32_t>(), status_u + 1, Kcap, bits, &rk, &rv, stream));
             fr->tkeys = rk;
             fr->ids = rv;
         }
-        tile_ranges_kernel<<<grid_for(M + 1, 256), 256, 0, stream>>>(fr->tkeys, K, M, fr->tile_off.as<int64_t>());
+        tile_ranges_kernel<<<grid_for(M + 1, 256), 256, 0, stream>>>(fr->tkeys, status_u + 1, Kcap, M,
+                                                                     fr->tile_off.as<int64_t>());
         UMGS_TRY(cudaGetLastError());
     }
     UMGS_TRY(fr->last.reserve(sizeof(int32_t) * (int64_t)ncams * W * H));

@@ -24,6 +24,7 @@ BLEND_FULL, BLEND_DIRECT, BLEND_MSAA_ALL, BLEND_ENTITY_ALL = 0, 1, 2, 3
 F32, BF16 = 0, 1
 BIND_BBX, BIND_CENTER, BIND_NEAREST = 0, 1, 2
 RENDER_SAVE_BACKWARD = 1
+RENDER_MIXED = 2
 DEFORM_FRAME, DEFORM_LITERAL = 0, 1
 
 
@@ -63,7 +64,7 @@ class CMeshGrads(ctypes.Structure):
 
 class CRenderOpts(ctypes.Structure):
     _fields_ = [("tile_size", ctypes.c_int32), ("blend_mode", ctypes.c_int32), ("t_eps", ctypes.c_float),
-                ("bg", ctypes.c_float * 3), ("flags", ctypes.c_int32)]
+                ("bg", ctypes.c_float * 3), ("flags", ctypes.c_int32), ("sched", ctypes.c_int32)]
 
 
 _lib = None
@@ -89,6 +90,8 @@ def lib():
                                   ctypes.POINTER(CCamera), i32, ctypes.POINTER(CRenderOpts), vp, vp, vp]
         L.umgs_frame_counts.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]
         L.umgs_frame_lists.argtypes = [vp, vp, vp, vp, vp]
+        L.umgs_frame_evaluations.argtypes = [vp, ctypes.POINTER(i64), vp]
+        L.umgs_frame_evaluations.restype = ctypes.c_int
         L.umgs_ctx_sync.argtypes = [vp, vp]
         L.umgs_deform.argtypes = [vp, ctypes.POINTER(CGaussians), vp, vp, vp, vp, vp, i64, i64, i32, vp, vp, vp, vp]
         L.umgs_deform_vertex_table.argtypes = [vp, vp, i64, vp]
@@ -101,6 +104,17 @@ def lib():
         L.umgs_deform_noalloc.argtypes = [ctypes.POINTER(CGaussians), vp, vp, vp, vp, vp, i64, i64, i32, vp, vp,
                                           vp, vp]
         L.umgs_deform_noalloc.restype = ctypes.c_int
+        L.umgs_render_graph_create.argtypes = [vp, vp, ctypes.POINTER(CGaussians), ctypes.POINTER(CMesh), i32,
+                                               ctypes.POINTER(CCamera), i32, ctypes.POINTER(CRenderOpts), vp,
+                                               ctypes.c_float, ctypes.POINTER(vp), vp]
+        L.umgs_graph_launch.argtypes = [vp, vp]
+        L.umgs_graph_check.argtypes = [vp, vp]
+        L.umgs_graph_destroy.argtypes = [vp]
+        L.umgs_autotune.argtypes = [vp, ctypes.POINTER(CGaussians), ctypes.POINTER(CMesh), i32,
+                                    ctypes.POINTER(CCamera), i32, ctypes.POINTER(CRenderOpts), vp,
+                                    ctypes.POINTER(ctypes.c_double), vp]
+        for name in ("umgs_render_graph_create", "umgs_graph_launch", "umgs_graph_check", "umgs_autotune"):
+            getattr(L, name).restype = ctypes.c_int
         L.umgs_profile_enable.argtypes = [vp, i32]
         L.umgs_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
         for name in ("umgs_profile_enable", "umgs_profile_read", "umgs_ctx_create", "umgs_frame_create", "umgs_render", "umgs_frame_counts",
@@ -165,6 +179,12 @@ class Frame:
         k, t = ctypes.c_int64(), ctypes.c_int64()
         self.ctx.check(lib().umgs_frame_counts(self._h, ctypes.byref(k), ctypes.byref(t)), "umgs_frame_counts")
         return k.value, t.value
+
+    def evaluations(self):
+        """(pixel, fragment) evaluations of the last render (synchronises)."""
+        v = ctypes.c_int64()
+        self.ctx.check(lib().umgs_frame_evaluations(self._h, ctypes.byref(v), _stream()), "umgs_frame_evaluations")
+        return v.value
 
     def lists(self):
         """(tile_ptr int64 [T+1], ids int32 [K], dbits int32 [K] (uint32 bits)) on the device."""
@@ -250,10 +270,12 @@ def mesh_to_device(m, device="cuda") -> DevMesh:
                    _t(m.valpha, device), _t(m.falpha, device))
 
 
-def render_opts(tile_size=16, blend_mode=BLEND_FULL, t_eps=1e-4, bg=(0.0, 0.0, 0.0), save=False) -> CRenderOpts:
+def render_opts(tile_size=16, blend_mode=BLEND_FULL, t_eps=1e-4, bg=(0.0, 0.0, 0.0), save=False,
+                mixed=False, sched=0) -> CRenderOpts:
     o = CRenderOpts()
     lib().umgs_default_render_opts(ctypes.byref(o))
-    o.flags = RENDER_SAVE_BACKWARD if save else 0
+    o.sched = int(sched)
+    o.flags = (RENDER_SAVE_BACKWARD if save else 0) | (RENDER_MIXED if mixed else 0)
     o.tile_size = int(tile_size)
     o.blend_mode = int(blend_mode)
     o.t_eps = float(t_eps)
@@ -405,3 +427,48 @@ def render_backward(ctx: Context, frame: Frame, gaussians: DevGaussians | None, 
                                     _ptr(dL_drgbt.contiguous()), ctypes.byref(gg), cmg, _stream(stream))
     ctx.check(st, "umgs_render_backward")
     return out
+
+
+class Graph:
+    """umgs_render_graph_*: a render captured in a CUDA graph (see include/umgs.h)."""
+
+    def __init__(self, ctx: Context, frame: Frame, gaussians, meshes, cameras, opts, out, key_headroom=1.25,
+                 stream=None):
+        self.ctx, self.frame, self.out = ctx, frame, out
+        self._keep = (gaussians, meshes)
+        self._cams = (CCamera * len(cameras))(*[camera_struct(c) for c in cameras])
+        self._cm = (CMesh * max(1, len(meshes)))(*[m.c() for m in meshes]) if meshes else None
+        self._cg = gaussians.c() if gaussians is not None else None
+        self._opts = opts
+        self._h = ctypes.c_void_p()
+        st = lib().umgs_render_graph_create(ctx._h, frame._h, ctypes.byref(self._cg) if self._cg else None, self._cm,
+                                            len(meshes), self._cams, len(cameras), ctypes.byref(opts), _ptr(out),
+                                            float(key_headroom), ctypes.byref(self._h), _stream(stream))
+        ctx.check(st, "umgs_render_graph_create")
+
+    def launch(self, stream=None):
+        self.ctx.check(lib().umgs_graph_launch(self._h, _stream(stream)), "umgs_graph_launch")
+
+    def check(self, stream=None):
+        self.ctx.check(lib().umgs_graph_check(self._h, _stream(stream)), "umgs_graph_check")
+
+    def __del__(self):
+        try:
+            if self._h:
+                lib().umgs_graph_destroy(self._h)
+        except Exception:
+            pass
+
+
+def autotune(ctx: Context, gaussians, meshes, cameras, opts: CRenderOpts, out, stream=None):
+    """umgs_autotune: returns (best opts, ms per render)."""
+    cams = (CCamera * len(cameras))(*[camera_struct(c) for c in cameras])
+    cm = (CMesh * max(1, len(meshes)))(*[m.c() for m in meshes]) if meshes else None
+    cg = gaussians.c() if gaussians is not None else None
+    o = CRenderOpts()
+    ctypes.memmove(ctypes.byref(o), ctypes.byref(opts), ctypes.sizeof(CRenderOpts))
+    ms = ctypes.c_double()
+    st = lib().umgs_autotune(ctx._h, ctypes.byref(cg) if cg else None, cm, len(meshes), cams, len(cameras),
+                             ctypes.byref(o), _ptr(out), ctypes.byref(ms), _stream(stream))
+    ctx.check(st, "umgs_autotune")
+    return o, ms.value

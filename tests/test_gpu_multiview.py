@@ -1,0 +1,108 @@
+"""Multi-view form: persistent compositor, CUDA-graph capture and autotuning.
+
+The schedule and the graph change how the work is launched, not what is
+computed: their outputs must equal the one-CTA-per-tile render bit for bit,
+and that render matches the oracle (keys exact, images within 2e-4)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2601_19233_gb300 import scenes as S
+from tests.test_gpu_render import check_image, check_lists, ctx  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+
+def _clustered(seed=2024, n=3000, cams=6, size=96):
+    """A small stand-in for the 64-view orbit workload: 70% of the Gaussians
+    in 3 blobs (uneven tile load), a torus, cameras on an orbit."""
+    rng = np.random.default_rng(seed)
+    nb = int(0.7 * n)
+    c = rng.uniform(-0.5, 0.5, size=(3, 3))
+    blob = c[rng.integers(0, 3, size=nb)] + rng.normal(0, 0.15, size=(nb, 3))
+    means = np.concatenate([blob, rng.uniform(-1, 1, size=(n - nb, 3))]).astype(np.float32)
+    g = S.make_gaussians(rng, means, -3.5, 3)
+    V, F = S.torus(40, 20)
+    vcol = rng.uniform(0, 1, size=(len(V), 3)).astype(np.float32)
+    fa = np.ones(len(F), np.float32)
+    m = rng.uniform(size=len(F)) < 0.3
+    fa[m] = rng.uniform(0.2, 0.8, size=int(m.sum())).astype(np.float32)
+    fx = S.focal_from_fov(size, 60.0)
+    camsl = S.orbit_cameras(cams, 3.0, size, size, fx, lambda k: 20.0 * math.sin(2 * math.pi * k / 16))
+    return S.Scene(g, [S.Mesh(V, F, vcol, None, fa)], camsl, tile=16)
+
+
+def _dev(sc):
+    from paper_2601_19233_gb300 import umgs
+    return umgs.gaussians_to_device(sc.gaussians), [umgs.mesh_to_device(m) for m in sc.meshes]
+
+
+def test_persistent_schedules_bit_identical(ctx):
+    from paper_2601_19233_gb300 import umgs
+    sc = _clustered()
+    g, ms = _dev(sc)
+    fr = umgs.Frame(ctx)
+    base = umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(16), frame=fr).cpu().numpy()
+    check_lists(sc, fr, 16)
+    check_image(sc, base)
+    for ts in (8, 16, 32):
+        ref = umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(ts)).cpu().numpy()
+        for sched in (1, 2, 4):
+            out = umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(ts, sched=sched)).cpu().numpy()
+            assert np.array_equal(out, ref), (ts, sched)
+        assert np.array_equal(ref, base)
+
+
+def test_graph_replay_matches_render(ctx):
+    from paper_2601_19233_gb300 import umgs
+    sc = _clustered(7)
+    g, ms = _dev(sc)
+    opts = umgs.render_opts(16, sched=2)
+    ref = umgs.render(ctx, g, ms, sc.cameras, opts).clone()
+    out = torch.zeros_like(ref)
+    fr = umgs.Frame(ctx)
+    gr = umgs.Graph(ctx, fr, g, ms, sc.cameras, opts, out)
+    for _ in range(3):
+        out.zero_()
+        gr.launch()
+        gr.check()
+        assert torch.equal(out, ref)
+    # new input values, same pointers: the replay follows them
+    g.means.add_(0.01)
+    ref2 = umgs.render(ctx, g, ms, sc.cameras, opts)
+    gr.launch()
+    gr.check()
+    assert torch.equal(out, ref2)
+    assert not torch.equal(ref2, ref)
+
+
+def test_graph_capacity_overflow_is_reported(ctx):
+    from paper_2601_19233_gb300 import umgs
+    sc = _clustered(9, n=1500)
+    g, ms = _dev(sc)
+    opts = umgs.render_opts(16)
+    out = torch.zeros((len(sc.cameras), 96, 96, 4), device="cuda")
+    fr = umgs.Frame(ctx)
+    gr = umgs.Graph(ctx, fr, g, ms, sc.cameras, opts, out, key_headroom=1.0)
+    gr.launch()
+    gr.check()
+    g.scales.mul_(6.0)  # much larger footprints: more pairs than the captured capacity
+    gr.launch()
+    with pytest.raises(umgs.UmgsError) as e:
+        gr.check()
+    assert e.value.status == 3
+
+
+def test_autotune_picks_a_valid_config(ctx):
+    from paper_2601_19233_gb300 import umgs
+    sc = _clustered(11)
+    g, ms = _dev(sc)
+    out = torch.zeros((len(sc.cameras), 96, 96, 4), device="cuda")
+    best, ms_per = umgs.autotune(ctx, g, ms, sc.cameras, umgs.render_opts(16), out)
+    assert best.tile_size in (8, 16, 32) and best.sched in (0, 1, 2, 4)
+    assert ms_per > 0
+    ref = umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(16)).cpu().numpy()
+    got = umgs.render(ctx, g, ms, sc.cameras, best).cpu().numpy()
+    assert np.array_equal(got, ref)

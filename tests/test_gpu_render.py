@@ -150,3 +150,14 @@ def test_invalid_arguments_rejected(ctx):
     with pytest.raises(umgs.UmgsError) as e:
         umgs.render(ctx, g, [umgs.mesh_to_device(bad)], sc.cameras)
     assert e.value.status == 1
+
+
+def test_evaluation_count_matches_oracle(ctx):
+    sc = S.config0()
+    out, fr = gpu_render(ctx, sc)
+    total, per_pix = R.evaluation_count(sc)
+    ref = R.render_image(sc)
+    got = fr.evaluations()
+    # termination ties may move the cut by a few entries on a tie pixel
+    assert abs(got - total) <= int(ref["tie"].sum()) * int(per_pix.max())
+    assert total > 10000
