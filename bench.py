@@ -17,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -42,6 +43,7 @@ def parse():
     p.add_argument("--impl", default="umgs", choices=["umgs", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--n-gauss", type=int, default=1_000_000)
+    p.add_argument("--no-forms", action="store_true", help="skip the multi-view / differentiable / mixed forms")
     return p.parse_args()
 
 
@@ -262,6 +264,8 @@ def run_umgs(args, rank, world, local_rank):
         "roofline": roof,
         "clocks": clk,
     }
+    if not args.no_forms:
+        res["forms"] = run_forms(ctx, dev, max(3, K // 6))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(sc, disp, face.cpu().numpy(), bary.cpu().numpy())
     if rank == 0:
@@ -314,6 +318,104 @@ def roofline(stages, nkeys, n, sc, clk, evals):
     ach = b / t / 1e9 if b else None
     return {"bound": "hbm", "stage": dom, "achieved": ach and round(ach, 1), "peak": hbm, "unit": "GB/s",
             "frac": ach and round(ach / hbm, 4), "traffic": None, "peak_source": hsrc, "hbm_stages": hbm_stages}
+
+
+# ----------------------------------------------------------------------------
+# the three other forms, each next to the plain fp32 forward on the same GPU
+
+def _time(fn, steps, warm=2):
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def run_forms(ctx, dev, steps):
+    import torch
+    from paper_2601_19233_gb300 import scenes, umgs
+    forms = {}
+    # config 2: 64 orbit views of 800x800, clustered Gaussians (uneven tile load)
+    sc = scenes.config2()
+    g = umgs.gaussians_to_device(sc.gaussians, dev)
+    ms = [umgs.mesh_to_device(m, dev) for m in sc.meshes]
+    nv = len(sc.cameras)
+    out = torch.empty((nv, 800, 800, 4), device=dev)
+    plain = umgs.render_opts(16)
+    fr = umgs.Frame(ctx)
+    t_plain = _time(lambda: umgs.render(ctx, g, ms, sc.cameras, plain, out=out, frame=fr), steps)
+    evals_plain = fr.evaluations()
+    best, t_tune = umgs.autotune(ctx, g, ms, sc.cameras, plain, out)
+    fr2 = umgs.Frame(ctx)
+    gr = umgs.Graph(ctx, fr2, g, ms, sc.cameras, best, out)
+    t_graph = _time(lambda: gr.launch(), steps)
+    gr.check()
+    forms["multiview_64x800"] = {
+        "workload": "64 orbit views 800x800, 500k Gaussians SH3 (70% in 3 blobs) + 100k-face torus",
+        "plain_views_per_s": round(nv * 1e3 / t_plain, 1), "plain_ms": round(t_plain, 3),
+        "graph_views_per_s": round(nv * 1e3 / t_graph, 1), "graph_ms": round(t_graph, 3),
+        "autotuned": {"tile_size": best.tile_size, "sched": best.sched, "ms": round(t_tune, 3)},
+        "keys": int(fr.counts()[0]), "evaluations": int(evals_plain)}
+    del gr, fr, fr2, out, g, ms
+    torch.cuda.empty_cache()
+    # config 3: 8 views of 512x512, forward vs forward+backward (L2 loss to a
+    # render of a perturbed copy of the scene)
+    sc = scenes.config3()
+    rng = np.random.default_rng(7)
+    pert = scenes.config3()
+    pert.gaussians.means = (pert.gaussians.means + rng.normal(0, 0.01, pert.gaussians.means.shape)).astype(np.float32)
+    pert.gaussians.sh = (pert.gaussians.sh + rng.normal(0, 0.05, pert.gaussians.sh.shape)).astype(np.float32)
+    g = umgs.gaussians_to_device(sc.gaussians, dev)
+    ms = [umgs.mesh_to_device(m, dev) for m in sc.meshes]
+    gp = umgs.gaussians_to_device(pert.gaussians, dev)
+    nv = len(sc.cameras)
+    target = umgs.render(ctx, gp, ms, sc.cameras, umgs.render_opts(16)).clone()
+    out = torch.empty_like(target)
+    fr = umgs.Frame(ctx)
+    t_f = _time(lambda: umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(16), out=out, frame=fr), steps)
+    so = umgs.render_opts(16, save=True)
+
+    def fb():
+        umgs.render(ctx, g, ms, sc.cameras, so, out=out, frame=fr)
+        dl = (2.0 / out.numel()) * (out - target)
+        return umgs.render_backward(ctx, fr, g, ms, dl)
+    t_fb = _time(fb, steps)
+    forms["differentiable_8x512"] = {
+        "workload": "8 orbit views 512x512, 300k Gaussians SH3 + 50k-face torus, L2 loss to a perturbed-scene render",
+        "fwd_views_per_s": round(nv * 1e3 / t_f, 1), "fwd_ms": round(t_f, 3),
+        "fwd_bwd_views_per_s": round(nv * 1e3 / t_fb, 1), "fwd_bwd_ms": round(t_fb, 3)}
+    del g, ms, gp, target, out, fr
+    torch.cuda.empty_cache()
+    # config 4: 4K, 6M Gaussians + 2M triangles, fp32 vs bf16 SH + fp16 records
+    sc = scenes.config4()
+    g32 = umgs.gaussians_to_device(sc.gaussians, dev)
+    g16 = umgs.gaussians_to_device(sc.gaussians, dev, sh_dtype=torch.bfloat16)
+    ms = [umgs.mesh_to_device(m, dev) for m in sc.meshes]
+    out32 = torch.empty((1, 2160, 3840, 4), device=dev)
+    out16 = torch.empty_like(out32)
+    fr = umgs.Frame(ctx)
+    t32 = _time(lambda: umgs.render(ctx, g32, ms, sc.cameras, umgs.render_opts(16), out=out32, frame=fr), steps)
+    keys4 = fr.counts()[0]
+    t16 = _time(lambda: umgs.render(ctx, g16, ms, sc.cameras, umgs.render_opts(16, mixed=True), out=out16, frame=fr),
+                steps)
+    d = (out16[..., :3] - out32[..., :3]).abs().flatten()
+    mse = float(((out16[..., :3] - out32[..., :3]) ** 2).mean())
+    forms["mixed_4k"] = {
+        "workload": "3840x2160, 6M Gaussians SH3 + 2M-face torus (30% transparent)",
+        "fp32_frames_per_s": round(1e3 / t32, 2), "fp32_ms": round(t32, 3),
+        "mixed_frames_per_s": round(1e3 / t16, 2), "mixed_ms": round(t16, 3), "keys": int(keys4),
+        "mixed_vs_fp32": {"max_abs": float(d.max()), "p99_9": float(torch.quantile(d[::7].float(), 0.999)),
+                          "psnr_db": round(10 * math.log10(1.0 / max(mse, 1e-20)), 2)}}
+    del g32, g16, ms, out32, out16, fr
+    torch.cuda.empty_cache()
+    return forms
 
 
 # ----------------------------------------------------------------------------

@@ -505,6 +505,8 @@ __global__ void tile_ranges_kernel(const uint32_t* __restrict__ tk, const uint32
 // compositor
 
 constexpr int kBatch = 256;
+// records staged per batch: 256, or 128 for 32x32 tiles (32 warps of lists)
+template <int TS> struct BatchOf { static constexpr int value = TS == 32 ? 128 : 256; };
 
 struct PixelState {
     float C[3];
@@ -522,6 +524,7 @@ struct PixelState {
 template <int TS, bool SAVE>
 __device__ __forceinline__ void composite_tile(
     int tile, float4 (*__restrict__ s_rec)[10], uint32_t* __restrict__ s_id, uint32_t* __restrict__ s_wmask,
+    uint8_t* __restrict__ s_list,
     const uint32_t* __restrict__ ids, const int64_t* __restrict__ off, const GRec* __restrict__ grec,
     const GRec16* __restrict__ grec16, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
     int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, int mode, float4* __restrict__ out, int32_t* __restrict__ out_last,
@@ -557,9 +560,10 @@ __device__ __forceinline__ void composite_tile(
     const int warp = threadIdx.x >> 5;
     const int tile_y0 = ty * TS;
     const float pxf = (float)px, pyf = (float)py;
-    for (int64_t b0 = beg; b0 < end; b0 += kBatch) {
+    constexpr int NB = BatchOf<TS>::value;
+    for (int64_t b0 = beg; b0 < end; b0 += NB) {
         if (__syncthreads_count(done) == NT) break;
-        const int n = (int)min((int64_t)kBatch, end - b0);
+        const int n = (int)min((int64_t)NB, end - b0);
         for (int k = threadIdx.x; k < n; k += NT) {
             const uint32_t id = ids[b0 + k];
             s_id[k] = id;
@@ -589,19 +593,56 @@ __device__ __forceinline__ void composite_tile(
                 rx = tr.rx;
                 ry = tr.ry;
             }
-            // warps whose rows intersect the record's rows
-            const int r0 = max((int)(ry & 0xffff) - tile_y0, 0), r1 = min((int)(ry >> 16) - tile_y0, TS - 1);
+            // pixel box that can hold a fragment of this record: the rect, and for
+            // a Gaussian also the box of its alpha >= 1/255 ellipse (widened so
+            // rounding can never cut a fragment) -> mask of the warps whose
+            // pixel block meets it
+            int bx0 = (int)(rx & 0xffff), bx1 = (int)(rx >> 16), by0 = (int)(ry & 0xffff), by1 = (int)(ry >> 16);
+            if (id < Ng) {
+                const float4 a = s_rec[k][0], b = s_rec[k][1];
+                const float o = b.y;
+                // conic Q = [[A B][B C]] from the base-2 scaled record
+                const float A = -2.f * 0.6931471805599453f * a.z, B = -0.6931471805599453f * a.w,
+                            Cq = -2.f * 0.6931471805599453f * b.x;
+                const float det = A * Cq - B * B;
+                const float L = __logf(255.f * o);
+                if (!(L > 0.f) || !(det > 0.f)) {
+                    bx0 = 1; bx1 = 0;  // opacity below 1/255: no fragment anywhere
+                } else {
+                    const float ex = sqrtf(2.f * L * Cq / det) * 1.01f + 0.5f;
+                    const float ey = sqrtf(2.f * L * A / det) * 1.01f + 0.5f;
+                    bx0 = max(bx0, (int)floorf(a.x - ex - 0.5f));
+                    bx1 = min(bx1, (int)ceilf(a.x + ex - 0.5f));
+                    by0 = max(by0, (int)floorf(a.y - ey - 0.5f));
+                    by1 = min(by1, (int)ceilf(a.y + ey - 0.5f));
+                }
+            }
             uint32_t wm = 0;
-            if (r0 <= r1) {
-                const int w0 = (r0 * TS) >> 5, w1 = (r1 * TS + TS - 1) >> 5;
-                wm = ((2u << w1) - 1u) & ~((1u << w0) - 1u);
+            const int tile_x0 = tx * TS;
+            if (bx0 <= bx1 && bx0 <= tile_x0 + TS - 1 && bx1 >= tile_x0) {
+                const int r0 = max(by0 - tile_y0, 0), r1 = min(by1 - tile_y0, TS - 1);
+                if (r0 <= r1) {
+                    const int w0 = (r0 * TS) >> 5, w1 = (r1 * TS + TS - 1) >> 5;
+                    wm = ((2u << w1) - 1u) & ~((1u << w0) - 1u);
+                }
             }
             s_wmask[k] = wm;
         }
         __syncthreads();
         if (__any_sync(0xffffffffu, !done)) {
-            for (int k = 0; k < n; ++k) {
-                if (!((s_wmask[k] >> warp) & 1u)) continue;  // uniform across the warp
+            // this warp's records of the batch, in order
+            uint8_t* lst = s_list + warp * BatchOf<TS>::value;
+            int cnt = 0;
+            const int lane = threadIdx.x & 31;
+            for (int c0 = 0; c0 < n; c0 += 32) {
+                const bool mine = c0 + lane < n && ((s_wmask[c0 + lane] >> warp) & 1u);
+                const unsigned bal = __ballot_sync(0xffffffffu, mine);
+                if (mine) lst[cnt + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)(c0 + lane);
+                cnt += __popc(bal);
+            }
+            __syncwarp();
+            for (int li = 0; li < cnt; ++li) {
+                const int k = lst[li];
                 if (done) continue;
                 const uint32_t id = s_id[k];
                 if (id < Ng) {
@@ -734,10 +775,12 @@ __global__ void __launch_bounds__(TS * TS) composite_kernel(
     int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, int mode, float4* __restrict__ out, int32_t* __restrict__ out_last,
     float* __restrict__ out_tfin, int32_t* __restrict__ out_ntri, float4* __restrict__ stack, int cap,
     int64_t npix, int32_t* __restrict__ need, unsigned long long* __restrict__ eval_count) {
-    __shared__ float4 s_rec[kBatch][10];
-    __shared__ uint32_t s_id[kBatch];
-    __shared__ uint32_t s_wmask[kBatch];
-    composite_tile<TS, SAVE>(blockIdx.x, s_rec, s_id, s_wmask, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, mode, out, out_last, out_tfin, out_ntri, stack, cap, npix, need, eval_count);
+    constexpr int NB = BatchOf<TS>::value;
+    __shared__ float4 s_rec[NB][10];
+    __shared__ uint32_t s_id[NB];
+    __shared__ uint32_t s_wmask[NB];
+    __shared__ uint8_t s_list[(TS * TS / 32) * NB];
+    composite_tile<TS, SAVE>(blockIdx.x, s_rec, s_id, s_wmask, s_list, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, mode, out, out_last, out_tfin, out_ntri, stack, cap, npix, need, eval_count);
 }
 
 // persistent launch: resident CTAs take tiles from an atomic queue in the
@@ -750,9 +793,11 @@ __global__ void __launch_bounds__(TS * TS) composite_persistent_kernel(
     int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, int mode, float4* __restrict__ out, int32_t* __restrict__ out_last,
     float* __restrict__ out_tfin, int32_t* __restrict__ out_ntri, float4* __restrict__ stack, int cap,
     int64_t npix, int32_t* __restrict__ need, unsigned long long* __restrict__ eval_count) {
-    __shared__ float4 s_rec[kBatch][10];
-    __shared__ uint32_t s_id[kBatch];
-    __shared__ uint32_t s_wmask[kBatch];
+    constexpr int NB = BatchOf<TS>::value;
+    __shared__ float4 s_rec[NB][10];
+    __shared__ uint32_t s_id[NB];
+    __shared__ uint32_t s_wmask[NB];
+    __shared__ uint8_t s_list[(TS * TS / 32) * NB];
     __shared__ unsigned s_next;
     while (true) {
         if (threadIdx.x == 0) s_next = atomicAdd(work, 1u);
@@ -760,7 +805,7 @@ __global__ void __launch_bounds__(TS * TS) composite_persistent_kernel(
         const unsigned k = s_next;
         __syncthreads();
         if ((int64_t)k >= M) break;
-        composite_tile<TS, SAVE>((int)order[k], s_rec, s_id, s_wmask, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, mode, out, out_last, out_tfin, out_ntri, stack, cap, npix, need, eval_count);
+        composite_tile<TS, SAVE>((int)order[k], s_rec, s_id, s_wmask, s_list, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, mode, out, out_last, out_tfin, out_ntri, stack, cap, npix, need, eval_count);
         __syncthreads();
     }
 }
