@@ -20,7 +20,9 @@
 //                (Gaussian: u, v, conic, opacity, RGB; triangle: unsnapped
 //                screen positions, depths, vertex colours and alphas through
 //                the perspective-correct interpolation) are reduced across
-//                the warp and added with one atomic per warp.
+//                the warp (recursive halving, one component per lane) and
+//                added to shared-memory accumulators of the batch, which are
+//                flushed with one global atomic per record and component.
 // project_gaussians_bwd / setup_triangles_bwd
 //                chain rule from the records to the inputs (EWA projection,
 //                covariance from quaternion and scale, SH colour), summed
@@ -31,13 +33,29 @@
 
 namespace umgs {
 
-constexpr int kBatchB = 256;
+constexpr int kBatchB = 128;  // records per batch (shared-memory gradient accumulators beside them)
 constexpr float kLn2 = 0.6931471805599453f;
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Warp sum of V values per lane (V = 16 or 32) by recursive halving: at each
+// step every lane keeps one half of its values, sends the other half to its
+// partner and adds what it receives, so V - 1 shuffles (plus one for V = 16)
+// replace the 5 V of one butterfly per value.  On return v[0] of lane L holds
+// the warp sum of value L (V = 32) or of value L >> 1 (V = 16; both lanes of a
+// pair hold it).
+template <int V>
+__device__ __forceinline__ void warp_sum_transpose(float (&v)[V], int lane) {
+    static_assert(V == 16 || V == 32, "V");
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int half = V / 2, o = 16; half >= 1; half >>= 1, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < half; ++i) {
+            const float send = up ? v[i] : v[i + half];
+            const float keep = up ? v[i + half] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    if (V == 16) v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
 template <int TS>
@@ -48,8 +66,13 @@ __global__ void __launch_bounds__(TS * TS) composite_bwd_kernel(
     const float* __restrict__ tfin, const int32_t* __restrict__ ntri, const float4* __restrict__ stack, int64_t npix,
     float* __restrict__ ggrad, float* __restrict__ tgrad) {
     constexpr int NT = TS * TS;
+    constexpr int NW = NT / 32;
     __shared__ float4 s_rec[kBatchB][10];
     __shared__ uint32_t s_id[kBatchB];
+    __shared__ uint32_t s_wmask[kBatchB];
+    __shared__ float s_acc[kBatchB][22];     // per record gradient (Gaussian: 9, triangle: 21)
+    __shared__ uint8_t s_list[NW * kBatchB];
+    __shared__ int s_wmax[NW];
     __shared__ int s_max;
     const int tile = blockIdx.x;
     const int cam = tile / tiles_per_cam;
@@ -77,11 +100,20 @@ __global__ void __launch_bounds__(TS * TS) composite_bwd_kernel(
     }
     float Uj[4] = {0.f, 0.f, 0.f, 0.f};
     bool in_ent = false;
+    const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) s_max = 0;
     __syncthreads();
     atomicMax(&s_max, nlast);
+    {
+        int wm = nlast;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) wm = max(wm, __shfl_xor_sync(0xffffffffu, wm, o));
+        if (lane == 0) s_wmax[warp] = wm;
+    }
     __syncthreads();
     const int maxlast = s_max;
+    const int wmaxlast = s_wmax[warp];
+    const int tile_y0 = ty * TS, tile_x0 = tx * TS;
 
     for (int bend = maxlast; bend > 0; bend -= kBatchB) {
         const int b0 = max(0, bend - kBatchB);
@@ -90,17 +122,61 @@ __global__ void __launch_bounds__(TS * TS) composite_bwd_kernel(
         for (int k = threadIdx.x; k < n; k += NT) {
             const uint32_t id = ids[beg + b0 + k];
             s_id[k] = id;
+            uint32_t rx, ry;
+            int bx0, bx1, by0, by1;
             if (id < Ng) {
                 const float4* src = reinterpret_cast<const float4*>(G + id);
-                s_rec[k][0] = src[0]; s_rec[k][1] = src[1]; s_rec[k][2] = src[2];
+                const float4 a = src[0], q1 = src[1], c = src[2];
+                s_rec[k][0] = a; s_rec[k][1] = q1; s_rec[k][2] = c;
+                rx = __float_as_uint(c.y);
+                ry = __float_as_uint(c.z);
+                bx0 = (int)(rx & 0xffff); bx1 = (int)(rx >> 16); by0 = (int)(ry & 0xffff); by1 = (int)(ry >> 16);
+                // box of the alpha >= 1/255 ellipse, widened (conservative), as in the forward
+                const float A = -2.f * kLn2 * a.z, B = -kLn2 * a.w, Cq = -2.f * kLn2 * q1.x;
+                const float det = A * Cq - B * B;
+                const float L = __logf(255.f * q1.y);
+                if (!(L > 0.f) || !(det > 0.f)) {
+                    bx0 = 1; bx1 = 0;
+                } else {
+                    const float ex = sqrtf(2.f * L * Cq / det) * 1.01f + 0.5f;
+                    const float ey = sqrtf(2.f * L * A / det) * 1.01f + 0.5f;
+                    bx0 = max(bx0, (int)floorf(a.x - ex - 0.5f));
+                    bx1 = min(bx1, (int)ceilf(a.x + ex - 0.5f));
+                    by0 = max(by0, (int)floorf(a.y - ey - 0.5f));
+                    by1 = min(by1, (int)ceilf(a.y + ey - 0.5f));
+                }
             } else {
                 const float4* src = reinterpret_cast<const float4*>(TR + (id - Ng));
 #pragma unroll
                 for (int q = 0; q < 10; ++q) s_rec[k][q] = src[q];
+                const TRec& tr = *reinterpret_cast<const TRec*>(&s_rec[k][0]);
+                bx0 = (int)(tr.rx & 0xffff); bx1 = (int)(tr.rx >> 16); by0 = (int)(tr.ry & 0xffff); by1 = (int)(tr.ry >> 16);
             }
+            uint32_t wm = 0;
+            if (bx0 <= bx1 && bx0 <= tile_x0 + TS - 1 && bx1 >= tile_x0) {
+                const int r0 = max(by0 - tile_y0, 0), r1 = min(by1 - tile_y0, TS - 1);
+                if (r0 <= r1) {
+                    const int w0 = (r0 * TS) >> 5, w1 = (r1 * TS + TS - 1) >> 5;
+                    wm = ((2u << w1) - 1u) & ~((1u << w0) - 1u);
+                }
+            }
+            s_wmask[k] = wm;
+#pragma unroll
+            for (int e = 0; e < 22; ++e) s_acc[k][e] = 0.f;
         }
         __syncthreads();
-        for (int k = n - 1; k >= 0; --k) {
+        // this warp's records of the batch (in order; replayed back to front)
+        uint8_t* lst = s_list + warp * kBatchB;
+        int cnt = 0;
+        for (int c0 = 0; c0 < n; c0 += 32) {
+            const bool mine = c0 + lane < n && b0 + c0 + lane < wmaxlast && ((s_wmask[c0 + lane] >> warp) & 1u);
+            const unsigned bal = __ballot_sync(0xffffffffu, mine);
+            if (mine) lst[cnt + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)(c0 + lane);
+            cnt += __popc(bal);
+        }
+        __syncwarp();
+        for (int li = cnt - 1; li >= 0; --li) {
+            const int k = lst[li];
             const int pos = b0 + k;
             const bool active = inside && pos < nlast;
             const uint32_t id = s_id[k];
@@ -116,7 +192,9 @@ __global__ void __launch_bounds__(TS * TS) composite_bwd_kernel(
                 const float ag = __fmul_rn(q1.y, Gv);
                 const float alpha = fminf(kAlphaMax, ag);
                 const bool contrib = active && inrect && alpha >= kAlphaMin;
-                float v[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+                float v[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) v[e] = 0.f;
                 if (contrib) {
                     if (in_ent) { U = 0.25f * ((Uj[0] + Uj[1]) + (Uj[2] + Uj[3])); in_ent = false; }
                     const float Tk = T / (1.f - alpha);
@@ -138,14 +216,8 @@ __global__ void __launch_bounds__(TS * TS) composite_bwd_kernel(
                     }
                 }
                 if (__any_sync(0xffffffffu, contrib)) {
-#pragma unroll
-                    for (int e = 0; e < 9; ++e) v[e] = warp_sum(v[e]);
-                    if (lane == 0) {
-                        float* dst = ggrad + ((int64_t)cam * Ng + id) * 12;
-#pragma unroll
-                        for (int e = 0; e < 9; ++e)
-                            if (v[e] != 0.f) atomicAdd(dst + e, v[e]);
-                    }
+                    warp_sum_transpose<16>(v, lane);
+                    if ((lane & 1) == 0 && lane < 18 && v[0] != 0.f) atomicAdd(&s_acc[k][lane >> 1], v[0]);
                 }
             } else {
                 // ---- triangle fragment
@@ -165,9 +237,9 @@ __global__ void __launch_bounds__(TS * TS) composite_bwd_kernel(
                     }
                 }
                 const bool cover = mask != 0;
-                float v[21];
+                float v[32];
 #pragma unroll
-                for (int e = 0; e < 21; ++e) v[e] = 0.f;
+                for (int e = 0; e < 32; ++e) v[e] = 0.f;
                 if (cover) {
                     if (!in_ent) { Uj[0] = Uj[1] = Uj[2] = Uj[3] = U; in_ent = true; }
                     // replayed coverage equals the forward's, so sp > 0 here; the
@@ -254,15 +326,25 @@ __global__ void __launch_bounds__(TS * TS) composite_bwd_kernel(
                     }
                 }
                 if (__any_sync(0xffffffffu, cover)) {
-#pragma unroll
-                    for (int e = 0; e < 21; ++e) v[e] = warp_sum(v[e]);
-                    if (lane == 0) {
-                        float* dst = tgrad + ((int64_t)cam * Nt + (id - Ng)) * 24;
-#pragma unroll
-                        for (int e = 0; e < 21; ++e)
-                            if (v[e] != 0.f) atomicAdd(dst + e, v[e]);
-                    }
+                    warp_sum_transpose<32>(v, lane);
+                    if (lane < 21 && v[0] != 0.f) atomicAdd(&s_acc[k][lane], v[0]);
                 }
+            }
+        }
+        __syncthreads();
+        // one global atomic per (record, component) of this tile's batch
+        for (int k = threadIdx.x; k < n; k += NT) {
+            const uint32_t id = s_id[k];
+            if (id < Ng) {
+                float* dst = ggrad + ((int64_t)cam * Ng + id) * 12;
+#pragma unroll
+                for (int e = 0; e < 9; ++e)
+                    if (s_acc[k][e] != 0.f) atomicAdd(dst + e, s_acc[k][e]);
+            } else {
+                float* dst = tgrad + ((int64_t)cam * Nt + (id - Ng)) * 24;
+#pragma unroll
+                for (int e = 0; e < 21; ++e)
+                    if (s_acc[k][e] != 0.f) atomicAdd(dst + e, s_acc[k][e]);
             }
         }
     }
@@ -270,23 +352,23 @@ __global__ void __launch_bounds__(TS * TS) composite_bwd_kernel(
 
 // ---- records -> Gaussian parameters ---------------------------------------
 
-__device__ void sh_grad(const void* sh, int dtype, int deg, int64_t i, float dx, float dy, float dz, const float drgb[3],
-                        float* __restrict__ dsh, float ddir[3]) {
-    const int K = (deg + 1) * (deg + 1);
-    const int64_t base = i * (int64_t)K * 3;
-    const float nrm = sqrtf(dx * dx + dy * dy + dz * dz);
-    const float inv = 1.f / nrm;
-    const float x = dx * inv, y = dy * inv, z = dz * inv;
-    float Y[16], gx[16], gy[16], gz[16];
-    for (int k = 0; k < 16; ++k) { Y[k] = 0.f; gx[k] = gy[k] = gz[k] = 0.f; }
+// Real SH basis (Condon-Shortley phase, index l*l + (m + l)) of the unit
+// direction (x, y, z) and its partial derivatives with respect to x, y, z.
+template <int DEG>
+__device__ __forceinline__ void sh_basis_grad(float x, float y, float z, float (&Y)[(DEG + 1) * (DEG + 1)],
+                                              float (&gx)[(DEG + 1) * (DEG + 1)], float (&gy)[(DEG + 1) * (DEG + 1)],
+                                              float (&gz)[(DEG + 1) * (DEG + 1)]) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+#pragma unroll
+    for (int k = 0; k < K; ++k) { Y[k] = 0.f; gx[k] = gy[k] = gz[k] = 0.f; }
     Y[0] = 0.28209479177387814f;
-    const float c1 = 0.4886025119029199f;
-    if (deg > 0) {
+    if constexpr (DEG > 0) {
+        const float c1 = 0.4886025119029199f;
         Y[1] = -c1 * y; gy[1] = -c1;
         Y[2] = c1 * z;  gz[2] = c1;
         Y[3] = -c1 * x; gx[3] = -c1;
     }
-    if (deg > 1) {
+    if constexpr (DEG > 1) {
         const float a = 1.0925484305920792f, b = 0.31539156525252005f, c = 0.5462742152960396f;
         const float xx = x * x, yy = y * y, zz = z * z;
         Y[4] = a * x * y;   gx[4] = a * y; gy[4] = a * x;
@@ -294,7 +376,7 @@ __device__ void sh_grad(const void* sh, int dtype, int deg, int64_t i, float dx,
         Y[6] = b * (2.f * zz - xx - yy); gx[6] = -2.f * b * x; gy[6] = -2.f * b * y; gz[6] = 4.f * b * z;
         Y[7] = -a * x * z;  gx[7] = -a * z; gz[7] = -a * x;
         Y[8] = c * (xx - yy); gx[8] = 2.f * c * x; gy[8] = -2.f * c * y;
-        if (deg > 2) {
+        if constexpr (DEG > 2) {
             const float d0 = -0.5900435899266435f, d1 = 2.890611442640554f, d2 = -0.4570457994644658f,
                         d3 = 0.3731763325901154f, d5 = 1.445305721320277f;
             Y[9] = d0 * y * (3.f * xx - yy);  gx[9] = 6.f * d0 * x * y; gy[9] = d0 * (3.f * xx - 3.f * yy);
@@ -306,174 +388,246 @@ __device__ void sh_grad(const void* sh, int dtype, int deg, int64_t i, float dx,
             Y[15] = d0 * x * (xx - 3.f * yy); gx[15] = d0 * (3.f * xx - 3.f * yy); gy[15] = -6.f * d0 * x * y;
         }
     }
-    float gdx = 0.f, gdy = 0.f, gdz = 0.f;
-    for (int c = 0; c < 3; ++c) {
-        float acc = 0.f;
-        for (int k = 0; k < K; ++k) {
-            const float coef = (dtype == UMGS_BF16)
-                                   ? __uint_as_float(((unsigned int)static_cast<const unsigned short*>(sh)[base + 3 * k + c]) << 16)
-                                   : static_cast<const float*>(sh)[base + 3 * k + c];
-            acc = fmaf(coef, Y[k], acc);
-        }
-        if (acc + 0.5f < 0.f) continue;  // clamped channel
-        const float g = drgb[c];
-        if (g == 0.f) continue;
-        for (int k = 0; k < K; ++k) {
-            const float coef = (dtype == UMGS_BF16)
-                                   ? __uint_as_float(((unsigned int)static_cast<const unsigned short*>(sh)[base + 3 * k + c]) << 16)
-                                   : static_cast<const float*>(sh)[base + 3 * k + c];
-            dsh[3 * k + c] += g * Y[k];
-            gdx += g * coef * gx[k]; gdy += g * coef * gy[k]; gdz += g * coef * gz[k];
-        }
-    }
-    // project onto the tangent plane of the unit direction, divide by |dir|
-    const float r = gdx * x + gdy * y + gdz * z;
-    ddir[0] = (gdx - r * x) * inv; ddir[1] = (gdy - r * y) * inv; ddir[2] = (gdz - r * z) * inv;
 }
 
-__global__ void __launch_bounds__(128) project_gaussians_bwd_kernel(
+// Gradient of one camera's colour (SH of the view direction dir = mean -
+// camera centre, clamped at 0 after the +0.5 offset) with respect to the
+// coefficients (added to dsh) and to the mean (added to dmu).  coef and dsh
+// point at this Gaussian's 3K coefficients and gradients in shared memory.
+template <int DEG>
+__device__ __forceinline__ void sh_grad(const float* coef, float dx, float dy, float dz, const float drgb[3],
+                                        float* dsh, float dmu[3]) {
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    // the direction is normalised as in the forward shading
+    const float inv = rsqrtf(dx * dx + dy * dy + dz * dz);
+    const float x = dx * inv, y = dy * inv, z = dz * inv;
+    float Y[K], gx[K], gy[K], gz[K];
+    sh_basis_grad<DEG>(x, y, z, Y, gx, gy, gz);
+    float gdx = 0.f, gdy = 0.f, gdz = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc = fmaf(coef[3 * k + c], Y[k], acc);
+        const float g = (acc + 0.5f < 0.f) ? 0.f : drgb[c];  // clamped channel: no gradient
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            dsh[3 * k + c] += g * Y[k];
+            const float gc = g * coef[3 * k + c];
+            gdx += gc * gx[k]; gdy += gc * gy[k]; gdz += gc * gz[k];
+        }
+    }
+    if (DEG > 0) {
+        // project onto the tangent plane of the unit direction, divide by |dir|
+        const float r = gdx * x + gdy * y + gdz * z;
+        dmu[0] += (gdx - r * x) * inv; dmu[1] += (gdy - r * y) * inv; dmu[2] += (gdz - r * z) * inv;
+    }
+}
+
+// One thread per Gaussian, 32 Gaussians per warp, kProjBwdWarps warps per
+// CTA.  The warp's SH coefficients are staged through shared memory
+// (coalesced in; rows padded to an odd length so the per-thread rows are
+// conflict-free), the SH gradients are accumulated in a second such buffer
+// and leave coalesced.  Every output element is written.
+constexpr int kProjBwdWarps = 2;
+
+template <int DEG>
+__global__ void __launch_bounds__(kProjBwdWarps * 32) project_gaussians_bwd_kernel(
     const float* __restrict__ means, const float* __restrict__ quats, const float* __restrict__ scales,
-    const void* __restrict__ sh, int sh_dtype, int sh_deg, const float* __restrict__ cov3d, int64_t N,
+    const void* __restrict__ sh, int sh_dtype, const float* __restrict__ cov3d, int64_t N,
     const DevCam* __restrict__ cams, int ncams, const BinInfo* __restrict__ bin, int64_t ntot,
     const float* __restrict__ ggrad, float* __restrict__ d_means, float* __restrict__ d_quats,
     float* __restrict__ d_scales, float* __restrict__ d_opac, float* __restrict__ d_sh, float* __restrict__ d_cov) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    const int K = (sh_deg + 1) * (sh_deg + 1);
-    const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
-    // 3D covariance and its factors
-    float S[9], Rq[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, s3[3] = {0, 0, 0}, qn[4] = {1, 0, 0, 0}, qlen = 1.f;
-    if (cov3d) {
-        const float* c = cov3d + 6 * i;
-        S[0] = c[0]; S[1] = c[1]; S[2] = c[2]; S[3] = c[1]; S[4] = c[3]; S[5] = c[4]; S[6] = c[2]; S[7] = c[4]; S[8] = c[5];
+    constexpr int K = (DEG + 1) * (DEG + 1);
+    constexpr int K3 = 3 * K;
+    constexpr int KP = K3 | 1;
+    __shared__ float s_sh[kProjBwdWarps][2][32 * KP];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t wbase = ((int64_t)blockIdx.x * kProjBwdWarps + warp) * 32;
+    if (wbase >= N) return;  // whole warp (only warp-level synchronisation below)
+    const int nw = N - wbase < 32 ? (int)(N - wbase) : 32;
+    float* buf = s_sh[warp][0];
+    float* gbuf = s_sh[warp][1];
+    if (sh_dtype == UMGS_BF16) {
+        const unsigned short* p = static_cast<const unsigned short*>(sh) + wbase * K3;
+        for (int j = lane; j < nw * K3; j += 32) {
+            const int g = j / K3;
+            buf[g * KP + (j - g * K3)] = __uint_as_float(((unsigned int)p[j]) << 16);
+        }
     } else {
-        float w = quats[4 * i], x = quats[4 * i + 1], y = quats[4 * i + 2], z = quats[4 * i + 3];
-        qlen = sqrtf(w * w + x * x + y * y + z * z);
-        if (qlen > 0.f) { w /= qlen; x /= qlen; y /= qlen; z /= qlen; } else { w = 1.f; x = y = z = 0.f; qlen = 1.f; }
-        qn[0] = w; qn[1] = x; qn[2] = y; qn[3] = z;
-        Rq[0] = 1.f - 2.f * (y * y + z * z); Rq[1] = 2.f * (x * y - w * z); Rq[2] = 2.f * (x * z + w * y);
-        Rq[3] = 2.f * (x * y + w * z); Rq[4] = 1.f - 2.f * (x * x + z * z); Rq[5] = 2.f * (y * z - w * x);
-        Rq[6] = 2.f * (x * z - w * y); Rq[7] = 2.f * (y * z + w * x); Rq[8] = 1.f - 2.f * (x * x + y * y);
-        s3[0] = scales[3 * i]; s3[1] = scales[3 * i + 1]; s3[2] = scales[3 * i + 2];
-        float M[9];
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) M[3 * a + b] = Rq[3 * a + b] * s3[b];
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) S[3 * a + b] = M[3 * a] * M[3 * b] + M[3 * a + 1] * M[3 * b + 1] + M[3 * a + 2] * M[3 * b + 2];
-    }
-    float dmu[3] = {0, 0, 0}, dS[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, dop = 0.f;
-    float dsh[48];
-    for (int k = 0; k < 48; ++k) dsh[k] = 0.f;
-    for (int cam = 0; cam < ncams; ++cam) {
-        if (!bin[(int64_t)cam * ntot + i].valid) continue;
-        const float* gv = ggrad + ((int64_t)cam * N + i) * 12;
-        const float du = gv[0], dv = gv[1], dA = gv[2], dB = gv[3], dC = gv[4], dO = gv[5];
-        const float drgb[3] = {gv[6], gv[7], gv[8]};
-        if (du == 0.f && dv == 0.f && dA == 0.f && dB == 0.f && dC == 0.f && dO == 0.f && drgb[0] == 0.f &&
-            drgb[1] == 0.f && drgb[2] == 0.f)
-            continue;
-        const DevCam& Cm = cams[cam];
-        const float* R = Cm.R;
-        const float X = R[0] * mx + R[1] * my + R[2] * mz + Cm.t[0];
-        const float Y = R[3] * mx + R[4] * my + R[5] * mz + Cm.t[1];
-        const float Z = R[6] * mx + R[7] * my + R[8] * mz + Cm.t[2];
-        const float iz = 1.f / Z, iz2 = iz * iz;
-        const float limx = 1.3f * ((float)Cm.W / (2.f * Cm.fx)), limy = 1.3f * ((float)Cm.H / (2.f * Cm.fy));
-        const float txz = X * iz, tyz = Y * iz;
-        const bool cx_in = txz >= -limx && txz <= limx, cy_in = tyz >= -limy && tyz <= limy;
-        const float xc = fminf(limx, fmaxf(-limx, txz)) * Z, yc = fminf(limy, fmaxf(-limy, tyz)) * Z;
-        const float J00 = Cm.fx * iz, J11 = Cm.fy * iz, J02 = -Cm.fx * xc * iz2, J12 = -Cm.fy * yc * iz2;
-        float T0[3], T1[3];
-        for (int k = 0; k < 3; ++k) { T0[k] = J00 * R[k] + J02 * R[6 + k]; T1[k] = J11 * R[3 + k] + J12 * R[6 + k]; }
-        float U0[3], U1[3];
-        for (int k = 0; k < 3; ++k) {
-            U0[k] = T0[0] * S[k] + T0[1] * S[3 + k] + T0[2] * S[6 + k];
-            U1[k] = T1[0] * S[k] + T1[1] * S[3 + k] + T1[2] * S[6 + k];
+        const float* p = static_cast<const float*>(sh) + wbase * K3;
+        for (int j = lane; j < nw * K3; j += 32) {
+            const int g = j / K3;
+            buf[g * KP + (j - g * K3)] = p[j];
         }
-        const float a = U0[0] * T0[0] + U0[1] * T0[1] + U0[2] * T0[2] + 0.3f;
-        const float b = U0[0] * T1[0] + U0[1] * T1[1] + U0[2] * T1[2];
-        const float c = U1[0] * T1[0] + U1[1] * T1[1] + U1[2] * T1[2] + 0.3f;
-        // conic Q = inv([[a b][b c]])
-        float QA, QB, QC;
-        const float det = a * c - b * b;
-        if (det < 0.0009765625f * a * c) {
-            const double dd = (double)a * c - (double)b * b;
-            QA = (float)(c / dd); QB = (float)(-b / dd); QC = (float)(a / dd);
+    }
+    const int64_t i = wbase + lane;
+    const bool live = lane < nw;
+    float* dsh = gbuf + lane * KP;
+#pragma unroll
+    for (int k = 0; k < K3; ++k) dsh[k] = 0.f;
+    __syncwarp();
+    if (live) {
+        const float* coef = buf + lane * KP;
+        const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
+        // 3D covariance and its factors
+        float S[9], Rq[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, s3[3] = {0, 0, 0}, qn[4] = {1, 0, 0, 0}, qlen = 1.f;
+        if (cov3d) {
+            const float* c = cov3d + 6 * i;
+            S[0] = c[0]; S[1] = c[1]; S[2] = c[2]; S[3] = c[1]; S[4] = c[3]; S[5] = c[4]; S[6] = c[2]; S[7] = c[4]; S[8] = c[5];
         } else {
-            const float id = 1.f / det;
-            QA = c * id; QB = -b * id; QC = a * id;
+            const float4 q4 = reinterpret_cast<const float4*>(quats)[i];
+            float w = q4.x, x = q4.y, y = q4.z, z = q4.w;
+            qlen = sqrtf(w * w + x * x + y * y + z * z);
+            if (qlen > 0.f) { w /= qlen; x /= qlen; y /= qlen; z /= qlen; } else { w = 1.f; x = y = z = 0.f; qlen = 1.f; }
+            qn[0] = w; qn[1] = x; qn[2] = y; qn[3] = z;
+            Rq[0] = 1.f - 2.f * (y * y + z * z); Rq[1] = 2.f * (x * y - w * z); Rq[2] = 2.f * (x * z + w * y);
+            Rq[3] = 2.f * (x * y + w * z); Rq[4] = 1.f - 2.f * (x * x + z * z); Rq[5] = 2.f * (y * z - w * x);
+            Rq[6] = 2.f * (x * z - w * y); Rq[7] = 2.f * (y * z + w * x); Rq[8] = 1.f - 2.f * (x * x + y * y);
+            s3[0] = scales[3 * i]; s3[1] = scales[3 * i + 1]; s3[2] = scales[3 * i + 2];
+            float M[9];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) M[3 * a + b] = Rq[3 * a + b] * s3[b];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) S[3 * a + b] = M[3 * a] * M[3 * b] + M[3 * a + 1] * M[3 * b + 1] + M[3 * a + 2] * M[3 * b + 2];
         }
-        // dL/dSigma2D = -Q G_Q Q with G_Q = [[dA, dB/2],[dB/2, dC]]
-        const float g01 = 0.5f * dB;
-        const float m00 = QA * dA + QB * g01, m01 = QA * g01 + QB * dC;
-        const float m10 = QB * dA + QC * g01, m11 = QB * g01 + QC * dC;
-        const float G00 = -(m00 * QA + m01 * QB), G01 = -(m00 * QB + m01 * QC), G11 = -(m10 * QB + m11 * QC);
-        // Sigma2D = T S T^T: dS3 = T^T G T, dT = 2 G T S
-        float GT0[3], GT1[3];
-        for (int k = 0; k < 3; ++k) { GT0[k] = G00 * T0[k] + G01 * T1[k]; GT1[k] = G01 * T0[k] + G11 * T1[k]; }
-        for (int p = 0; p < 3; ++p)
-            for (int q = 0; q < 3; ++q) dS[3 * p + q] += T0[p] * GT0[q] + T1[p] * GT1[q];
-        float dT0[3], dT1[3];
-        for (int k = 0; k < 3; ++k) {
-            dT0[k] = 2.f * (GT0[0] * S[k] + GT0[1] * S[3 + k] + GT0[2] * S[6 + k]);
-            dT1[k] = 2.f * (GT1[0] * S[k] + GT1[1] * S[3 + k] + GT1[2] * S[6 + k]);
+        float dmu[3] = {0, 0, 0}, dS[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, dop = 0.f;
+        for (int cam = 0; cam < ncams; ++cam) {
+            if (!bin[(int64_t)cam * ntot + i].valid) continue;
+            const float4* gv4 = reinterpret_cast<const float4*>(ggrad + ((int64_t)cam * N + i) * 12);
+            const float4 g0 = gv4[0], g1 = gv4[1], g2 = gv4[2];
+            const float du = g0.x, dv = g0.y, dA = g0.z, dB = g0.w, dC = g1.x, dO = g1.y;
+            const float drgb[3] = {g1.z, g1.w, g2.x};
+            if (du == 0.f && dv == 0.f && dA == 0.f && dB == 0.f && dC == 0.f && dO == 0.f && drgb[0] == 0.f &&
+                drgb[1] == 0.f && drgb[2] == 0.f)
+                continue;
+            const DevCam& Cm = cams[cam];
+            const float* R = Cm.R;
+            const float X = R[0] * mx + R[1] * my + R[2] * mz + Cm.t[0];
+            const float Yc = R[3] * mx + R[4] * my + R[5] * mz + Cm.t[1];
+            const float Z = R[6] * mx + R[7] * my + R[8] * mz + Cm.t[2];
+            const float iz = 1.f / Z, iz2 = iz * iz;
+            const float limx = 1.3f * ((float)Cm.W / (2.f * Cm.fx)), limy = 1.3f * ((float)Cm.H / (2.f * Cm.fy));
+            const float txz = X * iz, tyz = Yc * iz;
+            const bool cx_in = txz >= -limx && txz <= limx, cy_in = tyz >= -limy && tyz <= limy;
+            const float xc = fminf(limx, fmaxf(-limx, txz)) * Z, yc = fminf(limy, fmaxf(-limy, tyz)) * Z;
+            const float J00 = Cm.fx * iz, J11 = Cm.fy * iz, J02 = -Cm.fx * xc * iz2, J12 = -Cm.fy * yc * iz2;
+            float T0[3], T1[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) { T0[k] = J00 * R[k] + J02 * R[6 + k]; T1[k] = J11 * R[3 + k] + J12 * R[6 + k]; }
+            float U0[3], U1[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                U0[k] = T0[0] * S[k] + T0[1] * S[3 + k] + T0[2] * S[6 + k];
+                U1[k] = T1[0] * S[k] + T1[1] * S[3 + k] + T1[2] * S[6 + k];
+            }
+            const float a = U0[0] * T0[0] + U0[1] * T0[1] + U0[2] * T0[2] + 0.3f;
+            const float b = U0[0] * T1[0] + U0[1] * T1[1] + U0[2] * T1[2];
+            const float c = U1[0] * T1[0] + U1[1] * T1[1] + U1[2] * T1[2] + 0.3f;
+            // conic Q = inv([[a b][b c]])
+            float QA, QB, QC;
+            const float det = a * c - b * b;
+            if (det < 0.0009765625f * a * c) {
+                const double dd = (double)a * c - (double)b * b;
+                QA = (float)(c / dd); QB = (float)(-b / dd); QC = (float)(a / dd);
+            } else {
+                const float id = 1.f / det;
+                QA = c * id; QB = -b * id; QC = a * id;
+            }
+            // dL/dSigma2D = -Q G_Q Q with G_Q = [[dA, dB/2],[dB/2, dC]]
+            const float g01 = 0.5f * dB;
+            const float m00 = QA * dA + QB * g01, m01 = QA * g01 + QB * dC;
+            const float m10 = QB * dA + QC * g01, m11 = QB * g01 + QC * dC;
+            const float G00 = -(m00 * QA + m01 * QB), G01 = -(m00 * QB + m01 * QC), G11 = -(m10 * QB + m11 * QC);
+            // Sigma2D = T S T^T: dS3 = T^T G T, dT = 2 G T S
+            float GT0[3], GT1[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) { GT0[k] = G00 * T0[k] + G01 * T1[k]; GT1[k] = G01 * T0[k] + G11 * T1[k]; }
+#pragma unroll
+            for (int p = 0; p < 3; ++p)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) dS[3 * p + q] += T0[p] * GT0[q] + T1[p] * GT1[q];
+            float dT0[3], dT1[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                dT0[k] = 2.f * (GT0[0] * S[k] + GT0[1] * S[3 + k] + GT0[2] * S[6 + k]);
+                dT1[k] = 2.f * (GT1[0] * S[k] + GT1[1] * S[3 + k] + GT1[2] * S[6 + k]);
+            }
+            // T = J R: dJ = dT R^T (only J00, J02, J11, J12 are variables)
+            const float dJ00 = dT0[0] * R[0] + dT0[1] * R[1] + dT0[2] * R[2];
+            const float dJ02 = dT0[0] * R[6] + dT0[1] * R[7] + dT0[2] * R[8];
+            const float dJ11 = dT1[0] * R[3] + dT1[1] * R[4] + dT1[2] * R[5];
+            const float dJ12 = dT1[0] * R[6] + dT1[1] * R[7] + dT1[2] * R[8];
+            float dX = du * Cm.fx * iz, dY = dv * Cm.fy * iz;
+            float dZ = -du * Cm.fx * X * iz2 - dv * Cm.fy * Yc * iz2;
+            dZ += -dJ00 * Cm.fx * iz2 - dJ11 * Cm.fy * iz2;
+            if (cx_in) { dX += -dJ02 * Cm.fx * iz2; dZ += dJ02 * 2.f * Cm.fx * X * iz2 * iz; }
+            else { dZ += dJ02 * Cm.fx * copysignf(limx, txz) * iz2; }
+            if (cy_in) { dY += -dJ12 * Cm.fy * iz2; dZ += dJ12 * 2.f * Cm.fy * Yc * iz2 * iz; }
+            else { dZ += dJ12 * Cm.fy * copysignf(limy, tyz) * iz2; }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) dmu[k] += R[k] * dX + R[3 + k] * dY + R[6 + k] * dZ;
+            dop += dO;
+            if (drgb[0] != 0.f || drgb[1] != 0.f || drgb[2] != 0.f)
+                sh_grad<DEG>(coef, mx - Cm.campos[0], my - Cm.campos[1], mz - Cm.campos[2], drgb, dsh, dmu);
         }
-        // T = J R: dJ = dT R^T (only J00, J02, J11, J12 are variables)
-        const float dJ00 = dT0[0] * R[0] + dT0[1] * R[1] + dT0[2] * R[2];
-        const float dJ02 = dT0[0] * R[6] + dT0[1] * R[7] + dT0[2] * R[8];
-        const float dJ11 = dT1[0] * R[3] + dT1[1] * R[4] + dT1[2] * R[5];
-        const float dJ12 = dT1[0] * R[6] + dT1[1] * R[7] + dT1[2] * R[8];
-        float dX = du * Cm.fx * iz, dY = dv * Cm.fy * iz;
-        float dZ = -du * Cm.fx * X * iz2 - dv * Cm.fy * Y * iz2;
-        dZ += -dJ00 * Cm.fx * iz2 - dJ11 * Cm.fy * iz2;
-        if (cx_in) { dX += -dJ02 * Cm.fx * iz2; dZ += dJ02 * 2.f * Cm.fx * X * iz2 * iz; }
-        else { dZ += dJ02 * Cm.fx * copysignf(limx, txz) * iz2; }
-        if (cy_in) { dY += -dJ12 * Cm.fy * iz2; dZ += dJ12 * 2.f * Cm.fy * Y * iz2 * iz; }
-        else { dZ += dJ12 * Cm.fy * copysignf(limy, tyz) * iz2; }
-        for (int k = 0; k < 3; ++k) dmu[k] += R[k] * dX + R[3 + k] * dY + R[6 + k] * dZ;
-        dop += dO;
-        float ddir[3];
-        sh_grad(sh, sh_dtype, sh_deg, i, mx - Cm.campos[0], my - Cm.campos[1], mz - Cm.campos[2], drgb, dsh, ddir);
-        dmu[0] += ddir[0]; dmu[1] += ddir[1]; dmu[2] += ddir[2];
+        if (d_means) { d_means[3 * i] = dmu[0]; d_means[3 * i + 1] = dmu[1]; d_means[3 * i + 2] = dmu[2]; }
+        if (d_opac) d_opac[i] = dop;
+        // symmetrise dS (a function of the symmetric Sigma)
+        const float G3[9] = {dS[0], 0.5f * (dS[1] + dS[3]), 0.5f * (dS[2] + dS[6]),
+                             0.5f * (dS[1] + dS[3]), dS[4], 0.5f * (dS[5] + dS[7]),
+                             0.5f * (dS[2] + dS[6]), 0.5f * (dS[5] + dS[7]), dS[8]};
+        if (cov3d) {
+            if (d_cov) {
+                float* o = d_cov + 6 * i;
+                o[0] = G3[0]; o[1] = 2.f * G3[1]; o[2] = 2.f * G3[2]; o[3] = G3[4]; o[4] = 2.f * G3[5]; o[5] = G3[8];
+            }
+        } else {
+            // Sigma = M M^T, M = Rq diag(s): dM = 2 G3 M
+            float M[9], dM[9];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) M[3 * a + b] = Rq[3 * a + b] * s3[b];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b)
+                    dM[3 * a + b] = 2.f * (G3[3 * a] * M[b] + G3[3 * a + 1] * M[3 + b] + G3[3 * a + 2] * M[6 + b]);
+            if (d_scales)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) d_scales[3 * i + b] = dM[b] * Rq[b] + dM[3 + b] * Rq[3 + b] + dM[6 + b] * Rq[6 + b];
+            if (d_quats) {
+                float Gr[9];
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int b = 0; b < 3; ++b) Gr[3 * a + b] = dM[3 * a + b] * s3[b];
+                const float w = qn[0], x = qn[1], y = qn[2], z = qn[3];
+                float dq[4];
+                dq[0] = 2.f * (-z * Gr[1] + y * Gr[2] + z * Gr[3] - x * Gr[5] - y * Gr[6] + x * Gr[7]);
+                dq[1] = 2.f * (y * Gr[1] + z * Gr[2] + y * Gr[3] - 2.f * x * Gr[4] - w * Gr[5] + z * Gr[6] + w * Gr[7] - 2.f * x * Gr[8]);
+                dq[2] = 2.f * (-2.f * y * Gr[0] + x * Gr[1] + w * Gr[2] + x * Gr[3] + z * Gr[5] - w * Gr[6] + z * Gr[7] - 2.f * y * Gr[8]);
+                dq[3] = 2.f * (-2.f * z * Gr[0] - w * Gr[1] + x * Gr[2] + w * Gr[3] - 2.f * z * Gr[4] + y * Gr[5] + x * Gr[6] + y * Gr[7]);
+                const float dd = dq[0] * w + dq[1] * x + dq[2] * y + dq[3] * z;
+                const float il = 1.f / qlen;
+                reinterpret_cast<float4*>(d_quats)[i] =
+                    make_float4((dq[0] - dd * w) * il, (dq[1] - dd * x) * il, (dq[2] - dd * y) * il, (dq[3] - dd * z) * il);
+            }
+        }
     }
-    if (d_means) { d_means[3 * i] = dmu[0]; d_means[3 * i + 1] = dmu[1]; d_means[3 * i + 2] = dmu[2]; }
-    if (d_opac) d_opac[i] = dop;
-    if (d_sh) for (int k = 0; k < 3 * K; ++k) d_sh[(int64_t)i * 3 * K + k] = dsh[k];
-    // symmetrise dS (a function of the symmetric Sigma)
-    const float G3[9] = {dS[0], 0.5f * (dS[1] + dS[3]), 0.5f * (dS[2] + dS[6]),
-                         0.5f * (dS[1] + dS[3]), dS[4], 0.5f * (dS[5] + dS[7]),
-                         0.5f * (dS[2] + dS[6]), 0.5f * (dS[5] + dS[7]), dS[8]};
-    if (cov3d) {
-        if (d_cov) {
-            float* o = d_cov + 6 * i;
-            o[0] = G3[0]; o[1] = 2.f * G3[1]; o[2] = 2.f * G3[2]; o[3] = G3[4]; o[4] = 2.f * G3[5]; o[5] = G3[8];
-        }
-        return;
-    }
-    // Sigma = M M^T, M = Rq diag(s): dM = 2 G3 M
-    float M[9], dM[9];
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) M[3 * a + b] = Rq[3 * a + b] * s3[b];
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 3; ++b) dM[3 * a + b] = 2.f * (G3[3 * a] * M[b] + G3[3 * a + 1] * M[3 + b] + G3[3 * a + 2] * M[6 + b]);
-    if (d_scales)
-        for (int b = 0; b < 3; ++b) d_scales[3 * i + b] = dM[b] * Rq[b] + dM[3 + b] * Rq[3 + b] + dM[6 + b] * Rq[6 + b];
-    if (d_quats) {
-        float Gr[9];
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) Gr[3 * a + b] = dM[3 * a + b] * s3[b];
-        const float w = qn[0], x = qn[1], y = qn[2], z = qn[3];
-        float dq[4];
-        dq[0] = 2.f * (-z * Gr[1] + y * Gr[2] + z * Gr[3] - x * Gr[5] - y * Gr[6] + x * Gr[7]);
-        dq[1] = 2.f * (y * Gr[1] + z * Gr[2] + y * Gr[3] - 2.f * x * Gr[4] - w * Gr[5] + z * Gr[6] + w * Gr[7] - 2.f * x * Gr[8]);
-        dq[2] = 2.f * (-2.f * y * Gr[0] + x * Gr[1] + w * Gr[2] + x * Gr[3] + z * Gr[5] - w * Gr[6] + z * Gr[7] - 2.f * y * Gr[8]);
-        dq[3] = 2.f * (-2.f * z * Gr[0] - w * Gr[1] + x * Gr[2] + w * Gr[3] - 2.f * z * Gr[4] + y * Gr[5] + x * Gr[6] + y * Gr[7]);
-        const float dd = dq[0] * w + dq[1] * x + dq[2] * y + dq[3] * z;
-        for (int k = 0; k < 4; ++k) d_quats[4 * i + k] = (dq[k] - dd * qn[k]) / qlen;
+    if (!d_sh) return;
+    __syncwarp();
+    float* o = d_sh + wbase * K3;
+    for (int j = lane; j < nw * K3; j += 32) {
+        const int g = j / K3;
+        o[j] = gbuf[g * KP + (j - g * K3)];
     }
 }
-
-// ---- records -> mesh vertices ---------------------------------------------
 
 __global__ void __launch_bounds__(256) setup_triangles_bwd_kernel(
     const float* __restrict__ verts, const int32_t* __restrict__ faces, const float* __restrict__ valpha,
@@ -563,17 +717,19 @@ umgs_status render_backward(umgs_ctx* ctx, umgs_frame* fr, const umgs_gaussians*
     }
     StageTimer tm(ctx, UMGS_STAGE_BACKWARD_PROJECT, stream);
     if (Ng > 0 && gg) {
-        const int K = (g->sh_degree + 1) * (g->sh_degree + 1);
-        if (gg->means) UMGS_TRY(cudaMemsetAsync(gg->means, 0, sizeof(float) * 3 * Ng, stream));
-        if (gg->opacities) UMGS_TRY(cudaMemsetAsync(gg->opacities, 0, sizeof(float) * Ng, stream));
-        if (gg->sh) UMGS_TRY(cudaMemsetAsync(gg->sh, 0, sizeof(float) * 3 * K * Ng, stream));
-        if (gg->quats) UMGS_TRY(cudaMemsetAsync(gg->quats, 0, sizeof(float) * 4 * Ng, stream));
-        if (gg->scales) UMGS_TRY(cudaMemsetAsync(gg->scales, 0, sizeof(float) * 3 * Ng, stream));
-        if (gg->cov3d) UMGS_TRY(cudaMemsetAsync(gg->cov3d, 0, sizeof(float) * 6 * Ng, stream));
-        project_gaussians_bwd_kernel<<<grid_for(Ng, 128), 128, 0, stream>>>(
-            g->means, g->quats, g->scales, g->sh, g->sh_dtype, g->sh_degree, g->cov3d, Ng, fr->cams.as<DevCam>(),
-            fr->ncams, fr->bin.as<BinInfo>(), Ntot, fr->ggrad.as<float>(), gg->means, g->cov3d ? nullptr : gg->quats,
-            g->cov3d ? nullptr : gg->scales, gg->opacities, gg->sh, g->cov3d ? gg->cov3d : nullptr);
+        // every element of the requested outputs is written by the kernel
+#define UMGS_LAUNCH(D)                                                                                          \
+        project_gaussians_bwd_kernel<D><<<grid_for(Ng, kProjBwdWarps * 32), kProjBwdWarps * 32, 0, stream>>>(                                \
+            g->means, g->quats, g->scales, g->sh, g->sh_dtype, g->cov3d, Ng, fr->cams.as<DevCam>(), fr->ncams,      \
+            fr->bin.as<BinInfo>(), Ntot, fr->ggrad.as<float>(), gg->means, g->cov3d ? nullptr : gg->quats,         \
+            g->cov3d ? nullptr : gg->scales, gg->opacities, gg->sh, g->cov3d ? gg->cov3d : nullptr)
+        switch (g->sh_degree) {
+            case 0: UMGS_LAUNCH(0); break;
+            case 1: UMGS_LAUNCH(1); break;
+            case 2: UMGS_LAUNCH(2); break;
+            default: UMGS_LAUNCH(3); break;
+        }
+#undef UMGS_LAUNCH
         UMGS_TRY(cudaGetLastError());
     }
     int64_t tri_base = 0;

@@ -90,3 +90,50 @@ def test_opaque_stack_overflow_rerun(ctx):
     sc = Hh.scene(Hh.no_gaussians(), [m], c)
     ref, got, out, rgb = _run(ctx, sc, 5, tile=8)
     _compare(ref, got, ["verts0", "vcolor0", "falpha0"])
+
+
+def test_multi_camera_gradients_sum_over_views(ctx):
+    # three views of one scene, SH degree 2: the backward sums the per-view
+    # gradients, the oracle is run per view and summed
+    from paper_2601_19233_gb300 import umgs
+    sc = S.small_scene(91, 36, 30, 400, mesh_subdiv=1, sh_degree=2, n_cams=3)
+    rng = np.random.default_rng(91)
+    dls, ref = [], None
+    for c, cam in enumerate(sc.cameras):
+        img = R.render_image(sc, c)
+        gC = rng.normal(size=(cam.height, cam.width, 3))
+        gT = rng.normal(size=(cam.height, cam.width))
+        gC[img["tie"]] = 0
+        gT[img["tie"]] = 0
+        r, _, _ = OG.image_grad(sc, gC, gT, cam_index=c)
+        ref = r if ref is None else {k: ref[k] + r[k] for k in ref}
+        dls.append(np.concatenate([gC, gT[..., None]], -1))
+    g = umgs.gaussians_to_device(sc.gaussians)
+    ms = [umgs.mesh_to_device(m) for m in sc.meshes]
+    fr = umgs.Frame(ctx)
+    umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(16, save=True), frame=fr)
+    dl = torch.as_tensor(np.stack(dls).astype(np.float32)).cuda()
+    got = {k: v.cpu().numpy() for k, v in umgs.render_backward(ctx, fr, g, ms, dl).items()}
+    _compare(ref, got, ["means", "quats", "scales", "opacities", "sh", "verts0", "vcolor0", "falpha0"])
+
+
+def test_bf16_sh_gradients(ctx):
+    # SH stored in bf16: the oracle sees the same (bf16-representable) values
+    from paper_2601_19233_gb300 import umgs
+    sc = S.small_scene(93, 40, 33, 500, mesh_subdiv=1, sh_degree=3)
+    sc.gaussians.sh = torch.as_tensor(sc.gaussians.sh).to(torch.bfloat16).to(torch.float32).numpy()
+    cam = sc.cameras[0]
+    rng = np.random.default_rng(93)
+    img = R.render_image(sc)
+    gC = rng.normal(size=(cam.height, cam.width, 3))
+    gC[img["tie"]] = 0
+    ref, _, _ = OG.image_grad(sc, gC, None)
+    g = umgs.gaussians_to_device(sc.gaussians, sh_dtype=torch.bfloat16)
+    ms = [umgs.mesh_to_device(m) for m in sc.meshes]
+    fr = umgs.Frame(ctx)
+    umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(16, save=True), frame=fr)
+    dl = np.zeros((1, cam.height, cam.width, 4), np.float32)
+    dl[0, ..., :3] = gC
+    got = {k: v.cpu().numpy() for k, v in umgs.render_backward(ctx, fr, g, ms, torch.as_tensor(dl).cuda()).items()}
+    assert got["sh"].dtype == np.float32
+    _compare(ref, got, ["means", "quats", "scales", "opacities", "sh"])
