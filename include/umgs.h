@@ -341,6 +341,13 @@ enum {
 umgs_status umgs_profile_enable(umgs_ctx* ctx, int32_t on);
 umgs_status umgs_profile_read(umgs_ctx* ctx, double* ms, int64_t* launches);
 
+/* Number of kernels this library has launched in this process since it was
+ * loaded, over all contexts and devices (a launch of a render graph adds the
+ * number of kernels captured into it; capturing adds nothing).  Never fails;
+ * thread-safe.  The difference of two reads counts the kernels launched in
+ * between by the calling thread when no other thread uses the library. */
+long long umgs_kernel_launches(void);
+
 /* ---- deformation without device allocation ---------------------------------
  * No counterpart in the paper.  For callers that cannot allocate device
  * memory - e.g. a host application that hands all device memory to its own

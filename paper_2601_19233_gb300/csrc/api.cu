@@ -4,6 +4,8 @@
 
 #include "internal.h"
 
+std::atomic<long long> g_kernel_launches{0};
+
 namespace umgs {
 
 umgs_status fail(umgs_ctx* ctx, umgs_status s, const std::string& msg) {
@@ -87,6 +89,8 @@ umgs_status umgs_ctx_sync(umgs_ctx* ctx, void* stream) {
     }
     return UMGS_OK;
 }
+
+long long umgs_kernel_launches(void) { return g_kernel_launches.load(std::memory_order_relaxed); }
 
 umgs_status umgs_profile_enable(umgs_ctx* ctx, int32_t on) {
     if (!ctx) return UMGS_ERR_INVALID_ARG;

@@ -708,7 +708,7 @@ umgs_status render_backward(umgs_ctx* ctx, umgs_frame* fr, const umgs_gaussians*
             fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->trec.as<TRec>(), Ng, Nt,               \
             fr->tiles_x, tpc, fr->W, fr->H, fr->bg[0], fr->bg[1], fr->bg[2], dout, fr->last.as<int32_t>(),         \
             fr->tfin.as<float>(), fr->ntri.as<int32_t>(), fr->stack.as<float4>(), npix, fr->ggrad.as<float>(),     \
-            fr->tgrad.as<float>())
+            fr->tgrad.as<float>()), count_launch()
         if (fr->tile == 16) UMGS_LAUNCH(16);
         else if (fr->tile == 8) UMGS_LAUNCH(8);
         else UMGS_LAUNCH(32);
@@ -722,7 +722,7 @@ umgs_status render_backward(umgs_ctx* ctx, umgs_frame* fr, const umgs_gaussians*
         project_gaussians_bwd_kernel<D><<<grid_for(Ng, kProjBwdWarps * 32), kProjBwdWarps * 32, 0, stream>>>(                                \
             g->means, g->quats, g->scales, g->sh, g->sh_dtype, g->cov3d, Ng, fr->cams.as<DevCam>(), fr->ncams,      \
             fr->bin.as<BinInfo>(), Ntot, fr->ggrad.as<float>(), gg->means, g->cov3d ? nullptr : gg->quats,         \
-            g->cov3d ? nullptr : gg->scales, gg->opacities, gg->sh, g->cov3d ? gg->cov3d : nullptr)
+            g->cov3d ? nullptr : gg->scales, gg->opacities, gg->sh, g->cov3d ? gg->cov3d : nullptr), count_launch()
         switch (g->sh_degree) {
             case 0: UMGS_LAUNCH(0); break;
             case 1: UMGS_LAUNCH(1); break;
@@ -745,7 +745,7 @@ umgs_status render_backward(umgs_ctx* ctx, umgs_frame* fr, const umgs_gaussians*
                 setup_triangles_bwd_kernel<<<grid_for(me.nf, 256), 256, 0, stream>>>(
                     me.verts, me.faces, me.valpha, me.falpha, me.nf, tri_base, Nt, Ng + tri_base, fr->cams.as<DevCam>(),
                     fr->ncams, fr->bin.as<BinInfo>(), Ntot, fr->tgrad.as<float>(), o.verts, o.vcolor, o.valpha,
-                    o.falpha);
+                    o.falpha), count_launch();
                 UMGS_TRY(cudaGetLastError());
             }
         }

@@ -453,7 +453,7 @@ umgs_status bind_forward(umgs_ctx* ctx, const umgs_gaussians* g, const float* V,
     UMGS_TRY(cudaMemsetAsync(ctx->dstatus.ptr, 0, sizeof(int32_t), stream));
     {
         StageTimer tm(ctx, UMGS_STAGE_BIND_GRID, stream);
-        grid_stats_kernel<<<1, 1024, 0, stream>>>(V, F, nv, nf, stats, ctx->dstatus.as<int32_t>());
+        grid_stats_kernel<<<1, 1024, 0, stream>>>(V, F, nv, nf, stats, ctx->dstatus.as<int32_t>()), count_launch();
         UMGS_TRY(cudaGetLastError());
     }
     float hs[8];
@@ -494,8 +494,8 @@ umgs_status bind_forward(umgs_ctx* ctx, const umgs_gaussians* g, const float* V,
     int32_t nent = 0;
     {
         StageTimer tm(ctx, UMGS_STAGE_BIND_GRID, stream);
-        grid_count_kernel<<<grid_for(nf, 256), 256, 0, stream>>>(V, F, nf, gi, cnt, nullptr);
-        grid_scan_kernel<<<1, 1024, 0, stream>>>(cnt, (int)cells, start);
+        grid_count_kernel<<<grid_for(nf, 256), 256, 0, stream>>>(V, F, nf, gi, cnt, nullptr), count_launch();
+        grid_scan_kernel<<<1, 1024, 0, stream>>>(cnt, (int)cells, start), count_launch();
         UMGS_TRY(cudaGetLastError());
     }
     UMGS_TRY(cudaMemcpyAsync(&nent, start + cells, sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
@@ -519,7 +519,7 @@ umgs_status bind_forward(umgs_ctx* ctx, const umgs_gaussians* g, const float* V,
     float4* ent = reinterpret_cast<float4*>(ws.as<char>() + off_ent0);
     {
         StageTimer tm(ctx, UMGS_STAGE_BIND_GRID, stream);
-        grid_fill_kernel<<<grid_for(nf, 256), 256, 0, stream>>>(V, F, nf, gi, start, fill, ent);
+        grid_fill_kernel<<<grid_for(nf, 256), 256, 0, stream>>>(V, F, nf, gi, start, fill, ent), count_launch();
         UMGS_TRY(cudaGetLastError());
     }
     // cameras
@@ -542,13 +542,13 @@ umgs_status bind_forward(umgs_ctx* ctx, const umgs_gaussians* g, const float* V,
             StageTimer tm(ctx, UMGS_STAGE_BIND_RAYCAST, stream);
             bind_raycast_kernel<<<grid_for(ntg, 128), 128, 0, stream>>>(
                 g->means, g->quats, g->scales, g->n, mode, k_sigma, ctx->bind_cams.as<DevCam>(), ncams, gi, start, ent,
-                out_face, out_bary, out_dist, out_flags, ctx->dstatus.as<int32_t>());
+                out_face, out_bary, out_dist, out_flags, ctx->dstatus.as<int32_t>()), count_launch();
             UMGS_TRY(cudaGetLastError());
         }
         StageTimer tm(ctx, UMGS_STAGE_BIND_NEAREST, stream);
         bind_nearest_kernel<<<grid_for(ntg, 128), 128, 0, stream>>>(
             g->means, g->quats, g->scales, g->n, mode, k_sigma, gi, start, ent, out_face, out_bary, out_dist, out_flags,
-            ctx->bind_cnt.as<unsigned long long>());
+            ctx->bind_cnt.as<unsigned long long>()), count_launch();
         UMGS_TRY(cudaGetLastError());
     }
     unsigned long long nfb = 0;

@@ -400,18 +400,18 @@ umgs_status deform_forward(umgs_ctx* ctx, const umgs_gaussians* g, const int32_t
     int32_t* status = ctx->dstatus.as<int32_t>();
     {
         StageTimer tm(ctx, UMGS_STAGE_DEFORM_FACES, stream);
-        face_gradients_kernel<<<grid_for(nf, 256), 256, 0, stream>>>(V, Vd, F, nv, nf, ctx->vacc.as<float>(), status);
+        face_gradients_kernel<<<grid_for(nf, 256), 256, 0, stream>>>(V, Vd, F, nv, nf, ctx->vacc.as<float>(), status), count_launch();
     }
     {
         StageTimer tm(ctx, UMGS_STAGE_DEFORM_VERTICES, stream);
         vertex_xforms_kernel<<<grid_for(nv, 256), 256, 0, stream>>>(V, Vd, ctx->vacc.as<float>(), nv,
-                                                                    ctx->vtab.as<float>());
+                                                                    ctx->vtab.as<float>()), count_launch();
     }
     StageTimer tm(ctx, UMGS_STAGE_DEFORM_GAUSSIANS, stream);
     if (g->n > 0)
         deform_gaussians_kernel<<<grid_for(8 * g->n, 256), 256, 0, stream>>>(
             g->means, g->quats, g->scales, g->cov3d, g->n, face, bary, V, F, nv, nf, ctx->vtab.as<float>(), mode,
-            out_means, out_cov, out_quats, status);
+            out_means, out_cov, out_quats, status), count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "deform kernels");
     return UMGS_OK;
 }
@@ -492,13 +492,13 @@ extern "C" umgs_status umgs_deform_noalloc(const umgs_gaussians* rest, const int
     int32_t* status = reinterpret_cast<int32_t*>(base + 22 * kNoAllocMaxVerts);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // the accumulators and the status word keep the previous call's values
-    noalloc_clear_kernel<<<grid_for(10 * nv, 256), 256, 0, s>>>(vacc, 10 * nv);
-    noalloc_clear_kernel<<<1, 64, 0, s>>>(reinterpret_cast<float*>(status), 64);
-    face_gradients_kernel<<<grid_for(nf, 256), 256, 0, s>>>(proxy_v, proxy_vd, proxy_f, nv, nf, vacc, status);
-    vertex_xforms_kernel<<<grid_for(nv, 256), 256, 0, s>>>(proxy_v, proxy_vd, vacc, nv, vtab);
+    noalloc_clear_kernel<<<grid_for(10 * nv, 256), 256, 0, s>>>(vacc, 10 * nv), count_launch();
+    noalloc_clear_kernel<<<1, 64, 0, s>>>(reinterpret_cast<float*>(status), 64), count_launch();
+    face_gradients_kernel<<<grid_for(nf, 256), 256, 0, s>>>(proxy_v, proxy_vd, proxy_f, nv, nf, vacc, status), count_launch();
+    vertex_xforms_kernel<<<grid_for(nv, 256), 256, 0, s>>>(proxy_v, proxy_vd, vacc, nv, vtab), count_launch();
     if (rest->n > 0)
         deform_gaussians_kernel<<<grid_for(8 * rest->n, 256), 256, 0, s>>>(
             rest->means, rest->quats, rest->scales, rest->cov3d, rest->n, face, bary, proxy_v, proxy_f, nv, nf, vtab,
-            mode, out_means, out_cov3d, out_quats, status);
+            mode, out_means, out_cov3d, out_quats, status), count_launch();
     return cudaGetLastError() == cudaSuccess ? UMGS_OK : UMGS_ERR_CUDA;
 }

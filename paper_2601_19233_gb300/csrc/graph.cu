@@ -13,6 +13,7 @@ struct umgs_graph {
     cudaStream_t cap = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;  // kernel launches captured into the graph
 };
 
 namespace umgs {
@@ -75,9 +76,13 @@ umgs_status umgs_render_graph_create(umgs_ctx* ctx, umgs_frame* frame, const umg
     umgs_default_render_opts(&o);
     if (opts) o = *opts;
     if (o.tile_size == 0) o.tile_size = 16;
+    const long long launches0 = g_kernel_launches.load();
     cudaError_t e = cudaStreamBeginCapture(gr->cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         st = render_forward(ctx, g, meshes, nmeshes, cams, ncams, o, out_rgbt, frame, gr->cap);
+        // captured launches do not run: they are counted per graph launch
+        gr->kernels = g_kernel_launches.load() - launches0;
+        count_launch(-gr->kernels);
         cudaGraph_t graph = nullptr;
         e = cudaStreamEndCapture(gr->cap, &graph);
         gr->graph = graph;
@@ -98,6 +103,7 @@ umgs_status umgs_graph_launch(umgs_graph* gr, void* stream) {
     if (!gr || !gr->exec) return UMGS_ERR_INVALID_ARG;
     const cudaError_t e = cudaGraphLaunch(gr->exec, static_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return cuda_fail(gr->ctx, e, "cudaGraphLaunch");
+    count_launch(gr->kernels);
     return UMGS_OK;
 }
 

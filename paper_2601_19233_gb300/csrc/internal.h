@@ -1,5 +1,6 @@
 // Host-side internals of libumgs: context, frames, workspace, launchers.
 #pragma once
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -68,6 +69,12 @@ struct umgs_frame {
             b->release();
     }
 };
+
+// Kernels launched by this library in this process, all devices
+// (umgs_kernel_launches).  Every launch site adds one; a launch of a captured
+// graph adds the number of kernels captured into it.
+extern std::atomic<long long> g_kernel_launches;
+inline void count_launch(long long n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // Per-stage CUDA-event timing (umgs_profile_enable / umgs_profile_read).
 struct StageProfiler {

@@ -863,7 +863,7 @@ cudaError_t launch_composite(umgs_frame* fr, const umgs_render_opts& opts, float
         uint32_t* mdev = reinterpret_cast<uint32_t*>(fr->status.as<int32_t>() + 4);
         work = reinterpret_cast<unsigned*>(fr->status.as<int32_t>() + 8);
         tile_order_keys_kernel<<<(M + 255) / 256, 256, 0, stream>>>(fr->tile_off.as<int64_t>(), M, fr->ord_k.as<uint32_t>(),
-                                                                     fr->ord_v.as<uint32_t>(), mdev);
+                                                                     fr->ord_v.as<uint32_t>(), mdev), count_launch();
         uint32_t* rk = nullptr;
         uint32_t* rv = nullptr;
         if ((e = radix_sort_pairs(fr, fr->ord_k.as<uint32_t>(), fr->ord_v.as<uint32_t>(), fr->ord_k2.as<uint32_t>(),
@@ -880,14 +880,14 @@ cudaError_t launch_composite(umgs_frame* fr, const umgs_render_opts& opts, float
         fr->nt, fr->tiles_x, tpc, fr->W, fr->H, te, opts.bg[0], opts.bg[1], opts.bg[2], opts.blend_mode, out,     \
         fr->last.as<int32_t>(), save ? fr->tfin.as<float>() : nullptr, save ? fr->ntri.as<int32_t>() : nullptr,   \
         save ? fr->stack.as<float4>() : nullptr, fr->stack_cap, npix, fr->status.as<int32_t>() + 2,             \
-        reinterpret_cast<unsigned long long*>(fr->status.as<int32_t>() + 6));                                   \
+        reinterpret_cast<unsigned long long*>(fr->status.as<int32_t>() + 6)), count_launch();                                   \
     else composite_kernel<TSV, SV><<<M, TSV * TSV, 0, stream>>>(                                                \
         fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->mixed ? fr->grec.as<GRec16>() : nullptr,  \
         fr->trec.as<TRec>(), fr->ng,                                                                            \
         fr->nt, fr->tiles_x, tpc, fr->W, fr->H, te, opts.bg[0], opts.bg[1], opts.bg[2], opts.blend_mode, out,     \
         fr->last.as<int32_t>(), save ? fr->tfin.as<float>() : nullptr, save ? fr->ntri.as<int32_t>() : nullptr,   \
         save ? fr->stack.as<float4>() : nullptr, fr->stack_cap, npix, fr->status.as<int32_t>() + 2,             \
-        reinterpret_cast<unsigned long long*>(fr->status.as<int32_t>() + 6))
+        reinterpret_cast<unsigned long long*>(fr->status.as<int32_t>() + 6)), count_launch()
     if (ts == 16) { if (save) UMGS_LAUNCH(16, true); else UMGS_LAUNCH(16, false); }
     else if (ts == 8) { if (save) UMGS_LAUNCH(8, true); else UMGS_LAUNCH(8, false); }
     else { if (save) UMGS_LAUNCH(32, true); else UMGS_LAUNCH(32, false); }
@@ -902,9 +902,9 @@ cudaError_t scan_u32(umgs_frame* fr, const uint32_t* in, uint32_t* out, int64_t 
     cudaError_t e = fr->rs_bsum.reserve(sizeof(uint32_t) * std::max<int64_t>(1, nb));
     if (e != cudaSuccess) return e;
     if (nb > (1 << 22)) return cudaErrorInvalidValue;
-    scan_reduce_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(in, n, fr->rs_bsum.as<uint32_t>());
-    scan_blocks_kernel<<<1, 1024, 0, s>>>(fr->rs_bsum.as<uint32_t>(), (int)nb, total);
-    scan_apply_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(in, n, fr->rs_bsum.as<uint32_t>(), out);
+    scan_reduce_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(in, n, fr->rs_bsum.as<uint32_t>()), count_launch();
+    scan_blocks_kernel<<<1, 1024, 0, s>>>(fr->rs_bsum.as<uint32_t>(), (int)nb, total), count_launch();
+    scan_apply_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(in, n, fr->rs_bsum.as<uint32_t>(), out), count_launch();
     return cudaGetLastError();
 }
 
@@ -924,10 +924,10 @@ cudaError_t radix_sort_pairs(umgs_frame* fr, uint32_t* k, uint32_t* v, uint32_t*
     uint32_t* hist = fr->rs_hist.as<uint32_t>();
     uint32_t* dtotal = fr->rs_hist2.as<uint32_t>();
     for (int shift = 0; shift < bits; shift += 8) {
-        radix_upsweep_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(k, n_dev, n_cap, shift, (int)nb, hist);
-        radix_hist_scan_kernel<<<256, kRsThreads, 0, s>>>(hist, (int)nb, dtotal);
+        radix_upsweep_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(k, n_dev, n_cap, shift, (int)nb, hist), count_launch();
+        radix_hist_scan_kernel<<<256, kRsThreads, 0, s>>>(hist, (int)nb, dtotal), count_launch();
         radix_downsweep_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(k, v, n_dev, n_cap, shift, (int)nb, hist, dtotal,
-                                                                   k2, v2);
+                                                                   k2, v2), count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         uint32_t* t = k; k = k2; k2 = t;
@@ -1021,12 +1021,12 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
             g->means, g->quats, g->scales, g->opacities, g->sh, g->sh_dtype, g->sh_degree, g->cov3d, Ng, dcams,
             ncams, ts, tiles_x, tiles_per_cam, fr->grec.as<GRec>(), mixed ? fr->grec.as<GRec16>() : nullptr,
             fr->bin.as<BinInfo>(), Ntot, reinterpret_cast<unsigned*>(fr->status.as<int32_t>() + 3),
-            fr->fix_list.as<int64_t>(), fix_cap);
+            fr->fix_list.as<int64_t>(), fix_cap), count_launch();
         UMGS_TRY(cudaGetLastError());
         refine_conics_kernel<<<4 * ctx->num_sms, 128, 0, stream>>>(
             g->means, g->quats, g->scales, g->cov3d, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot,
             reinterpret_cast<unsigned*>(fr->status.as<int32_t>() + 3), fr->fix_list.as<int64_t>(), fix_cap,
-            fr->grec.as<GRec>(), mixed ? fr->grec.as<GRec16>() : nullptr);
+            fr->grec.as<GRec>(), mixed ? fr->grec.as<GRec16>() : nullptr), count_launch();
         UMGS_TRY(cudaGetLastError());
     }
     if (Ng > 0) {
@@ -1034,10 +1034,10 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
         const unsigned gb = grid_for(Ng, 256);
         GRec16* g16 = mixed ? fr->grec.as<GRec16>() : nullptr;
         switch (g->sh_degree) {
-            case 0: shade_gaussians_kernel<0><<<gb, 256, 0, stream>>>(g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16); break;
-            case 1: shade_gaussians_kernel<1><<<gb, 256, 0, stream>>>(g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16); break;
-            case 2: shade_gaussians_kernel<2><<<gb, 256, 0, stream>>>(g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16); break;
-            default: shade_gaussians_kernel<3><<<gb, 256, 0, stream>>>(g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16); break;
+            case 0: shade_gaussians_kernel<0><<<gb, 256, 0, stream>>>(g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16), count_launch(); break;
+            case 1: shade_gaussians_kernel<1><<<gb, 256, 0, stream>>>(g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16), count_launch(); break;
+            case 2: shade_gaussians_kernel<2><<<gb, 256, 0, stream>>>(g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16), count_launch(); break;
+            default: shade_gaussians_kernel<3><<<gb, 256, 0, stream>>>(g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16), count_launch(); break;
         }
         UMGS_TRY(cudaGetLastError());
     }
@@ -1049,7 +1049,7 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
             setup_triangles_kernel<<<grid_for(me.nf, 256), 256, 0, stream>>>(
                 me.verts, me.faces, me.vcolor, me.valpha, me.falpha, me.nv, me.nf, tri_base, Nt, Ng + tri_base,
                 dcams, ncams, ts, tiles_x, tiles_per_cam, fr->trec.as<TRec>(), fr->bin.as<BinInfo>(), Ntot,
-                fr->status.as<int32_t>());
+                fr->status.as<int32_t>()), count_launch();
             UMGS_TRY(cudaGetLastError());
         }
         tri_base += me.nf;
@@ -1067,7 +1067,7 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     uint32_t* status_u = reinterpret_cast<uint32_t*>(fr->status.as<int32_t>());
     if (NR > 0) {
         StageTimer tm(ctx, UMGS_STAGE_SCAN, stream);
-        prim_keys_kernel<<<grid_for(NR, 256), 256, 0, stream>>>(fr->bin.as<BinInfo>(), NR, pk, pv, status_u + 5);
+        prim_keys_kernel<<<grid_for(NR, 256), 256, 0, stream>>>(fr->bin.as<BinInfo>(), NR, pk, pv, status_u + 5), count_launch();
         UMGS_TRY(cudaGetLastError());
         uint32_t* rk = nullptr;
         uint32_t* rv = nullptr;
@@ -1076,7 +1076,7 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
         pk = rk;
         pv = rv;
         tile_counts_kernel<<<grid_for(NR, 256), 256, 0, stream>>>(fr->bin.as<BinInfo>(), pv, NR, ts,
-                                                                  fr->pcnt.as<uint32_t>());
+                                                                  fr->pcnt.as<uint32_t>()), count_launch();
         UMGS_TRY(scan_u32(fr, fr->pcnt.as<uint32_t>(), fr->poff.as<uint32_t>(), NR, status_u + 1, stream));
     }
     int64_t Kcap;
@@ -1105,7 +1105,7 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
         StageTimer tm(ctx, UMGS_STAGE_SCATTER, stream);
         emit_pairs_kernel<<<grid_for(NR, 256), 256, 0, stream>>>(fr->bin.as<BinInfo>(), pv, fr->poff.as<uint32_t>(), NR,
                                                                  Ntot, ts, tiles_x, tiles_per_cam, fr->tk.as<uint32_t>(),
-                                                                 fr->tv.as<uint32_t>(), Kcap, fr->status.as<int32_t>());
+                                                                 fr->tv.as<uint32_t>(), Kcap, fr->status.as<int32_t>()), count_launch();
         UMGS_TRY(cudaGetLastError());
     }
     {
@@ -1121,7 +1121,7 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
             fr->ids = rv;
         }
         tile_ranges_kernel<<<grid_for(M + 1, 256), 256, 0, stream>>>(fr->tkeys, status_u + 1, Kcap, M,
-                                                                     fr->tile_off.as<int64_t>());
+                                                                     fr->tile_off.as<int64_t>()), count_launch();
         UMGS_TRY(cudaGetLastError());
     }
     UMGS_TRY(fr->last.reserve(sizeof(int32_t) * (int64_t)ncams * W * H));
@@ -1148,7 +1148,7 @@ umgs_status frame_lists(const umgs_frame* fr, int64_t* tile_ptr, int32_t* ids, u
     if (fr->num_keys > 0) {
         lists_kernel<<<grid_for(fr->num_keys, 256), 256, 0, stream>>>(
             fr->tkeys, fr->ids, fr->num_keys, fr->bin.as<BinInfo>(), fr->ng + fr->nt, fr->tiles_x * fr->tiles_y, ids,
-            dbits);
+            dbits), count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(fr->ctx, e, "lists_kernel");
     }

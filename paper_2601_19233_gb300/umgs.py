@@ -117,6 +117,8 @@ def lib():
             getattr(L, name).restype = ctypes.c_int
         L.umgs_profile_enable.argtypes = [vp, i32]
         L.umgs_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
+        L.umgs_kernel_launches.argtypes = []
+        L.umgs_kernel_launches.restype = ctypes.c_longlong
         for name in ("umgs_profile_enable", "umgs_profile_read", "umgs_ctx_create", "umgs_frame_create", "umgs_render", "umgs_frame_counts",
                      "umgs_frame_lists", "umgs_ctx_sync", "umgs_deform", "umgs_deform_vertex_table"):
             getattr(L, name).restype = ctypes.c_int
@@ -348,6 +350,11 @@ NUM_STAGES = 16
 
 def profile_enable(ctx: Context, on=True):
     ctx.check(lib().umgs_profile_enable(ctx._h, 1 if on else 0), "umgs_profile_enable")
+
+
+def kernel_launches() -> int:
+    """umgs_kernel_launches: kernels launched by the library in this process so far."""
+    return int(lib().umgs_kernel_launches())
 
 
 def profile_read(ctx: Context):

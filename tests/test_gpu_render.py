@@ -161,3 +161,15 @@ def test_evaluation_count_matches_oracle(ctx):
     # termination ties may move the cut by a few entries on a tie pixel
     assert abs(got - total) <= int(ref["tie"].sum()) * int(per_pix.max())
     assert total > 10000
+
+
+def test_kernel_launch_counter(ctx):
+    # every render launches the projection, shading, triangle setup, the
+    # binning kernels and the compositor; the library counts them
+    from paper_2601_19233_gb300 import umgs
+    sc = S.config0()
+    gpu_render(ctx, sc)
+    n0 = umgs.kernel_launches()
+    gpu_render(ctx, sc)
+    n1 = umgs.kernel_launches()
+    assert 15 <= n1 - n0 <= 60
