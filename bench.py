@@ -248,10 +248,42 @@ def run_umgs(args, rank, world, local_rank):
     h2d = int(host_vd[0].numel() * 4)
     d2h = int(host_out.numel() * 4)
 
+    # fragment counts of the last frame: N_alg (evaluations: (pixel, record)
+    # pairs whose footprint holds the pixel, up to termination, counted on the
+    # device) and the tile-granularity pairs (list length x pixels of the tile)
+    evals = frame.evaluations()
+    tptr, _, _ = frame.lists()
+    tl = (tptr[1:] - tptr[:-1]).double()
+    ts = 16
+    tx_n = (W + ts - 1) // ts
+    tix = torch.arange(tl.numel(), device=dev)
+    tw = torch.clamp(W - (tix % tx_n) * ts, max=ts).double()
+    th = torch.clamp(H - (tix // tx_n) * ts, max=ts).double()
+    tile_pairs = int((tl * tw * th).sum().item())
+
+    # mesh-added vs Gaussians-only (and mesh-only) render time of the same frame
+    def t_render(gg, mm, k=max(5, K // 4)):
+        for _ in range(3):
+            umgs.render(ctx, gg, mm, [cam], opts, out=out, frame=frame)
+        torch.cuda.synchronize()
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        r0.record()
+        for _ in range(k):
+            umgs.render(ctx, gg, mm, [cam], opts, out=out, frame=frame)
+        r1.record()
+        torch.cuda.synchronize()
+        return r0.elapsed_time(r1) / k
+    render_ms = {"gaussians_and_mesh": round(t_render(gdef, [mesh]), 4),
+                 "gaussians_only": round(t_render(gdef, []), 4),
+                 "mesh_only": round(t_render(None, [mesh]), 4)}
+
     names = stage_names()
     stages = {names[k]: {"ms_per_launch": stage_ms[k] / stage_n[k], "launches": int(stage_n[k])}
               for k in range(16) if stage_n[k] > 0}
-    roof = roofline(stages, nkeys, n, sc, clk, frame.evaluations())
+    roof = roofline(stages, nkeys, n, sc, clk, evals, ms_step)
+    comp_ms = stages["composite"]["ms_per_launch"] if "composite" in stages else float("nan")
+    frags = {"n_alg": int(evals), "mfragments_per_s": round(evals / comp_ms / 1e3, 1),
+             "tile_pairs": tile_pairs, "tile_pairs_over_n_alg": round(tile_pairs / max(evals, 1), 3)}
     res = {
         "metric": METRIC, "value": round(value, 3), "unit": "frames/s", "n_gpus": world, "steps": K,
         "warmup": Wm, "ms_per_step": round(ms_step, 4), "higher_is_better": True, "scaling": "weak",
@@ -268,6 +300,8 @@ def run_umgs(args, rank, world, local_rank):
                     "steps": Kb, "backward_stages_ms": {names[k]: round(fb_stage_ms[k] / fb_stage_n[k], 4)
                                                         for k in (12, 13) if fb_stage_n[k] > 0}},
         "bind_s": round(bind_s, 3),
+        "fragments": frags,
+        "render_ms": render_ms,
         "roofline": roof,
         "clocks": clk,
     }
@@ -281,7 +315,7 @@ def run_umgs(args, rank, world, local_rank):
         torch.distributed.destroy_process_group()
 
 
-def roofline(stages, nkeys, n, sc, clk, evals):
+def roofline(stages, nkeys, n, sc, clk, evals, ms_step):
     """Roofline of the dominant stage, plus HBM figures of the streaming stages.
 
     composite: ALU-bound; algorithmic work = 12 FP32 operations per
@@ -298,12 +332,20 @@ def roofline(stages, nkeys, n, sc, clk, evals):
     hbm = peaks.get("hbm_gbs", 6800.0)
     hsrc = "measured hbm_gbs" if "hbm_gbs" in peaks else "fallback 6.8 TB/s"
     ng, nt = n, sc.meshes[0].nf
+    npf, npv = int(sc.proxy_faces.shape[0]), int(sc.proxy_verts.shape[0])
     alg = {  # algorithmic bytes per launch
         "project_gaussians": ng * (12 + 28 + 4 + 36 + 16),
         "shade_gaussians": ng * (192 + 12 + 16 + 12),
         "setup_triangles": nt * (12 + 16 + 160 + 16) + sc.meshes[0].nv * 28,
         "deform_gaussians": ng * (96 + 40 + 36),
+        "deform_faces": npf * (12 + 72) + npv * 40,
+        "deform_vertices": npv * (40 + 24 + 48),
+        # records: info read, (depth, id) pair written, one read+write of the
+        # pair (a single sort pass), tile count and offset written
+        "scan": (ng + nt) * (16 + 8 + 16 + 8),
         "scatter": nkeys * 8,
+        # one read and one write of every (tile, id) pair, tile ranges read
+        "sort": nkeys * (16 + 4),
     }
     hbm_stages = {}
     for k, b in alg.items():
@@ -312,19 +354,42 @@ def roofline(stages, nkeys, n, sc, clk, evals):
             hbm_stages[k] = {"achieved_gbs": round(b / t / 1e9, 1), "frac": round(b / t / 1e9 / hbm, 4)}
     dom = max(stages, key=lambda k: stages[k]["ms_per_launch"])
     t = stages[dom]["ms_per_launch"] * 1e-3
+    mhz = clk.get("sm_mhz") or 2070.0
+    peak_alu = 2 * 128 * 152 * mhz * 1e6 / 1e12
+    # whole frame: sum of the per-stage lower bounds against the step time
+    t_bound = sum(b / (hbm * 1e9) for k, b in alg.items() if k in stages)
+    t_bound += 12.0 * evals / (peak_alu * 1e12)
+    frame = {"bound_ms": round(t_bound * 1e3, 4), "ms_per_step": round(ms_step, 4),
+             "frac": round(t_bound * 1e3 / ms_step, 4)}
     if dom == "composite":
-        mhz = clk.get("sm_mhz") or 2070.0
-        peak = 2 * 128 * 152 * mhz * 1e6 / 1e12
         ach = 12.0 * evals / t / 1e12
-        return {"bound": "alu", "stage": dom, "achieved": round(ach, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
-                "frac": round(ach / peak, 4), "traffic": None, "evaluations": int(evals),
-                "work": "12 FP32 ops per (pixel, fragment) evaluation",
+        return {"bound": "alu", "stage": dom, "achieved": round(ach, 3), "peak": round(peak_alu, 2),
+                "unit": "TFLOP/s", "frac": round(ach / peak_alu, 4), "traffic": composite_traffic(),
+                "evaluations": int(evals), "work": "12 FP32 ops per (pixel, fragment) evaluation",
                 "peak_source": "FP32 FMA rate 2x128 lanes x 152 SMs at %.0f MHz (sampled)" % mhz,
-                "hbm_stages": hbm_stages, "hbm_peak_gbs": hbm, "hbm_peak_source": hsrc}
+                "hbm_stages": hbm_stages, "hbm_peak_gbs": hbm, "hbm_peak_source": hsrc, "frame": frame}
     b = alg.get(dom)
     ach = b / t / 1e9 if b else None
     return {"bound": "hbm", "stage": dom, "achieved": ach and round(ach, 1), "peak": hbm, "unit": "GB/s",
-            "frac": ach and round(ach / hbm, 4), "traffic": None, "peak_source": hsrc, "hbm_stages": hbm_stages}
+            "frac": ach and round(ach / hbm, 4), "traffic": None, "peak_source": hsrc, "hbm_stages": hbm_stages,
+            "frame": frame}
+
+
+def composite_traffic():
+    """DRAM bytes per launch of the compositor from the committed ncu summary
+    (profiles/composite_1080p.md, line `traffic_bytes_per_launch: B source_sha256: H`),
+    or None when render.cu has changed since those counters were taken."""
+    import hashlib
+    try:
+        src = hashlib.sha256(open(os.path.join(ROOT, "paper_2601_19233_gb300", "csrc", "render.cu"), "rb").read())
+        for line in open(os.path.join(ROOT, "profiles", "composite_1080p.md")):
+            if line.startswith("traffic_bytes_per_launch:"):
+                parts = line.split()
+                if parts[3] == src.hexdigest():
+                    return int(parts[1])
+    except Exception:
+        pass
+    return None
 
 
 # ----------------------------------------------------------------------------

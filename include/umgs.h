@@ -93,9 +93,12 @@ typedef struct {
 /* umgs_render_opts.flags */
 enum {
     UMGS_RENDER_SAVE_BACKWARD = 1,  /* keep per-pixel state for umgs_render_backward (FULL mode) */
-    UMGS_RENDER_MIXED = 2           /* Gaussian fragment records in fp16 (screen position fp32), fp32
+    UMGS_RENDER_MIXED = 2,          /* Gaussian fragment records in fp16 (screen position fp32), fp32
                                        blending; pair with bf16 SH for the mixed-precision form.  Keys,
                                        footprints and order are unchanged (still exact); no backward. */
+    UMGS_RENDER_T_PRODUCT = 4       /* FULL mode only: inside an entity T <- T (1 - O_i alpha_i), the
+                                       literal reading of Sec. 3.2's Eq. 6 instead of T = T_in mean_j t^j
+                                       (the two agree for one-triangle entities); no backward. */
 };
 
 typedef struct {
@@ -184,8 +187,9 @@ umgs_status umgs_frame_counts(const umgs_frame* frame, int64_t* num_keys, int64_
 /* Number of (pixel, fragment) evaluations of the last render into `frame`:
  * for every pixel, the entries of its tile list whose footprint (Gaussian
  * pixel rect, triangle pixel rect) holds the pixel, up to and including the
- * one after which T < t_eps.  The algorithmic work unit of the compositor.
- * Host output; synchronises `stream`. */
+ * one after which T < t_eps.  The algorithmic work unit of the compositor
+ * (N_alg).  Counted by one diagnostic kernel over the saved tile lists (the
+ * render itself counts nothing); host output; synchronises `stream`. */
 umgs_status umgs_frame_evaluations(const umgs_frame* frame, int64_t* evals, void* stream);
 
 /* Copy the sorted tile lists of the last render into caller buffers (device):

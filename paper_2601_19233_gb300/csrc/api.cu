@@ -152,6 +152,9 @@ umgs_status umgs_render(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_mesh*
     if (opts.tile_size != 8 && opts.tile_size != 16 && opts.tile_size != 32)
         return fail(ctx, UMGS_ERR_INVALID_ARG, "tile_size must be 8, 16 or 32");
     if (opts.blend_mode < 0 || opts.blend_mode > 3) return fail(ctx, UMGS_ERR_INVALID_ARG, "unknown blend_mode");
+    if ((opts.flags & UMGS_RENDER_T_PRODUCT) &&
+        (opts.blend_mode != UMGS_BLEND_FULL || (opts.flags & UMGS_RENDER_SAVE_BACKWARD)))
+        return fail(ctx, UMGS_ERR_INVALID_ARG, "UMGS_RENDER_T_PRODUCT needs FULL mode and no saved backward state");
     if (!cams || ncams < 1) return fail(ctx, UMGS_ERR_INVALID_ARG, "need at least one camera");
     if (!out_rgbt) return fail(ctx, UMGS_ERR_INVALID_ARG, "out_rgbt is NULL");
     if (nmeshes < 0 || (nmeshes > 0 && !meshes)) return fail(ctx, UMGS_ERR_INVALID_ARG, "bad mesh array");
@@ -277,13 +280,8 @@ umgs_status umgs_frame_counts(const umgs_frame* frame, int64_t* num_keys, int64_
 
 umgs_status umgs_frame_evaluations(const umgs_frame* frame, int64_t* evals, void* stream) {
     if (!frame || !evals || !frame->valid) return UMGS_ERR_INVALID_ARG;
-    unsigned long long v = 0;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (cudaMemcpyAsync(&v, frame->status.as<int32_t>() + 6, sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-        return UMGS_ERR_CUDA;
-    *evals = (int64_t)v;
-    return UMGS_OK;
+    if (cudaSetDevice(frame->ctx->device) != cudaSuccess) return fail(frame->ctx, UMGS_ERR_CUDA, "cudaSetDevice");
+    return frame_evaluations(frame, evals, static_cast<cudaStream_t>(stream));
 }
 
 umgs_status umgs_frame_lists(const umgs_frame* frame, int64_t* tile_ptr, int32_t* ids, uint32_t* dbits,

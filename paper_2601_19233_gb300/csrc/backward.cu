@@ -60,8 +60,9 @@ __device__ __forceinline__ void warp_sum_transpose(float (&v)[V], int lane) {
 
 template <int TS>
 __global__ void __launch_bounds__(TS * TS) composite_bwd_kernel(
-    const uint32_t* __restrict__ ids, const int64_t* __restrict__ off, const GRec* __restrict__ grec,
-    const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x, int tiles_per_cam, int W, int H, float bg0,
+    const uint32_t* __restrict__ ids, const int64_t* __restrict__ off,
+    const GRec* __restrict__ grec, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
+    int tiles_per_cam, int W, int H, float bg0,
     float bg1, float bg2, const float4* __restrict__ dout, const int32_t* __restrict__ last,
     const float* __restrict__ tfin, const int32_t* __restrict__ ntri, const float4* __restrict__ stack, int64_t npix,
     float* __restrict__ ggrad, float* __restrict__ tgrad) {
@@ -78,7 +79,9 @@ __global__ void __launch_bounds__(TS * TS) composite_bwd_kernel(
     const int cam = tile / tiles_per_cam;
     const int lt = tile - cam * tiles_per_cam;
     const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
-    const int px = tx * TS + (threadIdx.x % TS), py = ty * TS + (threadIdx.x / TS);
+    int lx, ly;
+    block_pixel<TS>(threadIdx.x, lx, ly);
+    const int px = tx * TS + lx, py = ty * TS + ly;
     const bool inside = px < W && py < H;
     const int64_t beg = off[tile];
     const GRec* G = grec + (int64_t)cam * Ng;
@@ -91,7 +94,7 @@ __global__ void __launch_bounds__(TS * TS) composite_bwd_kernel(
     int nlast = 0, sp = 0;
     float T = 1.f, U = 0.f, gr = 0.f, gg = 0.f, gb = 0.f;
     if (inside) {
-        nlast = last[pix];
+        nlast = last[pix] & 0x7fffffff;  // bit 31: stopped at T < t_eps
         sp = ntri[pix];
         T = tfin[pix];
         const float4 d = dout[pix];
@@ -113,7 +116,7 @@ __global__ void __launch_bounds__(TS * TS) composite_bwd_kernel(
     __syncthreads();
     const int maxlast = s_max;
     const int wmaxlast = s_wmax[warp];
-    const int tile_y0 = ty * TS, tile_x0 = tx * TS;
+    const int tile_x0 = tx * TS, tile_y0 = ty * TS;
 
     for (int bend = maxlast; bend > 0; bend -= kBatchB) {
         const int b0 = max(0, bend - kBatchB);
@@ -122,45 +125,21 @@ __global__ void __launch_bounds__(TS * TS) composite_bwd_kernel(
         for (int k = threadIdx.x; k < n; k += NT) {
             const uint32_t id = ids[beg + b0 + k];
             s_id[k] = id;
-            uint32_t rx, ry;
-            int bx0, bx1, by0, by1;
             if (id < Ng) {
                 const float4* src = reinterpret_cast<const float4*>(G + id);
                 const float4 a = src[0], q1 = src[1], c = src[2];
                 s_rec[k][0] = a; s_rec[k][1] = q1; s_rec[k][2] = c;
-                rx = __float_as_uint(c.y);
-                ry = __float_as_uint(c.z);
-                bx0 = (int)(rx & 0xffff); bx1 = (int)(rx >> 16); by0 = (int)(ry & 0xffff); by1 = (int)(ry >> 16);
-                // box of the alpha >= 1/255 ellipse, widened (conservative), as in the forward
-                const float A = -2.f * kLn2 * a.z, B = -kLn2 * a.w, Cq = -2.f * kLn2 * q1.x;
-                const float det = A * Cq - B * B;
-                const float L = __logf(255.f * q1.y);
-                if (!(L > 0.f) || !(det > 0.f)) {
-                    bx0 = 1; bx1 = 0;
-                } else {
-                    const float ex = sqrtf(2.f * L * Cq / det) * 1.01f + 0.5f;
-                    const float ey = sqrtf(2.f * L * A / det) * 1.01f + 0.5f;
-                    bx0 = max(bx0, (int)floorf(a.x - ex - 0.5f));
-                    bx1 = min(bx1, (int)ceilf(a.x + ex - 0.5f));
-                    by0 = max(by0, (int)floorf(a.y - ey - 0.5f));
-                    by1 = min(by1, (int)ceilf(a.y + ey - 0.5f));
-                }
+                const uint32_t rx = __float_as_uint(c.y), ry = __float_as_uint(c.z);
+                s_wmask[k] = gauss_block_mask<TS>(a.x, a.y, a.z, a.w, q1.x, q1.y, (int)(rx & 0xffff), (int)(rx >> 16),
+                                                  (int)(ry & 0xffff), (int)(ry >> 16), tile_x0, tile_y0);
             } else {
                 const float4* src = reinterpret_cast<const float4*>(TR + (id - Ng));
 #pragma unroll
                 for (int q = 0; q < 10; ++q) s_rec[k][q] = src[q];
                 const TRec& tr = *reinterpret_cast<const TRec*>(&s_rec[k][0]);
-                bx0 = (int)(tr.rx & 0xffff); bx1 = (int)(tr.rx >> 16); by0 = (int)(tr.ry & 0xffff); by1 = (int)(tr.ry >> 16);
+                s_wmask[k] = box_block_mask<TS>((int)(tr.rx & 0xffff), (int)(tr.rx >> 16), (int)(tr.ry & 0xffff),
+                                                (int)(tr.ry >> 16), tile_x0, tile_y0);
             }
-            uint32_t wm = 0;
-            if (bx0 <= bx1 && bx0 <= tile_x0 + TS - 1 && bx1 >= tile_x0) {
-                const int r0 = max(by0 - tile_y0, 0), r1 = min(by1 - tile_y0, TS - 1);
-                if (r0 <= r1) {
-                    const int w0 = (r0 * TS) >> 5, w1 = (r1 * TS + TS - 1) >> 5;
-                    wm = ((2u << w1) - 1u) & ~((1u << w0) - 1u);
-                }
-            }
-            s_wmask[k] = wm;
 #pragma unroll
             for (int e = 0; e < 22; ++e) s_acc[k][e] = 0.f;
         }

@@ -113,4 +113,68 @@ constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kLog2e = 1.4426950408889634f;
 
+// ---- warp <-> pixel layout of the compositors -------------------------------
+// Warp w of a TS x TS tile (TS = 8, 16, 32) owns the 8 x 4 pixel block
+// (w % (TS/8), w / (TS/8)); lane l is pixel (l % 8, l / 8) of that block.
+// Near-square blocks let a record skip every warp whose block its footprint
+// misses (the compositors build per-warp record lists from these masks).
+template <int TS>
+__device__ __forceinline__ void block_pixel(int t, int& lx, int& ly) {
+    const int w = t >> 5, l = t & 31;
+    lx = (w % (TS / 8)) * 8 + (l & 7);
+    ly = (w / (TS / 8)) * 4 + (l >> 3);
+}
+
+// Warps (8 x 4 blocks) of the tile with origin (tx0, ty0) that meet the pixel
+// box [x0,x1] x [y0,y1].
+template <int TS>
+__device__ __forceinline__ uint32_t box_block_mask(int x0, int x1, int y0, int y1, int tx0, int ty0) {
+    x0 = max(x0, tx0); x1 = min(x1, tx0 + TS - 1);
+    y0 = max(y0, ty0); y1 = min(y1, ty0 + TS - 1);
+    if (x0 > x1 || y0 > y1) return 0u;
+    const int wx0 = (x0 - tx0) >> 3, wx1 = (x1 - tx0) >> 3, wy0 = (y0 - ty0) >> 2, wy1 = (y1 - ty0) >> 2;
+    const uint32_t cols = ((2u << wx1) - 1u) & ~((1u << wx0) - 1u);
+    uint32_t m = 0u;
+    for (int wy = wy0; wy <= wy1; ++wy) m |= cols << (wy * (TS / 8));
+    return m;
+}
+
+// Warps (8 x 4 blocks, see block_pixel) of the tile with origin (tx0, ty0)
+// whose pixels can hold a fragment of a Gaussian record with projected mean
+// (u, v), base-2 conic (ca, cb, cc) (alpha = o 2^p2, p2 = ca dx^2 + cb dx dy +
+// cc dy^2), opacity o and pixel rect [x0,x1] x [y0,y1].  A fragment needs
+// the pixel in the rect and alpha >= 1/255, i.e. d = (dx, dy) inside the
+// ellipse d^T Q d <= lim with Q = -[[ca, cb/2], [cb/2, cc]], lim =
+// log2(255 o).  The ellipse lies inside the octagon bounded by its support
+// in the directions x, y, x + y and x - y (h(n)^2 = lim n^T Q^-1 n); a block
+// is kept when its pixel-centre rectangle meets that octagon.  The bounds
+// are widened by 2% of lim plus 1% + 0.01 px, far beyond the rounding of this
+// test and of the compositor's own alpha.  o < 1/255: no fragment; a conic
+// that is not positive definite keeps every block of the rect.
+template <int TS>
+__device__ __forceinline__ uint32_t gauss_block_mask(float u, float v, float ca, float cb, float cc, float o, int x0,
+                                                     int x1, int y0, int y1, int tx0, int ty0) {
+    if (!(o >= kAlphaMin)) return 0u;
+    const float qa = -ca, qb = -0.5f * cb, qc = -cc, det = qa * qc - qb * qb;
+    if (!(qa > 0.f && qc > 0.f && det > 0.f)) return box_block_mask<TS>(x0, x1, y0, y1, tx0, ty0);
+    const float s = (__log2f(255.f * o) * 1.02f + 1e-4f) / det;  // lim Q^-1 = s [[qc, -qb], [-qb, qa]]
+    const float hx = sqrtf(s * qc) * 1.01f + 0.01f, hy = sqrtf(s * qa) * 1.01f + 0.01f;
+    const float hp = sqrtf(s * (qc + qa - 2.f * qb)) * 1.01f + 0.01f;  // direction x + y
+    const float hm = sqrtf(s * (qc + qa + 2.f * qb)) * 1.01f + 0.01f;  // direction x - y
+    x0 = max(max(x0, (int)floorf(u - hx - 0.5f)), tx0); x1 = min(min(x1, (int)ceilf(u + hx - 0.5f)), tx0 + TS - 1);
+    y0 = max(max(y0, (int)floorf(v - hy - 0.5f)), ty0); y1 = min(min(y1, (int)ceilf(v + hy - 0.5f)), ty0 + TS - 1);
+    if (x0 > x1 || y0 > y1) return 0u;
+    const int wx0 = (x0 - tx0) >> 3, wx1 = (x1 - tx0) >> 3, wy0 = (y0 - ty0) >> 2, wy1 = (y1 - ty0) >> 2;
+    uint32_t m = 0u;
+    for (int wy = wy0; wy <= wy1; ++wy) {
+        const float Y0 = (float)max(y0, ty0 + 4 * wy) + 0.5f - v, Y1 = (float)min(y1, ty0 + 4 * wy + 3) + 0.5f - v;
+        for (int wx = wx0; wx <= wx1; ++wx) {
+            const float X0 = (float)max(x0, tx0 + 8 * wx) + 0.5f - u;
+            const float X1 = (float)min(x1, tx0 + 8 * wx + 7) + 0.5f - u;
+            if (X1 + Y1 >= -hp && X0 + Y0 <= hp && X1 - Y0 >= -hm && X0 - Y1 <= hm) m |= 1u << (wy * (TS / 8) + wx);
+        }
+    }
+    return m;
+}
+
 }  // namespace umgs

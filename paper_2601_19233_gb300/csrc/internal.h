@@ -146,6 +146,7 @@ umgs_status render_backward(umgs_ctx* ctx, umgs_frame* fr, const umgs_gaussians*
                             int32_t nmeshes, const float* dL_drgbt, const umgs_gaussian_grads* gg,
                             const umgs_mesh_grads* mg, cudaStream_t stream);
 
+umgs_status frame_evaluations(const umgs_frame* fr, int64_t* evals, cudaStream_t stream);
 umgs_status frame_lists(const umgs_frame* fr, int64_t* tile_ptr, int32_t* ids, uint32_t* dbits,
                         cudaStream_t stream);
 

@@ -19,6 +19,7 @@
 //      for entities of depth-adjacent triangles) and the CTA stops when
 //      every pixel has T < t_eps (block-wide vote).
 #include <cstdio>
+#include <cstring>
 #include <cmath>
 #include <algorithm>
 
@@ -463,6 +464,7 @@ __global__ void tile_counts_kernel(const BinInfo* __restrict__ bin, const uint32
     cnt[i] = tiles_of(bin[pv[i]], ts);
 }
 
+// One thread per depth-sorted record: its (tile, id) pairs in row-major tile order.
 __global__ void emit_pairs_kernel(const BinInfo* __restrict__ bin, const uint32_t* __restrict__ pv,
                                   const uint32_t* __restrict__ off, int64_t n, int64_t ntot, int ts, int tiles_x,
                                   int tiles_per_cam, uint32_t* __restrict__ tk, uint32_t* __restrict__ tv, int64_t cap,
@@ -521,20 +523,28 @@ struct PixelState {
 // the number of covering triangle fragments, and per covering triangle
 // fragment the four sub-sample transmittances before it (scaled by T_in/4)
 // in a per-pixel stack of capacity `cap` (`need` records the largest count).
-template <int TS, bool SAVE>
+// MODE: UMGS_BLEND_* or kModeTProduct (FULL with the literal Eq. 6
+// transmittance T <- T (1 - O_i alpha_i) inside an entity).
+constexpr int kModeTProduct = 4;
+
+template <int TS, bool SAVE, int MODE>
 __device__ __forceinline__ void composite_tile(
     int tile, float4 (*__restrict__ s_rec)[10], uint32_t* __restrict__ s_id, uint32_t* __restrict__ s_wmask,
     uint8_t* __restrict__ s_list,
-    const uint32_t* __restrict__ ids, const int64_t* __restrict__ off, const GRec* __restrict__ grec,
+    const uint32_t* __restrict__ ids, const int64_t* __restrict__ off,
+    const GRec* __restrict__ grec,
     const GRec16* __restrict__ grec16, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
-    int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, int mode, float4* __restrict__ out, int32_t* __restrict__ out_last,
+    int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, float4* __restrict__ out, int32_t* __restrict__ out_last,
     float* __restrict__ out_tfin, int32_t* __restrict__ out_ntri, float4* __restrict__ stack, int cap,
-    int64_t npix, int32_t* __restrict__ need, unsigned long long* __restrict__ eval_count) {
+    int64_t npix, int32_t* __restrict__ need) {
     constexpr int NT = TS * TS;
+    constexpr int mode = MODE;
     const int cam = tile / tiles_per_cam;
     const int lt = tile - cam * tiles_per_cam;
     const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
-    const int px = tx * TS + (threadIdx.x % TS), py = ty * TS + (threadIdx.x / TS);
+    int lx, ly;
+    block_pixel<TS>(threadIdx.x, lx, ly);
+    const int px = tx * TS + lx, py = ty * TS + ly;
     const bool inside = px < W && py < H;
     const int64_t beg = off[tile], end = off[tile + 1];
     const GRec* G = grec + (int64_t)cam * Ng;
@@ -551,23 +561,21 @@ __device__ __forceinline__ void composite_tile(
     bool done = !inside;
     int last = 0;
     int sp = 0;
-    unsigned nevals = 0;  // (pixel, fragment) pairs whose footprint holds the pixel, up to termination
     const int64_t pix = ((int64_t)cam * H + py) * W + px;
 
-    // warp w covers the tile rows [w*32/TS, (w+1)*32/TS); a record whose rect
-    // misses those rows is skipped by the whole warp with one test
-    constexpr int ROWS_PER_WARP = 32 / TS > 0 ? 32 / TS : 1;
+    // warp w owns one 8 x 4 pixel block of the tile (block_pixel); every
+    // record carries the mask of the blocks that can hold a fragment of it
     const int warp = threadIdx.x >> 5;
-    const int tile_y0 = ty * TS;
+    const int tile_x0 = tx * TS, tile_y0 = ty * TS;
     const float pxf = (float)px, pyf = (float)py;
     constexpr int NB = BatchOf<TS>::value;
     for (int64_t b0 = beg; b0 < end; b0 += NB) {
         if (__syncthreads_count(done) == NT) break;
         const int n = (int)min((int64_t)NB, end - b0);
+        const int lbase = (int)(b0 - beg) + 1;  // list position + 1 of the batch's first record
         for (int k = threadIdx.x; k < n; k += NT) {
             const uint32_t id = ids[b0 + k];
             s_id[k] = id;
-            uint32_t rx, ry;
             if (id < Ng) {
                 float4 a, b, c;
                 if (G16) {  // fp16 record: widen to the fp32 layout
@@ -579,54 +587,21 @@ __device__ __forceinline__ void composite_tile(
                     const float4* src = reinterpret_cast<const float4*>(G + id);
                     a = src[0]; b = src[1]; c = src[2];
                 }
-                rx = __float_as_uint(c.y);
-                ry = __float_as_uint(c.z);
+                const uint32_t rx = __float_as_uint(c.y), ry = __float_as_uint(c.z);
                 s_rec[k][0] = a;
                 s_rec[k][1] = make_float4(b.x, b.y, (float)(rx & 0xffff), (float)(rx >> 16));
                 s_rec[k][2] = make_float4((float)(ry & 0xffff), (float)(ry >> 16), b.z, b.w);
                 s_rec[k][3] = make_float4(c.x, 0.f, 0.f, 0.f);
+                s_wmask[k] = gauss_block_mask<TS>(a.x, a.y, a.z, a.w, b.x, b.y, (int)(rx & 0xffff), (int)(rx >> 16),
+                                                  (int)(ry & 0xffff), (int)(ry >> 16), tile_x0, tile_y0);
             } else {
                 const float4* src = reinterpret_cast<const float4*>(TR + (id - Ng));
 #pragma unroll
                 for (int q = 0; q < 10; ++q) s_rec[k][q] = src[q];
                 const TRec& tr = *reinterpret_cast<const TRec*>(&s_rec[k][0]);
-                rx = tr.rx;
-                ry = tr.ry;
+                s_wmask[k] = box_block_mask<TS>((int)(tr.rx & 0xffff), (int)(tr.rx >> 16), (int)(tr.ry & 0xffff),
+                                                (int)(tr.ry >> 16), tile_x0, tile_y0);
             }
-            // pixel box that can hold a fragment of this record: the rect, and for
-            // a Gaussian also the box of its alpha >= 1/255 ellipse (widened so
-            // rounding can never cut a fragment) -> mask of the warps whose
-            // pixel block meets it
-            int bx0 = (int)(rx & 0xffff), bx1 = (int)(rx >> 16), by0 = (int)(ry & 0xffff), by1 = (int)(ry >> 16);
-            if (id < Ng) {
-                const float4 a = s_rec[k][0], b = s_rec[k][1];
-                const float o = b.y;
-                // conic Q = [[A B][B C]] from the base-2 scaled record
-                const float A = -2.f * 0.6931471805599453f * a.z, B = -0.6931471805599453f * a.w,
-                            Cq = -2.f * 0.6931471805599453f * b.x;
-                const float det = A * Cq - B * B;
-                const float L = __logf(255.f * o);
-                if (!(L > 0.f) || !(det > 0.f)) {
-                    bx0 = 1; bx1 = 0;  // opacity below 1/255: no fragment anywhere
-                } else {
-                    const float ex = sqrtf(2.f * L * Cq / det) * 1.01f + 0.5f;
-                    const float ey = sqrtf(2.f * L * A / det) * 1.01f + 0.5f;
-                    bx0 = max(bx0, (int)floorf(a.x - ex - 0.5f));
-                    bx1 = min(bx1, (int)ceilf(a.x + ex - 0.5f));
-                    by0 = max(by0, (int)floorf(a.y - ey - 0.5f));
-                    by1 = min(by1, (int)ceilf(a.y + ey - 0.5f));
-                }
-            }
-            uint32_t wm = 0;
-            const int tile_x0 = tx * TS;
-            if (bx0 <= bx1 && bx0 <= tile_x0 + TS - 1 && bx1 >= tile_x0) {
-                const int r0 = max(by0 - tile_y0, 0), r1 = min(by1 - tile_y0, TS - 1);
-                if (r0 <= r1) {
-                    const int w0 = (r0 * TS) >> 5, w1 = (r1 * TS + TS - 1) >> 5;
-                    wm = ((2u << w1) - 1u) & ~((1u << w0) - 1u);
-                }
-            }
-            s_wmask[k] = wm;
         }
         __syncthreads();
         if (__any_sync(0xffffffffu, !done)) {
@@ -648,7 +623,6 @@ __device__ __forceinline__ void composite_tile(
                 if (id < Ng) {
                     const float4 q1 = s_rec[k][1], q2 = s_rec[k][2];
                     if (pxf < q1.z || pxf > q1.w || pyf < q2.x || pyf > q2.y) continue;
-                    ++nevals;
                     const float4 q0 = s_rec[k][0];
                     const float dx = __fsub_rn(qx, q0.x), dy = __fsub_rn(qy, q0.y);
                     const float p2 = gauss_power2(q0.z, q0.w, q1.x, dx, dy);
@@ -664,7 +638,6 @@ __device__ __forceinline__ void composite_tile(
                     if (px < (int)(t.rx & 0xffff) || px > (int)(t.rx >> 16) || py < (int)(t.ry & 0xffff) ||
                         py > (int)(t.ry >> 16))
                         continue;
-                    ++nevals;
                     long long E[3];
 #pragma unroll
                     for (int e = 0; e < 3; ++e) E[e] = (long long)t.A[e] * scx + (long long)t.B[e] * scy + t.C[e];
@@ -741,23 +714,19 @@ __device__ __forceinline__ void composite_tile(
                         for (int j = 0; j < 4; ++j)
                             if ((mask >> j) & 1) st.t[j] *= (1.f - a);
                         const float tm = 0.25f * ((st.t[0] + st.t[1]) + (st.t[2] + st.t[3]));
-                        st.T = (mode == UMGS_BLEND_ENTITY_ALL) ? st.Tin * tm * st.g_since : st.Tin * tm;
+                        if (mode == kModeTProduct) st.T *= (1.f - O * a);
+                        else st.T = (mode == UMGS_BLEND_ENTITY_ALL) ? st.Tin * tm * st.g_since : st.Tin * tm;
                     }
                 }
-                last = (int)(b0 - beg) + k + 1;
+                last = lbase + k;
                 if (st.T < t_eps) done = true;
             }
         }
     }
-    {
-        unsigned s = nevals;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if ((threadIdx.x & 31) == 0 && s) atomicAdd(eval_count, (unsigned long long)s);
-    }
     if (inside) {
         out[pix] = make_float4(st.C[0] + st.T * bg0, st.C[1] + st.T * bg1, st.C[2] + st.T * bg2, st.T);
-        if (out_last) out_last[pix] = last;
+        // bit 31: the pixel stopped at T < t_eps after list position `last`
+        if (out_last) out_last[pix] = last | (st.T < t_eps ? (int)0x80000000u : 0);
         if (SAVE) {
             out_tfin[pix] = st.T;
             out_ntri[pix] = sp;
@@ -768,31 +737,31 @@ __device__ __forceinline__ void composite_tile(
 
 
 // one CTA per tile (grid launch)
-template <int TS, bool SAVE>
+template <int TS, bool SAVE, int MODE>
 __global__ void __launch_bounds__(TS * TS) composite_kernel(
     const uint32_t* __restrict__ ids, const int64_t* __restrict__ off, const GRec* __restrict__ grec,
     const GRec16* __restrict__ grec16, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
-    int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, int mode, float4* __restrict__ out, int32_t* __restrict__ out_last,
+    int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, float4* __restrict__ out, int32_t* __restrict__ out_last,
     float* __restrict__ out_tfin, int32_t* __restrict__ out_ntri, float4* __restrict__ stack, int cap,
-    int64_t npix, int32_t* __restrict__ need, unsigned long long* __restrict__ eval_count) {
+    int64_t npix, int32_t* __restrict__ need) {
     constexpr int NB = BatchOf<TS>::value;
     __shared__ float4 s_rec[NB][10];
     __shared__ uint32_t s_id[NB];
     __shared__ uint32_t s_wmask[NB];
     __shared__ uint8_t s_list[(TS * TS / 32) * NB];
-    composite_tile<TS, SAVE>(blockIdx.x, s_rec, s_id, s_wmask, s_list, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, mode, out, out_last, out_tfin, out_ntri, stack, cap, npix, need, eval_count);
+    composite_tile<TS, SAVE, MODE>(blockIdx.x, s_rec, s_id, s_wmask, s_list, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, out, out_last, out_tfin, out_ntri, stack, cap, npix, need);
 }
 
 // persistent launch: resident CTAs take tiles from an atomic queue in the
 // order `order` (decreasing list length: the heaviest tiles start first)
-template <int TS, bool SAVE>
+template <int TS, bool SAVE, int MODE>
 __global__ void __launch_bounds__(TS * TS) composite_persistent_kernel(
     const uint32_t* __restrict__ order, unsigned* __restrict__ work, int64_t M,
     const uint32_t* __restrict__ ids, const int64_t* __restrict__ off, const GRec* __restrict__ grec,
     const GRec16* __restrict__ grec16, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
-    int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, int mode, float4* __restrict__ out, int32_t* __restrict__ out_last,
+    int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, float4* __restrict__ out, int32_t* __restrict__ out_last,
     float* __restrict__ out_tfin, int32_t* __restrict__ out_ntri, float4* __restrict__ stack, int cap,
-    int64_t npix, int32_t* __restrict__ need, unsigned long long* __restrict__ eval_count) {
+    int64_t npix, int32_t* __restrict__ need) {
     constexpr int NB = BatchOf<TS>::value;
     __shared__ float4 s_rec[NB][10];
     __shared__ uint32_t s_id[NB];
@@ -805,7 +774,7 @@ __global__ void __launch_bounds__(TS * TS) composite_persistent_kernel(
         const unsigned k = s_next;
         __syncthreads();
         if ((int64_t)k >= M) break;
-        composite_tile<TS, SAVE>((int)order[k], s_rec, s_id, s_wmask, s_list, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, mode, out, out_last, out_tfin, out_ntri, stack, cap, npix, need, eval_count);
+        composite_tile<TS, SAVE, MODE>((int)order[k], s_rec, s_id, s_wmask, s_list, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, out, out_last, out_tfin, out_ntri, stack, cap, npix, need);
         __syncthreads();
     }
 }
@@ -824,8 +793,7 @@ __global__ void tile_order_keys_kernel(const int64_t* __restrict__ off, int64_t 
 // ---------------------------------------------------------------------------
 // frame inspection: split sorted keys into ids / depth bits
 
-__global__ void lists_kernel(const uint32_t* __restrict__ tk, const uint32_t* __restrict__ tv, int64_t n,
-                             const BinInfo* __restrict__ bin, int64_t ntot, int tiles_per_cam,
+__global__ void lists_kernel(const uint32_t* __restrict__ tk, const uint32_t* __restrict__ tv, int64_t n, const BinInfo* __restrict__ bin, int64_t ntot, int tiles_per_cam,
                              int32_t* __restrict__ ids, uint32_t* __restrict__ dbits) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -873,24 +841,35 @@ cudaError_t launch_composite(umgs_frame* fr, const umgs_render_opts& opts, float
         cudaMemsetAsync(work, 0, sizeof(unsigned), stream);
         nblk = opts.sched * fr->ctx->num_sms;
     }
-#define UMGS_LAUNCH(TSV, SV)                                                                                    \
-    if (persist) composite_persistent_kernel<TSV, SV><<<nblk, TSV * TSV, 0, stream>>>(order, work, M,          \
+#define UMGS_LAUNCH(TSV, SV, MV)                                                                                \
+    if (persist) composite_persistent_kernel<TSV, SV, MV><<<nblk, TSV * TSV, 0, stream>>>(order, work, M,      \
         fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->mixed ? fr->grec.as<GRec16>() : nullptr,  \
         fr->trec.as<TRec>(), fr->ng,                                                                            \
-        fr->nt, fr->tiles_x, tpc, fr->W, fr->H, te, opts.bg[0], opts.bg[1], opts.bg[2], opts.blend_mode, out,     \
+        fr->nt, fr->tiles_x, tpc, fr->W, fr->H, te, opts.bg[0], opts.bg[1], opts.bg[2], out,                      \
         fr->last.as<int32_t>(), save ? fr->tfin.as<float>() : nullptr, save ? fr->ntri.as<int32_t>() : nullptr,   \
-        save ? fr->stack.as<float4>() : nullptr, fr->stack_cap, npix, fr->status.as<int32_t>() + 2,             \
-        reinterpret_cast<unsigned long long*>(fr->status.as<int32_t>() + 6)), count_launch();                                   \
-    else composite_kernel<TSV, SV><<<M, TSV * TSV, 0, stream>>>(                                                \
+        save ? fr->stack.as<float4>() : nullptr, fr->stack_cap, npix, fr->status.as<int32_t>() + 2),            \
+        count_launch();                                                                                         \
+    else composite_kernel<TSV, SV, MV><<<M, TSV * TSV, 0, stream>>>(                                            \
         fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->mixed ? fr->grec.as<GRec16>() : nullptr,  \
         fr->trec.as<TRec>(), fr->ng,                                                                            \
-        fr->nt, fr->tiles_x, tpc, fr->W, fr->H, te, opts.bg[0], opts.bg[1], opts.bg[2], opts.blend_mode, out,     \
+        fr->nt, fr->tiles_x, tpc, fr->W, fr->H, te, opts.bg[0], opts.bg[1], opts.bg[2], out,                      \
         fr->last.as<int32_t>(), save ? fr->tfin.as<float>() : nullptr, save ? fr->ntri.as<int32_t>() : nullptr,   \
-        save ? fr->stack.as<float4>() : nullptr, fr->stack_cap, npix, fr->status.as<int32_t>() + 2,             \
-        reinterpret_cast<unsigned long long*>(fr->status.as<int32_t>() + 6)), count_launch()
-    if (ts == 16) { if (save) UMGS_LAUNCH(16, true); else UMGS_LAUNCH(16, false); }
-    else if (ts == 8) { if (save) UMGS_LAUNCH(8, true); else UMGS_LAUNCH(8, false); }
-    else { if (save) UMGS_LAUNCH(32, true); else UMGS_LAUNCH(32, false); }
+        save ? fr->stack.as<float4>() : nullptr, fr->stack_cap, npix, fr->status.as<int32_t>() + 2),            \
+        count_launch()
+    // the saved (backward) form exists for FULL only
+#define UMGS_MODES(TSV)                                                                                         \
+    if (save) { UMGS_LAUNCH(TSV, true, UMGS_BLEND_FULL); }                                                      \
+    else if (mode == kModeTProduct) { UMGS_LAUNCH(TSV, false, kModeTProduct); }                                 \
+    else if (mode == UMGS_BLEND_DIRECT) { UMGS_LAUNCH(TSV, false, UMGS_BLEND_DIRECT); }                         \
+    else if (mode == UMGS_BLEND_MSAA_ALL) { UMGS_LAUNCH(TSV, false, UMGS_BLEND_MSAA_ALL); }                     \
+    else if (mode == UMGS_BLEND_ENTITY_ALL) { UMGS_LAUNCH(TSV, false, UMGS_BLEND_ENTITY_ALL); }                 \
+    else { UMGS_LAUNCH(TSV, false, UMGS_BLEND_FULL); }
+    const int mode = (opts.blend_mode == UMGS_BLEND_FULL && (opts.flags & UMGS_RENDER_T_PRODUCT)) ? kModeTProduct
+                                                                                                : opts.blend_mode;
+    if (ts == 16) { UMGS_MODES(16) }
+    else if (ts == 8) { UMGS_MODES(8) }
+    else { UMGS_MODES(32) }
+#undef UMGS_MODES
 #undef UMGS_LAUNCH
     return cudaGetLastError();
 }
@@ -1103,9 +1082,10 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     fr->tkeys = fr->tk.as<uint32_t>();
     if (NR > 0) {
         StageTimer tm(ctx, UMGS_STAGE_SCATTER, stream);
-        emit_pairs_kernel<<<grid_for(NR, 256), 256, 0, stream>>>(fr->bin.as<BinInfo>(), pv, fr->poff.as<uint32_t>(), NR,
+emit_pairs_kernel<<<grid_for(NR, 256), 256, 0, stream>>>(fr->bin.as<BinInfo>(), pv, fr->poff.as<uint32_t>(), NR,
                                                                  Ntot, ts, tiles_x, tiles_per_cam, fr->tk.as<uint32_t>(),
-                                                                 fr->tv.as<uint32_t>(), Kcap, fr->status.as<int32_t>()), count_launch();
+                                                                 fr->tv.as<uint32_t>(), Kcap, fr->status.as<int32_t>()),
+            count_launch();
         UMGS_TRY(cudaGetLastError());
     }
     {
@@ -1138,6 +1118,79 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     }
     fr->valid = true;
 #undef UMGS_TRY
+    return UMGS_OK;
+}
+
+// N_alg of the last render (diagnostic, not part of the render): per pixel
+// the entries of its tile list whose pixel rect holds the pixel, up to and
+// including list position `last` when the pixel stopped at T < t_eps (bit 31
+// of the compositor's `last`), else all of them.  One CTA per tile, one
+// thread per pixel, summed into *count.
+template <int TS>
+__global__ void __launch_bounds__(TS * TS) eval_count_kernel(
+    const uint32_t* __restrict__ ids, const int64_t* __restrict__ off, const GRec* __restrict__ grec,
+    const GRec16* __restrict__ grec16, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
+    int tiles_per_cam, int W, int H, const int32_t* __restrict__ last, unsigned long long* __restrict__ count) {
+    const int tile = blockIdx.x;
+    const int cam = tile / tiles_per_cam;
+    const int lt = tile - cam * tiles_per_cam;
+    const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
+    int lx, ly;
+    block_pixel<TS>(threadIdx.x, lx, ly);
+    const int px = tx * TS + lx, py = ty * TS + ly;
+    unsigned long long c = 0;
+    if (px < W && py < H) {
+        const int64_t beg = off[tile], end = off[tile + 1];
+        const int32_t l = last[((int64_t)cam * H + py) * W + px];
+        const int64_t lim = (l < 0) ? (int64_t)(l & 0x7fffffff) : end - beg;
+        for (int64_t p = 0; p < lim; ++p) {
+            const uint32_t id = ids[beg + p];
+            uint32_t rx, ry;
+            if (id < Ng) {
+                if (grec16) {
+                    const uint4 h1 = grec16[(int64_t)cam * Ng + id].v1;
+                    rx = h1.z; ry = h1.w;
+                } else {
+                    const float4 c2 = reinterpret_cast<const float4*>(grec + (int64_t)cam * Ng + id)[2];
+                    rx = __float_as_uint(c2.y); ry = __float_as_uint(c2.z);
+                }
+            } else {
+                const TRec& t = trec[(int64_t)cam * Nt + (id - Ng)];
+                rx = t.rx; ry = t.ry;
+            }
+            c += (px >= (int)(rx & 0xffff) && px <= (int)(rx >> 16) && py >= (int)(ry & 0xffff) &&
+                  py <= (int)(ry >> 16)) ? 1ull : 0ull;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+umgs_status frame_evaluations(const umgs_frame* fr, int64_t* evals, cudaStream_t stream) {
+    cudaError_t e;
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(fr->status.as<int32_t>() + 6);
+    if ((e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), stream)) != cudaSuccess)
+        return cuda_fail(fr->ctx, e, "cudaMemsetAsync");
+    const int tpc = fr->tiles_x * fr->tiles_y;
+    const unsigned M = (unsigned)fr->num_tiles;
+    if (M > 0) {
+#define UMGS_LAUNCH(TSV)                                                                                        \
+        eval_count_kernel<TSV><<<M, TSV * TSV, 0, stream>>>(fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), \
+            fr->mixed ? fr->grec.as<GRec16>() : nullptr, fr->trec.as<TRec>(), fr->ng, fr->nt, fr->tiles_x, tpc,   \
+            fr->W, fr->H, fr->last.as<int32_t>(), cnt), count_launch()
+        if (fr->tile == 16) UMGS_LAUNCH(16);
+        else if (fr->tile == 8) UMGS_LAUNCH(8);
+        else UMGS_LAUNCH(32);
+#undef UMGS_LAUNCH
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(fr->ctx, e, "eval_count_kernel");
+    }
+    unsigned long long v = 0;
+    if ((e = cudaMemcpyAsync(fr->ctx->pinned, cnt, sizeof(v), cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(stream)) != cudaSuccess)
+        return cuda_fail(fr->ctx, e, "reading the evaluation count");
+    std::memcpy(&v, fr->ctx->pinned, sizeof(v));
+    *evals = (int64_t)v;
     return UMGS_OK;
 }
 

@@ -25,6 +25,7 @@ F32, BF16 = 0, 1
 BIND_BBX, BIND_CENTER, BIND_NEAREST = 0, 1, 2
 RENDER_SAVE_BACKWARD = 1
 RENDER_MIXED = 2
+RENDER_T_PRODUCT = 4
 DEFORM_FRAME, DEFORM_LITERAL = 0, 1
 
 
@@ -273,11 +274,12 @@ def mesh_to_device(m, device="cuda") -> DevMesh:
 
 
 def render_opts(tile_size=16, blend_mode=BLEND_FULL, t_eps=1e-4, bg=(0.0, 0.0, 0.0), save=False,
-                mixed=False, sched=0) -> CRenderOpts:
+                mixed=False, sched=0, t_product=False) -> CRenderOpts:
     o = CRenderOpts()
     lib().umgs_default_render_opts(ctypes.byref(o))
     o.sched = int(sched)
-    o.flags = (RENDER_SAVE_BACKWARD if save else 0) | (RENDER_MIXED if mixed else 0)
+    o.flags = ((RENDER_SAVE_BACKWARD if save else 0) | (RENDER_MIXED if mixed else 0)
+               | (RENDER_T_PRODUCT if t_product else 0))
     o.tile_size = int(tile_size)
     o.blend_mode = int(blend_mode)
     o.t_eps = float(t_eps)

@@ -85,6 +85,25 @@ def test_ablation_modes(ctx, mode):
     check_image(sc, out, mode=mode)
 
 
+def test_t_product_reading(ctx):
+    # the literal Eq. 6 transmittance inside entities (flag), against the
+    # oracle's t_product reading; differs from FULL only on multi-triangle entities
+    from paper_2601_19233_gb300 import umgs
+    sc = S.config0()
+    g = umgs.gaussians_to_device(sc.gaussians)
+    ms = [umgs.mesh_to_device(m) for m in sc.meshes]
+    out = umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(sc.tile, t_product=True)).cpu().numpy()
+    ref = R.render_image(sc, t_product=True)
+    ok = ~ref["tie"]
+    assert ok.mean() > 0.99
+    assert np.abs(out[0, ..., :3] - ref["rgb"])[ok].max() <= TOL
+    assert np.abs(out[0, ..., 3] - ref["T"])[ok].max() <= TOL
+    with pytest.raises(umgs.UmgsError):
+        umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(sc.tile, t_product=True, save=True))
+    with pytest.raises(umgs.UmgsError):
+        umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(sc.tile, blend_mode=R.DIRECT, t_product=True))
+
+
 def test_tile_sizes_bit_identical(ctx):
     sc = S.small_scene(41, 77, 45, 900, mesh_subdiv=2, sh_degree=1)
     outs = []
