@@ -1,0 +1,171 @@
+"""Parity at the full workload sizes, in the launch configurations bench.py times.
+
+- 1080p (1M Gaussians SH3, 200k-face torus, tile 16, FULL, one CTA per tile):
+  every tile list bit-exact against the oracle, and sampled pixels within
+  2e-4 of the fp64 oracle (tie pixels excluded).
+- 1080p deform + render: Eq. 12-13 on a seeded near-surface binding of all
+  1M Gaussians (GPU vs fp64 oracle, every Gaussian), then the oracle-deformed
+  Gaussians (cov3d input) rendered by both: lists bit-exact, sampled pixels.
+- 64 views of 800x800 (500k Gaussians, 100k-face torus) through the
+  autotuned configuration and a captured graph: graph output equal to the
+  plain render bit for bit, lists of three views bit-exact, sampled pixels.
+- 4K mixed precision (6M Gaussians, 2M-triangle torus, bf16 SH, fp16
+  records): the lists of 24 tiles bit-exact (footprint decisions stay fp32),
+  sampled pixels within the mixed-precision budget.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import canonical as cn
+from oracle import render as R
+from paper_2601_19233_gb300 import scenes as S
+from tests.test_gpu_render import ctx  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+TOL = 2e-4
+
+
+def _tile_list(P, tile, ts, tiles_x):
+    """Oracle list of one tile (single-camera Primitives): the records whose
+    pixel rect touches the tile, in (depth bits, id) order."""
+    ty, tx = divmod(tile, tiles_x)
+    r = P.rect
+    m = P.valid & (r[:, 0] // ts <= tx) & (r[:, 1] // ts >= tx) & (r[:, 2] // ts <= ty) & (r[:, 3] // ts >= ty)
+    cand = np.nonzero(m)[0]
+    return cand[np.lexsort((cand, P.dbits[cand]))]
+
+
+def _gpu_lists(fr):
+    ptr, ids, db = fr.lists()
+    return ptr.cpu().numpy(), ids.cpu().numpy().astype(np.int64), db.cpu().numpy().view(np.uint32)
+
+
+def _sample_pixels(rng, W, H, n, crop=None):
+    pix = np.stack([rng.integers(0, W, n), rng.integers(0, H, n)], 1)
+    if crop is not None:
+        x0, y0, w, h = crop
+        pix2 = np.stack([rng.integers(x0, x0 + w, n // 2), rng.integers(y0, y0 + h, n // 2)], 1)
+        pix = np.concatenate([pix, pix2])
+    return pix
+
+
+def _check_pixels(sc, out_cam, pix, cam_index=0, tol=TOL, cov3d=None, frame=None):
+    rgb, T, tie, _ = R.render_pixels(sc, pix, cam_index=cam_index, cov3d=cov3d, frame=frame)
+    got = out_cam[pix[:, 1], pix[:, 0]]
+    ok = ~tie
+    assert ok.mean() > 0.98
+    e_rgb = np.abs(got[:, :3] - rgb)[ok].max()
+    e_T = np.abs(got[:, 3] - T)[ok].max()
+    assert e_rgb <= tol and e_T <= tol, (e_rgb, e_T)
+    return e_rgb, e_T
+
+
+def _device_scene(sc, sh_dtype=torch.float32):
+    from paper_2601_19233_gb300 import umgs
+    return umgs.gaussians_to_device(sc.gaussians, sh_dtype=sh_dtype), [umgs.mesh_to_device(m) for m in sc.meshes]
+
+
+def test_1080p_lists_and_pixels(ctx):
+    from paper_2601_19233_gb300 import umgs
+    sc = S.config1()
+    g, ms = _device_scene(sc)
+    fr = umgs.Frame(ctx)
+    out = umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(16), frame=fr)[0].cpu().numpy()
+    ptr, ids, db = cn.sorted_tile_lists([cn.Primitives(sc, 0)], 16)
+    gptr, gids, gdb = _gpu_lists(fr)
+    assert len(gids) > 5_000_000
+    assert np.array_equal(gptr, ptr) and np.array_equal(gids, ids) and np.array_equal(gdb, db)
+    rng = np.random.default_rng(11)
+    _check_pixels(sc, out, _sample_pixels(rng, 1920, 1080, 192, crop=(760, 340, 400, 400)))
+
+
+def test_1080p_deform_then_render(ctx):
+    from scipy.spatial import cKDTree
+
+    from oracle import deform as D
+    from paper_2601_19233_gb300 import umgs
+    sc = S.config1()
+    g0 = sc.gaussians
+    V, F = sc.proxy_verts.astype(np.float32), sc.proxy_faces.astype(np.int32)
+    Vd = S.displace(V, sc.extra["sinusoids"], 7).astype(np.float32)
+    # seeded binding near the surface: 8 points on faces among each
+    # Gaussian's 6 nearest face centroids, uniform barycentrics
+    rng = np.random.default_rng(12)
+    _, near = cKDTree(V[F].mean(1)).query(g0.means, k=6)
+    face = np.take_along_axis(near, rng.integers(0, 6, size=(g0.n, 8)), 1).astype(np.int32)
+    b = rng.uniform(0, 1, size=(g0.n, 8, 2))
+    b = np.where(b.sum(-1, keepdims=True) > 1, 1 - b, b).astype(np.float32)
+    mr, Sr, _ = D.deform_gaussians(g0.means, g0.quats, g0.scales, face, b, V, Vd, F)
+    dg = umgs.gaussians_to_device(g0)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a)).cuda()
+    m, c, _ = umgs.deform(ctx, dg, t(face), t(b), t(V), t(Vd), t(F))
+    m, c = m.cpu().numpy(), c.cpu().numpy()
+    ref6 = D.sym6(Sr)
+    assert np.abs(m - mr).max() < 1e-5
+    assert (np.abs(c - ref6) / np.abs(ref6).max(1, keepdims=True)).max() < 1e-4
+    # render the oracle-deformed Gaussians on both sides
+    cov = ref6.astype(np.float32)
+    sc.gaussians = S.Gaussians(mr.astype(np.float32), g0.quats, g0.scales, g0.opacities, g0.sh, g0.sh_degree)
+    gd = umgs.gaussians_to_device(sc.gaussians)
+    gd.cov3d = torch.as_tensor(cov).cuda()
+    ms = [umgs.mesh_to_device(mm) for mm in sc.meshes]
+    fr = umgs.Frame(ctx)
+    out = umgs.render(ctx, gd, ms, sc.cameras, umgs.render_opts(16), frame=fr)[0].cpu().numpy()
+    ptr, ids, db = cn.sorted_tile_lists([cn.Primitives(sc, 0, cov3d=cov)], 16)
+    gptr, gids, gdb = _gpu_lists(fr)
+    assert np.array_equal(gptr, ptr) and np.array_equal(gids, ids) and np.array_equal(gdb, db)
+    _check_pixels(sc, out, _sample_pixels(rng, 1920, 1080, 128, crop=(760, 340, 400, 400)), cov3d=cov)
+
+
+def test_64_views_graph_autotuned(ctx):
+    from paper_2601_19233_gb300 import umgs
+    sc = S.config2()
+    g, ms = _device_scene(sc)
+    out = torch.zeros((64, 800, 800, 4), device="cuda")
+    best, _ = umgs.autotune(ctx, g, ms, sc.cameras, umgs.render_opts(16), out)
+    fr = umgs.Frame(ctx)
+    ref = umgs.render(ctx, g, ms, sc.cameras, best, frame=fr)
+    gptr, gids, gdb = _gpu_lists(fr)
+    ts = best.tile_size
+    tiles_x = (800 + ts - 1) // ts
+    tpc = tiles_x * tiles_x
+    for c in (0, 21, 42):
+        P = cn.Primitives(sc, c)
+        _, ids, db = cn.sorted_tile_lists([P], ts)
+        lo, hi = gptr[c * tpc], gptr[(c + 1) * tpc]
+        assert np.array_equal(gids[lo:hi], ids) and np.array_equal(gdb[lo:hi], db)
+    gr = umgs.Graph(ctx, umgs.Frame(ctx), g, ms, sc.cameras, best, out)
+    gr.launch()
+    gr.check()
+    assert torch.equal(out, ref)
+    rng = np.random.default_rng(13)
+    outn = ref.cpu().numpy()
+    for c in (0, 42):
+        _check_pixels(sc, outn[c], _sample_pixels(rng, 800, 800, 64, crop=(250, 250, 300, 300)), cam_index=c)
+
+
+def test_4k_mixed_precision(ctx):
+    from paper_2601_19233_gb300 import umgs
+    sc = S.config4()
+    g, ms = _device_scene(sc, sh_dtype=torch.bfloat16)
+    fr = umgs.Frame(ctx)
+    out = umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(16, mixed=True), frame=fr)[0].cpu().numpy()
+    gptr, gids, gdb = _gpu_lists(fr)
+    # footprint decisions are fp32 and use the bf16-rounded SH only for colour:
+    # the lists equal those of the fp32 oracle
+    P = cn.Primitives(sc, 0)
+    rng = np.random.default_rng(14)
+    tiles_x = (3840 + 15) // 16
+    for t in rng.choice(tiles_x * ((2160 + 15) // 16), size=24, replace=False):
+        ref = _tile_list(P, int(t), 16, tiles_x)
+        got = gids[gptr[t]:gptr[t + 1]]
+        assert np.array_equal(got, ref), t
+    # colours: the oracle on the bf16-rounded SH, error budget of the fp16 records
+    sc.gaussians.sh = torch.as_tensor(sc.gaussians.sh).to(torch.bfloat16).float().numpy()
+    pix = _sample_pixels(rng, 3840, 2160, 128, crop=(1600, 800, 640, 560))
+    rgb, T, tie, _ = R.render_pixels(sc, pix)
+    got = out[pix[:, 1], pix[:, 0]]
+    ok = ~tie
+    assert np.abs(got[:, :3] - rgb)[ok].max() < 2e-2
+    assert np.abs(got[:, 3] - T)[ok].max() < 2e-2
