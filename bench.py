@@ -378,10 +378,12 @@ def roofline(stages, nkeys, n, sc, clk, evals, ms_step):
 def composite_traffic():
     """DRAM bytes per launch of the compositor from the committed ncu summary
     (profiles/composite_1080p.md, line `traffic_bytes_per_launch: B source_sha256: H`),
-    or None when render.cu has changed since those counters were taken."""
+    or None when render.cu or common.cuh has changed since those counters were taken."""
     import hashlib
     try:
-        src = hashlib.sha256(open(os.path.join(ROOT, "paper_2601_19233_gb300", "csrc", "render.cu"), "rb").read())
+        src = hashlib.sha256()
+        for f in ("render.cu", "common.cuh"):
+            src.update(open(os.path.join(ROOT, "paper_2601_19233_gb300", "csrc", f), "rb").read())
         for line in open(os.path.join(ROOT, "profiles", "composite_1080p.md")):
             if line.startswith("traffic_bytes_per_launch:"):
                 parts = line.split()
