@@ -438,6 +438,52 @@ def render_backward(ctx: Context, frame: Frame, gaussians: DevGaussians | None, 
     return out
 
 
+class _RenderFunction(torch.autograd.Function):
+    """umgs_render (saved state) forward, umgs_render_backward backward.
+    Differentiable inputs: the Gaussian tensors (means, quats, scales,
+    opacities, SH, cov3d) and per mesh (verts, vcolor, valpha, falpha)."""
+
+    @staticmethod
+    def forward(fctx, ctx, frame, cameras, opts, gaussians, meshes, *tensors):
+        out = render(ctx, gaussians, meshes, cameras, opts, frame=frame)
+        fctx.state = (ctx, frame, gaussians, meshes)
+        fctx.dtypes = [t.dtype if t is not None else None for t in tensors]
+        return out
+
+    @staticmethod
+    def backward(fctx, dout):
+        ctx, frame, g, meshes = fctx.state
+        grads = render_backward(ctx, frame, g, meshes, dout.contiguous())
+        names = ["means", "quats", "scales", "opacities", "sh", "cov3d"]
+        for mi in range(len(meshes)):
+            names += ["verts%d" % mi, "vcolor%d" % mi, "valpha%d" % mi, "falpha%d" % mi]
+        out = []
+        for name, dt in zip(names, fctx.dtypes):
+            gr = grads.get(name)
+            out.append(gr.to(dt) if (gr is not None and dt is not None) else None)
+        return (None,) * 6 + tuple(out)
+
+
+def render_autograd(ctx: Context, gaussians: DevGaussians | None, meshes, cameras, opts: CRenderOpts | None = None,
+                    frame: Frame | None = None) -> torch.Tensor:
+    """Differentiable render: [ncams, H, W, 4] (RGB, T) whose backward runs
+    umgs_render_backward.  Each call keeps its state in its own Frame (pass
+    one to reuse its buffers; it must not be re-rendered before backward).
+    FULL blending, fp32 records only (the backward's scope)."""
+    o = CRenderOpts()
+    if opts is None:
+        o = render_opts(16, save=True)
+    else:
+        ctypes.memmove(ctypes.byref(o), ctypes.byref(opts), ctypes.sizeof(CRenderOpts))
+        o.flags |= RENDER_SAVE_BACKWARD
+    frame = frame or Frame(ctx)
+    g = gaussians
+    ts = [g.means, g.quats, g.scales, g.opacities, g.sh, g.cov3d] if g is not None else [None] * 6
+    for m in meshes:
+        ts += [m.verts, m.vcolor, m.valpha, m.falpha]
+    return _RenderFunction.apply(ctx, frame, cameras, o, gaussians, meshes, *ts)
+
+
 class Graph:
     """umgs_render_graph_*: a render captured in a CUDA graph (see include/umgs.h)."""
 
