@@ -307,7 +307,8 @@ umgs_status umgs_deform_vertex_table(umgs_ctx* ctx, float* out_table, int64_t nv
  * input and output device pointers and the cameras of the creation call
  * (their contents may change between launches, the cameras may not);
  * umgs_graph_check synchronises `stream` and reports CAPACITY if a launch
- * needed more pairs (re-create the graph), INVALID_ARG for bad face indices.
+ * needed more pairs (re-create the graph; that launch composited no tile, so
+ * its output is the background with T = 1), INVALID_ARG for bad face indices.
  * The frame belongs to the graph until umgs_graph_destroy.
  */
 typedef struct umgs_graph umgs_graph;

@@ -125,7 +125,9 @@ __global__ void __launch_bounds__(TS * TS) composite_bwd_kernel(
         for (int k = threadIdx.x; k < n; k += NT) {
             const uint32_t id = ids[beg + b0 + k];
             s_id[k] = id;
-            if (id < Ng) {
+            if (id >= Ng + Nt) {
+                s_wmask[k] = 0u;  // not a record of this frame
+            } else if (id < Ng) {
                 const float4* src = reinterpret_cast<const float4*>(G + id);
                 const float4 a = src[0], q1 = src[1], c = src[2];
                 s_rec[k][0] = a; s_rec[k][1] = q1; s_rec[k][2] = c;

@@ -487,12 +487,15 @@ __global__ void emit_pairs_kernel(const BinInfo* __restrict__ bin, const uint32_
         }
 }
 
-// tile_off[t] = first index of tile t in the sorted keys (lower bound)
+// tile_off[t] = first index of tile t in the sorted keys (lower bound).
+// More pairs than the capacity (flagged by emit_pairs): the emission skipped
+// records, so slots below the capacity may hold no pair; every tile is then
+// left empty rather than reading them.
 __global__ void tile_ranges_kernel(const uint32_t* __restrict__ tk, const uint32_t* __restrict__ K_dev, int64_t Kcap,
                                    int64_t M, int64_t* __restrict__ off) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t > M) return;
-    const int64_t K = min((int64_t)*K_dev, Kcap);
+    const int64_t K = (int64_t)*K_dev > Kcap ? 0 : (int64_t)*K_dev;
     if (t == M) { off[M] = K; return; }
     int64_t lo = 0, hi = K;
     while (lo < hi) {
@@ -576,7 +579,9 @@ __device__ __forceinline__ void composite_tile(
         for (int k = threadIdx.x; k < n; k += NT) {
             const uint32_t id = ids[b0 + k];
             s_id[k] = id;
-            if (id < Ng) {
+            if (id >= Ng + Nt) {
+                s_wmask[k] = 0u;  // not a record of this frame: no fragment
+            } else if (id < Ng) {
                 float4 a, b, c;
                 if (G16) {  // fp16 record: widen to the fp32 layout
                     const uint4 h0 = G16[id].v0, h1 = G16[id].v1;
@@ -1146,6 +1151,7 @@ __global__ void __launch_bounds__(TS * TS) eval_count_kernel(
         for (int64_t p = 0; p < lim; ++p) {
             const uint32_t id = ids[beg + p];
             uint32_t rx, ry;
+            if (id >= Ng + Nt) continue;
             if (id < Ng) {
                 if (grec16) {
                     const uint4 h1 = grec16[(int64_t)cam * Ng + id].v1;

@@ -89,10 +89,13 @@ def test_graph_capacity_overflow_is_reported(ctx):
     gr.launch()
     gr.check()
     g.scales.mul_(6.0)  # much larger footprints: more pairs than the captured capacity
+    out.fill_(-1.0)
     gr.launch()
     with pytest.raises(umgs.UmgsError) as e:
         gr.check()
     assert e.value.status == 3
+    # no tile was composited: background (black) with T = 1 everywhere
+    assert torch.all(out[..., 3] == 1.0) and torch.all(out[..., :3] == 0.0)
 
 
 def test_autotune_picks_a_valid_config(ctx):
