@@ -58,8 +58,10 @@ __device__ __forceinline__ void warp_sum_transpose(float (&v)[V], int lane) {
     if (V == 16) v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
+// 16x16 tiles: registers capped for four resident CTAs per SM (32 warps),
+// which hides the per-batch barriers better than the three of an uncapped build
 template <int TS>
-__global__ void __launch_bounds__(TS * TS) composite_bwd_kernel(
+__global__ void __launch_bounds__(TS * TS, TS == 16 ? 4 : 1) composite_bwd_kernel(
     const uint32_t* __restrict__ ids, const int64_t* __restrict__ off,
     const GRec* __restrict__ grec, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
     int tiles_per_cam, int W, int H, float bg0,
