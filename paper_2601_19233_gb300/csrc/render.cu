@@ -266,9 +266,32 @@ __global__ void __launch_bounds__(256) shade_gaussians_kernel(const float* __res
     if (i >= N) return;
     float c[3 * K];
     if (sh_dtype == UMGS_BF16) {
-        const unsigned short* p = static_cast<const unsigned short*>(sh) + i * 3 * K;
+        // 3K bf16 values per Gaussian: widest aligned vector loads (16 B for SH3)
+        constexpr int NB = 3 * K * 2;
+        const unsigned char* p = static_cast<const unsigned char*>(sh) + i * NB;
+        if (NB % 16 == 0) {
 #pragma unroll
-        for (int k = 0; k < 3 * K; ++k) c[k] = __uint_as_float(((unsigned int)p[k]) << 16);
+            for (int q = 0; q < NB / 16; ++q) {
+                const uint4 u = reinterpret_cast<const uint4*>(p)[q];
+                const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    c[8 * q + 2 * h] = __uint_as_float(w[h] << 16);
+                    c[8 * q + 2 * h + 1] = __uint_as_float(w[h] & 0xffff0000u);
+                }
+            }
+        } else if (NB % 8 == 0) {
+#pragma unroll
+            for (int q = 0; q < NB / 8; ++q) {
+                const uint2 u = reinterpret_cast<const uint2*>(p)[q];
+                c[4 * q] = __uint_as_float(u.x << 16); c[4 * q + 1] = __uint_as_float(u.x & 0xffff0000u);
+                c[4 * q + 2] = __uint_as_float(u.y << 16); c[4 * q + 3] = __uint_as_float(u.y & 0xffff0000u);
+            }
+        } else {
+            const unsigned short* q = reinterpret_cast<const unsigned short*>(p);
+#pragma unroll
+            for (int k = 0; k < 3 * K; ++k) c[k] = __uint_as_float(((unsigned int)q[k]) << 16);
+        }
     } else if ((3 * K) % 4 == 0) {
         const float4* p = reinterpret_cast<const float4*>(static_cast<const float*>(sh) + i * 3 * K);
 #pragma unroll
@@ -464,27 +487,77 @@ __global__ void tile_counts_kernel(const BinInfo* __restrict__ bin, const uint32
     cnt[i] = tiles_of(bin[pv[i]], ts);
 }
 
-// One thread per depth-sorted record: its (tile, id) pairs in row-major tile order.
-__global__ void emit_pairs_kernel(const BinInfo* __restrict__ bin, const uint32_t* __restrict__ pv,
-                                  const uint32_t* __restrict__ off, int64_t n, int64_t ntot, int ts, int tiles_x,
-                                  int tiles_per_cam, uint32_t* __restrict__ tk, uint32_t* __restrict__ tv, int64_t cap,
-                                  int32_t* __restrict__ status) {
+// (tile, id) pairs of the depth-sorted records: record i owns the slots
+// [off[i], off[i] + tiles(i)), its tiles in row-major order.  Each warp takes
+// 32 consecutive records and fills their (contiguous) slots together: lane l
+// writes slots s = l, l + 32, ... of the warp's range, finding the owning
+// record by binary search over the warp's exclusive prefix of tile counts,
+// so the writes are coalesced and a record with many tiles does not hold up
+// its warp.  Slots at or beyond `cap` are not written (the overflow is
+// flagged in status bit 2); every slot below it is.
+__global__ void __launch_bounds__(256) emit_pairs_kernel(const BinInfo* __restrict__ bin,
+                                                         const uint32_t* __restrict__ pv,
+                                                         const uint32_t* __restrict__ off, int64_t n, int64_t ntot,
+                                                         int ts, int tiles_x, int tiles_per_cam,
+                                                         uint32_t* __restrict__ tk, uint32_t* __restrict__ tv,
+                                                         int64_t cap, int32_t* __restrict__ status) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t rec = pv[i];
-    const BinInfo b = bin[rec];
-    if (!b.valid) return;
-    const int cam = (int)(rec / ntot);
-    const uint32_t id = (uint32_t)(rec - (int64_t)cam * ntot);
-    const int xlo = (b.rx & 0xffff) / ts, xhi = (b.rx >> 16) / ts, ylo = (b.ry & 0xffff) / ts, yhi = (b.ry >> 16) / ts;
-    int64_t o = off[i];
-    if (o + (int64_t)(yhi - ylo + 1) * (xhi - xlo + 1) > cap) { atomicOr(status, 4); return; }  // capacity overflow
-    for (int ty = ylo; ty <= yhi; ++ty)
-        for (int tx = xlo; tx <= xhi; ++tx) {
-            tk[o] = (uint32_t)(cam * tiles_per_cam + ty * tiles_x + tx);
-            tv[o] = id;
-            ++o;
+    const int lane = threadIdx.x & 31;
+    if (i - lane >= n) return;  // whole warp past the end
+    int xlo = 0, ylo = 0, w = 1, cnt = 0;
+    uint32_t id = 0, tbase = 0;
+    int64_t start = 0;
+    if (i < n) {
+        const uint32_t rec = pv[i];
+        const BinInfo b = bin[rec];
+        start = off[i];
+        if (b.valid) {
+            const int cam = (int)(rec / ntot);
+            id = (uint32_t)(rec - (int64_t)cam * ntot);
+            xlo = (int)(b.rx & 0xffff) / ts;
+            const int xhi = (int)(b.rx >> 16) / ts;
+            ylo = (int)(b.ry & 0xffff) / ts;
+            const int yhi = (int)(b.ry >> 16) / ts;
+            w = xhi - xlo + 1;
+            cnt = w * (yhi - ylo + 1);
+            tbase = (uint32_t)cam * (uint32_t)tiles_per_cam;
         }
+    }
+    // exclusive prefix of the counts within the warp
+    int incl = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+    }
+    const int excl = incl - cnt;
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int64_t base = __shfl_sync(0xffffffffu, start, 0);  // offsets are contiguous in record order
+    if (lane == 0 && base + total > cap) atomicOr(status, 4);  // capacity overflow
+    for (int s0 = 0; s0 < total; s0 += 32) {
+        const int s = s0 + lane;
+        // owner: the last lane r with excl[r] <= s
+        int r = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            const int c = r + step;
+            const int e = __shfl_sync(0xffffffffu, excl, c & 31);
+            if (c < 32 && e <= s) r = c;
+        }
+        const int re = __shfl_sync(0xffffffffu, excl, r);
+        const int rx = __shfl_sync(0xffffffffu, xlo, r);
+        const int ry = __shfl_sync(0xffffffffu, ylo, r);
+        const int rw = __shfl_sync(0xffffffffu, w, r);
+        const uint32_t rid = __shfl_sync(0xffffffffu, id, r);
+        const uint32_t rtb = __shfl_sync(0xffffffffu, tbase, r);
+        const int64_t o = base + s;
+        if (s < total && o < cap) {
+            const int k = s - re;
+            const int ty = ry + k / rw, tx = rx + k % rw;
+            tk[o] = rtb + (uint32_t)(ty * tiles_x + tx);
+            tv[o] = rid;
+        }
+    }
 }
 
 // tile_off[t] = first index of tile t in the sorted keys (lower bound).
