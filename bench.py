@@ -428,7 +428,9 @@ def run_forms(ctx, dev, steps):
     evals_plain = fr.evaluations()
     best, t_tune = umgs.autotune(ctx, g, ms, sc.cameras, plain, out)
     fr2 = umgs.Frame(ctx)
-    gr = umgs.Graph(ctx, fr2, g, ms, sc.cameras, best, out)
+    # the scene and cameras are the same every replay: pair capacity = the
+    # sizing render's count (+ 4096), no 25% headroom
+    gr = umgs.Graph(ctx, fr2, g, ms, sc.cameras, best, out, key_headroom=1.0)
     t_graph = _time(lambda: gr.launch(), steps)
     gr.check()
     forms["multiview_64x800"] = {

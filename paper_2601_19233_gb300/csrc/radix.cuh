@@ -122,9 +122,13 @@ static __global__ void __launch_bounds__(kRsThreads) radix_upsweep_kernel(const 
                                                                           uint32_t* __restrict__ hist) {
     __shared__ uint32_t cnt[256];
     const int64_t n = min((int64_t)*n_dev, n_cap);
+    const int64_t base = (int64_t)blockIdx.x * kRsTile;
+    if (base >= n) {  // a block past the live count (capacity-sized grids): empty histogram column
+        hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = 0u;
+        return;
+    }
     cnt[threadIdx.x] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kRsTile;
 #pragma unroll
     for (int k = 0; k < kRsItems; ++k) {
         const int64_t i = base + k * kRsThreads + threadIdx.x;
@@ -170,6 +174,7 @@ static __global__ void __launch_bounds__(kRsThreads) radix_downsweep_kernel(
     __shared__ uint2 stage[kRsTile];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int64_t bbase = (int64_t)blockIdx.x * kRsTile;
+    if (bbase >= n) return;  // nothing of this block is live (uniform over the block)
     const int64_t base = bbase + (int64_t)w * (32 * kRsItems);
     const unsigned lt = (1u << lane) - 1u;
     uint32_t key[kRsItems], val[kRsItems], rank[kRsItems], dig[kRsItems];
