@@ -151,8 +151,14 @@ def run_umgs(args, rank, world, local_rank):
     cov2 = torch.empty((n, 6), device=dev)
     out = torch.empty((1, H, W, 4), device=dev)
     gdef = umgs.DevGaussians(mu2, g.quats, g.scales, g.opacities, g.sh, g.sh_degree, cov3d=cov2)
-    opts = umgs.render_opts(16)
     frame = umgs.Frame(ctx)
+    # one synchronous render sizes the frame; the timed steps render
+    # asynchronously (no host read-back) into a pair capacity of 1.25x that
+    # count, and umgs_frame_check after the region confirms no step overflowed
+    umgs.deform(ctx, g, face, bary, PV, Vd_all[0], PF, out=(mu2, cov2, None))
+    umgs.render(ctx, gdef, [mesh], [cam], umgs.render_opts(16), out=out, frame=frame)
+    frame.reserve(int(frame.counts()[0] * 1.25) + 4096)
+    opts = umgs.render_opts(16, asynchronous=True)
 
     def step(f, vd=None):
         umgs.deform(ctx, g, face, bary, PV, Vd_all[f % nframes] if vd is None else vd, PF,
@@ -162,6 +168,7 @@ def run_umgs(args, rank, world, local_rank):
     for f in range(Wm):
         step(f)
     torch.cuda.synchronize()
+    frame.check()
     ctx.sync()
     if world > 1:
         torch.distributed.barrier()
@@ -182,6 +189,7 @@ def run_umgs(args, rank, world, local_rank):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clk = clocks.stop()
+    frame.check()
     ms_total = e0.elapsed_time(e1)
     stage_ms, stage_n = umgs.profile_read(ctx)
     umgs.profile_enable(ctx, False)
@@ -191,12 +199,14 @@ def run_umgs(args, rank, world, local_rank):
         ms_total = float(t.item())
     ms_step = ms_total / K
     value = K * world / (ms_total / 1e3)
+    # counts of the last timed frame's input, from a synchronous render of it
+    umgs.render(ctx, gdef, [mesh], [cam], umgs.render_opts(16), out=out, frame=frame)
     nkeys, ntiles = frame.counts()
 
     # forward + backward: the render keeps its backward state and the gradient
     # of a fixed synthetic upstream dL/d(rgb, T) is propagated to the deformed
     # Gaussians (means, cov3d, opacity, SH) and the mesh (vertices, colours, alpha)
-    opts_s = umgs.render_opts(16, save=True)
+    opts_s = umgs.render_opts(16, save=True, asynchronous=True)
     gen = torch.Generator(device=dev).manual_seed(1)
     dl = torch.randn((1, H, W, 4), generator=gen, device=dev) * 1e-3
 
@@ -221,6 +231,7 @@ def run_umgs(args, rank, world, local_rank):
         step_fb(f)
     b1.record()
     torch.cuda.synchronize()
+    frame.check()
     fb_ms = b0.elapsed_time(b1) / Kb
     fb_stage_ms, fb_stage_n = umgs.profile_read(ctx)
     umgs.profile_enable(ctx, False)
@@ -244,6 +255,7 @@ def run_umgs(args, rank, world, local_rank):
         host_out.copy_(out, non_blocking=True)
     a1.record()
     torch.cuda.synchronize()
+    frame.check()
     e2e_ms = a0.elapsed_time(a1) / Ke
     h2d = int(host_vd[0].numel() * 4)
     d2h = int(host_out.numel() * 4)
@@ -272,6 +284,7 @@ def run_umgs(args, rank, world, local_rank):
             umgs.render(ctx, gg, mm, [cam], opts, out=out, frame=frame)
         r1.record()
         torch.cuda.synchronize()
+        frame.check()
         return r0.elapsed_time(r1) / k
     render_ms = {"gaussians_and_mesh": round(t_render(gdef, [mesh]), 4),
                  "gaussians_only": round(t_render(gdef, []), 4),

@@ -96,9 +96,12 @@ enum {
     UMGS_RENDER_MIXED = 2,          /* Gaussian fragment records in fp16 (screen position fp32), fp32
                                        blending; pair with bf16 SH for the mixed-precision form.  Keys,
                                        footprints and order are unchanged (still exact); no backward. */
-    UMGS_RENDER_T_PRODUCT = 4       /* FULL mode only: inside an entity T <- T (1 - O_i alpha_i), the
+    UMGS_RENDER_T_PRODUCT = 4,      /* FULL mode only: inside an entity T <- T (1 - O_i alpha_i), the
                                        literal reading of Sec. 3.2's Eq. 6 instead of T = T_in mean_j t^j
                                        (the two agree for one-triangle entities); no backward. */
+    UMGS_RENDER_ASYNC = 8           /* no host read-back inside umgs_render: the (tile, primitive) pairs
+                                       are held to the frame's reserved capacity (umgs_frame_reserve);
+                                       check the result with umgs_frame_check */
 };
 
 typedef struct {
@@ -170,9 +173,14 @@ void umgs_frame_destroy(umgs_frame* frame);
  *            final transmittance T
  * frame      nullable; when given, the frame keeps everything
  *            umgs_render_backward needs (and the call uses its buffers)
- * Synchronises once per call on `stream` to read the number of keys.
+ * Synchronises once per call on `stream` to read the number of keys, except
+ * with UMGS_RENDER_ASYNC (then asynchronous on `stream`; the frame must have
+ * a pair capacity from umgs_frame_reserve, the number of keys is not known
+ * on the host afterwards, and a render that needs more pairs composites no
+ * tile and is reported by umgs_frame_check).
  * Errors: INVALID_ARG (NULL arrays with n > 0, ncams < 1, mixed image sizes,
- * tile_size not 8/16/32, sh_degree > 3), OUT_OF_MEMORY, CUDA.
+ * tile_size not 8/16/32, sh_degree > 3, ASYNC without a frame or capacity),
+ * OUT_OF_MEMORY, CUDA.
  */
 umgs_status umgs_render(umgs_ctx* ctx, const umgs_gaussians* gaussians,
                         const umgs_mesh* meshes, int32_t nmeshes,
@@ -181,8 +189,23 @@ umgs_status umgs_render(umgs_ctx* ctx, const umgs_gaussians* gaussians,
                         umgs_frame* frame, void* stream);
 
 /* Number of keys (tile, primitive) pairs and tiles (all cameras) of the last
- * render into `frame`.  Host outputs; synchronises nothing. */
+ * render into `frame` (num_keys = -1 after an asynchronous render).  Host
+ * outputs; synchronises nothing. */
 umgs_status umgs_frame_counts(const umgs_frame* frame, int64_t* num_keys, int64_t* num_tiles);
+
+/* Pair capacity of asynchronous renders (UMGS_RENDER_ASYNC) into `frame`:
+ * the pair buffers are sized to key_capacity at the next such render (an
+ * allocation at most once per growth).  A capacity from a synchronous
+ * render's count with some headroom (e.g. 1.25 x) suits a scene whose
+ * footprints change little between calls.  Errors: INVALID_ARG
+ * (key_capacity < 1). */
+umgs_status umgs_frame_reserve(umgs_frame* frame, int64_t key_capacity);
+
+/* Synchronises `stream` and reports the device-side conditions of the last
+ * asynchronous render into `frame`: CAPACITY if it needed more pairs than
+ * the reserved capacity (that render composited no tile: background, T = 1;
+ * reserve more and render again), INVALID_ARG for an out-of-range face index. */
+umgs_status umgs_frame_check(umgs_frame* frame, void* stream);
 
 /* Number of (pixel, fragment) evaluations of the last render into `frame`:
  * for every pixel, the entries of its tile list whose footprint (Gaussian

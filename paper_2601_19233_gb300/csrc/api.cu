@@ -183,10 +183,28 @@ umgs_status umgs_render(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_mesh*
     }
     umgs_frame* fr = frame ? frame : ctx->default_frame;
     if (fr->ctx != ctx) return fail(ctx, UMGS_ERR_INVALID_ARG, "frame belongs to another context");
+    const bool async = (opts.flags & UMGS_RENDER_ASYNC) != 0;
+    if (async && (!frame || frame->key_capacity < 1))
+        return fail(ctx, UMGS_ERR_INVALID_ARG, "UMGS_RENDER_ASYNC needs a frame with a reserved pair capacity");
     umgs_gaussians empty;
     std::memset(&empty, 0, sizeof(empty));
-    return render_forward(ctx, g ? g : &empty, meshes, nmeshes, cams, ncams, opts, out_rgbt, fr,
-                          static_cast<cudaStream_t>(stream));
+    fr->nosync = async;
+    const umgs_status st = render_forward(ctx, g ? g : &empty, meshes, nmeshes, cams, ncams, opts, out_rgbt, fr,
+                                          static_cast<cudaStream_t>(stream));
+    fr->nosync = false;
+    return st;
+}
+
+umgs_status umgs_frame_reserve(umgs_frame* frame, int64_t key_capacity) {
+    if (!frame || key_capacity < 1) return UMGS_ERR_INVALID_ARG;
+    frame->key_capacity = key_capacity;
+    return UMGS_OK;
+}
+
+umgs_status umgs_frame_check(umgs_frame* frame, void* stream) {
+    if (!frame) return UMGS_ERR_INVALID_ARG;
+    frame->ctx->err.clear();
+    return frame_check(frame, static_cast<cudaStream_t>(stream));
 }
 
 umgs_status umgs_render_backward(umgs_ctx* ctx, umgs_frame* frame, const umgs_gaussians* g,

@@ -44,7 +44,11 @@ umgs_status umgs_render_graph_create(umgs_ctx* ctx, umgs_frame* frame, const umg
     if (!(key_headroom >= 1.f)) key_headroom = 1.25f;
     // 1) sizing render (ordinary, synchronising): validates the arguments,
     //    sizes every buffer and uploads the cameras
-    umgs_status st = umgs_render(ctx, g, meshes, nmeshes, cams, ncams, opts, out_rgbt, frame, stream);
+    umgs_render_opts so;
+    umgs_default_render_opts(&so);
+    if (opts) so = *opts;
+    so.flags &= ~UMGS_RENDER_ASYNC;  // the sizing render reads the pair count back
+    umgs_status st = umgs_render(ctx, g, meshes, nmeshes, cams, ncams, &so, out_rgbt, frame, stream);
     if (st != UMGS_OK) return st;
     cudaStream_t us = static_cast<cudaStream_t>(stream);
     if (cudaStreamSynchronize(us) != cudaSuccess) return fail(ctx, UMGS_ERR_CUDA, "cudaStreamSynchronize");
@@ -71,10 +75,9 @@ umgs_status umgs_render_graph_create(umgs_ctx* ctx, umgs_frame* frame, const umg
     const bool prof = ctx->prof.on;
     ctx->prof.on = false;
     frame->nosync = true;
+    frame->capture = true;
     frame->key_capacity = Kcap;
-    umgs_render_opts o;
-    umgs_default_render_opts(&o);
-    if (opts) o = *opts;
+    umgs_render_opts o = so;
     if (o.tile_size == 0) o.tile_size = 16;
     const long long launches0 = g_kernel_launches.load();
     cudaError_t e = cudaStreamBeginCapture(gr->cap, cudaStreamCaptureModeThreadLocal);
@@ -88,6 +91,7 @@ umgs_status umgs_render_graph_create(umgs_ctx* ctx, umgs_frame* frame, const umg
         gr->graph = graph;
     }
     frame->nosync = false;
+    frame->capture = false;
     ctx->prof.on = prof;
     if (e != cudaSuccess) return graph_fail(ctx, gr, UMGS_ERR_CUDA, std::string("stream capture: ") + cudaGetErrorName(e));
     if (st != UMGS_OK) return graph_fail(ctx, gr, st, "render during capture: " + ctx->err);
@@ -110,15 +114,9 @@ umgs_status umgs_graph_launch(umgs_graph* gr, void* stream) {
 umgs_status umgs_graph_check(umgs_graph* gr, void* stream) {
     if (!gr) return UMGS_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    int32_t w[2] = {0, 0};
-    if (cudaMemcpyAsync(w, gr->frame->status.ptr, sizeof(w), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-        cudaStreamSynchronize(s) != cudaSuccess)
-        return fail(gr->ctx, UMGS_ERR_CUDA, "reading the frame status");
-    if (w[0] & 1) return fail(gr->ctx, UMGS_ERR_INVALID_ARG, "a face index is out of range");
-    if (w[0] & 4)
-        return fail(gr->ctx, UMGS_ERR_CAPACITY, "more (tile, primitive) pairs than the graph's capacity (" +
-                                                     std::to_string(gr->frame->key_capacity) + "): re-create it");
-    return UMGS_OK;
+    const umgs_status st = frame_check(gr->frame, s);
+    if (st == UMGS_ERR_CAPACITY) gr->ctx->err += ": re-create the graph";
+    return st;
 }
 
 void umgs_graph_destroy(umgs_graph* gr) {

@@ -49,8 +49,9 @@ struct umgs_frame {
     int32_t stack_cap = 8;
     bool saved = false;
     bool mixed = false;               // Gaussian records in fp16 (GRec16)
-    bool nosync = false;              // capture-safe mode: no host read-back inside umgs_render
-    int64_t key_capacity = 0;         // pair capacity in capture-safe mode
+    bool nosync = false;              // no host read-back inside umgs_render (async and graph capture)
+    bool capture = false;             // inside a graph capture: buffers and cameras already in place
+    int64_t key_capacity = 0;         // pair capacity when there is no read-back
     umgs_render_opts opts{};
     int64_t ng = 0, nt = 0;          // Gaussians, triangles (all meshes)
     int32_t ncams = 0, W = 0, H = 0;
@@ -146,6 +147,7 @@ umgs_status render_backward(umgs_ctx* ctx, umgs_frame* fr, const umgs_gaussians*
                             int32_t nmeshes, const float* dL_drgbt, const umgs_gaussian_grads* gg,
                             const umgs_mesh_grads* mg, cudaStream_t stream);
 
+umgs_status frame_check(umgs_frame* fr, cudaStream_t stream);
 umgs_status frame_evaluations(const umgs_frame* fr, int64_t* evals, cudaStream_t stream);
 umgs_status frame_lists(const umgs_frame* fr, int64_t* tile_ptr, int32_t* ids, uint32_t* dbits,
                         cudaStream_t stream);

@@ -1064,8 +1064,8 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
         }
         d.pad = 0;
     }
-    // (capture-safe mode: the cameras were uploaded by the sizing render)
-    if (!fr->nosync)
+    // (inside a graph capture the cameras were uploaded by the sizing render)
+    if (!fr->capture)
         UMGS_TRY(cudaMemcpyAsync(fr->cams.ptr, dc.data(), sizeof(DevCam) * ncams, cudaMemcpyHostToDevice, stream));
     UMGS_TRY(cudaMemsetAsync(fr->status.ptr, 0, sizeof(int32_t) * 16, stream));
 
@@ -1151,10 +1151,17 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
         UMGS_TRY(fr->tk2.reserve(sizeof(uint32_t) * std::max<int64_t>(1, K)));
         UMGS_TRY(fr->tv2.reserve(sizeof(uint32_t) * std::max<int64_t>(1, K)));
     } else {
-        // capture-safe: no host read-back; buffers were sized beforehand and an
-        // overflow is flagged in the status word (bit 2)
+        // no host read-back: the pairs are held to the reserved capacity and an
+        // overflow is flagged in the status word (bit 2); inside a capture the
+        // buffers were sized beforehand
         Kcap = fr->key_capacity;
         fr->num_keys = -1;
+        if (!fr->capture) {
+            UMGS_TRY(fr->tk.reserve(sizeof(uint32_t) * std::max<int64_t>(1, Kcap)));
+            UMGS_TRY(fr->tv.reserve(sizeof(uint32_t) * std::max<int64_t>(1, Kcap)));
+            UMGS_TRY(fr->tk2.reserve(sizeof(uint32_t) * std::max<int64_t>(1, Kcap)));
+            UMGS_TRY(fr->tv2.reserve(sizeof(uint32_t) * std::max<int64_t>(1, Kcap)));
+        }
     }
     fr->ids = fr->tv.as<uint32_t>();
     fr->tkeys = fr->tk.as<uint32_t>();
@@ -1270,6 +1277,18 @@ umgs_status frame_evaluations(const umgs_frame* fr, int64_t* evals, cudaStream_t
         return cuda_fail(fr->ctx, e, "reading the evaluation count");
     std::memcpy(&v, fr->ctx->pinned, sizeof(v));
     *evals = (int64_t)v;
+    return UMGS_OK;
+}
+
+umgs_status frame_check(umgs_frame* fr, cudaStream_t stream) {
+    int32_t* w = reinterpret_cast<int32_t*>(fr->ctx->pinned);
+    cudaError_t e = cudaMemcpyAsync(w, fr->status.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(fr->ctx, e, "reading the frame status");
+    if (w[0] & 1) return fail(fr->ctx, UMGS_ERR_INVALID_ARG, "a face index is out of range");
+    if (w[0] & 4)
+        return fail(fr->ctx, UMGS_ERR_CAPACITY, "more (tile, primitive) pairs than the reserved capacity (" +
+                                                     std::to_string(fr->key_capacity) + ")");
     return UMGS_OK;
 }
 

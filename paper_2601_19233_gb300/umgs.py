@@ -26,6 +26,7 @@ BIND_BBX, BIND_CENTER, BIND_NEAREST = 0, 1, 2
 RENDER_SAVE_BACKWARD = 1
 RENDER_MIXED = 2
 RENDER_T_PRODUCT = 4
+RENDER_ASYNC = 8
 DEFORM_FRAME, DEFORM_LITERAL = 0, 1
 
 
@@ -118,6 +119,10 @@ def lib():
             getattr(L, name).restype = ctypes.c_int
         L.umgs_profile_enable.argtypes = [vp, i32]
         L.umgs_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
+        L.umgs_frame_reserve.argtypes = [vp, i64]
+        L.umgs_frame_reserve.restype = ctypes.c_int
+        L.umgs_frame_check.argtypes = [vp, vp]
+        L.umgs_frame_check.restype = ctypes.c_int
         L.umgs_kernel_launches.argtypes = []
         L.umgs_kernel_launches.restype = ctypes.c_longlong
         for name in ("umgs_profile_enable", "umgs_profile_read", "umgs_ctx_create", "umgs_frame_create", "umgs_render", "umgs_frame_counts",
@@ -182,6 +187,14 @@ class Frame:
         k, t = ctypes.c_int64(), ctypes.c_int64()
         self.ctx.check(lib().umgs_frame_counts(self._h, ctypes.byref(k), ctypes.byref(t)), "umgs_frame_counts")
         return k.value, t.value
+
+    def reserve(self, key_capacity: int):
+        """umgs_frame_reserve: pair capacity of asynchronous renders into this frame."""
+        self.ctx.check(lib().umgs_frame_reserve(self._h, ctypes.c_int64(int(key_capacity))), "umgs_frame_reserve")
+
+    def check(self, stream=None):
+        """umgs_frame_check: raises on a pair-capacity overflow or bad face index of an asynchronous render."""
+        self.ctx.check(lib().umgs_frame_check(self._h, _stream(stream)), "umgs_frame_check")
 
     def evaluations(self):
         """(pixel, fragment) evaluations of the last render (synchronises)."""
@@ -274,12 +287,12 @@ def mesh_to_device(m, device="cuda") -> DevMesh:
 
 
 def render_opts(tile_size=16, blend_mode=BLEND_FULL, t_eps=1e-4, bg=(0.0, 0.0, 0.0), save=False,
-                mixed=False, sched=0, t_product=False) -> CRenderOpts:
+                mixed=False, sched=0, t_product=False, asynchronous=False) -> CRenderOpts:
     o = CRenderOpts()
     lib().umgs_default_render_opts(ctypes.byref(o))
     o.sched = int(sched)
     o.flags = ((RENDER_SAVE_BACKWARD if save else 0) | (RENDER_MIXED if mixed else 0)
-               | (RENDER_T_PRODUCT if t_product else 0))
+               | (RENDER_T_PRODUCT if t_product else 0) | (RENDER_ASYNC if asynchronous else 0))
     o.tile_size = int(tile_size)
     o.blend_mode = int(blend_mode)
     o.t_eps = float(t_eps)

@@ -109,3 +109,32 @@ def test_autotune_picks_a_valid_config(ctx):
     ref = umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(16)).cpu().numpy()
     got = umgs.render(ctx, g, ms, sc.cameras, best).cpu().numpy()
     assert np.array_equal(got, ref)
+
+
+def test_async_render_matches_sync_and_reports_overflow(ctx):
+    from paper_2601_19233_gb300 import umgs
+    sc = _clustered(13)
+    g, ms = _dev(sc)
+    fr = umgs.Frame(ctx)
+    ref = umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(16), frame=fr).clone()
+    K = fr.counts()[0]
+    fa = umgs.Frame(ctx)
+    fa.reserve(K + 16)
+    aopts = umgs.render_opts(16, asynchronous=True)
+    for _ in range(2):
+        out = umgs.render(ctx, g, ms, sc.cameras, aopts, frame=fa)
+        fa.check()
+        assert torch.equal(out, ref)
+    assert fa.counts()[0] == -1
+    # too small a capacity: reported, and no tile is composited
+    fs = umgs.Frame(ctx)
+    fs.reserve(K // 2)
+    out = umgs.render(ctx, g, ms, sc.cameras, aopts, frame=fs)
+    with pytest.raises(umgs.UmgsError) as e:
+        fs.check()
+    assert e.value.status == 3
+    assert torch.all(out[..., 3] == 1.0)
+    # asynchronous without a reserved capacity is refused
+    with pytest.raises(umgs.UmgsError) as e:
+        umgs.render(ctx, g, ms, sc.cameras, aopts, frame=umgs.Frame(ctx))
+    assert e.value.status == 1
