@@ -145,6 +145,12 @@ def run_umgs(args, rank, world, local_rank):
     face, bary, bind_info = umgs.bind_or_fallback(ctx, g, PV, PF, sc.bind_cameras, dev)
     torch.cuda.synchronize()
     bind_s = time.time() - t0
+    # the binding regrouped per Gaussian into its distinct proxy vertices and
+    # weights (once, like the binding itself); every step deforms through it
+    t0 = time.time()
+    bcount, bent = umgs.binding_compact(ctx, face, bary, PF, PV.shape[0])
+    torch.cuda.synchronize()
+    compact_s = time.time() - t0
 
     n = g.n
     mu2 = torch.empty((n, 3), device=dev)
@@ -155,14 +161,14 @@ def run_umgs(args, rank, world, local_rank):
     # one synchronous render sizes the frame; the timed steps render
     # asynchronously (no host read-back) into a pair capacity of 1.25x that
     # count, and umgs_frame_check after the region confirms no step overflowed
-    umgs.deform(ctx, g, face, bary, PV, Vd_all[0], PF, out=(mu2, cov2, None))
+    umgs.deform_compact(ctx, g, bcount, bent, PV, Vd_all[0], PF, out=(mu2, cov2, None))
     umgs.render(ctx, gdef, [mesh], [cam], umgs.render_opts(16), out=out, frame=frame)
     frame.reserve(int(frame.counts()[0] * 1.25) + 4096)
     opts = umgs.render_opts(16, asynchronous=True)
 
     def step(f, vd=None):
-        umgs.deform(ctx, g, face, bary, PV, Vd_all[f % nframes] if vd is None else vd, PF,
-                    out=(mu2, cov2, None))
+        umgs.deform_compact(ctx, g, bcount, bent, PV, Vd_all[f % nframes] if vd is None else vd, PF,
+                            out=(mu2, cov2, None))
         umgs.render(ctx, gdef, [mesh], [cam], opts, out=out, frame=frame)
 
     for f in range(Wm):
@@ -216,7 +222,7 @@ def run_umgs(args, rank, world, local_rank):
         return umgs.render_backward(ctx, frame, gdef, [mesh], dl)
 
     def step_deform(f):
-        umgs.deform(ctx, g, face, bary, PV, Vd_all[f % nframes], PF, out=(mu2, cov2, None))
+        umgs.deform_compact(ctx, g, bcount, bent, PV, Vd_all[f % nframes], PF, out=(mu2, cov2, None))
 
     for f in range(max(2, Wm)):
         step_fb(f)
@@ -293,7 +299,9 @@ def run_umgs(args, rank, world, local_rank):
     names = stage_names()
     stages = {names[k]: {"ms_per_launch": stage_ms[k] / stage_n[k], "launches": int(stage_n[k])}
               for k in range(16) if stage_n[k] > 0}
-    roof = roofline(stages, nkeys, n, sc, clk, evals, ms_step)
+    # algorithmic binding bytes per Gaussian: its count and its used entries
+    bind_bytes = 4.0 + 8.0 * float(bcount.float().mean())
+    roof = roofline(stages, nkeys, n, sc, clk, evals, ms_step, bind_bytes)
     comp_ms = stages["composite"]["ms_per_launch"] if "composite" in stages else float("nan")
     frags = {"n_alg": int(evals), "mfragments_per_s": round(evals / comp_ms / 1e3, 1),
              "tile_pairs": tile_pairs, "tile_pairs_over_n_alg": round(tile_pairs / max(evals, 1), 3)}
@@ -313,6 +321,7 @@ def run_umgs(args, rank, world, local_rank):
                     "steps": Kb, "backward_stages_ms": {names[k]: round(fb_stage_ms[k] / fb_stage_n[k], 4)
                                                         for k in (12, 13) if fb_stage_n[k] > 0}},
         "bind_s": round(bind_s, 3),
+        "binding_compact_s": round(compact_s, 4),
         "fragments": frags,
         "render_ms": render_ms,
         "roofline": roof,
@@ -328,7 +337,7 @@ def run_umgs(args, rank, world, local_rank):
         torch.distributed.destroy_process_group()
 
 
-def roofline(stages, nkeys, n, sc, clk, evals, ms_step):
+def roofline(stages, nkeys, n, sc, clk, evals, ms_step, bind_bytes=96.0):
     """Roofline of the dominant stage, plus HBM figures of the streaming stages.
 
     composite: ALU-bound; algorithmic work = 12 FP32 operations per
@@ -350,7 +359,7 @@ def roofline(stages, nkeys, n, sc, clk, evals, ms_step):
         "project_gaussians": ng * (12 + 28 + 4 + 36 + 16),
         "shade_gaussians": ng * (192 + 12 + 16 + 12),
         "setup_triangles": nt * (12 + 16 + 160 + 16) + sc.meshes[0].nv * 28,
-        "deform_gaussians": ng * (96 + 40 + 36),
+        "deform_gaussians": ng * (bind_bytes + 40 + 36),
         "deform_faces": npf * (12 + 72) + npv * 40,
         "deform_vertices": npv * (40 + 24 + 48),
         # records: info read, (depth, id) pair written, one read+write of the

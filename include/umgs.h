@@ -318,6 +318,30 @@ umgs_status umgs_deform(umgs_ctx* ctx, const umgs_gaussians* rest, const int32_t
  * caller buffer [nv,12] (Delta xyz, r xyz, S xx xy xz yy yz zz).  Async. */
 umgs_status umgs_deform_vertex_table(umgs_ctx* ctx, float* out_table, int64_t nv, void* stream);
 
+/* Compact binding: a regrouping of Eq. 12-13, not a step of the paper.
+ * Every interpolant that Eq. 13 averages is linear in the proxy vertex
+ * rows, so a Gaussian's deformation needs only its distinct bound vertices v
+ * and the weights w_v = (1/8) x (sum over its 8 bound points of the
+ * barycentric weight of v).  umgs_binding_compact derives them once from a
+ * binding as umgs_bind writes it (face [n,8], bary [n,8,2]) and the proxy
+ * faces:
+ *   out_count   [n] int32 device: distinct vertices (1..24), or -1 for an
+ *               out-of-range face or vertex index
+ *   out_entries [n,24,2] int32 device: (vertex id, weight as float bits);
+ *               the first out_count[i] are used, in order of first appearance
+ * umgs_deform_compact is umgs_deform (same modes, outputs and errors; NaN and
+ * a status bit for a -1 count) over that form: about 10 vertex rows gathered
+ * per Gaussian instead of 24; it agrees with umgs_deform up to fp32
+ * summation order.  Both asynchronous on `stream`; bary and the entries
+ * 8-byte aligned.  Errors: INVALID_ARG (sizes, NULL arrays, alignment), CUDA. */
+umgs_status umgs_binding_compact(umgs_ctx* ctx, const int32_t* face, const float* bary, int64_t n,
+                                 const int32_t* proxy_f, int64_t nv, int64_t nf, int32_t* out_count,
+                                 int32_t* out_entries, void* stream);
+umgs_status umgs_deform_compact(umgs_ctx* ctx, const umgs_gaussians* rest, const int32_t* count,
+                                const int32_t* entries, const float* proxy_v, const float* proxy_vd,
+                                const int32_t* proxy_f, int64_t nv, int64_t nf, int32_t mode, float* out_means,
+                                float* out_cov3d, float* out_quats, void* stream);
+
 /* ---- multi-view form: CUDA graph and autotuning -----------------------------
  *
  * umgs_render_graph_create renders once (an ordinary umgs_render into

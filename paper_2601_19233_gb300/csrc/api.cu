@@ -254,6 +254,42 @@ umgs_status umgs_deform(umgs_ctx* ctx, const umgs_gaussians* rest, const int32_t
                           out_quats, static_cast<cudaStream_t>(stream));
 }
 
+umgs_status umgs_binding_compact(umgs_ctx* ctx, const int32_t* face, const float* bary, int64_t n,
+                                 const int32_t* proxy_f, int64_t nv, int64_t nf, int32_t* out_count,
+                                 int32_t* out_entries, void* stream) {
+    if (!ctx) return UMGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, UMGS_ERR_CUDA, "cudaSetDevice");
+    if (n < 0 || nv < 3 || nf < 1 || !proxy_f) return fail(ctx, UMGS_ERR_INVALID_ARG, "bad sizes or proxy mesh");
+    if (n > 0 && (!face || !bary || !out_count || !out_entries)) return fail(ctx, UMGS_ERR_INVALID_ARG, "NULL array");
+    if ((reinterpret_cast<uintptr_t>(bary) | reinterpret_cast<uintptr_t>(out_entries)) & 7)
+        return fail(ctx, UMGS_ERR_INVALID_ARG, "bary and out_entries must be 8-byte aligned");
+    return binding_compact(ctx, face, bary, n, proxy_f, nv, nf, out_count, reinterpret_cast<int2*>(out_entries),
+                           static_cast<cudaStream_t>(stream));
+}
+
+umgs_status umgs_deform_compact(umgs_ctx* ctx, const umgs_gaussians* rest, const int32_t* count,
+                                const int32_t* entries, const float* proxy_v, const float* proxy_vd,
+                                const int32_t* proxy_f, int64_t nv, int64_t nf, int32_t mode, float* out_means,
+                                float* out_cov3d, float* out_quats, void* stream) {
+    if (!ctx) return UMGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, UMGS_ERR_CUDA, "cudaSetDevice");
+    if (!rest || rest->n < 0) return fail(ctx, UMGS_ERR_INVALID_ARG, "rest Gaussians missing");
+    if (mode != UMGS_DEFORM_FRAME && mode != UMGS_DEFORM_LITERAL) return fail(ctx, UMGS_ERR_INVALID_ARG, "bad mode");
+    if (!proxy_v || !proxy_vd || !proxy_f || nv < 3 || nf < 1) return fail(ctx, UMGS_ERR_INVALID_ARG, "bad proxy mesh");
+    if (rest->n > 0) {
+        if (!rest->means || !count || !entries || !out_means || !out_cov3d)
+            return fail(ctx, UMGS_ERR_INVALID_ARG, "NULL array");
+        if (!rest->cov3d && (!rest->quats || !rest->scales))
+            return fail(ctx, UMGS_ERR_INVALID_ARG, "need quats+scales or cov3d");
+        if (reinterpret_cast<uintptr_t>(entries) & 7) return fail(ctx, UMGS_ERR_INVALID_ARG, "entries must be 8-byte aligned");
+    }
+    return deform_compact_forward(ctx, rest, count, reinterpret_cast<const int2*>(entries), proxy_v, proxy_vd,
+                                  proxy_f, nv, nf, mode, out_means, out_cov3d, out_quats,
+                                  static_cast<cudaStream_t>(stream));
+}
+
 umgs_status umgs_bind(umgs_ctx* ctx, const umgs_gaussians* g, const float* proxy_v, const int32_t* proxy_f,
                       int64_t nv, int64_t nf, const umgs_camera* cams, int32_t ncams, int32_t mode, float k_sigma,
                       int32_t* out_face, float* out_bary, float* out_dist, uint8_t* out_flags,

@@ -264,54 +264,16 @@ __device__ void exp_rot(const float r[3], float R[9], float q[4]) {
     q[0] = hc; q[1] = hs * x; q[2] = hs * y; q[3] = hs * z;
 }
 
-// One thread per (Gaussian, bound point): 8 consecutive lanes gather the
-// Eq. 12 interpolants of one Gaussian's 8 points (independent loads, and a
-// single broadcast when points share a face), reduce them with shuffles and
-// then all 8 lanes evaluate Eq. 13; lanes 0-2 write mu', Sigma', q'.
-__global__ void __launch_bounds__(256) deform_gaussians_kernel(
-    const float* __restrict__ means, const float* __restrict__ quats, const float* __restrict__ scales,
-    const float* __restrict__ cov3d, int64_t n, const int32_t* __restrict__ face, const float* __restrict__ bary,
-    const float* __restrict__ V, const int32_t* __restrict__ F, int64_t nv, int64_t nf,
-    const float* __restrict__ vtab, int mode, float* __restrict__ out_means, float* __restrict__ out_cov,
-    float* __restrict__ out_quats, int32_t* __restrict__ status) {
-    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t i = tid >> 3;
-    const int corner = (int)(tid & 7);
-    const bool live = i < n;
-    float acc[15];
-#pragma unroll
-    for (int e = 0; e < 15; ++e) acc[e] = 0.f;
-    int bad = 0;
-    if (live) {
-        const int f = face[8 * i + corner];
-        const float2 b = reinterpret_cast<const float2*>(bary)[8 * i + corner];
-        if (f < 0 || f >= nf) {
-            bad = 1;
-        } else {
-            const float w[3] = {1.f - b.x - b.y, b.x, b.y};
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const int v = F[3 * (int64_t)f + k];
-                if (v < 0 || v >= nv) { bad = 1; continue; }
-                const float4* row = reinterpret_cast<const float4*>(vtab + 12 * (int64_t)v);
-                const float4 t0 = row[0], t1 = row[1], t2 = row[2];
-                const float px = V[3 * (int64_t)v], py = V[3 * (int64_t)v + 1], pz = V[3 * (int64_t)v + 2];
-                const float wk = w[k];
-                acc[0] += wk * t0.x; acc[1] += wk * t0.y; acc[2] += wk * t0.z;     // Delta
-                acc[3] += wk * t0.w; acc[4] += wk * t1.x; acc[5] += wk * t1.y;     // log R
-                acc[6] += wk * t1.z; acc[7] += wk * t1.w; acc[8] += wk * t2.x;     // S
-                acc[9] += wk * t2.y; acc[10] += wk * t2.z; acc[11] += wk * t2.w;
-                acc[12] += wk * px; acc[13] += wk * py; acc[14] += wk * pz;         // P
-            }
-        }
-    }
-    // sum over the 8 lanes of this Gaussian
-#pragma unroll
-    for (int o = 4; o > 0; o >>= 1) {
-#pragma unroll
-        for (int e = 0; e < 15; ++e) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
-        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
-    }
+// Eq. 13 for one Gaussian from acc = scale^-1 x the means of its bound
+// points' Eq. 12 interpolants (Delta, log R, S (6), rest position P) and
+// bad (an index was out of range), held by every lane of the Gaussian:
+// lanes corner 0, 1, 2 write mu', Sigma', q' (NaN and a status bit if bad).
+__device__ __forceinline__ void deform_finish(const float (&acc)[15], float scale, int bad, bool live, int corner,
+                                              int64_t i, const float* __restrict__ means,
+                                              const float* __restrict__ quats, const float* __restrict__ scales,
+                                              const float* __restrict__ cov3d, int mode, float* __restrict__ out_means,
+                                              float* __restrict__ out_cov, float* __restrict__ out_quats,
+                                              int32_t* __restrict__ status) {
     if (!live || corner > 2) return;
     if (bad) {
         if (corner == 0) atomicOr(status, kStatusBadIndex);
@@ -321,7 +283,7 @@ __global__ void __launch_bounds__(256) deform_gaussians_kernel(
         if (corner == 2 && out_quats) for (int d = 0; d < 4; ++d) out_quats[4 * i + d] = nanv;
         return;
     }
-    const float e = 0.125f;
+    const float e = scale;
     float rb[3] = {acc[3] * e, acc[4] * e, acc[5] * e};
     float Rp[9], qr[4];
     exp_rot(rb, Rp, qr);
@@ -386,11 +348,147 @@ __global__ void __launch_bounds__(256) deform_gaussians_kernel(
     }
 }
 
+// One thread per (Gaussian, bound point): 8 consecutive lanes gather the
+// Eq. 12 interpolants of one Gaussian's 8 points (independent loads, and a
+// single broadcast when points share a face), reduce them with shuffles and
+// then all 8 lanes evaluate Eq. 13; lanes 0-2 write mu', Sigma', q'.
+__global__ void __launch_bounds__(256) deform_gaussians_kernel(
+    const float* __restrict__ means, const float* __restrict__ quats, const float* __restrict__ scales,
+    const float* __restrict__ cov3d, int64_t n, const int32_t* __restrict__ face, const float* __restrict__ bary,
+    const float* __restrict__ V, const int32_t* __restrict__ F, int64_t nv, int64_t nf,
+    const float* __restrict__ vtab, int mode, float* __restrict__ out_means, float* __restrict__ out_cov,
+    float* __restrict__ out_quats, int32_t* __restrict__ status) {
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = tid >> 3;
+    const int corner = (int)(tid & 7);
+    const bool live = i < n;
+    float acc[15];
+#pragma unroll
+    for (int e = 0; e < 15; ++e) acc[e] = 0.f;
+    int bad = 0;
+    if (live) {
+        const int f = face[8 * i + corner];
+        const float2 b = reinterpret_cast<const float2*>(bary)[8 * i + corner];
+        if (f < 0 || f >= nf) {
+            bad = 1;
+        } else {
+            const float w[3] = {1.f - b.x - b.y, b.x, b.y};
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int v = F[3 * (int64_t)f + k];
+                if (v < 0 || v >= nv) { bad = 1; continue; }
+                const float4* row = reinterpret_cast<const float4*>(vtab + 12 * (int64_t)v);
+                const float4 t0 = row[0], t1 = row[1], t2 = row[2];
+                const float px = V[3 * (int64_t)v], py = V[3 * (int64_t)v + 1], pz = V[3 * (int64_t)v + 2];
+                const float wk = w[k];
+                acc[0] += wk * t0.x; acc[1] += wk * t0.y; acc[2] += wk * t0.z;     // Delta
+                acc[3] += wk * t0.w; acc[4] += wk * t1.x; acc[5] += wk * t1.y;     // log R
+                acc[6] += wk * t1.z; acc[7] += wk * t1.w; acc[8] += wk * t2.x;     // S
+                acc[9] += wk * t2.y; acc[10] += wk * t2.z; acc[11] += wk * t2.w;
+                acc[12] += wk * px; acc[13] += wk * py; acc[14] += wk * pz;         // P
+            }
+        }
+    }
+    // sum over the 8 lanes of this Gaussian
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+#pragma unroll
+        for (int e = 0; e < 15; ++e) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    deform_finish(acc, 0.125f, bad, live, corner, i, means, quats, scales, cov3d, mode, out_means, out_cov,
+                  out_quats, status);
+}
+
+// Compact binding (Sec. 3.3, Eq. 12-13 regrouped): every interpolant that
+// Eq. 13 averages is linear in the vertex rows, so a Gaussian's means are
+// sum_v w_v row(v) with w_v = (1/8) x the barycentric weights of vertex v
+// summed over its 8 bound points.  One thread per Gaussian merges its 24
+// (vertex, weight) terms into its distinct vertices (in order of first
+// appearance); count -1 marks an out-of-range face or vertex index.
+__global__ void __launch_bounds__(256) binding_compact_kernel(const int32_t* __restrict__ face,
+                                                              const float* __restrict__ bary, int64_t n,
+                                                              const int32_t* __restrict__ F, int64_t nv, int64_t nf,
+                                                              int32_t* __restrict__ count,
+                                                              int2* __restrict__ entries) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int2* out = entries + 24 * i;
+    int c = 0;
+    for (int p = 0; p < 8; ++p) {
+        const int f = face[8 * i + p];
+        const float2 b = reinterpret_cast<const float2*>(bary)[8 * i + p];
+        if (f < 0 || f >= nf) { c = -1; break; }
+        const float wk[3] = {1.f - b.x - b.y, b.x, b.y};
+        bool bad = false;
+        for (int k = 0; k < 3; ++k) {
+            const int v = F[3 * (int64_t)f + k];
+            if (v < 0 || v >= nv) { bad = true; break; }
+            const float w = 0.125f * wk[k];
+            int j = 0;
+            while (j < c && out[j].x != v) ++j;
+            if (j < c) out[j].y = __float_as_int(__int_as_float(out[j].y) + w);
+            else { out[c] = make_int2(v, __float_as_int(w)); ++c; }
+        }
+        if (bad) { c = -1; break; }
+    }
+    count[i] = c;
+}
+
+// Deformation over a compact binding: four lanes per Gaussian share its
+// entries (lane l takes entries l, l+4, ...: consecutive lanes read
+// consecutive 8-byte entries), gather the weighted vertex rows (48-byte table
+// row + rest position), reduce over the 4 lanes and finish as above.
+__global__ void __launch_bounds__(256) deform_gaussians_compact_kernel(
+    const float* __restrict__ means, const float* __restrict__ quats, const float* __restrict__ scales,
+    const float* __restrict__ cov3d, int64_t n, const int32_t* __restrict__ count, const int2* __restrict__ entries,
+    const float* __restrict__ V, int64_t nv, const float* __restrict__ vtab, int mode, float* __restrict__ out_means,
+    float* __restrict__ out_cov, float* __restrict__ out_quats, int32_t* __restrict__ status) {
+    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = tid >> 2;
+    const int part = (int)(tid & 3);
+    const bool live = i < n;
+    float acc[15];
+#pragma unroll
+    for (int e = 0; e < 15; ++e) acc[e] = 0.f;
+    int bad = 0;
+    if (live) {
+        const int c = count[i];
+        if (c < 0 || c > 24) {
+            bad = 1;
+        } else {
+            const int2* row = entries + 24 * i;
+            for (int j = part; j < c; j += 4) {
+                const int2 en = row[j];
+                const int v = en.x;
+                if (v < 0 || v >= nv) { bad = 1; continue; }
+                const float wk = __int_as_float(en.y);
+                const float4* t = reinterpret_cast<const float4*>(vtab + 12 * (int64_t)v);
+                const float4 t0 = t[0], t1 = t[1], t2 = t[2];
+                const float px = V[3 * (int64_t)v], py = V[3 * (int64_t)v + 1], pz = V[3 * (int64_t)v + 2];
+                acc[0] += wk * t0.x; acc[1] += wk * t0.y; acc[2] += wk * t0.z;     // Delta
+                acc[3] += wk * t0.w; acc[4] += wk * t1.x; acc[5] += wk * t1.y;     // log R
+                acc[6] += wk * t1.z; acc[7] += wk * t1.w; acc[8] += wk * t2.x;     // S
+                acc[9] += wk * t2.y; acc[10] += wk * t2.z; acc[11] += wk * t2.w;
+                acc[12] += wk * px; acc[13] += wk * py; acc[14] += wk * pz;         // P
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 2; o > 0; o >>= 1) {
+#pragma unroll
+        for (int e = 0; e < 15; ++e) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    deform_finish(acc, 1.f, bad, live, part, i, means, quats, scales, cov3d, mode, out_means, out_cov, out_quats,
+                  status);
+}
+
 static inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
 
-umgs_status deform_forward(umgs_ctx* ctx, const umgs_gaussians* g, const int32_t* face, const float* bary,
-                           const float* V, const float* Vd, const int32_t* F, int64_t nv, int64_t nf, int32_t mode,
-                           float* out_means, float* out_cov, float* out_quats, cudaStream_t stream) {
+// per-face gradients and the per-vertex table of the deformed proxy (A1)
+static umgs_status proxy_table(umgs_ctx* ctx, const float* V, const float* Vd, const int32_t* F, int64_t nv,
+                               int64_t nf, cudaStream_t stream) {
     cudaError_t e;
     if ((e = ctx->vacc.reserve(sizeof(float) * 10 * nv)) != cudaSuccess) return fail(ctx, UMGS_ERR_OUT_OF_MEMORY, "vacc");
     if ((e = ctx->vtab.reserve(sizeof(float) * 12 * nv)) != cudaSuccess) return fail(ctx, UMGS_ERR_OUT_OF_MEMORY, "vtab");
@@ -407,12 +505,48 @@ umgs_status deform_forward(umgs_ctx* ctx, const umgs_gaussians* g, const int32_t
         vertex_xforms_kernel<<<grid_for(nv, 256), 256, 0, stream>>>(V, Vd, ctx->vacc.as<float>(), nv,
                                                                     ctx->vtab.as<float>()), count_launch();
     }
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "proxy table kernels");
+    return UMGS_OK;
+}
+
+umgs_status deform_forward(umgs_ctx* ctx, const umgs_gaussians* g, const int32_t* face, const float* bary,
+                           const float* V, const float* Vd, const int32_t* F, int64_t nv, int64_t nf, int32_t mode,
+                           float* out_means, float* out_cov, float* out_quats, cudaStream_t stream) {
+    const umgs_status st = proxy_table(ctx, V, Vd, F, nv, nf, stream);
+    if (st != UMGS_OK) return st;
     StageTimer tm(ctx, UMGS_STAGE_DEFORM_GAUSSIANS, stream);
     if (g->n > 0)
         deform_gaussians_kernel<<<grid_for(8 * g->n, 256), 256, 0, stream>>>(
             g->means, g->quats, g->scales, g->cov3d, g->n, face, bary, V, F, nv, nf, ctx->vtab.as<float>(), mode,
-            out_means, out_cov, out_quats, status), count_launch();
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "deform kernels");
+            out_means, out_cov, out_quats, ctx->dstatus.as<int32_t>()), count_launch();
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "deform kernels");
+    return UMGS_OK;
+}
+
+umgs_status binding_compact(umgs_ctx* ctx, const int32_t* face, const float* bary, int64_t n, const int32_t* F,
+                            int64_t nv, int64_t nf, int32_t* out_count, int2* out_entries, cudaStream_t stream) {
+    if (n > 0)
+        binding_compact_kernel<<<grid_for(n, 256), 256, 0, stream>>>(face, bary, n, F, nv, nf, out_count,
+                                                                     out_entries), count_launch();
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "binding_compact_kernel");
+    return UMGS_OK;
+}
+
+umgs_status deform_compact_forward(umgs_ctx* ctx, const umgs_gaussians* g, const int32_t* count, const int2* entries,
+                                   const float* V, const float* Vd, const int32_t* F, int64_t nv, int64_t nf,
+                                   int32_t mode, float* out_means, float* out_cov, float* out_quats,
+                                   cudaStream_t stream) {
+    const umgs_status st = proxy_table(ctx, V, Vd, F, nv, nf, stream);
+    if (st != UMGS_OK) return st;
+    StageTimer tm(ctx, UMGS_STAGE_DEFORM_GAUSSIANS, stream);
+    if (g->n > 0)
+        deform_gaussians_compact_kernel<<<grid_for(4 * g->n, 256), 256, 0, stream>>>(
+            g->means, g->quats, g->scales, g->cov3d, g->n, count, entries, V, nv, ctx->vtab.as<float>(), mode,
+            out_means, out_cov, out_quats, ctx->dstatus.as<int32_t>()), count_launch();
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "deform kernels");
     return UMGS_OK;
 }
 

@@ -119,6 +119,11 @@ def lib():
             getattr(L, name).restype = ctypes.c_int
         L.umgs_profile_enable.argtypes = [vp, i32]
         L.umgs_profile_read.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
+        L.umgs_binding_compact.argtypes = [vp, vp, vp, i64, vp, i64, i64, vp, vp, vp]
+        L.umgs_binding_compact.restype = ctypes.c_int
+        L.umgs_deform_compact.argtypes = [vp, ctypes.POINTER(CGaussians), vp, vp, vp, vp, vp, i64, i64, i32, vp, vp,
+                                          vp, vp]
+        L.umgs_deform_compact.restype = ctypes.c_int
         L.umgs_frame_reserve.argtypes = [vp, i64]
         L.umgs_frame_reserve.restype = ctypes.c_int
         L.umgs_frame_check.argtypes = [vp, vp]
@@ -333,6 +338,37 @@ def deform(ctx: Context, rest: DevGaussians, face: torch.Tensor, bary: torch.Ten
                            _ptr(proxy_f), int(proxy_v.shape[0]), int(proxy_f.shape[0]), int(mode), _ptr(out[0]),
                            _ptr(out[1]), _ptr(out[2]), _stream(stream))
     ctx.check(st, "umgs_deform")
+    return out
+
+
+def binding_compact(ctx: Context, face: torch.Tensor, bary: torch.Tensor, proxy_f: torch.Tensor, nv: int,
+                    stream=None):
+    """umgs_binding_compact: (count int32 [n], entries int32 [n,24,2]) on the device."""
+    n = int(face.shape[0])
+    dev = torch.device("cuda", ctx.device)
+    count = torch.empty((n,), dtype=torch.int32, device=dev)
+    entries = torch.empty((n, 24, 2), dtype=torch.int32, device=dev)
+    ctx.check(lib().umgs_binding_compact(ctx._h, _ptr(face), _ptr(bary), n, _ptr(proxy_f), int(nv),
+                                         int(proxy_f.shape[0]), _ptr(count), _ptr(entries), _stream(stream)),
+              "umgs_binding_compact")
+    return count, entries
+
+
+def deform_compact(ctx: Context, rest: DevGaussians, count: torch.Tensor, entries: torch.Tensor,
+                   proxy_v: torch.Tensor, proxy_vd: torch.Tensor, proxy_f: torch.Tensor, mode=DEFORM_FRAME,
+                   out=None, with_quats=True, stream=None):
+    """umgs_deform_compact: umgs_deform over a compact binding; returns (means', cov3d', quats' or None)."""
+    n = rest.n
+    dev = torch.device("cuda", ctx.device)
+    if out is None:
+        out = (torch.empty((n, 3), dtype=torch.float32, device=dev),
+               torch.empty((n, 6), dtype=torch.float32, device=dev),
+               torch.empty((n, 4), dtype=torch.float32, device=dev) if with_quats else None)
+    cg = rest.c()
+    st = lib().umgs_deform_compact(ctx._h, ctypes.byref(cg), _ptr(count), _ptr(entries), _ptr(proxy_v),
+                                   _ptr(proxy_vd), _ptr(proxy_f), int(proxy_v.shape[0]), int(proxy_f.shape[0]),
+                                   int(mode), _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), _stream(stream))
+    ctx.check(st, "umgs_deform_compact")
     return out
 
 

@@ -101,3 +101,54 @@ def test_out_of_range_face_is_reported(ctx):
         _run(ctx, V, V, F, g, face, b)
     assert e.value.status == 1
     ctx.sync()  # status cleared
+
+
+def test_compact_binding_and_deformation(ctx):
+    from paper_2601_19233_gb300 import umgs
+    V, F, g, face, b = _problem(3)
+    Vd = S.displace(V, S.sinusoid_params(np.random.default_rng(8)), 23)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a)).cuda()
+    tf = t(F)
+    cnt, ent = umgs.binding_compact(ctx, t(face), t(b), tf, len(V))
+    cnt, ent = cnt.cpu().numpy(), ent.cpu().numpy()
+    # the compact form is the binding regrouped: distinct vertices, weights summing
+    # (1/8) x the barycentric weights of each vertex over the 8 points
+    for i in (0, 17, 4999):
+        wv = {}
+        for p in range(8):
+            w3 = (1.0 - b[i, p, 0] - b[i, p, 1], b[i, p, 0], b[i, p, 1])
+            for k in range(3):
+                v = int(F[face[i, p], k])
+                wv[v] = wv.get(v, 0.0) + 0.125 * float(w3[k])
+        assert cnt[i] == len(wv)
+        got = {int(ent[i, j, 0]): float(ent[i, j, 1:2].view(np.float32)[0]) for j in range(cnt[i])}
+        assert set(got) == set(wv)
+        assert max(abs(got[v] - wv[v]) for v in wv) < 1e-6
+    assert np.all((cnt >= 1) & (cnt <= 24))
+    for mode in (D.FRAME, D.LITERAL):
+        m0, c0, q0 = _run(ctx, V, Vd, F, g, face, b, mode)
+        dg = umgs.gaussians_to_device(g)
+        m1, c1, q1 = umgs.deform_compact(ctx, dg, t(cnt), t(ent), t(V.astype(np.float32)),
+                                         t(Vd.astype(np.float32)), tf, mode=mode)
+        m1, c1, q1 = m1.cpu().numpy(), c1.cpu().numpy(), q1.cpu().numpy()
+        assert np.abs(m1 - m0).max() < 2e-6
+        assert (np.abs(c1 - c0) / np.abs(c0).max(1, keepdims=True)).max() < 2e-5
+        assert _quat_err(q1, q0) < 2e-6
+        mr, Sr, qr = D.deform_gaussians(g.means, g.quats, g.scales, face, b, V, Vd, F, mode=mode)
+        assert np.abs(m1 - mr).max() < 1e-5
+        assert _cov_err(c1, Sr) < 1e-4
+
+
+def test_compact_binding_bad_index(ctx):
+    from paper_2601_19233_gb300 import umgs
+    V, F, g, face, b = _problem(4, n=64)
+    face[5, 3] = len(F) + 7
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a)).cuda()
+    cnt, ent = umgs.binding_compact(ctx, t(face), t(b), t(F), len(V))
+    assert int(cnt[5]) == -1 and int((cnt >= 1).sum()) == 63
+    m, c, q = umgs.deform_compact(ctx, umgs.gaussians_to_device(g), cnt, ent, t(V.astype(np.float32)),
+                                  t(V.astype(np.float32)), t(F))
+    with pytest.raises(umgs.UmgsError):
+        ctx.sync()
+    m = m.cpu().numpy()
+    assert np.all(np.isnan(m[5])) and np.all(np.isfinite(np.delete(m, 5, axis=0)))
