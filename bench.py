@@ -47,6 +47,19 @@ def parse():
     return p.parse_args()
 
 
+def aggregate_ranks(ms_local, steps, world, device=None):
+    """Whole-job timing over `world` replicas that each timed `steps` frames:
+    the slowest rank's time (all_reduce MAX) and the throughput of all ranks
+    together, steps * world frames in that time."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_local = float(t.item())
+    return ms_local, steps * world / (ms_local / 1e3)
+
+
 def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
@@ -199,12 +212,8 @@ def run_umgs(args, rank, world, local_rank):
     ms_total = e0.elapsed_time(e1)
     stage_ms, stage_n = umgs.profile_read(ctx)
     umgs.profile_enable(ctx, False)
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total, value = aggregate_ranks(ms_total, K, world, dev)
     ms_step = ms_total / K
-    value = K * world / (ms_total / 1e3)
     # counts of the last timed frame's input, from a synchronous render of it
     umgs.render(ctx, gdef, [mesh], [cam], umgs.render_opts(16), out=out, frame=frame)
     nkeys, ntiles = frame.counts()
