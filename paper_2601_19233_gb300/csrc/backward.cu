@@ -33,7 +33,13 @@
 
 namespace umgs {
 
-constexpr int kBatchB = 128;  // records per batch (shared-memory gradient accumulators beside them)
+// Records per batch and the dynamic shared memory of a CTA: the records
+// (160 B), their gradient accumulators (22 floats), ids, warp masks and the
+// per-warp lists.  16x16 tiles stage 192 records (51 KB: four CTAs per SM).
+template <int TS> struct BwdBatch { static constexpr int value = TS == 16 ? 192 : 128; };
+template <int TS> constexpr int bwd_smem_bytes() {
+    return BwdBatch<TS>::value * (160 + 88 + 4 + 4 + TS * TS / 32) + 4 * (TS * TS / 32) + 16;
+}
 constexpr float kLn2 = 0.6931471805599453f;
 
 // Warp sum of V values per lane (V = 16 or 32) by recursive halving: at each
@@ -70,13 +76,15 @@ __global__ void __launch_bounds__(TS * TS, TS == 16 ? 4 : 1) composite_bwd_kerne
     float* __restrict__ ggrad, float* __restrict__ tgrad) {
     constexpr int NT = TS * TS;
     constexpr int NW = NT / 32;
-    __shared__ float4 s_rec[kBatchB][10];
-    __shared__ uint32_t s_id[kBatchB];
-    __shared__ uint32_t s_wmask[kBatchB];
-    __shared__ float s_acc[kBatchB][22];     // per record gradient (Gaussian: 9, triangle: 21)
-    __shared__ uint8_t s_list[NW * kBatchB];
-    __shared__ int s_wmax[NW];
-    __shared__ int s_max;
+    constexpr int kBatchB = BwdBatch<TS>::value;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float4 (*s_rec)[10] = reinterpret_cast<float4 (*)[10]>(smem);
+    float (*s_acc)[22] = reinterpret_cast<float (*)[22]>(smem + kBatchB * 160);  // per record gradient
+    uint32_t* s_id = reinterpret_cast<uint32_t*>(smem + kBatchB * (160 + 88));
+    uint32_t* s_wmask = s_id + kBatchB;
+    int* s_wmax = reinterpret_cast<int*>(s_wmask + kBatchB);
+    int& s_max = s_wmax[NW];
+    uint8_t* s_list = reinterpret_cast<uint8_t*>(s_wmax + NW + 4);
     const int tile = blockIdx.x;
     const int cam = tile / tiles_per_cam;
     const int lt = tile - cam * tiles_per_cam;
@@ -687,14 +695,17 @@ umgs_status render_backward(umgs_ctx* ctx, umgs_frame* fr, const umgs_gaussians*
         const int tpc = fr->tiles_x * fr->tiles_y;
         const float4* dout = reinterpret_cast<const float4*>(dL_drgbt);
 #define UMGS_LAUNCH(TSV)                                                                                         \
-        composite_bwd_kernel<TSV><<<M, TSV * TSV, 0, stream>>>(                                                  \
+        static const cudaError_t attr##TSV = cudaFuncSetAttribute(                                               \
+            composite_bwd_kernel<TSV>, cudaFuncAttributeMaxDynamicSharedMemorySize, bwd_smem_bytes<TSV>());      \
+        UMGS_TRY(attr##TSV);                                                                                     \
+        composite_bwd_kernel<TSV><<<M, TSV * TSV, bwd_smem_bytes<TSV>(), stream>>>(                              \
             fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->trec.as<TRec>(), Ng, Nt,               \
             fr->tiles_x, tpc, fr->W, fr->H, fr->bg[0], fr->bg[1], fr->bg[2], dout, fr->last.as<int32_t>(),         \
             fr->tfin.as<float>(), fr->ntri.as<int32_t>(), fr->stack.as<float4>(), npix, fr->ggrad.as<float>(),     \
             fr->tgrad.as<float>()), count_launch()
-        if (fr->tile == 16) UMGS_LAUNCH(16);
-        else if (fr->tile == 8) UMGS_LAUNCH(8);
-        else UMGS_LAUNCH(32);
+        if (fr->tile == 16) { UMGS_LAUNCH(16); }
+        else if (fr->tile == 8) { UMGS_LAUNCH(8); }
+        else { UMGS_LAUNCH(32); }
 #undef UMGS_LAUNCH
         UMGS_TRY(cudaGetLastError());
     }
