@@ -181,6 +181,15 @@ umgs_status umgs_render(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_mesh*
         if (me.nf > 0 && (!me.verts || !me.faces || !me.vcolor || me.nv < 1))
             return fail(ctx, UMGS_ERR_INVALID_ARG, "mesh array is NULL");
     }
+    {   // unified 32-bit primitive ids and 32-bit (camera, tile) keys
+        int64_t nprim = (g && g->n > 0) ? g->n : 0;
+        for (int m = 0; m < nmeshes; ++m) nprim += meshes[m].nf;
+        if (nprim > (int64_t)0xfffffffe)
+            return fail(ctx, UMGS_ERR_INVALID_ARG, "more than 4294967294 primitives (Gaussians + triangles)");
+        const int64_t tiles = (int64_t)ncams * ((cams[0].width + opts.tile_size - 1) / opts.tile_size) *
+                              ((cams[0].height + opts.tile_size - 1) / opts.tile_size);
+        if (tiles > (int64_t)0xffffffff) return fail(ctx, UMGS_ERR_INVALID_ARG, "more than 2^32 tiles over the cameras");
+    }
     umgs_frame* fr = frame ? frame : ctx->default_frame;
     if (fr->ctx != ctx) return fail(ctx, UMGS_ERR_INVALID_ARG, "frame belongs to another context");
     const bool async = (opts.flags & UMGS_RENDER_ASYNC) != 0;

@@ -45,30 +45,44 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t x, uint32_
     return r;
 }
 
-// phase 1: per-block sums of kRsTile elements
+// phase 1: per-block sums of kRsTile elements (a block sum that does not
+// fit in 32 bits sets *overflow)
 static __global__ void __launch_bounds__(kRsThreads) scan_reduce_kernel(const uint32_t* __restrict__ in, int64_t n,
-                                                                         uint32_t* __restrict__ bsum) {
+                                                                         uint32_t* __restrict__ bsum,
+                                                                         uint32_t* __restrict__ overflow) {
     __shared__ uint32_t s_warp[32];
     const int64_t base = (int64_t)blockIdx.x * kRsTile;
-    uint32_t s = 0;
+    uint64_t s = 0;
 #pragma unroll
     for (int k = 0; k < kRsItems; ++k) {
         const int64_t i = base + k * kRsThreads + threadIdx.x;
         if (i < n) s += in[i];
     }
+    if (s > 0xffffffffull) atomicOr(overflow, 1u);
     uint32_t tot;
-    block_exclusive_scan_256(s, s_warp, tot);
+    block_exclusive_scan_256((uint32_t)s, s_warp, tot);
     if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
 }
 
-// phase 2: exclusive scan of the block sums (one block); writes the grand total
+// phase 2: exclusive scan of the block sums (one block); writes the grand
+// total, or 0xffffffff when the total does not fit in 32 bits (then the
+// offsets are meaningless and the callers treat the pairs as overflowing)
 static __global__ void __launch_bounds__(1024) scan_blocks_kernel(uint32_t* __restrict__ bsum, int nb,
-                                                                 uint32_t* __restrict__ total) {
+                                                                 uint32_t* __restrict__ total,
+                                                                 uint32_t* __restrict__ overflow) {
     __shared__ uint32_t s_warp[32];
+    __shared__ unsigned long long s_tot64[32];
     const int per = (nb + 1023) / 1024;
     const int b = min((int)threadIdx.x * per, nb), e = min(b + per, nb);
     uint32_t local = 0;
-    for (int k = b; k < e; ++k) local += bsum[k];
+    unsigned long long local64 = 0ull;
+    for (int k = b; k < e; ++k) { local += bsum[k]; local64 += bsum[k]; }
+    {   // the 64-bit grand total, to detect a 32-bit wrap
+        unsigned long long t64 = local64;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) t64 += __shfl_xor_sync(0xffffffffu, t64, d);
+        if ((threadIdx.x & 31) == 0) s_tot64[threadIdx.x >> 5] = t64;
+    }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t inc = local;
     for (int d = 1; d < 32; d <<= 1) {
@@ -88,7 +102,11 @@ static __global__ void __launch_bounds__(1024) scan_blocks_kernel(uint32_t* __re
     __syncthreads();
     uint32_t run = inc - local + (w > 0 ? s_warp[w - 1] : 0u);
     for (int k = b; k < e; ++k) { const uint32_t c = bsum[k]; bsum[k] = run; run += c; }
-    if (threadIdx.x == 1023) *total = s_warp[31];
+    if (threadIdx.x == 1023) {
+        unsigned long long t64 = 0ull;
+        for (int k = 0; k < 32; ++k) t64 += s_tot64[k];
+        *total = (*overflow != 0u || t64 > 0xfffffffeull) ? 0xffffffffu : s_warp[31];
+    }
 }
 
 // phase 3: block-local exclusive scan plus the block's prefix

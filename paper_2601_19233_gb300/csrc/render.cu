@@ -959,8 +959,10 @@ cudaError_t scan_u32(umgs_frame* fr, const uint32_t* in, uint32_t* out, int64_t 
     cudaError_t e = fr->rs_bsum.reserve(sizeof(uint32_t) * std::max<int64_t>(1, nb));
     if (e != cudaSuccess) return e;
     if (nb > (1 << 22)) return cudaErrorInvalidValue;
-    scan_reduce_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(in, n, fr->rs_bsum.as<uint32_t>()), count_launch();
-    scan_blocks_kernel<<<1, 1024, 0, s>>>(fr->rs_bsum.as<uint32_t>(), (int)nb, total), count_launch();
+    uint32_t* overflow = reinterpret_cast<uint32_t*>(fr->status.as<int32_t>() + 9);
+    scan_reduce_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(in, n, fr->rs_bsum.as<uint32_t>(), overflow),
+        count_launch();
+    scan_blocks_kernel<<<1, 1024, 0, s>>>(fr->rs_bsum.as<uint32_t>(), (int)nb, total, overflow), count_launch();
     scan_apply_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(in, n, fr->rs_bsum.as<uint32_t>(), out), count_launch();
     return cudaGetLastError();
 }
@@ -1043,7 +1045,7 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     // status words: [0] error bits, [1] number of (tile, id) pairs, [2] largest
     // saved-stack need, [3] fp64 conic list length, [4] tile count for the
     // tile-order sort, [5] record count for the depth sort, [6..7] evaluation
-    // count (u64), [8] persistent work counter
+    // count (u64), [8] persistent work counter, [9] pair-count overflow
     UMGS_TRY(fr->status.reserve(sizeof(int32_t) * 16));
 
     // cameras: host -> pinned staging -> device
@@ -1144,6 +1146,7 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
         const int32_t st = (int32_t)(ctx->pinned[0] & 0xffffffff);
         const int64_t K = NR > 0 ? (int64_t)(uint32_t)(ctx->pinned[0] >> 32) : 0;
         if (st & 1) return fail(ctx, UMGS_ERR_INVALID_ARG, "a face index is out of range");
+        if (K == 0xffffffffll) return fail(ctx, UMGS_ERR_CAPACITY, "more than 4294967294 (tile, primitive) pairs");
         fr->num_keys = K;
         Kcap = K;
         UMGS_TRY(fr->tk.reserve(sizeof(uint32_t) * std::max<int64_t>(1, K)));
@@ -1282,10 +1285,12 @@ umgs_status frame_evaluations(const umgs_frame* fr, int64_t* evals, cudaStream_t
 
 umgs_status frame_check(umgs_frame* fr, cudaStream_t stream) {
     int32_t* w = reinterpret_cast<int32_t*>(fr->ctx->pinned);
-    cudaError_t e = cudaMemcpyAsync(w, fr->status.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, stream);
+    cudaError_t e = cudaMemcpyAsync(w, fr->status.ptr, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_fail(fr->ctx, e, "reading the frame status");
     if (w[0] & 1) return fail(fr->ctx, UMGS_ERR_INVALID_ARG, "a face index is out of range");
+    if ((uint32_t)w[1] == 0xffffffffu)
+        return fail(fr->ctx, UMGS_ERR_CAPACITY, "more than 4294967294 (tile, primitive) pairs");
     if (w[0] & 4)
         return fail(fr->ctx, UMGS_ERR_CAPACITY, "more (tile, primitive) pairs than the reserved capacity (" +
                                                      std::to_string(fr->key_capacity) + ")");

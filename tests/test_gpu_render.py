@@ -5,6 +5,8 @@ bit-exact; images agree with the fp64 oracle within max-abs 2e-4 per channel
 (fp32 path), excluding "tie" pixels where a fragment's alpha sits within 1e-6
 of the 1/255 cut or T within 0.1% of the termination threshold.
 """
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -192,3 +194,36 @@ def test_kernel_launch_counter(ctx):
     gpu_render(ctx, sc)
     n1 = umgs.kernel_launches()
     assert 15 <= n1 - n0 <= 60
+
+
+def test_maximum_image_width(ctx):
+    # 32768 px wide (the largest size the 16-bit packed rects hold) and a
+    # ragged 6 px high: Gaussians and a triangle at both horizontal ends and
+    # across the 16-bit boundary of the tile index
+    W, Hh = 32768, 6
+    c = H.cam(W, Hh, fx=W / 2.0)
+    Z = 3.0
+    xs = [3.0, 40.0, 16380.0, 16390.0, 32700.0, 32766.5]
+    means = [[(x - c.cx) * Z / c.fx, (3.0 - c.cy) * Z / c.fy, 0.0] for x in xs]
+    g = H.gaussians(means, scales=np.full((len(xs), 3), 0.0006, np.float32),
+                    colors=np.linspace(0.1, 0.9, 3 * len(xs)).reshape(-1, 3))
+    tri = H.single_triangle(c, [(32740.0, -2.0), (32767.9, 7.5), (32730.0, 8.0)], -0.2, 0.7)
+    tri2 = H.single_triangle(c, [(-1.0, 0.5), (12.0, 1.0), (2.0, 7.0)], 0.3, 1.0)
+    sc = H.scene(g, [tri, tri2], c, tile=16)
+    out, fr = gpu_render(ctx, sc, tile=16)
+    check_lists(sc, fr, 16)
+    check_image(sc, out)
+
+
+def test_primitive_count_limits_rejected(ctx):
+    from paper_2601_19233_gb300 import umgs
+    sc = S.config0()
+    g = umgs.gaussians_to_device(sc.gaussians)
+    cg = g.c()
+    cg.n = 1 << 40  # more primitives than unified 32-bit ids can name
+    out = torch.empty((1, 128, 128, 4), device="cuda")
+    cams = (umgs.CCamera * 1)(umgs.camera_struct(sc.cameras[0]))
+    opts = umgs.render_opts(8)
+    st = umgs.lib().umgs_render(ctx._h, ctypes.byref(cg), None, 0, cams, 1, ctypes.byref(opts),
+                                umgs._ptr(out), None, None)
+    assert st == 1
