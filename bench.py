@@ -8,7 +8,7 @@ intersecting it, a 20,480-face proxy icosphere displaced every frame by a sum
 of 8 sinusoids (amplitude 0.1); Gaussians bound to the proxy once (BBX mode,
 100 cameras), then every step = one frame:
     umgs_deform (per-face gradients, per-vertex polar/log table, Eq. 12-13)
-    umgs_render (projection, triangle setup, binning, tile sort, composite).
+    umgs_render (projection, triangle setup, binning into tile lists, composite).
 
 One JSON line on rank 0.  `--impl reference` times the CPU oracle instead
 (a bounded sample of the same frame per step, extrapolated to frames/s).
@@ -371,18 +371,21 @@ def roofline(stages, nkeys, n, sc, clk, evals, ms_step, bind_bytes=96.0):
         "deform_gaussians": ng * (bind_bytes + 40 + 36),
         "deform_faces": npf * (12 + 72) + npv * 40,
         "deform_vertices": npv * (40 + 24 + 48),
-        # records: info read, (depth, id) pair written, one read+write of the
-        # pair (a single sort pass), tile count and offset written
-        "scan": (ng + nt) * (16 + 8 + 16 + 8),
-        "scatter": nkeys * 8,
-        # one read and one write of every (tile, id) pair, tile ranges read
-        "sort": nkeys * (16 + 4),
+        # binning (stages scan + scatter + sort): per record its info read,
+        # (depth, id) written, one read+write of it (a single sort pass), a
+        # count and an offset written; per tile-list entry its id written
+        "binning": (ng + nt) * (16 + 8 + 16 + 8) + nkeys * 4,
     }
+    stages = dict(stages)
+    if all(k in stages for k in ("scan", "scatter", "sort")):
+        stages["binning"] = {"ms_per_launch": sum(stages[k]["ms_per_launch"] for k in ("scan", "scatter", "sort"))}
     hbm_stages = {}
     for k, b in alg.items():
         if k in stages:
             t = stages[k]["ms_per_launch"] * 1e-3
             hbm_stages[k] = {"achieved_gbs": round(b / t / 1e9, 1), "frac": round(b / t / 1e9 / hbm, 4)}
+    for k in ("scan", "scatter", "sort"):
+        stages.pop(k, None)
     dom = max(stages, key=lambda k: stages[k]["ms_per_launch"])
     t = stages[dom]["ms_per_launch"] * 1e-3
     mhz = clk.get("sm_mhz") or 2070.0
@@ -409,11 +412,11 @@ def roofline(stages, nkeys, n, sc, clk, evals, ms_step, bind_bytes=96.0):
 def composite_traffic():
     """DRAM bytes per launch of the compositor from the committed ncu summary
     (profiles/composite_1080p.md, line `traffic_bytes_per_launch: B source_sha256: H`),
-    or None when render.cu or common.cuh has changed since those counters were taken."""
+    or None when composite.cu or common.cuh has changed since those counters were taken."""
     import hashlib
     try:
         src = hashlib.sha256()
-        for f in ("render.cu", "common.cuh"):
+        for f in ("composite.cu", "common.cuh"):
             src.update(open(os.path.join(ROOT, "paper_2601_19233_gb300", "csrc", f), "rb").read())
         for line in open(os.path.join(ROOT, "profiles", "composite_1080p.md")):
             if line.startswith("traffic_bytes_per_launch:"):

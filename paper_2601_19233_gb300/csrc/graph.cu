@@ -59,8 +59,7 @@ umgs_status umgs_render_graph_create(umgs_ctx* ctx, umgs_frame* frame, const umg
     const int64_t M = frame->num_tiles;
     const int64_t nbmax = std::max({(Kcap + kRsTile - 1) / kRsTile, (NR + kRsTile - 1) / kRsTile,
                                     (M + kRsTile - 1) / kRsTile, (int64_t)1});
-    for (DevBuf* b : {&frame->tk, &frame->tv, &frame->tk2, &frame->tv2})
-        if (b->reserve(sizeof(uint32_t) * Kcap) != cudaSuccess) return fail(ctx, UMGS_ERR_OUT_OF_MEMORY, "pairs");
+    if (reserve_binning(frame, Kcap, Kcap) != cudaSuccess) return fail(ctx, UMGS_ERR_OUT_OF_MEMORY, "pairs");
     if (frame->rs_hist.reserve(sizeof(uint32_t) * 256 * nbmax) != cudaSuccess)
         return fail(ctx, UMGS_ERR_OUT_OF_MEMORY, "histograms");
     for (DevBuf* b : {&frame->ord_k, &frame->ord_v, &frame->ord_k2, &frame->ord_v2})

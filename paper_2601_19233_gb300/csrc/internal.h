@@ -36,11 +36,14 @@ struct DevBuf {
 struct umgs_frame {
     umgs_ctx* ctx = nullptr;
     umgs::DevBuf cams, grec, trec, bin, tile_off;
-    // binning: record depth keys/values (+ ping-pong), per-record tile counts
-    // and offsets, (tile, id) pairs (+ ping-pong), radix histograms, scan sums
+    // binning: record depth keys/values (+ ping-pong), per-record region
+    // counts and offsets, (region, id) pairs (+ ping-pong), radix histograms,
+    // scan sums; per region its first pair, chunk count and first chunk; per
+    // chunk and region tile the count and the count of earlier chunks; per
+    // tile its list length and first entry; the tile lists
     umgs::DevBuf pk, pv, pk2, pv2, pcnt, poff, tk, tv, tk2, tv2, rs_hist, rs_hist2, rs_bsum;
-    uint32_t* ids = nullptr;    // sorted unified ids (into tv or tv2)
-    uint32_t* tkeys = nullptr;  // sorted tile keys
+    umgs::DevBuf rg_start, rg_nchunk, rg_coff, rg_ccnt, rg_cpre, tl_cnt, tl_off, tl_ids;
+    uint32_t* ids = nullptr;    // tile lists: unified ids (tl_ids)
     umgs::DevBuf last, status;
     umgs::DevBuf tfin, ntri, stack;   // backward state (saved renders only)
     umgs::DevBuf ggrad, tgrad, rerun_out;
@@ -64,7 +67,8 @@ struct umgs_frame {
     std::vector<int64_t> mesh_offset;  // unified id of each mesh's first face
     void release() {
         for (auto* b : {&cams, &grec, &trec, &bin, &tile_off, &pk, &pv, &pk2, &pv2, &pcnt, &poff, &tk, &tv, &tk2, &tv2,
-                        &rs_hist, &rs_hist2, &rs_bsum,
+                        &rs_hist, &rs_hist2, &rs_bsum, &rg_start, &rg_nchunk, &rg_coff, &rg_ccnt, &rg_cpre, &tl_cnt,
+                        &tl_off, &tl_ids,
                         &last, &status, &tfin, &ntri, &stack, &ggrad, &tgrad, &rerun_out, &fix_list, &ord_k, &ord_v,
                         &ord_k2, &ord_v2})
             b->release();
@@ -148,6 +152,12 @@ umgs_status bind_forward(umgs_ctx* ctx, const umgs_gaussians* g, const float* V,
                          int64_t* out_num_fallback, cudaStream_t stream);
 
 cudaError_t launch_composite(umgs_frame* fr, const umgs_render_opts& opts, float* out_rgbt, cudaStream_t stream);
+cudaError_t reserve_binning(umgs_frame* fr, int64_t rcap, int64_t kcap);
+// stable LSD radix sort of (k, v) on the low `bits` bits (binning stage);
+// the element count is read from n_dev (at most n_cap, which sizes the grids)
+cudaError_t radix_sort_pairs(umgs_frame* fr, uint32_t* k, uint32_t* v, uint32_t* k2, uint32_t* v2,
+                             const uint32_t* n_dev, int64_t n_cap, int bits, uint32_t** rk, uint32_t** rv,
+                             cudaStream_t s);
 
 umgs_status render_backward(umgs_ctx* ctx, umgs_frame* fr, const umgs_gaussians* g, const umgs_mesh* meshes,
                             int32_t nmeshes, const float* dL_drgbt, const umgs_gaussian_grads* gg,

@@ -5,19 +5,15 @@
 //      over cameras; canonical fp32 footprint (pixel rect) + depth key and a
 //      compact record for the compositor; refine_conics_kernel recomputes the
 //      few near-singular conics in fp64; shade_gaussians_kernel evaluates SH.
-//   2. binning, a two-level stable radix sort (the onion sort):
+//   2. binning into per-tile lists in (depth bits, id) order:
 //      a. every (camera, primitive) record sorted by its depth bits
 //         (4 x 8-bit passes, stable, so equal depths stay in id order);
-//      b. in that order every record emits one (tile, id) pair per tile its
-//         rect touches (offsets from an exclusive scan of the tile counts);
-//      c. the pairs are sorted stably by tile (8-bit passes over the tile
-//         bits): each tile's list is then in (depth bits, id) order;
-//      d. tile_ranges: per tile, the first index of its list (binary search).
-//   3. composite: one CTA per tile, one thread per pixel; records of the
-//      sorted list are staged through shared memory in batches; every pixel
-//      blends its fragments front to back (Eq. 1-2 for Gaussians, Eq. 7-9
-//      for entities of depth-adjacent triangles) and the CTA stops when
-//      every pixel has T < t_eps (block-wide vote).
+//      b. in that order every record emits one (region, id) pair per region
+//         of 8 x 4 tiles its rect touches (offsets from an exclusive scan);
+//      c. the pairs are sorted stably by region;
+//      d. each region's pairs are expanded into the lists of its 32 tiles
+//         (count pass, scans over chunks and tiles, ballot-ranked fill).
+//   3. composite (composite.cu).
 #include <cstdio>
 #include <cstring>
 #include <cmath>
@@ -459,10 +455,25 @@ __global__ void __launch_bounds__(256) setup_triangles_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// binning: a two-level stable radix sort (the "onion"): all (camera,
-// primitive) records by depth bits, then the emitted (tile, primitive) pairs
-// by tile.  Stability makes each tile's list come out in (depth bits, id)
-// order without a per-tile sort.
+// binning.  Every tile's list must hold the records whose pixel rect touches
+// it, in (depth bits, id) order.  Instead of emitting one (tile, id) pair per
+// covered tile and sorting all of them by tile, the records are
+//   1. sorted once by depth bits (stable LSD radix sort of all (camera,
+//      primitive) records; ties stay in id order),
+//   2. emitted in that order as (region, id) pairs, a region being a block of
+//      kRegionTX x kRegionTY tiles (4x fewer pairs than tiles at 1080p),
+//   3. sorted stably by region (one 8-bit pass for up to 256 regions),
+//   4. expanded region by region into the tile lists: each region's pairs
+//      are cut into chunks of kRegionChunk; a counting pass gives every
+//      (chunk, tile of the region) its count, an exclusive scan over the
+//      chunks of a region and over all tiles gives each its first slot, and
+//      a fill pass writes each id to its tiles in chunk order, ranking the
+//      ids of a chunk per tile with warp ballots (so the order within a tile
+//      is the region order, which is the depth order).
+
+constexpr int kRegionTX = 8, kRegionTY = 4;  // tiles per region: one bit each of a 32-bit mask
+constexpr int kRegionChunk = 2048;           // region pairs per count/fill block
+constexpr int kRegionThreads = 256;
 
 __global__ void prim_keys_kernel(const BinInfo* __restrict__ bin, int64_t n, uint32_t* __restrict__ pk,
                                  uint32_t* __restrict__ pv, uint32_t* __restrict__ n_dev) {
@@ -474,38 +485,72 @@ __global__ void prim_keys_kernel(const BinInfo* __restrict__ bin, int64_t n, uin
     pv[i] = (uint32_t)i;
 }
 
-__device__ __forceinline__ uint32_t tiles_of(const BinInfo& b, int ts) {
-    if (!b.valid) return 0u;
-    const int xlo = b.rx & 0xffff, xhi = b.rx >> 16, ylo = b.ry & 0xffff, yhi = b.ry >> 16;
-    return (uint32_t)((xhi / ts - xlo / ts + 1) * (yhi / ts - ylo / ts + 1));
-}
-
-__global__ void tile_counts_kernel(const BinInfo* __restrict__ bin, const uint32_t* __restrict__ pv, int64_t n, int ts,
-                                   uint32_t* __restrict__ cnt) {
+// Per depth-sorted record: the number of regions its tile rect meets; the
+// number of tiles it meets is summed (64-bit, one atomic per block) into
+// *ktotal, the length of all tile lists together.
+__global__ void __launch_bounds__(256) region_counts_kernel(const BinInfo* __restrict__ bin,
+                                                            const uint32_t* __restrict__ pv, int64_t n, int ts,
+                                                            uint32_t* __restrict__ rcnt,
+                                                            unsigned long long* __restrict__ ktotal) {
+    __shared__ unsigned long long s_sum[8];
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    cnt[i] = tiles_of(bin[pv[i]], ts);
+    unsigned long long tiles = 0;
+    if (i < n) {
+        const BinInfo b = bin[pv[i]];
+        uint32_t regions = 0;
+        if (b.valid) {
+            const int tx0 = (int)(b.rx & 0xffff) / ts, tx1 = (int)(b.rx >> 16) / ts;
+            const int ty0 = (int)(b.ry & 0xffff) / ts, ty1 = (int)(b.ry >> 16) / ts;
+            tiles = (unsigned long long)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+            regions = (uint32_t)((tx1 / kRegionTX - tx0 / kRegionTX + 1) * (ty1 / kRegionTY - ty0 / kRegionTY + 1));
+        }
+        rcnt[i] = regions;
+    }
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) tiles += __shfl_down_sync(0xffffffffu, tiles, d);
+    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = tiles;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t += s_sum[w];
+        if (t) atomicAdd(ktotal, t);
+    }
 }
 
-// (tile, id) pairs of the depth-sorted records: record i owns the slots
-// [off[i], off[i] + tiles(i)), its tiles in row-major order.  Each warp takes
-// 32 consecutive records and fills their (contiguous) slots together: lane l
-// writes slots s = l, l + 32, ... of the warp's range, finding the owning
-// record by binary search over the warp's exclusive prefix of tile counts,
-// so the writes are coalesced and a record with many tiles does not hold up
-// its warp.  Slots at or beyond `cap` are not written (the overflow is
-// flagged in status bit 2); every slot below it is.
-__global__ void __launch_bounds__(256) emit_pairs_kernel(const BinInfo* __restrict__ bin,
-                                                         const uint32_t* __restrict__ pv,
-                                                         const uint32_t* __restrict__ off, int64_t n, int64_t ntot,
-                                                         int ts, int tiles_x, int tiles_per_cam,
-                                                         uint32_t* __restrict__ tk, uint32_t* __restrict__ tv,
-                                                         int64_t cap, int32_t* __restrict__ status) {
+// (region, id) pairs of the depth-sorted records: record i owns the slots
+// [off[i], off[i] + regions(i)), its regions in row-major order.  Each warp
+// takes 32 consecutive records and fills their (contiguous) slots together:
+// lane l writes slots l, l + 32, ... of the warp's range, finding the owning
+// record by binary search over the warp's exclusive prefix of region counts,
+// so the writes are coalesced and a record with many regions does not hold
+// up its warp.
+// Capacity: when the tile lists would hold more than `kcap` entries (or more
+// than 2^32 - 2), nothing is emitted, the region-pair count *rn is set to 0
+// (so no tile list gets an entry) and the overflow is recorded: status bit 2
+// for the capacity, status[1] = 0xffffffff for the 32-bit limit.  Thread 0
+// also publishes the number of tile-list entries in status[1].
+__global__ void __launch_bounds__(256) emit_region_pairs_kernel(
+    const BinInfo* __restrict__ bin, const uint32_t* __restrict__ pv, const uint32_t* __restrict__ off, int64_t n,
+    int64_t ntot, int ts, int regions_x, int regions_per_cam, const unsigned long long* __restrict__ ktotal,
+    int64_t kcap, uint32_t* __restrict__ rk, uint32_t* __restrict__ rv, int64_t rcap, uint32_t* __restrict__ rn,
+    int32_t* __restrict__ status) {
+    const unsigned long long K = *ktotal;
+    const bool over = K > (unsigned long long)kcap || K >= 0xffffffffull;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        status[1] = (int32_t)(uint32_t)(K >= 0xffffffffull ? 0xffffffffull : K);
+        if (over) {
+            if (K > (unsigned long long)kcap) atomicOr(status, 4);
+            *rn = 0u;
+        }
+    }
+    if (over) return;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     if (i - lane >= n) return;  // whole warp past the end
+    const int rts_x = ts * kRegionTX, rts_y = ts * kRegionTY;  // region size in pixels
     int xlo = 0, ylo = 0, w = 1, cnt = 0;
-    uint32_t id = 0, tbase = 0;
+    uint32_t id = 0, rbase = 0;
     int64_t start = 0;
     if (i < n) {
         const uint32_t rec = pv[i];
@@ -514,13 +559,13 @@ __global__ void __launch_bounds__(256) emit_pairs_kernel(const BinInfo* __restri
         if (b.valid) {
             const int cam = (int)(rec / ntot);
             id = (uint32_t)(rec - (int64_t)cam * ntot);
-            xlo = (int)(b.rx & 0xffff) / ts;
-            const int xhi = (int)(b.rx >> 16) / ts;
-            ylo = (int)(b.ry & 0xffff) / ts;
-            const int yhi = (int)(b.ry >> 16) / ts;
+            xlo = (int)(b.rx & 0xffff) / rts_x;
+            const int xhi = (int)(b.rx >> 16) / rts_x;
+            ylo = (int)(b.ry & 0xffff) / rts_y;
+            const int yhi = (int)(b.ry >> 16) / rts_y;
             w = xhi - xlo + 1;
             cnt = w * (yhi - ylo + 1);
-            tbase = (uint32_t)cam * (uint32_t)tiles_per_cam;
+            rbase = (uint32_t)cam * (uint32_t)regions_per_cam;
         }
     }
     // exclusive prefix of the counts within the warp
@@ -533,7 +578,6 @@ __global__ void __launch_bounds__(256) emit_pairs_kernel(const BinInfo* __restri
     const int excl = incl - cnt;
     const int total = __shfl_sync(0xffffffffu, incl, 31);
     const int64_t base = __shfl_sync(0xffffffffu, start, 0);  // offsets are contiguous in record order
-    if (lane == 0 && base + total > cap) atomicOr(status, 4);  // capacity overflow
     for (int s0 = 0; s0 < total; s0 += 32) {
         const int s = s0 + lane;
         // owner: the last lane r with excl[r] <= s
@@ -549,407 +593,264 @@ __global__ void __launch_bounds__(256) emit_pairs_kernel(const BinInfo* __restri
         const int ry = __shfl_sync(0xffffffffu, ylo, r);
         const int rw = __shfl_sync(0xffffffffu, w, r);
         const uint32_t rid = __shfl_sync(0xffffffffu, id, r);
-        const uint32_t rtb = __shfl_sync(0xffffffffu, tbase, r);
+        const uint32_t rrb = __shfl_sync(0xffffffffu, rbase, r);
         const int64_t o = base + s;
-        if (s < total && o < cap) {
+        if (s < total && o < rcap) {
             const int k = s - re;
-            const int ty = ry + k / rw, tx = rx + k % rw;
-            tk[o] = rtb + (uint32_t)(ty * tiles_x + tx);
-            tv[o] = rid;
+            const int gy = ry + k / rw, gx = rx + k % rw;
+            rk[o] = rrb + (uint32_t)(gy * regions_x + gx);
+            rv[o] = rid;
         }
     }
 }
 
-// tile_off[t] = first index of tile t in the sorted keys (lower bound).
-// More pairs than the capacity (flagged by emit_pairs): the emission skipped
-// records, so slots below the capacity may hold no pair; every tile is then
-// left empty rather than reading them.
-__global__ void tile_ranges_kernel(const uint32_t* __restrict__ tk, const uint32_t* __restrict__ K_dev, int64_t Kcap,
-                                   int64_t M, int64_t* __restrict__ off) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t > M) return;
-    const int64_t K = (int64_t)*K_dev > Kcap ? 0 : (int64_t)*K_dev;
-    if (t == M) { off[M] = K; return; }
-    int64_t lo = 0, hi = K;
+__device__ __forceinline__ int64_t lower_bound_u32(const uint32_t* __restrict__ a, int64_t n, uint32_t key) {
+    int64_t lo = 0, hi = n;
     while (lo < hi) {
         const int64_t mid = (lo + hi) >> 1;
-        if (tk[mid] < (uint32_t)t) lo = mid + 1;
+        if (a[mid] < key) lo = mid + 1;
         else hi = mid;
     }
-    off[t] = lo;
+    return lo;
 }
 
-// ---------------------------------------------------------------------------
-// compositor
+// Per region r (of R): its first pair in the region-sorted keys, and the
+// number of chunks (count/fill blocks) it needs; rstart[R] = pair count.
+__global__ void region_ranges_kernel(const uint32_t* __restrict__ rk, const uint32_t* __restrict__ rn, int64_t rcap,
+                                     int64_t R, uint32_t* __restrict__ rstart, uint32_t* __restrict__ nchunk) {
+    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (r > R) return;
+    const int64_t n = min((int64_t)*rn, rcap);
+    const int64_t s = lower_bound_u32(rk, n, (uint32_t)r);
+    rstart[r] = (uint32_t)s;
+    if (r < R) {
+        const int64_t e = lower_bound_u32(rk, n, (uint32_t)(r + 1));
+        nchunk[r] = (uint32_t)((e - s + kRegionChunk - 1) / kRegionChunk);
+    }
+}
 
-constexpr int kBatch = 256;
-// records staged per batch: 256, or 128 for 32x32 tiles (32 warps of lists)
-template <int TS> struct BatchOf { static constexpr int value = TS == 32 ? 128 : 256; };
+// Exclusive scan of n (<= kSmallScanMax) uint32 in one block of 1024
+// threads, 1024 elements per round; the total goes to *total.
+constexpr int64_t kSmallScanMax = 1 << 15;
+__global__ void __launch_bounds__(1024) scan_small_kernel(const uint32_t* __restrict__ in, int64_t n,
+                                                          uint32_t* __restrict__ out, uint32_t* __restrict__ total) {
+    __shared__ uint32_t s_warp[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t carry = 0;
+    for (int64_t b = 0; b < n; b += 1024) {
+        const int64_t i = b + threadIdx.x;
+        const uint32_t x = i < n ? in[i] : 0u;
+        uint32_t inc = x;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d) inc += y;
+        }
+        if (lane == 31) s_warp[w] = inc;
+        __syncthreads();
+        if (w == 0) {
+            uint32_t v = s_warp[lane];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, v, d);
+                if (lane >= d) v += y;
+            }
+            s_warp[lane] = v;
+        }
+        __syncthreads();
+        if (i < n) out[i] = carry + inc - x + (w > 0 ? s_warp[w - 1] : 0u);
+        carry += s_warp[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
 
-struct PixelState {
-    float C[3];
-    float T;
-    float Tin;
-    float t[4];
-    float g_since;
-    bool in_ent;
+// The region and chunk of count/fill block `blk` (< nblk): the last region
+// whose first chunk is at or before it (regions without pairs own no chunk).
+__device__ __forceinline__ int64_t region_of_chunk(const uint32_t* __restrict__ coff, int64_t R, uint32_t blk) {
+    int64_t lo = 0, hi = R - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (coff[mid] <= blk) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Tiles of region-local rect: bit (ly * kRegionTX + lx) for every tile of the
+// record's tile rect inside the region whose first tile is (tx0, ty0).
+__device__ __forceinline__ uint32_t region_tile_mask(const BinInfo& b, int ts, int tx0, int ty0) {
+    const int lx0 = max((int)(b.rx & 0xffff) / ts - tx0, 0), lx1 = min((int)(b.rx >> 16) / ts - tx0, kRegionTX - 1);
+    const int ly0 = max((int)(b.ry & 0xffff) / ts - ty0, 0), ly1 = min((int)(b.ry >> 16) / ts - ty0, kRegionTY - 1);
+    if (lx0 > lx1 || ly0 > ly1) return 0u;
+    const uint32_t row = (0xffu >> (kRegionTX - 1 - lx1)) & (0xffu << lx0);
+    const uint32_t rows = (0xffffffffu >> (8 * (kRegionTY - 1 - ly1))) & (0xffffffffu << (8 * ly0));
+    return (row * 0x01010101u) & rows;
+}
+static_assert(kRegionTX == 8 && kRegionTY == 4, "region_tile_mask packs 8 tiles per byte, 4 rows");
+
+struct RegionChunk {
+    int64_t e0, e1;      // pair range of the chunk
+    int64_t rec_base;    // camera * primitives per camera
+    int tx0, ty0;        // first tile of the region
+    int64_t tile0;       // global index of the region's first tile
 };
 
-// SAVE: also keep what the backward pass needs: per pixel the final T and
-// the number of covering triangle fragments, and per covering triangle
-// fragment the four sub-sample transmittances before it (scaled by T_in/4)
-// in a per-pixel stack of capacity `cap` (`need` records the largest count).
-// MODE: UMGS_BLEND_* or kModeTProduct (FULL with the literal Eq. 6
-// transmittance T <- T (1 - O_i alpha_i) inside an entity).
-constexpr int kModeTProduct = 4;
+__device__ __forceinline__ RegionChunk region_chunk(const uint32_t* __restrict__ coff, const uint32_t* __restrict__ rstart,
+                                                    int64_t R, uint32_t blk, int regions_x, int regions_per_cam,
+                                                    int tiles_x, int tiles_per_cam, int64_t ntot) {
+    RegionChunk c;
+    const int64_t r = region_of_chunk(coff, R, blk);
+    const int64_t j = blk - coff[r];
+    const int64_t s = rstart[r], e = rstart[r + 1];
+    c.e0 = s + j * kRegionChunk;
+    c.e1 = min(c.e0 + kRegionChunk, e);
+    const int cam = (int)(r / regions_per_cam);
+    const int lr = (int)(r - (int64_t)cam * regions_per_cam);
+    const int gy = lr / regions_x, gx = lr - gy * regions_x;
+    c.tx0 = gx * kRegionTX;
+    c.ty0 = gy * kRegionTY;
+    c.tile0 = (int64_t)cam * tiles_per_cam + (int64_t)c.ty0 * tiles_x + c.tx0;
+    c.rec_base = (int64_t)cam * ntot;
+    return c;
+}
 
-template <int TS, bool SAVE, int MODE>
-__device__ __forceinline__ void composite_tile(
-    int tile, float4 (*__restrict__ s_rec)[10], uint32_t* __restrict__ s_id, uint32_t* __restrict__ s_wmask,
-    uint8_t* __restrict__ s_list,
-    const uint32_t* __restrict__ ids, const int64_t* __restrict__ off,
-    const GRec* __restrict__ grec,
-    const GRec16* __restrict__ grec16, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
-    int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, float4* __restrict__ out, int32_t* __restrict__ out_last,
-    float* __restrict__ out_tfin, int32_t* __restrict__ out_ntri, float4* __restrict__ stack, int cap,
-    int64_t npix, int32_t* __restrict__ need) {
-    constexpr int NT = TS * TS;
-    constexpr int mode = MODE;
-    const int cam = tile / tiles_per_cam;
-    const int lt = tile - cam * tiles_per_cam;
-    const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
-    int lx, ly;
-    block_pixel<TS>(threadIdx.x, lx, ly);
-    const int px = tx * TS + lx, py = ty * TS + ly;
-    const bool inside = px < W && py < H;
-    const int64_t beg = off[tile], end = off[tile + 1];
-    const GRec* G = grec + (int64_t)cam * Ng;
-    const GRec16* G16 = grec16 ? grec16 + (int64_t)cam * Ng : nullptr;
-    const TRec* TR = trec + (int64_t)cam * Nt;
-    const float qx = px + 0.5f, qy = py + 0.5f;
-    const long long scx = (long long)px * 256 + 128, scy = (long long)py * 256 + 128;
-
-    PixelState st;
-    st.C[0] = st.C[1] = st.C[2] = 0.f;
-    st.T = 1.f; st.Tin = 1.f; st.g_since = 1.f;
-    st.t[0] = st.t[1] = st.t[2] = st.t[3] = 1.f;
-    st.in_ent = false;
-    bool done = !inside;
-    int last = 0;
-    int sp = 0;
-    const int64_t pix = ((int64_t)cam * H + py) * W + px;
-
-    // warp w owns one 8 x 4 pixel block of the tile (block_pixel); every
-    // record carries the mask of the blocks that can hold a fragment of it
-    const int warp = threadIdx.x >> 5;
-    const int tile_x0 = tx * TS, tile_y0 = ty * TS;
-    const float pxf = (float)px, pyf = (float)py;
-    constexpr int NB = BatchOf<TS>::value;
-    for (int64_t b0 = beg; b0 < end; b0 += NB) {
-        if (__syncthreads_count(done) == NT) break;
-        const int n = (int)min((int64_t)NB, end - b0);
-        const int lbase = (int)(b0 - beg) + 1;  // list position + 1 of the batch's first record
-        for (int k = threadIdx.x; k < n; k += NT) {
-            const uint32_t id = ids[b0 + k];
-            s_id[k] = id;
-            if (id >= Ng + Nt) {
-                s_wmask[k] = 0u;  // not a record of this frame: no fragment
-            } else if (id < Ng) {
-                float4 a, b, c;
-                if (G16) {  // fp16 record: widen to the fp32 layout
-                    const uint4 h0 = G16[id].v0, h1 = G16[id].v1;
-                    a = make_float4(__uint_as_float(h0.x), __uint_as_float(h0.y), half_lo(h0.z), half_hi(h0.z));
-                    b = make_float4(half_lo(h0.w), half_hi(h0.w), half_lo(h1.x), half_hi(h1.x));
-                    c = make_float4(half_lo(h1.y), __uint_as_float(h1.z), __uint_as_float(h1.w), 0.f);
-                } else {
-                    const float4* src = reinterpret_cast<const float4*>(G + id);
-                    a = src[0]; b = src[1]; c = src[2];
-                }
-                const uint32_t rx = __float_as_uint(c.y), ry = __float_as_uint(c.z);
-                s_rec[k][0] = a;
-                s_rec[k][1] = make_float4(b.x, b.y, (float)(rx & 0xffff), (float)(rx >> 16));
-                s_rec[k][2] = make_float4((float)(ry & 0xffff), (float)(ry >> 16), b.z, b.w);
-                s_rec[k][3] = make_float4(c.x, 0.f, 0.f, 0.f);
-                s_wmask[k] = gauss_block_mask<TS>(a.x, a.y, a.z, a.w, b.x, b.y, (int)(rx & 0xffff), (int)(rx >> 16),
-                                                  (int)(ry & 0xffff), (int)(ry >> 16), tile_x0, tile_y0);
-            } else {
-                const float4* src = reinterpret_cast<const float4*>(TR + (id - Ng));
+// Counting pass: per chunk and tile of its region (lane t of each warp keeps
+// tile t), the number of the chunk's pairs whose record covers the tile.
+__global__ void __launch_bounds__(kRegionThreads) region_count_kernel(
+    const uint32_t* __restrict__ rv, const BinInfo* __restrict__ bin, const uint32_t* __restrict__ coff,
+    const uint32_t* __restrict__ rstart, const uint32_t* __restrict__ nblk_dev, int64_t R, int ts, int regions_x,
+    int regions_per_cam, int tiles_x, int tiles_per_cam, int64_t ntot, uint32_t* __restrict__ ccnt) {
+    __shared__ uint32_t s_cnt[kRegionThreads / 32][32];
+    if (blockIdx.x >= *nblk_dev) return;
+    const RegionChunk c = region_chunk(coff, rstart, R, blockIdx.x, regions_x, regions_per_cam, tiles_x,
+                                       tiles_per_cam, ntot);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t mine = 0;
+    for (int64_t b0 = c.e0; b0 < c.e1; b0 += kRegionThreads) {
+        const int64_t e = b0 + threadIdx.x;
+        uint32_t m = 0;
+        if (e < c.e1) m = region_tile_mask(bin[c.rec_base + rv[e]], ts, c.tx0, c.ty0);
 #pragma unroll
-                for (int q = 0; q < 10; ++q) s_rec[k][q] = src[q];
-                const TRec& tr = *reinterpret_cast<const TRec*>(&s_rec[k][0]);
-                s_wmask[k] = box_block_mask<TS>((int)(tr.rx & 0xffff), (int)(tr.rx >> 16), (int)(tr.ry & 0xffff),
-                                                (int)(tr.ry >> 16), tile_x0, tile_y0);
-            }
-        }
-        __syncthreads();
-        if (__any_sync(0xffffffffu, !done)) {
-            // this warp's records of the batch, in order
-            uint8_t* lst = s_list + warp * BatchOf<TS>::value;
-            int cnt = 0;
-            const int lane = threadIdx.x & 31;
-            for (int c0 = 0; c0 < n; c0 += 32) {
-                const bool mine = c0 + lane < n && ((s_wmask[c0 + lane] >> warp) & 1u);
-                const unsigned bal = __ballot_sync(0xffffffffu, mine);
-                if (mine) lst[cnt + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)(c0 + lane);
-                cnt += __popc(bal);
-            }
-            __syncwarp();
-            for (int li = 0; li < cnt; ++li) {
-                const int k = lst[li];
-                if (done) continue;
-                const uint32_t id = s_id[k];
-                if (id < Ng) {
-                    const float4 q1 = s_rec[k][1], q2 = s_rec[k][2];
-                    if (pxf < q1.z || pxf > q1.w || pyf < q2.x || pyf > q2.y) continue;
-                    const float4 q0 = s_rec[k][0];
-                    const float dx = __fsub_rn(qx, q0.x), dy = __fsub_rn(qy, q0.y);
-                    const float p2 = gauss_power2(q0.z, q0.w, q1.x, dx, dy);
-                    const float alpha = fminf(kAlphaMax, __fmul_rn(q1.y, fast_exp2(p2)));
-                    if (alpha < kAlphaMin) continue;
-                    const float w = alpha * st.T;
-                    st.C[0] += w * q2.z; st.C[1] += w * q2.w; st.C[2] += w * s_rec[k][3].x;
-                    st.T *= (1.f - alpha);
-                    if (mode == UMGS_BLEND_ENTITY_ALL) st.g_since *= (1.f - alpha);
-                    else st.in_ent = false;
-                } else {
-                    const TRec& t = *reinterpret_cast<const TRec*>(&s_rec[k][0]);
-                    if (px < (int)(t.rx & 0xffff) || px > (int)(t.rx >> 16) || py < (int)(t.ry & 0xffff) ||
-                        py > (int)(t.ry >> 16))
-                        continue;
-                    long long E[3];
-#pragma unroll
-                    for (int e = 0; e < 3; ++e) E[e] = (long long)t.A[e] * scx + (long long)t.B[e] * scy + t.C[e];
-                    int mask = 0;
-                    if (mode == UMGS_BLEND_DIRECT) {
-                        mask = (E[0] >= 0 && E[1] >= 0 && E[2] >= 0) ? 0xf : 0;
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const int sdx = sample_dx(j), sdy = sample_dy(j);
-                            bool in = true;
-#pragma unroll
-                            for (int e = 0; e < 3; ++e) in = in && (E[e] + (long long)(t.A[e] * sdx + t.B[e] * sdy) >= 0);
-                            mask |= in ? (1 << j) : 0;
-                        }
-                    }
-                    if (mask == 0) continue;
-                    // attributes at the pixel centre: perspective-correct
-                    // barycentrics of the unsnapped triangle, clamped at 0
-                    float lam[3];
-#pragma unroll
-                    for (int e = 0; e < 3; ++e) {
-                        const int a = (e + 1) % 3, b = (e + 2) % 3;
-                        lam[e] = (t.u[a] - qx) * (t.v[b] - qy) - (t.u[b] - qx) * (t.v[a] - qy);
-                    }
-                    const float area = lam[0] + lam[1] + lam[2];
-                    float wv[3];
-                    if (area != 0.f) {
-                        const float ia = 1.f / area;
-#pragma unroll
-                        for (int e = 0; e < 3; ++e) wv[e] = fmaxf(lam[e] * ia, 0.f) * t.iz[e];
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < 3; ++e) wv[e] = (1.f / 3.f) * t.iz[e];
-                    }
-                    const float ws = wv[0] + wv[1] + wv[2];
-                    if (ws > 0.f) { const float is = 1.f / ws; wv[0] *= is; wv[1] *= is; wv[2] *= is; }
-                    else { wv[0] = wv[1] = wv[2] = 1.f / 3.f; }
-                    float col[3];
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) col[c] = wv[0] * t.col[c] + wv[1] * t.col[3 + c] + wv[2] * t.col[6 + c];
-                    float a = t.const_alpha ? t.alpha[0] : (wv[0] * t.alpha[0] + wv[1] * t.alpha[1] + wv[2] * t.alpha[2]);
-                    a = fminf(fmaxf(a, 0.f), 1.f);
-                    if (mode == UMGS_BLEND_DIRECT) {
-                        const float w = a * st.T;
-                        st.C[0] += w * col[0]; st.C[1] += w * col[1]; st.C[2] += w * col[2];
-                        st.T *= (1.f - a);
-                    } else if (mode == UMGS_BLEND_MSAA_ALL) {
-                        const float O = 0.25f * (float)__popc(mask);
-                        const float w = O * a * st.T;
-                        st.C[0] += w * col[0]; st.C[1] += w * col[1]; st.C[2] += w * col[2];
-                        st.T *= (1.f - O * a);
-                    } else {
-                        if (!st.in_ent) {
-                            st.Tin = st.T;
-                            st.t[0] = st.t[1] = st.t[2] = st.t[3] = 1.f;
-                            st.g_since = 1.f;
-                            st.in_ent = true;
-                        }
-                        if (SAVE && mode == UMGS_BLEND_FULL) {
-                            if (sp < cap) {
-                                const float q = 0.25f * st.Tin;
-                                stack[(int64_t)sp * npix + pix] = make_float4(q * st.t[0], q * st.t[1], q * st.t[2], q * st.t[3]);
-                            }
-                            ++sp;
-                        }
-                        float O = 0.f;
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) O += ((mask >> j) & 1) ? st.t[j] : 0.f;
-                        O *= 0.25f;
-                        const float w = st.Tin * O * a;
-                        st.C[0] += w * col[0]; st.C[1] += w * col[1]; st.C[2] += w * col[2];
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            if ((mask >> j) & 1) st.t[j] *= (1.f - a);
-                        const float tm = 0.25f * ((st.t[0] + st.t[1]) + (st.t[2] + st.t[3]));
-                        if (mode == kModeTProduct) st.T *= (1.f - O * a);
-                        else st.T = (mode == UMGS_BLEND_ENTITY_ALL) ? st.Tin * tm * st.g_since : st.Tin * tm;
-                    }
-                }
-                last = lbase + k;
-                if (st.T < t_eps) done = true;
-            }
+        for (int t = 0; t < 32; ++t) {
+            const uint32_t bal = __ballot_sync(0xffffffffu, (m >> t) & 1u);
+            if (lane == t) mine += __popc(bal);
         }
     }
-    if (inside) {
-        out[pix] = make_float4(st.C[0] + st.T * bg0, st.C[1] + st.T * bg1, st.C[2] + st.T * bg2, st.T);
-        // bit 31: the pixel stopped at T < t_eps after list position `last`
-        if (out_last) out_last[pix] = last | (st.T < t_eps ? (int)0x80000000u : 0);
-        if (SAVE) {
-            out_tfin[pix] = st.T;
-            out_ntri[pix] = sp;
-            if (sp > cap) atomicMax(need, sp);
-        }
+    s_cnt[warp][lane] = mine;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t s = 0;
+#pragma unroll
+        for (int w = 0; w < kRegionThreads / 32; ++w) s += s_cnt[w][threadIdx.x];
+        ccnt[(int64_t)blockIdx.x * 32 + threadIdx.x] = s;
     }
 }
 
-
-// one CTA per tile (grid launch)
-template <int TS, bool SAVE, int MODE>
-__global__ void __launch_bounds__(TS * TS) composite_kernel(
-    const uint32_t* __restrict__ ids, const int64_t* __restrict__ off, const GRec* __restrict__ grec,
-    const GRec16* __restrict__ grec16, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
-    int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, float4* __restrict__ out, int32_t* __restrict__ out_last,
-    float* __restrict__ out_tfin, int32_t* __restrict__ out_ntri, float4* __restrict__ stack, int cap,
-    int64_t npix, int32_t* __restrict__ need) {
-    constexpr int NB = BatchOf<TS>::value;
-    __shared__ float4 s_rec[NB][10];
-    __shared__ uint32_t s_id[NB];
-    __shared__ uint32_t s_wmask[NB];
-    __shared__ uint8_t s_list[(TS * TS / 32) * NB];
-    composite_tile<TS, SAVE, MODE>(blockIdx.x, s_rec, s_id, s_wmask, s_list, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, out, out_last, out_tfin, out_ntri, stack, cap, npix, need);
-}
-
-// persistent launch: resident CTAs take tiles from an atomic queue in the
-// order `order` (decreasing list length: the heaviest tiles start first)
-template <int TS, bool SAVE, int MODE>
-__global__ void __launch_bounds__(TS * TS) composite_persistent_kernel(
-    const uint32_t* __restrict__ order, unsigned* __restrict__ work, int64_t M,
-    const uint32_t* __restrict__ ids, const int64_t* __restrict__ off, const GRec* __restrict__ grec,
-    const GRec16* __restrict__ grec16, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
-    int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, float4* __restrict__ out, int32_t* __restrict__ out_last,
-    float* __restrict__ out_tfin, int32_t* __restrict__ out_ntri, float4* __restrict__ stack, int cap,
-    int64_t npix, int32_t* __restrict__ need) {
-    constexpr int NB = BatchOf<TS>::value;
-    __shared__ float4 s_rec[NB][10];
-    __shared__ uint32_t s_id[NB];
-    __shared__ uint32_t s_wmask[NB];
-    __shared__ uint8_t s_list[(TS * TS / 32) * NB];
-    __shared__ unsigned s_next;
-    while (true) {
-        if (threadIdx.x == 0) s_next = atomicAdd(work, 1u);
-        __syncthreads();
-        const unsigned k = s_next;
-        __syncthreads();
-        if ((int64_t)k >= M) break;
-        composite_tile<TS, SAVE, MODE>((int)order[k], s_rec, s_id, s_wmask, s_list, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, out, out_last, out_tfin, out_ntri, stack, cap, npix, need);
-        __syncthreads();
-    }
-}
-
-// tile order for the persistent launch: key = 0xffff - min(list length, 0xffff)
-__global__ void tile_order_keys_kernel(const int64_t* __restrict__ off, int64_t M, uint32_t* __restrict__ k,
-                                       uint32_t* __restrict__ v, uint32_t* __restrict__ m_dev) {
+// Per tile: its list length (sum over its region's chunks) and, per chunk,
+// the count of the region's earlier chunks (the chunk's first slot within
+// the tile's list).
+__global__ void tile_totals_kernel(const uint32_t* __restrict__ coff, const uint32_t* __restrict__ nblk_dev, int64_t R,
+                                   int64_t M, int tiles_x, int tiles_per_cam, int regions_x, int regions_per_cam,
+                                   const uint32_t* __restrict__ ccnt, uint32_t* __restrict__ cpre,
+                                   uint32_t* __restrict__ tcnt) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t == 0) *m_dev = (uint32_t)M;
     if (t >= M) return;
-    const int64_t c = off[t + 1] - off[t];
-    k[t] = 0xffffu - (uint32_t)min(c, (int64_t)0xffff);
-    v[t] = (uint32_t)t;
+    const int cam = (int)(t / tiles_per_cam);
+    const int lt = (int)(t - (int64_t)cam * tiles_per_cam);
+    const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
+    const int64_t r = (int64_t)cam * regions_per_cam + (ty / kRegionTY) * regions_x + tx / kRegionTX;
+    const int l = (ty % kRegionTY) * kRegionTX + tx % kRegionTX;
+    const uint32_t b0 = coff[r], b1 = r + 1 < R ? coff[r + 1] : *nblk_dev;
+    uint32_t run = 0;
+    for (uint32_t b = b0; b < b1; ++b) {
+        cpre[(int64_t)b * 32 + l] = run;
+        run += ccnt[(int64_t)b * 32 + l];
+    }
+    tcnt[t] = run;
+}
+
+// Fill pass: writes each pair's id into the lists of the tiles its record
+// covers.  Rounds of 256 pairs in order; per tile, ballots rank the pairs of
+// a warp and a scan over the warps ranks the warps, so each tile receives the
+// chunk's ids in pair order.
+__global__ void __launch_bounds__(kRegionThreads) region_fill_kernel(
+    const uint32_t* __restrict__ rv, const BinInfo* __restrict__ bin, const uint32_t* __restrict__ coff,
+    const uint32_t* __restrict__ rstart, const uint32_t* __restrict__ nblk_dev, int64_t R, int ts, int regions_x,
+    int regions_per_cam, int tiles_x, int tiles_y, int tiles_per_cam, int64_t ntot, const uint32_t* __restrict__ toff,
+    const uint32_t* __restrict__ cpre, uint32_t* __restrict__ ids) {
+    constexpr int NW = kRegionThreads / 32;
+    __shared__ uint32_t s_bal[NW][32];
+    __shared__ uint32_t s_pre[NW][32];
+    __shared__ uint32_t s_base[32];
+    if (blockIdx.x >= *nblk_dev) return;
+    const RegionChunk c = region_chunk(coff, rstart, R, blockIdx.x, regions_x, regions_per_cam, tiles_x,
+                                       tiles_per_cam, ntot);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x < 32) {
+        const int lx = threadIdx.x % kRegionTX, ly = threadIdx.x / kRegionTX;
+        const bool exists = c.tx0 + lx < tiles_x && c.ty0 + ly < tiles_y;
+        s_base[threadIdx.x] = exists ? toff[c.tile0 + (int64_t)ly * tiles_x + lx] +
+                                           cpre[(int64_t)blockIdx.x * 32 + threadIdx.x]
+                                     : 0u;
+    }
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    for (int64_t b0 = c.e0; b0 < c.e1; b0 += kRegionThreads) {
+        const int64_t e = b0 + threadIdx.x;
+        uint32_t m = 0, id = 0;
+        if (e < c.e1) {
+            id = rv[e];
+            m = region_tile_mask(bin[c.rec_base + id], ts, c.tx0, c.ty0);
+        }
+        uint32_t mine = 0;
+#pragma unroll
+        for (int t = 0; t < 32; ++t) {
+            const uint32_t bal = __ballot_sync(0xffffffffu, (m >> t) & 1u);
+            if (lane == t) mine = bal;
+        }
+        s_bal[warp][lane] = mine;
+        __syncthreads();  // (also orders s_base's first write before its use)
+        if (threadIdx.x < 32) {
+            uint32_t run = s_base[threadIdx.x];
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                s_pre[w][threadIdx.x] = run;
+                run += __popc(s_bal[w][threadIdx.x]);
+            }
+            s_base[threadIdx.x] = run;
+        }
+        __syncthreads();
+        while (m) {
+            const int t = __ffs(m) - 1;
+            m &= m - 1u;
+            ids[s_pre[warp][t] + __popc(s_bal[warp][t] & lt_mask)] = id;
+        }
+        __syncthreads();  // s_bal / s_pre are rewritten by the next round
+    }
+}
+
+// tile_off (int64, M + 1 entries) from the 32-bit tile scan and its total.
+__global__ void tile_off_kernel(const uint32_t* __restrict__ toff, const uint32_t* __restrict__ total, int64_t M,
+                                int64_t* __restrict__ off) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < M) off[t] = toff[t];
+    else if (t == M) off[M] = *total;
 }
 
 // ---------------------------------------------------------------------------
-// frame inspection: split sorted keys into ids / depth bits
+// frame inspection: per tile (one thread each), its ids and their depth bits
 
-__global__ void lists_kernel(const uint32_t* __restrict__ tk, const uint32_t* __restrict__ tv, int64_t n, const BinInfo* __restrict__ bin, int64_t ntot, int tiles_per_cam,
+__global__ void lists_kernel(const int64_t* __restrict__ off, const uint32_t* __restrict__ tids, int64_t M,
+                             const BinInfo* __restrict__ bin, int64_t ntot, int tiles_per_cam,
                              int32_t* __restrict__ ids, uint32_t* __restrict__ dbits) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const uint32_t id = tv[i];
-    const int cam = (int)(tk[i] / (uint32_t)tiles_per_cam);
-    ids[i] = (int32_t)id;
-    dbits[i] = bin[(int64_t)cam * ntot + id].dbits;
-}
-
-
-cudaError_t radix_sort_pairs(umgs_frame* fr, uint32_t* k, uint32_t* v, uint32_t* k2, uint32_t* v2,
-                             const uint32_t* n_dev, int64_t n_cap, int bits, uint32_t** rk, uint32_t** rv,
-                             cudaStream_t s);
-
-cudaError_t launch_composite(umgs_frame* fr, const umgs_render_opts& opts, float* out_rgbt, cudaStream_t stream) {
-    const float te = opts.t_eps > 0.f ? opts.t_eps : -1.f;
-    float4* out = reinterpret_cast<float4*>(out_rgbt);
-    const int ts = fr->tile;
-    const unsigned M = (unsigned)fr->num_tiles;
-    const int tpc = fr->tiles_x * fr->tiles_y;
-    const int64_t npix = (int64_t)fr->ncams * fr->W * fr->H;
-    const bool save = fr->saved;
-    if (save) cudaMemsetAsync(fr->status.as<int32_t>() + 2, 0, sizeof(int32_t), stream);
-    const bool persist = opts.sched > 0;
-    const uint32_t* order = nullptr;
-    unsigned* work = nullptr;
-    int nblk = 0;
-    if (persist) {
-        // tiles in decreasing order of list length (stable radix sort of 16-bit keys)
-        cudaError_t e;
-        if ((e = fr->ord_k.reserve(sizeof(uint32_t) * M)) != cudaSuccess) return e;
-        if ((e = fr->ord_v.reserve(sizeof(uint32_t) * M)) != cudaSuccess) return e;
-        if ((e = fr->ord_k2.reserve(sizeof(uint32_t) * M)) != cudaSuccess) return e;
-        if ((e = fr->ord_v2.reserve(sizeof(uint32_t) * M)) != cudaSuccess) return e;
-        uint32_t* mdev = reinterpret_cast<uint32_t*>(fr->status.as<int32_t>() + 4);
-        work = reinterpret_cast<unsigned*>(fr->status.as<int32_t>() + 8);
-        tile_order_keys_kernel<<<(M + 255) / 256, 256, 0, stream>>>(fr->tile_off.as<int64_t>(), M, fr->ord_k.as<uint32_t>(),
-                                                                     fr->ord_v.as<uint32_t>(), mdev), count_launch();
-        uint32_t* rk = nullptr;
-        uint32_t* rv = nullptr;
-        if ((e = radix_sort_pairs(fr, fr->ord_k.as<uint32_t>(), fr->ord_v.as<uint32_t>(), fr->ord_k2.as<uint32_t>(),
-                                  fr->ord_v2.as<uint32_t>(), mdev, M, 16, &rk, &rv, stream)) != cudaSuccess)
-            return e;
-        order = rv;
-        cudaMemsetAsync(work, 0, sizeof(unsigned), stream);
-        nblk = opts.sched * fr->ctx->num_sms;
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= M) return;
+    const int64_t cam = t / tiles_per_cam;
+    for (int64_t i = off[t]; i < off[t + 1]; ++i) {
+        const uint32_t id = tids[i];
+        ids[i] = (int32_t)id;
+        dbits[i] = bin[cam * ntot + id].dbits;
     }
-#define UMGS_LAUNCH(TSV, SV, MV)                                                                                \
-    if (persist) composite_persistent_kernel<TSV, SV, MV><<<nblk, TSV * TSV, 0, stream>>>(order, work, M,      \
-        fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->mixed ? fr->grec.as<GRec16>() : nullptr,  \
-        fr->trec.as<TRec>(), fr->ng,                                                                            \
-        fr->nt, fr->tiles_x, tpc, fr->W, fr->H, te, opts.bg[0], opts.bg[1], opts.bg[2], out,                      \
-        fr->last.as<int32_t>(), save ? fr->tfin.as<float>() : nullptr, save ? fr->ntri.as<int32_t>() : nullptr,   \
-        save ? fr->stack.as<float4>() : nullptr, fr->stack_cap, npix, fr->status.as<int32_t>() + 2),            \
-        count_launch();                                                                                         \
-    else composite_kernel<TSV, SV, MV><<<M, TSV * TSV, 0, stream>>>(                                            \
-        fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->mixed ? fr->grec.as<GRec16>() : nullptr,  \
-        fr->trec.as<TRec>(), fr->ng,                                                                            \
-        fr->nt, fr->tiles_x, tpc, fr->W, fr->H, te, opts.bg[0], opts.bg[1], opts.bg[2], out,                      \
-        fr->last.as<int32_t>(), save ? fr->tfin.as<float>() : nullptr, save ? fr->ntri.as<int32_t>() : nullptr,   \
-        save ? fr->stack.as<float4>() : nullptr, fr->stack_cap, npix, fr->status.as<int32_t>() + 2),            \
-        count_launch()
-    // the saved (backward) form exists for FULL only
-#define UMGS_MODES(TSV)                                                                                         \
-    if (save) { UMGS_LAUNCH(TSV, true, UMGS_BLEND_FULL); }                                                      \
-    else if (mode == kModeTProduct) { UMGS_LAUNCH(TSV, false, kModeTProduct); }                                 \
-    else if (mode == UMGS_BLEND_DIRECT) { UMGS_LAUNCH(TSV, false, UMGS_BLEND_DIRECT); }                         \
-    else if (mode == UMGS_BLEND_MSAA_ALL) { UMGS_LAUNCH(TSV, false, UMGS_BLEND_MSAA_ALL); }                     \
-    else if (mode == UMGS_BLEND_ENTITY_ALL) { UMGS_LAUNCH(TSV, false, UMGS_BLEND_ENTITY_ALL); }                 \
-    else { UMGS_LAUNCH(TSV, false, UMGS_BLEND_FULL); }
-    const int mode = (opts.blend_mode == UMGS_BLEND_FULL && (opts.flags & UMGS_RENDER_T_PRODUCT)) ? kModeTProduct
-                                                                                                : opts.blend_mode;
-    if (ts == 16) { UMGS_MODES(16) }
-    else if (ts == 8) { UMGS_MODES(8) }
-    else { UMGS_MODES(32) }
-#undef UMGS_MODES
-#undef UMGS_LAUNCH
-    return cudaGetLastError();
 }
 
 
@@ -1002,6 +903,27 @@ cudaError_t radix_sort_pairs(umgs_frame* fr, uint32_t* k, uint32_t* v, uint32_t*
 
 static inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
 
+// Buffers of the binning stage for `rcap` (region, id) pairs and `kcap`
+// tile-list entries, for the frame's current image, tile size and cameras.
+cudaError_t reserve_binning(umgs_frame* fr, int64_t rcap, int64_t kcap) {
+    const int regions_x = (fr->tiles_x + kRegionTX - 1) / kRegionTX;
+    const int64_t R = (int64_t)regions_x * ((fr->tiles_y + kRegionTY - 1) / kRegionTY) * fr->ncams;
+    const int64_t M = fr->num_tiles;
+    const int64_t nblk_max = (rcap + kRegionChunk - 1) / kRegionChunk + R;
+    cudaError_t e;
+    for (DevBuf* b : {&fr->tk, &fr->tv, &fr->tk2, &fr->tv2})
+        if ((e = b->reserve(sizeof(uint32_t) * std::max<int64_t>(1, rcap))) != cudaSuccess) return e;
+    if ((e = fr->tl_ids.reserve(sizeof(uint32_t) * std::max<int64_t>(1, kcap))) != cudaSuccess) return e;
+    if ((e = fr->rg_start.reserve(sizeof(uint32_t) * (R + 1))) != cudaSuccess) return e;
+    if ((e = fr->rg_nchunk.reserve(sizeof(uint32_t) * R)) != cudaSuccess) return e;
+    if ((e = fr->rg_coff.reserve(sizeof(uint32_t) * R)) != cudaSuccess) return e;
+    if ((e = fr->rg_ccnt.reserve(sizeof(uint32_t) * 32 * nblk_max)) != cudaSuccess) return e;
+    if ((e = fr->rg_cpre.reserve(sizeof(uint32_t) * 32 * nblk_max)) != cudaSuccess) return e;
+    if ((e = fr->tl_cnt.reserve(sizeof(uint32_t) * std::max<int64_t>(1, M))) != cudaSuccess) return e;
+    if ((e = fr->tl_off.reserve(sizeof(uint32_t) * std::max<int64_t>(1, M))) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
 umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_mesh* meshes, int32_t nmeshes,
                            const umgs_camera* cams, int32_t ncams, const umgs_render_opts& opts, float* out_rgbt,
                            umgs_frame* fr, cudaStream_t stream) {
@@ -1042,10 +964,13 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     UMGS_TRY(fr->trec.reserve(sizeof(TRec) * std::max<int64_t>(1, Nt * ncams)));
     UMGS_TRY(fr->bin.reserve(sizeof(BinInfo) * std::max<int64_t>(1, Ntot * ncams)));
     UMGS_TRY(fr->tile_off.reserve(sizeof(int64_t) * (M + 1)));
-    // status words: [0] error bits, [1] number of (tile, id) pairs, [2] largest
-    // saved-stack need, [3] fp64 conic list length, [4] tile count for the
-    // tile-order sort, [5] record count for the depth sort, [6..7] evaluation
-    // count (u64), [8] persistent work counter, [9] pair-count overflow
+    // status words: [0] error bits, [1] number of tile-list entries (32-bit,
+    // 0xffffffff when it does not fit), [2] largest saved-stack need, [3] fp64
+    // conic list length, [4] tile count for the tile-order sort, [5] record
+    // count for the depth sort, [6..7] evaluation count (u64), [8] persistent
+    // work counter, [9] scan overflow, [10..11] tile-list entries (u64),
+    // [12] (region, id) pairs, [13] count/fill chunks, [14] tile-list entries
+    // from the tile scan
     UMGS_TRY(fr->status.reserve(sizeof(int32_t) * 16));
 
     // cameras: host -> pinned staging -> device
@@ -1113,8 +1038,12 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
         }
         tri_base += me.nf;
     }
-    // ---- binning: depth sort of all records, pair emission, stable tile sort
+    // ---- binning: depth sort of all records, (region, id) emission, stable
+    // region sort, expansion into the tile lists (see prim_keys_kernel)
     const int64_t NR = Ntot * ncams;  // (camera, primitive) records
+    const int regions_x = (tiles_x + kRegionTX - 1) / kRegionTX;
+    const int regions_per_cam = regions_x * ((tiles_y + kRegionTY - 1) / kRegionTY);
+    const int64_t R = (int64_t)regions_per_cam * ncams;
     UMGS_TRY(fr->pk.reserve(sizeof(uint32_t) * std::max<int64_t>(1, NR)));
     UMGS_TRY(fr->pv.reserve(sizeof(uint32_t) * std::max<int64_t>(1, NR)));
     UMGS_TRY(fr->pk2.reserve(sizeof(uint32_t) * std::max<int64_t>(1, NR)));
@@ -1124,6 +1053,10 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     uint32_t* pk = fr->pk.as<uint32_t>();
     uint32_t* pv = fr->pv.as<uint32_t>();
     uint32_t* status_u = reinterpret_cast<uint32_t*>(fr->status.as<int32_t>());
+    unsigned long long* ktotal = reinterpret_cast<unsigned long long*>(status_u + 10);
+    uint32_t* rn = status_u + 12;    // number of (region, id) pairs
+    uint32_t* nblk = status_u + 13;  // number of count/fill chunks
+    uint32_t* ktot32 = status_u + 14;
     if (NR > 0) {
         StageTimer tm(ctx, UMGS_STAGE_SCAN, stream);
         prim_keys_kernel<<<grid_for(NR, 256), 256, 0, stream>>>(fr->bin.as<BinInfo>(), NR, pk, pv, status_u + 5), count_launch();
@@ -1134,62 +1067,85 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
                                   &rv, stream));
         pk = rk;
         pv = rv;
-        tile_counts_kernel<<<grid_for(NR, 256), 256, 0, stream>>>(fr->bin.as<BinInfo>(), pv, NR, ts,
-                                                                  fr->pcnt.as<uint32_t>()), count_launch();
-        UMGS_TRY(scan_u32(fr, fr->pcnt.as<uint32_t>(), fr->poff.as<uint32_t>(), NR, status_u + 1, stream));
+        region_counts_kernel<<<grid_for(NR, 256), 256, 0, stream>>>(fr->bin.as<BinInfo>(), pv, NR, ts,
+                                                                    fr->pcnt.as<uint32_t>(), ktotal), count_launch();
+        UMGS_TRY(cudaGetLastError());
+        UMGS_TRY(scan_u32(fr, fr->pcnt.as<uint32_t>(), fr->poff.as<uint32_t>(), NR, rn, stream));
     }
-    int64_t Kcap;
+    int64_t Kcap, rcap;
     if (!fr->nosync) {
-        // read back the number of pairs (and the status word)
-        UMGS_TRY(cudaMemcpyAsync(ctx->pinned, fr->status.ptr, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
+        // read back the status words: error bits, list entries, region pairs
+        UMGS_TRY(cudaMemcpyAsync(ctx->pinned, fr->status.ptr, 16 * sizeof(int32_t), cudaMemcpyDeviceToHost, stream));
         UMGS_TRY(cudaStreamSynchronize(stream));
-        const int32_t st = (int32_t)(ctx->pinned[0] & 0xffffffff);
-        const int64_t K = NR > 0 ? (int64_t)(uint32_t)(ctx->pinned[0] >> 32) : 0;
-        if (st & 1) return fail(ctx, UMGS_ERR_INVALID_ARG, "a face index is out of range");
-        if (K == 0xffffffffll) return fail(ctx, UMGS_ERR_CAPACITY, "more than 4294967294 (tile, primitive) pairs");
-        fr->num_keys = K;
-        Kcap = K;
-        UMGS_TRY(fr->tk.reserve(sizeof(uint32_t) * std::max<int64_t>(1, K)));
-        UMGS_TRY(fr->tv.reserve(sizeof(uint32_t) * std::max<int64_t>(1, K)));
-        UMGS_TRY(fr->tk2.reserve(sizeof(uint32_t) * std::max<int64_t>(1, K)));
-        UMGS_TRY(fr->tv2.reserve(sizeof(uint32_t) * std::max<int64_t>(1, K)));
+        const uint32_t* w = reinterpret_cast<const uint32_t*>(ctx->pinned);
+        const uint64_t K64 = (uint64_t)w[10] | ((uint64_t)w[11] << 32);
+        if (w[0] & 1) return fail(ctx, UMGS_ERR_INVALID_ARG, "a face index is out of range");
+        if (K64 >= 0xffffffffull) return fail(ctx, UMGS_ERR_CAPACITY, "more than 4294967294 (tile, primitive) pairs");
+        fr->num_keys = (int64_t)K64;
+        Kcap = (int64_t)K64;
+        rcap = NR > 0 ? (int64_t)w[12] : 0;
     } else {
-        // no host read-back: the pairs are held to the reserved capacity and an
-        // overflow is flagged in the status word (bit 2); inside a capture the
-        // buffers were sized beforehand
+        // no host read-back: the lists are held to the reserved capacity and
+        // an overflow is flagged in the status word (bit 2); inside a capture
+        // the buffers were sized beforehand
         Kcap = fr->key_capacity;
+        rcap = Kcap;  // region pairs never outnumber list entries
         fr->num_keys = -1;
-        if (!fr->capture) {
-            UMGS_TRY(fr->tk.reserve(sizeof(uint32_t) * std::max<int64_t>(1, Kcap)));
-            UMGS_TRY(fr->tv.reserve(sizeof(uint32_t) * std::max<int64_t>(1, Kcap)));
-            UMGS_TRY(fr->tk2.reserve(sizeof(uint32_t) * std::max<int64_t>(1, Kcap)));
-            UMGS_TRY(fr->tv2.reserve(sizeof(uint32_t) * std::max<int64_t>(1, Kcap)));
-        }
     }
-    fr->ids = fr->tv.as<uint32_t>();
-    fr->tkeys = fr->tk.as<uint32_t>();
+    if (!fr->capture) UMGS_TRY(reserve_binning(fr, rcap, Kcap));
+    fr->ids = fr->tl_ids.as<uint32_t>();
     if (NR > 0) {
         StageTimer tm(ctx, UMGS_STAGE_SCATTER, stream);
-emit_pairs_kernel<<<grid_for(NR, 256), 256, 0, stream>>>(fr->bin.as<BinInfo>(), pv, fr->poff.as<uint32_t>(), NR,
-                                                                 Ntot, ts, tiles_x, tiles_per_cam, fr->tk.as<uint32_t>(),
-                                                                 fr->tv.as<uint32_t>(), Kcap, fr->status.as<int32_t>()),
-            count_launch();
+        emit_region_pairs_kernel<<<grid_for(NR, 256), 256, 0, stream>>>(
+            fr->bin.as<BinInfo>(), pv, fr->poff.as<uint32_t>(), NR, Ntot, ts, regions_x, regions_per_cam, ktotal,
+            Kcap, fr->tk.as<uint32_t>(), fr->tv.as<uint32_t>(), rcap, rn, fr->status.as<int32_t>()), count_launch();
         UMGS_TRY(cudaGetLastError());
     }
     {
         StageTimer tm(ctx, UMGS_STAGE_SORT, stream);
-        if (Kcap > 0) {
+        uint32_t* rk = fr->tk.as<uint32_t>();
+        uint32_t* rv = fr->tv.as<uint32_t>();
+        if (NR > 0 && rcap > 0 && R > 1) {
             int bits = 1;
-            while (((int64_t)1 << bits) < M) ++bits;
-            uint32_t* rk = nullptr;
-            uint32_t* rv = nullptr;
+            while (((int64_t)1 << bits) < R) ++bits;
             UMGS_TRY(radix_sort_pairs(fr, fr->tk.as<uint32_t>(), fr->tv.as<uint32_t>(), fr->tk2.as<uint32_t>(),
-                                      fr->tv2.as<uint32_t>(), status_u + 1, Kcap, bits, &rk, &rv, stream));
-            fr->tkeys = rk;
-            fr->ids = rv;
+                                      fr->tv2.as<uint32_t>(), rn, rcap, bits, &rk, &rv, stream));
         }
-        tile_ranges_kernel<<<grid_for(M + 1, 256), 256, 0, stream>>>(fr->tkeys, status_u + 1, Kcap, M,
-                                                                     fr->tile_off.as<int64_t>()), count_launch();
+        const int64_t nblk_max = (rcap + kRegionChunk - 1) / kRegionChunk + R;
+        uint32_t* rstart = fr->rg_start.as<uint32_t>();
+        uint32_t* coff = fr->rg_coff.as<uint32_t>();
+        region_ranges_kernel<<<grid_for(R + 1, 256), 256, 0, stream>>>(rk, rn, rcap, R, rstart,
+                                                                       fr->rg_nchunk.as<uint32_t>()), count_launch();
+        UMGS_TRY(cudaGetLastError());
+        if (R <= kSmallScanMax) {
+            scan_small_kernel<<<1, 1024, 0, stream>>>(fr->rg_nchunk.as<uint32_t>(), R, coff, nblk), count_launch();
+            UMGS_TRY(cudaGetLastError());
+        } else {
+            UMGS_TRY(scan_u32(fr, fr->rg_nchunk.as<uint32_t>(), coff, R, nblk, stream));
+        }
+        region_count_kernel<<<(unsigned)nblk_max, kRegionThreads, 0, stream>>>(
+            rv, fr->bin.as<BinInfo>(), coff, rstart, nblk, R, ts, regions_x, regions_per_cam, tiles_x, tiles_per_cam,
+            Ntot, fr->rg_ccnt.as<uint32_t>()), count_launch();
+        UMGS_TRY(cudaGetLastError());
+        tile_totals_kernel<<<grid_for(M, 256), 256, 0, stream>>>(coff, nblk, R, M, tiles_x, tiles_per_cam, regions_x,
+                                                                 regions_per_cam, fr->rg_ccnt.as<uint32_t>(),
+                                                                 fr->rg_cpre.as<uint32_t>(), fr->tl_cnt.as<uint32_t>()),
+            count_launch();
+        UMGS_TRY(cudaGetLastError());
+        if (M <= kSmallScanMax) {
+            scan_small_kernel<<<1, 1024, 0, stream>>>(fr->tl_cnt.as<uint32_t>(), M, fr->tl_off.as<uint32_t>(), ktot32),
+                count_launch();
+            UMGS_TRY(cudaGetLastError());
+        } else {
+            UMGS_TRY(scan_u32(fr, fr->tl_cnt.as<uint32_t>(), fr->tl_off.as<uint32_t>(), M, ktot32, stream));
+        }
+        region_fill_kernel<<<(unsigned)nblk_max, kRegionThreads, 0, stream>>>(
+            rv, fr->bin.as<BinInfo>(), coff, rstart, nblk, R, ts, regions_x, regions_per_cam, tiles_x, tiles_y,
+            tiles_per_cam, Ntot, fr->tl_off.as<uint32_t>(), fr->rg_cpre.as<uint32_t>(), fr->tl_ids.as<uint32_t>()),
+            count_launch();
+        UMGS_TRY(cudaGetLastError());
+        tile_off_kernel<<<grid_for(M + 1, 256), 256, 0, stream>>>(fr->tl_off.as<uint32_t>(), ktot32, M,
+                                                                  fr->tile_off.as<int64_t>()), count_launch();
         UMGS_TRY(cudaGetLastError());
     }
     UMGS_TRY(fr->last.reserve(sizeof(int32_t) * (int64_t)ncams * W * H));
@@ -1206,80 +1162,6 @@ emit_pairs_kernel<<<grid_for(NR, 256), 256, 0, stream>>>(fr->bin.as<BinInfo>(), 
     }
     fr->valid = true;
 #undef UMGS_TRY
-    return UMGS_OK;
-}
-
-// N_alg of the last render (diagnostic, not part of the render): per pixel
-// the entries of its tile list whose pixel rect holds the pixel, up to and
-// including list position `last` when the pixel stopped at T < t_eps (bit 31
-// of the compositor's `last`), else all of them.  One CTA per tile, one
-// thread per pixel, summed into *count.
-template <int TS>
-__global__ void __launch_bounds__(TS * TS) eval_count_kernel(
-    const uint32_t* __restrict__ ids, const int64_t* __restrict__ off, const GRec* __restrict__ grec,
-    const GRec16* __restrict__ grec16, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
-    int tiles_per_cam, int W, int H, const int32_t* __restrict__ last, unsigned long long* __restrict__ count) {
-    const int tile = blockIdx.x;
-    const int cam = tile / tiles_per_cam;
-    const int lt = tile - cam * tiles_per_cam;
-    const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
-    int lx, ly;
-    block_pixel<TS>(threadIdx.x, lx, ly);
-    const int px = tx * TS + lx, py = ty * TS + ly;
-    unsigned long long c = 0;
-    if (px < W && py < H) {
-        const int64_t beg = off[tile], end = off[tile + 1];
-        const int32_t l = last[((int64_t)cam * H + py) * W + px];
-        const int64_t lim = (l < 0) ? (int64_t)(l & 0x7fffffff) : end - beg;
-        for (int64_t p = 0; p < lim; ++p) {
-            const uint32_t id = ids[beg + p];
-            uint32_t rx, ry;
-            if (id >= Ng + Nt) continue;
-            if (id < Ng) {
-                if (grec16) {
-                    const uint4 h1 = grec16[(int64_t)cam * Ng + id].v1;
-                    rx = h1.z; ry = h1.w;
-                } else {
-                    const float4 c2 = reinterpret_cast<const float4*>(grec + (int64_t)cam * Ng + id)[2];
-                    rx = __float_as_uint(c2.y); ry = __float_as_uint(c2.z);
-                }
-            } else {
-                const TRec& t = trec[(int64_t)cam * Nt + (id - Ng)];
-                rx = t.rx; ry = t.ry;
-            }
-            c += (px >= (int)(rx & 0xffff) && px <= (int)(rx >> 16) && py >= (int)(ry & 0xffff) &&
-                  py <= (int)(ry >> 16)) ? 1ull : 0ull;
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
-}
-
-umgs_status frame_evaluations(const umgs_frame* fr, int64_t* evals, cudaStream_t stream) {
-    cudaError_t e;
-    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(fr->status.as<int32_t>() + 6);
-    if ((e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), stream)) != cudaSuccess)
-        return cuda_fail(fr->ctx, e, "cudaMemsetAsync");
-    const int tpc = fr->tiles_x * fr->tiles_y;
-    const unsigned M = (unsigned)fr->num_tiles;
-    if (M > 0) {
-#define UMGS_LAUNCH(TSV)                                                                                        \
-        eval_count_kernel<TSV><<<M, TSV * TSV, 0, stream>>>(fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), \
-            fr->mixed ? fr->grec.as<GRec16>() : nullptr, fr->trec.as<TRec>(), fr->ng, fr->nt, fr->tiles_x, tpc,   \
-            fr->W, fr->H, fr->last.as<int32_t>(), cnt), count_launch()
-        if (fr->tile == 16) UMGS_LAUNCH(16);
-        else if (fr->tile == 8) UMGS_LAUNCH(8);
-        else UMGS_LAUNCH(32);
-#undef UMGS_LAUNCH
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(fr->ctx, e, "eval_count_kernel");
-    }
-    unsigned long long v = 0;
-    if ((e = cudaMemcpyAsync(fr->ctx->pinned, cnt, sizeof(v), cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
-        (e = cudaStreamSynchronize(stream)) != cudaSuccess)
-        return cuda_fail(fr->ctx, e, "reading the evaluation count");
-    std::memcpy(&v, fr->ctx->pinned, sizeof(v));
-    *evals = (int64_t)v;
     return UMGS_OK;
 }
 
@@ -1302,9 +1184,9 @@ umgs_status frame_lists(const umgs_frame* fr, int64_t* tile_ptr, int32_t* ids, u
                                     cudaMemcpyDeviceToDevice, stream);
     if (e != cudaSuccess) return cuda_fail(fr->ctx, e, "cudaMemcpyAsync(tile_ptr)");
     if (fr->num_keys > 0) {
-        lists_kernel<<<grid_for(fr->num_keys, 256), 256, 0, stream>>>(
-            fr->tkeys, fr->ids, fr->num_keys, fr->bin.as<BinInfo>(), fr->ng + fr->nt, fr->tiles_x * fr->tiles_y, ids,
-            dbits), count_launch();
+        lists_kernel<<<grid_for(fr->num_tiles, 256), 256, 0, stream>>>(
+            fr->tile_off.as<int64_t>(), fr->ids, fr->num_tiles, fr->bin.as<BinInfo>(), fr->ng + fr->nt,
+            fr->tiles_x * fr->tiles_y, ids, dbits), count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(fr->ctx, e, "lists_kernel");
     }
