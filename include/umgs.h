@@ -157,9 +157,10 @@ void umgs_frame_destroy(umgs_frame* frame);
  * Renders ncams views of the Gaussians and nmeshes meshes in ONE pass per
  * view: Gaussians are EWA-projected to 2D conics, triangles are set up with
  * integer edge functions over 4 samples per pixel; every primitive is binned
- * into the screen tiles its footprint touches with the key
- * (camera*tiles + tile, depth bits, unified id), the keys are sorted, and
- * each pixel composites its depth-ordered fragments front to back.  A run of
+ * into the lists of the screen tiles its footprint touches, each list in
+ * (depth bits, unified id) order (records sorted by depth once, then binned
+ * through regions of 8 x 4 tiles), and each pixel composites its
+ * depth-ordered fragments front to back.  A run of
  * depth-adjacent triangle fragments with no Gaussian between them forms one
  * entity whose sub-pixel transmittances t^j give the continuous coverage
  * O_i (Eq. 7-9); T after an entity is T_in * mean_j t^j.  Gaussian alpha is
@@ -179,8 +180,10 @@ void umgs_frame_destroy(umgs_frame* frame);
  * on the host afterwards, and a render that needs more pairs composites no
  * tile and is reported by umgs_frame_check).
  * Errors: INVALID_ARG (NULL arrays with n > 0, ncams < 1, mixed image sizes,
- * tile_size not 8/16/32, sh_degree > 3, ASYNC without a frame or capacity),
- * OUT_OF_MEMORY, CUDA.
+ * image sides above 32768, tile_size not 8/16/32, sh_degree > 3, more than
+ * 4294967294 primitives, more than 2^22 regions of 8 x 4 tiles over the
+ * cameras, ASYNC without a frame or capacity), CAPACITY (more than
+ * 4294967294 (tile, primitive) list entries), OUT_OF_MEMORY, CUDA.
  */
 umgs_status umgs_render(umgs_ctx* ctx, const umgs_gaussians* gaussians,
                         const umgs_mesh* meshes, int32_t nmeshes,
@@ -332,8 +335,10 @@ umgs_status umgs_deform_vertex_table(umgs_ctx* ctx, float* out_table, int64_t nv
  * umgs_deform_compact is umgs_deform (same modes, outputs and errors; NaN and
  * a status bit for a -1 count) over that form: about 10 vertex rows gathered
  * per Gaussian instead of 24; it agrees with umgs_deform up to fp32
- * summation order.  Both asynchronous on `stream`; bary and the entries
- * 8-byte aligned.  Errors: INVALID_ARG (sizes, NULL arrays, alignment), CUDA. */
+ * summation order.  Both asynchronous on `stream`; bary 8-byte aligned, the
+ * entries 8-byte aligned for umgs_binding_compact and 16-byte aligned for
+ * umgs_deform_compact (it reads two entries per load).  Errors: INVALID_ARG
+ * (sizes, NULL arrays, alignment), CUDA. */
 umgs_status umgs_binding_compact(umgs_ctx* ctx, const int32_t* face, const float* bary, int64_t n,
                                  const int32_t* proxy_f, int64_t nv, int64_t nf, int32_t* out_count,
                                  int32_t* out_entries, void* stream);
@@ -411,7 +416,7 @@ long long umgs_kernel_launches(void);
  *
  * Its scratch (per-vertex accumulators, the vertex transform table and a
  * status word) lives in one file-scope __device__ array sized for
- * UMGS_NOALLOC_MAX_PROXY_VERTICES proxy vertices (about 2.9 MB), which every
+ * UMGS_NOALLOC_MAX_PROXY_VERTICES proxy vertices (about 3.4 MB), which every
  * GPU that loads the library keeps until the process exits.
  *  - Runs on the CALLING thread's current device and on `stream`.
  *  - The first call on a device looks up the array's device address

@@ -181,14 +181,17 @@ umgs_status umgs_render(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_mesh*
         if (me.nf > 0 && (!me.verts || !me.faces || !me.vcolor || me.nv < 1))
             return fail(ctx, UMGS_ERR_INVALID_ARG, "mesh array is NULL");
     }
-    {   // unified 32-bit primitive ids and 32-bit (camera, tile) keys
+    {   // unified 32-bit primitive ids; (camera, region) keys of 22 bits
         int64_t nprim = (g && g->n > 0) ? g->n : 0;
         for (int m = 0; m < nmeshes; ++m) nprim += meshes[m].nf;
         if (nprim > (int64_t)0xfffffffe)
             return fail(ctx, UMGS_ERR_INVALID_ARG, "more than 4294967294 primitives (Gaussians + triangles)");
-        const int64_t tiles = (int64_t)ncams * ((cams[0].width + opts.tile_size - 1) / opts.tile_size) *
-                              ((cams[0].height + opts.tile_size - 1) / opts.tile_size);
-        if (tiles > (int64_t)0xffffffff) return fail(ctx, UMGS_ERR_INVALID_ARG, "more than 2^32 tiles over the cameras");
+        const int64_t tx = (cams[0].width + opts.tile_size - 1) / opts.tile_size;
+        const int64_t ty = (cams[0].height + opts.tile_size - 1) / opts.tile_size;
+        const int64_t regions = (int64_t)ncams * ((tx + 7) / 8) * ((ty + 3) / 4);
+        if (regions > ((int64_t)1 << 22))
+            return fail(ctx, UMGS_ERR_INVALID_ARG,
+                        "more than 2^22 regions of 8x4 tiles over the cameras (fewer cameras or larger tiles)");
     }
     umgs_frame* fr = frame ? frame : ctx->default_frame;
     if (fr->ctx != ctx) return fail(ctx, UMGS_ERR_INVALID_ARG, "frame belongs to another context");
@@ -292,7 +295,8 @@ umgs_status umgs_deform_compact(umgs_ctx* ctx, const umgs_gaussians* rest, const
             return fail(ctx, UMGS_ERR_INVALID_ARG, "NULL array");
         if (!rest->cov3d && (!rest->quats || !rest->scales))
             return fail(ctx, UMGS_ERR_INVALID_ARG, "need quats+scales or cov3d");
-        if (reinterpret_cast<uintptr_t>(entries) & 7) return fail(ctx, UMGS_ERR_INVALID_ARG, "entries must be 8-byte aligned");
+        if (reinterpret_cast<uintptr_t>(entries) & 15)
+            return fail(ctx, UMGS_ERR_INVALID_ARG, "entries must be 16-byte aligned");
     }
     return deform_compact_forward(ctx, rest, count, reinterpret_cast<const int2*>(entries), proxy_v, proxy_vd,
                                   proxy_f, nv, nf, mode, out_means, out_cov3d, out_quats,
@@ -327,9 +331,11 @@ umgs_status umgs_bind(umgs_ctx* ctx, const umgs_gaussians* g, const float* proxy
 umgs_status umgs_deform_vertex_table(umgs_ctx* ctx, float* out_table, int64_t nv, void* stream) {
     if (!ctx || !out_table) return UMGS_ERR_INVALID_ARG;
     if (nv != ctx->vtab_rows || nv <= 0) return fail(ctx, UMGS_ERR_INVALID_ARG, "nv differs from the last umgs_deform");
-    cudaError_t e = cudaMemcpyAsync(out_table, ctx->vtab.ptr, sizeof(float) * 12 * nv, cudaMemcpyDeviceToDevice,
-                                    static_cast<cudaStream_t>(stream));
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpyAsync");
+    // the first 12 of the 16 floats of each internal row
+    cudaError_t e = cudaMemcpy2DAsync(out_table, sizeof(float) * 12, ctx->vtab.ptr, sizeof(float) * 16,
+                                      sizeof(float) * 12, (size_t)nv, cudaMemcpyDeviceToDevice,
+                                      static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMemcpy2DAsync");
     return UMGS_OK;
 }
 

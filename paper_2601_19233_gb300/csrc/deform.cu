@@ -6,8 +6,9 @@
 //                    three vertices (atomics).
 //   vertex_xforms    one thread per proxy vertex: D_v = sum / area, polar
 //                    D_v = R_v S_v (Jacobi eigen-decomposition of D^T D),
-//                    r_v = log R_v, Delta_v = V'_v - V_v -> a 48-byte row of
-//                    the vertex table (stays in L2: 10K vertices = 0.5 MB).
+//                    r_v = log R_v, Delta_v = V'_v - V_v -> a 64-byte row of
+//                    the vertex table (Delta, r, S (6), rest position V_v;
+//                    stays in L2: 10K vertices = 0.66 MB).
 //   deform_gaussians eight threads per Gaussian (one per bound point): 3 vertex
 //                    rows gathered from the table each, Eq. 12 interpolation,
 //                    shuffle-reduced over the 8 points, Eq. 13 averaging,
@@ -22,6 +23,7 @@
 namespace umgs {
 
 constexpr int kStatusBadIndex = 2;
+constexpr int64_t kVtabStride = 16;  // floats per vertex-table row
 
 // ---- small 3x3 helpers (row-major) ---------------------------------------
 
@@ -230,10 +232,12 @@ __global__ void __launch_bounds__(256) vertex_xforms_kernel(const float* __restr
     float R[9], S6[6], r[3];
     polar3(D, R, S6);
     log_rot(R, r);
-    float* o = vtab + 12 * v;
-    for (int d = 0; d < 3; ++d) o[d] = Vd[3 * v + d] - V[3 * v + d];
-    o[3] = r[0]; o[4] = r[1]; o[5] = r[2];
-    for (int k = 0; k < 6; ++k) o[6 + k] = S6[k];
+    float4* o = reinterpret_cast<float4*>(vtab + kVtabStride * v);
+    const float p0 = V[3 * v], p1 = V[3 * v + 1], p2 = V[3 * v + 2];
+    o[0] = make_float4(Vd[3 * v] - p0, Vd[3 * v + 1] - p1, Vd[3 * v + 2] - p2, r[0]);
+    o[1] = make_float4(r[1], r[2], S6[0], S6[1]);
+    o[2] = make_float4(S6[2], S6[3], S6[4], S6[5]);
+    o[3] = make_float4(p0, p1, p2, 0.f);
 }
 
 // ---- K2: per-Gaussian update ------------------------------------------------
@@ -377,9 +381,9 @@ __global__ void __launch_bounds__(256) deform_gaussians_kernel(
             for (int k = 0; k < 3; ++k) {
                 const int v = F[3 * (int64_t)f + k];
                 if (v < 0 || v >= nv) { bad = 1; continue; }
-                const float4* row = reinterpret_cast<const float4*>(vtab + 12 * (int64_t)v);
-                const float4 t0 = row[0], t1 = row[1], t2 = row[2];
-                const float px = V[3 * (int64_t)v], py = V[3 * (int64_t)v + 1], pz = V[3 * (int64_t)v + 2];
+                const float4* row = reinterpret_cast<const float4*>(vtab + kVtabStride * (int64_t)v);
+                const float4 t0 = row[0], t1 = row[1], t2 = row[2], t3 = row[3];
+                const float px = t3.x, py = t3.y, pz = t3.z;
                 const float wk = w[k];
                 acc[0] += wk * t0.x; acc[1] += wk * t0.y; acc[2] += wk * t0.z;     // Delta
                 acc[3] += wk * t0.w; acc[4] += wk * t1.x; acc[5] += wk * t1.y;     // log R
@@ -435,51 +439,64 @@ __global__ void __launch_bounds__(256) binding_compact_kernel(const int32_t* __r
     count[i] = c;
 }
 
-// Deformation over a compact binding: four lanes per Gaussian share its
-// entries (lane l takes entries l, l+4, ...: consecutive lanes read
-// consecutive 8-byte entries), gather the weighted vertex rows (48-byte table
-// row + rest position), reduce over the 4 lanes and finish as above.
+// Deformation over a compact binding: four lanes per Gaussian walk its
+// entries together; for each entry lane p gathers float4 p of the vertex's
+// 64-byte table row and accumulates those four of the 15 interpolated
+// components (so one warp-wide row load touches 8 rows of 64 contiguous
+// bytes instead of 32 scattered ones).  Entries are read two at a time
+// (16-byte loads) and four are in flight per step.  A shuffle round gives
+// every lane all 15 sums, and lanes 0-2 finish as above.
 __global__ void __launch_bounds__(256) deform_gaussians_compact_kernel(
     const float* __restrict__ means, const float* __restrict__ quats, const float* __restrict__ scales,
     const float* __restrict__ cov3d, int64_t n, const int32_t* __restrict__ count, const int2* __restrict__ entries,
-    const float* __restrict__ V, int64_t nv, const float* __restrict__ vtab, int mode, float* __restrict__ out_means,
+    int64_t nv, const float* __restrict__ vtab, int mode, float* __restrict__ out_means,
     float* __restrict__ out_cov, float* __restrict__ out_quats, int32_t* __restrict__ status) {
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t i = tid >> 2;
     const int part = (int)(tid & 3);
     const bool live = i < n;
-    float acc[15];
-#pragma unroll
-    for (int e = 0; e < 15; ++e) acc[e] = 0.f;
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
     int bad = 0;
+    int c = 0;
     if (live) {
-        const int c = count[i];
-        if (c < 0 || c > 24) {
-            bad = 1;
-        } else {
-            const int2* row = entries + 24 * i;
-            for (int j = part; j < c; j += 4) {
-                const int2 en = row[j];
-                const int v = en.x;
-                if (v < 0 || v >= nv) { bad = 1; continue; }
-                const float wk = __int_as_float(en.y);
-                const float4* t = reinterpret_cast<const float4*>(vtab + 12 * (int64_t)v);
-                const float4 t0 = t[0], t1 = t[1], t2 = t[2];
-                const float px = V[3 * (int64_t)v], py = V[3 * (int64_t)v + 1], pz = V[3 * (int64_t)v + 2];
-                acc[0] += wk * t0.x; acc[1] += wk * t0.y; acc[2] += wk * t0.z;     // Delta
-                acc[3] += wk * t0.w; acc[4] += wk * t1.x; acc[5] += wk * t1.y;     // log R
-                acc[6] += wk * t1.z; acc[7] += wk * t1.w; acc[8] += wk * t2.x;     // S
-                acc[9] += wk * t2.y; acc[10] += wk * t2.z; acc[11] += wk * t2.w;
-                acc[12] += wk * px; acc[13] += wk * py; acc[14] += wk * pz;         // P
-            }
+        c = count[i];
+        if (c < 0 || c > 24) { bad = 1; c = 0; }
+    }
+    const int4* row = reinterpret_cast<const int4*>(entries + 24 * i);  // two entries per int4
+    const float4* tab = reinterpret_cast<const float4*>(vtab);
+    for (int j = 0; j < c; j += 4) {
+        const int4 e01 = row[j >> 1];
+        const int4 e23 = j + 2 < c ? row[(j >> 1) + 1] : make_int4(0, 0, 0, 0);
+        const int vv[4] = {e01.x, e01.z, e23.x, e23.z};
+        const int ww[4] = {e01.y, e01.w, e23.y, e23.w};
+        float4 t[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const bool use = j + q < c;
+            const int v = vv[q];
+            if (use && (v < 0 || v >= nv)) bad = 1;
+            t[q] = (use && v >= 0 && v < nv) ? tab[4 * (int64_t)v + part] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float wk = j + q < c ? __int_as_float(ww[q]) : 0.f;
+            a.x += wk * t[q].x; a.y += wk * t[q].y; a.z += wk * t[q].z; a.w += wk * t[q].w;
         }
     }
+    // lane q of the group holds components 4q .. 4q+3 (the 16th is padding)
+    const int g0 = (threadIdx.x & 31) & ~3;
+    float acc[15];
 #pragma unroll
-    for (int o = 2; o > 0; o >>= 1) {
-#pragma unroll
-        for (int e = 0; e < 15; ++e) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
-        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    for (int q = 0; q < 4; ++q) {
+        const float x = __shfl_sync(0xffffffffu, a.x, g0 + q);
+        const float y = __shfl_sync(0xffffffffu, a.y, g0 + q);
+        const float z = __shfl_sync(0xffffffffu, a.z, g0 + q);
+        const float w = __shfl_sync(0xffffffffu, a.w, g0 + q);
+        acc[4 * q] = x; acc[4 * q + 1] = y; acc[4 * q + 2] = z;
+        if (q < 3) acc[4 * q + 3] = w;
     }
+#pragma unroll
+    for (int o = 2; o > 0; o >>= 1) bad |= __shfl_xor_sync(0xffffffffu, bad, o);
     deform_finish(acc, 1.f, bad, live, part, i, means, quats, scales, cov3d, mode, out_means, out_cov, out_quats,
                   status);
 }
@@ -491,7 +508,8 @@ static umgs_status proxy_table(umgs_ctx* ctx, const float* V, const float* Vd, c
                                int64_t nf, cudaStream_t stream) {
     cudaError_t e;
     if ((e = ctx->vacc.reserve(sizeof(float) * 10 * nv)) != cudaSuccess) return fail(ctx, UMGS_ERR_OUT_OF_MEMORY, "vacc");
-    if ((e = ctx->vtab.reserve(sizeof(float) * 12 * nv)) != cudaSuccess) return fail(ctx, UMGS_ERR_OUT_OF_MEMORY, "vtab");
+    if ((e = ctx->vtab.reserve(sizeof(float) * kVtabStride * nv)) != cudaSuccess)
+        return fail(ctx, UMGS_ERR_OUT_OF_MEMORY, "vtab");
     ctx->vtab_rows = nv;
     if ((e = cudaMemsetAsync(ctx->vacc.ptr, 0, sizeof(float) * 10 * nv, stream)) != cudaSuccess)
         return cuda_fail(ctx, e, "cudaMemsetAsync");
@@ -543,7 +561,7 @@ umgs_status deform_compact_forward(umgs_ctx* ctx, const umgs_gaussians* g, const
     StageTimer tm(ctx, UMGS_STAGE_DEFORM_GAUSSIANS, stream);
     if (g->n > 0)
         deform_gaussians_compact_kernel<<<grid_for(4 * g->n, 256), 256, 0, stream>>>(
-            g->means, g->quats, g->scales, g->cov3d, g->n, count, entries, V, nv, ctx->vtab.as<float>(), mode,
+            g->means, g->quats, g->scales, g->cov3d, g->n, count, entries, nv, ctx->vtab.as<float>(), mode,
             out_means, out_cov, out_quats, ctx->dstatus.as<int32_t>()), count_launch();
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "deform kernels");
@@ -564,15 +582,15 @@ umgs_status deform_compact_forward(umgs_ctx* ctx, const umgs_gaussians* g, const
 // a status word) in the file-scope array below, so it needs no context and
 // never calls cudaMalloc, cudaFree or any allocating library routine.
 //
-// The array holds UMGS_NOALLOC_MAX_PROXY_VERTICES vertices (22 floats each)
-// plus 64 words; every GPU that loads the library keeps it (about 2.9 MB)
+// The array holds UMGS_NOALLOC_MAX_PROXY_VERTICES vertices (26 floats each)
+// plus 64 words; every GPU that loads the library keeps it (about 3.4 MB)
 // until the process exits.  All calls share it: calls whose work overlaps
 // on the GPU (other streams, other host threads) race on it.
 
 namespace umgs {
 
 constexpr int64_t kNoAllocMaxVerts = UMGS_NOALLOC_MAX_PROXY_VERTICES;
-constexpr int64_t kNoAllocFloats = kNoAllocMaxVerts * 22 + 64;
+constexpr int64_t kNoAllocFloats = kNoAllocMaxVerts * (10 + kVtabStride) + 64;
 
 static __device__ __align__(256) float g_noalloc_scratch[kNoAllocFloats];
 
@@ -622,8 +640,8 @@ extern "C" umgs_status umgs_deform_noalloc(const umgs_gaussians* rest, const int
     float* base = nullptr;
     if (noalloc_scratch_address(&base) != cudaSuccess) return UMGS_ERR_CUDA;
     float* vacc = base;                                   // [nv,10]
-    float* vtab = base + 10 * kNoAllocMaxVerts;           // [nv,12]
-    int32_t* status = reinterpret_cast<int32_t*>(base + 22 * kNoAllocMaxVerts);
+    float* vtab = base + 10 * kNoAllocMaxVerts;           // [nv,16]
+    int32_t* status = reinterpret_cast<int32_t*>(base + (10 + kVtabStride) * kNoAllocMaxVerts);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // the accumulators and the status word keep the previous call's values
     noalloc_clear_kernel<<<grid_for(10 * nv, 256), 256, 0, s>>>(vacc, 10 * nv), count_launch();

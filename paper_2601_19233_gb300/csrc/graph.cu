@@ -57,8 +57,7 @@ umgs_status umgs_render_graph_create(umgs_ctx* ctx, umgs_frame* frame, const umg
     const int64_t Kcap = (int64_t)std::ceil((double)K * key_headroom) + 4096;
     const int64_t NR = (frame->ng + frame->nt) * frame->ncams;
     const int64_t M = frame->num_tiles;
-    const int64_t nbmax = std::max({(Kcap + kRsTile - 1) / kRsTile, (NR + kRsTile - 1) / kRsTile,
-                                    (M + kRsTile - 1) / kRsTile, (int64_t)1});
+    const int64_t nbmax = std::max({radix_blocks(Kcap), radix_blocks(NR), radix_blocks(M), (int64_t)1});
     if (reserve_binning(frame, Kcap, Kcap) != cudaSuccess) return fail(ctx, UMGS_ERR_OUT_OF_MEMORY, "pairs");
     if (frame->rs_hist.reserve(sizeof(uint32_t) * 256 * nbmax) != cudaSuccess)
         return fail(ctx, UMGS_ERR_OUT_OF_MEMORY, "histograms");

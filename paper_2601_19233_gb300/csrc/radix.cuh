@@ -15,7 +15,15 @@ namespace umgs {
 
 constexpr int kRsThreads = 256;
 constexpr int kRsItems = 16;
-constexpr int kRsTile = kRsThreads * kRsItems;  // elements per block per pass
+constexpr int kRsTile = kRsThreads * kRsItems;  // elements per block of the scan
+// Radix sorts of up to kRsSmallMax elements (the count that sizes the grid)
+// take 4 elements per thread, longer ones 16.
+constexpr int64_t kRsSmallMax = (int64_t)1 << 24;
+inline int radix_items(int64_t n_cap) { return n_cap <= kRsSmallMax ? 4 : 16; }
+inline int64_t radix_blocks(int64_t n_cap) {
+    const int64_t tile = (int64_t)kRsThreads * radix_items(n_cap);
+    return n_cap > 0 ? (n_cap + tile - 1) / tile : 1;
+}
 
 // ---- exclusive scan of uint32 (sum must fit in uint32) ------------------------
 
@@ -134,21 +142,21 @@ static __global__ void __launch_bounds__(kRsThreads) scan_apply_kernel(const uin
 
 // ---- stable LSD radix sort, 8 bits per pass -----------------------------------
 
+// Radix passes take ITEMS elements per thread (a block sorts 256 x ITEMS):
+// 16 for long inputs, 4 for short ones (more blocks in flight).
+template <int ITEMS>
 static __global__ void __launch_bounds__(kRsThreads) radix_upsweep_kernel(const uint32_t* __restrict__ keys,
                                                                           const uint32_t* __restrict__ n_dev,
                                                                           int64_t n_cap, int shift, int nblocks,
                                                                           uint32_t* __restrict__ hist) {
     __shared__ uint32_t cnt[256];
     const int64_t n = min((int64_t)*n_dev, n_cap);
-    const int64_t base = (int64_t)blockIdx.x * kRsTile;
-    if (base >= n) {  // a block past the live count (capacity-sized grids): empty histogram column
-        hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = 0u;
-        return;
-    }
+    const int64_t base = (int64_t)blockIdx.x * (kRsThreads * ITEMS);
+    if (base >= n) return;  // a block past the live count (capacity-sized grids): its column is not scanned
     cnt[threadIdx.x] = 0;
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < kRsItems; ++k) {
+    for (int k = 0; k < ITEMS; ++k) {
         const int64_t i = base + k * kRsThreads + threadIdx.x;
         if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1u);
     }
@@ -157,13 +165,18 @@ static __global__ void __launch_bounds__(kRsThreads) radix_upsweep_kernel(const 
 }
 
 // Digit-major histogram [256][nblocks] -> per digit, exclusive prefix over
-// the blocks (in place) and the digit total.  One CTA per digit.
+// the live blocks (those holding elements; in place) and the digit total.
+// One CTA per digit.
 static __global__ void __launch_bounds__(kRsThreads) radix_hist_scan_kernel(uint32_t* __restrict__ hist, int nblocks,
+                                                                            const uint32_t* __restrict__ n_dev,
+                                                                            int64_t n_cap, int tile,
                                                                             uint32_t* __restrict__ dtotal) {
     __shared__ uint32_t s_warp[32];
     uint32_t* h = hist + (int64_t)blockIdx.x * nblocks;
-    const int per = (nblocks + kRsThreads - 1) / kRsThreads;
-    const int b = min((int)threadIdx.x * per, nblocks), e = min(b + per, nblocks);
+    const int64_t n = min((int64_t)*n_dev, n_cap);
+    const int live = (int)min((int64_t)nblocks, (n + tile - 1) / tile);
+    const int per = (live + kRsThreads - 1) / kRsThreads;
+    const int b = min((int)threadIdx.x * per, live), e = min(b + per, live);
     uint32_t local = 0;
     for (int k = b; k < e; ++k) local += h[k];
     uint32_t tot;
@@ -172,13 +185,14 @@ static __global__ void __launch_bounds__(kRsThreads) radix_hist_scan_kernel(uint
     if (threadIdx.x == 0) dtotal[blockIdx.x] = tot;
 }
 
-// Each warp owns a contiguous chunk of kRsItems * 32 elements of the block and
+// Each warp owns a contiguous chunk of ITEMS * 32 elements of the block and
 // ranks it round by round (32 consecutive elements per round) against a
 // per-warp digit counter; per-digit scans over the warps and over the digits
 // give every element its position in the block's digit-sorted order.  The
 // block's elements are staged in shared memory in that order and written out
 // as contiguous runs per digit (coalesced).  Input order is preserved for
 // equal digits.
+template <int ITEMS>
 static __global__ void __launch_bounds__(kRsThreads) radix_downsweep_kernel(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, const uint32_t* __restrict__ n_dev,
     int64_t n_cap, int shift, int nblocks, const uint32_t* __restrict__ hist, const uint32_t* __restrict__ dtotal,
@@ -189,15 +203,15 @@ static __global__ void __launch_bounds__(kRsThreads) radix_downsweep_kernel(
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t bstart[256];   // block-local start of each digit
     __shared__ uint32_t gstart[256];   // global start of this block's run of each digit
-    __shared__ uint2 stage[kRsTile];
+    __shared__ uint2 stage[kRsThreads * ITEMS];
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-    const int64_t bbase = (int64_t)blockIdx.x * kRsTile;
+    const int64_t bbase = (int64_t)blockIdx.x * (kRsThreads * ITEMS);
     if (bbase >= n) return;  // nothing of this block is live (uniform over the block)
-    const int64_t base = bbase + (int64_t)w * (32 * kRsItems);
+    const int64_t base = bbase + (int64_t)w * (32 * ITEMS);
     const unsigned lt = (1u << lane) - 1u;
-    uint32_t key[kRsItems], val[kRsItems], rank[kRsItems], dig[kRsItems];
+    uint32_t key[ITEMS], val[ITEMS], rank[ITEMS], dig[ITEMS];
 #pragma unroll
-    for (int k = 0; k < kRsItems; ++k) {
+    for (int k = 0; k < ITEMS; ++k) {
         const int64_t i = base + k * 32 + lane;
         const bool valid = i < n;
         key[k] = valid ? kin[i] : 0u;
@@ -212,7 +226,7 @@ static __global__ void __launch_bounds__(kRsThreads) radix_downsweep_kernel(
     gstart[t] = dbase + hist[(int64_t)t * nblocks + blockIdx.x];
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < kRsItems; ++k) {
+    for (int k = 0; k < ITEMS; ++k) {
         const unsigned peers = __match_any_sync(0xffffffffu, dig[k]);
         const uint32_t lr = __popc(peers & lt);
         const uint32_t before = dig[k] < 256u ? wcnt[w][dig[k]] : 0u;
@@ -231,7 +245,7 @@ static __global__ void __launch_bounds__(kRsThreads) radix_downsweep_kernel(
     bstart[t] = block_exclusive_scan_256(cnt_t, s_warp, btot);
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < kRsItems; ++k)
+    for (int k = 0; k < ITEMS; ++k)
         if (dig[k] < 256u) stage[bstart[dig[k]] + wcnt[w][dig[k]] + rank[k]] = make_uint2(key[k], val[k]);
     __syncthreads();
     for (int i = t; i < (int)btot; i += kRsThreads) {

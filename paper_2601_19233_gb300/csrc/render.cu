@@ -472,6 +472,11 @@ __global__ void __launch_bounds__(256) setup_triangles_kernel(
 //      is the region order, which is the depth order).
 
 constexpr int kRegionTX = 8, kRegionTY = 4;  // tiles per region: one bit each of a 32-bit mask
+// A (region, id) key carries the record's region-local tile rect in its low
+// kRectBits bits (x0, x1: 3 bits each, y0, y1: 2 bits each) and the region
+// index above them; the region sort skips the rect bits.
+constexpr int kRectBits = 10;
+constexpr int64_t kMaxRegions = (int64_t)1 << (32 - kRectBits);
 constexpr int kRegionChunk = 2048;           // region pairs per count/fill block
 constexpr int kRegionThreads = 256;
 
@@ -526,30 +531,29 @@ __global__ void __launch_bounds__(256) region_counts_kernel(const BinInfo* __res
 // so the writes are coalesced and a record with many regions does not hold
 // up its warp.
 // Capacity: when the tile lists would hold more than `kcap` entries (or more
-// than 2^32 - 2), nothing is emitted, the region-pair count *rn is set to 0
-// (so no tile list gets an entry) and the overflow is recorded: status bit 2
-// for the capacity, status[1] = 0xffffffff for the 32-bit limit.  Thread 0
-// also publishes the number of tile-list entries in status[1].
+// than 2^32 - 2), or the pairs more than `rcap`, nothing is emitted, the
+// region-pair count *rn (the sort's count; *rn_scan is the scan's) is set to
+// 0 so that no tile list gets an entry, and the overflow is recorded: status
+// bit 2 for a capacity, status[1] = 0xffffffff for the 32-bit limit.
+// Thread 0 also publishes the number of tile-list entries in status[1].
 __global__ void __launch_bounds__(256) emit_region_pairs_kernel(
     const BinInfo* __restrict__ bin, const uint32_t* __restrict__ pv, const uint32_t* __restrict__ off, int64_t n,
     int64_t ntot, int ts, int regions_x, int regions_per_cam, const unsigned long long* __restrict__ ktotal,
-    int64_t kcap, uint32_t* __restrict__ rk, uint32_t* __restrict__ rv, int64_t rcap, uint32_t* __restrict__ rn,
-    int32_t* __restrict__ status) {
+    int64_t kcap, uint32_t* __restrict__ rk, uint32_t* __restrict__ rv, int64_t rcap,
+    const uint32_t* __restrict__ rn_scan, uint32_t* __restrict__ rn, int32_t* __restrict__ status) {
     const unsigned long long K = *ktotal;
-    const bool over = K > (unsigned long long)kcap || K >= 0xffffffffull;
+    const bool over = K > (unsigned long long)kcap || K >= 0xffffffffull || (int64_t)*rn_scan > rcap;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         status[1] = (int32_t)(uint32_t)(K >= 0xffffffffull ? 0xffffffffull : K);
-        if (over) {
-            if (K > (unsigned long long)kcap) atomicOr(status, 4);
-            *rn = 0u;
-        }
+        if (over && K < 0xffffffffull) atomicOr(status, 4);
+        *rn = over ? 0u : *rn_scan;
     }
     if (over) return;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     if (i - lane >= n) return;  // whole warp past the end
-    const int rts_x = ts * kRegionTX, rts_y = ts * kRegionTY;  // region size in pixels
     int xlo = 0, ylo = 0, w = 1, cnt = 0;
+    int tx0 = 0, tx1 = 0, ty0 = 0, ty1 = 0;  // tile rect
     uint32_t id = 0, rbase = 0;
     int64_t start = 0;
     if (i < n) {
@@ -559,12 +563,12 @@ __global__ void __launch_bounds__(256) emit_region_pairs_kernel(
         if (b.valid) {
             const int cam = (int)(rec / ntot);
             id = (uint32_t)(rec - (int64_t)cam * ntot);
-            xlo = (int)(b.rx & 0xffff) / rts_x;
-            const int xhi = (int)(b.rx >> 16) / rts_x;
-            ylo = (int)(b.ry & 0xffff) / rts_y;
-            const int yhi = (int)(b.ry >> 16) / rts_y;
-            w = xhi - xlo + 1;
-            cnt = w * (yhi - ylo + 1);
+            tx0 = (int)(b.rx & 0xffff) / ts; tx1 = (int)(b.rx >> 16) / ts;
+            ty0 = (int)(b.ry & 0xffff) / ts; ty1 = (int)(b.ry >> 16) / ts;
+            xlo = tx0 / kRegionTX;
+            ylo = ty0 / kRegionTY;
+            w = tx1 / kRegionTX - xlo + 1;
+            cnt = w * (ty1 / kRegionTY - ylo + 1);
             rbase = (uint32_t)cam * (uint32_t)regions_per_cam;
         }
     }
@@ -594,52 +598,94 @@ __global__ void __launch_bounds__(256) emit_region_pairs_kernel(
         const int rw = __shfl_sync(0xffffffffu, w, r);
         const uint32_t rid = __shfl_sync(0xffffffffu, id, r);
         const uint32_t rrb = __shfl_sync(0xffffffffu, rbase, r);
+        const int rtx0 = __shfl_sync(0xffffffffu, tx0, r), rtx1 = __shfl_sync(0xffffffffu, tx1, r);
+        const int rty0 = __shfl_sync(0xffffffffu, ty0, r), rty1 = __shfl_sync(0xffffffffu, ty1, r);
         const int64_t o = base + s;
         if (s < total && o < rcap) {
             const int k = s - re;
             const int gy = ry + k / rw, gx = rx + k % rw;
-            rk[o] = rrb + (uint32_t)(gy * regions_x + gx);
+            // the record's tiles inside region (gx, gy), region-local
+            const int lx0 = max(rtx0 - gx * kRegionTX, 0), lx1 = min(rtx1 - gx * kRegionTX, kRegionTX - 1);
+            const int ly0 = max(rty0 - gy * kRegionTY, 0), ly1 = min(rty1 - gy * kRegionTY, kRegionTY - 1);
+            const uint32_t lrect = (uint32_t)(lx0 | (lx1 << 3) | (ly0 << 6) | (ly1 << 8));
+            rk[o] = ((rrb + (uint32_t)(gy * regions_x + gx)) << kRectBits) | lrect;
             rv[o] = rid;
         }
     }
 }
 
-__device__ __forceinline__ int64_t lower_bound_u32(const uint32_t* __restrict__ a, int64_t n, uint32_t key) {
-    int64_t lo = 0, hi = n;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (a[mid] < key) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
-// Per region r (of R): its first pair in the region-sorted keys, and the
-// number of chunks (count/fill blocks) it needs; rstart[R] = pair count.
-__global__ void region_ranges_kernel(const uint32_t* __restrict__ rk, const uint32_t* __restrict__ rn, int64_t rcap,
-                                     int64_t R, uint32_t* __restrict__ rstart, uint32_t* __restrict__ nchunk) {
-    const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (r > R) return;
+// Region starts from the region-sorted keys: rstart[r] = first pair of region
+// r (regions without pairs get the next region's start), rstart[R] = count.
+// Grid-stride over the pairs: a pair whose region differs from its
+// predecessor's writes the starts of the regions in between.
+__global__ void region_starts_kernel(const uint32_t* __restrict__ rk, const uint32_t* __restrict__ rn, int64_t rcap,
+                                     int64_t R, uint32_t* __restrict__ rstart) {
     const int64_t n = min((int64_t)*rn, rcap);
-    const int64_t s = lower_bound_u32(rk, n, (uint32_t)r);
-    rstart[r] = (uint32_t)s;
-    if (r < R) {
-        const int64_t e = lower_bound_u32(rk, n, (uint32_t)(r + 1));
-        nchunk[r] = (uint32_t)((e - s + kRegionChunk - 1) / kRegionChunk);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (n == 0) {
+        for (int64_t r = i0; r <= R; r += stride) rstart[r] = 0u;
+        return;
+    }
+    for (int64_t i = i0; i < n; i += stride) {
+        const int64_t k = rk[i] >> kRectBits;
+        const int64_t kp = i > 0 ? (int64_t)(rk[i - 1] >> kRectBits) : -1;
+        for (int64_t r = kp + 1; r <= k; ++r) rstart[r] = (uint32_t)i;
+        if (i == n - 1)
+            for (int64_t r = k + 1; r <= R; ++r) rstart[r] = (uint32_t)n;
     }
 }
 
-// Exclusive scan of n (<= kSmallScanMax) uint32 in one block of 1024
-// threads, 1024 elements per round; the total goes to *total.
+// Inputs of the exclusive scans below, one uint32 per index.
+struct ArrayIn {
+    const uint32_t* a;
+    __device__ uint32_t operator()(int64_t i) const { return a[i]; }
+};
+// number of count/fill chunks of region i
+struct ChunksIn {
+    const uint32_t* rstart;
+    __device__ uint32_t operator()(int64_t i) const {
+        return (rstart[i + 1] - rstart[i] + kRegionChunk - 1) / kRegionChunk;
+    }
+};
+// list length of tile t (sum over its region's chunks); also writes, per
+// chunk, the count of the region's earlier chunks for that tile (the
+// chunk's first slot within the tile's list)
+struct TileTotalIn {
+    const uint32_t* coff;
+    const uint32_t* nblk;
+    const uint32_t* ccnt;
+    uint32_t* cpre;
+    int64_t R;
+    int tiles_x, tiles_per_cam, regions_x, regions_per_cam;
+    __device__ uint32_t operator()(int64_t t) const {
+        const int cam = (int)(t / tiles_per_cam);
+        const int lt = (int)(t - (int64_t)cam * tiles_per_cam);
+        const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
+        const int64_t r = (int64_t)cam * regions_per_cam + (ty / kRegionTY) * regions_x + tx / kRegionTX;
+        const int l = (ty % kRegionTY) * kRegionTX + tx % kRegionTX;
+        const uint32_t b0 = coff[r], b1 = r + 1 < R ? coff[r + 1] : *nblk;
+        uint32_t run = 0;
+        for (uint32_t b = b0; b < b1; ++b) {
+            cpre[(int64_t)b * 32 + l] = run;
+            run += ccnt[(int64_t)b * 32 + l];
+        }
+        return run;
+    }
+};
+
+// Exclusive scan of n (<= kSmallScanMax) values in one block of 1024
+// threads, 1024 per round: out[i] for i < n, out[n] = total = *total.
 constexpr int64_t kSmallScanMax = 1 << 15;
-__global__ void __launch_bounds__(1024) scan_small_kernel(const uint32_t* __restrict__ in, int64_t n,
-                                                          uint32_t* __restrict__ out, uint32_t* __restrict__ total) {
+template <class In, class Out>
+__global__ void __launch_bounds__(1024) scan_small_kernel(In in, int64_t n, Out* __restrict__ out,
+                                                          uint32_t* __restrict__ total) {
     __shared__ uint32_t s_warp[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t carry = 0;
     for (int64_t b = 0; b < n; b += 1024) {
         const int64_t i = b + threadIdx.x;
-        const uint32_t x = i < n ? in[i] : 0u;
+        const uint32_t x = i < n ? in(i) : 0u;
         uint32_t inc = x;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -658,11 +704,21 @@ __global__ void __launch_bounds__(1024) scan_small_kernel(const uint32_t* __rest
             s_warp[lane] = v;
         }
         __syncthreads();
-        if (i < n) out[i] = carry + inc - x + (w > 0 ? s_warp[w - 1] : 0u);
+        if (i < n) out[i] = (Out)(carry + inc - x + (w > 0 ? s_warp[w - 1] : 0u));
         carry += s_warp[31];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *total = carry;
+    if (threadIdx.x == 0) {
+        out[n] = (Out)carry;
+        *total = carry;
+    }
+}
+
+// Per-index values of an input functor (for the multi-block paths).
+template <class In>
+__global__ void gather_in_kernel(In in, int64_t n, uint32_t* __restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in(i);
 }
 
 // The region and chunk of count/fill block `blk` (< nblk): the last region
@@ -677,28 +733,25 @@ __device__ __forceinline__ int64_t region_of_chunk(const uint32_t* __restrict__ 
     return lo;
 }
 
-// Tiles of region-local rect: bit (ly * kRegionTX + lx) for every tile of the
-// record's tile rect inside the region whose first tile is (tx0, ty0).
-__device__ __forceinline__ uint32_t region_tile_mask(const BinInfo& b, int ts, int tx0, int ty0) {
-    const int lx0 = max((int)(b.rx & 0xffff) / ts - tx0, 0), lx1 = min((int)(b.rx >> 16) / ts - tx0, kRegionTX - 1);
-    const int ly0 = max((int)(b.ry & 0xffff) / ts - ty0, 0), ly1 = min((int)(b.ry >> 16) / ts - ty0, kRegionTY - 1);
-    if (lx0 > lx1 || ly0 > ly1) return 0u;
+// Region-local tile mask of a (region, id) key: bit (ly * kRegionTX + lx)
+// for every tile of the rect packed in its low kRectBits bits.
+__device__ __forceinline__ uint32_t key_tile_mask(uint32_t key) {
+    const int lx0 = key & 7, lx1 = (key >> 3) & 7, ly0 = (key >> 6) & 3, ly1 = (key >> 8) & 3;
     const uint32_t row = (0xffu >> (kRegionTX - 1 - lx1)) & (0xffu << lx0);
     const uint32_t rows = (0xffffffffu >> (8 * (kRegionTY - 1 - ly1))) & (0xffffffffu << (8 * ly0));
     return (row * 0x01010101u) & rows;
 }
-static_assert(kRegionTX == 8 && kRegionTY == 4, "region_tile_mask packs 8 tiles per byte, 4 rows");
+static_assert(kRegionTX == 8 && kRegionTY == 4, "key_tile_mask packs 8 tiles per byte, 4 rows");
 
 struct RegionChunk {
     int64_t e0, e1;      // pair range of the chunk
-    int64_t rec_base;    // camera * primitives per camera
     int tx0, ty0;        // first tile of the region
     int64_t tile0;       // global index of the region's first tile
 };
 
 __device__ __forceinline__ RegionChunk region_chunk(const uint32_t* __restrict__ coff, const uint32_t* __restrict__ rstart,
                                                     int64_t R, uint32_t blk, int regions_x, int regions_per_cam,
-                                                    int tiles_x, int tiles_per_cam, int64_t ntot) {
+                                                    int tiles_x, int tiles_per_cam) {
     RegionChunk c;
     const int64_t r = region_of_chunk(coff, R, blk);
     const int64_t j = blk - coff[r];
@@ -711,32 +764,47 @@ __device__ __forceinline__ RegionChunk region_chunk(const uint32_t* __restrict__
     c.tx0 = gx * kRegionTX;
     c.ty0 = gy * kRegionTY;
     c.tile0 = (int64_t)cam * tiles_per_cam + (int64_t)c.ty0 * tiles_x + c.tx0;
-    c.rec_base = (int64_t)cam * ntot;
     return c;
 }
 
-// Counting pass: per chunk and tile of its region (lane t of each warp keeps
-// tile t), the number of the chunk's pairs whose record covers the tile.
+constexpr int kRegionItems = kRegionChunk / kRegionThreads;
+
+// 32 x 32 bit-matrix transpose across a warp (recursive 2 x 2 block swaps):
+// on entry lane r holds row r (bit c = element (r, c)); on exit lane c holds
+// column c (bit r).  For tile masks this gives lane t the ballot of tile t.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int j = 16; j >= 1; j >>= 1) {
+        const uint32_t m = j == 16 ? 0x0000ffffu : j == 8 ? 0x00ff00ffu : j == 4 ? 0x0f0f0f0fu : j == 2 ? 0x33333333u
+                                                                                                     : 0x55555555u;
+        const uint32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+        x = (lane & j) ? ((x & ~m) | ((y >> j) & m)) : ((x & m) | ((y << j) & ~m));
+    }
+    return x;
+}
+
+// Counting pass: per chunk and tile of its region, the number of the chunk's
+// pairs whose record covers the tile (lane t of a warp counts tile t from the
+// transposed masks).
 __global__ void __launch_bounds__(kRegionThreads) region_count_kernel(
-    const uint32_t* __restrict__ rv, const BinInfo* __restrict__ bin, const uint32_t* __restrict__ coff,
-    const uint32_t* __restrict__ rstart, const uint32_t* __restrict__ nblk_dev, int64_t R, int ts, int regions_x,
-    int regions_per_cam, int tiles_x, int tiles_per_cam, int64_t ntot, uint32_t* __restrict__ ccnt) {
+    const uint32_t* __restrict__ rk, const uint32_t* __restrict__ coff, const uint32_t* __restrict__ rstart,
+    const uint32_t* __restrict__ nblk_dev, int64_t R, int regions_x, int regions_per_cam, int tiles_x,
+    int tiles_per_cam, uint32_t* __restrict__ ccnt) {
     __shared__ uint32_t s_cnt[kRegionThreads / 32][32];
     if (blockIdx.x >= *nblk_dev) return;
     const RegionChunk c = region_chunk(coff, rstart, R, blockIdx.x, regions_x, regions_per_cam, tiles_x,
-                                       tiles_per_cam, ntot);
+                                       tiles_per_cam);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t mine = 0;
-    for (int64_t b0 = c.e0; b0 < c.e1; b0 += kRegionThreads) {
-        const int64_t e = b0 + threadIdx.x;
-        uint32_t m = 0;
-        if (e < c.e1) m = region_tile_mask(bin[c.rec_base + rv[e]], ts, c.tx0, c.ty0);
+    uint32_t m[kRegionItems];
 #pragma unroll
-        for (int t = 0; t < 32; ++t) {
-            const uint32_t bal = __ballot_sync(0xffffffffu, (m >> t) & 1u);
-            if (lane == t) mine += __popc(bal);
-        }
+    for (int q = 0; q < kRegionItems; ++q) {
+        const int64_t e = c.e0 + q * kRegionThreads + threadIdx.x;
+        m[q] = e < c.e1 ? key_tile_mask(rk[e]) : 0u;
     }
+    uint32_t mine = 0;
+#pragma unroll
+    for (int q = 0; q < kRegionItems; ++q) mine += __popc(warp_transpose32(m[q]));
     s_cnt[warp][lane] = mine;
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -747,89 +815,98 @@ __global__ void __launch_bounds__(kRegionThreads) region_count_kernel(
     }
 }
 
-// Per tile: its list length (sum over its region's chunks) and, per chunk,
-// the count of the region's earlier chunks (the chunk's first slot within
-// the tile's list).
-__global__ void tile_totals_kernel(const uint32_t* __restrict__ coff, const uint32_t* __restrict__ nblk_dev, int64_t R,
-                                   int64_t M, int tiles_x, int tiles_per_cam, int regions_x, int regions_per_cam,
-                                   const uint32_t* __restrict__ ccnt, uint32_t* __restrict__ cpre,
-                                   uint32_t* __restrict__ tcnt) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= M) return;
-    const int cam = (int)(t / tiles_per_cam);
-    const int lt = (int)(t - (int64_t)cam * tiles_per_cam);
-    const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
-    const int64_t r = (int64_t)cam * regions_per_cam + (ty / kRegionTY) * regions_x + tx / kRegionTX;
-    const int l = (ty % kRegionTY) * kRegionTX + tx % kRegionTX;
-    const uint32_t b0 = coff[r], b1 = r + 1 < R ? coff[r + 1] : *nblk_dev;
-    uint32_t run = 0;
-    for (uint32_t b = b0; b < b1; ++b) {
-        cpre[(int64_t)b * 32 + l] = run;
-        run += ccnt[(int64_t)b * 32 + l];
-    }
-    tcnt[t] = run;
-}
-
 // Fill pass: writes each pair's id into the lists of the tiles its record
-// covers.  Rounds of 256 pairs in order; per tile, ballots rank the pairs of
-// a warp and a scan over the warps ranks the warps, so each tile receives the
-// chunk's ids in pair order.
+// covers.  Rounds of 256 pairs in order; per tile, the warp's ballot (its
+// transposed masks) ranks the pairs of a warp and a scan over the warps ranks
+// the warps, so each tile receives the chunk's ids in pair order.  The ids
+// are staged in shared memory, tile by
+// tile (the chunk's tile counts are known from the counting pass), and then
+// written out as contiguous runs; a chunk with more than kFillStage entries
+// writes them directly.  Ballots and warp prefixes alternate between two
+// buffers, so one barrier per round orders their reuse.
+constexpr int kFillStage = 10240;  // staged ids per chunk (40 KB)
 __global__ void __launch_bounds__(kRegionThreads) region_fill_kernel(
-    const uint32_t* __restrict__ rv, const BinInfo* __restrict__ bin, const uint32_t* __restrict__ coff,
-    const uint32_t* __restrict__ rstart, const uint32_t* __restrict__ nblk_dev, int64_t R, int ts, int regions_x,
-    int regions_per_cam, int tiles_x, int tiles_y, int tiles_per_cam, int64_t ntot, const uint32_t* __restrict__ toff,
-    const uint32_t* __restrict__ cpre, uint32_t* __restrict__ ids) {
+    const uint32_t* __restrict__ rk, const uint32_t* __restrict__ rv, const uint32_t* __restrict__ coff,
+    const uint32_t* __restrict__ rstart, const uint32_t* __restrict__ nblk_dev, int64_t R, int regions_x,
+    int regions_per_cam, int tiles_x, int tiles_y, int tiles_per_cam, const int64_t* __restrict__ tile_off,
+    const uint32_t* __restrict__ ccnt, const uint32_t* __restrict__ cpre, uint32_t* __restrict__ ids) {
     constexpr int NW = kRegionThreads / 32;
-    __shared__ uint32_t s_bal[NW][32];
-    __shared__ uint32_t s_pre[NW][32];
-    __shared__ uint32_t s_base[32];
+    __shared__ uint32_t s_bal[2][NW][32];
+    __shared__ uint32_t s_pre[2][NW][32];
+    __shared__ uint32_t s_run[32];    // next slot of each tile (staged or global)
+    __shared__ uint32_t s_cst[33];    // staged start of each tile
+    __shared__ uint32_t s_base[32];   // global first slot of each tile's run
+    __shared__ uint32_t s_stage[kFillStage];
     if (blockIdx.x >= *nblk_dev) return;
     const RegionChunk c = region_chunk(coff, rstart, R, blockIdx.x, regions_x, regions_per_cam, tiles_x,
-                                       tiles_per_cam, ntot);
+                                       tiles_per_cam);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x < 32) {
-        const int lx = threadIdx.x % kRegionTX, ly = threadIdx.x / kRegionTX;
+    if (warp == 0) {
+        const int lx = lane % kRegionTX, ly = lane / kRegionTX;
         const bool exists = c.tx0 + lx < tiles_x && c.ty0 + ly < tiles_y;
-        s_base[threadIdx.x] = exists ? toff[c.tile0 + (int64_t)ly * tiles_x + lx] +
-                                           cpre[(int64_t)blockIdx.x * 32 + threadIdx.x]
-                                     : 0u;
-    }
-    const uint32_t lt_mask = (1u << lane) - 1u;
-    for (int64_t b0 = c.e0; b0 < c.e1; b0 += kRegionThreads) {
-        const int64_t e = b0 + threadIdx.x;
-        uint32_t m = 0, id = 0;
-        if (e < c.e1) {
-            id = rv[e];
-            m = region_tile_mask(bin[c.rec_base + id], ts, c.tx0, c.ty0);
-        }
-        uint32_t mine = 0;
+        const uint32_t cnt = ccnt[(int64_t)blockIdx.x * 32 + lane];
+        s_base[lane] = exists ? (uint32_t)tile_off[c.tile0 + (int64_t)ly * tiles_x + lx] +
+                                    cpre[(int64_t)blockIdx.x * 32 + lane]
+                              : 0u;
+        uint32_t inc = cnt;
 #pragma unroll
-        for (int t = 0; t < 32; ++t) {
-            const uint32_t bal = __ballot_sync(0xffffffffu, (m >> t) & 1u);
-            if (lane == t) mine = bal;
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d) inc += y;
         }
-        s_bal[warp][lane] = mine;
-        __syncthreads();  // (also orders s_base's first write before its use)
+        s_cst[lane] = inc - cnt;
+        if (lane == 31) s_cst[32] = inc;
+    }
+    __syncthreads();
+    const bool staged = s_cst[32] <= (uint32_t)kFillStage;  // block-uniform
+    if (threadIdx.x < 32) s_run[threadIdx.x] = staged ? s_cst[threadIdx.x] : s_base[threadIdx.x];
+    uint32_t id[kRegionItems], m[kRegionItems];
+#pragma unroll
+    for (int q = 0; q < kRegionItems; ++q) {
+        const int64_t e = c.e0 + q * kRegionThreads + threadIdx.x;
+        const bool in = e < c.e1;
+        m[q] = in ? key_tile_mask(rk[e]) : 0u;
+        id[q] = in ? rv[e] : 0u;
+    }
+    uint32_t* const dst = staged ? s_stage : ids;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+#pragma unroll
+    for (int q = 0; q < kRegionItems; ++q) {
+        if (c.e0 + q * kRegionThreads >= c.e1) break;  // block-uniform
+        const int buf = q & 1;
+        s_bal[buf][warp][lane] = warp_transpose32(m[q]);  // lane t: the warp's ballot of tile t
+        __syncthreads();  // (also orders s_run's first write before its use)
         if (threadIdx.x < 32) {
-            uint32_t run = s_base[threadIdx.x];
+            uint32_t run = s_run[threadIdx.x];
 #pragma unroll
             for (int w = 0; w < NW; ++w) {
-                s_pre[w][threadIdx.x] = run;
-                run += __popc(s_bal[w][threadIdx.x]);
+                s_pre[buf][w][threadIdx.x] = run;
+                run += __popc(s_bal[buf][w][threadIdx.x]);
             }
-            s_base[threadIdx.x] = run;
+            s_run[threadIdx.x] = run;
         }
         __syncthreads();
-        while (m) {
-            const int t = __ffs(m) - 1;
-            m &= m - 1u;
-            ids[s_pre[warp][t] + __popc(s_bal[warp][t] & lt_mask)] = id;
+        uint32_t mm = m[q];
+        while (mm) {
+            const int t = __ffs(mm) - 1;
+            mm &= mm - 1u;
+            dst[s_pre[buf][warp][t] + __popc(s_bal[buf][warp][t] & lt_mask)] = id[q];
         }
-        __syncthreads();  // s_bal / s_pre are rewritten by the next round
+    }
+    if (!staged) return;
+    __syncthreads();
+    // staged slot k belongs to the last tile t with s_cst[t] <= k
+    const uint32_t E = s_cst[32];
+    for (uint32_t k = threadIdx.x; k < E; k += kRegionThreads) {
+        int t = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1)
+            if (t + step < 32 && s_cst[t + step] <= k) t += step;
+        ids[s_base[t] + (k - s_cst[t])] = s_stage[k];
     }
 }
 
-// tile_off (int64, M + 1 entries) from the 32-bit tile scan and its total.
+// tile_off (int64, M + 1 entries) from a 32-bit tile scan and its total.
 __global__ void tile_off_kernel(const uint32_t* __restrict__ toff, const uint32_t* __restrict__ total, int64_t M,
                                 int64_t* __restrict__ off) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -868,14 +945,15 @@ cudaError_t scan_u32(umgs_frame* fr, const uint32_t* in, uint32_t* out, int64_t 
     return cudaGetLastError();
 }
 
-// stable LSD radix sort of (k, v) on the low `bits` bits; the element count
-// is read from device memory (n_dev, at most n_cap, which sizes the grids);
-// ping-pongs with (k2, v2) and returns where the result ended
+// stable LSD radix sort of (k, v) on key bits [lo, lo + bits) (the bits above
+// must be zero); the element count is read from device memory (n_dev, at most
+// n_cap, which sizes the grids); ping-pongs with (k2, v2) and returns where
+// the result ended
 cudaError_t radix_sort_pairs(umgs_frame* fr, uint32_t* k, uint32_t* v, uint32_t* k2, uint32_t* v2,
                              const uint32_t* n_dev, int64_t n_cap, int bits, uint32_t** rk, uint32_t** rv,
-                             cudaStream_t s) {
-    const int64_t n = n_cap;
-    const int64_t nb = std::max<int64_t>(1, (n + kRsTile - 1) / kRsTile);
+                             cudaStream_t s, int lo) {
+    const int64_t nb = radix_blocks(n_cap);
+    const int items = radix_items(n_cap);
     const int64_t nh = 256 * nb;
     cudaError_t e = fr->rs_hist.reserve(sizeof(uint32_t) * nh);
     if (e != cudaSuccess) return e;
@@ -883,11 +961,23 @@ cudaError_t radix_sort_pairs(umgs_frame* fr, uint32_t* k, uint32_t* v, uint32_t*
     if (e != cudaSuccess) return e;
     uint32_t* hist = fr->rs_hist.as<uint32_t>();
     uint32_t* dtotal = fr->rs_hist2.as<uint32_t>();
-    for (int shift = 0; shift < bits; shift += 8) {
-        radix_upsweep_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(k, n_dev, n_cap, shift, (int)nb, hist), count_launch();
-        radix_hist_scan_kernel<<<256, kRsThreads, 0, s>>>(hist, (int)nb, dtotal), count_launch();
-        radix_downsweep_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(k, v, n_dev, n_cap, shift, (int)nb, hist, dtotal,
-                                                                   k2, v2), count_launch();
+    for (int shift = lo; shift < lo + bits; shift += 8) {
+        if (items == 4) {
+            radix_upsweep_kernel<4><<<(unsigned)nb, kRsThreads, 0, s>>>(k, n_dev, n_cap, shift, (int)nb, hist),
+                count_launch();
+        } else {
+            radix_upsweep_kernel<16><<<(unsigned)nb, kRsThreads, 0, s>>>(k, n_dev, n_cap, shift, (int)nb, hist),
+                count_launch();
+        }
+        radix_hist_scan_kernel<<<256, kRsThreads, 0, s>>>(hist, (int)nb, n_dev, n_cap, kRsThreads * items, dtotal),
+            count_launch();
+        if (items == 4) {
+            radix_downsweep_kernel<4><<<(unsigned)nb, kRsThreads, 0, s>>>(k, v, n_dev, n_cap, shift, (int)nb, hist,
+                                                                          dtotal, k2, v2), count_launch();
+        } else {
+            radix_downsweep_kernel<16><<<(unsigned)nb, kRsThreads, 0, s>>>(k, v, n_dev, n_cap, shift, (int)nb, hist,
+                                                                           dtotal, k2, v2), count_launch();
+        }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         uint32_t* t = k; k = k2; k2 = t;
@@ -916,7 +1006,7 @@ cudaError_t reserve_binning(umgs_frame* fr, int64_t rcap, int64_t kcap) {
     if ((e = fr->tl_ids.reserve(sizeof(uint32_t) * std::max<int64_t>(1, kcap))) != cudaSuccess) return e;
     if ((e = fr->rg_start.reserve(sizeof(uint32_t) * (R + 1))) != cudaSuccess) return e;
     if ((e = fr->rg_nchunk.reserve(sizeof(uint32_t) * R)) != cudaSuccess) return e;
-    if ((e = fr->rg_coff.reserve(sizeof(uint32_t) * R)) != cudaSuccess) return e;
+    if ((e = fr->rg_coff.reserve(sizeof(uint32_t) * (R + 1))) != cudaSuccess) return e;
     if ((e = fr->rg_ccnt.reserve(sizeof(uint32_t) * 32 * nblk_max)) != cudaSuccess) return e;
     if ((e = fr->rg_cpre.reserve(sizeof(uint32_t) * 32 * nblk_max)) != cudaSuccess) return e;
     if ((e = fr->tl_cnt.reserve(sizeof(uint32_t) * std::max<int64_t>(1, M))) != cudaSuccess) return e;
@@ -969,8 +1059,9 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     // conic list length, [4] tile count for the tile-order sort, [5] record
     // count for the depth sort, [6..7] evaluation count (u64), [8] persistent
     // work counter, [9] scan overflow, [10..11] tile-list entries (u64),
-    // [12] (region, id) pairs, [13] count/fill chunks, [14] tile-list entries
-    // from the tile scan
+    // [12] (region, id) pairs sorted (0 after an overflow), [13] count/fill
+    // chunks, [14] tile-list entries from the tile scan, [15] (region, id)
+    // pairs counted
     UMGS_TRY(fr->status.reserve(sizeof(int32_t) * 16));
 
     // cameras: host -> pinned staging -> device
@@ -1044,6 +1135,7 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     const int regions_x = (tiles_x + kRegionTX - 1) / kRegionTX;
     const int regions_per_cam = regions_x * ((tiles_y + kRegionTY - 1) / kRegionTY);
     const int64_t R = (int64_t)regions_per_cam * ncams;
+    if (R > kMaxRegions) return fail(ctx, UMGS_ERR_INVALID_ARG, "too many tile regions (cameras x regions > 2^22)");
     UMGS_TRY(fr->pk.reserve(sizeof(uint32_t) * std::max<int64_t>(1, NR)));
     UMGS_TRY(fr->pv.reserve(sizeof(uint32_t) * std::max<int64_t>(1, NR)));
     UMGS_TRY(fr->pk2.reserve(sizeof(uint32_t) * std::max<int64_t>(1, NR)));
@@ -1054,7 +1146,8 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     uint32_t* pv = fr->pv.as<uint32_t>();
     uint32_t* status_u = reinterpret_cast<uint32_t*>(fr->status.as<int32_t>());
     unsigned long long* ktotal = reinterpret_cast<unsigned long long*>(status_u + 10);
-    uint32_t* rn = status_u + 12;    // number of (region, id) pairs
+    uint32_t* rn = status_u + 12;    // number of (region, id) pairs sorted
+    uint32_t* rn_scan = status_u + 15;  // number of (region, id) pairs counted
     uint32_t* nblk = status_u + 13;  // number of count/fill chunks
     uint32_t* ktot32 = status_u + 14;
     if (NR > 0) {
@@ -1070,7 +1163,7 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
         region_counts_kernel<<<grid_for(NR, 256), 256, 0, stream>>>(fr->bin.as<BinInfo>(), pv, NR, ts,
                                                                     fr->pcnt.as<uint32_t>(), ktotal), count_launch();
         UMGS_TRY(cudaGetLastError());
-        UMGS_TRY(scan_u32(fr, fr->pcnt.as<uint32_t>(), fr->poff.as<uint32_t>(), NR, rn, stream));
+        UMGS_TRY(scan_u32(fr, fr->pcnt.as<uint32_t>(), fr->poff.as<uint32_t>(), NR, rn_scan, stream));
     }
     int64_t Kcap, rcap;
     if (!fr->nosync) {
@@ -1083,7 +1176,7 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
         if (K64 >= 0xffffffffull) return fail(ctx, UMGS_ERR_CAPACITY, "more than 4294967294 (tile, primitive) pairs");
         fr->num_keys = (int64_t)K64;
         Kcap = (int64_t)K64;
-        rcap = NR > 0 ? (int64_t)w[12] : 0;
+        rcap = NR > 0 ? (int64_t)w[15] : 0;
     } else {
         // no host read-back: the lists are held to the reserved capacity and
         // an overflow is flagged in the status word (bit 2); inside a capture
@@ -1098,7 +1191,8 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
         StageTimer tm(ctx, UMGS_STAGE_SCATTER, stream);
         emit_region_pairs_kernel<<<grid_for(NR, 256), 256, 0, stream>>>(
             fr->bin.as<BinInfo>(), pv, fr->poff.as<uint32_t>(), NR, Ntot, ts, regions_x, regions_per_cam, ktotal,
-            Kcap, fr->tk.as<uint32_t>(), fr->tv.as<uint32_t>(), rcap, rn, fr->status.as<int32_t>()), count_launch();
+            Kcap, fr->tk.as<uint32_t>(), fr->tv.as<uint32_t>(), rcap, rn_scan, rn, fr->status.as<int32_t>()),
+            count_launch();
         UMGS_TRY(cudaGetLastError());
     }
     {
@@ -1109,43 +1203,45 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
             int bits = 1;
             while (((int64_t)1 << bits) < R) ++bits;
             UMGS_TRY(radix_sort_pairs(fr, fr->tk.as<uint32_t>(), fr->tv.as<uint32_t>(), fr->tk2.as<uint32_t>(),
-                                      fr->tv2.as<uint32_t>(), rn, rcap, bits, &rk, &rv, stream));
+                                      fr->tv2.as<uint32_t>(), rn, rcap, bits, &rk, &rv, stream, kRectBits));
         }
         const int64_t nblk_max = (rcap + kRegionChunk - 1) / kRegionChunk + R;
         uint32_t* rstart = fr->rg_start.as<uint32_t>();
         uint32_t* coff = fr->rg_coff.as<uint32_t>();
-        region_ranges_kernel<<<grid_for(R + 1, 256), 256, 0, stream>>>(rk, rn, rcap, R, rstart,
-                                                                       fr->rg_nchunk.as<uint32_t>()), count_launch();
+        int64_t* toff64 = fr->tile_off.as<int64_t>();
+        const unsigned sgrid = (unsigned)std::min<int64_t>(grid_for(std::max(rcap, R + 1), 256), 8 * ctx->num_sms);
+        region_starts_kernel<<<sgrid, 256, 0, stream>>>(rk, rn, rcap, R, rstart), count_launch();
         UMGS_TRY(cudaGetLastError());
         if (R <= kSmallScanMax) {
-            scan_small_kernel<<<1, 1024, 0, stream>>>(fr->rg_nchunk.as<uint32_t>(), R, coff, nblk), count_launch();
-            UMGS_TRY(cudaGetLastError());
+            scan_small_kernel<ChunksIn, uint32_t><<<1, 1024, 0, stream>>>(ChunksIn{rstart}, R, coff, nblk), count_launch();
         } else {
+            gather_in_kernel<ChunksIn><<<grid_for(R, 256), 256, 0, stream>>>(ChunksIn{rstart}, R,
+                                                                             fr->rg_nchunk.as<uint32_t>()), count_launch();
             UMGS_TRY(scan_u32(fr, fr->rg_nchunk.as<uint32_t>(), coff, R, nblk, stream));
         }
-        region_count_kernel<<<(unsigned)nblk_max, kRegionThreads, 0, stream>>>(
-            rv, fr->bin.as<BinInfo>(), coff, rstart, nblk, R, ts, regions_x, regions_per_cam, tiles_x, tiles_per_cam,
-            Ntot, fr->rg_ccnt.as<uint32_t>()), count_launch();
         UMGS_TRY(cudaGetLastError());
-        tile_totals_kernel<<<grid_for(M, 256), 256, 0, stream>>>(coff, nblk, R, M, tiles_x, tiles_per_cam, regions_x,
-                                                                 regions_per_cam, fr->rg_ccnt.as<uint32_t>(),
-                                                                 fr->rg_cpre.as<uint32_t>(), fr->tl_cnt.as<uint32_t>()),
+        region_count_kernel<<<(unsigned)nblk_max, kRegionThreads, 0, stream>>>(
+            rk, coff, rstart, nblk, R, regions_x, regions_per_cam, tiles_x, tiles_per_cam, fr->rg_ccnt.as<uint32_t>()),
+            count_launch();
+        UMGS_TRY(cudaGetLastError());
+        const TileTotalIn tin{coff, nblk, fr->rg_ccnt.as<uint32_t>(), fr->rg_cpre.as<uint32_t>(), R, tiles_x,
+                              tiles_per_cam, regions_x, regions_per_cam};
+        gather_in_kernel<TileTotalIn><<<grid_for(M, 256), 256, 0, stream>>>(tin, M, fr->tl_cnt.as<uint32_t>()),
             count_launch();
         UMGS_TRY(cudaGetLastError());
         if (M <= kSmallScanMax) {
-            scan_small_kernel<<<1, 1024, 0, stream>>>(fr->tl_cnt.as<uint32_t>(), M, fr->tl_off.as<uint32_t>(), ktot32),
-                count_launch();
-            UMGS_TRY(cudaGetLastError());
+            scan_small_kernel<ArrayIn, int64_t><<<1, 1024, 0, stream>>>(ArrayIn{fr->tl_cnt.as<uint32_t>()}, M, toff64,
+                                                                        ktot32), count_launch();
         } else {
             UMGS_TRY(scan_u32(fr, fr->tl_cnt.as<uint32_t>(), fr->tl_off.as<uint32_t>(), M, ktot32, stream));
+            tile_off_kernel<<<grid_for(M + 1, 256), 256, 0, stream>>>(fr->tl_off.as<uint32_t>(), ktot32, M, toff64),
+                count_launch();
         }
-        region_fill_kernel<<<(unsigned)nblk_max, kRegionThreads, 0, stream>>>(
-            rv, fr->bin.as<BinInfo>(), coff, rstart, nblk, R, ts, regions_x, regions_per_cam, tiles_x, tiles_y,
-            tiles_per_cam, Ntot, fr->tl_off.as<uint32_t>(), fr->rg_cpre.as<uint32_t>(), fr->tl_ids.as<uint32_t>()),
-            count_launch();
         UMGS_TRY(cudaGetLastError());
-        tile_off_kernel<<<grid_for(M + 1, 256), 256, 0, stream>>>(fr->tl_off.as<uint32_t>(), ktot32, M,
-                                                                  fr->tile_off.as<int64_t>()), count_launch();
+        region_fill_kernel<<<(unsigned)nblk_max, kRegionThreads, 0, stream>>>(
+            rk, rv, coff, rstart, nblk, R, regions_x, regions_per_cam, tiles_x, tiles_y, tiles_per_cam, toff64,
+            fr->rg_ccnt.as<uint32_t>(), fr->rg_cpre.as<uint32_t>(), fr->tl_ids.as<uint32_t>()),
+            count_launch();
         UMGS_TRY(cudaGetLastError());
     }
     UMGS_TRY(fr->last.reserve(sizeof(int32_t) * (int64_t)ncams * W * H));

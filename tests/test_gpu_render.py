@@ -227,3 +227,50 @@ def test_primitive_count_limits_rejected(ctx):
     st = umgs.lib().umgs_render(ctx._h, ctypes.byref(cg), None, 0, cams, 1, ctypes.byref(opts),
                                 umgs._ptr(out), None, None)
     assert st == 1
+
+
+def test_region_count_limit_rejected(ctx):
+    # 9 views of 32768 x 32768 with 8-pixel tiles: 9 x 512 x 1024 regions of
+    # 8 x 4 tiles, more than the 2^22 that (region, id) keys can name; the
+    # call fails before launching or allocating anything
+    from paper_2601_19233_gb300 import umgs
+    sc = S.config0()
+    g = umgs.gaussians_to_device(sc.gaussians)
+    big = H.cam(32768, 32768, fx=16384.0)
+    out = torch.empty((1, 4), device="cuda")
+    cams = (umgs.CCamera * 9)(*[umgs.camera_struct(big)] * 9)
+    opts = umgs.render_opts(8)
+    n0 = umgs.kernel_launches()
+    st = umgs.lib().umgs_render(ctx._h, ctypes.byref(g.c()), None, 0, cams, 9, ctypes.byref(opts),
+                                umgs._ptr(out), None, None)
+    assert st == 1 and b"regions" in umgs.lib().umgs_last_error(ctx._h)
+    assert umgs.kernel_launches() == n0
+
+
+def test_wide_records_fill_unstaged(ctx):
+    # 2,200 wide Gaussians (3 sigma = 36 px) over a 128 x 32 image with 8-pixel
+    # tiles (two regions of 8 x 4 tiles): each pair of a region covers most of
+    # its 32 tiles, so a chunk of 2,048 (region, id) pairs carries ~60k list
+    # entries, more than the fill stages in shared memory, and writes them
+    # directly; lists bit-exact, image against the oracle
+    c0 = H.cam(128, 32, fx=100.0)
+    rng = np.random.default_rng(21)
+    n = 2200
+    Z = 3.0
+    u = rng.uniform(28.0, 100.0, n)
+    v = rng.uniform(12.0, 20.0, n)
+    means = np.stack([(u - c0.cx) * Z / c0.fx, (v - c0.cy) * Z / c0.fy, rng.uniform(-0.3, 0.3, n)], 1)
+    scales = np.full((n, 3), 12.0 * Z / c0.fx, np.float32)
+    g = H.gaussians(means, scales=scales, opac=np.full(n, 0.05, np.float32),
+                    colors=rng.uniform(0.1, 0.9, (n, 3)))
+    sc = H.scene(g, [], c0, tile=8)
+    # no early termination (hundreds of fragments per pixel would put many
+    # pixels next to the t_eps threshold)
+    out, fr = gpu_render(ctx, sc, tile=8, t_eps=-1.0)
+    k = check_lists(sc, fr, 8)
+    assert k > 2048 * 20
+    ref = R.render_image(sc, 0, t_eps=None)
+    ok = ~ref["tie"]  # (~2,000 fragments per pixel: 9% of the pixels hold an alpha within 1e-6 of 1/255)
+    assert ok.mean() > 0.85
+    assert np.abs(out[0, ..., :3] - ref["rgb"])[ok].max() <= TOL
+    assert np.abs(out[0, ..., 3] - ref["T"])[ok].max() <= TOL
