@@ -270,21 +270,21 @@ __device__ void exp_rot(const float r[3], float R[9], float q[4]) {
 
 // Eq. 13 for one Gaussian from acc = scale^-1 x the means of its bound
 // points' Eq. 12 interpolants (Delta, log R, S (6), rest position P) and
-// bad (an index was out of range), held by every lane of the Gaussian:
-// lanes corner 0, 1, 2 write mu', Sigma', q' (NaN and a status bit if bad).
-__device__ __forceinline__ void deform_finish(const float (&acc)[15], float scale, int bad, bool live, int corner,
+// bad (an index was out of range): writes the outputs selected by `which`
+// (bit 0: mu', bit 1: Sigma', bit 2: q'; NaN and a status bit if bad).
+__device__ __forceinline__ void deform_finish(const float (&acc)[15], float scale, int bad, bool live, int which,
                                               int64_t i, const float* __restrict__ means,
                                               const float* __restrict__ quats, const float* __restrict__ scales,
                                               const float* __restrict__ cov3d, int mode, float* __restrict__ out_means,
                                               float* __restrict__ out_cov, float* __restrict__ out_quats,
                                               int32_t* __restrict__ status) {
-    if (!live || corner > 2) return;
+    if (!live || which == 0) return;
     if (bad) {
-        if (corner == 0) atomicOr(status, kStatusBadIndex);
+        if (which & 1) atomicOr(status, kStatusBadIndex);
         const float nanv = __int_as_float(0x7fc00000);
-        if (corner == 0) for (int d = 0; d < 3; ++d) out_means[3 * i + d] = nanv;
-        if (corner == 1) for (int d = 0; d < 6; ++d) out_cov[6 * i + d] = nanv;
-        if (corner == 2 && out_quats) for (int d = 0; d < 4; ++d) out_quats[4 * i + d] = nanv;
+        if (which & 1) for (int d = 0; d < 3; ++d) out_means[3 * i + d] = nanv;
+        if (which & 2) for (int d = 0; d < 6; ++d) out_cov[6 * i + d] = nanv;
+        if ((which & 4) && out_quats) for (int d = 0; d < 4; ++d) out_quats[4 * i + d] = nanv;
         return;
     }
     const float e = scale;
@@ -295,7 +295,7 @@ __device__ __forceinline__ void deform_finish(const float (&acc)[15], float scal
                          acc[8] * e, acc[10] * e, acc[11] * e};
     float A[9];
     matmul3(Rp, Sb, A);
-    if (corner == 0) {
+    if (which & 1) {
         const float mu[3] = {means[3 * i], means[3 * i + 1], means[3 * i + 2]};
         float mo[3];
         for (int d = 0; d < 3; ++d) mo[d] = mu[d] + acc[d] * e;
@@ -304,8 +304,8 @@ __device__ __forceinline__ void deform_finish(const float (&acc)[15], float scal
             for (int d = 0; d < 3; ++d) mo[d] += A[3 * d] * rel[0] + A[3 * d + 1] * rel[1] + A[3 * d + 2] * rel[2] - rel[d];
         }
         for (int d = 0; d < 3; ++d) out_means[3 * i + d] = mo[d];
-        return;
     }
+    if ((which & 6) == 0) return;
     float qn[4] = {1.f, 0.f, 0.f, 0.f};
     float S[9];
     if (cov3d) {
@@ -317,7 +317,7 @@ __device__ __forceinline__ void deform_finish(const float (&acc)[15], float scal
         const float nq = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
         if (nq > 0.f) { qw /= nq; qx /= nq; qy /= nq; qz /= nq; } else { qw = 1.f; qx = qy = qz = 0.f; }
         qn[0] = qw; qn[1] = qx; qn[2] = qy; qn[3] = qz;
-        if (corner == 1) {
+        if (which & 2) {
             const float r[9] = {1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
                                 2.f * (qx * qy + qw * qz), 1.f - 2.f * (qx * qx + qz * qz), 2.f * (qy * qz - qw * qx),
                                 2.f * (qx * qz - qw * qy), 2.f * (qy * qz + qw * qx), 1.f - 2.f * (qx * qx + qy * qy)};
@@ -330,7 +330,7 @@ __device__ __forceinline__ void deform_finish(const float (&acc)[15], float scal
                     S[3 * a + bb] = M[3 * a] * M[3 * bb] + M[3 * a + 1] * M[3 * bb + 1] + M[3 * a + 2] * M[3 * bb + 2];
         }
     }
-    if (corner == 1) {
+    if (which & 2) {
         float AS[9], Sig[9];
         matmul3(A, S, AS);
         for (int a = 0; a < 3; ++a)
@@ -338,9 +338,8 @@ __device__ __forceinline__ void deform_finish(const float (&acc)[15], float scal
                 Sig[3 * a + bb] = AS[3 * a] * A[3 * bb] + AS[3 * a + 1] * A[3 * bb + 1] + AS[3 * a + 2] * A[3 * bb + 2];
         float* oc = out_cov + 6 * i;
         oc[0] = Sig[0]; oc[1] = Sig[1]; oc[2] = Sig[2]; oc[3] = Sig[4]; oc[4] = Sig[5]; oc[5] = Sig[8];
-        return;
     }
-    if (out_quats) {
+    if ((which & 4) && out_quats) {
         // q' = qr * qn (Hamilton product), canonical sign w >= 0
         float o[4];
         o[0] = qr[0] * qn[0] - qr[1] * qn[1] - qr[2] * qn[2] - qr[3] * qn[3];
@@ -400,7 +399,7 @@ __global__ void __launch_bounds__(256) deform_gaussians_kernel(
         for (int e = 0; e < 15; ++e) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
         bad |= __shfl_xor_sync(0xffffffffu, bad, o);
     }
-    deform_finish(acc, 0.125f, bad, live, corner, i, means, quats, scales, cov3d, mode, out_means, out_cov,
+    deform_finish(acc, 0.125f, bad, live, corner < 3 ? 1 << corner : 0, i, means, quats, scales, cov3d, mode, out_means, out_cov,
                   out_quats, status);
 }
 
@@ -439,65 +438,74 @@ __global__ void __launch_bounds__(256) binding_compact_kernel(const int32_t* __r
     count[i] = c;
 }
 
-// Deformation over a compact binding: four lanes per Gaussian walk its
-// entries together; for each entry lane p gathers float4 p of the vertex's
-// 64-byte table row and accumulates those four of the 15 interpolated
-// components (so one warp-wide row load touches 8 rows of 64 contiguous
-// bytes instead of 32 scattered ones).  Entries are read two at a time
-// (16-byte loads) and four are in flight per step.  A shuffle round gives
-// every lane all 15 sums, and lanes 0-2 finish as above.
-__global__ void __launch_bounds__(256) deform_gaussians_compact_kernel(
+// Deformation over a compact binding.  A block of 256 threads takes 256
+// Gaussians.  Gather phase, 4 rounds of 64 Gaussians: the four lanes of a
+// Gaussian walk its entries together; for each entry lane p gathers float4 p
+// of the vertex's 64-byte table row and accumulates those four of the 15
+// interpolated components (one warp-wide row load touches 8 rows of 64
+// contiguous bytes).  Entries are read two at a time (16-byte loads), four in
+// flight per step.  The sums go to shared memory; then every thread finishes
+// one Gaussian (Eq. 13 and all three outputs), so that math runs with every
+// lane busy.
+constexpr int kDefBlock = 256;
+__global__ void __launch_bounds__(kDefBlock) deform_gaussians_compact_kernel(
     const float* __restrict__ means, const float* __restrict__ quats, const float* __restrict__ scales,
     const float* __restrict__ cov3d, int64_t n, const int32_t* __restrict__ count, const int2* __restrict__ entries,
     int64_t nv, const float* __restrict__ vtab, int mode, float* __restrict__ out_means,
     float* __restrict__ out_cov, float* __restrict__ out_quats, int32_t* __restrict__ status) {
-    const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t i = tid >> 2;
-    const int part = (int)(tid & 3);
-    const bool live = i < n;
-    float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-    int bad = 0;
-    int c = 0;
-    if (live) {
-        c = count[i];
-        if (c < 0 || c > 24) { bad = 1; c = 0; }
-    }
-    const int4* row = reinterpret_cast<const int4*>(entries + 24 * i);  // two entries per int4
+    __shared__ float s_acc[kDefBlock][17];  // odd row length: conflict-free row reads
+    __shared__ int s_bad[kDefBlock];
+    const int t = threadIdx.x;
+    const int part = t & 3;
+    const int64_t g0 = (int64_t)blockIdx.x * kDefBlock;
     const float4* tab = reinterpret_cast<const float4*>(vtab);
-    for (int j = 0; j < c; j += 4) {
-        const int4 e01 = row[j >> 1];
-        const int4 e23 = j + 2 < c ? row[(j >> 1) + 1] : make_int4(0, 0, 0, 0);
-        const int vv[4] = {e01.x, e01.z, e23.x, e23.z};
-        const int ww[4] = {e01.y, e01.w, e23.y, e23.w};
-        float4 t[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const bool use = j + q < c;
-            const int v = vv[q];
-            if (use && (v < 0 || v >= nv)) bad = 1;
-            t[q] = (use && v >= 0 && v < nv) ? tab[4 * (int64_t)v + part] : make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int r = 0; r < kDefBlock / 64; ++r) {
+        const int local = r * 64 + (t >> 2);
+        const int64_t i = g0 + local;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+        int bad = 0;
+        int c = 0;
+        if (i < n) {
+            c = count[i];
+            if (c < 0 || c > 24) { bad = 1; c = 0; }
         }
+        const int4* row = reinterpret_cast<const int4*>(entries + 24 * i);  // two entries per int4
+        for (int j = 0; j < c; j += 4) {
+            const int4 e01 = row[j >> 1];
+            const int4 e23 = j + 2 < c ? row[(j >> 1) + 1] : make_int4(0, 0, 0, 0);
+            const int vv[4] = {e01.x, e01.z, e23.x, e23.z};
+            const int ww[4] = {e01.y, e01.w, e23.y, e23.w};
+            float4 tq[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float wk = j + q < c ? __int_as_float(ww[q]) : 0.f;
-            a.x += wk * t[q].x; a.y += wk * t[q].y; a.z += wk * t[q].z; a.w += wk * t[q].w;
+            for (int q = 0; q < 4; ++q) {
+                const bool use = j + q < c;
+                const int v = vv[q];
+                if (use && (v < 0 || v >= nv)) bad = 1;
+                tq[q] = (use && v >= 0 && v < nv) ? tab[4 * (int64_t)v + part] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float wk = j + q < c ? __int_as_float(ww[q]) : 0.f;
+                a.x += wk * tq[q].x; a.y += wk * tq[q].y; a.z += wk * tq[q].z; a.w += wk * tq[q].w;
+            }
         }
+        // lane p of the Gaussian holds components 4p .. 4p+3 (the 16th is padding)
+        s_acc[local][4 * part] = a.x;
+        s_acc[local][4 * part + 1] = a.y;
+        s_acc[local][4 * part + 2] = a.z;
+        s_acc[local][4 * part + 3] = a.w;
+        bad |= __shfl_xor_sync(0xffffffffu, bad, 1);
+        bad |= __shfl_xor_sync(0xffffffffu, bad, 2);
+        if (part == 0) s_bad[local] = bad;
     }
-    // lane q of the group holds components 4q .. 4q+3 (the 16th is padding)
-    const int g0 = (threadIdx.x & 31) & ~3;
+    __syncthreads();
+    const int64_t i = g0 + t;
+    if (i >= n) return;
     float acc[15];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const float x = __shfl_sync(0xffffffffu, a.x, g0 + q);
-        const float y = __shfl_sync(0xffffffffu, a.y, g0 + q);
-        const float z = __shfl_sync(0xffffffffu, a.z, g0 + q);
-        const float w = __shfl_sync(0xffffffffu, a.w, g0 + q);
-        acc[4 * q] = x; acc[4 * q + 1] = y; acc[4 * q + 2] = z;
-        if (q < 3) acc[4 * q + 3] = w;
-    }
-#pragma unroll
-    for (int o = 2; o > 0; o >>= 1) bad |= __shfl_xor_sync(0xffffffffu, bad, o);
-    deform_finish(acc, 1.f, bad, live, part, i, means, quats, scales, cov3d, mode, out_means, out_cov, out_quats,
+    for (int e = 0; e < 15; ++e) acc[e] = s_acc[t][e];
+    deform_finish(acc, 1.f, s_bad[t], true, 7, i, means, quats, scales, cov3d, mode, out_means, out_cov, out_quats,
                   status);
 }
 
@@ -560,7 +568,7 @@ umgs_status deform_compact_forward(umgs_ctx* ctx, const umgs_gaussians* g, const
     if (st != UMGS_OK) return st;
     StageTimer tm(ctx, UMGS_STAGE_DEFORM_GAUSSIANS, stream);
     if (g->n > 0)
-        deform_gaussians_compact_kernel<<<grid_for(4 * g->n, 256), 256, 0, stream>>>(
+        deform_gaussians_compact_kernel<<<grid_for(g->n, kDefBlock), kDefBlock, 0, stream>>>(
             g->means, g->quats, g->scales, g->cov3d, g->n, count, entries, nv, ctx->vtab.as<float>(), mode,
             out_means, out_cov, out_quats, ctx->dstatus.as<int32_t>()), count_launch();
     const cudaError_t e = cudaGetLastError();

@@ -962,8 +962,8 @@ cudaError_t radix_sort_pairs(umgs_frame* fr, uint32_t* k, uint32_t* v, uint32_t*
     uint32_t* hist = fr->rs_hist.as<uint32_t>();
     uint32_t* dtotal = fr->rs_hist2.as<uint32_t>();
     for (int shift = lo; shift < lo + bits; shift += 8) {
-        if (items == 4) {
-            radix_upsweep_kernel<4><<<(unsigned)nb, kRsThreads, 0, s>>>(k, n_dev, n_cap, shift, (int)nb, hist),
+        if (items == 8) {
+            radix_upsweep_kernel<8><<<(unsigned)nb, kRsThreads, 0, s>>>(k, n_dev, n_cap, shift, (int)nb, hist),
                 count_launch();
         } else {
             radix_upsweep_kernel<16><<<(unsigned)nb, kRsThreads, 0, s>>>(k, n_dev, n_cap, shift, (int)nb, hist),
@@ -971,8 +971,8 @@ cudaError_t radix_sort_pairs(umgs_frame* fr, uint32_t* k, uint32_t* v, uint32_t*
         }
         radix_hist_scan_kernel<<<256, kRsThreads, 0, s>>>(hist, (int)nb, n_dev, n_cap, kRsThreads * items, dtotal),
             count_launch();
-        if (items == 4) {
-            radix_downsweep_kernel<4><<<(unsigned)nb, kRsThreads, 0, s>>>(k, v, n_dev, n_cap, shift, (int)nb, hist,
+        if (items == 8) {
+            radix_downsweep_kernel<8><<<(unsigned)nb, kRsThreads, 0, s>>>(k, v, n_dev, n_cap, shift, (int)nb, hist,
                                                                           dtotal, k2, v2), count_launch();
         } else {
             radix_downsweep_kernel<16><<<(unsigned)nb, kRsThreads, 0, s>>>(k, v, n_dev, n_cap, shift, (int)nb, hist,
