@@ -99,9 +99,15 @@ enum {
     UMGS_RENDER_T_PRODUCT = 4,      /* FULL mode only: inside an entity T <- T (1 - O_i alpha_i), the
                                        literal reading of Sec. 3.2's Eq. 6 instead of T = T_in mean_j t^j
                                        (the two agree for one-triangle entities); no backward. */
-    UMGS_RENDER_ASYNC = 8           /* no host read-back inside umgs_render: the (tile, primitive) pairs
+    UMGS_RENDER_ASYNC = 8,          /* no host read-back inside umgs_render: the (tile, primitive) pairs
                                        are held to the frame's reserved capacity (umgs_frame_reserve);
                                        check the result with umgs_frame_check */
+    UMGS_RENDER_DEPTH = 16          /* FULL mode only, needs a frame: also keep each pixel's expected
+                                       depth sum_i w_i z_i / sum_i w_i over its blended fragments (w_i
+                                       the blend weight of Eq. 2 or Eq. 9, z_i the camera depth of a
+                                       Gaussian's mean or a triangle's perspective-correct depth at the
+                                       pixel centre; +inf where nothing blends), for umgs_frame_depth;
+                                       not with SAVE_BACKWARD, MIXED or T_PRODUCT. */
 };
 
 typedef struct {
@@ -203,6 +209,24 @@ umgs_status umgs_frame_counts(const umgs_frame* frame, int64_t* num_keys, int64_
  * footprints change little between calls.  Errors: INVALID_ARG
  * (key_capacity < 1). */
 umgs_status umgs_frame_reserve(umgs_frame* frame, int64_t key_capacity);
+
+/* Expected depth of every pixel of the last render into `frame` made with
+ * UMGS_RENDER_DEPTH (see the flag): out_depth [ncams,H,W] float device
+ * (caller-owned); asynchronous on `stream`.  Errors: INVALID_ARG (no such
+ * render), CUDA. */
+umgs_status umgs_frame_depth(const umgs_frame* frame, float* out_depth, void* stream);
+
+/* Separate-pass baseline (the scheme Sec. 4.1 and Fig. 5b compare against;
+ * not a step of the method): two layers rendered apart, each with a zero
+ * background and UMGS_RENDER_DEPTH, composited per pixel in the order of
+ * their expected depths (the nearer layer over the farther, layer a first
+ * on equal depths), then the background bg:
+ *   C = C_f + T_f C_b + T_f T_b bg,  T = T_f T_b.
+ * a_rgbt, b_rgbt, out_rgbt [npix,4] and a_depth, b_depth [npix] float device;
+ * bg host float[3].  Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA. */
+umgs_status umgs_composite_layers(umgs_ctx* ctx, const float* a_rgbt, const float* a_depth, const float* b_rgbt,
+                                  const float* b_depth, int64_t npix, const float* bg, float* out_rgbt,
+                                  void* stream);
 
 /* Synchronises `stream` and reports the device-side conditions of the last
  * asynchronous render into `frame`: CAPACITY if it needed more pairs than

@@ -19,4 +19,6 @@ Layout:
                 the closest-point fallback, canonical float32.
   grad.py       analytic fp64 gradient of the composite and a finite-difference
                 helper.
+  layers.py     the separate-pass baseline of Sec. 4.1 / Fig. 5b (two layers
+                composited per pixel by their expected depths), fp64.
 """

@@ -81,7 +81,7 @@ def gaussians_fp64(g, cam, cov3d=None):
         conic = np.stack([c2 / det, -b / det, a / det], -1)
     campos = -R.T @ t
     rgb = sh_to_rgb(g.sh, mu - campos, g.sh_degree)
-    return dict(u=u, v=v, conic=conic, opacity=np.asarray(g.opacities, np.float64), rgb=rgb)
+    return dict(u=u, v=v, conic=conic, opacity=np.asarray(g.opacities, np.float64), rgb=rgb, Z=Z)
 
 
 def quat_rotmat_fp64(q):
@@ -119,6 +119,7 @@ def triangle_attributes(mesh, fid, vu, vv, vz, px, py):
     projected triangle, clamped at 0, then perspective-corrected with 1/Z and
     normalised; colour and alpha are interpolated from the vertices (alpha is
     the per-face value when given) and alpha is clamped to [0, 1].
+    Returns (colour, alpha, weights); triangle_depth gives the depth there.
     """
     f = np.asarray(mesh.faces, np.int64)[fid]
     u = vu[f]
@@ -143,6 +144,26 @@ def triangle_attributes(mesh, fid, vu, vv, vz, px, py):
     else:
         alpha = np.ones(len(fid))
     return col, np.clip(alpha, 0.0, 1.0), w
+
+
+def triangle_depth(mesh, fid, vu, vv, vz, px, py):
+    """Camera depth of faces `fid` at the centre of pixel (px, py): with the
+    same clamped screen barycentrics l_m as triangle_attributes, the
+    perspective-correct z = (sum_m l_m) / (sum_m l_m / z_m); 3 / sum_m 1/z_m
+    when every l_m is 0."""
+    f = np.asarray(mesh.faces, np.int64)[fid]
+    u, v, z = vu[f], vv[f], vz[f]
+    qx, qy = px + 0.5, py + 0.5
+    lam = np.zeros(u.shape)
+    for k in range(3):
+        a, b = (k + 1) % 3, (k + 2) % 3
+        lam[:, k] = (u[:, a] - qx) * (v[:, b] - qy) - (u[:, b] - qx) * (v[:, a] - qy)
+    area = lam.sum(1, keepdims=True)
+    lam = np.where(area != 0, lam / np.where(area == 0, 1.0, area), 1.0 / 3.0)
+    lam = np.maximum(lam, 0.0)
+    s = (lam / z).sum(1)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        return np.where(s > 0, lam.sum(1) / np.where(s > 0, s, 1.0), 3.0 / (1.0 / z).sum(1))
 
 
 # ----------------------------------------------------------------------------
@@ -171,8 +192,9 @@ class Frame:
         """All fragments of pixel (px, py), sorted by (depth bits, id).
 
         Each fragment is a dict: id, kind ('g'|'t'), alpha (Gaussian alpha
-        before the 1/255 test, or triangle alpha), color (3), mask (triangle
-        sample bits), centre (triangle centre coverage).
+        before the 1/255 test, or triangle alpha), color (3), z (camera depth
+        of a Gaussian's mean, or of the triangle at the pixel centre), mask
+        (triangle sample bits), centre (triangle centre coverage).
         """
         P = self.P
         if candidates is None:
@@ -189,7 +211,7 @@ class Frame:
             power = -0.5 * (A * dx * dx + C * dy * dy) - B * dx * dy
             alpha = np.minimum(ALPHA_MAX, G["opacity"][gi] * np.exp(power))
             for k, i in enumerate(gi):
-                frags.append(dict(id=int(i), kind="g", alpha=float(alpha[k]), color=G["rgb"][i]))
+                frags.append(dict(id=int(i), kind="g", alpha=float(alpha[k]), color=G["rgb"][i], z=float(G["Z"][i])))
         ti = candidates[candidates >= self.ng]
         if len(ti):
             loc = ti - self.ng
@@ -201,7 +223,8 @@ class Frame:
                 mi, fi = self.mesh_of(int(tid))
                 vu, vv, vz = self.V[mi]
                 col, alpha, _ = triangle_attributes(self.scene.meshes[mi], np.array([fi]), vu, vv, vz, px, py)
-                frags.append(dict(id=int(tid), kind="t", alpha=float(alpha[0]), color=col[0],
+                zt = triangle_depth(self.scene.meshes[mi], np.array([fi]), vu, vv, vz, px, py)
+                frags.append(dict(id=int(tid), kind="t", alpha=float(alpha[0]), color=col[0], z=float(zt[0]),
                                   mask=int(mask[k]), centre=bool(cen[k])))
         frags.sort(key=lambda f: (int(P.dbits[f["id"]]), f["id"]))
         return frags
@@ -214,7 +237,8 @@ def composite(frags, mode=FULL, t_eps=T_EPS, t_product=False, bg=(0.0, 0.0, 0.0)
     """Composite a depth-ordered fragment list of one pixel.
 
     Returns dict: color (3, background included), T (final transmittance),
-    weights (list of (id, weight)), tie (True when a decision sits within
+    weights (list of (id, weight)), depth (sum_i w_i z_i / sum_i w_i over the
+    blended fragments, +inf when none), tie (True when a decision sits within
     rounding distance of a threshold: |alpha - 1/255| < 1e-6 or
     |T - t_eps| < 1e-3 t_eps), n (fragments consumed).
     """
@@ -288,7 +312,11 @@ def composite(frags, mode=FULL, t_eps=T_EPS, t_product=False, bg=(0.0, 0.0, 0.0)
             if T < t_eps:
                 break
     C = C + T * np.asarray(bg, np.float64)
-    return dict(color=C, T=T, weights=weights, tie=tie, n=n)
+    # expected depth of the blended fragments: sum w z / sum w (+inf if none)
+    zmap = {f["id"]: f.get("z", np.nan) for f in frags}
+    wsum = sum(w for _, w in weights)
+    depth = sum(w * zmap[i] for i, w in weights) / wsum if wsum > 0 else np.inf
+    return dict(color=C, T=T, weights=weights, tie=tie, n=n, depth=depth)
 
 
 def render_pixels(scene, pixels, cam_index=0, mode=FULL, t_eps=T_EPS, t_product=False,
@@ -315,7 +343,8 @@ def render_image(scene, cam_index=0, mode=FULL, t_eps=T_EPS, t_product=False,
     """Full image by primitive-major gather: every (primitive, pixel-in-rect)
     pair is evaluated, pairs are grouped per pixel, ordered by (depth bits,
     id) and composited.  Returns dict rgb [H,W,3], T [H,W], tie [H,W],
-    wsum [H,W], nfrag [H,W]."""
+    wsum [H,W], nfrag [H,W], depth [H,W] (expected depth, +inf where nothing
+    blends)."""
     fr = frame or Frame(scene, cam_index, cov3d)
     P = fr.P
     W, H = fr.cam.width, fr.cam.height
@@ -338,6 +367,7 @@ def render_image(scene, cam_index=0, mode=FULL, t_eps=T_EPS, t_product=False,
     out_tie = np.zeros(H * W, bool)
     out_ws = np.zeros(H * W)
     out_n = np.zeros(H * W, np.int64)
+    out_d = np.full(H * W, np.inf)
     sig = []
     bgv = np.asarray(bg, np.float64)
     out_rgb[:] = bgv
@@ -351,10 +381,12 @@ def render_image(scene, cam_index=0, mode=FULL, t_eps=T_EPS, t_product=False,
         out_tie[p] = res["tie"]
         out_ws[p] = sum(x for _, x in res["weights"])
         out_n[p] = len(frags)
+        out_d[p] = res["depth"]
         sig.append((p, res["n"], tuple(i for i, _ in res["weights"]),
                     tuple(f.get("mask", -1) for f in frags[:res["n"]])))
     return dict(rgb=out_rgb.reshape(H, W, 3), T=out_T.reshape(H, W), tie=out_tie.reshape(H, W),
-                wsum=out_ws.reshape(H, W), nfrag=out_n.reshape(H, W), sig=hash(tuple(sig)))
+                wsum=out_ws.reshape(H, W), nfrag=out_n.reshape(H, W), depth=out_d.reshape(H, W),
+                sig=hash(tuple(sig)))
 
 
 def evaluation_count(scene, cam_index=0, mode=FULL, t_eps=T_EPS, frame=None):

@@ -155,6 +155,11 @@ umgs_status umgs_render(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_mesh*
     if ((opts.flags & UMGS_RENDER_T_PRODUCT) &&
         (opts.blend_mode != UMGS_BLEND_FULL || (opts.flags & UMGS_RENDER_SAVE_BACKWARD)))
         return fail(ctx, UMGS_ERR_INVALID_ARG, "UMGS_RENDER_T_PRODUCT needs FULL mode and no saved backward state");
+    if ((opts.flags & UMGS_RENDER_DEPTH) &&
+        (!frame || opts.blend_mode != UMGS_BLEND_FULL ||
+         (opts.flags & (UMGS_RENDER_SAVE_BACKWARD | UMGS_RENDER_MIXED | UMGS_RENDER_T_PRODUCT))))
+        return fail(ctx, UMGS_ERR_INVALID_ARG,
+                    "UMGS_RENDER_DEPTH needs a frame, FULL mode and none of SAVE_BACKWARD, MIXED, T_PRODUCT");
     if (!cams || ncams < 1) return fail(ctx, UMGS_ERR_INVALID_ARG, "need at least one camera");
     if (!out_rgbt) return fail(ctx, UMGS_ERR_INVALID_ARG, "out_rgbt is NULL");
     if (nmeshes < 0 || (nmeshes > 0 && !meshes)) return fail(ctx, UMGS_ERR_INVALID_ARG, "bad mesh array");
@@ -351,6 +356,18 @@ umgs_status umgs_frame_evaluations(const umgs_frame* frame, int64_t* evals, void
     if (!frame || !evals || !frame->valid) return UMGS_ERR_INVALID_ARG;
     if (cudaSetDevice(frame->ctx->device) != cudaSuccess) return fail(frame->ctx, UMGS_ERR_CUDA, "cudaSetDevice");
     return frame_evaluations(frame, evals, static_cast<cudaStream_t>(stream));
+}
+
+umgs_status umgs_frame_depth(const umgs_frame* frame, float* out_depth, void* stream) {
+    if (!frame || !out_depth) return UMGS_ERR_INVALID_ARG;
+    if (!frame->valid || !frame->has_depth)
+        return fail(frame->ctx, UMGS_ERR_INVALID_ARG, "the last render into this frame kept no depth");
+    if (cudaSetDevice(frame->ctx->device) != cudaSuccess) return fail(frame->ctx, UMGS_ERR_CUDA, "cudaSetDevice");
+    const cudaError_t e = cudaMemcpyAsync(out_depth, frame->depth.ptr,
+                                          sizeof(float) * (int64_t)frame->ncams * frame->W * frame->H,
+                                          cudaMemcpyDeviceToDevice, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(frame->ctx, e, "cudaMemcpyAsync(depth)");
+    return UMGS_OK;
 }
 
 umgs_status umgs_frame_lists(const umgs_frame* frame, int64_t* tile_ptr, int32_t* ids, uint32_t* dbits,

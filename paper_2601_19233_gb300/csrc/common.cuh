@@ -35,7 +35,8 @@ struct DevCam {
 };
 
 // Projected Gaussian record: 48 bytes, three 16-byte vectors.
-//  q0 = (u, v, ca, cb), q1 = (cc, opacity, r, g), q2 = (b, rect_x, rect_y, -)
+//  q0 = (u, v, ca, cb), q1 = (cc, opacity, r, g), q2 = (b, rect_x, rect_y, Z)
+//  (Z: camera depth of the mean, for the expected-depth output)
 //  power2 = ca*dx^2 + cb*dx*dy + cc*dy^2 is the exponent in base 2:
 //  alpha = min(0.99, opacity * exp2(power2)); rect_x = x_lo | x_hi << 16.
 struct __align__(16) GRec {

@@ -25,6 +25,7 @@ template <int TS> struct BatchOf { static constexpr int value = TS == 32 ? 128 :
 struct PixelState {
     float C[3];
     float T;
+    float D, Wd;  // expected-depth mode: sum w z, sum w
     float Tin;
     float t[4];
     float g_since;
@@ -38,6 +39,11 @@ struct PixelState {
 // MODE: UMGS_BLEND_* or kModeTProduct (FULL with the literal Eq. 6
 // transmittance T <- T (1 - O_i alpha_i) inside an entity).
 constexpr int kModeTProduct = 4;
+// kModeDepth: FULL blending that also accumulates each pixel's expected depth
+// sum w z / sum w (w the blend weight; z the Gaussian mean's camera depth or
+// the triangle's perspective-correct depth at the pixel centre) into
+// out_depth (+inf where nothing blends).
+constexpr int kModeDepth = 5;
 
 template <int TS, bool SAVE, int MODE>
 __device__ __forceinline__ void composite_tile(
@@ -48,7 +54,7 @@ __device__ __forceinline__ void composite_tile(
     const GRec16* __restrict__ grec16, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
     int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, float4* __restrict__ out, int32_t* __restrict__ out_last,
     float* __restrict__ out_tfin, int32_t* __restrict__ out_ntri, float4* __restrict__ stack, int cap,
-    int64_t npix, int32_t* __restrict__ need) {
+    int64_t npix, int32_t* __restrict__ need, float* __restrict__ out_depth) {
     constexpr int NT = TS * TS;
     constexpr int mode = MODE;
     const int cam = tile / tiles_per_cam;
@@ -68,6 +74,7 @@ __device__ __forceinline__ void composite_tile(
     PixelState st;
     st.C[0] = st.C[1] = st.C[2] = 0.f;
     st.T = 1.f; st.Tin = 1.f; st.g_since = 1.f;
+    st.D = 0.f; st.Wd = 0.f;
     st.t[0] = st.t[1] = st.t[2] = st.t[3] = 1.f;
     st.in_ent = false;
     bool done = !inside;
@@ -105,7 +112,7 @@ __device__ __forceinline__ void composite_tile(
                 s_rec[k][0] = a;
                 s_rec[k][1] = make_float4(b.x, b.y, (float)(rx & 0xffff), (float)(rx >> 16));
                 s_rec[k][2] = make_float4((float)(ry & 0xffff), (float)(ry >> 16), b.z, b.w);
-                s_rec[k][3] = make_float4(c.x, 0.f, 0.f, 0.f);
+                s_rec[k][3] = make_float4(c.x, c.w, 0.f, 0.f);  // (b, Z)
                 s_wmask[k] = gauss_block_mask<TS>(a.x, a.y, a.z, a.w, b.x, b.y, (int)(rx & 0xffff), (int)(rx >> 16),
                                                   (int)(ry & 0xffff), (int)(ry >> 16), tile_x0, tile_y0);
             } else {
@@ -144,6 +151,7 @@ __device__ __forceinline__ void composite_tile(
                     if (alpha < kAlphaMin) continue;
                     const float w = alpha * st.T;
                     st.C[0] += w * q2.z; st.C[1] += w * q2.w; st.C[2] += w * s_rec[k][3].x;
+                    if (mode == kModeDepth) { st.D += w * s_rec[k][3].y; st.Wd += w; }
                     st.T *= (1.f - alpha);
                     if (mode == UMGS_BLEND_ENTITY_ALL) st.g_since *= (1.f - alpha);
                     else st.in_ent = false;
@@ -188,6 +196,13 @@ __device__ __forceinline__ void composite_tile(
                         for (int e = 0; e < 3; ++e) wv[e] = (1.f / 3.f) * t.iz[e];
                     }
                     const float ws = wv[0] + wv[1] + wv[2];
+                    float zt = 0.f;  // perspective-correct depth at the pixel centre (depth mode)
+                    if (mode == kModeDepth) {
+                        const float ls = area != 0.f ? fmaxf(lam[0] / area, 0.f) + fmaxf(lam[1] / area, 0.f) +
+                                                           fmaxf(lam[2] / area, 0.f)
+                                                     : 1.f;
+                        zt = ws > 0.f ? ls / ws : 3.f / (t.iz[0] + t.iz[1] + t.iz[2]);
+                    }
                     if (ws > 0.f) { const float is = 1.f / ws; wv[0] *= is; wv[1] *= is; wv[2] *= is; }
                     else { wv[0] = wv[1] = wv[2] = 1.f / 3.f; }
                     float col[3];
@@ -224,6 +239,7 @@ __device__ __forceinline__ void composite_tile(
                         O *= 0.25f;
                         const float w = st.Tin * O * a;
                         st.C[0] += w * col[0]; st.C[1] += w * col[1]; st.C[2] += w * col[2];
+                        if (mode == kModeDepth) { st.D += w * zt; st.Wd += w; }
 #pragma unroll
                         for (int j = 0; j < 4; ++j)
                             if ((mask >> j) & 1) st.t[j] *= (1.f - a);
@@ -246,6 +262,7 @@ __device__ __forceinline__ void composite_tile(
             out_ntri[pix] = sp;
             if (sp > cap) atomicMax(need, sp);
         }
+        if (mode == kModeDepth) out_depth[pix] = st.Wd > 0.f ? st.D / st.Wd : __int_as_float(0x7f800000);
     }
 }
 
@@ -257,13 +274,13 @@ __global__ void __launch_bounds__(TS * TS) composite_kernel(
     const GRec16* __restrict__ grec16, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
     int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, float4* __restrict__ out, int32_t* __restrict__ out_last,
     float* __restrict__ out_tfin, int32_t* __restrict__ out_ntri, float4* __restrict__ stack, int cap,
-    int64_t npix, int32_t* __restrict__ need) {
+    int64_t npix, int32_t* __restrict__ need, float* __restrict__ out_depth) {
     constexpr int NB = BatchOf<TS>::value;
     __shared__ float4 s_rec[NB][10];
     __shared__ uint32_t s_id[NB];
     __shared__ uint32_t s_wmask[NB];
     __shared__ uint8_t s_list[(TS * TS / 32) * NB];
-    composite_tile<TS, SAVE, MODE>(blockIdx.x, s_rec, s_id, s_wmask, s_list, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, out, out_last, out_tfin, out_ntri, stack, cap, npix, need);
+    composite_tile<TS, SAVE, MODE>(blockIdx.x, s_rec, s_id, s_wmask, s_list, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, out, out_last, out_tfin, out_ntri, stack, cap, npix, need, out_depth);
 }
 
 // persistent launch: resident CTAs take tiles from an atomic queue in the
@@ -275,7 +292,7 @@ __global__ void __launch_bounds__(TS * TS) composite_persistent_kernel(
     const GRec16* __restrict__ grec16, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
     int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, float4* __restrict__ out, int32_t* __restrict__ out_last,
     float* __restrict__ out_tfin, int32_t* __restrict__ out_ntri, float4* __restrict__ stack, int cap,
-    int64_t npix, int32_t* __restrict__ need) {
+    int64_t npix, int32_t* __restrict__ need, float* __restrict__ out_depth) {
     constexpr int NB = BatchOf<TS>::value;
     __shared__ float4 s_rec[NB][10];
     __shared__ uint32_t s_id[NB];
@@ -288,7 +305,7 @@ __global__ void __launch_bounds__(TS * TS) composite_persistent_kernel(
         const unsigned k = s_next;
         __syncthreads();
         if ((int64_t)k >= M) break;
-        composite_tile<TS, SAVE, MODE>((int)order[k], s_rec, s_id, s_wmask, s_list, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, out, out_last, out_tfin, out_ntri, stack, cap, npix, need);
+        composite_tile<TS, SAVE, MODE>((int)order[k], s_rec, s_id, s_wmask, s_list, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, out, out_last, out_tfin, out_ntri, stack, cap, npix, need, out_depth);
         __syncthreads();
     }
 }
@@ -344,25 +361,29 @@ cudaError_t launch_composite(umgs_frame* fr, const umgs_render_opts& opts, float
         fr->trec.as<TRec>(), fr->ng,                                                                            \
         fr->nt, fr->tiles_x, tpc, fr->W, fr->H, te, opts.bg[0], opts.bg[1], opts.bg[2], out,                      \
         fr->last.as<int32_t>(), save ? fr->tfin.as<float>() : nullptr, save ? fr->ntri.as<int32_t>() : nullptr,   \
-        save ? fr->stack.as<float4>() : nullptr, fr->stack_cap, npix, fr->status.as<int32_t>() + 2),            \
+        save ? fr->stack.as<float4>() : nullptr, fr->stack_cap, npix, fr->status.as<int32_t>() + 2,             \
+        fr->has_depth ? fr->depth.as<float>() : nullptr),                                                        \
         count_launch();                                                                                         \
     else composite_kernel<TSV, SV, MV><<<M, TSV * TSV, 0, stream>>>(                                            \
         fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->mixed ? fr->grec.as<GRec16>() : nullptr,  \
         fr->trec.as<TRec>(), fr->ng,                                                                            \
         fr->nt, fr->tiles_x, tpc, fr->W, fr->H, te, opts.bg[0], opts.bg[1], opts.bg[2], out,                      \
         fr->last.as<int32_t>(), save ? fr->tfin.as<float>() : nullptr, save ? fr->ntri.as<int32_t>() : nullptr,   \
-        save ? fr->stack.as<float4>() : nullptr, fr->stack_cap, npix, fr->status.as<int32_t>() + 2),            \
+        save ? fr->stack.as<float4>() : nullptr, fr->stack_cap, npix, fr->status.as<int32_t>() + 2,             \
+        fr->has_depth ? fr->depth.as<float>() : nullptr),                                                        \
         count_launch()
     // the saved (backward) form exists for FULL only
 #define UMGS_MODES(TSV)                                                                                         \
     if (save) { UMGS_LAUNCH(TSV, true, UMGS_BLEND_FULL); }                                                      \
+    else if (mode == kModeDepth) { UMGS_LAUNCH(TSV, false, kModeDepth); }                                       \
     else if (mode == kModeTProduct) { UMGS_LAUNCH(TSV, false, kModeTProduct); }                                 \
     else if (mode == UMGS_BLEND_DIRECT) { UMGS_LAUNCH(TSV, false, UMGS_BLEND_DIRECT); }                         \
     else if (mode == UMGS_BLEND_MSAA_ALL) { UMGS_LAUNCH(TSV, false, UMGS_BLEND_MSAA_ALL); }                     \
     else if (mode == UMGS_BLEND_ENTITY_ALL) { UMGS_LAUNCH(TSV, false, UMGS_BLEND_ENTITY_ALL); }                 \
     else { UMGS_LAUNCH(TSV, false, UMGS_BLEND_FULL); }
-    const int mode = (opts.blend_mode == UMGS_BLEND_FULL && (opts.flags & UMGS_RENDER_T_PRODUCT)) ? kModeTProduct
-                                                                                                : opts.blend_mode;
+    const int mode = fr->has_depth ? kModeDepth
+                     : (opts.blend_mode == UMGS_BLEND_FULL && (opts.flags & UMGS_RENDER_T_PRODUCT)) ? kModeTProduct
+                                                                                                  : opts.blend_mode;
     if (ts == 16) { UMGS_MODES(16) }
     else if (ts == 8) { UMGS_MODES(8) }
     else { UMGS_MODES(32) }

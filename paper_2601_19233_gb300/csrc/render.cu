@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(256, 2) project_gaussians_kernel(
             gp[0] = make_float4(u, v, -0.5f * kLog2e * ia, -kLog2e * ib);
             reinterpret_cast<float2*>(gp + 1)[0] = make_float2(-0.5f * kLog2e * ic, o);
             reinterpret_cast<float2*>(gp + 2)[0] = make_float2(0.f, __uint_as_float(bi.rx));
-            reinterpret_cast<float*>(gp + 2)[2] = __uint_as_float(bi.ry);
+            reinterpret_cast<float2*>(gp + 2)[1] = make_float2(__uint_as_float(bi.ry), Z);  // Z: expected-depth output
         }
     }
 }
@@ -1245,6 +1245,8 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
         UMGS_TRY(cudaGetLastError());
     }
     UMGS_TRY(fr->last.reserve(sizeof(int32_t) * (int64_t)ncams * W * H));
+    fr->has_depth = (opts.flags & UMGS_RENDER_DEPTH) != 0;
+    if (fr->has_depth) UMGS_TRY(fr->depth.reserve(sizeof(float) * (int64_t)ncams * W * H));
     fr->saved = (opts.flags & UMGS_RENDER_SAVE_BACKWARD) != 0 && opts.blend_mode == UMGS_BLEND_FULL;
     if (fr->saved) {
         const int64_t npix = (int64_t)ncams * W * H;

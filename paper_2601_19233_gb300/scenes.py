@@ -369,3 +369,36 @@ def config4(seed=1004, n_gauss=6_000_000, torus_ab=(1000, 1000), width=3840, hei
     m = rng.uniform(size=F.shape[0]) < 0.3
     falpha[m] = rng.uniform(0.2, 0.8, size=int(m.sum())).astype(np.float32)
     return Scene(g, [Mesh(V, F, vcol, None, falpha)], [cam], tile=16)
+
+
+def nested_scene(seed=1005, size=256, n_gauss=30_000, bowl_subdiv=3, bowl_alpha=0.35, n_cams=1):
+    """Nested transparency (the setting of Sec. 4.1, Fig. 5b): a Gaussian
+    object (three overlapping coloured boxes of points, 0.5 across) and an
+    opaque mesh sphere beside it, both enclosed by a transparent sphere
+    ("bowl", radius 0.8, face alpha `bowl_alpha`, bluish).  Returns
+    (scene, gaussian_layer, mesh_layer): the full scene and the two
+    representations as scenes of their own (for the separate-pass baseline)."""
+    rng = np.random.default_rng(seed)
+    fx = focal_from_fov(size, 60.0)
+    if n_cams == 1:
+        cams = [front_camera(size, size, fx, 3.0)]
+    else:
+        cams = orbit_cameras(n_cams, 3.0, size, size, fx, lambda k: 15.0 * math.sin(2 * math.pi * k / 8))
+    centres = np.array([[-0.15, 0.05, 0.0], [0.05, -0.1, 0.1], [0.0, 0.15, -0.1]])
+    cols = np.array([[0.9, 0.2, 0.1], [0.95, 0.8, 0.1], [0.2, 0.5, 0.9]])
+    which = rng.integers(0, 3, size=n_gauss)
+    means = (centres[which] + rng.uniform(-0.12, 0.12, size=(n_gauss, 3))).astype(np.float32)
+    means[:, 0] -= 0.15
+    g = make_gaussians(rng, means, -4.0, 0, dc_colors=cols[which])
+    g.opacities[:] = rng.uniform(0.6, 0.95, size=n_gauss).astype(np.float32)
+    Vb, Fb = icosphere(bowl_subdiv, 0.8)
+    bowl = Mesh(Vb, Fb, np.tile(np.array([[0.55, 0.75, 1.0]], np.float32), (Vb.shape[0], 1)), None,
+                np.full(Fb.shape[0], bowl_alpha, np.float32))
+    Vs, Fs = icosphere(2, 0.18)
+    Vs = (Vs + np.array([0.38, 0.1, 0.05], np.float32)).astype(np.float32)
+    ball = Mesh(Vs, Fs, rng.uniform(0.2, 0.4, size=(Vs.shape[0], 3)).astype(np.float32) + np.float32([0.5, 0.0, 0.3]),
+                None, np.ones(Fs.shape[0], np.float32))
+    empty = Gaussians(np.zeros((0, 3), np.float32), np.zeros((0, 4), np.float32), np.zeros((0, 3), np.float32),
+                      np.zeros(0, np.float32), np.zeros((0, 1, 3), np.float32), 0)
+    scene = Scene(g, [ball, bowl], cams, tile=16)
+    return scene, Scene(g, [], cams, tile=16), Scene(empty, [ball, bowl], cams, tile=16)

@@ -27,6 +27,7 @@ RENDER_SAVE_BACKWARD = 1
 RENDER_MIXED = 2
 RENDER_T_PRODUCT = 4
 RENDER_ASYNC = 8
+RENDER_DEPTH = 16
 DEFORM_FRAME, DEFORM_LITERAL = 0, 1
 
 
@@ -128,6 +129,10 @@ def lib():
         L.umgs_frame_reserve.restype = ctypes.c_int
         L.umgs_frame_check.argtypes = [vp, vp]
         L.umgs_frame_check.restype = ctypes.c_int
+        L.umgs_frame_depth.argtypes = [vp, vp, vp]
+        L.umgs_frame_depth.restype = ctypes.c_int
+        L.umgs_composite_layers.argtypes = [vp, vp, vp, vp, vp, i64, ctypes.POINTER(ctypes.c_float), vp, vp]
+        L.umgs_composite_layers.restype = ctypes.c_int
         L.umgs_kernel_launches.argtypes = []
         L.umgs_kernel_launches.restype = ctypes.c_longlong
         for name in ("umgs_profile_enable", "umgs_profile_read", "umgs_ctx_create", "umgs_frame_create", "umgs_render", "umgs_frame_counts",
@@ -218,6 +223,12 @@ class Frame:
                        "umgs_frame_lists")
         return ptr, ids[:k], db[:k]
 
+    def depth(self, ncams, height, width):
+        """umgs_frame_depth: expected depth [ncams, H, W] float32 on the device (+inf where nothing blends)."""
+        out = torch.empty((ncams, height, width), dtype=torch.float32, device=torch.device("cuda", self.ctx.device))
+        self.ctx.check(lib().umgs_frame_depth(self._h, _ptr(out), _stream()), "umgs_frame_depth")
+        return out
+
     def __del__(self):
         try:
             if self._h:
@@ -292,12 +303,13 @@ def mesh_to_device(m, device="cuda") -> DevMesh:
 
 
 def render_opts(tile_size=16, blend_mode=BLEND_FULL, t_eps=1e-4, bg=(0.0, 0.0, 0.0), save=False,
-                mixed=False, sched=0, t_product=False, asynchronous=False) -> CRenderOpts:
+                mixed=False, sched=0, t_product=False, asynchronous=False, depth=False) -> CRenderOpts:
     o = CRenderOpts()
     lib().umgs_default_render_opts(ctypes.byref(o))
     o.sched = int(sched)
     o.flags = ((RENDER_SAVE_BACKWARD if save else 0) | (RENDER_MIXED if mixed else 0)
-               | (RENDER_T_PRODUCT if t_product else 0) | (RENDER_ASYNC if asynchronous else 0))
+               | (RENDER_T_PRODUCT if t_product else 0) | (RENDER_ASYNC if asynchronous else 0)
+               | (RENDER_DEPTH if depth else 0))
     o.tile_size = int(tile_size)
     o.blend_mode = int(blend_mode)
     o.t_eps = float(t_eps)
@@ -401,6 +413,18 @@ NUM_STAGES = 16
 
 def profile_enable(ctx: Context, on=True):
     ctx.check(lib().umgs_profile_enable(ctx._h, 1 if on else 0), "umgs_profile_enable")
+
+
+def composite_layers(ctx: Context, a_rgbt, a_depth, b_rgbt, b_depth, bg=(0.0, 0.0, 0.0), out=None, stream=None):
+    """umgs_composite_layers: separate-pass baseline, the nearer of two layers over the other, then bg."""
+    if out is None:
+        out = torch.empty_like(a_rgbt)
+    npix = a_rgbt.numel() // 4
+    assert a_depth.numel() == npix and b_depth.numel() == npix and b_rgbt.numel() == 4 * npix
+    cbg = (ctypes.c_float * 3)(*[float(x) for x in bg])
+    ctx.check(lib().umgs_composite_layers(ctx._h, _ptr(a_rgbt), _ptr(a_depth), _ptr(b_rgbt), _ptr(b_depth), npix,
+                                          cbg, _ptr(out), _stream(stream)), "umgs_composite_layers")
+    return out
 
 
 def kernel_launches() -> int:
