@@ -52,8 +52,9 @@ enum { UMGS_F32 = 0, UMGS_BF16 = 1 };
 /* binding modes (Sec. 3.3) */
 enum { UMGS_BIND_BBX = 0, UMGS_BIND_CENTER = 1, UMGS_BIND_NEAREST = 2 };
 
-/* deformation modes (Eq. 13) */
-enum { UMGS_DEFORM_FRAME = 0, UMGS_DEFORM_LITERAL = 1 };
+/* deformation modes: the mean update of Eq. 13 (FRAME or LITERAL), optionally
+ * OR'ed with ONE_RING for the per-vertex transform (see umgs_deform) */
+enum { UMGS_DEFORM_FRAME = 0, UMGS_DEFORM_LITERAL = 1, UMGS_DEFORM_ONE_RING = 16 };
 
 typedef struct umgs_ctx umgs_ctx;
 typedef struct umgs_frame umgs_frame;
@@ -324,6 +325,13 @@ umgs_status umgs_bind(umgs_ctx* ctx, const umgs_gaussians* g, const float* proxy
  * mu' = mu + mean Delta_i (mode LITERAL, Eq. 13 as printed) or
  * mu' = mu + mean Delta_i + (R'S' - I)(mu - mean P_i) (mode FRAME, default:
  * exact for rigid motions and uniform scalings of the proxy).
+ * With UMGS_DEFORM_ONE_RING in `mode` (closer to ACAP's own per-vertex fit)
+ * D_v is instead the cotangent-weighted least-squares map of the vertex's
+ * one-ring edges plus its normal:
+ *   D_v = (sum_j c_vj e'_vj e_vj^T + n'_v n_v^T)(sum_j c_vj e_vj e_vj^T + n_v n_v^T)^-1
+ * (e_vj = V_j - V_v, c_vj = sum over the edge's faces of max(0, cot/2) of the
+ * opposite angle, N_v = sum of e1 x e2 over the faces at v, n_v = N_v/sqrt|N_v|;
+ * primes: deformed); the rest is unchanged.
  *
  * rest       Gaussians at rest (means, quats, scales or cov3d; n); SH/opacity unused
  * face       [n,8] int32 proxy face per bound point (from umgs_bind)
@@ -451,8 +459,9 @@ long long umgs_kernel_launches(void);
  *    (several streams or host threads at once) race and give wrong results.
  *  - Out-of-range face or vertex ids give NaN outputs for the affected
  *    Gaussians; no deferred status is kept.
- * Errors: INVALID_ARG (as umgs_deform), CAPACITY (nv above the maximum),
- * CUDA (lookup or launch failure).  Asynchronous.
+ *  - The per-face transform only: UMGS_DEFORM_ONE_RING is rejected.
+ * Errors: INVALID_ARG (as umgs_deform, and ONE_RING), CAPACITY (nv above the
+ * maximum), CUDA (lookup or launch failure).  Asynchronous.
  */
 #define UMGS_NOALLOC_MAX_PROXY_VERTICES 32768
 umgs_status umgs_deform_noalloc(const umgs_gaussians* rest, const int32_t* face, const float* bary,

@@ -15,6 +15,17 @@ D_v = R_v S_v by polar decomposition (SVD; if det D_v < 0 the smallest
 singular direction is flipped so R_v is a proper rotation), r_v = log R_v as
 an axis-angle vector with angle in [0, pi].
 
+A second reading (ONE_RING), closer to ACAP's own per-vertex fit: D_v is
+the least-squares map of the vertex's one-ring edges, cotangent-weighted,
+plus its area-weighted normal:
+    D_v = argmin_D  sum_j c_vj |e'_vj - D e_vj|^2 + |n'_v - D n_v|^2
+        = (sum_j c_vj e'_vj e_vj^T + n'_v n_v^T)(sum_j c_vj e_vj e_vj^T + n_v n_v^T)^-1
+with e_vj = V_j - V_v over the edges at v, c_vj = sum over the faces holding
+the edge of max(0, cot(angle opposite the edge) / 2), N_v = sum over the
+faces at v of e1 x e2 and n_v = N_v / sqrt(|N_v|) (the normal term keeps a
+flat one-ring well posed); primes are the deformed mesh.  Rigid motions and
+uniform scalings give D_v = R and s I exactly.
+
 Eq. 13's mean update mu' = mu + mean Delta_i is exact only for translations;
 mode FRAME (default) adds (R'S' - I)(mu - P_bar), P_bar = mean P_i, so that a
 rigidly moved proxy moves the bound Gaussians rigidly.  Mode LITERAL is Eq. 13
@@ -29,6 +40,7 @@ from scipy.spatial.transform import Rotation
 from .render import cov3d_fp64, quat_rotmat_fp64
 
 FRAME, LITERAL = 0, 1
+FACES, ONE_RING = "faces", "one_ring"  # per-vertex transform readings
 
 
 def face_frames(V, F):
@@ -42,18 +54,21 @@ def face_frames(V, F):
     return np.stack([e1, e2, n3], -1), 0.5 * nn  # columns e1, e2, n3; area
 
 
-def vertex_transforms(V, Vd, F):
+def vertex_transforms(V, Vd, F, method=FACES):
     """Per-vertex offset Delta [Nv,3], log-rotation r [Nv,3], stretch S [Nv,3,3]."""
-    _, area = face_frames(V, F)
-    Df = face_gradients(V, Vd, F)
-    nv = len(V)
-    F = np.asarray(F, np.int64)
-    Dv = np.zeros((nv, 3, 3))
-    wv = np.zeros(nv)
-    for k in range(3):
-        np.add.at(Dv, F[:, k], area[:, None, None] * Df)
-        np.add.at(wv, F[:, k], area)
-    Dv = Dv / wv[:, None, None]
+    if method == ONE_RING:
+        Dv = one_ring_gradients(V, Vd, F)
+    else:
+        _, area = face_frames(V, F)
+        Df = face_gradients(V, Vd, F)
+        nv = len(V)
+        F = np.asarray(F, np.int64)
+        Dv = np.zeros((nv, 3, 3))
+        wv = np.zeros(nv)
+        for k in range(3):
+            np.add.at(Dv, F[:, k], area[:, None, None] * Df)
+            np.add.at(wv, F[:, k], area)
+        Dv = Dv / wv[:, None, None]
     r, S = polar_log(Dv)
     delta = np.asarray(Vd, np.float64) - np.asarray(V, np.float64)
     return delta, r, S
@@ -64,6 +79,40 @@ def face_gradients(V, Vd, F):
     Fr, _ = face_frames(V, F)
     Fd, _ = face_frames(Vd, F)
     return Fd @ np.linalg.inv(Fr)
+
+
+def one_ring_gradients(V, Vd, F):
+    """D_v of the ONE_RING reading (module docstring), every vertex."""
+    V = np.asarray(V, np.float64)
+    Vd = np.asarray(Vd, np.float64)
+    F = np.asarray(F, np.int64)
+    nv = len(V)
+    A = np.zeros((nv, 3, 3))
+    B = np.zeros((nv, 3, 3))
+    P, Q = V[F], Vd[F]
+    for k in range(3):
+        i, j = (k + 1) % 3, (k + 2) % 3
+        u1, u2 = P[:, i] - P[:, k], P[:, j] - P[:, k]
+        cot = (u1 * u2).sum(1) / np.linalg.norm(np.cross(u1, u2), axis=1)
+        w = np.maximum(0.5 * cot, 0.0)
+        e, ed = P[:, j] - P[:, i], Q[:, j] - Q[:, i]
+        EE = w[:, None, None] * e[:, :, None] * e[:, None, :]
+        DE = w[:, None, None] * ed[:, :, None] * e[:, None, :]
+        for v in (i, j):
+            np.add.at(A, F[:, v], EE)
+            np.add.at(B, F[:, v], DE)
+    N = np.zeros((nv, 3))
+    Nd = np.zeros((nv, 3))
+    nf = np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0])
+    ndf = np.cross(Q[:, 1] - Q[:, 0], Q[:, 2] - Q[:, 0])
+    for k in range(3):
+        np.add.at(N, F[:, k], nf)
+        np.add.at(Nd, F[:, k], ndf)
+    n = N / np.sqrt(np.linalg.norm(N, axis=1))[:, None]
+    nd = Nd / np.sqrt(np.linalg.norm(Nd, axis=1))[:, None]
+    A += n[:, :, None] * n[:, None, :]
+    B += nd[:, :, None] * n[:, None, :]
+    return B @ np.linalg.inv(A)
 
 
 def polar_log(D):
@@ -78,13 +127,13 @@ def polar_log(D):
     return r, S
 
 
-def deform_gaussians(means, quats, scales, face, bary, V, Vd, F, mode=FRAME, cov3d=None):
+def deform_gaussians(means, quats, scales, face, bary, V, Vd, F, mode=FRAME, cov3d=None, method=FACES):
     """Eq. 12-13 for every Gaussian.
 
     face [N,8] int, bary [N,8,2] (weights of face vertices 1 and 2).
     Returns (mu' [N,3], Sigma' [N,3,3], q' [N,4] (w,x,y,z), w >= 0).
     """
-    delta, r, S = vertex_transforms(V, Vd, F)
+    delta, r, S = vertex_transforms(V, Vd, F, method)
     Fi = np.asarray(F, np.int64)[np.asarray(face, np.int64)]           # [N,8,3]
     b = np.asarray(bary, np.float64)
     w = np.stack([1.0 - b[..., 0] - b[..., 1], b[..., 0], b[..., 1]], -1)  # [N,8,3]

@@ -257,7 +257,8 @@ umgs_status umgs_deform(umgs_ctx* ctx, const umgs_gaussians* rest, const int32_t
     ctx->err.clear();
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, UMGS_ERR_CUDA, "cudaSetDevice");
     if (!rest || rest->n < 0) return fail(ctx, UMGS_ERR_INVALID_ARG, "rest Gaussians missing");
-    if (mode != UMGS_DEFORM_FRAME && mode != UMGS_DEFORM_LITERAL) return fail(ctx, UMGS_ERR_INVALID_ARG, "bad mode");
+    if ((mode & ~(UMGS_DEFORM_LITERAL | UMGS_DEFORM_ONE_RING)) != 0)
+        return fail(ctx, UMGS_ERR_INVALID_ARG, "bad mode");
     if (!proxy_v || !proxy_vd || !proxy_f || nv < 3 || nf < 1) return fail(ctx, UMGS_ERR_INVALID_ARG, "bad proxy mesh");
     if (rest->n > 0) {
         if (!rest->means || !face || !bary || !out_means || !out_cov3d)
@@ -293,7 +294,8 @@ umgs_status umgs_deform_compact(umgs_ctx* ctx, const umgs_gaussians* rest, const
     ctx->err.clear();
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, UMGS_ERR_CUDA, "cudaSetDevice");
     if (!rest || rest->n < 0) return fail(ctx, UMGS_ERR_INVALID_ARG, "rest Gaussians missing");
-    if (mode != UMGS_DEFORM_FRAME && mode != UMGS_DEFORM_LITERAL) return fail(ctx, UMGS_ERR_INVALID_ARG, "bad mode");
+    if ((mode & ~(UMGS_DEFORM_LITERAL | UMGS_DEFORM_ONE_RING)) != 0)
+        return fail(ctx, UMGS_ERR_INVALID_ARG, "bad mode");
     if (!proxy_v || !proxy_vd || !proxy_f || nv < 3 || nf < 1) return fail(ctx, UMGS_ERR_INVALID_ARG, "bad proxy mesh");
     if (rest->n > 0) {
         if (!rest->means || !count || !entries || !out_means || !out_cov3d)

@@ -219,6 +219,21 @@ __device__ void log_rot(const float R[9], float r[3]) {
     }
 }
 
+// the table row of vertex v from its transform D: polar D = R S, r = log R,
+// Delta = V' - V and the rest position
+__device__ __forceinline__ void write_vertex_row(const float (&D)[9], const float* __restrict__ V,
+                                                 const float* __restrict__ Vd, int64_t v, float* __restrict__ vtab) {
+    float R[9], S6[6], r[3];
+    polar3(D, R, S6);
+    log_rot(R, r);
+    float4* o = reinterpret_cast<float4*>(vtab + kVtabStride * v);
+    const float p0 = V[3 * v], p1 = V[3 * v + 1], p2 = V[3 * v + 2];
+    o[0] = make_float4(Vd[3 * v] - p0, Vd[3 * v + 1] - p1, Vd[3 * v + 2] - p2, r[0]);
+    o[1] = make_float4(r[1], r[2], S6[0], S6[1]);
+    o[2] = make_float4(S6[2], S6[3], S6[4], S6[5]);
+    o[3] = make_float4(p0, p1, p2, 0.f);
+}
+
 __global__ void __launch_bounds__(256) vertex_xforms_kernel(const float* __restrict__ V, const float* __restrict__ Vd,
                                                             const float* __restrict__ vacc, int64_t nv,
                                                             float* __restrict__ vtab) {
@@ -229,15 +244,84 @@ __global__ void __launch_bounds__(256) vertex_xforms_kernel(const float* __restr
     const float w = a[9];
     if (w > 0.f) { const float iw = 1.f / w; for (int k = 0; k < 9; ++k) D[k] = a[k] * iw; }
     else { for (int k = 0; k < 9; ++k) D[k] = (k % 4 == 0) ? 1.f : 0.f; }
-    float R[9], S6[6], r[3];
-    polar3(D, R, S6);
-    log_rot(R, r);
-    float4* o = reinterpret_cast<float4*>(vtab + kVtabStride * v);
-    const float p0 = V[3 * v], p1 = V[3 * v + 1], p2 = V[3 * v + 2];
-    o[0] = make_float4(Vd[3 * v] - p0, Vd[3 * v + 1] - p1, Vd[3 * v + 2] - p2, r[0]);
-    o[1] = make_float4(r[1], r[2], S6[0], S6[1]);
-    o[2] = make_float4(S6[2], S6[3], S6[4], S6[5]);
-    o[3] = make_float4(p0, p1, p2, 0.f);
+    write_vertex_row(D, V, Vd, v, vtab);
+}
+
+// ---- one-ring reading of the per-vertex transform --------------------------
+// D_v = (sum_j c_vj e'_vj e_vj^T + n'_v n_v^T)(sum_j c_vj e_vj e_vj^T + n_v n_v^T)^-1
+// over the edges at v, c_vj = sum over the edge's faces of max(0, cot/2) of the
+// opposite angle, N_v = sum of the faces' e1 x e2 at v, n_v = N_v / sqrt|N_v|
+// (rest and deformed).  Per-vertex accumulators (21 floats): A (xx xy xz yy yz
+// zz), B (row-major 3x3), N (3), N' (3).
+constexpr int kOneRingAcc = 21;
+
+__global__ void __launch_bounds__(256) one_ring_faces_kernel(const float* __restrict__ V, const float* __restrict__ Vd,
+                                                             const int32_t* __restrict__ F, int64_t nv, int64_t nf,
+                                                             float* __restrict__ vacc, int32_t* __restrict__ status) {
+    const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (f >= nf) return;
+    const int idx[3] = {F[3 * f], F[3 * f + 1], F[3 * f + 2]};
+    for (int k = 0; k < 3; ++k)
+        if (idx[k] < 0 || idx[k] >= nv) { atomicOr(status, kStatusBadIndex); return; }
+    float P[3][3], Q[3][3];
+    for (int k = 0; k < 3; ++k)
+        for (int d = 0; d < 3; ++d) { P[k][d] = V[3 * (int64_t)idx[k] + d]; Q[k][d] = Vd[3 * (int64_t)idx[k] + d]; }
+    for (int k = 0; k < 3; ++k) {  // edge (i, j) opposite corner k
+        const int i = (k + 1) % 3, j = (k + 2) % 3;
+        const float u1[3] = {P[i][0] - P[k][0], P[i][1] - P[k][1], P[i][2] - P[k][2]};
+        const float u2[3] = {P[j][0] - P[k][0], P[j][1] - P[k][1], P[j][2] - P[k][2]};
+        float cr[3];
+        cross3(u1, u2, cr);
+        const float len = sqrtf(dot3(cr, cr));
+        const float w = len > 0.f ? fmaxf(0.5f * dot3(u1, u2) / len, 0.f) : 0.f;
+        if (!(w > 0.f)) continue;
+        const float e[3] = {P[j][0] - P[i][0], P[j][1] - P[i][1], P[j][2] - P[i][2]};
+        const float ed[3] = {Q[j][0] - Q[i][0], Q[j][1] - Q[i][1], Q[j][2] - Q[i][2]};
+        const float a6[6] = {w * e[0] * e[0], w * e[0] * e[1], w * e[0] * e[2],
+                             w * e[1] * e[1], w * e[1] * e[2], w * e[2] * e[2]};
+        for (const int vert : {idx[i], idx[j]}) {
+            float* acc = vacc + kOneRingAcc * (int64_t)vert;
+            for (int q = 0; q < 6; ++q) atomicAdd(acc + q, a6[q]);
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c) atomicAdd(acc + 6 + 3 * r + c, w * ed[r] * e[c]);
+        }
+    }
+    const float e1[3] = {P[1][0] - P[0][0], P[1][1] - P[0][1], P[1][2] - P[0][2]};
+    const float e2[3] = {P[2][0] - P[0][0], P[2][1] - P[0][1], P[2][2] - P[0][2]};
+    const float d1[3] = {Q[1][0] - Q[0][0], Q[1][1] - Q[0][1], Q[1][2] - Q[0][2]};
+    const float d2[3] = {Q[2][0] - Q[0][0], Q[2][1] - Q[0][1], Q[2][2] - Q[0][2]};
+    float n[3], nd[3];
+    cross3(e1, e2, n);
+    cross3(d1, d2, nd);
+    for (int k = 0; k < 3; ++k) {
+        float* acc = vacc + kOneRingAcc * (int64_t)idx[k];
+        for (int d = 0; d < 3; ++d) { atomicAdd(acc + 15 + d, n[d]); atomicAdd(acc + 18 + d, nd[d]); }
+    }
+}
+
+__global__ void __launch_bounds__(256) one_ring_vertices_kernel(const float* __restrict__ V,
+                                                                const float* __restrict__ Vd,
+                                                                const float* __restrict__ vacc, int64_t nv,
+                                                                float* __restrict__ vtab) {
+    const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    const float* a = vacc + kOneRingAcc * v;
+    const float* N = a + 15;
+    const float* Nd = a + 18;
+    const float ln = sqrtf(dot3(N, N)), lnd = sqrtf(dot3(Nd, Nd));
+    const float sn = ln > 0.f ? rsqrtf(ln) : 0.f, snd = lnd > 0.f ? rsqrtf(lnd) : 0.f;
+    const float n[3] = {N[0] * sn, N[1] * sn, N[2] * sn}, nd[3] = {Nd[0] * snd, Nd[1] * snd, Nd[2] * snd};
+    float A[9] = {a[0], a[1], a[2], a[1], a[3], a[4], a[2], a[4], a[5]};
+    float B[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            A[3 * r + c] += n[r] * n[c];
+            B[3 * r + c] = a[6 + 3 * r + c] + nd[r] * n[c];
+        }
+    float Ai[9], D[9];
+    if (inv3_fp64(A, Ai)) matmul3(B, Ai, D);
+    else for (int k = 0; k < 9; ++k) D[k] = (k % 4 == 0) ? 1.f : 0.f;  // isolated vertex: identity
+    write_vertex_row(D, V, Vd, v, vtab);
 }
 
 // ---- K2: per-Gaussian update ------------------------------------------------
@@ -513,23 +597,33 @@ static inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + b
 
 // per-face gradients and the per-vertex table of the deformed proxy (A1)
 static umgs_status proxy_table(umgs_ctx* ctx, const float* V, const float* Vd, const int32_t* F, int64_t nv,
-                               int64_t nf, cudaStream_t stream) {
+                               int64_t nf, bool one_ring, cudaStream_t stream) {
     cudaError_t e;
-    if ((e = ctx->vacc.reserve(sizeof(float) * 10 * nv)) != cudaSuccess) return fail(ctx, UMGS_ERR_OUT_OF_MEMORY, "vacc");
+    const int64_t nacc = (one_ring ? kOneRingAcc : 10) * nv;
+    if ((e = ctx->vacc.reserve(sizeof(float) * nacc)) != cudaSuccess) return fail(ctx, UMGS_ERR_OUT_OF_MEMORY, "vacc");
     if ((e = ctx->vtab.reserve(sizeof(float) * kVtabStride * nv)) != cudaSuccess)
         return fail(ctx, UMGS_ERR_OUT_OF_MEMORY, "vtab");
     ctx->vtab_rows = nv;
-    if ((e = cudaMemsetAsync(ctx->vacc.ptr, 0, sizeof(float) * 10 * nv, stream)) != cudaSuccess)
+    if ((e = cudaMemsetAsync(ctx->vacc.ptr, 0, sizeof(float) * nacc, stream)) != cudaSuccess)
         return cuda_fail(ctx, e, "cudaMemsetAsync");
     int32_t* status = ctx->dstatus.as<int32_t>();
     {
         StageTimer tm(ctx, UMGS_STAGE_DEFORM_FACES, stream);
-        face_gradients_kernel<<<grid_for(nf, 256), 256, 0, stream>>>(V, Vd, F, nv, nf, ctx->vacc.as<float>(), status), count_launch();
+        if (one_ring)
+            one_ring_faces_kernel<<<grid_for(nf, 256), 256, 0, stream>>>(V, Vd, F, nv, nf, ctx->vacc.as<float>(),
+                                                                         status), count_launch();
+        else
+            face_gradients_kernel<<<grid_for(nf, 256), 256, 0, stream>>>(V, Vd, F, nv, nf, ctx->vacc.as<float>(),
+                                                                         status), count_launch();
     }
     {
         StageTimer tm(ctx, UMGS_STAGE_DEFORM_VERTICES, stream);
-        vertex_xforms_kernel<<<grid_for(nv, 256), 256, 0, stream>>>(V, Vd, ctx->vacc.as<float>(), nv,
-                                                                    ctx->vtab.as<float>()), count_launch();
+        if (one_ring)
+            one_ring_vertices_kernel<<<grid_for(nv, 256), 256, 0, stream>>>(V, Vd, ctx->vacc.as<float>(), nv,
+                                                                            ctx->vtab.as<float>()), count_launch();
+        else
+            vertex_xforms_kernel<<<grid_for(nv, 256), 256, 0, stream>>>(V, Vd, ctx->vacc.as<float>(), nv,
+                                                                        ctx->vtab.as<float>()), count_launch();
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "proxy table kernels");
     return UMGS_OK;
@@ -538,7 +632,8 @@ static umgs_status proxy_table(umgs_ctx* ctx, const float* V, const float* Vd, c
 umgs_status deform_forward(umgs_ctx* ctx, const umgs_gaussians* g, const int32_t* face, const float* bary,
                            const float* V, const float* Vd, const int32_t* F, int64_t nv, int64_t nf, int32_t mode,
                            float* out_means, float* out_cov, float* out_quats, cudaStream_t stream) {
-    const umgs_status st = proxy_table(ctx, V, Vd, F, nv, nf, stream);
+    const umgs_status st = proxy_table(ctx, V, Vd, F, nv, nf, (mode & UMGS_DEFORM_ONE_RING) != 0, stream);
+    mode &= 1;  // the mean update: FRAME or LITERAL
     if (st != UMGS_OK) return st;
     StageTimer tm(ctx, UMGS_STAGE_DEFORM_GAUSSIANS, stream);
     if (g->n > 0)
@@ -564,7 +659,8 @@ umgs_status deform_compact_forward(umgs_ctx* ctx, const umgs_gaussians* g, const
                                    const float* V, const float* Vd, const int32_t* F, int64_t nv, int64_t nf,
                                    int32_t mode, float* out_means, float* out_cov, float* out_quats,
                                    cudaStream_t stream) {
-    const umgs_status st = proxy_table(ctx, V, Vd, F, nv, nf, stream);
+    const umgs_status st = proxy_table(ctx, V, Vd, F, nv, nf, (mode & UMGS_DEFORM_ONE_RING) != 0, stream);
+    mode &= 1;  // the mean update: FRAME or LITERAL
     if (st != UMGS_OK) return st;
     StageTimer tm(ctx, UMGS_STAGE_DEFORM_GAUSSIANS, stream);
     if (g->n > 0)

@@ -28,7 +28,7 @@ RENDER_MIXED = 2
 RENDER_T_PRODUCT = 4
 RENDER_ASYNC = 8
 RENDER_DEPTH = 16
-DEFORM_FRAME, DEFORM_LITERAL = 0, 1
+DEFORM_FRAME, DEFORM_LITERAL, DEFORM_ONE_RING = 0, 1, 16
 
 
 class UmgsError(RuntimeError):

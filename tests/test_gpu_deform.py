@@ -152,3 +152,46 @@ def test_compact_binding_bad_index(ctx):
         ctx.sync()
     m = m.cpu().numpy()
     assert np.all(np.isnan(m[5])) and np.all(np.isfinite(np.delete(m, 5, axis=0)))
+
+
+@pytest.mark.parametrize("mode", [D.FRAME, D.LITERAL])
+def test_one_ring_transform_matches_oracle(ctx, mode):
+    # UMGS_DEFORM_ONE_RING: the per-vertex table from the cotangent-weighted
+    # one-ring least squares, then the same Eq. 12-13
+    from paper_2601_19233_gb300 import umgs
+    V, F, g, face, b = _problem(7)
+    Vd = S.displace(V, S.sinusoid_params(np.random.default_rng(8)), 23)
+    m, c, q = _run(ctx, V, Vd, F, g, face, b, mode | umgs.DEFORM_ONE_RING)
+    tab = umgs.deform_vertex_table(ctx, len(V)).cpu().numpy()
+    delta, r, Sv = D.vertex_transforms(V, Vd, F, D.ONE_RING)
+    assert np.abs(tab[:, :3] - delta).max() < 1e-6
+    assert np.abs(tab[:, 3:6] - r).max() < 2e-5
+    assert np.abs(tab[:, 6:] - D.sym6(Sv)).max() < 2e-5
+    mr, Sr, qr = D.deform_gaussians(g.means, g.quats, g.scales, face, b, V, Vd, F, mode=mode, method=D.ONE_RING)
+    assert np.abs(m - mr).max() < 1e-5
+    assert _cov_err(c, Sr) < 1e-4
+    assert _quat_err(q, qr) < 1e-5
+    # the two readings differ on a smooth non-rigid deformation
+    _, r_f, S_f = D.vertex_transforms(V, Vd, F)
+    assert np.abs(D.sym6(S_f) - D.sym6(Sv)).max() > 1e-3
+
+
+def test_one_ring_rigid_and_noalloc_rejects(ctx):
+    from paper_2601_19233_gb300 import umgs
+    V, F, g, face, b = _problem(9)
+    Rm = Rotation.random(random_state=9).as_matrix()
+    t = np.array([-0.2, 0.1, 0.3])
+    Vd = V.astype(np.float64) @ Rm.T + t
+    m, c, q = _run(ctx, V, Vd, F, g, face, b, umgs.DEFORM_ONE_RING)
+    assert np.abs(m - (g.means.astype(np.float64) @ Rm.T + t)).max() < 1e-5
+    Sig = cov3d_fp64(g.quats, g.scales)
+    assert _cov_err(c, Rm @ Sig @ Rm.T) < 1e-5
+    with pytest.raises(umgs.UmgsError):  # unknown mode bits
+        _run(ctx, V, Vd, F, g, face, b, 2)
+    # the allocation-free entry point keeps the per-face reading only
+    dg = umgs.gaussians_to_device(g)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a)).cuda()
+    out = (torch.empty((g.n, 3), device="cuda"), torch.empty((g.n, 6), device="cuda"), None)
+    with pytest.raises(umgs.UmgsError):
+        umgs.deform_noalloc(dg, t(face), t(b), t(V.astype(np.float32)), t(Vd.astype(np.float32)), t(F), out,
+                            mode=umgs.DEFORM_ONE_RING)

@@ -115,3 +115,58 @@ def test_similarity_gives_scaled_rotation_per_vertex():
     delta, r, Sv = D.vertex_transforms(V, V.astype(np.float64) @ (k * Rm).T, F)
     assert np.abs(Rotation.from_rotvec(r).as_matrix() - Rm).max() < 1e-12
     assert np.abs(Sv - k * np.eye(3)).max() < 1e-12
+
+
+# -- the ONE_RING per-vertex reading (cotangent-weighted one-ring least squares) --
+
+def test_one_ring_similarity_gives_scaled_rotation():
+    # rigid motions and uniform scalings are reproduced exactly: e' = kR e and
+    # n' = kR n make the normal equations B = kR A
+    V, F = S.icosphere(2, 1.0)
+    Rm, k = _rot(12), 0.7
+    Vd = V.astype(np.float64) @ (k * Rm).T + np.array([0.3, -0.2, 0.5])
+    delta, r, Sv = D.vertex_transforms(V, Vd, F, D.ONE_RING)
+    assert np.abs(Rotation.from_rotvec(r).as_matrix() - Rm).max() < 1e-12
+    assert np.abs(Sv - k * np.eye(3)).max() < 1e-12
+
+
+def test_one_ring_is_the_weighted_least_squares_fit():
+    # against the stacked least-squares problem solved directly per vertex
+    # (rows sqrt(c) e -> sqrt(c) e' for every face edge at v, plus n -> n'),
+    # built here from the mesh without the normal-equation algebra
+    V, F = S.icosphere(1, 1.0)
+    rng = np.random.default_rng(13)
+    V = V.astype(np.float64)
+    Vd = V + 0.15 * rng.normal(size=V.shape)
+    Dv = D.one_ring_gradients(V, Vd, F)
+    for v in range(len(V)):
+        rows, rhs = [], []
+        nsum, ndsum = np.zeros(3), np.zeros(3)
+        for f in np.nonzero((F == v).any(1))[0]:
+            tri = F[f]
+            nsum += np.cross(V[tri[1]] - V[tri[0]], V[tri[2]] - V[tri[0]])
+            ndsum += np.cross(Vd[tri[1]] - Vd[tri[0]], Vd[tri[2]] - Vd[tri[0]])
+            for k in range(3):  # edge (tri[k+1], tri[k+2]) opposite corner k
+                i, j = tri[(k + 1) % 3], tri[(k + 2) % 3]
+                if v not in (i, j):
+                    continue
+                a, b = V[i] - V[tri[k]], V[j] - V[tri[k]]
+                c = max(0.0, 0.5 * np.dot(a, b) / np.linalg.norm(np.cross(a, b)))
+                o = j if v == i else i
+                rows.append(np.sqrt(c) * (V[o] - V[v]))
+                rhs.append(np.sqrt(c) * (Vd[o] - Vd[v]))
+        rows.append(nsum / np.sqrt(np.linalg.norm(nsum)))
+        rhs.append(ndsum / np.sqrt(np.linalg.norm(ndsum)))
+        X, *_ = np.linalg.lstsq(np.array(rows), np.array(rhs), rcond=None)  # rows @ X = rhs, X = D^T
+        assert np.abs(X.T - Dv[v]).max() < 1e-10
+
+
+def test_one_ring_deformation_of_gaussians_rigid():
+    V, F, mu, q, s, face, b = _setup(21)
+    Rm = _rot(22)
+    t = np.array([0.1, 0.4, -0.3])
+    Vd = V.astype(np.float64) @ Rm.T + t
+    mu2, Sig2, q2 = D.deform_gaussians(mu, q, s, face, b, V, Vd, F, method=D.ONE_RING)
+    assert np.abs(mu2 - (mu.astype(np.float64) @ Rm.T + t)).max() < 1e-10
+    Sig = cov3d_fp64(q, s)
+    assert np.abs(Sig2 - Rm @ Sig @ Rm.T).max() < 1e-12
