@@ -72,14 +72,22 @@ typedef struct {
     int32_t sh_dtype;        /* UMGS_F32 or UMGS_BF16 */
 } umgs_gaussians;
 
-/* A triangle mesh with per-vertex colour and alpha (Sec. 3.2: c_i, alpha_i). */
+/* A triangle mesh with per-vertex colour and alpha (Sec. 3.2: c_i, alpha_i),
+ * or a textured mesh: with uv and texture given, c_i at a pixel is the
+ * bilinear (clamp-to-edge) texture value at the perspective-correct
+ * interpolation of the vertex uv (texel (i, j) centred at ((i+0.5)/tex_w,
+ * (j+0.5)/tex_h)); vcolor is then unused and may be NULL.  Textured meshes
+ * render in every mode but have no backward (NOT_IMPLEMENTED). */
 typedef struct {
     const float* verts;      /* [nv,3] world positions */
     const int32_t* faces;    /* [nf,3] vertex indices in [0,nv) */
-    const float* vcolor;     /* [nv,3] linear RGB */
+    const float* vcolor;     /* [nv,3] linear RGB (NULL allowed for a textured mesh) */
     const float* valpha;     /* nullable [nv] per-vertex alpha, interpolated */
     const float* falpha;     /* nullable [nf] per-face alpha, overrides valpha */
     int64_t nv, nf;
+    const float* uv;         /* nullable [nv,2] texture coordinates */
+    const float* texture;    /* nullable [tex_h,tex_w,3] linear RGB, row-major (with uv) */
+    int32_t tex_w, tex_h;
 } umgs_mesh;
 
 /* Pinhole camera, world->camera [R|t], x right, y down, z forward;

@@ -119,7 +119,10 @@ def triangle_attributes(mesh, fid, vu, vv, vz, px, py):
     projected triangle, clamped at 0, then perspective-corrected with 1/Z and
     normalised; colour and alpha are interpolated from the vertices (alpha is
     the per-face value when given) and alpha is clamped to [0, 1].
-    Returns (colour, alpha, weights); triangle_depth gives the depth there.
+    A textured mesh (uv and texture given) takes its colour from the texture
+    at the same perspective-correct interpolation of the vertex uv
+    (sample_texture).  Returns (colour, alpha, weights); triangle_depth gives
+    the depth there.
     """
     f = np.asarray(mesh.faces, np.int64)[fid]
     u = vu[f]
@@ -136,7 +139,11 @@ def triangle_attributes(mesh, fid, vu, vv, vz, px, py):
     w = lam / z
     s = w.sum(1, keepdims=True)
     w = np.where(s > 0, w / np.where(s > 0, s, 1.0), 1.0 / 3.0)
-    col = np.einsum("fk,fkc->fc", w, np.asarray(mesh.vcolor, np.float64)[f])
+    if getattr(mesh, "texture", None) is not None:
+        uv = np.einsum("fk,fkc->fc", w, np.asarray(mesh.uv, np.float64)[f])
+        col = sample_texture(np.asarray(mesh.texture, np.float64), uv)
+    else:
+        col = np.einsum("fk,fkc->fc", w, np.asarray(mesh.vcolor, np.float64)[f])
     if mesh.falpha is not None:
         alpha = np.asarray(mesh.falpha, np.float64)[fid]
     elif mesh.valpha is not None:
@@ -144,6 +151,24 @@ def triangle_attributes(mesh, fid, vu, vv, vz, px, py):
     else:
         alpha = np.ones(len(fid))
     return col, np.clip(alpha, 0.0, 1.0), w
+
+
+def sample_texture(tex, uv):
+    """Bilinear texture lookup with clamp-to-edge addressing: texel (i, j)
+    (column i, row j) of a [TH,TW,3] texture sits at uv ((i+0.5)/TW,
+    (j+0.5)/TH); the four texels around uv are weighted by their distance."""
+    th, tw = tex.shape[:2]
+    x = uv[:, 0] * tw - 0.5
+    y = uv[:, 1] * th - 0.5
+    x0, y0 = np.floor(x), np.floor(y)
+    fx, fy = (x - x0)[:, None], (y - y0)[:, None]
+    ix0 = np.clip(x0, 0, tw - 1).astype(np.int64)
+    ix1 = np.clip(x0 + 1, 0, tw - 1).astype(np.int64)
+    iy0 = np.clip(y0, 0, th - 1).astype(np.int64)
+    iy1 = np.clip(y0 + 1, 0, th - 1).astype(np.int64)
+    top = (1 - fx) * tex[iy0, ix0] + fx * tex[iy0, ix1]
+    bot = (1 - fx) * tex[iy1, ix0] + fx * tex[iy1, ix1]
+    return (1 - fy) * top + fy * bot
 
 
 def triangle_depth(mesh, fid, vu, vv, vz, px, py):

@@ -183,7 +183,10 @@ umgs_status umgs_render(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_mesh*
     for (int m = 0; m < nmeshes; ++m) {
         const umgs_mesh& me = meshes[m];
         if (me.nf < 0 || me.nv < 0) return fail(ctx, UMGS_ERR_INVALID_ARG, "negative mesh size");
-        if (me.nf > 0 && (!me.verts || !me.faces || !me.vcolor || me.nv < 1))
+        const bool textured = me.uv || me.texture;
+        if (textured && (!me.uv || !me.texture || me.tex_w < 1 || me.tex_h < 1))
+            return fail(ctx, UMGS_ERR_INVALID_ARG, "a textured mesh needs uv, texture and tex_w, tex_h >= 1");
+        if (me.nf > 0 && (!me.verts || !me.faces || (!me.vcolor && !textured) || me.nv < 1))
             return fail(ctx, UMGS_ERR_INVALID_ARG, "mesh array is NULL");
     }
     {   // unified 32-bit primitive ids; (camera, region) keys of 22 bits
@@ -241,7 +244,11 @@ umgs_status umgs_render_backward(umgs_ctx* ctx, umgs_frame* frame, const umgs_ga
     if (nmeshes != (int32_t)frame->mesh_offset.size() || (nmeshes > 0 && !meshes))
         return fail(ctx, UMGS_ERR_INVALID_ARG, "mesh count differs from the forward call");
     int64_t nt = 0;
-    for (int m = 0; m < nmeshes; ++m) nt += meshes[m].nf;
+    for (int m = 0; m < nmeshes; ++m) {
+        nt += meshes[m].nf;
+        if (meshes[m].uv || meshes[m].texture)
+            return fail(ctx, UMGS_ERR_NOT_IMPLEMENTED, "backward of a textured mesh");
+    }
     if (nt != frame->nt) return fail(ctx, UMGS_ERR_INVALID_ARG, "triangle count differs from the forward call");
     umgs_gaussians empty;
     std::memset(&empty, 0, sizeof(empty));

@@ -64,12 +64,14 @@ __device__ __forceinline__ float half_hi(uint32_t p) { return __half2float(__ush
 //     folded into C_k, sample covered <=> all E_k >= 0
 //  u, v: unsnapped screen positions (ORIGINAL vertex order) for attributes
 //  iz: 1/Z per vertex, col: vertex colours, alpha: per-vertex alpha;
-//  const_alpha != 0 means alpha[0] is the face alpha (no interpolation).
+//  const_alpha != 0 means alpha[0] is the face alpha (no interpolation);
+//  tex > 0: a textured face, col[0..5] = the vertices' (u, v) and the colour
+//  comes from texture tex - 1 of the render's texture table.
 struct __align__(16) TRec {
     int32_t A[3];
     int32_t B[3];
     int32_t const_alpha;
-    int32_t pad0;
+    int32_t tex;
     long long C[3];
     long long pad1;
     float u[3], v[3];
@@ -82,6 +84,32 @@ struct __align__(16) TRec {
 static_assert(sizeof(GRec) == 48, "GRec size");
 static_assert(sizeof(GRec16) == 32, "GRec16 size");
 static_assert(sizeof(TRec) == 160, "TRec size");
+
+// Texture of a textured mesh: RGB float, row-major [h][w][3].
+struct DevTex {
+    const float* data;
+    int32_t w, h;
+    int64_t pad;
+};
+
+// Bilinear lookup with clamp-to-edge addressing: texel (i, j) sits at
+// ((i + 0.5) / w, (j + 0.5) / h); the four texels around (u, v) are weighted
+// by their distance.
+__device__ __forceinline__ void sample_texture(const DevTex& tx, float u, float v, float (&c)[3]) {
+    const float x = u * (float)tx.w - 0.5f, y = v * (float)tx.h - 0.5f;
+    const float x0 = floorf(x), y0 = floorf(y);
+    const float fx = x - x0, fy = y - y0;
+    const int ix0 = (int)fminf(fmaxf(x0, 0.f), (float)(tx.w - 1)), ix1 = (int)fminf(fmaxf(x0 + 1.f, 0.f), (float)(tx.w - 1));
+    const int iy0 = (int)fminf(fmaxf(y0, 0.f), (float)(tx.h - 1)), iy1 = (int)fminf(fmaxf(y0 + 1.f, 0.f), (float)(tx.h - 1));
+    const float* r0 = tx.data + (int64_t)iy0 * tx.w * 3;
+    const float* r1 = tx.data + (int64_t)iy1 * tx.w * 3;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float top = (1.f - fx) * r0[3 * ix0 + k] + fx * r0[3 * ix1 + k];
+        const float bot = (1.f - fx) * r1[3 * ix0 + k] + fx * r1[3 * ix1 + k];
+        c[k] = (1.f - fy) * top + fy * bot;
+    }
+}
 
 // Per (camera, primitive) binning info: pixel rect packed as lo | hi << 16,
 // depth bits; an empty rect (lo > hi) means culled.

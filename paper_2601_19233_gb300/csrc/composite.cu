@@ -54,7 +54,7 @@ __device__ __forceinline__ void composite_tile(
     const GRec16* __restrict__ grec16, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
     int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, float4* __restrict__ out, int32_t* __restrict__ out_last,
     float* __restrict__ out_tfin, int32_t* __restrict__ out_ntri, float4* __restrict__ stack, int cap,
-    int64_t npix, int32_t* __restrict__ need, float* __restrict__ out_depth) {
+    int64_t npix, int32_t* __restrict__ need, float* __restrict__ out_depth, const DevTex* __restrict__ textab) {
     constexpr int NT = TS * TS;
     constexpr int mode = MODE;
     const int cam = tile / tiles_per_cam;
@@ -206,8 +206,15 @@ __device__ __forceinline__ void composite_tile(
                     if (ws > 0.f) { const float is = 1.f / ws; wv[0] *= is; wv[1] *= is; wv[2] *= is; }
                     else { wv[0] = wv[1] = wv[2] = 1.f / 3.f; }
                     float col[3];
+                    if (t.tex > 0) {  // textured face: (u, v) interpolated like a colour, then sampled
+                        const float tu = wv[0] * t.col[0] + wv[1] * t.col[2] + wv[2] * t.col[4];
+                        const float tv = wv[0] * t.col[1] + wv[1] * t.col[3] + wv[2] * t.col[5];
+                        sample_texture(textab[t.tex - 1], tu, tv, col);
+                    } else {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) col[c] = wv[0] * t.col[c] + wv[1] * t.col[3 + c] + wv[2] * t.col[6 + c];
+                        for (int c = 0; c < 3; ++c)
+                            col[c] = wv[0] * t.col[c] + wv[1] * t.col[3 + c] + wv[2] * t.col[6 + c];
+                    }
                     float a = t.const_alpha ? t.alpha[0] : (wv[0] * t.alpha[0] + wv[1] * t.alpha[1] + wv[2] * t.alpha[2]);
                     a = fminf(fmaxf(a, 0.f), 1.f);
                     if (mode == UMGS_BLEND_DIRECT) {
@@ -274,13 +281,13 @@ __global__ void __launch_bounds__(TS * TS) composite_kernel(
     const GRec16* __restrict__ grec16, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
     int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, float4* __restrict__ out, int32_t* __restrict__ out_last,
     float* __restrict__ out_tfin, int32_t* __restrict__ out_ntri, float4* __restrict__ stack, int cap,
-    int64_t npix, int32_t* __restrict__ need, float* __restrict__ out_depth) {
+    int64_t npix, int32_t* __restrict__ need, float* __restrict__ out_depth, const DevTex* __restrict__ textab) {
     constexpr int NB = BatchOf<TS>::value;
     __shared__ float4 s_rec[NB][10];
     __shared__ uint32_t s_id[NB];
     __shared__ uint32_t s_wmask[NB];
     __shared__ uint8_t s_list[(TS * TS / 32) * NB];
-    composite_tile<TS, SAVE, MODE>(blockIdx.x, s_rec, s_id, s_wmask, s_list, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, out, out_last, out_tfin, out_ntri, stack, cap, npix, need, out_depth);
+    composite_tile<TS, SAVE, MODE>(blockIdx.x, s_rec, s_id, s_wmask, s_list, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, out, out_last, out_tfin, out_ntri, stack, cap, npix, need, out_depth, textab);
 }
 
 // persistent launch: resident CTAs take tiles from an atomic queue in the
@@ -292,7 +299,7 @@ __global__ void __launch_bounds__(TS * TS) composite_persistent_kernel(
     const GRec16* __restrict__ grec16, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
     int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, float4* __restrict__ out, int32_t* __restrict__ out_last,
     float* __restrict__ out_tfin, int32_t* __restrict__ out_ntri, float4* __restrict__ stack, int cap,
-    int64_t npix, int32_t* __restrict__ need, float* __restrict__ out_depth) {
+    int64_t npix, int32_t* __restrict__ need, float* __restrict__ out_depth, const DevTex* __restrict__ textab) {
     constexpr int NB = BatchOf<TS>::value;
     __shared__ float4 s_rec[NB][10];
     __shared__ uint32_t s_id[NB];
@@ -305,7 +312,7 @@ __global__ void __launch_bounds__(TS * TS) composite_persistent_kernel(
         const unsigned k = s_next;
         __syncthreads();
         if ((int64_t)k >= M) break;
-        composite_tile<TS, SAVE, MODE>((int)order[k], s_rec, s_id, s_wmask, s_list, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, out, out_last, out_tfin, out_ntri, stack, cap, npix, need, out_depth);
+        composite_tile<TS, SAVE, MODE>((int)order[k], s_rec, s_id, s_wmask, s_list, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, out, out_last, out_tfin, out_ntri, stack, cap, npix, need, out_depth, textab);
         __syncthreads();
     }
 }
@@ -362,7 +369,7 @@ cudaError_t launch_composite(umgs_frame* fr, const umgs_render_opts& opts, float
         fr->nt, fr->tiles_x, tpc, fr->W, fr->H, te, opts.bg[0], opts.bg[1], opts.bg[2], out,                      \
         fr->last.as<int32_t>(), save ? fr->tfin.as<float>() : nullptr, save ? fr->ntri.as<int32_t>() : nullptr,   \
         save ? fr->stack.as<float4>() : nullptr, fr->stack_cap, npix, fr->status.as<int32_t>() + 2,             \
-        fr->has_depth ? fr->depth.as<float>() : nullptr),                                                        \
+        fr->has_depth ? fr->depth.as<float>() : nullptr, fr->textab.as<DevTex>()),                               \
         count_launch();                                                                                         \
     else composite_kernel<TSV, SV, MV><<<M, TSV * TSV, 0, stream>>>(                                            \
         fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->mixed ? fr->grec.as<GRec16>() : nullptr,  \
@@ -370,7 +377,7 @@ cudaError_t launch_composite(umgs_frame* fr, const umgs_render_opts& opts, float
         fr->nt, fr->tiles_x, tpc, fr->W, fr->H, te, opts.bg[0], opts.bg[1], opts.bg[2], out,                      \
         fr->last.as<int32_t>(), save ? fr->tfin.as<float>() : nullptr, save ? fr->ntri.as<int32_t>() : nullptr,   \
         save ? fr->stack.as<float4>() : nullptr, fr->stack_cap, npix, fr->status.as<int32_t>() + 2,             \
-        fr->has_depth ? fr->depth.as<float>() : nullptr),                                                        \
+        fr->has_depth ? fr->depth.as<float>() : nullptr, fr->textab.as<DevTex>()),                               \
         count_launch()
     // the saved (backward) form exists for FULL only
 #define UMGS_MODES(TSV)                                                                                         \

@@ -47,6 +47,7 @@ struct umgs_frame {
     umgs::DevBuf last, status;
     umgs::DevBuf tfin, ntri, stack;   // backward state (saved renders only)
     umgs::DevBuf depth;               // expected depth per pixel (UMGS_RENDER_DEPTH renders only)
+    umgs::DevBuf textab;              // DevTex per textured mesh
     bool has_depth = false;
     umgs::DevBuf ggrad, tgrad, rerun_out;
     umgs::DevBuf fix_list;            // (camera, Gaussian) records whose conic is refined in fp64
@@ -71,7 +72,7 @@ struct umgs_frame {
         for (auto* b : {&cams, &grec, &trec, &bin, &tile_off, &pk, &pv, &pk2, &pv2, &pcnt, &poff, &tk, &tv, &tk2, &tv2,
                         &rs_hist, &rs_hist2, &rs_bsum, &rg_start, &rg_nchunk, &rg_coff, &rg_ccnt, &rg_cpre, &tl_cnt,
                         &tl_off, &tl_ids,
-                        &last, &status, &tfin, &ntri, &stack, &depth, &ggrad, &tgrad, &rerun_out, &fix_list, &ord_k, &ord_v,
+                        &last, &status, &tfin, &ntri, &stack, &depth, &textab, &ggrad, &tgrad, &rerun_out, &fix_list, &ord_k, &ord_v,
                         &ord_k2, &ord_v2})
             b->release();
     }

@@ -357,7 +357,8 @@ __device__ __forceinline__ long long ceil_div256(long long a) { return -((-a) >>
 
 __global__ void __launch_bounds__(256) setup_triangles_kernel(
     const float* __restrict__ verts, const int32_t* __restrict__ faces, const float* __restrict__ vcolor,
-    const float* __restrict__ valpha, const float* __restrict__ falpha, int64_t nv, int64_t nf,
+    const float* __restrict__ valpha, const float* __restrict__ falpha, const float* __restrict__ uv, int tex,
+    int64_t nv, int64_t nf,
     int64_t tri_base /* index of this mesh's first face among all triangles */, int64_t nt_total,
     int64_t id_base /* unified id of this mesh's first face */, const DevCam* __restrict__ cams, int ncams,
     int ts, int tiles_x, int tiles_per_cam, TRec* __restrict__ trec, BinInfo* __restrict__ bin,
@@ -381,10 +382,20 @@ __global__ void __launch_bounds__(256) setup_triangles_kernel(
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            P[k][d] = verts[3 * (int64_t)vid[k] + d];
-            col[3 * k + d] = vcolor[3 * (int64_t)vid[k] + d];
+        for (int d = 0; d < 3; ++d) P[k][d] = verts[3 * (int64_t)vid[k] + d];
+    }
+    if (uv) {  // textured: the vertices' (u, v) in col[0..5]
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            col[2 * k] = uv[2 * (int64_t)vid[k]];
+            col[2 * k + 1] = uv[2 * (int64_t)vid[k] + 1];
+            col[6 + k] = 0.f;
         }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) col[3 * k + d] = vcolor[3 * (int64_t)vid[k] + d];
     }
     int const_alpha = 1;  // 0: interpolated vertex alpha, 1: face alpha, 2: no alpha (1)
     if (falpha) { al[0] = al[1] = al[2] = falpha[f]; }
@@ -445,7 +456,8 @@ __global__ void __launch_bounds__(256) setup_triangles_kernel(
 #pragma unroll
         for (int k = 0; k < 9; ++k) t.col[k] = col[k];
         t.const_alpha = const_alpha;
-        t.pad0 = 0; t.pad1 = 0;
+        t.tex = uv ? tex + 1 : 0;
+        t.pad1 = 0;
 #pragma unroll
         t.rx = bi.rx;
         t.ry = bi.ry;
@@ -1116,13 +1128,26 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
         }
         UMGS_TRY(cudaGetLastError());
     }
+    // texture table of the textured meshes (uploaded like the cameras)
+    std::vector<DevTex> texs;
+    std::vector<int> mesh_tex(std::max(1, (int)nmeshes), -1);
+    for (int m = 0; m < nmeshes; ++m)
+        if (meshes[m].uv && meshes[m].texture) {
+            mesh_tex[m] = (int)texs.size();
+            texs.push_back(DevTex{meshes[m].texture, meshes[m].tex_w, meshes[m].tex_h, 0});
+        }
+    UMGS_TRY(fr->textab.reserve(sizeof(DevTex) * std::max<size_t>(1, texs.size())));
+    if (!texs.empty() && !fr->capture)
+        UMGS_TRY(cudaMemcpyAsync(fr->textab.ptr, texs.data(), sizeof(DevTex) * texs.size(), cudaMemcpyHostToDevice,
+                                 stream));
     int64_t tri_base = 0;
     for (int m = 0; m < nmeshes; ++m) {
         const umgs_mesh& me = meshes[m];
         if (me.nf > 0) {
             StageTimer tm(ctx, UMGS_STAGE_SETUP_TRIANGLES, stream);
             setup_triangles_kernel<<<grid_for(me.nf, 256), 256, 0, stream>>>(
-                me.verts, me.faces, me.vcolor, me.valpha, me.falpha, me.nv, me.nf, tri_base, Nt, Ng + tri_base,
+                me.verts, me.faces, me.vcolor, me.valpha, me.falpha, mesh_tex[m] >= 0 ? me.uv : nullptr,
+                mesh_tex[m], me.nv, me.nf, tri_base, Nt, Ng + tri_base,
                 dcams, ncams, ts, tiles_x, tiles_per_cam, fr->trec.as<TRec>(), fr->bin.as<BinInfo>(), Ntot,
                 fr->status.as<int32_t>()), count_launch();
             UMGS_TRY(cudaGetLastError());

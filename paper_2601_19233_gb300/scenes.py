@@ -62,6 +62,8 @@ class Mesh:
     vcolor: np.ndarray           # f32 [V,3]
     valpha: np.ndarray | None = None  # f32 [V]
     falpha: np.ndarray | None = None  # f32 [F] (overrides valpha)
+    uv: np.ndarray | None = None       # f32 [V,2] texture coordinates (with `texture`)
+    texture: np.ndarray | None = None  # f32 [TH,TW,3] RGB; when given, c_i is sampled from it
 
     @property
     def nv(self) -> int:

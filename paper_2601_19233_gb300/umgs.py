@@ -46,7 +46,8 @@ class CGaussians(ctypes.Structure):
 class CMesh(ctypes.Structure):
     _fields_ = [("verts", ctypes.c_void_p), ("faces", ctypes.c_void_p), ("vcolor", ctypes.c_void_p),
                 ("valpha", ctypes.c_void_p), ("falpha", ctypes.c_void_p), ("nv", ctypes.c_int64),
-                ("nf", ctypes.c_int64)]
+                ("nf", ctypes.c_int64), ("uv", ctypes.c_void_p), ("texture", ctypes.c_void_p),
+                ("tex_w", ctypes.c_int32), ("tex_h", ctypes.c_int32)]
 
 
 class CCamera(ctypes.Structure):
@@ -267,10 +268,13 @@ class DevMesh:
     vcolor: torch.Tensor
     valpha: torch.Tensor | None = None
     falpha: torch.Tensor | None = None
+    uv: torch.Tensor | None = None       # [nv,2] texture coordinates
+    texture: torch.Tensor | None = None  # [TH,TW,3] RGB
 
     def c(self):
+        th, tw = (int(self.texture.shape[0]), int(self.texture.shape[1])) if self.texture is not None else (0, 0)
         return CMesh(_ptr(self.verts), _ptr(self.faces), _ptr(self.vcolor), _ptr(self.valpha), _ptr(self.falpha),
-                     int(self.verts.shape[0]), int(self.faces.shape[0]))
+                     int(self.verts.shape[0]), int(self.faces.shape[0]), _ptr(self.uv), _ptr(self.texture), tw, th)
 
 
 def camera_struct(cam) -> CCamera:
@@ -299,7 +303,8 @@ def gaussians_to_device(g, device="cuda", sh_dtype=torch.float32) -> DevGaussian
 
 def mesh_to_device(m, device="cuda") -> DevMesh:
     return DevMesh(_t(m.verts, device), _t(m.faces.astype(np.int32), device), _t(m.vcolor, device),
-                   _t(m.valpha, device), _t(m.falpha, device))
+                   _t(m.valpha, device), _t(m.falpha, device), _t(getattr(m, "uv", None), device),
+                   _t(getattr(m, "texture", None), device))
 
 
 def render_opts(tile_size=16, blend_mode=BLEND_FULL, t_eps=1e-4, bg=(0.0, 0.0, 0.0), save=False,
