@@ -85,6 +85,16 @@ static_assert(sizeof(GRec) == 48, "GRec size");
 static_assert(sizeof(GRec16) == 32, "GRec16 size");
 static_assert(sizeof(TRec) == 160, "TRec size");
 
+// Programmatic dependent launch (the kernels of a render are launched with
+// programmatic stream serialisation): wait until the preceding kernel of the
+// stream has finished and its writes are visible, then let the next kernel's
+// blocks be scheduled while this one runs.  Without a programmatic
+// predecessor the wait returns at once.
+__device__ __forceinline__ void pdl_enter() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Texture of a textured mesh: RGB float, row-major [h][w][3].
 struct DevTex {
     const float* data;

@@ -282,6 +282,7 @@ __global__ void __launch_bounds__(TS * TS) composite_kernel(
     int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, float4* __restrict__ out, int32_t* __restrict__ out_last,
     float* __restrict__ out_tfin, int32_t* __restrict__ out_ntri, float4* __restrict__ stack, int cap,
     int64_t npix, int32_t* __restrict__ need, float* __restrict__ out_depth, const DevTex* __restrict__ textab) {
+    pdl_enter();
     constexpr int NB = BatchOf<TS>::value;
     __shared__ float4 s_rec[NB][10];
     __shared__ uint32_t s_id[NB];
@@ -300,6 +301,7 @@ __global__ void __launch_bounds__(TS * TS) composite_persistent_kernel(
     int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, float4* __restrict__ out, int32_t* __restrict__ out_last,
     float* __restrict__ out_tfin, int32_t* __restrict__ out_ntri, float4* __restrict__ stack, int cap,
     int64_t npix, int32_t* __restrict__ need, float* __restrict__ out_depth, const DevTex* __restrict__ textab) {
+    pdl_enter();
     constexpr int NB = BatchOf<TS>::value;
     __shared__ float4 s_rec[NB][10];
     __shared__ uint32_t s_id[NB];
@@ -320,6 +322,7 @@ __global__ void __launch_bounds__(TS * TS) composite_persistent_kernel(
 // tile order for the persistent launch: key = 0xffff - min(list length, 0xffff)
 __global__ void tile_order_keys_kernel(const int64_t* __restrict__ off, int64_t M, uint32_t* __restrict__ k,
                                        uint32_t* __restrict__ v, uint32_t* __restrict__ m_dev) {
+    pdl_enter();
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t == 0) *m_dev = (uint32_t)M;
     if (t >= M) return;
@@ -351,8 +354,8 @@ cudaError_t launch_composite(umgs_frame* fr, const umgs_render_opts& opts, float
         if ((e = fr->ord_v2.reserve(sizeof(uint32_t) * M)) != cudaSuccess) return e;
         uint32_t* mdev = reinterpret_cast<uint32_t*>(fr->status.as<int32_t>() + 4);
         work = reinterpret_cast<unsigned*>(fr->status.as<int32_t>() + 8);
-        tile_order_keys_kernel<<<(M + 255) / 256, 256, 0, stream>>>(fr->tile_off.as<int64_t>(), M, fr->ord_k.as<uint32_t>(),
-                                                                     fr->ord_v.as<uint32_t>(), mdev), count_launch();
+        launch_pdl(tile_order_keys_kernel, (M + 255) / 256, 256, 0, stream, fr->tile_off.as<int64_t>(), M, fr->ord_k.as<uint32_t>(),
+                                                                     fr->ord_v.as<uint32_t>(), mdev);
         uint32_t* rk = nullptr;
         uint32_t* rv = nullptr;
         if ((e = radix_sort_pairs(fr, fr->ord_k.as<uint32_t>(), fr->ord_v.as<uint32_t>(), fr->ord_k2.as<uint32_t>(),
@@ -363,22 +366,20 @@ cudaError_t launch_composite(umgs_frame* fr, const umgs_render_opts& opts, float
         nblk = opts.sched * fr->ctx->num_sms;
     }
 #define UMGS_LAUNCH(TSV, SV, MV)                                                                                \
-    if (persist) composite_persistent_kernel<TSV, SV, MV><<<nblk, TSV * TSV, 0, stream>>>(order, work, M,      \
+    if (persist) launch_pdl(composite_persistent_kernel<TSV, SV, MV>, nblk, TSV * TSV, 0, stream, order, work, M,      \
         fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->mixed ? fr->grec.as<GRec16>() : nullptr,  \
         fr->trec.as<TRec>(), fr->ng,                                                                            \
         fr->nt, fr->tiles_x, tpc, fr->W, fr->H, te, opts.bg[0], opts.bg[1], opts.bg[2], out,                      \
         fr->last.as<int32_t>(), save ? fr->tfin.as<float>() : nullptr, save ? fr->ntri.as<int32_t>() : nullptr,   \
         save ? fr->stack.as<float4>() : nullptr, fr->stack_cap, npix, fr->status.as<int32_t>() + 2,             \
-        fr->has_depth ? fr->depth.as<float>() : nullptr, fr->textab.as<DevTex>()),                               \
-        count_launch();                                                                                         \
-    else composite_kernel<TSV, SV, MV><<<M, TSV * TSV, 0, stream>>>(                                            \
+        fr->has_depth ? fr->depth.as<float>() : nullptr, fr->textab.as<DevTex>());                                                                                         \
+    else launch_pdl(composite_kernel<TSV, SV, MV>, M, TSV * TSV, 0, stream,                                             \
         fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->mixed ? fr->grec.as<GRec16>() : nullptr,  \
         fr->trec.as<TRec>(), fr->ng,                                                                            \
         fr->nt, fr->tiles_x, tpc, fr->W, fr->H, te, opts.bg[0], opts.bg[1], opts.bg[2], out,                      \
         fr->last.as<int32_t>(), save ? fr->tfin.as<float>() : nullptr, save ? fr->ntri.as<int32_t>() : nullptr,   \
         save ? fr->stack.as<float4>() : nullptr, fr->stack_cap, npix, fr->status.as<int32_t>() + 2,             \
-        fr->has_depth ? fr->depth.as<float>() : nullptr, fr->textab.as<DevTex>()),                               \
-        count_launch()
+        fr->has_depth ? fr->depth.as<float>() : nullptr, fr->textab.as<DevTex>())
     // the saved (backward) form exists for FULL only
 #define UMGS_MODES(TSV)                                                                                         \
     if (save) { UMGS_LAUNCH(TSV, true, UMGS_BLEND_FULL); }                                                      \

@@ -84,6 +84,30 @@ struct umgs_frame {
 extern std::atomic<long long> g_kernel_launches;
 inline void count_launch(long long n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
 
+namespace umgs {
+// Launch `kernel` on `s` with programmatic stream serialisation: it may be
+// scheduled before the preceding kernel of the stream finishes and must call
+// pdl_enter() before touching anything that kernel writes.  Errors surface
+// through cudaGetLastError like a <<< >>> launch.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args... args) {
+    static_assert(sizeof...(KArgs) == sizeof...(Args), "kernel argument count");
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    count_launch();
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+}  // namespace umgs
+
 // Per-stage CUDA-event timing (umgs_profile_enable / umgs_profile_read).
 struct StageProfiler {
     bool on = false;

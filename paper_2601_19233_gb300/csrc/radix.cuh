@@ -60,6 +60,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan_256(uint32_t x, uint32_
 static __global__ void __launch_bounds__(kRsThreads) scan_reduce_kernel(const uint32_t* __restrict__ in, int64_t n,
                                                                          uint32_t* __restrict__ bsum,
                                                                          uint32_t* __restrict__ overflow) {
+    pdl_enter();
     __shared__ uint32_t s_warp[32];
     const int64_t base = (int64_t)blockIdx.x * kRsTile;
     uint64_t s = 0;
@@ -80,6 +81,7 @@ static __global__ void __launch_bounds__(kRsThreads) scan_reduce_kernel(const ui
 static __global__ void __launch_bounds__(1024) scan_blocks_kernel(uint32_t* __restrict__ bsum, int nb,
                                                                  uint32_t* __restrict__ total,
                                                                  uint32_t* __restrict__ overflow) {
+    pdl_enter();
     __shared__ uint32_t s_warp[32];
     __shared__ unsigned long long s_tot64[32];
     const int per = (nb + 1023) / 1024;
@@ -123,6 +125,7 @@ static __global__ void __launch_bounds__(1024) scan_blocks_kernel(uint32_t* __re
 static __global__ void __launch_bounds__(kRsThreads) scan_apply_kernel(const uint32_t* __restrict__ in, int64_t n,
                                                                         const uint32_t* __restrict__ bsum,
                                                                         uint32_t* __restrict__ out) {
+    pdl_enter();
     __shared__ uint32_t s_warp[32];
     // each thread handles kRsItems consecutive elements
     const int64_t base = (int64_t)blockIdx.x * kRsTile + (int64_t)threadIdx.x * kRsItems;
@@ -151,6 +154,7 @@ static __global__ void __launch_bounds__(kRsThreads) radix_upsweep_kernel(const 
                                                                           const uint32_t* __restrict__ n_dev,
                                                                           int64_t n_cap, int shift, int nblocks,
                                                                           uint32_t* __restrict__ hist) {
+    pdl_enter();
     __shared__ uint32_t cnt[256];
     const int64_t n = min((int64_t)*n_dev, n_cap);
     const int64_t base = (int64_t)blockIdx.x * (kRsThreads * ITEMS);
@@ -173,6 +177,7 @@ static __global__ void __launch_bounds__(kRsThreads) radix_hist_scan_kernel(uint
                                                                             const uint32_t* __restrict__ n_dev,
                                                                             int64_t n_cap, int tile,
                                                                             uint32_t* __restrict__ dtotal) {
+    pdl_enter();
     __shared__ uint32_t s_warp[32];
     uint32_t* h = hist + (int64_t)blockIdx.x * nblocks;
     const int64_t n = min((int64_t)*n_dev, n_cap);
@@ -199,6 +204,7 @@ static __global__ void __launch_bounds__(kRsThreads) radix_downsweep_kernel(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, const uint32_t* __restrict__ n_dev,
     int64_t n_cap, int shift, int nblocks, const uint32_t* __restrict__ hist, const uint32_t* __restrict__ dtotal,
     uint32_t* __restrict__ kout, uint32_t* __restrict__ vout) {
+    pdl_enter();
     const int64_t n = min((int64_t)*n_dev, n_cap);
     constexpr int NW = kRsThreads / 32;
     __shared__ uint32_t wcnt[NW][256];

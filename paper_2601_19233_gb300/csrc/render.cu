@@ -122,6 +122,7 @@ __global__ void refine_conics_kernel(const float* __restrict__ means, const floa
                                      int64_t ntot, const unsigned* __restrict__ fix_count,
                                      const int64_t* __restrict__ fix_list, unsigned fix_cap, GRec* __restrict__ grec,
                                      GRec16* __restrict__ grec16) {
+    pdl_enter();
     const unsigned cnt = *fix_count;
     const bool overflow = cnt > fix_cap;
     const int64_t total = overflow ? N * ncams : (int64_t)cnt;
@@ -153,6 +154,7 @@ __global__ void __launch_bounds__(256, 2) project_gaussians_kernel(
     int ts, int tiles_x, int tiles_per_cam, GRec* __restrict__ grec, GRec16* __restrict__ grec16,
     BinInfo* __restrict__ bin, int64_t ntot_prims, unsigned* __restrict__ fix_count, int64_t* __restrict__ fix_list,
     unsigned fix_cap) {
+    pdl_enter();
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N) return;
     const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
@@ -257,6 +259,7 @@ __global__ void __launch_bounds__(256) shade_gaussians_kernel(const float* __res
                                                               int sh_dtype, int64_t N, const DevCam* __restrict__ cams,
                                                               int ncams, const BinInfo* __restrict__ bin, int64_t ntot,
                                                               GRec* __restrict__ grec, GRec16* __restrict__ grec16) {
+    pdl_enter();
     constexpr int K = (DEG + 1) * (DEG + 1);
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -363,6 +366,7 @@ __global__ void __launch_bounds__(256) setup_triangles_kernel(
     int64_t id_base /* unified id of this mesh's first face */, const DevCam* __restrict__ cams, int ncams,
     int ts, int tiles_x, int tiles_per_cam, TRec* __restrict__ trec, BinInfo* __restrict__ bin,
     int64_t ntot_prims, int32_t* __restrict__ status) {
+    pdl_enter();
     const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (f >= nf) return;
     int vid[3] = {faces[3 * f], faces[3 * f + 1], faces[3 * f + 2]};
@@ -494,6 +498,7 @@ constexpr int kRegionThreads = 256;
 
 __global__ void prim_keys_kernel(const BinInfo* __restrict__ bin, int64_t n, uint32_t* __restrict__ pk,
                                  uint32_t* __restrict__ pv, uint32_t* __restrict__ n_dev) {
+    pdl_enter();
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i == 0) *n_dev = (uint32_t)n;
     if (i >= n) return;
@@ -509,6 +514,7 @@ __global__ void __launch_bounds__(256) region_counts_kernel(const BinInfo* __res
                                                             const uint32_t* __restrict__ pv, int64_t n, int ts,
                                                             uint32_t* __restrict__ rcnt,
                                                             unsigned long long* __restrict__ ktotal) {
+    pdl_enter();
     __shared__ unsigned long long s_sum[8];
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     unsigned long long tiles = 0;
@@ -553,6 +559,7 @@ __global__ void __launch_bounds__(256) emit_region_pairs_kernel(
     int64_t ntot, int ts, int regions_x, int regions_per_cam, const unsigned long long* __restrict__ ktotal,
     int64_t kcap, uint32_t* __restrict__ rk, uint32_t* __restrict__ rv, int64_t rcap,
     const uint32_t* __restrict__ rn_scan, uint32_t* __restrict__ rn, int32_t* __restrict__ status) {
+    pdl_enter();
     const unsigned long long K = *ktotal;
     const bool over = K > (unsigned long long)kcap || K >= 0xffffffffull || (int64_t)*rn_scan > rcap;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -632,6 +639,7 @@ __global__ void __launch_bounds__(256) emit_region_pairs_kernel(
 // predecessor's writes the starts of the regions in between.
 __global__ void region_starts_kernel(const uint32_t* __restrict__ rk, const uint32_t* __restrict__ rn, int64_t rcap,
                                      int64_t R, uint32_t* __restrict__ rstart) {
+    pdl_enter();
     const int64_t n = min((int64_t)*rn, rcap);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -692,6 +700,7 @@ constexpr int64_t kSmallScanMax = 1 << 15;
 template <class In, class Out>
 __global__ void __launch_bounds__(1024) scan_small_kernel(In in, int64_t n, Out* __restrict__ out,
                                                           uint32_t* __restrict__ total) {
+    pdl_enter();
     __shared__ uint32_t s_warp[32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     uint32_t carry = 0;
@@ -729,6 +738,7 @@ __global__ void __launch_bounds__(1024) scan_small_kernel(In in, int64_t n, Out*
 // Per-index values of an input functor (for the multi-block paths).
 template <class In>
 __global__ void gather_in_kernel(In in, int64_t n, uint32_t* __restrict__ out) {
+    pdl_enter();
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) out[i] = in(i);
 }
@@ -803,6 +813,7 @@ __global__ void __launch_bounds__(kRegionThreads) region_count_kernel(
     const uint32_t* __restrict__ rk, const uint32_t* __restrict__ coff, const uint32_t* __restrict__ rstart,
     const uint32_t* __restrict__ nblk_dev, int64_t R, int regions_x, int regions_per_cam, int tiles_x,
     int tiles_per_cam, uint32_t* __restrict__ ccnt) {
+    pdl_enter();
     __shared__ uint32_t s_cnt[kRegionThreads / 32][32];
     if (blockIdx.x >= *nblk_dev) return;
     const RegionChunk c = region_chunk(coff, rstart, R, blockIdx.x, regions_x, regions_per_cam, tiles_x,
@@ -842,6 +853,7 @@ __global__ void __launch_bounds__(kRegionThreads) region_fill_kernel(
     const uint32_t* __restrict__ rstart, const uint32_t* __restrict__ nblk_dev, int64_t R, int regions_x,
     int regions_per_cam, int tiles_x, int tiles_y, int tiles_per_cam, const int64_t* __restrict__ tile_off,
     const uint32_t* __restrict__ ccnt, const uint32_t* __restrict__ cpre, uint32_t* __restrict__ ids) {
+    pdl_enter();
     constexpr int NW = kRegionThreads / 32;
     __shared__ uint32_t s_bal[2][NW][32];
     __shared__ uint32_t s_pre[2][NW][32];
@@ -921,6 +933,7 @@ __global__ void __launch_bounds__(kRegionThreads) region_fill_kernel(
 // tile_off (int64, M + 1 entries) from a 32-bit tile scan and its total.
 __global__ void tile_off_kernel(const uint32_t* __restrict__ toff, const uint32_t* __restrict__ total, int64_t M,
                                 int64_t* __restrict__ off) {
+    pdl_enter();
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t < M) off[t] = toff[t];
     else if (t == M) off[M] = *total;
@@ -950,10 +963,9 @@ cudaError_t scan_u32(umgs_frame* fr, const uint32_t* in, uint32_t* out, int64_t 
     if (e != cudaSuccess) return e;
     if (nb > (1 << 22)) return cudaErrorInvalidValue;
     uint32_t* overflow = reinterpret_cast<uint32_t*>(fr->status.as<int32_t>() + 9);
-    scan_reduce_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(in, n, fr->rs_bsum.as<uint32_t>(), overflow),
-        count_launch();
-    scan_blocks_kernel<<<1, 1024, 0, s>>>(fr->rs_bsum.as<uint32_t>(), (int)nb, total, overflow), count_launch();
-    scan_apply_kernel<<<(unsigned)nb, kRsThreads, 0, s>>>(in, n, fr->rs_bsum.as<uint32_t>(), out), count_launch();
+    launch_pdl(scan_reduce_kernel, (unsigned)nb, kRsThreads, 0, s, in, n, fr->rs_bsum.as<uint32_t>(), overflow);
+    launch_pdl(scan_blocks_kernel, 1, 1024, 0, s, fr->rs_bsum.as<uint32_t>(), (int)nb, total, overflow);
+    launch_pdl(scan_apply_kernel, (unsigned)nb, kRsThreads, 0, s, in, n, fr->rs_bsum.as<uint32_t>(), out);
     return cudaGetLastError();
 }
 
@@ -975,20 +987,17 @@ cudaError_t radix_sort_pairs(umgs_frame* fr, uint32_t* k, uint32_t* v, uint32_t*
     uint32_t* dtotal = fr->rs_hist2.as<uint32_t>();
     for (int shift = lo; shift < lo + bits; shift += 8) {
         if (items == 8) {
-            radix_upsweep_kernel<8><<<(unsigned)nb, kRsThreads, 0, s>>>(k, n_dev, n_cap, shift, (int)nb, hist),
-                count_launch();
+            launch_pdl(radix_upsweep_kernel<8>, (unsigned)nb, kRsThreads, 0, s, k, n_dev, n_cap, shift, (int)nb, hist);
         } else {
-            radix_upsweep_kernel<16><<<(unsigned)nb, kRsThreads, 0, s>>>(k, n_dev, n_cap, shift, (int)nb, hist),
-                count_launch();
+            launch_pdl(radix_upsweep_kernel<16>, (unsigned)nb, kRsThreads, 0, s, k, n_dev, n_cap, shift, (int)nb, hist);
         }
-        radix_hist_scan_kernel<<<256, kRsThreads, 0, s>>>(hist, (int)nb, n_dev, n_cap, kRsThreads * items, dtotal),
-            count_launch();
+        launch_pdl(radix_hist_scan_kernel, 256, kRsThreads, 0, s, hist, (int)nb, n_dev, n_cap, kRsThreads * items, dtotal);
         if (items == 8) {
-            radix_downsweep_kernel<8><<<(unsigned)nb, kRsThreads, 0, s>>>(k, v, n_dev, n_cap, shift, (int)nb, hist,
-                                                                          dtotal, k2, v2), count_launch();
+            launch_pdl(radix_downsweep_kernel<8>, (unsigned)nb, kRsThreads, 0, s, k, v, n_dev, n_cap, shift, (int)nb, hist,
+                                                                          dtotal, k2, v2);
         } else {
-            radix_downsweep_kernel<16><<<(unsigned)nb, kRsThreads, 0, s>>>(k, v, n_dev, n_cap, shift, (int)nb, hist,
-                                                                           dtotal, k2, v2), count_launch();
+            launch_pdl(radix_downsweep_kernel<16>, (unsigned)nb, kRsThreads, 0, s, k, v, n_dev, n_cap, shift, (int)nb, hist,
+                                                                           dtotal, k2, v2);
         }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -1104,16 +1113,16 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     UMGS_TRY(fr->fix_list.reserve(sizeof(int64_t) * fix_cap));
     if (Ng > 0) {
         StageTimer tm(ctx, UMGS_STAGE_PROJECT_GAUSSIANS, stream);
-        project_gaussians_kernel<<<grid_for(Ng, 256), 256, 0, stream>>>(
+        launch_pdl(project_gaussians_kernel, grid_for(Ng, 256), 256, 0, stream, 
             g->means, g->quats, g->scales, g->opacities, g->sh, g->sh_dtype, g->sh_degree, g->cov3d, Ng, dcams,
             ncams, ts, tiles_x, tiles_per_cam, fr->grec.as<GRec>(), mixed ? fr->grec.as<GRec16>() : nullptr,
             fr->bin.as<BinInfo>(), Ntot, reinterpret_cast<unsigned*>(fr->status.as<int32_t>() + 3),
-            fr->fix_list.as<int64_t>(), fix_cap), count_launch();
+            fr->fix_list.as<int64_t>(), fix_cap);
         UMGS_TRY(cudaGetLastError());
-        refine_conics_kernel<<<4 * ctx->num_sms, 128, 0, stream>>>(
+        launch_pdl(refine_conics_kernel, 4 * ctx->num_sms, 128, 0, stream, 
             g->means, g->quats, g->scales, g->cov3d, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot,
             reinterpret_cast<unsigned*>(fr->status.as<int32_t>() + 3), fr->fix_list.as<int64_t>(), fix_cap,
-            fr->grec.as<GRec>(), mixed ? fr->grec.as<GRec16>() : nullptr), count_launch();
+            fr->grec.as<GRec>(), mixed ? fr->grec.as<GRec16>() : nullptr);
         UMGS_TRY(cudaGetLastError());
     }
     if (Ng > 0) {
@@ -1121,10 +1130,10 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
         const unsigned gb = grid_for(Ng, 256);
         GRec16* g16 = mixed ? fr->grec.as<GRec16>() : nullptr;
         switch (g->sh_degree) {
-            case 0: shade_gaussians_kernel<0><<<gb, 256, 0, stream>>>(g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16), count_launch(); break;
-            case 1: shade_gaussians_kernel<1><<<gb, 256, 0, stream>>>(g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16), count_launch(); break;
-            case 2: shade_gaussians_kernel<2><<<gb, 256, 0, stream>>>(g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16), count_launch(); break;
-            default: shade_gaussians_kernel<3><<<gb, 256, 0, stream>>>(g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16), count_launch(); break;
+            case 0: launch_pdl(shade_gaussians_kernel<0>, gb, 256, 0, stream, g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16); break;
+            case 1: launch_pdl(shade_gaussians_kernel<1>, gb, 256, 0, stream, g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16); break;
+            case 2: launch_pdl(shade_gaussians_kernel<2>, gb, 256, 0, stream, g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16); break;
+            default: launch_pdl(shade_gaussians_kernel<3>, gb, 256, 0, stream, g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16); break;
         }
         UMGS_TRY(cudaGetLastError());
     }
@@ -1145,11 +1154,11 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
         const umgs_mesh& me = meshes[m];
         if (me.nf > 0) {
             StageTimer tm(ctx, UMGS_STAGE_SETUP_TRIANGLES, stream);
-            setup_triangles_kernel<<<grid_for(me.nf, 256), 256, 0, stream>>>(
+            launch_pdl(setup_triangles_kernel, grid_for(me.nf, 256), 256, 0, stream, 
                 me.verts, me.faces, me.vcolor, me.valpha, me.falpha, mesh_tex[m] >= 0 ? me.uv : nullptr,
                 mesh_tex[m], me.nv, me.nf, tri_base, Nt, Ng + tri_base,
                 dcams, ncams, ts, tiles_x, tiles_per_cam, fr->trec.as<TRec>(), fr->bin.as<BinInfo>(), Ntot,
-                fr->status.as<int32_t>()), count_launch();
+                fr->status.as<int32_t>());
             UMGS_TRY(cudaGetLastError());
         }
         tri_base += me.nf;
@@ -1177,7 +1186,7 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     uint32_t* ktot32 = status_u + 14;
     if (NR > 0) {
         StageTimer tm(ctx, UMGS_STAGE_SCAN, stream);
-        prim_keys_kernel<<<grid_for(NR, 256), 256, 0, stream>>>(fr->bin.as<BinInfo>(), NR, pk, pv, status_u + 5), count_launch();
+        launch_pdl(prim_keys_kernel, grid_for(NR, 256), 256, 0, stream, fr->bin.as<BinInfo>(), NR, pk, pv, status_u + 5);
         UMGS_TRY(cudaGetLastError());
         uint32_t* rk = nullptr;
         uint32_t* rv = nullptr;
@@ -1185,8 +1194,8 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
                                   &rv, stream));
         pk = rk;
         pv = rv;
-        region_counts_kernel<<<grid_for(NR, 256), 256, 0, stream>>>(fr->bin.as<BinInfo>(), pv, NR, ts,
-                                                                    fr->pcnt.as<uint32_t>(), ktotal), count_launch();
+        launch_pdl(region_counts_kernel, grid_for(NR, 256), 256, 0, stream, fr->bin.as<BinInfo>(), pv, NR, ts,
+                                                                    fr->pcnt.as<uint32_t>(), ktotal);
         UMGS_TRY(cudaGetLastError());
         UMGS_TRY(scan_u32(fr, fr->pcnt.as<uint32_t>(), fr->poff.as<uint32_t>(), NR, rn_scan, stream));
     }
@@ -1214,10 +1223,9 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     fr->ids = fr->tl_ids.as<uint32_t>();
     if (NR > 0) {
         StageTimer tm(ctx, UMGS_STAGE_SCATTER, stream);
-        emit_region_pairs_kernel<<<grid_for(NR, 256), 256, 0, stream>>>(
+        launch_pdl(emit_region_pairs_kernel, grid_for(NR, 256), 256, 0, stream, 
             fr->bin.as<BinInfo>(), pv, fr->poff.as<uint32_t>(), NR, Ntot, ts, regions_x, regions_per_cam, ktotal,
-            Kcap, fr->tk.as<uint32_t>(), fr->tv.as<uint32_t>(), rcap, rn_scan, rn, fr->status.as<int32_t>()),
-            count_launch();
+            Kcap, fr->tk.as<uint32_t>(), fr->tv.as<uint32_t>(), rcap, rn_scan, rn, fr->status.as<int32_t>());
         UMGS_TRY(cudaGetLastError());
     }
     {
@@ -1235,38 +1243,34 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
         uint32_t* coff = fr->rg_coff.as<uint32_t>();
         int64_t* toff64 = fr->tile_off.as<int64_t>();
         const unsigned sgrid = (unsigned)std::min<int64_t>(grid_for(std::max(rcap, R + 1), 256), 8 * ctx->num_sms);
-        region_starts_kernel<<<sgrid, 256, 0, stream>>>(rk, rn, rcap, R, rstart), count_launch();
+        launch_pdl(region_starts_kernel, sgrid, 256, 0, stream, rk, rn, rcap, R, rstart);
         UMGS_TRY(cudaGetLastError());
         if (R <= kSmallScanMax) {
-            scan_small_kernel<ChunksIn, uint32_t><<<1, 1024, 0, stream>>>(ChunksIn{rstart}, R, coff, nblk), count_launch();
+            launch_pdl(scan_small_kernel<ChunksIn, uint32_t>, 1, 1024, 0, stream, ChunksIn{rstart}, R, coff, nblk);
         } else {
-            gather_in_kernel<ChunksIn><<<grid_for(R, 256), 256, 0, stream>>>(ChunksIn{rstart}, R,
-                                                                             fr->rg_nchunk.as<uint32_t>()), count_launch();
+            launch_pdl(gather_in_kernel<ChunksIn>, grid_for(R, 256), 256, 0, stream, ChunksIn{rstart}, R,
+                                                                             fr->rg_nchunk.as<uint32_t>());
             UMGS_TRY(scan_u32(fr, fr->rg_nchunk.as<uint32_t>(), coff, R, nblk, stream));
         }
         UMGS_TRY(cudaGetLastError());
-        region_count_kernel<<<(unsigned)nblk_max, kRegionThreads, 0, stream>>>(
-            rk, coff, rstart, nblk, R, regions_x, regions_per_cam, tiles_x, tiles_per_cam, fr->rg_ccnt.as<uint32_t>()),
-            count_launch();
+        launch_pdl(region_count_kernel, (unsigned)nblk_max, kRegionThreads, 0, stream, 
+            rk, coff, rstart, nblk, R, regions_x, regions_per_cam, tiles_x, tiles_per_cam, fr->rg_ccnt.as<uint32_t>());
         UMGS_TRY(cudaGetLastError());
         const TileTotalIn tin{coff, nblk, fr->rg_ccnt.as<uint32_t>(), fr->rg_cpre.as<uint32_t>(), R, tiles_x,
                               tiles_per_cam, regions_x, regions_per_cam};
-        gather_in_kernel<TileTotalIn><<<grid_for(M, 256), 256, 0, stream>>>(tin, M, fr->tl_cnt.as<uint32_t>()),
-            count_launch();
+        launch_pdl(gather_in_kernel<TileTotalIn>, grid_for(M, 256), 256, 0, stream, tin, M, fr->tl_cnt.as<uint32_t>());
         UMGS_TRY(cudaGetLastError());
         if (M <= kSmallScanMax) {
-            scan_small_kernel<ArrayIn, int64_t><<<1, 1024, 0, stream>>>(ArrayIn{fr->tl_cnt.as<uint32_t>()}, M, toff64,
-                                                                        ktot32), count_launch();
+            launch_pdl(scan_small_kernel<ArrayIn, int64_t>, 1, 1024, 0, stream, ArrayIn{fr->tl_cnt.as<uint32_t>()}, M, toff64,
+                                                                        ktot32);
         } else {
             UMGS_TRY(scan_u32(fr, fr->tl_cnt.as<uint32_t>(), fr->tl_off.as<uint32_t>(), M, ktot32, stream));
-            tile_off_kernel<<<grid_for(M + 1, 256), 256, 0, stream>>>(fr->tl_off.as<uint32_t>(), ktot32, M, toff64),
-                count_launch();
+            launch_pdl(tile_off_kernel, grid_for(M + 1, 256), 256, 0, stream, fr->tl_off.as<uint32_t>(), ktot32, M, toff64);
         }
         UMGS_TRY(cudaGetLastError());
-        region_fill_kernel<<<(unsigned)nblk_max, kRegionThreads, 0, stream>>>(
+        launch_pdl(region_fill_kernel, (unsigned)nblk_max, kRegionThreads, 0, stream, 
             rk, rv, coff, rstart, nblk, R, regions_x, regions_per_cam, tiles_x, tiles_y, tiles_per_cam, toff64,
-            fr->rg_ccnt.as<uint32_t>(), fr->rg_cpre.as<uint32_t>(), fr->tl_ids.as<uint32_t>()),
-            count_launch();
+            fr->rg_ccnt.as<uint32_t>(), fr->rg_cpre.as<uint32_t>(), fr->tl_ids.as<uint32_t>());
         UMGS_TRY(cudaGetLastError());
     }
     UMGS_TRY(fr->last.reserve(sizeof(int32_t) * (int64_t)ncams * W * H));
