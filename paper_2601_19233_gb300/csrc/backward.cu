@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(TS * TS, TS == 16 ? 4 : 1) composite_bwd_kerne
     float bg1, float bg2, const float4* __restrict__ dout, const int32_t* __restrict__ last,
     const float* __restrict__ tfin, const int32_t* __restrict__ ntri, const float4* __restrict__ stack, int64_t npix,
     float* __restrict__ ggrad, float* __restrict__ tgrad) {
+    pdl_enter();
     constexpr int NT = TS * TS;
     constexpr int NW = NT / 32;
     constexpr int kBatchB = BwdBatch<TS>::value;
@@ -429,6 +430,7 @@ __global__ void __launch_bounds__(kProjBwdWarps * 32) project_gaussians_bwd_kern
     const DevCam* __restrict__ cams, int ncams, const BinInfo* __restrict__ bin, int64_t ntot,
     const float* __restrict__ ggrad, float* __restrict__ d_means, float* __restrict__ d_quats,
     float* __restrict__ d_scales, float* __restrict__ d_opac, float* __restrict__ d_sh, float* __restrict__ d_cov) {
+    pdl_enter();
     constexpr int K = (DEG + 1) * (DEG + 1);
     constexpr int K3 = 3 * K;
     constexpr int KP = K3 | 1;
@@ -626,6 +628,7 @@ __global__ void __launch_bounds__(256) setup_triangles_bwd_kernel(
     const DevCam* __restrict__ cams, int ncams, const BinInfo* __restrict__ bin, int64_t ntot,
     const float* __restrict__ tgrad, float* __restrict__ d_verts, float* __restrict__ d_vcolor,
     float* __restrict__ d_valpha, float* __restrict__ d_falpha) {
+    pdl_enter();
     const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (f >= nf) return;
     const int vid[3] = {faces[3 * f], faces[3 * f + 1], faces[3 * f + 2]};
@@ -698,11 +701,11 @@ umgs_status render_backward(umgs_ctx* ctx, umgs_frame* fr, const umgs_gaussians*
         static const cudaError_t attr##TSV = cudaFuncSetAttribute(                                               \
             composite_bwd_kernel<TSV>, cudaFuncAttributeMaxDynamicSharedMemorySize, bwd_smem_bytes<TSV>());      \
         UMGS_TRY(attr##TSV);                                                                                     \
-        composite_bwd_kernel<TSV><<<M, TSV * TSV, bwd_smem_bytes<TSV>(), stream>>>(                              \
+        launch_pdl(composite_bwd_kernel<TSV>, M, TSV * TSV, bwd_smem_bytes<TSV>(), stream,                               \
             fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->trec.as<TRec>(), Ng, Nt,               \
             fr->tiles_x, tpc, fr->W, fr->H, fr->bg[0], fr->bg[1], fr->bg[2], dout, fr->last.as<int32_t>(),         \
             fr->tfin.as<float>(), fr->ntri.as<int32_t>(), fr->stack.as<float4>(), npix, fr->ggrad.as<float>(),     \
-            fr->tgrad.as<float>()), count_launch()
+            fr->tgrad.as<float>())
         if (fr->tile == 16) { UMGS_LAUNCH(16); }
         else if (fr->tile == 8) { UMGS_LAUNCH(8); }
         else { UMGS_LAUNCH(32); }
@@ -713,10 +716,10 @@ umgs_status render_backward(umgs_ctx* ctx, umgs_frame* fr, const umgs_gaussians*
     if (Ng > 0 && gg) {
         // every element of the requested outputs is written by the kernel
 #define UMGS_LAUNCH(D)                                                                                          \
-        project_gaussians_bwd_kernel<D><<<grid_for(Ng, kProjBwdWarps * 32), kProjBwdWarps * 32, 0, stream>>>(                                \
+        launch_pdl(project_gaussians_bwd_kernel<D>, grid_for(Ng, kProjBwdWarps * 32), kProjBwdWarps * 32, 0, stream,                                 \
             g->means, g->quats, g->scales, g->sh, g->sh_dtype, g->cov3d, Ng, fr->cams.as<DevCam>(), fr->ncams,      \
             fr->bin.as<BinInfo>(), Ntot, fr->ggrad.as<float>(), gg->means, g->cov3d ? nullptr : gg->quats,         \
-            g->cov3d ? nullptr : gg->scales, gg->opacities, gg->sh, g->cov3d ? gg->cov3d : nullptr), count_launch()
+            g->cov3d ? nullptr : gg->scales, gg->opacities, gg->sh, g->cov3d ? gg->cov3d : nullptr)
         switch (g->sh_degree) {
             case 0: UMGS_LAUNCH(0); break;
             case 1: UMGS_LAUNCH(1); break;
@@ -736,10 +739,10 @@ umgs_status render_backward(umgs_ctx* ctx, umgs_frame* fr, const umgs_gaussians*
             if (o.valpha) UMGS_TRY(cudaMemsetAsync(o.valpha, 0, sizeof(float) * me.nv, stream));
             if (o.falpha) UMGS_TRY(cudaMemsetAsync(o.falpha, 0, sizeof(float) * me.nf, stream));
             if (me.nf > 0) {
-                setup_triangles_bwd_kernel<<<grid_for(me.nf, 256), 256, 0, stream>>>(
+                launch_pdl(setup_triangles_bwd_kernel, grid_for(me.nf, 256), 256, 0, stream, 
                     me.verts, me.faces, me.valpha, me.falpha, me.nf, tri_base, Nt, Ng + tri_base, fr->cams.as<DevCam>(),
                     fr->ncams, fr->bin.as<BinInfo>(), Ntot, fr->tgrad.as<float>(), o.verts, o.vcolor, o.valpha,
-                    o.falpha), count_launch();
+                    o.falpha);
                 UMGS_TRY(cudaGetLastError());
             }
         }

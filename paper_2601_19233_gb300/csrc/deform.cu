@@ -84,6 +84,7 @@ __device__ __forceinline__ void matmul3(const float A[9], const float B[9], floa
 __global__ void __launch_bounds__(256) face_gradients_kernel(const float* __restrict__ V, const float* __restrict__ Vd,
                                                              const int32_t* __restrict__ F, int64_t nv, int64_t nf,
                                                              float* __restrict__ vacc, int32_t* __restrict__ status) {
+    pdl_enter();
     const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (f >= nf) return;
     const int i0 = F[3 * f], i1 = F[3 * f + 1], i2 = F[3 * f + 2];
@@ -237,6 +238,7 @@ __device__ __forceinline__ void write_vertex_row(const float (&D)[9], const floa
 __global__ void __launch_bounds__(256) vertex_xforms_kernel(const float* __restrict__ V, const float* __restrict__ Vd,
                                                             const float* __restrict__ vacc, int64_t nv,
                                                             float* __restrict__ vtab) {
+    pdl_enter();
     const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (v >= nv) return;
     const float* a = vacc + 10 * v;
@@ -258,6 +260,7 @@ constexpr int kOneRingAcc = 21;
 __global__ void __launch_bounds__(256) one_ring_faces_kernel(const float* __restrict__ V, const float* __restrict__ Vd,
                                                              const int32_t* __restrict__ F, int64_t nv, int64_t nf,
                                                              float* __restrict__ vacc, int32_t* __restrict__ status) {
+    pdl_enter();
     const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (f >= nf) return;
     const int idx[3] = {F[3 * f], F[3 * f + 1], F[3 * f + 2]};
@@ -303,6 +306,7 @@ __global__ void __launch_bounds__(256) one_ring_vertices_kernel(const float* __r
                                                                 const float* __restrict__ Vd,
                                                                 const float* __restrict__ vacc, int64_t nv,
                                                                 float* __restrict__ vtab) {
+    pdl_enter();
     const int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (v >= nv) return;
     const float* a = vacc + kOneRingAcc * v;
@@ -445,6 +449,7 @@ __global__ void __launch_bounds__(256) deform_gaussians_kernel(
     const float* __restrict__ V, const int32_t* __restrict__ F, int64_t nv, int64_t nf,
     const float* __restrict__ vtab, int mode, float* __restrict__ out_means, float* __restrict__ out_cov,
     float* __restrict__ out_quats, int32_t* __restrict__ status) {
+    pdl_enter();
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t i = tid >> 3;
     const int corner = (int)(tid & 7);
@@ -537,6 +542,7 @@ __global__ void __launch_bounds__(kDefBlock) deform_gaussians_compact_kernel(
     const float* __restrict__ cov3d, int64_t n, const int32_t* __restrict__ count, const int2* __restrict__ entries,
     int64_t nv, const float* __restrict__ vtab, int mode, float* __restrict__ out_means,
     float* __restrict__ out_cov, float* __restrict__ out_quats, int32_t* __restrict__ status) {
+    pdl_enter();
     __shared__ float s_acc[kDefBlock][17];  // odd row length: conflict-free row reads
     __shared__ int s_bad[kDefBlock];
     const int t = threadIdx.x;
@@ -610,20 +616,20 @@ static umgs_status proxy_table(umgs_ctx* ctx, const float* V, const float* Vd, c
     {
         StageTimer tm(ctx, UMGS_STAGE_DEFORM_FACES, stream);
         if (one_ring)
-            one_ring_faces_kernel<<<grid_for(nf, 256), 256, 0, stream>>>(V, Vd, F, nv, nf, ctx->vacc.as<float>(),
-                                                                         status), count_launch();
+            launch_pdl(one_ring_faces_kernel, grid_for(nf, 256), 256, 0, stream, V, Vd, F, nv, nf, ctx->vacc.as<float>(),
+                                                                         status);
         else
-            face_gradients_kernel<<<grid_for(nf, 256), 256, 0, stream>>>(V, Vd, F, nv, nf, ctx->vacc.as<float>(),
-                                                                         status), count_launch();
+            launch_pdl(face_gradients_kernel, grid_for(nf, 256), 256, 0, stream, V, Vd, F, nv, nf, ctx->vacc.as<float>(),
+                                                                         status);
     }
     {
         StageTimer tm(ctx, UMGS_STAGE_DEFORM_VERTICES, stream);
         if (one_ring)
-            one_ring_vertices_kernel<<<grid_for(nv, 256), 256, 0, stream>>>(V, Vd, ctx->vacc.as<float>(), nv,
-                                                                            ctx->vtab.as<float>()), count_launch();
+            launch_pdl(one_ring_vertices_kernel, grid_for(nv, 256), 256, 0, stream, V, Vd, ctx->vacc.as<float>(), nv,
+                                                                            ctx->vtab.as<float>());
         else
-            vertex_xforms_kernel<<<grid_for(nv, 256), 256, 0, stream>>>(V, Vd, ctx->vacc.as<float>(), nv,
-                                                                        ctx->vtab.as<float>()), count_launch();
+            launch_pdl(vertex_xforms_kernel, grid_for(nv, 256), 256, 0, stream, V, Vd, ctx->vacc.as<float>(), nv,
+                                                                        ctx->vtab.as<float>());
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "proxy table kernels");
     return UMGS_OK;
@@ -637,9 +643,9 @@ umgs_status deform_forward(umgs_ctx* ctx, const umgs_gaussians* g, const int32_t
     if (st != UMGS_OK) return st;
     StageTimer tm(ctx, UMGS_STAGE_DEFORM_GAUSSIANS, stream);
     if (g->n > 0)
-        deform_gaussians_kernel<<<grid_for(8 * g->n, 256), 256, 0, stream>>>(
+        launch_pdl(deform_gaussians_kernel, grid_for(8 * g->n, 256), 256, 0, stream, 
             g->means, g->quats, g->scales, g->cov3d, g->n, face, bary, V, F, nv, nf, ctx->vtab.as<float>(), mode,
-            out_means, out_cov, out_quats, ctx->dstatus.as<int32_t>()), count_launch();
+            out_means, out_cov, out_quats, ctx->dstatus.as<int32_t>());
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "deform kernels");
     return UMGS_OK;
@@ -664,9 +670,9 @@ umgs_status deform_compact_forward(umgs_ctx* ctx, const umgs_gaussians* g, const
     if (st != UMGS_OK) return st;
     StageTimer tm(ctx, UMGS_STAGE_DEFORM_GAUSSIANS, stream);
     if (g->n > 0)
-        deform_gaussians_compact_kernel<<<grid_for(g->n, kDefBlock), kDefBlock, 0, stream>>>(
+        launch_pdl(deform_gaussians_compact_kernel, grid_for(g->n, kDefBlock), kDefBlock, 0, stream, 
             g->means, g->quats, g->scales, g->cov3d, g->n, count, entries, nv, ctx->vtab.as<float>(), mode,
-            out_means, out_cov, out_quats, ctx->dstatus.as<int32_t>()), count_launch();
+            out_means, out_cov, out_quats, ctx->dstatus.as<int32_t>());
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "deform kernels");
     return UMGS_OK;
