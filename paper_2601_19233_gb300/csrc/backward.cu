@@ -698,9 +698,9 @@ umgs_status render_backward(umgs_ctx* ctx, umgs_frame* fr, const umgs_gaussians*
         const int tpc = fr->tiles_x * fr->tiles_y;
         const float4* dout = reinterpret_cast<const float4*>(dL_drgbt);
 #define UMGS_LAUNCH(TSV)                                                                                         \
-        static const cudaError_t attr##TSV = cudaFuncSetAttribute(                                               \
-            composite_bwd_kernel<TSV>, cudaFuncAttributeMaxDynamicSharedMemorySize, bwd_smem_bytes<TSV>());      \
-        UMGS_TRY(attr##TSV);                                                                                     \
+        /* per call: the attribute belongs to the current device */                                         \
+        UMGS_TRY(cudaFuncSetAttribute(composite_bwd_kernel<TSV>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                      bwd_smem_bytes<TSV>()));                                                   \
         launch_pdl(composite_bwd_kernel<TSV>, M, TSV * TSV, bwd_smem_bytes<TSV>(), stream,                               \
             fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->trec.as<TRec>(), Ng, Nt,               \
             fr->tiles_x, tpc, fr->W, fr->H, fr->bg[0], fr->bg[1], fr->bg[2], dout, fr->last.as<int32_t>(),         \
