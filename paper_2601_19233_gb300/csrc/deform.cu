@@ -602,6 +602,12 @@ __global__ void __launch_bounds__(kDefBlock) deform_gaussians_compact_kernel(
 static inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
 
 // per-face gradients and the per-vertex table of the deformed proxy (A1)
+__global__ void zero_floats_kernel(float* __restrict__ p, int64_t n) {
+    pdl_enter();
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) p[i] = 0.f;
+}
+
 static umgs_status proxy_table(umgs_ctx* ctx, const float* V, const float* Vd, const int32_t* F, int64_t nv,
                                int64_t nf, bool one_ring, cudaStream_t stream) {
     cudaError_t e;
@@ -610,8 +616,9 @@ static umgs_status proxy_table(umgs_ctx* ctx, const float* V, const float* Vd, c
     if ((e = ctx->vtab.reserve(sizeof(float) * kVtabStride * nv)) != cudaSuccess)
         return fail(ctx, UMGS_ERR_OUT_OF_MEMORY, "vtab");
     ctx->vtab_rows = nv;
-    if ((e = cudaMemsetAsync(ctx->vacc.ptr, 0, sizeof(float) * nacc, stream)) != cudaSuccess)
-        return cuda_fail(ctx, e, "cudaMemsetAsync");
+    // accumulators cleared by a kernel, so the programmatic launch chain runs on
+    launch_pdl(zero_floats_kernel, grid_for(nacc, 256), 256, 0, stream, ctx->vacc.as<float>(), nacc);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "zero_floats_kernel");
     int32_t* status = ctx->dstatus.as<int32_t>();
     {
         StageTimer tm(ctx, UMGS_STAGE_DEFORM_FACES, stream);

@@ -48,6 +48,8 @@ struct umgs_frame {
     umgs::DevBuf tfin, ntri, stack;   // backward state (saved renders only)
     umgs::DevBuf depth;               // expected depth per pixel (UMGS_RENDER_DEPTH renders only)
     umgs::DevBuf textab;              // DevTex per textured mesh
+    std::vector<umgs::DevCam> cams_host;  // the cameras last uploaded into `cams`
+    void* cams_dev = nullptr;             // ... and the buffer they went to
     bool has_depth = false;
     umgs::DevBuf ggrad, tgrad, rerun_out;
     umgs::DevBuf fix_list;            // (camera, Gaussian) records whose conic is refined in fp64
@@ -75,6 +77,8 @@ struct umgs_frame {
                         &last, &status, &tfin, &ntri, &stack, &depth, &textab, &ggrad, &tgrad, &rerun_out, &fix_list, &ord_k, &ord_v,
                         &ord_k2, &ord_v2})
             b->release();
+        cams_host.clear();
+        cams_dev = nullptr;
     }
 };
 

@@ -470,6 +470,11 @@ __global__ void __launch_bounds__(256) setup_triangles_kernel(
     }
 }
 
+__global__ void zero_words_kernel(uint32_t* __restrict__ p, int n) {
+    pdl_enter();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = 0u;
+}
+
 // ---------------------------------------------------------------------------
 // binning.  Every tile's list must hold the records whose pixel rect touches
 // it, in (depth bits, id) order.  Instead of emitting one (tile, id) pair per
@@ -1103,10 +1108,19 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
         }
         d.pad = 0;
     }
-    // (inside a graph capture the cameras were uploaded by the sizing render)
-    if (!fr->capture)
+    // (inside a graph capture the cameras were uploaded by the sizing render;
+    // cameras equal to the frame's last upload into the same buffer are not
+    // sent again)
+    const bool same_cams = fr->cams_dev == fr->cams.ptr && fr->cams_host.size() == (size_t)ncams &&
+                           std::memcmp(fr->cams_host.data(), dc.data(), sizeof(DevCam) * ncams) == 0;
+    if (!fr->capture && !same_cams) {
         UMGS_TRY(cudaMemcpyAsync(fr->cams.ptr, dc.data(), sizeof(DevCam) * ncams, cudaMemcpyHostToDevice, stream));
-    UMGS_TRY(cudaMemsetAsync(fr->status.ptr, 0, sizeof(int32_t) * 16, stream));
+        fr->cams_host = dc;
+        fr->cams_dev = fr->cams.ptr;
+    }
+    // status words cleared by a kernel (not a memset node), so that the
+    // programmatic launch chain runs on from the stream's previous kernel
+    launch_pdl(zero_words_kernel, 1, 32, 0, stream, reinterpret_cast<uint32_t*>(fr->status.ptr), 16);
 
     const DevCam* dcams = fr->cams.as<DevCam>();
     const unsigned fix_cap = (unsigned)std::min<int64_t>(std::max<int64_t>(1, Ng * ncams), 1 << 22);
