@@ -186,10 +186,10 @@ cudaError_t launch_composite(umgs_frame* fr, const umgs_render_opts& opts, float
 cudaError_t reserve_binning(umgs_frame* fr, int64_t rcap, int64_t kcap);
 // stable LSD radix sort of (k, v) on key bits [lo, lo + bits) (binning
 // stage); the element count is read from n_dev (at most n_cap, which sizes
-// the grids)
+// the grids); key_mm: the optional key map of radix.cuh (RadixMap)
 cudaError_t radix_sort_pairs(umgs_frame* fr, uint32_t* k, uint32_t* v, uint32_t* k2, uint32_t* v2,
                              const uint32_t* n_dev, int64_t n_cap, int bits, uint32_t** rk, uint32_t** rv,
-                             cudaStream_t s, int lo = 0);
+                             cudaStream_t s, int lo = 0, const uint32_t* key_mm = nullptr);
 
 umgs_status render_backward(umgs_ctx* ctx, umgs_frame* fr, const umgs_gaussians* g, const umgs_mesh* meshes,
                             int32_t nmeshes, const float* dL_drgbt, const umgs_gaussian_grads* gg,

@@ -149,13 +149,53 @@ static __global__ void __launch_bounds__(kRsThreads) scan_apply_kernel(const uin
 
 // Radix passes take ITEMS elements per thread (a block sorts 256 x ITEMS):
 // 16 for long inputs, 8 for short ones (more blocks in flight).
+//
+// Optional key map (the depth sort): ~min and max of the keys other than
+// 0xffffffff (the invalid records), spread over kRadixMapSlots slots
+// (mm[2s] = ~min, mm[2s+1] = max of the keys that slot saw).  Keys are then sorted by
+// k - min (0xffffffff by span = max - min + 1, after every valid key), which
+// orders them as k does, and a pass whose digit lies above every mapped key
+// (span >> shift == 0) is skipped: its upsweep and scan do nothing and its
+// downsweep copies the elements through.  mm == nullptr: keys as they are.
+struct RadixMap {
+    uint32_t kmin, span;
+    bool on;
+    __device__ __forceinline__ uint32_t key(uint32_t k) const {
+        return !on ? k : (k == 0xffffffffu ? span : k - kmin);
+    }
+    __device__ __forceinline__ bool skip(int shift) const { return on && (span >> shift) == 0u; }
+};
+constexpr int kRadixMapSlots = 32;
+// (called by every thread; each warp reduces the slots, one per lane)
+__device__ __forceinline__ RadixMap radix_map(const uint32_t* __restrict__ mm) {
+    RadixMap m;
+    m.on = mm != nullptr;
+    m.kmin = 0u;
+    m.span = 0u;
+    if (m.on) {
+        const int lane = threadIdx.x & 31;
+        uint32_t a = mm[2 * lane], b = mm[2 * lane + 1];
+#pragma unroll
+        for (int d = 16; d >= 1; d >>= 1) {
+            a = max(a, __shfl_xor_sync(0xffffffffu, a, d));
+            b = max(b, __shfl_xor_sync(0xffffffffu, b, d));
+        }
+        const uint32_t kmin = ~a, kmax = b;
+        m.kmin = kmin;
+        m.span = kmax >= kmin ? kmax - kmin + 1u : 0u;  // no valid key: every key maps to 0
+    }
+    return m;
+}
 template <int ITEMS>
 static __global__ void __launch_bounds__(kRsThreads) radix_upsweep_kernel(const uint32_t* __restrict__ keys,
                                                                           const uint32_t* __restrict__ n_dev,
                                                                           int64_t n_cap, int shift, int nblocks,
-                                                                          uint32_t* __restrict__ hist) {
+                                                                          uint32_t* __restrict__ hist,
+                                                                          const uint32_t* __restrict__ mm) {
     pdl_enter();
     __shared__ uint32_t cnt[256];
+    const RadixMap map = radix_map(mm);
+    if (map.skip(shift)) return;
     const int64_t n = min((int64_t)*n_dev, n_cap);
     const int64_t base = (int64_t)blockIdx.x * (kRsThreads * ITEMS);
     if (base >= n) return;  // a block past the live count (capacity-sized grids): its column is not scanned
@@ -164,7 +204,7 @@ static __global__ void __launch_bounds__(kRsThreads) radix_upsweep_kernel(const 
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
         const int64_t i = base + k * kRsThreads + threadIdx.x;
-        if (i < n) atomicAdd(&cnt[(keys[i] >> shift) & 255u], 1u);
+        if (i < n) atomicAdd(&cnt[(map.key(keys[i]) >> shift) & 255u], 1u);
     }
     __syncthreads();
     hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = cnt[threadIdx.x];
@@ -176,9 +216,11 @@ static __global__ void __launch_bounds__(kRsThreads) radix_upsweep_kernel(const 
 static __global__ void __launch_bounds__(kRsThreads) radix_hist_scan_kernel(uint32_t* __restrict__ hist, int nblocks,
                                                                             const uint32_t* __restrict__ n_dev,
                                                                             int64_t n_cap, int tile,
-                                                                            uint32_t* __restrict__ dtotal) {
+                                                                            uint32_t* __restrict__ dtotal, int shift,
+                                                                            const uint32_t* __restrict__ mm) {
     pdl_enter();
     __shared__ uint32_t s_warp[32];
+    if (radix_map(mm).skip(shift)) return;
     uint32_t* h = hist + (int64_t)blockIdx.x * nblocks;
     const int64_t n = min((int64_t)*n_dev, n_cap);
     const int live = (int)min((int64_t)nblocks, (n + tile - 1) / tile);
@@ -203,9 +245,10 @@ template <int ITEMS>
 static __global__ void __launch_bounds__(kRsThreads) radix_downsweep_kernel(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, const uint32_t* __restrict__ n_dev,
     int64_t n_cap, int shift, int nblocks, const uint32_t* __restrict__ hist, const uint32_t* __restrict__ dtotal,
-    uint32_t* __restrict__ kout, uint32_t* __restrict__ vout) {
+    uint32_t* __restrict__ kout, uint32_t* __restrict__ vout, const uint32_t* __restrict__ mm) {
     pdl_enter();
     const int64_t n = min((int64_t)*n_dev, n_cap);
+    const RadixMap map = radix_map(mm);
     constexpr int NW = kRsThreads / 32;
     __shared__ uint32_t wcnt[NW][256];
     __shared__ uint32_t s_warp[32];
@@ -215,6 +258,13 @@ static __global__ void __launch_bounds__(kRsThreads) radix_downsweep_kernel(
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     const int64_t bbase = (int64_t)blockIdx.x * (kRsThreads * ITEMS);
     if (bbase >= n) return;  // nothing of this block is live (uniform over the block)
+    if (map.skip(shift)) {  // a constant digit: the pass copies the elements through
+        for (int64_t i = bbase + t; i < min(n, bbase + (int64_t)kRsThreads * ITEMS); i += kRsThreads) {
+            kout[i] = kin[i];
+            vout[i] = vin[i];
+        }
+        return;
+    }
     const int64_t base = bbase + (int64_t)w * (32 * ITEMS);
     const unsigned lt = (1u << lane) - 1u;
     uint32_t key[ITEMS], val[ITEMS], rank[ITEMS], dig[ITEMS];
@@ -224,7 +274,7 @@ static __global__ void __launch_bounds__(kRsThreads) radix_downsweep_kernel(
         const bool valid = i < n;
         key[k] = valid ? kin[i] : 0u;
         val[k] = valid ? vin[i] : 0u;
-        dig[k] = valid ? ((key[k] >> shift) & 255u) : 256u;
+        dig[k] = valid ? ((map.key(key[k]) >> shift) & 255u) : 256u;
     }
 #pragma unroll
     for (int q = 0; q < NW; ++q) wcnt[q][t] = 0;
@@ -258,7 +308,7 @@ static __global__ void __launch_bounds__(kRsThreads) radix_downsweep_kernel(
     __syncthreads();
     for (int i = t; i < (int)btot; i += kRsThreads) {
         const uint2 e = stage[i];
-        const uint32_t d = (e.x >> shift) & 255u;
+        const uint32_t d = (map.key(e.x) >> shift) & 255u;
         const uint32_t pos = gstart[d] + (uint32_t)i - bstart[d];
         kout[pos] = e.x;
         vout[pos] = e.y;

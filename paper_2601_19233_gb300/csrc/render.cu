@@ -501,15 +501,41 @@ constexpr int64_t kMaxRegions = (int64_t)1 << (32 - kRectBits);
 constexpr int kRegionChunk = 2048;           // region pairs per count/fill block
 constexpr int kRegionThreads = 256;
 
-__global__ void prim_keys_kernel(const BinInfo* __restrict__ bin, int64_t n, uint32_t* __restrict__ pk,
-                                 uint32_t* __restrict__ pv, uint32_t* __restrict__ n_dev) {
+// Depth keys (0xffffffff for culled records) and, for the depth sort's key
+// map, ~min and max of the valid keys: one atomic pair per block into slot
+// blockIdx % kRadixMapSlots of mm (mm[2s] = ~min, mm[2s+1] = max; all start
+// at 0), so that no single address takes every block's update.
+__global__ void __launch_bounds__(256) prim_keys_kernel(const BinInfo* __restrict__ bin, int64_t n,
+                                                        uint32_t* __restrict__ pk, uint32_t* __restrict__ pv,
+                                                        uint32_t* __restrict__ n_dev, uint32_t* __restrict__ mm) {
     pdl_enter();
+    __shared__ uint32_t s_mm[2][8];
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i == 0) *n_dev = (uint32_t)n;
-    if (i >= n) return;
-    const BinInfo b = bin[i];
-    pk[i] = b.valid ? b.dbits : 0xffffffffu;
-    pv[i] = (uint32_t)i;
+    uint32_t nmin = 0u, kmax = 0u;  // ~min, max over this thread's valid key
+    if (i < n) {
+        const BinInfo b = bin[i];
+        const uint32_t k = b.valid ? b.dbits : 0xffffffffu;
+        pk[i] = k;
+        pv[i] = (uint32_t)i;
+        if (b.valid) { nmin = ~k; kmax = k; }
+    }
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+        nmin = max(nmin, __shfl_xor_sync(0xffffffffu, nmin, d));
+        kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, d));
+    }
+    if ((threadIdx.x & 31) == 0) { s_mm[0][threadIdx.x >> 5] = nmin; s_mm[1][threadIdx.x >> 5] = kmax; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t a = 0u, b = 0u;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a = max(a, s_mm[0][w]); b = max(b, s_mm[1][w]); }
+        if (a | b) {
+            uint32_t* slot = mm + 2 * (blockIdx.x % kRadixMapSlots);
+            atomicMax(slot, a);
+            atomicMax(slot + 1, b);
+        }
+    }
 }
 
 // Per depth-sorted record: the number of regions its tile rect meets; the
@@ -980,7 +1006,7 @@ cudaError_t scan_u32(umgs_frame* fr, const uint32_t* in, uint32_t* out, int64_t 
 // the result ended
 cudaError_t radix_sort_pairs(umgs_frame* fr, uint32_t* k, uint32_t* v, uint32_t* k2, uint32_t* v2,
                              const uint32_t* n_dev, int64_t n_cap, int bits, uint32_t** rk, uint32_t** rv,
-                             cudaStream_t s, int lo) {
+                             cudaStream_t s, int lo, const uint32_t* key_mm) {
     const int64_t nb = radix_blocks(n_cap);
     const int items = radix_items(n_cap);
     const int64_t nh = 256 * nb;
@@ -992,17 +1018,20 @@ cudaError_t radix_sort_pairs(umgs_frame* fr, uint32_t* k, uint32_t* v, uint32_t*
     uint32_t* dtotal = fr->rs_hist2.as<uint32_t>();
     for (int shift = lo; shift < lo + bits; shift += 8) {
         if (items == 8) {
-            launch_pdl(radix_upsweep_kernel<8>, (unsigned)nb, kRsThreads, 0, s, k, n_dev, n_cap, shift, (int)nb, hist);
+            launch_pdl(radix_upsweep_kernel<8>, (unsigned)nb, kRsThreads, 0, s, k, n_dev, n_cap, shift, (int)nb, hist,
+                       key_mm);
         } else {
-            launch_pdl(radix_upsweep_kernel<16>, (unsigned)nb, kRsThreads, 0, s, k, n_dev, n_cap, shift, (int)nb, hist);
+            launch_pdl(radix_upsweep_kernel<16>, (unsigned)nb, kRsThreads, 0, s, k, n_dev, n_cap, shift, (int)nb, hist,
+                       key_mm);
         }
-        launch_pdl(radix_hist_scan_kernel, 256, kRsThreads, 0, s, hist, (int)nb, n_dev, n_cap, kRsThreads * items, dtotal);
+        launch_pdl(radix_hist_scan_kernel, 256, kRsThreads, 0, s, hist, (int)nb, n_dev, n_cap, kRsThreads * items, dtotal,
+                   shift, key_mm);
         if (items == 8) {
             launch_pdl(radix_downsweep_kernel<8>, (unsigned)nb, kRsThreads, 0, s, k, v, n_dev, n_cap, shift, (int)nb, hist,
-                                                                          dtotal, k2, v2);
+                       dtotal, k2, v2, key_mm);
         } else {
-            launch_pdl(radix_downsweep_kernel<16>, (unsigned)nb, kRsThreads, 0, s, k, v, n_dev, n_cap, shift, (int)nb, hist,
-                                                                           dtotal, k2, v2);
+            launch_pdl(radix_downsweep_kernel<16>, (unsigned)nb, kRsThreads, 0, s, k, v, n_dev, n_cap, shift, (int)nb,
+                       hist, dtotal, k2, v2, key_mm);
         }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -1087,8 +1116,8 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     // work counter, [9] scan overflow, [10..11] tile-list entries (u64),
     // [12] (region, id) pairs sorted (0 after an overflow), [13] count/fill
     // chunks, [14] tile-list entries from the tile scan, [15] (region, id)
-    // pairs counted
-    UMGS_TRY(fr->status.reserve(sizeof(int32_t) * 16));
+    // pairs counted, [16 ..) the depth sort's key-map slots (~min, max)
+    UMGS_TRY(fr->status.reserve(sizeof(int32_t) * (16 + 2 * kRadixMapSlots)));
 
     // cameras: host -> pinned staging -> device
     std::vector<DevCam> dc(ncams);
@@ -1120,7 +1149,8 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     }
     // status words cleared by a kernel (not a memset node), so that the
     // programmatic launch chain runs on from the stream's previous kernel
-    launch_pdl(zero_words_kernel, 1, 32, 0, stream, reinterpret_cast<uint32_t*>(fr->status.ptr), 16);
+    launch_pdl(zero_words_kernel, 1, 128, 0, stream, reinterpret_cast<uint32_t*>(fr->status.ptr),
+               16 + 2 * kRadixMapSlots);
 
     const DevCam* dcams = fr->cams.as<DevCam>();
     const unsigned fix_cap = (unsigned)std::min<int64_t>(std::max<int64_t>(1, Ng * ncams), 1 << 22);
@@ -1200,12 +1230,13 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     uint32_t* ktot32 = status_u + 14;
     if (NR > 0) {
         StageTimer tm(ctx, UMGS_STAGE_SCAN, stream);
-        launch_pdl(prim_keys_kernel, grid_for(NR, 256), 256, 0, stream, fr->bin.as<BinInfo>(), NR, pk, pv, status_u + 5);
+        launch_pdl(prim_keys_kernel, grid_for(NR, 256), 256, 0, stream, fr->bin.as<BinInfo>(), NR, pk, pv, status_u + 5,
+                   status_u + 16);
         UMGS_TRY(cudaGetLastError());
         uint32_t* rk = nullptr;
         uint32_t* rv = nullptr;
         UMGS_TRY(radix_sort_pairs(fr, pk, pv, fr->pk2.as<uint32_t>(), fr->pv2.as<uint32_t>(), status_u + 5, NR, 32, &rk,
-                                  &rv, stream));
+                                  &rv, stream, 0, status_u + 16));
         pk = rk;
         pv = rv;
         launch_pdl(region_counts_kernel, grid_for(NR, 256), 256, 0, stream, fr->bin.as<BinInfo>(), pv, NR, ts,
