@@ -189,7 +189,8 @@ __global__ void __launch_bounds__(TS * TS, TS == 16 ? 4 : 1) composite_bwd_kerne
                 for (int e = 0; e < 16; ++e) v[e] = 0.f;
                 if (contrib) {
                     if (in_ent) { U = 0.25f * ((Uj[0] + Uj[1]) + (Uj[2] + Uj[3])); in_ent = false; }
-                    const float Tk = T / (1.f - alpha);
+                    // (fast division: alpha <= 0.99 keeps the divisor in [0.01, 1])
+                    const float Tk = __fdividef(T, 1.f - alpha);
                     const float gc = gr * q1.z + gg * q1.w + gb * q2.x;
                     const float dalpha = Tk * (gc - U);
                     const float w = Tk * alpha;

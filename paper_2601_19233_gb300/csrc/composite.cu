@@ -65,6 +65,7 @@ __device__ __forceinline__ void composite_tile(
     const int px = tx * TS + lx, py = ty * TS + ly;
     const bool inside = px < W && py < H;
     const int64_t beg = off[tile], end = off[tile + 1];
+    const uint32_t ng32 = (uint32_t)Ng;  // unified ids are 32-bit: a 32-bit compare per fragment
     const GRec* G = grec + (int64_t)cam * Ng;
     const GRec16* G16 = grec16 ? grec16 + (int64_t)cam * Ng : nullptr;
     const TRec* TR = trec + (int64_t)cam * Nt;
@@ -141,7 +142,7 @@ __device__ __forceinline__ void composite_tile(
                 const int k = lst[li];
                 if (done) continue;
                 const uint32_t id = s_id[k];
-                if (id < Ng) {
+                if (id < ng32) {
                     const float4 q1 = s_rec[k][1], q2 = s_rec[k][2];
                     if (pxf < q1.z || pxf > q1.w || pyf < q2.x || pyf > q2.y) continue;
                     const float4 q0 = s_rec[k][0];
@@ -152,7 +153,7 @@ __device__ __forceinline__ void composite_tile(
                     const float w = alpha * st.T;
                     st.C[0] += w * q2.z; st.C[1] += w * q2.w; st.C[2] += w * s_rec[k][3].x;
                     if (mode == kModeDepth) { st.D += w * s_rec[k][3].y; st.Wd += w; }
-                    st.T *= (1.f - alpha);
+                    st.T = __fmaf_rn(-alpha, st.T, st.T);  // T (1 - alpha), one rounding
                     if (mode == UMGS_BLEND_ENTITY_ALL) st.g_since *= (1.f - alpha);
                     else st.in_ent = false;
                 } else {
