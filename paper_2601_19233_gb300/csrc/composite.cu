@@ -189,7 +189,7 @@ __device__ __forceinline__ void composite_tile(
                     const float area = lam[0] + lam[1] + lam[2];
                     float wv[3];
                     if (area != 0.f) {
-                        const float ia = 1.f / area;
+                        const float ia = __fdividef(1.f, area);  // (fast division: screen areas stay far from 2^126)
 #pragma unroll
                         for (int e = 0; e < 3; ++e) wv[e] = fmaxf(lam[e] * ia, 0.f) * t.iz[e];
                     } else {
@@ -204,7 +204,7 @@ __device__ __forceinline__ void composite_tile(
                                                      : 1.f;
                         zt = ws > 0.f ? ls / ws : 3.f / (t.iz[0] + t.iz[1] + t.iz[2]);
                     }
-                    if (ws > 0.f) { const float is = 1.f / ws; wv[0] *= is; wv[1] *= is; wv[2] *= is; }
+                    if (ws > 0.f) { const float is = __fdividef(1.f, ws); wv[0] *= is; wv[1] *= is; wv[2] *= is; }
                     else { wv[0] = wv[1] = wv[2] = 1.f / 3.f; }
                     float col[3];
                     if (t.tex > 0) {  // textured face: (u, v) interpolated like a colour, then sampled
