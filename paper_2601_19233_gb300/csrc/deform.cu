@@ -340,13 +340,13 @@ __device__ void exp_rot(const float r[3], float R[9], float q[4]) {
         hs = 0.5f - th2 / 48.f;
         hc = 1.f - th2 / 8.f;
     } else {
-        float s, c;
-        sincosf(th, &s, &c);
-        A = s / th;
-        B = (1.f - c) / th2;
+        // one sincos of th/2: sin th = 2 s c, 1 - cos th = 2 s^2 (no cancellation)
         float s2, c2;
         sincosf(0.5f * th, &s2, &c2);
-        hs = s2 / th;
+        const float ith = 1.f / th;
+        hs = s2 * ith;
+        A = 2.f * c2 * hs;
+        B = 2.f * hs * hs;
         hc = c2;
     }
     const float x = r[0], y = r[1], z = r[2];
@@ -402,8 +402,13 @@ __device__ __forceinline__ void deform_finish(const float (&acc)[15], float scal
         S[6] = c6[2]; S[7] = c6[4]; S[8] = c6[5];
     } else {
         float qw = quats[4 * i], qx = quats[4 * i + 1], qy = quats[4 * i + 2], qz = quats[4 * i + 3];
-        const float nq = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
-        if (nq > 0.f) { qw /= nq; qx /= nq; qy /= nq; qz /= nq; } else { qw = 1.f; qx = qy = qz = 0.f; }
+        const float nq2 = qw * qw + qx * qx + qy * qy + qz * qz;
+        if (nq2 > 0.f) {
+            const float inq = rsqrtf(nq2);
+            qw *= inq; qx *= inq; qy *= inq; qz *= inq;
+        } else {
+            qw = 1.f; qx = qy = qz = 0.f;
+        }
         qn[0] = qw; qn[1] = qx; qn[2] = qy; qn[3] = qz;
         if (which & 2) {
             const float r[9] = {1.f - 2.f * (qy * qy + qz * qz), 2.f * (qx * qy - qw * qz), 2.f * (qx * qz + qw * qy),
