@@ -158,8 +158,10 @@ def _floordiv(a, b):
     return np.floor_divide(a, b)
 
 
-def setup_triangles(verts, faces, cam):
-    """Canonical triangle setup for one camera.
+def setup_triangles(verts, faces, cam, dilate=0):
+    """Canonical triangle setup for one camera.  `dilate` widens the pixel
+    rect by that many pixels on every side before clipping (soft-edge
+    coverage, where a triangle reaches pixels near but outside its samples).
 
     Returns dict: valid, sx, sy (int64 [F,3] snapped coords, original vertex
     order), A, B (int64 [F,3]), Cb (int64 [F,3], edge constant with the
@@ -204,10 +206,10 @@ def setup_triangles(verts, faces, cam):
         Cb[:, k] = Cu[:, k] - np.where(topleft, 0, 1)
     xmin, xmax = sx.min(1), sx.max(1)
     ymin, ymax = sy.min(1), sy.max(1)
-    xlo = np.maximum(-_floordiv(-(xmin - 224), SNAP), 0)
-    xhi = np.minimum(_floordiv(xmax - 32, SNAP), W - 1)
-    ylo = np.maximum(-_floordiv(-(ymin - 224), SNAP), 0)
-    yhi = np.minimum(_floordiv(ymax - 32, SNAP), H - 1)
+    xlo = np.maximum(-_floordiv(-(xmin - 224), SNAP) - dilate, 0)
+    xhi = np.minimum(_floordiv(xmax - 32, SNAP) + dilate, W - 1)
+    ylo = np.maximum(-_floordiv(-(ymin - 224), SNAP) - dilate, 0)
+    yhi = np.minimum(_floordiv(ymax - 32, SNAP) + dilate, H - 1)
     valid &= (xlo <= xhi) & (ylo <= yhi)
     rect = np.stack([xlo, xhi, ylo, yhi], 1)
     rect[~valid] = 0
@@ -251,7 +253,7 @@ def depth_bits(z):
 class Primitives:
     """Canonical per-camera decisions for a whole scene (Gaussians + meshes)."""
 
-    def __init__(self, scene, cam_index=0, cov3d=None):
+    def __init__(self, scene, cam_index=0, cov3d=None, dilate=0):
         g = scene.gaussians
         cam = scene.cameras[cam_index]
         self.cam = cam
@@ -265,7 +267,7 @@ class Primitives:
         off = g.n
         self.mesh_offsets = []
         for m in scene.meshes:
-            t = setup_triangles(m.verts, m.faces, cam)
+            t = setup_triangles(m.verts, m.faces, cam, dilate)
             self.tris.append(t)
             self.mesh_offsets.append(off)
             off += m.nf

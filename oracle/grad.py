@@ -10,7 +10,8 @@ the exact gradient of L = sum_pixels (g . C + h T) with respect to
   Gaussians: means, quats, scales, opacities, SH coefficients (or cov3d),
   meshes:    vertex positions, vertex colours, vertex / face alpha.
 Vertex positions receive gradient through attribute interpolation only
-(coverage is piecewise constant).  The torch forward is pinned against the
+(coverage is piecewise constant), and with soft-edge coverage (soft=sigma)
+also through the coverage c^j of every sample.  The torch forward is pinned against the
 numpy forward, and the gradient against central finite differences of the
 numpy forward (see tests/test_oracle_grad.py).
 """
@@ -24,6 +25,7 @@ from numpy.polynomial import legendre as npleg
 from numpy.polynomial import polynomial as nppoly
 
 from . import render as R
+from .canonical import SAMPLE_OFFSETS as cn_offsets
 
 DT = torch.float64
 
@@ -115,10 +117,10 @@ def vertices_torch(verts, cam):
     return u, v, pc[:, 2]
 
 
-def decision_table(scene, cam_index=0, t_eps=R.T_EPS, pixels=None):
+def decision_table(scene, cam_index=0, t_eps=R.T_EPS, pixels=None, soft=None):
     """Per pixel: ordered contributing fragments [(id, kind, mask)] up to the
     termination point, from the numpy oracle (FULL mode)."""
-    fr = R.Frame(scene, cam_index)
+    fr = R.Frame(scene, cam_index, soft=soft)
     cam = fr.cam
     if pixels is None:
         pixels = [(x, y) for y in range(cam.height) for x in range(cam.width)]
@@ -154,7 +156,9 @@ def leaf_params(scene, with_cov3d=None):
 
 def composite_torch(scene, p, fr, pixels, table, bg=(0.0, 0.0, 0.0)):
     """Differentiable FULL-mode composite of the given pixels with the
-    decision table fixed.  Returns (C [P,3], T [P])."""
+    decision table fixed (with fr.soft set, triangle coverage is the
+    differentiable soft-edge coverage of render.soft_coverage).  Returns
+    (C [P,3], T [P])."""
     cam = fr.cam
     ng = fr.ng
     P = len(pixels)
@@ -186,6 +190,7 @@ def composite_torch(scene, p, fr, pixels, table, bg=(0.0, 0.0, 0.0)):
     # triangle alpha and colour per (pixel, slot)
     ta = torch.zeros((P, L), dtype=DT)
     tc = torch.zeros((P, L, 3), dtype=DT)
+    o = torch.stack([torch.as_tensor((mask >> j) & 1, dtype=DT) for j in range(4)], -1)  # [P,L,4]
     for mi, m in enumerate(scene.meshes):
         off = fr.P.mesh_offsets[mi]
         sel = (kind == 2) & (gid >= off) & (gid < off + m.nf)
@@ -218,7 +223,21 @@ def composite_torch(scene, p, fr, pixels, table, bg=(0.0, 0.0, 0.0)):
         selt = torch.as_tensor(sel)
         ta = torch.where(selt, al, ta)
         tc = torch.where(selt[..., None], col, tc)
-    o = torch.stack([torch.as_tensor((mask >> j) & 1, dtype=DT) for j in range(4)], -1)  # [P,L,4]
+        if fr.soft:
+            area = (U_[..., 1] - U_[..., 0]) * (V_[..., 2] - V_[..., 0]) - (U_[..., 2] - U_[..., 0]) * (V_[..., 1] - V_[..., 0])
+            sg = torch.sign(area).detach()
+            cov = []
+            for j in range(4):
+                sx = px + float(cn_offsets[j, 0]) / 256.0
+                sy = py + float(cn_offsets[j, 1]) / 256.0
+                c = torch.ones_like(px)
+                for e in range(3):
+                    a, b = (e + 1) % 3, (e + 2) % 3
+                    lam_e = (U_[..., a] - sx) * (V_[..., b] - sy) - (U_[..., b] - sx) * (V_[..., a] - sy)
+                    Le = torch.sqrt((U_[..., b] - U_[..., a]) ** 2 + (V_[..., b] - V_[..., a]) ** 2)
+                    c = c * torch.sigmoid(sg * lam_e / Le / fr.soft)
+                cov.append(torch.where(sg != 0, c, torch.zeros_like(c)))
+            o = torch.where(selt[..., None], torch.stack(cov, -1), o)
     Cacc = torch.zeros((P, 3), dtype=DT)
     T = torch.ones(P, dtype=DT)
     Tin = torch.ones(P, dtype=DT)
@@ -250,10 +269,11 @@ def composite_torch(scene, p, fr, pixels, table, bg=(0.0, 0.0, 0.0)):
     return Cout, T
 
 
-def image_grad(scene, dL_drgb, dL_dT=None, cam_index=0, cov3d=None, bg=(0.0, 0.0, 0.0), t_eps=R.T_EPS):
+def image_grad(scene, dL_drgb, dL_dT=None, cam_index=0, cov3d=None, bg=(0.0, 0.0, 0.0), t_eps=R.T_EPS,
+               soft=None):
     """Gradient of L = sum(dL_drgb . rgb) + sum(dL_dT * T) over the full image.
     Returns (grads dict of numpy fp64 arrays, rgb [H,W,3], T [H,W])."""
-    fr, pixels, table = decision_table(scene, cam_index, t_eps)
+    fr, pixels, table = decision_table(scene, cam_index, t_eps, soft=soft)
     p = leaf_params(scene, cov3d)
     C, T = composite_torch(scene, p, fr, pixels, table, bg)
     H, W = fr.cam.height, fr.cam.width
@@ -267,10 +287,10 @@ def image_grad(scene, dL_drgb, dL_dT=None, cam_index=0, cov3d=None, bg=(0.0, 0.0
     return out, C.detach().numpy().reshape(H, W, 3), T.detach().numpy().reshape(H, W)
 
 
-def loss_numpy(scene, dL_drgb, dL_dT=None, cam_index=0, bg=(0.0, 0.0, 0.0), t_eps=R.T_EPS):
+def loss_numpy(scene, dL_drgb, dL_dT=None, cam_index=0, bg=(0.0, 0.0, 0.0), t_eps=R.T_EPS, soft=None):
     """L evaluated by the numpy forward oracle (decisions recomputed), plus a
     decision signature for finite-difference checks."""
-    r = R.render_image(scene, cam_index, bg=bg, t_eps=t_eps)
+    r = R.render_image(scene, cam_index, bg=bg, t_eps=t_eps, soft=soft)
     L = float((r["rgb"] * np.asarray(dL_drgb, np.float64)).sum())
     if dL_dT is not None:
         L += float((r["T"] * np.asarray(dL_dT, np.float64)).sum())

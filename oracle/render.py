@@ -28,6 +28,15 @@ Ablation modes of Fig. 3 / Fig. 4:
               with O_i = (1/M) sum_j o_i^j.
   ENTITY_ALL  all triangles of the pixel form one entity even with Gaussians
               between them (the colour-overflow case of Fig. 3c).
+
+Soft-edge coverage (an extension beyond the paper, FULL mode only; parity
+pinned in tests/test_oracle_soft.py): the binary sample coverage o_i^j of
+Eq. 7-8 is replaced by c_i^j = prod_e sigmoid(d_e(s_j) / sigma), d_e the
+signed distance (pixels, positive inside) from sample s_j to edge e of the
+unsnapped projected triangle, so that the composite is differentiable in the
+vertex positions through coverage.  A triangle is a fragment of every pixel
+of its pixel rect widened by ceil(8 sigma) pixels; Eq. 7-9 are unchanged with
+c in place of o (they reduce to the binary form when every c is 0 or 1).
 """
 from __future__ import annotations
 
@@ -110,6 +119,39 @@ def vertices_fp64(mesh, cam):
         u = cam.fx * p[:, 0] / p[:, 2] + cam.cx
         v = cam.fy * p[:, 1] / p[:, 2] + cam.cy
     return u, v, p[:, 2]
+
+
+def soft_dilation(sigma):
+    """Pixels by which a triangle's rect is widened for soft-edge coverage."""
+    return int(np.ceil(8.0 * float(np.float32(sigma)))) if sigma else 0
+
+
+def soft_coverage(tu, tv, px, py, sigma):
+    """Soft coverage c^j (j = 0..3, the samples of canonical.SAMPLE_OFFSETS)
+    of pixel (px, py) by triangles with unsnapped screen vertices tu, tv
+    ([K,3] fp64, original vertex order): c^j = prod_e sigmoid(d_e / sigma),
+    d_e = s * lambda_e / |P_b - P_a| for the edge (a, b) = (e+1, e+2) opposite
+    vertex e, lambda_e(x) = (u_a - x)(v_b - y) - (u_b - x)(v_a - y) twice the
+    signed area of (x, P_a, P_b) and s the sign of the triangle's signed
+    area.  A triangle of zero area covers nothing.  Returns [K,4]."""
+    tu = np.asarray(tu, np.float64).reshape(-1, 3)
+    tv = np.asarray(tv, np.float64).reshape(-1, 3)
+    area = (tu[:, 1] - tu[:, 0]) * (tv[:, 2] - tv[:, 0]) - (tu[:, 2] - tu[:, 0]) * (tv[:, 1] - tv[:, 0])
+    sg = np.sign(area)
+    out = np.ones((tu.shape[0], 4))
+    for j in range(4):
+        sx = px + 0.5 + cn.SAMPLE_OFFSETS[j, 0] / 256.0
+        sy = py + 0.5 + cn.SAMPLE_OFFSETS[j, 1] / 256.0
+        for e in range(3):
+            a, b = (e + 1) % 3, (e + 2) % 3
+            lam = (tu[:, a] - sx) * (tv[:, b] - sy) - (tu[:, b] - sx) * (tv[:, a] - sy)
+            L = np.hypot(tu[:, b] - tu[:, a], tv[:, b] - tv[:, a])
+            with np.errstate(all="ignore"):
+                d = np.where(L > 0, sg * lam / np.where(L > 0, L, 1.0), 0.0)
+            with np.errstate(over="ignore"):  # exp overflow -> factor 0, as the limit
+                out[:, j] *= 1.0 / (1.0 + np.exp(-d / sigma))
+    out[sg == 0] = 0.0
+    return out
 
 
 def triangle_attributes(mesh, fid, vu, vv, vz, px, py):
@@ -197,10 +239,11 @@ def triangle_depth(mesh, fid, vu, vv, vz, px, py):
 class Frame:
     """Canonical decisions + fp64 quantities of a scene seen by one camera."""
 
-    def __init__(self, scene, cam_index=0, cov3d=None):
+    def __init__(self, scene, cam_index=0, cov3d=None, soft=None):
         self.scene = scene
         self.cam = scene.cameras[cam_index]
-        self.P = cn.Primitives(scene, cam_index, cov3d)
+        self.soft = soft  # soft-edge width sigma (pixels), or None for binary coverage
+        self.P = cn.Primitives(scene, cam_index, cov3d, soft_dilation(soft))
         self.G = gaussians_fp64(scene.gaussians, self.cam, cov3d)
         self.V = [vertices_fp64(m, self.cam) for m in scene.meshes]
         self.ng = scene.gaussians.n
@@ -243,14 +286,18 @@ class Frame:
             mask = cn.sample_coverage(P.A[loc], P.B[loc], P.Cb[loc], px, py)
             cen = cn.centre_coverage(P.A[loc], P.B[loc], P.Cb[loc], px, py)
             for k, tid in enumerate(ti):
-                if mask[k] == 0 and not cen[k]:
+                if mask[k] == 0 and not cen[k] and not self.soft:
                     continue
                 mi, fi = self.mesh_of(int(tid))
                 vu, vv, vz = self.V[mi]
                 col, alpha, _ = triangle_attributes(self.scene.meshes[mi], np.array([fi]), vu, vv, vz, px, py)
                 zt = triangle_depth(self.scene.meshes[mi], np.array([fi]), vu, vv, vz, px, py)
-                frags.append(dict(id=int(tid), kind="t", alpha=float(alpha[0]), color=col[0], z=float(zt[0]),
-                                  mask=int(mask[k]), centre=bool(cen[k])))
+                f = dict(id=int(tid), kind="t", alpha=float(alpha[0]), color=col[0], z=float(zt[0]),
+                         mask=int(mask[k]), centre=bool(cen[k]))
+                if self.soft:
+                    fv = np.asarray(self.scene.meshes[mi].faces, np.int64)[fi]
+                    f["cov"] = soft_coverage(vu[fv], vv[fv], px, py, self.soft)[0]
+                frags.append(f)
         frags.sort(key=lambda f: (int(P.dbits[f["id"]]), f["id"]))
         return frags
 
@@ -312,9 +359,13 @@ def composite(frags, mode=FULL, t_eps=T_EPS, t_product=False, bg=(0.0, 0.0, 0.0)
                 T = T * (1.0 - O * a)
             else:
                 m = f["mask"]
-                if m == 0:
+                if "cov" in f:  # soft-edge coverage: a fragment wherever its widened rect holds the pixel
+                    assert mode == FULL and not t_product
+                    o = np.asarray(f["cov"], np.float64)
+                elif m == 0:
                     continue
-                o = np.array([(m >> j) & 1 for j in range(4)], np.float64)
+                else:
+                    o = np.array([(m >> j) & 1 for j in range(4)], np.float64)
                 if not in_ent:
                     T_in = T
                     t = np.ones(4)
@@ -345,10 +396,10 @@ def composite(frags, mode=FULL, t_eps=T_EPS, t_product=False, bg=(0.0, 0.0, 0.0)
 
 
 def render_pixels(scene, pixels, cam_index=0, mode=FULL, t_eps=T_EPS, t_product=False,
-                  bg=(0.0, 0.0, 0.0), cov3d=None, frame=None):
+                  bg=(0.0, 0.0, 0.0), cov3d=None, frame=None, soft=None):
     """Composite an explicit list of pixels [(x, y), ...] by brute-force gather
     over all primitives.  Returns (rgb [K,3], T [K], tie [K], wsum [K])."""
-    fr = frame or Frame(scene, cam_index, cov3d)
+    fr = frame or Frame(scene, cam_index, cov3d, soft)
     K = len(pixels)
     rgb = np.zeros((K, 3))
     T = np.zeros(K)
@@ -364,13 +415,13 @@ def render_pixels(scene, pixels, cam_index=0, mode=FULL, t_eps=T_EPS, t_product=
 
 
 def render_image(scene, cam_index=0, mode=FULL, t_eps=T_EPS, t_product=False,
-                 bg=(0.0, 0.0, 0.0), cov3d=None, frame=None):
+                 bg=(0.0, 0.0, 0.0), cov3d=None, frame=None, soft=None):
     """Full image by primitive-major gather: every (primitive, pixel-in-rect)
     pair is evaluated, pairs are grouped per pixel, ordered by (depth bits,
     id) and composited.  Returns dict rgb [H,W,3], T [H,W], tie [H,W],
     wsum [H,W], nfrag [H,W], depth [H,W] (expected depth, +inf where nothing
-    blends)."""
-    fr = frame or Frame(scene, cam_index, cov3d)
+    blends).  soft: soft-edge width sigma in pixels (FULL mode only)."""
+    fr = frame or Frame(scene, cam_index, cov3d, soft)
     P = fr.P
     W, H = fr.cam.width, fr.cam.height
     ids = np.nonzero(P.valid)[0]
