@@ -111,12 +111,21 @@ enum {
     UMGS_RENDER_ASYNC = 8,          /* no host read-back inside umgs_render: the (tile, primitive) pairs
                                        are held to the frame's reserved capacity (umgs_frame_reserve);
                                        check the result with umgs_frame_check */
-    UMGS_RENDER_DEPTH = 16          /* FULL mode only, needs a frame: also keep each pixel's expected
+    UMGS_RENDER_DEPTH = 16,         /* FULL mode only, needs a frame: also keep each pixel's expected
                                        depth sum_i w_i z_i / sum_i w_i over its blended fragments (w_i
                                        the blend weight of Eq. 2 or Eq. 9, z_i the camera depth of a
                                        Gaussian's mean or a triangle's perspective-correct depth at the
                                        pixel centre; +inf where nothing blends), for umgs_frame_depth;
                                        not with SAVE_BACKWARD, MIXED or T_PRODUCT. */
+    UMGS_RENDER_SOFT_EDGE = 32      /* FULL mode only (an extension beyond the paper): the binary sample
+                                       coverage o^j of Eq. 7-8 becomes c^j = prod_e sigmoid(d_e / edge_sigma),
+                                       d_e the signed distance in pixels (positive inside) from sample j to
+                                       edge e of the unsnapped projected triangle; a triangle is a fragment
+                                       of every pixel of its pixel rect widened by ceil(8 edge_sigma) pixels
+                                       and Eq. 7-9 use c for o.  With SAVE_BACKWARD, umgs_render_backward
+                                       also carries the gradient through c to the vertex positions.
+                                       Needs 0 < edge_sigma <= 16; not with MIXED, T_PRODUCT, DEPTH or a
+                                       persistent schedule (sched > 0).  Grid launch of its own compositor. */
 };
 
 typedef struct {
@@ -127,6 +136,7 @@ typedef struct {
     int32_t flags;           /* UMGS_RENDER_* bits */
     int32_t sched;           /* compositor schedule: 0 = one CTA per tile; k > 0 = persistent launch with
                                 k CTAs per SM taking tiles in decreasing order of list length */
+    float edge_sigma;        /* UMGS_RENDER_SOFT_EDGE: edge width sigma in pixels (default 0) */
 } umgs_render_opts;
 
 /* Gradient outputs of umgs_render_backward; every pointer is nullable (not
@@ -264,7 +274,8 @@ umgs_status umgs_frame_lists(const umgs_frame* frame, int64_t* tile_ptr, int32_t
  * UMGS_RENDER_SAVE_BACKWARD (blend mode FULL), computes dL/d of the inputs:
  * Gaussian means, quats, scales (or cov3d), opacities, SH; mesh vertex
  * positions (through the perspective-correct attribute interpolation), vertex
- * colours and alphas.  The sorted lists of the frame are replayed back to
+ * colours and alphas (vertex positions also through the sample coverage
+ * after a UMGS_RENDER_SOFT_EDGE render).  The sorted lists of the frame are replayed back to
  * front per pixel; Gaussian transmittance is recovered by division
  * (alpha <= 0.99), triangle entities use the per-pixel stack of sub-sample
  * transmittances saved by the forward, so opaque triangles need no division.
@@ -414,7 +425,8 @@ void umgs_graph_destroy(umgs_graph* graph);
 
 /* Autotuner: renders the given workload with every tile size (8, 16, 32)
  * and compositor schedule (one CTA per tile; persistent with 1, 2 or 4 CTAs
- * per SM), 1 warm-up + 3 timed renders each (CUDA events on `stream`), and
+ * per SM; one CTA per tile only with UMGS_RENDER_SOFT_EDGE), 1 warm-up +
+ * 3 timed renders each (CUDA events on `stream`), and
  * writes the fastest tile_size and sched into *inout (other fields kept) and
  * its time in ms per render into *best_ms (nullable).  out_rgbt receives the
  * renders ([ncams,H,W,4]).  Synchronises. */

@@ -160,6 +160,12 @@ umgs_status umgs_render(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_mesh*
          (opts.flags & (UMGS_RENDER_SAVE_BACKWARD | UMGS_RENDER_MIXED | UMGS_RENDER_T_PRODUCT))))
         return fail(ctx, UMGS_ERR_INVALID_ARG,
                     "UMGS_RENDER_DEPTH needs a frame, FULL mode and none of SAVE_BACKWARD, MIXED, T_PRODUCT");
+    if ((opts.flags & UMGS_RENDER_SOFT_EDGE) &&
+        (opts.blend_mode != UMGS_BLEND_FULL || !(opts.edge_sigma > 0.f) || !(opts.edge_sigma <= 16.f) ||
+         opts.sched > 0 || (opts.flags & (UMGS_RENDER_MIXED | UMGS_RENDER_T_PRODUCT | UMGS_RENDER_DEPTH))))
+        return fail(ctx, UMGS_ERR_INVALID_ARG,
+                    "UMGS_RENDER_SOFT_EDGE needs FULL mode, 0 < edge_sigma <= 16, sched 0 and none of MIXED, "
+                    "T_PRODUCT, DEPTH");
     if (!cams || ncams < 1) return fail(ctx, UMGS_ERR_INVALID_ARG, "need at least one camera");
     if (!out_rgbt) return fail(ctx, UMGS_ERR_INVALID_ARG, "out_rgbt is NULL");
     if (nmeshes < 0 || (nmeshes > 0 && !meshes)) return fail(ctx, UMGS_ERR_INVALID_ARG, "bad mesh array");

@@ -30,6 +30,7 @@
 #include <cmath>
 
 #include "internal.h"
+#include "soft_edge.cuh"
 
 namespace umgs {
 
@@ -66,7 +67,10 @@ __device__ __forceinline__ void warp_sum_transpose(float (&v)[V], int lane) {
 
 // 16x16 tiles: registers capped for four resident CTAs per SM (32 warps),
 // which hides the per-batch barriers better than the three of an uncapped build
-template <int TS>
+// SOFT: replay of a UMGS_RENDER_SOFT_EDGE render (soft-edge sample coverage
+// c^j; a triangle is a fragment wherever its rect holds the pixel), with the
+// gradient through c^j added to the vertex screen positions.
+template <int TS, bool SOFT>
 __global__ void __launch_bounds__(TS * TS, TS == 16 ? 4 : 1) composite_bwd_kernel(
     const uint32_t* __restrict__ ids, const int64_t* __restrict__ off,
     const GRec* __restrict__ grec, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
@@ -216,7 +220,14 @@ __global__ void __launch_bounds__(TS * TS, TS == 16 ? 4 : 1) composite_bwd_kerne
                 // ---- triangle fragment
                 const TRec& t = *reinterpret_cast<const TRec*>(&s_rec[k][0]);
                 int mask = 0;
-                if (active) {
+                float cov[4] = {0.f, 0.f, 0.f, 0.f}, sg = 0.f, il[3], sgm[4][3];
+                if (SOFT) {
+                    if (active && px >= (int)(t.rx & 0xffff) && px <= (int)(t.rx >> 16) &&
+                        py >= (int)(t.ry & 0xffff) && py <= (int)(t.ry >> 16)) {
+                        mask = 0xf;  // a fragment of this pixel
+                        soft_coverage(t, qx, qy, cov, sg, il, sgm);
+                    }
+                } else if (active) {
                     long long E[3];
 #pragma unroll
                     for (int e = 0; e < 3; ++e) E[e] = (long long)t.A[e] * scx + (long long)t.B[e] * scy + t.C[e];
@@ -267,14 +278,22 @@ __global__ void __launch_bounds__(TS * TS, TS == 16 ? 4 : 1) composite_bwd_kerne
                     const float alpha = fminf(fmaxf(araw, 0.f), 1.f);
                     const float gc = gr * col[0] + gg * col[1] + gb * col[2];
                     float dalpha = 0.f, wsum = 0.f;
+                    float dcov[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
-                        if ((mask >> j) & 1) {
+                        if (SOFT) {  // o^j = c^j in [0, 1]
+                            const float cj = cov[j];
+                            dcov[j] = s[j] * alpha * (gc - Uj[j]);
+                            dalpha += s[j] * cj * (gc - Uj[j]);
+                            wsum += s[j] * cj * alpha;
+                            Uj[j] = alpha * cj * gc + (1.f - alpha * cj) * Uj[j];
+                        } else if ((mask >> j) & 1) {
                             dalpha += s[j] * (gc - Uj[j]);
                             wsum += s[j] * alpha;
                             Uj[j] = alpha * gc + (1.f - alpha) * Uj[j];
                         }
                     }
+                    if (SOFT) soft_coverage_grad(t, qx, qy, cov, sg, il, sgm, dcov, &v[0], &v[3]);
                     T = (s[0] + s[1]) + (s[2] + s[3]);
                     const float dc[3] = {wsum * gr, wsum * gg, wsum * gb};
                     const float dar = (araw >= 0.f && araw <= 1.f) ? dalpha : 0.f;
@@ -687,7 +706,10 @@ umgs_status render_backward(umgs_ctx* ctx, umgs_frame* fr, const umgs_gaussians*
         fr->stack_cap = need + need / 4 + 1;
         UMGS_TRY(fr->stack.reserve(sizeof(float4) * npix * fr->stack_cap));
         UMGS_TRY(fr->rerun_out.reserve(sizeof(float4) * npix));
-        UMGS_TRY(launch_composite(fr, fr->opts, fr->rerun_out.as<float>(), stream));
+        if (fr->opts.flags & UMGS_RENDER_SOFT_EDGE)
+            UMGS_TRY(launch_soft_composite(fr, fr->opts, fr->rerun_out.as<float>(), stream));
+        else
+            UMGS_TRY(launch_composite(fr, fr->opts, fr->rerun_out.as<float>(), stream));
     }
     UMGS_TRY(fr->ggrad.reserve(sizeof(float) * 12 * std::max<int64_t>(1, Ng * fr->ncams)));
     UMGS_TRY(fr->tgrad.reserve(sizeof(float) * 24 * std::max<int64_t>(1, Nt * fr->ncams)));
@@ -698,18 +720,19 @@ umgs_status render_backward(umgs_ctx* ctx, umgs_frame* fr, const umgs_gaussians*
         const unsigned M = (unsigned)fr->num_tiles;
         const int tpc = fr->tiles_x * fr->tiles_y;
         const float4* dout = reinterpret_cast<const float4*>(dL_drgbt);
-#define UMGS_LAUNCH(TSV)                                                                                         \
+#define UMGS_LAUNCH(TSV, SOFTV)                                                                                  \
         /* per call: the attribute belongs to the current device */                                         \
-        UMGS_TRY(cudaFuncSetAttribute(composite_bwd_kernel<TSV>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+        UMGS_TRY(cudaFuncSetAttribute(composite_bwd_kernel<TSV, SOFTV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                       bwd_smem_bytes<TSV>()));                                                   \
-        launch_pdl(composite_bwd_kernel<TSV>, M, TSV * TSV, bwd_smem_bytes<TSV>(), stream,                               \
+        launch_pdl(composite_bwd_kernel<TSV, SOFTV>, M, TSV * TSV, bwd_smem_bytes<TSV>(), stream,                        \
             fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->trec.as<TRec>(), Ng, Nt,               \
             fr->tiles_x, tpc, fr->W, fr->H, fr->bg[0], fr->bg[1], fr->bg[2], dout, fr->last.as<int32_t>(),         \
             fr->tfin.as<float>(), fr->ntri.as<int32_t>(), fr->stack.as<float4>(), npix, fr->ggrad.as<float>(),     \
             fr->tgrad.as<float>())
-        if (fr->tile == 16) { UMGS_LAUNCH(16); }
-        else if (fr->tile == 8) { UMGS_LAUNCH(8); }
-        else { UMGS_LAUNCH(32); }
+        const bool soft = (fr->opts.flags & UMGS_RENDER_SOFT_EDGE) != 0;
+        if (fr->tile == 16) { if (soft) { UMGS_LAUNCH(16, true); } else { UMGS_LAUNCH(16, false); } }
+        else if (fr->tile == 8) { if (soft) { UMGS_LAUNCH(8, true); } else { UMGS_LAUNCH(8, false); } }
+        else { if (soft) { UMGS_LAUNCH(32, true); } else { UMGS_LAUNCH(32, false); } }
 #undef UMGS_LAUNCH
         UMGS_TRY(cudaGetLastError());
     }

@@ -140,8 +140,10 @@ umgs_status umgs_autotune(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_mes
     const int scheds[4] = {0, 1, 2, 4};
     double best = 1e30;
     umgs_render_opts bo = *inout;
+    // the soft-edge compositor has the grid launch only
+    const int nsched = (inout->flags & UMGS_RENDER_SOFT_EDGE) ? 1 : 4;
     for (int ti = 0; ti < 3 && st == UMGS_OK; ++ti)
-        for (int si = 0; si < 4 && st == UMGS_OK; ++si) {
+        for (int si = 0; si < nsched && st == UMGS_OK; ++si) {
             umgs_render_opts o = *inout;
             o.tile_size = tiles[ti];
             o.sched = scheds[si];

@@ -183,6 +183,8 @@ umgs_status bind_forward(umgs_ctx* ctx, const umgs_gaussians* g, const float* V,
                          int64_t* out_num_fallback, cudaStream_t stream);
 
 cudaError_t launch_composite(umgs_frame* fr, const umgs_render_opts& opts, float* out_rgbt, cudaStream_t stream);
+// compositor of UMGS_RENDER_SOFT_EDGE renders (soft.cu)
+cudaError_t launch_soft_composite(umgs_frame* fr, const umgs_render_opts& opts, float* out_rgbt, cudaStream_t stream);
 cudaError_t reserve_binning(umgs_frame* fr, int64_t rcap, int64_t kcap);
 // stable LSD radix sort of (k, v) on key bits [lo, lo + bits) (binning
 // stage); the element count is read from n_dev (at most n_cap, which sizes

@@ -365,7 +365,8 @@ __global__ void __launch_bounds__(256) setup_triangles_kernel(
     int64_t tri_base /* index of this mesh's first face among all triangles */, int64_t nt_total,
     int64_t id_base /* unified id of this mesh's first face */, const DevCam* __restrict__ cams, int ncams,
     int ts, int tiles_x, int tiles_per_cam, TRec* __restrict__ trec, BinInfo* __restrict__ bin,
-    int64_t ntot_prims, int32_t* __restrict__ status) {
+    int64_t ntot_prims, int32_t* __restrict__ status,
+    int dilate /* soft-edge coverage: rect widened by this many pixels */, float isig /* 1/edge_sigma or 0 */) {
     pdl_enter();
     const int64_t f = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (f >= nf) return;
@@ -430,8 +431,10 @@ __global__ void __launch_bounds__(256) setup_triangles_kernel(
         if (area < 0) { ox[1] = sx[2]; ox[2] = sx[1]; oy[1] = sy[2]; oy[2] = sy[1]; }
         const long long xmin = min(sx[0], min(sx[1], sx[2])), xmax = max(sx[0], max(sx[1], sx[2]));
         const long long ymin = min(sy[0], min(sy[1], sy[2])), ymax = max(sy[0], max(sy[1], sy[2]));
-        const long long xlo = max(ceil_div256(xmin - 224), 0LL), xhi = min(floor_div256(xmax - 32), (long long)(C.W - 1));
-        const long long ylo = max(ceil_div256(ymin - 224), 0LL), yhi = min(floor_div256(ymax - 32), (long long)(C.H - 1));
+        const long long xlo = max(ceil_div256(xmin - 224) - dilate, 0LL);
+        const long long xhi = min(floor_div256(xmax - 32) + dilate, (long long)(C.W - 1));
+        const long long ylo = max(ceil_div256(ymin - 224) - dilate, 0LL);
+        const long long yhi = min(floor_div256(ymax - 32) + dilate, (long long)(C.H - 1));
         valid = valid && xlo <= xhi && ylo <= yhi;
         BinInfo bi;
         bi.dbits = __float_as_uint(fdv(fa(fa(Zv[0], Zv[1]), Zv[2]), 3.f));
@@ -465,7 +468,7 @@ __global__ void __launch_bounds__(256) setup_triangles_kernel(
 #pragma unroll
         t.rx = bi.rx;
         t.ry = bi.ry;
-        t.pad2 = 0.f;
+        t.pad2 = isig;  // soft-edge coverage: 1/edge_sigma (0: binary sample coverage)
         trec[(int64_t)cam * nt_total + tri_base + f] = t;
     }
 }
@@ -1073,6 +1076,7 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
                            const umgs_camera* cams, int32_t ncams, const umgs_render_opts& opts, float* out_rgbt,
                            umgs_frame* fr, cudaStream_t stream) {
     const int ts = opts.tile_size;
+    const bool soft = (opts.flags & UMGS_RENDER_SOFT_EDGE) != 0;
     const int W = cams[0].width, H = cams[0].height;
     const int tiles_x = (W + ts - 1) / ts, tiles_y = (H + ts - 1) / ts;
     const int tiles_per_cam = tiles_x * tiles_y;
@@ -1202,7 +1206,8 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
                 me.verts, me.faces, me.vcolor, me.valpha, me.falpha, mesh_tex[m] >= 0 ? me.uv : nullptr,
                 mesh_tex[m], me.nv, me.nf, tri_base, Nt, Ng + tri_base,
                 dcams, ncams, ts, tiles_x, tiles_per_cam, fr->trec.as<TRec>(), fr->bin.as<BinInfo>(), Ntot,
-                fr->status.as<int32_t>());
+                fr->status.as<int32_t>(), soft ? (int)ceilf(8.f * opts.edge_sigma) : 0,
+                soft ? 1.f / opts.edge_sigma : 0.f);
             UMGS_TRY(cudaGetLastError());
         }
         tri_base += me.nf;
@@ -1330,7 +1335,8 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     }
     {
         StageTimer tm_comp(ctx, UMGS_STAGE_COMPOSITE, stream);
-        UMGS_TRY(launch_composite(fr, opts, out_rgbt, stream));
+        if (soft) UMGS_TRY(launch_soft_composite(fr, opts, out_rgbt, stream));
+        else UMGS_TRY(launch_composite(fr, opts, out_rgbt, stream));
     }
     fr->valid = true;
 #undef UMGS_TRY

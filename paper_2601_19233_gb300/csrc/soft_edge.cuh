@@ -1,0 +1,85 @@
+// Soft-edge sample coverage of a triangle (UMGS_RENDER_SOFT_EDGE; an
+// extension beyond the paper that makes the composite of Eq. 7-9
+// differentiable in the vertex positions through coverage).
+//
+// For sample s_j of the pixel and edge e = (a, b) = (e+1, e+2) of the
+// unsnapped projected triangle (record fields u, v):
+//   lambda_e(s) = (u_a - s_x)(v_b - s_y) - (u_b - s_x)(v_a - s_y)
+//     (twice the signed area of (s, P_a, P_b), the stable relative form),
+//   d_e = sg lambda_e / |P_b - P_a|   (signed distance, positive inside;
+//     sg = sign of the triangle's signed area),
+//   c^j = prod_e sigmoid(d_e / sigma),  sigma = 1 / t.pad2.
+// A triangle of zero area covers nothing.
+#pragma once
+
+#include "common.cuh"
+
+namespace umgs {
+
+__device__ __forceinline__ float soft_orientation(const TRec& t) {
+    const float area = (t.u[1] - t.u[0]) * (t.v[2] - t.v[0]) - (t.u[2] - t.u[0]) * (t.v[1] - t.v[0]);
+    return area > 0.f ? 1.f : (area < 0.f ? -1.f : 0.f);
+}
+
+// sigmoid(x) with the accurate expf (exp(-x) overflows to inf for x < -88:
+// the result is then 0, the limit)
+__device__ __forceinline__ float soft_sigmoid(float x) { return 1.f / (1.f + expf(-x)); }
+
+// c^j of pixel centre (qx, qy) for the four samples; sg, inverse edge lengths
+// and the per-(sample, edge) sigmoids are returned for the backward
+__device__ __forceinline__ void soft_coverage(const TRec& t, float qx, float qy, float c[4], float& sg,
+                                              float il[3], float sgm[4][3]) {
+    sg = soft_orientation(t);
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int a = (e + 1) % 3, b = (e + 2) % 3;
+        const float ex = t.u[b] - t.u[a], ey = t.v[b] - t.v[a];
+        const float L = sqrtf(ex * ex + ey * ey);
+        il[e] = L > 0.f ? 1.f / L : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float sx = qx + (float)sample_dx(j) * (1.f / 256.f);
+        const float sy = qy + (float)sample_dy(j) * (1.f / 256.f);
+        float cj = sg != 0.f ? 1.f : 0.f;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            const int a = (e + 1) % 3, b = (e + 2) % 3;
+            const float lam = (t.u[a] - sx) * (t.v[b] - sy) - (t.u[b] - sx) * (t.v[a] - sy);
+            const float s = soft_sigmoid(sg * lam * il[e] * t.pad2);
+            sgm[j][e] = s;
+            cj *= s;
+        }
+        c[j] = cj;
+    }
+}
+
+// Adds d(sum_j dc[j] c^j) / d(u_k, v_k) to du[k], dv[k] (k = vertex):
+// dc^j/dd_e = c^j (1 - sigmoid_e) / sigma and, with L = |P_b - P_a|,
+// dd/dx = sg (dlambda/dx) / L - d (dL/dx) / L.
+__device__ __forceinline__ void soft_coverage_grad(const TRec& t, float qx, float qy, const float c[4], float sg,
+                                                   const float il[3], const float sgm[4][3], const float dc[4],
+                                                   float du[3], float dv[3]) {
+    if (sg == 0.f) return;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (dc[j] == 0.f || c[j] == 0.f) continue;
+        const float sx = qx + (float)sample_dx(j) * (1.f / 256.f);
+        const float sy = qy + (float)sample_dy(j) * (1.f / 256.f);
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            const int a = (e + 1) % 3, b = (e + 2) % 3;
+            const float gd = dc[j] * c[j] * (1.f - sgm[j][e]) * t.pad2;  // dL/dd_e
+            const float lam = (t.u[a] - sx) * (t.v[b] - sy) - (t.u[b] - sx) * (t.v[a] - sy);
+            const float d = sg * lam * il[e];
+            const float ex = (t.u[b] - t.u[a]) * il[e], ey = (t.v[b] - t.v[a]) * il[e];  // unit edge
+            const float k = sg * il[e], m = d * il[e];
+            du[a] += gd * (k * (t.v[b] - sy) + m * ex);
+            du[b] += gd * (-k * (t.v[a] - sy) - m * ex);
+            dv[a] += gd * (-k * (t.u[b] - sx) + m * ey);
+            dv[b] += gd * (k * (t.u[a] - sx) - m * ey);
+        }
+    }
+}
+
+}  // namespace umgs

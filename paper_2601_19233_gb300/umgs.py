@@ -28,6 +28,7 @@ RENDER_MIXED = 2
 RENDER_T_PRODUCT = 4
 RENDER_ASYNC = 8
 RENDER_DEPTH = 16
+RENDER_SOFT_EDGE = 32
 DEFORM_FRAME, DEFORM_LITERAL, DEFORM_ONE_RING = 0, 1, 16
 
 
@@ -68,7 +69,8 @@ class CMeshGrads(ctypes.Structure):
 
 class CRenderOpts(ctypes.Structure):
     _fields_ = [("tile_size", ctypes.c_int32), ("blend_mode", ctypes.c_int32), ("t_eps", ctypes.c_float),
-                ("bg", ctypes.c_float * 3), ("flags", ctypes.c_int32), ("sched", ctypes.c_int32)]
+                ("bg", ctypes.c_float * 3), ("flags", ctypes.c_int32), ("sched", ctypes.c_int32),
+                ("edge_sigma", ctypes.c_float)]
 
 
 _lib = None
@@ -308,13 +310,17 @@ def mesh_to_device(m, device="cuda") -> DevMesh:
 
 
 def render_opts(tile_size=16, blend_mode=BLEND_FULL, t_eps=1e-4, bg=(0.0, 0.0, 0.0), save=False,
-                mixed=False, sched=0, t_product=False, asynchronous=False, depth=False) -> CRenderOpts:
+                mixed=False, sched=0, t_product=False, asynchronous=False, depth=False,
+                edge_sigma=None) -> CRenderOpts:
+    """edge_sigma: soft-edge triangle coverage of that width in pixels
+    (UMGS_RENDER_SOFT_EDGE), or None for the binary sample coverage."""
     o = CRenderOpts()
     lib().umgs_default_render_opts(ctypes.byref(o))
     o.sched = int(sched)
     o.flags = ((RENDER_SAVE_BACKWARD if save else 0) | (RENDER_MIXED if mixed else 0)
                | (RENDER_T_PRODUCT if t_product else 0) | (RENDER_ASYNC if asynchronous else 0)
-               | (RENDER_DEPTH if depth else 0))
+               | (RENDER_DEPTH if depth else 0) | (RENDER_SOFT_EDGE if edge_sigma else 0))
+    o.edge_sigma = float(edge_sigma or 0.0)
     o.tile_size = int(tile_size)
     o.blend_mode = int(blend_mode)
     o.t_eps = float(t_eps)
