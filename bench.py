@@ -527,10 +527,29 @@ def run_forms(ctx, dev, steps):
         dl = (2.0 / out.numel()) * (out - target)
         return umgs.render_backward(ctx, fr, g, ms, dl)
     t_fb = _time(fb, steps)
+    keys_bin = int(fr.counts()[0])
     forms["differentiable_8x512"] = {
         "workload": "8 orbit views 512x512, 300k Gaussians SH3 + 50k-face torus, L2 loss to a perturbed-scene render",
         "fwd_views_per_s": round(nv * 1e3 / t_f, 1), "fwd_ms": round(t_f, 3),
         "fwd_bwd_views_per_s": round(nv * 1e3 / t_fb, 1), "fwd_bwd_ms": round(t_fb, 3)}
+    # the same step with soft-edge triangle coverage (sigma 0.5 px): the
+    # backward also reaches the vertex positions through coverage
+    sig = 0.5
+    t_sf = _time(lambda: umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(16, edge_sigma=sig), out=out, frame=fr),
+                 steps)
+    keys_soft = int(fr.counts()[0])
+    so_soft = umgs.render_opts(16, save=True, edge_sigma=sig)
+
+    def fb_soft():
+        umgs.render(ctx, g, ms, sc.cameras, so_soft, out=out, frame=fr)
+        dl = (2.0 / out.numel()) * (out - target)
+        return umgs.render_backward(ctx, fr, g, ms, dl)
+    t_sfb = _time(fb_soft, steps)
+    forms["soft_edge_8x512"] = {
+        "workload": "differentiable_8x512 with soft-edge triangle coverage, edge_sigma 0.5 px (rects widened 4 px)",
+        "fwd_views_per_s": round(nv * 1e3 / t_sf, 1), "fwd_ms": round(t_sf, 3),
+        "fwd_bwd_views_per_s": round(nv * 1e3 / t_sfb, 1), "fwd_bwd_ms": round(t_sfb, 3),
+        "keys": keys_soft, "keys_binary_coverage": keys_bin}
     del g, ms, gp, target, out, fr
     torch.cuda.empty_cache()
     # config 4: 4K, 6M Gaussians + 2M triangles, fp32 vs bf16 SH + fp16 records

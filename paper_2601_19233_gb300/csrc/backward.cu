@@ -70,8 +70,9 @@ __device__ __forceinline__ void warp_sum_transpose(float (&v)[V], int lane) {
 // SOFT: replay of a UMGS_RENDER_SOFT_EDGE render (soft-edge sample coverage
 // c^j; a triangle is a fragment wherever its rect holds the pixel), with the
 // gradient through c^j added to the vertex screen positions.
+// (the soft replay holds more live values: two CTAs per SM, no register cap spills)
 template <int TS, bool SOFT>
-__global__ void __launch_bounds__(TS * TS, TS == 16 ? 4 : 1) composite_bwd_kernel(
+__global__ void __launch_bounds__(TS * TS, TS == 16 ? (SOFT ? 2 : 4) : 1) composite_bwd_kernel(
     const uint32_t* __restrict__ ids, const int64_t* __restrict__ off,
     const GRec* __restrict__ grec, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
     int tiles_per_cam, int W, int H, float bg0,

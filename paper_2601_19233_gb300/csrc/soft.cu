@@ -4,9 +4,12 @@
 // replaced by the soft-edge coverage c^j of soft_edge.cuh.  A triangle is a
 // fragment of every pixel of its (widened) pixel rect.
 //
-// One CTA per tile, one thread per pixel (row-major in the tile); records of
-// the tile's sorted list are staged through shared memory in batches of
-// kSoftBatch and every pixel walks the whole batch.  SAVE keeps the state
+// One CTA per tile, one thread per pixel; warp w owns an 8 x 4 block of the
+// tile (block_pixel).  Records of the tile's sorted list are staged through
+// shared memory in batches of kSoftBatch together with the mask of the warp
+// blocks that can hold a fragment of each (Gaussian: its alpha >= 1/255
+// octagon; triangle: its widened rect), and every warp walks only its own
+// records, in list order.  SAVE keeps the state
 // composite_bwd_kernel<TS, true> replays: final T, the number of triangle
 // fragments and, per triangle fragment, the four sample transmittances before
 // it scaled by T_in/4.
@@ -28,11 +31,17 @@ __global__ void __launch_bounds__(TS * TS) composite_soft_kernel(
     constexpr int NT = TS * TS;
     __shared__ float4 s_rec[kSoftBatch][10];
     __shared__ uint32_t s_id[kSoftBatch];
+    __shared__ uint32_t s_wmask[kSoftBatch];
+    __shared__ uint8_t s_list[(NT / 32) * kSoftBatch];
     const int tile = blockIdx.x;
     const int cam = tile / tiles_per_cam;
     const int lt = tile - cam * tiles_per_cam;
     const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
-    const int px = tx * TS + (int)(threadIdx.x % TS), py = ty * TS + (int)(threadIdx.x / TS);
+    int lx, ly;
+    block_pixel<TS>(threadIdx.x, lx, ly);
+    const int px = tx * TS + lx, py = ty * TS + ly;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tile_x0 = tx * TS, tile_y0 = ty * TS;
     const bool inside = px < W && py < H;
     const int64_t beg = off[tile], end = off[tile + 1];
     const GRec* G = grec + (int64_t)cam * Ng;
@@ -51,19 +60,38 @@ __global__ void __launch_bounds__(TS * TS) composite_soft_kernel(
         for (int k = threadIdx.x; k < n; k += NT) {
             const uint32_t id = ids[b0 + k];
             s_id[k] = id;
+            uint32_t wm = 0u;  // not a record of this frame: no fragment
             if (id < Ng) {
                 const float4* src = reinterpret_cast<const float4*>(G + id);
-                s_rec[k][0] = src[0]; s_rec[k][1] = src[1]; s_rec[k][2] = src[2];
+                const float4 a = src[0], b = src[1], c = src[2];
+                s_rec[k][0] = a; s_rec[k][1] = b; s_rec[k][2] = c;
+                const uint32_t rx = __float_as_uint(c.y), ry = __float_as_uint(c.z);
+                wm = gauss_block_mask<TS>(a.x, a.y, a.z, a.w, b.x, b.y, (int)(rx & 0xffff), (int)(rx >> 16),
+                                          (int)(ry & 0xffff), (int)(ry >> 16), tile_x0, tile_y0);
             } else if (id < Ng + Nt) {
                 const float4* src = reinterpret_cast<const float4*>(TR + (id - Ng));
 #pragma unroll
                 for (int q = 0; q < 10; ++q) s_rec[k][q] = src[q];
+                const TRec& tr = *reinterpret_cast<const TRec*>(&s_rec[k][0]);
+                wm = box_block_mask<TS>((int)(tr.rx & 0xffff), (int)(tr.rx >> 16), (int)(tr.ry & 0xffff),
+                                        (int)(tr.ry >> 16), tile_x0, tile_y0);
             }
+            s_wmask[k] = wm;
         }
         __syncthreads();
-        for (int k = 0; k < n && !done; ++k) {
+        // this warp's records of the batch, in order
+        uint8_t* lst = s_list + warp * kSoftBatch;
+        int cnt = 0;
+        for (int c0 = 0; c0 < n; c0 += 32) {
+            const bool mine = c0 + lane < n && ((s_wmask[c0 + lane] >> warp) & 1u);
+            const unsigned bal = __ballot_sync(0xffffffffu, mine);
+            if (mine) lst[cnt + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)(c0 + lane);
+            cnt += __popc(bal);
+        }
+        __syncwarp();
+        for (int li = 0; li < cnt && !done; ++li) {
+            const int k = lst[li];
             const uint32_t id = s_id[k];
-            if (id >= Ng + Nt) continue;  // not a record of this frame
             if (id < Ng) {
                 // Gaussian (Eq. 1-2), as in the binary-coverage compositor
                 const float4 q0 = s_rec[k][0], q1 = s_rec[k][1], q2 = s_rec[k][2];
