@@ -151,7 +151,8 @@ typedef struct {
 } umgs_gaussian_grads;
 
 typedef struct {
-    float* verts;      /* [nv,3] (through attribute interpolation; coverage is piecewise constant) */
+    float* verts;      /* [nv,3] (through attribute interpolation; through the sample coverage too
+                          after a UMGS_RENDER_SOFT_EDGE render, binary coverage being piecewise constant) */
     float* vcolor;     /* [nv,3] */
     float* valpha;     /* [nv]   (when the mesh has valpha and no falpha) */
     float* falpha;     /* [nf]   (when the mesh has falpha) */
