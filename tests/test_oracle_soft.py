@@ -163,3 +163,32 @@ def test_fd_vertex_positions_through_coverage():
         assert abs(fd - ga[idx]) <= 1e-5 * scale + 1e-6 * abs(fd), (idx, fd, ga[idx], scale)
         checked += 1
     assert checked >= 7
+
+
+def test_coverage_is_invariant_to_vertex_order():
+    rng = np.random.default_rng(11)
+    tu = rng.uniform(0, 20, (50, 3))
+    tv = rng.uniform(0, 20, (50, 3))
+    for px, py in [(5, 5), (10, 12), (17, 3)]:
+        c = R.soft_coverage(tu, tv, px, py, 0.7)
+        for perm in ([1, 2, 0], [2, 0, 1], [0, 2, 1], [2, 1, 0]):
+            c2 = R.soft_coverage(tu[:, perm], tv[:, perm], px, py, 0.7)
+            assert np.abs(c - c2).max() < 1e-12
+
+
+def test_widened_rects_are_the_binary_rects_plus_the_dilation():
+    sc = _scene(3)
+    cam = sc.cameras[0]
+    for sigma in (0.3, 0.5, 1.0):
+        R_ = R.soft_dilation(sigma)
+        m = sc.meshes[0]
+        hard = cn.setup_triangles(m.verts, m.faces, cam)
+        soft = cn.setup_triangles(m.verts, m.faces, cam, R_)
+        both = hard["valid"] & soft["valid"]
+        h, s = hard["rect"][both], soft["rect"][both]
+        assert np.array_equal(s[:, 0], np.maximum(h[:, 0] - R_, 0))
+        assert np.array_equal(s[:, 1], np.minimum(h[:, 1] + R_, cam.width - 1))
+        assert np.array_equal(s[:, 2], np.maximum(h[:, 2] - R_, 0))
+        assert np.array_equal(s[:, 3], np.minimum(h[:, 3] + R_, cam.height - 1))
+        # widening only adds triangles (those whose sample rect was empty)
+        assert np.all(soft["valid"][hard["valid"]])
