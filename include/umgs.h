@@ -262,6 +262,26 @@ umgs_status umgs_frame_check(umgs_frame* frame, void* stream);
  * render itself counts nothing); host output; synchronises `stream`. */
 umgs_status umgs_frame_evaluations(const umgs_frame* frame, int64_t* evals, void* stream);
 
+/* Counters of the last render into `frame` (diagnostic; host output;
+ * synchronises `stream`):
+ *   gaussian_evals, triangle_evals: umgs_frame_evaluations split by the kind
+ *     of record (their sum is N_alg); the compositor's work differs per kind
+ *     (a Gaussian evaluation is an exponential and a blend, Eq. 1-2; a
+ *     triangle evaluation is 12 sample/edge tests, perspective-correct
+ *     attributes and the entity blend, Eq. 7-9);
+ *   fp64_conics: (camera, Gaussian) records whose projected covariance was
+ *     near-singular (det < a c / 1024) and whose conic was therefore inverted
+ *     in fp64 (EWA projection, Sec. 3.2);
+ *   list_entries: total length of the tile lists.
+ * Errors: INVALID_ARG if nothing was rendered into the frame. */
+typedef struct {
+    int64_t gaussian_evals;
+    int64_t triangle_evals;
+    int64_t fp64_conics;
+    int64_t list_entries;
+} umgs_frame_stats;
+umgs_status umgs_frame_stats_read(const umgs_frame* frame, umgs_frame_stats* out, void* stream);
+
 /* Copy the sorted tile lists of the last render into caller buffers (device):
  * tile_ptr [num_tiles+1] int64 (list of tile t is [tile_ptr[t], tile_ptr[t+1])),
  * ids [num_keys] int32 unified primitive ids, dbits [num_keys] uint32 depth
@@ -373,6 +393,13 @@ umgs_status umgs_deform(umgs_ctx* ctx, const umgs_gaussians* rest, const int32_t
  * caller buffer [nv,12] (Delta xyz, r xyz, S xx xy xz yy yz zz).  Async. */
 umgs_status umgs_deform_vertex_table(umgs_ctx* ctx, float* out_table, int64_t nv, void* stream);
 
+/* Number of proxy faces of the last umgs_deform / umgs_deform_compact on
+ * `ctx` whose rest frame [e1, e2, n/sqrt|n|] was a sliver (|e1 x e2| <
+ * 1e-3 |e1||e2|) and was therefore inverted in fp64 (per-face deformation
+ * gradient of the per-vertex transform, Sec. 3.3).  Host output;
+ * synchronises `stream`. */
+umgs_status umgs_deform_fp64_faces(umgs_ctx* ctx, int64_t* count, void* stream);
+
 /* Compact binding: a regrouping of Eq. 12-13, not a step of the paper.
  * Every interpolant that Eq. 13 averages is linear in the proxy vertex
  * rows, so a Gaussian's deformation needs only its distinct bound vertices v
@@ -474,7 +501,10 @@ long long umgs_kernel_launches(void);
  *  - Runs on the CALLING thread's current device and on `stream`.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    before any stream capture.  The address is kept for the life of the
+ *    process: after cudaDeviceReset (or any other teardown of the device's
+ *    primary context) the array may move and this entry point must not be
+ *    called again on that device in this process.
  *  - All calls share the array and it keeps the last call's contents (each
  *    call clears what must start at zero): calls that overlap on the GPU
  *    (several streams or host threads at once) race and give wrong results.

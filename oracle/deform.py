@@ -127,13 +127,15 @@ def polar_log(D):
     return r, S
 
 
-def deform_gaussians(means, quats, scales, face, bary, V, Vd, F, mode=FRAME, cov3d=None, method=FACES):
+def deform_gaussians(means, quats, scales, face, bary, V, Vd, F, mode=FRAME, cov3d=None, method=FACES, table=None):
     """Eq. 12-13 for every Gaussian.
 
     face [N,8] int, bary [N,8,2] (weights of face vertices 1 and 2).
+    table: the per-vertex (Delta, r, S) of vertex_transforms(V, Vd, F, method)
+    when the caller has it already (it depends on the proxy only).
     Returns (mu' [N,3], Sigma' [N,3,3], q' [N,4] (w,x,y,z), w >= 0).
     """
-    delta, r, S = vertex_transforms(V, Vd, F, method)
+    delta, r, S = table if table is not None else vertex_transforms(V, Vd, F, method)
     Fi = np.asarray(F, np.int64)[np.asarray(face, np.int64)]           # [N,8,3]
     b = np.asarray(bary, np.float64)
     w = np.stack([1.0 - b[..., 0] - b[..., 1], b[..., 0], b[..., 1]], -1)  # [N,8,3]

@@ -415,17 +415,26 @@ def render_pixels(scene, pixels, cam_index=0, mode=FULL, t_eps=T_EPS, t_product=
 
 
 def render_image(scene, cam_index=0, mode=FULL, t_eps=T_EPS, t_product=False,
-                 bg=(0.0, 0.0, 0.0), cov3d=None, frame=None, soft=None):
+                 bg=(0.0, 0.0, 0.0), cov3d=None, frame=None, soft=None, window=None):
     """Full image by primitive-major gather: every (primitive, pixel-in-rect)
     pair is evaluated, pairs are grouped per pixel, ordered by (depth bits,
     id) and composited.  Returns dict rgb [H,W,3], T [H,W], tie [H,W],
     wsum [H,W], nfrag [H,W], depth [H,W] (expected depth, +inf where nothing
-    blends).  soft: soft-edge width sigma in pixels (FULL mode only)."""
+    blends).  soft: soft-edge width sigma in pixels (FULL mode only).
+    window: (x0, x1, y0, y1), inclusive: only the pixels of that rectangle are
+    composited (the rect of every primitive is cut to it); the others keep
+    the background and T = 1."""
     fr = frame or Frame(scene, cam_index, cov3d, soft)
     P = fr.P
     W, H = fr.cam.width, fr.cam.height
     ids = np.nonzero(P.valid)[0]
     r = P.rect[ids]
+    if window is not None:
+        x0, x1, y0, y1 = (int(v) for v in window)
+        r = np.stack([np.maximum(r[:, 0], x0), np.minimum(r[:, 1], x1),
+                      np.maximum(r[:, 2], y0), np.minimum(r[:, 3], y1)], 1)
+        keep = (r[:, 0] <= r[:, 1]) & (r[:, 2] <= r[:, 3])
+        ids, r = ids[keep], r[keep]
     w = r[:, 1] - r[:, 0] + 1
     h = r[:, 3] - r[:, 2] + 1
     cnt = w * h

@@ -373,6 +373,26 @@ umgs_status umgs_frame_evaluations(const umgs_frame* frame, int64_t* evals, void
     return frame_evaluations(frame, evals, static_cast<cudaStream_t>(stream));
 }
 
+umgs_status umgs_frame_stats_read(const umgs_frame* frame, umgs_frame_stats* out, void* stream) {
+    if (!frame || !out || !frame->valid) return UMGS_ERR_INVALID_ARG;
+    if (cudaSetDevice(frame->ctx->device) != cudaSuccess) return fail(frame->ctx, UMGS_ERR_CUDA, "cudaSetDevice");
+    return frame_stats(frame, out, static_cast<cudaStream_t>(stream));
+}
+
+umgs_status umgs_deform_fp64_faces(umgs_ctx* ctx, int64_t* count, void* stream) {
+    if (!ctx || !count) return UMGS_ERR_INVALID_ARG;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, UMGS_ERR_CUDA, "cudaSetDevice");
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemcpyAsync(ctx->pinned, ctx->dstatus.as<int32_t>() + 1, sizeof(int32_t),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "reading the fp64 face count");
+    int32_t v = 0;
+    std::memcpy(&v, ctx->pinned, sizeof(v));
+    *count = v;
+    return UMGS_OK;
+}
+
 umgs_status umgs_frame_depth(const umgs_frame* frame, float* out_depth, void* stream) {
     if (!frame || !out_depth) return UMGS_ERR_INVALID_ARG;
     if (!frame->valid || !frame->has_depth)

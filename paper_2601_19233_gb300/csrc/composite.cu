@@ -412,6 +412,7 @@ __global__ void __launch_bounds__(TS * TS) eval_count_kernel(
     const uint32_t* __restrict__ ids, const int64_t* __restrict__ off, const GRec* __restrict__ grec,
     const GRec16* __restrict__ grec16, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
     int tiles_per_cam, int W, int H, const int32_t* __restrict__ last, unsigned long long* __restrict__ count) {
+    // count[0]: evaluations of Gaussian records, count[1]: of triangle records
     const int tile = blockIdx.x;
     const int cam = tile / tiles_per_cam;
     const int lt = tile - cam * tiles_per_cam;
@@ -419,7 +420,7 @@ __global__ void __launch_bounds__(TS * TS) eval_count_kernel(
     int lx, ly;
     block_pixel<TS>(threadIdx.x, lx, ly);
     const int px = tx * TS + lx, py = ty * TS + ly;
-    unsigned long long c = 0;
+    unsigned long long c = 0, ct = 0;
     if (px < W && py < H) {
         const int64_t beg = off[tile], end = off[tile + 1];
         const int32_t l = last[((int64_t)cam * H + py) * W + px];
@@ -440,19 +441,26 @@ __global__ void __launch_bounds__(TS * TS) eval_count_kernel(
                 const TRec& t = trec[(int64_t)cam * Nt + (id - Ng)];
                 rx = t.rx; ry = t.ry;
             }
-            c += (px >= (int)(rx & 0xffff) && px <= (int)(rx >> 16) && py >= (int)(ry & 0xffff) &&
-                  py <= (int)(ry >> 16)) ? 1ull : 0ull;
+            const unsigned long long in = (px >= (int)(rx & 0xffff) && px <= (int)(rx >> 16) &&
+                                           py >= (int)(ry & 0xffff) && py <= (int)(ry >> 16)) ? 1ull : 0ull;
+            if (id < Ng) c += in;
+            else ct += in;
         }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+        ct += __shfl_xor_sync(0xffffffffu, ct, o);
+    }
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+    if ((threadIdx.x & 31) == 0 && ct) atomicAdd(count + 1, ct);
 }
 
-umgs_status frame_evaluations(const umgs_frame* fr, int64_t* evals, cudaStream_t stream) {
+// Evaluation counts of the last render: (Gaussian, triangle) (pixel, record) pairs.
+static umgs_status count_evaluations(const umgs_frame* fr, int64_t* g_evals, int64_t* t_evals, cudaStream_t stream) {
     cudaError_t e;
-    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(fr->status.as<int32_t>() + 6);
-    if ((e = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), stream)) != cudaSuccess)
+    unsigned long long* cnt = reinterpret_cast<unsigned long long*>(fr->status.as<int32_t>() + kStatusEvalWords);
+    if ((e = cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), stream)) != cudaSuccess)
         return cuda_fail(fr->ctx, e, "cudaMemsetAsync");
     const int tpc = fr->tiles_x * fr->tiles_y;
     const unsigned M = (unsigned)fr->num_tiles;
@@ -467,12 +475,40 @@ umgs_status frame_evaluations(const umgs_frame* fr, int64_t* evals, cudaStream_t
 #undef UMGS_LAUNCH
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(fr->ctx, e, "eval_count_kernel");
     }
-    unsigned long long v = 0;
+    unsigned long long v[2] = {0, 0};
     if ((e = cudaMemcpyAsync(fr->ctx->pinned, cnt, sizeof(v), cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
         (e = cudaStreamSynchronize(stream)) != cudaSuccess)
         return cuda_fail(fr->ctx, e, "reading the evaluation count");
-    std::memcpy(&v, fr->ctx->pinned, sizeof(v));
-    *evals = (int64_t)v;
+    std::memcpy(v, fr->ctx->pinned, sizeof(v));
+    *g_evals = (int64_t)v[0];
+    *t_evals = (int64_t)v[1];
+    return UMGS_OK;
+}
+
+umgs_status frame_evaluations(const umgs_frame* fr, int64_t* evals, cudaStream_t stream) {
+    int64_t g = 0, t = 0;
+    const umgs_status st = count_evaluations(fr, &g, &t, stream);
+    *evals = g + t;
+    return st;
+}
+
+umgs_status frame_stats(const umgs_frame* fr, umgs_frame_stats* out, cudaStream_t stream) {
+    umgs_status st = count_evaluations(fr, &out->gaussian_evals, &out->triangle_evals, stream);
+    if (st != UMGS_OK) return st;
+    // fp64 conic count (status word 3) and the list length, read after the
+    // evaluation count's synchronisation
+    uint32_t w[4];
+    cudaError_t e = cudaMemcpyAsync(fr->ctx->pinned, fr->status.ptr, sizeof(w), cudaMemcpyDeviceToHost, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(fr->ctx, e, "reading the frame status");
+    std::memcpy(w, fr->ctx->pinned, sizeof(w));
+    out->fp64_conics = (int64_t)w[3];
+    int64_t k = 0;
+    if ((e = cudaMemcpyAsync(&k, fr->tile_off.as<int64_t>() + fr->num_tiles, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                             stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(stream)) != cudaSuccess)
+        return cuda_fail(fr->ctx, e, "reading the list length");
+    out->list_entries = k;
     return UMGS_OK;
 }
 

@@ -100,7 +100,9 @@ __global__ void __launch_bounds__(256) face_gradients_kernel(const float* __rest
     // sliver: |n| = |e1||e2| sin(angle); invert in fp64 when sin < 1e-3
     const float l1 = sqrtf(Fr[0] * Fr[0] + Fr[3] * Fr[3] + Fr[6] * Fr[6]);
     const float l2 = sqrtf(Fr[1] * Fr[1] + Fr[4] * Fr[4] + Fr[7] * Fr[7]);
-    const bool ok = (nn < 1e-3f * l1 * l2) ? inv3_fp64(Fr, Fi) : inv3(Fr, Fi);
+    const bool sliver = nn < 1e-3f * l1 * l2;
+    if (sliver) atomicAdd(status + 1, 1);  // fp64 sliver inverses of this deformation (umgs_deform_fp64_faces)
+    const bool ok = sliver ? inv3_fp64(Fr, Fi) : inv3(Fr, Fi);
     if (!ok) return;
     matmul3(Fd, Fi, D);
     const float area = 0.5f * nn;
@@ -607,10 +609,12 @@ __global__ void __launch_bounds__(kDefBlock) deform_gaussians_compact_kernel(
 static inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
 
 // per-face gradients and the per-vertex table of the deformed proxy (A1)
-__global__ void zero_floats_kernel(float* __restrict__ p, int64_t n) {
+// (also clears *word, the fp64 sliver-face count of the deformation)
+__global__ void zero_floats_kernel(float* __restrict__ p, int64_t n, int32_t* __restrict__ word) {
     pdl_enter();
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i < n) p[i] = 0.f;
+    if (i == 0 && word) *word = 0;
 }
 
 static umgs_status proxy_table(umgs_ctx* ctx, const float* V, const float* Vd, const int32_t* F, int64_t nv,
@@ -622,7 +626,8 @@ static umgs_status proxy_table(umgs_ctx* ctx, const float* V, const float* Vd, c
         return fail(ctx, UMGS_ERR_OUT_OF_MEMORY, "vtab");
     ctx->vtab_rows = nv;
     // accumulators cleared by a kernel, so the programmatic launch chain runs on
-    launch_pdl(zero_floats_kernel, grid_for(nacc, 256), 256, 0, stream, ctx->vacc.as<float>(), nacc);
+    launch_pdl(zero_floats_kernel, grid_for(nacc, 256), 256, 0, stream, ctx->vacc.as<float>(), nacc,
+               ctx->dstatus.as<int32_t>() + 1);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "zero_floats_kernel");
     int32_t* status = ctx->dstatus.as<int32_t>();
     {
@@ -723,7 +728,9 @@ __global__ void noalloc_clear_kernel(float* __restrict__ p, int64_t n) {
 
 // Device address of g_noalloc_scratch on the current device, looked up once
 // per device.  In host code the symbol is only a host-side stand-in, so the
-// address must come from cudaGetSymbolAddress with that device current.
+// address must come from cudaGetSymbolAddress with that device current.  The
+// cached address lives as long as the device's primary context: a
+// cudaDeviceReset invalidates it (the header says so).
 static cudaError_t noalloc_scratch_address(float** out) {
     constexpr int kMaxDev = 64;
     static float* addr[kMaxDev] = {};

@@ -199,6 +199,11 @@ umgs_status render_backward(umgs_ctx* ctx, umgs_frame* fr, const umgs_gaussians*
 
 umgs_status frame_check(umgs_frame* fr, cudaStream_t stream);
 umgs_status frame_evaluations(const umgs_frame* fr, int64_t* evals, cudaStream_t stream);
+umgs_status frame_stats(const umgs_frame* fr, umgs_frame_stats* out, cudaStream_t stream);
+// first status word past the render's own (16 + the depth sort's key-map
+// slots): two u64 evaluation counters (Gaussian, triangle)
+constexpr int kStatusEvalWords = 16 + 2 * 32;
+constexpr int kStatusWords = kStatusEvalWords + 4;
 umgs_status frame_lists(const umgs_frame* fr, int64_t* tile_ptr, int32_t* ids, uint32_t* dbits,
                         cudaStream_t stream);
 

@@ -1121,7 +1121,8 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     // [12] (region, id) pairs sorted (0 after an overflow), [13] count/fill
     // chunks, [14] tile-list entries from the tile scan, [15] (region, id)
     // pairs counted, [16 ..) the depth sort's key-map slots (~min, max)
-    UMGS_TRY(fr->status.reserve(sizeof(int32_t) * (16 + 2 * kRadixMapSlots)));
+    static_assert(kStatusEvalWords == 16 + 2 * kRadixMapSlots, "status word layout");
+    UMGS_TRY(fr->status.reserve(sizeof(int32_t) * kStatusWords));
 
     // cameras: host -> pinned staging -> device
     std::vector<DevCam> dc(ncams);

@@ -67,6 +67,11 @@ class CMeshGrads(ctypes.Structure):
                 ("falpha", ctypes.c_void_p)]
 
 
+class CFrameStats(ctypes.Structure):
+    _fields_ = [("gaussian_evals", ctypes.c_int64), ("triangle_evals", ctypes.c_int64),
+                ("fp64_conics", ctypes.c_int64), ("list_entries", ctypes.c_int64)]
+
+
 class CRenderOpts(ctypes.Structure):
     _fields_ = [("tile_size", ctypes.c_int32), ("blend_mode", ctypes.c_int32), ("t_eps", ctypes.c_float),
                 ("bg", ctypes.c_float * 3), ("flags", ctypes.c_int32), ("sched", ctypes.c_int32),
@@ -98,6 +103,10 @@ def lib():
         L.umgs_frame_lists.argtypes = [vp, vp, vp, vp, vp]
         L.umgs_frame_evaluations.argtypes = [vp, ctypes.POINTER(i64), vp]
         L.umgs_frame_evaluations.restype = ctypes.c_int
+        L.umgs_frame_stats_read.argtypes = [vp, ctypes.POINTER(CFrameStats), vp]
+        L.umgs_frame_stats_read.restype = ctypes.c_int
+        L.umgs_deform_fp64_faces.argtypes = [vp, ctypes.POINTER(i64), vp]
+        L.umgs_deform_fp64_faces.restype = ctypes.c_int
         L.umgs_ctx_sync.argtypes = [vp, vp]
         L.umgs_deform.argtypes = [vp, ctypes.POINTER(CGaussians), vp, vp, vp, vp, vp, i64, i64, i32, vp, vp, vp, vp]
         L.umgs_deform_vertex_table.argtypes = [vp, vp, i64, vp]
@@ -214,6 +223,12 @@ class Frame:
         v = ctypes.c_int64()
         self.ctx.check(lib().umgs_frame_evaluations(self._h, ctypes.byref(v), _stream()), "umgs_frame_evaluations")
         return v.value
+
+    def stats(self):
+        """umgs_frame_stats_read: dict of gaussian_evals, triangle_evals, fp64_conics, list_entries (synchronises)."""
+        st = CFrameStats()
+        self.ctx.check(lib().umgs_frame_stats_read(self._h, ctypes.byref(st), _stream()), "umgs_frame_stats_read")
+        return {f: int(getattr(st, f)) for f, _ in CFrameStats._fields_}
 
     def lists(self):
         """(tile_ptr int64 [T+1], ids int32 [K], dbits int32 [K] (uint32 bits)) on the device."""
@@ -403,7 +418,36 @@ def deform_noalloc(rest: DevGaussians, face, bary, proxy_v, proxy_vd, proxy_f, o
     """umgs_deform_noalloc: the deformation for callers that cannot allocate
     device memory.  `out` = (means [n,3], cov3d [n,6], quats [n,4] or None),
     all preallocated by the caller; nothing is allocated on the device.
-    Runs on the current device; see include/umgs.h for the shared-scratch rules."""
+    Runs on the current device; see include/umgs.h for the shared-scratch rules.
+
+    The C entry point cannot see the sizes of the buffers it is given, so the
+    shapes, dtypes, devices and layouts are checked here (ValueError)."""
+    n = rest.n
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def need(t, shape, dtype, what):
+        if t is None or tuple(t.shape) != shape or t.dtype != dtype or t.device != dev or not t.is_contiguous():
+            got = "None" if t is None else "%s %s on %s%s" % (tuple(t.shape), t.dtype, t.device,
+                                                               "" if t.is_contiguous() else " (not contiguous)")
+            raise ValueError("deform_noalloc: %s must be a contiguous %s tensor of shape %s on %s, got %s"
+                             % (what, dtype, shape, dev, got))
+
+    nv, nf = int(proxy_v.shape[0]), int(proxy_f.shape[0])
+    need(face, (n, 8), torch.int32, "face")
+    need(bary, (n, 8, 2), torch.float32, "bary")
+    need(proxy_v, (nv, 3), torch.float32, "proxy_v")
+    need(proxy_vd, (nv, 3), torch.float32, "proxy_vd")
+    need(proxy_f, (nf, 3), torch.int32, "proxy_f")
+    if len(out) != 3:
+        raise ValueError("deform_noalloc: out must be (means, cov3d, quats or None)")
+    need(out[0], (n, 3), torch.float32, "out[0] (means)")
+    need(out[1], (n, 6), torch.float32, "out[1] (cov3d)")
+    if out[2] is not None:
+        need(out[2], (n, 4), torch.float32, "out[2] (quats)")
+    for name in ("means", "quats", "scales", "opacities"):
+        t = getattr(rest, name)
+        if t.device != dev:
+            raise ValueError("deform_noalloc: rest.%s is on %s, not the current device %s" % (name, t.device, dev))
     cg = rest.c()
     st = lib().umgs_deform_noalloc(ctypes.byref(cg), _ptr(face), _ptr(bary), _ptr(proxy_v), _ptr(proxy_vd),
                                    _ptr(proxy_f), int(proxy_v.shape[0]), int(proxy_f.shape[0]), int(mode),
@@ -411,6 +455,13 @@ def deform_noalloc(rest: DevGaussians, face, bary, proxy_v, proxy_vd, proxy_f, o
     if st != OK:
         raise UmgsError(st, "umgs_deform_noalloc")
     return out
+
+
+def deform_fp64_faces(ctx: Context, stream=None) -> int:
+    """umgs_deform_fp64_faces: proxy faces of the last deformation inverted in fp64 (slivers)."""
+    v = ctypes.c_int64()
+    ctx.check(lib().umgs_deform_fp64_faces(ctx._h, ctypes.byref(v), _stream(stream)), "umgs_deform_fp64_faces")
+    return int(v.value)
 
 
 def deform_vertex_table(ctx: Context, nv: int, stream=None) -> torch.Tensor:
@@ -468,20 +519,6 @@ def bind(ctx: Context, g: DevGaussians, proxy_v: torch.Tensor, proxy_f: torch.Te
                          _ptr(dist), _ptr(flags), ctypes.byref(nfb), _stream(stream))
     ctx.check(st, "umgs_bind")
     return face, bary, dist, flags, nfb.value
-
-
-def bind_or_fallback(ctx, g, proxy_v, proxy_f, cameras, device):
-    """Bind with umgs_bind when the library provides it, else a seeded random
-    face/barycentric table of the same shape (labelled in the returned info)."""
-    if hasattr(lib(), "umgs_bind"):
-        face, bary, dist, flags, nfb = bind(ctx, g, proxy_v, proxy_f, cameras, mode=BIND_BBX)
-        return face, bary, "umgs_bind BBX k=3, %d cameras, %d fallback targets" % (len(cameras), nfb)
-    gen = torch.Generator(device=device).manual_seed(0)
-    n = g.n
-    face = torch.randint(0, int(proxy_f.shape[0]), (n, 8), generator=gen, device=device, dtype=torch.int32)
-    b = torch.rand((n, 8, 2), generator=gen, device=device)
-    b = torch.where(b.sum(-1, keepdim=True) > 1, 1 - b, b).contiguous()
-    return face, b, "synthetic random table"
 
 
 def render_backward(ctx: Context, frame: Frame, gaussians: DevGaussians | None, meshes, dL_drgbt: torch.Tensor,

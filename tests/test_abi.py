@@ -53,7 +53,7 @@ def test_ctx_create_rejects_bad_device(libpath):
 
 _STRUCTS = {"umgs_gaussians": "CGaussians", "umgs_mesh": "CMesh", "umgs_camera": "CCamera",
             "umgs_gaussian_grads": "CGaussianGrads", "umgs_mesh_grads": "CMeshGrads",
-            "umgs_render_opts": "CRenderOpts"}
+            "umgs_render_opts": "CRenderOpts", "umgs_frame_stats": "CFrameStats"}
 
 
 def test_binding_structs_match_the_header(tmp_path):
