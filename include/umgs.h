@@ -270,7 +270,7 @@ umgs_status umgs_frame_evaluations(const umgs_frame* frame, int64_t* evals, void
  *     triangle evaluation is 12 sample/edge tests, perspective-correct
  *     attributes and the entity blend, Eq. 7-9);
  *   fp64_conics: (camera, Gaussian) records whose projected covariance was
- *     near-singular (det < a c / 1024) and whose conic was therefore inverted
+ *     near-singular (det < a c / 128) and whose conic was therefore inverted
  *     in fp64 (EWA projection, Sec. 3.2);
  *   list_entries: total length of the tile lists.
  * Errors: INVALID_ARG if nothing was rendered into the frame. */

@@ -545,7 +545,7 @@ __global__ void __launch_bounds__(kProjBwdWarps * 32) project_gaussians_bwd_kern
             // conic Q = inv([[a b][b c]])
             float QA, QB, QC;
             const float det = a * c - b * b;
-            if (det < 0.0009765625f * a * c) {
+            if (det < kConicFp64 * a * c) {
                 const double dd = (double)a * c - (double)b * b;
                 QA = (float)(c / dd); QB = (float)(-b / dd); QC = (float)(a / dd);
             } else {

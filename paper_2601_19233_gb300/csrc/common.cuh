@@ -148,6 +148,12 @@ __device__ __forceinline__ float gauss_power2(float ca, float cb, float cc, floa
     return __fmaf_rn(cc, __fmul_rn(dy, dy), __fmaf_rn(cb, __fmul_rn(dx, dy), __fmul_rn(ca, __fmul_rn(dx, dx))));
 }
 
+// A projected covariance [[a, b], [b, c]] with det < kConicFp64 * a * c is
+// near-singular: its conic is inverted in fp64 (the fp32 inverse would lose
+// log2(a c / det) bits, about 7 at this bound, which keeps the fp32 alpha
+// within 2e-5 of the exact one).
+constexpr float kConicFp64 = 1.0f / 128.0f;
+
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
 constexpr float kLog2e = 1.4426950408889634f;
@@ -164,21 +170,23 @@ __device__ __forceinline__ void block_pixel(int t, int& lx, int& ly) {
     ly = (w / (TS / 8)) * 4 + (l >> 3);
 }
 
-// Warps (8 x 4 blocks) of the tile with origin (tx0, ty0) that meet the pixel
-// box [x0,x1] x [y0,y1].
-template <int TS>
+// Blocks of 8 x BH pixels (bit wy * (TS/8) + wx for the block at (8 wx,
+// BH wy); BH = 4: the warps of block_pixel) of the tile with origin
+// (tx0, ty0) that meet the pixel box [x0,x1] x [y0,y1].
+template <int TS, int BH = 4>
 __device__ __forceinline__ uint32_t box_block_mask(int x0, int x1, int y0, int y1, int tx0, int ty0) {
+    constexpr int LB = BH == 4 ? 2 : 3;
     x0 = max(x0, tx0); x1 = min(x1, tx0 + TS - 1);
     y0 = max(y0, ty0); y1 = min(y1, ty0 + TS - 1);
     if (x0 > x1 || y0 > y1) return 0u;
-    const int wx0 = (x0 - tx0) >> 3, wx1 = (x1 - tx0) >> 3, wy0 = (y0 - ty0) >> 2, wy1 = (y1 - ty0) >> 2;
+    const int wx0 = (x0 - tx0) >> 3, wx1 = (x1 - tx0) >> 3, wy0 = (y0 - ty0) >> LB, wy1 = (y1 - ty0) >> LB;
     const uint32_t cols = ((2u << wx1) - 1u) & ~((1u << wx0) - 1u);
     uint32_t m = 0u;
     for (int wy = wy0; wy <= wy1; ++wy) m |= cols << (wy * (TS / 8));
     return m;
 }
 
-// Warps (8 x 4 blocks, see block_pixel) of the tile with origin (tx0, ty0)
+// Blocks of 8 x BH pixels (as box_block_mask) of the tile with origin (tx0, ty0)
 // whose pixels can hold a fragment of a Gaussian record with projected mean
 // (u, v), base-2 conic (ca, cb, cc) (alpha = o 2^p2, p2 = ca dx^2 + cb dx dy +
 // cc dy^2), opacity o and pixel rect [x0,x1] x [y0,y1].  A fragment needs
@@ -190,12 +198,13 @@ __device__ __forceinline__ uint32_t box_block_mask(int x0, int x1, int y0, int y
 // are widened by 2% of lim plus 1% + 0.01 px, far beyond the rounding of this
 // test and of the compositor's own alpha.  o < 1/255: no fragment; a conic
 // that is not positive definite keeps every block of the rect.
-template <int TS>
+template <int TS, int BH = 4>
 __device__ __forceinline__ uint32_t gauss_block_mask(float u, float v, float ca, float cb, float cc, float o, int x0,
                                                      int x1, int y0, int y1, int tx0, int ty0) {
+    constexpr int LB = BH == 4 ? 2 : 3;
     if (!(o >= kAlphaMin)) return 0u;
     const float qa = -ca, qb = -0.5f * cb, qc = -cc, det = qa * qc - qb * qb;
-    if (!(qa > 0.f && qc > 0.f && det > 0.f)) return box_block_mask<TS>(x0, x1, y0, y1, tx0, ty0);
+    if (!(qa > 0.f && qc > 0.f && det > 0.f)) return box_block_mask<TS, BH>(x0, x1, y0, y1, tx0, ty0);
     const float s = (__log2f(255.f * o) * 1.02f + 1e-4f) / det;  // lim Q^-1 = s [[qc, -qb], [-qb, qa]]
     const float hx = sqrtf(s * qc) * 1.01f + 0.01f, hy = sqrtf(s * qa) * 1.01f + 0.01f;
     const float hp = sqrtf(s * (qc + qa - 2.f * qb)) * 1.01f + 0.01f;  // direction x + y
@@ -203,10 +212,10 @@ __device__ __forceinline__ uint32_t gauss_block_mask(float u, float v, float ca,
     x0 = max(max(x0, (int)floorf(u - hx - 0.5f)), tx0); x1 = min(min(x1, (int)ceilf(u + hx - 0.5f)), tx0 + TS - 1);
     y0 = max(max(y0, (int)floorf(v - hy - 0.5f)), ty0); y1 = min(min(y1, (int)ceilf(v + hy - 0.5f)), ty0 + TS - 1);
     if (x0 > x1 || y0 > y1) return 0u;
-    const int wx0 = (x0 - tx0) >> 3, wx1 = (x1 - tx0) >> 3, wy0 = (y0 - ty0) >> 2, wy1 = (y1 - ty0) >> 2;
+    const int wx0 = (x0 - tx0) >> 3, wx1 = (x1 - tx0) >> 3, wy0 = (y0 - ty0) >> LB, wy1 = (y1 - ty0) >> LB;
     uint32_t m = 0u;
     for (int wy = wy0; wy <= wy1; ++wy) {
-        const float Y0 = (float)max(y0, ty0 + 4 * wy) + 0.5f - v, Y1 = (float)min(y1, ty0 + 4 * wy + 3) + 0.5f - v;
+        const float Y0 = (float)max(y0, ty0 + BH * wy) + 0.5f - v, Y1 = (float)min(y1, ty0 + BH * wy + BH - 1) + 0.5f - v;
         for (int wx = wx0; wx <= wx1; ++wx) {
             const float X0 = (float)max(x0, tx0 + 8 * wx) + 0.5f - u;
             const float X1 = (float)min(x1, tx0 + 8 * wx + 7) + 0.5f - u;

@@ -1,7 +1,7 @@
 // Compositor of the forward pass (Sec. 3.2, Eq. 1-2 and 7-11) and the
 // evaluation count of a rendered frame.
 //
-// One CTA per tile, one thread per pixel: records of the tile's sorted list
+// One CTA per tile, two pixels per thread: records of the tile's sorted list
 // are staged through shared memory in batches, every pixel blends its
 // fragments front to back (Eq. 1-2 for Gaussians, Eq. 7-9 for entities of
 // depth-adjacent triangles, background Eq. 10-11) and the CTA stops when
@@ -18,9 +18,23 @@ namespace umgs {
 // ---------------------------------------------------------------------------
 // compositor
 
-constexpr int kBatch = 256;
-// records staged per batch: 256, or 128 for 32x32 tiles (32 warps of lists)
-template <int TS> struct BatchOf { static constexpr int value = TS == 32 ? 128 : 256; };
+// ---- layout: two pixels per thread -----------------------------------------
+// Warp w of a TS x TS tile owns the 8 x 8 pixel block (w % (TS/8), w / (TS/8));
+// lane l holds the pixels (l % 8, l / 8) and (l % 8, l / 8 + 4) of it.  The
+// two pixels share a column, so the record loads, the list walk, the rect
+// test in x and the x part of a Gaussian's exponent are done once for both.
+template <int TS> struct Layout {
+    static constexpr int NW = TS * TS / 64;  // warps (8 x 8 blocks) per tile
+    static constexpr int NT = 32 * NW;       // threads per tile
+    static constexpr int NB = 256;           // records staged per batch
+    static constexpr int RPT = (NB + NT - 1) / NT;  // records per thread in the staging
+};
+#ifndef UMGS_COMP_MINB
+#define UMGS_COMP_MINB 6
+#endif
+template <int TS> struct MinBlocks { static constexpr int value = TS == 16 ? UMGS_COMP_MINB : 1; };
+constexpr int kSlot = 11;      // 16-byte vectors of shared memory per staged triangle
+constexpr int kTriSlots = 96;  // staged triangles per batch (a batch ends before the 97th)
 
 struct PixelState {
     float C[3];
@@ -30,6 +44,28 @@ struct PixelState {
     float t[4];
     float g_since;
     bool in_ent;
+    bool done;
+    int last;
+    int sp;
+};
+
+// Shared memory of the forward compositor: per batch the staged Gaussians
+// ((u, v, ca, cb), (cc, o, r, g), (b, Z, -, -), pixel rect (x0, x1 - x0,
+// y0, y1 - y0) as integers), up to kTriSlots staged triangles (kSlot x 16
+// bytes, stage_triangle), the ids and warp-block masks of the batch's
+// records, one ballot of "is a triangle" per 32 records, each triangle
+// record's slot, and per warp its list of entries (record | slot << 8 |
+// 0x8000 for a triangle).
+template <int TS>
+struct CompositeSmem {
+    static constexpr int NB = Layout<TS>::NB;
+    float4 g[NB][4];
+    float4 t[kTriSlots][kSlot];
+    uint32_t id[NB];
+    uint32_t wmask[NB];
+    uint32_t tbal[NB / 32];
+    uint8_t tslot[NB];
+    uint16_t list[Layout<TS>::NW * NB];
 };
 
 // SAVE: also keep what the backward pass needs: per pixel the final T and
@@ -45,59 +81,361 @@ constexpr int kModeTProduct = 4;
 // out_depth (+inf where nothing blends).
 constexpr int kModeDepth = 5;
 
+// ---- triangle records staged for one tile ----------------------------------
+// A triangle is staged for the tile it is composited in as kSlot 16-byte
+// vectors (int4 / float4 views of the same slot):
+//   w[0] = (E0_0, E0_1, E0_2, flags)  edge functions E_k (1/256 px units,
+//          top-left bias included) at the centre of the tile's first pixel
+//   w[1] = (A256_k, u_0), w[2] = (B256_k, v_0): change of E_k per pixel
+//          step in x and in y (256 A_k, 256 B_k); vertex 0 on the screen
+//   w[3] = (P_k, 0), w[4] = (Q_k, ia): sample j of a pixel is inside edge k
+//          iff E_k + o_kj >= 0, o_k = (P_k, Q_k, -Q_k, -P_k) for the offsets
+//          (-2,-6), (6,-2), (-6,2), (2,6) / 16 px, i.e. P = -32 A - 96 B and
+//          Q = 96 A - 32 B; ia = 1 / (twice the signed screen area)
+//   w[5..7] = (alpha_e | beta_e | gamma_e, c_e): lambda_e(q) = alpha_e +
+//          beta_e qx + gamma_e qy is twice the signed area of (q, P_a, P_b),
+//          (a, b) = (e+1, e+2), for q relative to vertex 0; c_e = iz_e ia
+//          (perspective-correct barycentric weight per unit lambda)
+//   w[8..10] = (colour or texture uv of vertex e, alpha_e)
+// Integer coverage stays exact in int32 when every edge function over the
+// tile's samples lies within +-2^30; an edge that every sample of the tile
+// passes is replaced by the constant 1 (A = B = P = Q = 0), and a triangle
+// with an edge no sample of the tile passes has no fragment there.  A record
+// beyond that range (an edge of more than about 1,000 px crossing the tile)
+// is flagged kTriWide and tested in int64 from its global record.
+constexpr int kTriWide = 1, kTriConstAlpha = 2;
+
+// a*b - c*d with one rounding of the result (Kahan's compensated form)
+__device__ __forceinline__ float diff_of_products(float a, float b, float c, float d) {
+    const float w = __fmul_rn(c, d);
+    const float e = __fmaf_rn(-c, d, w);
+    const float f = __fmaf_rn(a, b, -w);
+    return __fadd_rn(f, e);
+}
+
+// Stages triangle record t for the tile with origin (tx0, ty0) into slot w;
+// returns the mask of the tile's 8 x 8 blocks that can hold a fragment of it.
+template <int TS>
+__device__ __forceinline__ uint32_t stage_triangle(const TRec& t, int tx0, int ty0, float4* __restrict__ w) {
+    uint32_t m = box_block_mask<TS, 8>((int)(t.rx & 0xffff), (int)(t.rx >> 16), (int)(t.ry & 0xffff),
+                                       (int)(t.ry >> 16), tx0, ty0);
+    if (!m) return 0u;
+    const long long cx0 = (long long)tx0 * 256 + 128, cy0 = (long long)ty0 * 256 + 128;
+    constexpr long long kLim = 1LL << 30;
+    int E0[3], A2[3], B2[3], P[3], Q[3], off[3];
+    bool wide = false;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const long long A = t.A[k], B = t.B[k];
+        const long long e = A * cx0 + B * cy0 + t.C[k];
+        const long long a = A * 256, b = B * 256;
+        const long long p = -32 * A - 96 * B, q = 96 * A - 32 * B;
+        const long long o = max(llabs(p), llabs(q));
+        const long long lo = e + min(0LL, a * (TS - 1)) + min(0LL, b * (TS - 1)) - o;
+        const long long hi = e + max(0LL, a * (TS - 1)) + max(0LL, b * (TS - 1)) + o;
+        if (hi < 0) return 0u;  // no sample of the tile is inside edge k
+        if (lo >= 0) {          // every sample of the tile is inside edge k
+            E0[k] = 1; A2[k] = B2[k] = P[k] = Q[k] = off[k] = 0;
+            continue;
+        }
+        if (lo < -kLim || hi > kLim) wide = true;
+        E0[k] = (int)e; A2[k] = (int)a; B2[k] = (int)b; P[k] = (int)p; Q[k] = (int)q; off[k] = (int)o;
+    }
+    if (!wide) {
+        // drop the 8 x 8 blocks that an edge excludes entirely
+        uint32_t mm = m;
+        while (mm) {
+            const int wb = __ffs(mm) - 1;
+            mm &= mm - 1;
+            const int bx = (wb % (TS / 8)) * 8, by = (wb / (TS / 8)) * 8;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int hi = E0[k] + A2[k] * bx + B2[k] * by + max(0, A2[k] * 7) + max(0, B2[k] * 7) + off[k];
+                if (hi < 0) m &= ~(1u << wb);
+            }
+        }
+        if (!m) return 0u;
+    }
+    int4* wi = reinterpret_cast<int4*>(w);
+    const int flags = (wide ? kTriWide : 0) | (t.const_alpha ? kTriConstAlpha : 0) | (t.tex << 8);
+    wi[0] = make_int4(E0[0], E0[1], E0[2], flags);
+    wi[1] = make_int4(A2[0], A2[1], A2[2], __float_as_int(t.u[0]));
+    wi[2] = make_int4(B2[0], B2[1], B2[2], __float_as_int(t.v[0]));
+    // attribute planes relative to vertex 0 (the same for every tile, so
+    // that images do not depend on the tile size)
+    const float U[3] = {0.f, t.u[1] - t.u[0], t.u[2] - t.u[0]};
+    const float V[3] = {0.f, t.v[1] - t.v[0], t.v[2] - t.v[0]};
+    float al[3], be[3], ga[3], c[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int a = (e + 1) % 3, b = (e + 2) % 3;
+        al[e] = diff_of_products(U[a], V[b], U[b], V[a]);
+        be[e] = V[a] - V[b];
+        ga[e] = U[b] - U[a];
+    }
+    const float area = al[0] + al[1] + al[2];
+    float ia = 0.f;
+    if (area != 0.f) {
+        ia = 1.f / area;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) c[e] = t.iz[e] * ia;
+    } else {  // degenerate screen triangle: the three vertices weighted by 1/Z alike
+#pragma unroll
+        for (int e = 0; e < 3; ++e) { al[e] = 1.f; be[e] = ga[e] = 0.f; c[e] = t.iz[e] * (1.f / 3.f); }
+    }
+    wi[3] = make_int4(P[0], P[1], P[2], 0);
+    wi[4] = make_int4(Q[0], Q[1], Q[2], __float_as_int(ia));
+    w[5] = make_float4(al[0], al[1], al[2], c[0]);
+    w[6] = make_float4(be[0], be[1], be[2], c[1]);
+    w[7] = make_float4(ga[0], ga[1], ga[2], c[2]);
+    w[8] = make_float4(t.col[0], t.col[1], t.col[2], t.alpha[0]);
+    w[9] = make_float4(t.col[3], t.col[4], t.col[5], t.alpha[1]);
+    w[10] = make_float4(t.col[6], t.col[7], t.col[8], t.alpha[2]);
+    return m;
+}
+
+// Sample coverage (bit j: sample j) of the pixel (lx, ly) of the tile by a
+// staged (not wide) triangle; DIRECT: 0xf iff the pixel centre is covered.
+template <bool CENTRE>
+__device__ __forceinline__ int staged_coverage(const float4* __restrict__ w, int lx, int ly) {
+    const int4 e0 = reinterpret_cast<const int4*>(w)[0], a = reinterpret_cast<const int4*>(w)[1],
+               b = reinterpret_cast<const int4*>(w)[2];
+    const int E0 = e0.x + a.x * lx + b.x * ly, E1 = e0.y + a.y * lx + b.y * ly, E2 = e0.z + a.z * lx + b.z * ly;
+    if (CENTRE) return (E0 >= 0 && E1 >= 0 && E2 >= 0) ? 0xf : 0;
+    const int4 p = reinterpret_cast<const int4*>(w)[3], q = reinterpret_cast<const int4*>(w)[4];
+    const bool s0 = (E0 + p.x >= 0) & (E1 + p.y >= 0) & (E2 + p.z >= 0);
+    const bool s1 = (E0 + q.x >= 0) & (E1 + q.y >= 0) & (E2 + q.z >= 0);
+    const bool s2 = (E0 >= q.x) & (E1 >= q.y) & (E2 >= q.z);
+    const bool s3 = (E0 >= p.x) & (E1 >= p.y) & (E2 >= p.z);
+    return (s0 ? 1 : 0) | (s1 ? 2 : 0) | (s2 ? 4 : 0) | (s3 ? 8 : 0);
+}
+
+// Sample coverage of pixel (px, py) by a global triangle record in int64.
+__device__ __forceinline__ int record_coverage(const TRec& t, int px, int py, bool centre_only) {
+    const long long scx = (long long)px * 256 + 128, scy = (long long)py * 256 + 128;
+    long long E[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) E[e] = (long long)t.A[e] * scx + (long long)t.B[e] * scy + t.C[e];
+    if (centre_only) return (E[0] >= 0 && E[1] >= 0 && E[2] >= 0) ? 0xf : 0;
+    int mask = 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int sdx = sample_dx(j), sdy = sample_dy(j);
+        bool in = true;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) in = in && (E[e] + (long long)(t.A[e] * sdx + t.B[e] * sdy) >= 0);
+        mask |= in ? (1 << j) : 0;
+    }
+    return mask;
+}
+
+// One triangle record at one pixel: coverage, attributes, and the blend of
+// the blend mode (Eq. 7-9 for FULL).  Returns true when it was a fragment.
+template <bool SAVE, int MODE>
+__device__ __forceinline__ bool blend_triangle(PixelState& st, const float4* __restrict__ w, const TRec* __restrict__ TR,
+                                               uint32_t tid, int px, int py, int lx, int ly,
+                                               float4* __restrict__ stack, int cap, int64_t npix, int64_t pix,
+                                               const DevTex* __restrict__ textab) {
+    constexpr int mode = MODE;
+    const float qx = px + 0.5f, qy = py + 0.5f;
+    const int flags = reinterpret_cast<const int4*>(w)[0].w;
+    int mask;
+    float wv[3], zt = 0.f;
+    if (!(flags & kTriWide)) {
+        mask = staged_coverage<MODE == UMGS_BLEND_DIRECT>(w, lx, ly);
+        if (mask == 0) return false;
+        // perspective-correct barycentrics at the pixel centre, clamped at 0
+        const float4 fa = w[5], fb = w[6], fc = w[7];
+        const float rqx = __fsub_rn(qx, __int_as_float(reinterpret_cast<const int4*>(w)[1].w));
+        const float rqy = __fsub_rn(qy, __int_as_float(reinterpret_cast<const int4*>(w)[2].w));
+        const float l0 = __fmaf_rn(fb.x, rqx, __fmaf_rn(fc.x, rqy, fa.x));
+        const float l1 = __fmaf_rn(fb.y, rqx, __fmaf_rn(fc.y, rqy, fa.y));
+        const float l2 = __fmaf_rn(fb.z, rqx, __fmaf_rn(fc.z, rqy, fa.z));
+        wv[0] = fmaxf(l0 * fa.w, 0.f); wv[1] = fmaxf(l1 * fb.w, 0.f); wv[2] = fmaxf(l2 * fc.w, 0.f);
+        if (mode == kModeDepth) {
+            const float ia = __int_as_float(reinterpret_cast<const int4*>(w)[4].w);
+            const float ls = ia != 0.f ? fmaxf(l0 * ia, 0.f) + fmaxf(l1 * ia, 0.f) + fmaxf(l2 * ia, 0.f) : 1.f;
+            const float ws0 = wv[0] + wv[1] + wv[2];
+            const TRec& t = TR[tid];
+            zt = ws0 > 0.f ? ls / ws0 : 3.f / (t.iz[0] + t.iz[1] + t.iz[2]);
+        }
+    } else {  // wide record: int64 coverage and attributes from the global record
+        const TRec& t = TR[tid];
+        if (px < (int)(t.rx & 0xffff) || px > (int)(t.rx >> 16) || py < (int)(t.ry & 0xffff) ||
+            py > (int)(t.ry >> 16))
+            return false;
+        mask = record_coverage(t, px, py, mode == UMGS_BLEND_DIRECT);
+        if (mask == 0) return false;
+        float lam[3];
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            const int a = (e + 1) % 3, b = (e + 2) % 3;
+            lam[e] = (t.u[a] - qx) * (t.v[b] - qy) - (t.u[b] - qx) * (t.v[a] - qy);
+        }
+        const float area = lam[0] + lam[1] + lam[2];
+        if (area != 0.f) {
+            const float ia = __fdividef(1.f, area);
+#pragma unroll
+            for (int e = 0; e < 3; ++e) wv[e] = fmaxf(lam[e] * ia, 0.f) * t.iz[e];
+        } else {
+#pragma unroll
+            for (int e = 0; e < 3; ++e) wv[e] = (1.f / 3.f) * t.iz[e];
+        }
+        if (mode == kModeDepth) {
+            const float ls = area != 0.f ? fmaxf(lam[0] / area, 0.f) + fmaxf(lam[1] / area, 0.f) +
+                                               fmaxf(lam[2] / area, 0.f)
+                                         : 1.f;
+            const float ws0 = wv[0] + wv[1] + wv[2];
+            zt = ws0 > 0.f ? ls / ws0 : 3.f / (t.iz[0] + t.iz[1] + t.iz[2]);
+        }
+    }
+    const float ws = wv[0] + wv[1] + wv[2];
+    if (ws > 0.f) { const float is = __fdividef(1.f, ws); wv[0] *= is; wv[1] *= is; wv[2] *= is; }
+    else { wv[0] = wv[1] = wv[2] = 1.f / 3.f; }
+    const float4 v0 = w[8], v1 = w[9], v2 = w[10];
+    float col[3];
+    if (flags >> 8) {  // textured face: (u, v) interpolated like a colour, then sampled
+        const float tu = wv[0] * v0.x + wv[1] * v0.z + wv[2] * v1.y;
+        const float tv = wv[0] * v0.y + wv[1] * v1.x + wv[2] * v1.z;
+        sample_texture(textab[(flags >> 8) - 1], tu, tv, col);
+    } else {
+        col[0] = wv[0] * v0.x + wv[1] * v1.x + wv[2] * v2.x;
+        col[1] = wv[0] * v0.y + wv[1] * v1.y + wv[2] * v2.y;
+        col[2] = wv[0] * v0.z + wv[1] * v1.z + wv[2] * v2.z;
+    }
+    float a = (flags & kTriConstAlpha) ? v0.w : (wv[0] * v0.w + wv[1] * v1.w + wv[2] * v2.w);
+    a = fminf(fmaxf(a, 0.f), 1.f);
+    if (mode == UMGS_BLEND_DIRECT) {
+        const float wt = a * st.T;
+        st.C[0] += wt * col[0]; st.C[1] += wt * col[1]; st.C[2] += wt * col[2];
+        st.T *= (1.f - a);
+    } else if (mode == UMGS_BLEND_MSAA_ALL) {
+        const float O = 0.25f * (float)__popc(mask);
+        const float wt = O * a * st.T;
+        st.C[0] += wt * col[0]; st.C[1] += wt * col[1]; st.C[2] += wt * col[2];
+        st.T *= (1.f - O * a);
+    } else {
+        if (!st.in_ent) {
+            st.Tin = st.T;
+            st.t[0] = st.t[1] = st.t[2] = st.t[3] = 1.f;
+            st.g_since = 1.f;
+            st.in_ent = true;
+        }
+        if (SAVE && mode == UMGS_BLEND_FULL) {
+            if (st.sp < cap) {
+                const float q = 0.25f * st.Tin;
+                stack[(int64_t)st.sp * npix + pix] = make_float4(q * st.t[0], q * st.t[1], q * st.t[2], q * st.t[3]);
+            }
+            ++st.sp;
+        }
+        float O = 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) O += ((mask >> j) & 1) ? st.t[j] : 0.f;
+        O *= 0.25f;
+        const float wt = st.Tin * O * a;
+        st.C[0] += wt * col[0]; st.C[1] += wt * col[1]; st.C[2] += wt * col[2];
+        if (mode == kModeDepth) { st.D += wt * zt; st.Wd += wt; }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if ((mask >> j) & 1) st.t[j] *= (1.f - a);
+        const float tm = 0.25f * ((st.t[0] + st.t[1]) + (st.t[2] + st.t[3]));
+        if (mode == kModeTProduct) st.T *= (1.f - O * a);
+        else st.T = (mode == UMGS_BLEND_ENTITY_ALL) ? st.Tin * tm * st.g_since : st.Tin * tm;
+    }
+    return true;
+}
+
+// Blend of a Gaussian fragment of alpha `al` (Eq. 1-2).
+template <int MODE>
+__device__ __forceinline__ void blend_gaussian(PixelState& st, float al, float r, float g, float b, float z, int pos,
+                                               float t_eps) {
+    const float w = al * st.T;
+    st.C[0] += w * r; st.C[1] += w * g; st.C[2] += w * b;
+    if (MODE == kModeDepth) { st.D += w * z; st.Wd += w; }
+    st.T = __fmaf_rn(-al, st.T, st.T);  // T (1 - alpha), one rounding
+    if (MODE == UMGS_BLEND_ENTITY_ALL) st.g_since *= (1.f - al);
+    else st.in_ent = false;
+    st.last = pos;
+    if (st.T < t_eps) st.done = true;
+}
+
 template <int TS, bool SAVE, int MODE>
 __device__ __forceinline__ void composite_tile(
-    int tile, float4 (*__restrict__ s_rec)[10], uint32_t* __restrict__ s_id, uint32_t* __restrict__ s_wmask,
-    uint8_t* __restrict__ s_list,
+    int tile, CompositeSmem<TS>& sm,
     const uint32_t* __restrict__ ids, const int64_t* __restrict__ off,
     const GRec* __restrict__ grec,
     const GRec16* __restrict__ grec16, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
     int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, float4* __restrict__ out, int32_t* __restrict__ out_last,
     float* __restrict__ out_tfin, int32_t* __restrict__ out_ntri, float4* __restrict__ stack, int cap,
     int64_t npix, int32_t* __restrict__ need, float* __restrict__ out_depth, const DevTex* __restrict__ textab) {
-    constexpr int NT = TS * TS;
-    constexpr int mode = MODE;
+    using L = Layout<TS>;
+    constexpr int NT = L::NT, NB = L::NB, RPT = L::RPT;
     const int cam = tile / tiles_per_cam;
     const int lt = tile - cam * tiles_per_cam;
     const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
-    int lx, ly;
-    block_pixel<TS>(threadIdx.x, lx, ly);
-    const int px = tx * TS + lx, py = ty * TS + ly;
-    const bool inside = px < W && py < H;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lx = (warp % (TS / 8)) * 8 + (lane & 7);
+    const int ly0 = (warp / (TS / 8)) * 8 + (lane >> 3), ly1 = ly0 + 4;
+    const int tile_x0 = tx * TS, tile_y0 = ty * TS;
+    const int px = tile_x0 + lx, py0 = tile_y0 + ly0, py1 = tile_y0 + ly1;
     const int64_t beg = off[tile], end = off[tile + 1];
-    const uint32_t ng32 = (uint32_t)Ng;  // unified ids are 32-bit: a 32-bit compare per fragment
     const GRec* G = grec + (int64_t)cam * Ng;
     const GRec16* G16 = grec16 ? grec16 + (int64_t)cam * Ng : nullptr;
     const TRec* TR = trec + (int64_t)cam * Nt;
-    const float qx = px + 0.5f, qy = py + 0.5f;
-    const long long scx = (long long)px * 256 + 128, scy = (long long)py * 256 + 128;
+    const float qx = px + 0.5f, qy0 = py0 + 0.5f, qy1 = py1 + 0.5f;
 
-    PixelState st;
-    st.C[0] = st.C[1] = st.C[2] = 0.f;
-    st.T = 1.f; st.Tin = 1.f; st.g_since = 1.f;
-    st.D = 0.f; st.Wd = 0.f;
-    st.t[0] = st.t[1] = st.t[2] = st.t[3] = 1.f;
-    st.in_ent = false;
-    bool done = !inside;
-    int last = 0;
-    int sp = 0;
-    const int64_t pix = ((int64_t)cam * H + py) * W + px;
+    PixelState st[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        st[p].C[0] = st[p].C[1] = st[p].C[2] = 0.f;
+        st[p].T = 1.f; st[p].Tin = 1.f; st[p].g_since = 1.f;
+        st[p].D = 0.f; st[p].Wd = 0.f;
+        st[p].t[0] = st[p].t[1] = st[p].t[2] = st[p].t[3] = 1.f;
+        st[p].in_ent = false;
+        st[p].last = 0;
+        st[p].sp = 0;
+    }
+    st[0].done = !(px < W && py0 < H);
+    st[1].done = !(px < W && py1 < H);
+    const int64_t pix0 = ((int64_t)cam * H + py0) * W + px, pix1 = ((int64_t)cam * H + py1) * W + px;
 
-    // warp w owns one 8 x 4 pixel block of the tile (block_pixel); every
-    // record carries the mask of the blocks that can hold a fragment of it
-    const int warp = threadIdx.x >> 5;
-    const int tile_x0 = tx * TS, tile_y0 = ty * TS;
-    const float pxf = (float)px, pyf = (float)py;
-    constexpr int NB = BatchOf<TS>::value;
-    for (int64_t b0 = beg; b0 < end; b0 += NB) {
-        if (__syncthreads_count(done) == NT) break;
-        const int n = (int)min((int64_t)NB, end - b0);
+    for (int64_t b0 = beg; b0 < end;) {
+        int n = (int)min((int64_t)NB, end - b0);
+        uint32_t rid[RPT];
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            const int k = threadIdx.x + r * NT;
+            rid[r] = k < n ? ids[b0 + k] : 0xffffffffu;
+            const unsigned bal = __ballot_sync(0xffffffffu, rid[r] >= Ng && rid[r] < Ng + Nt);
+            // (written before the barrier: read only between it and the
+            // staging barrier, which every warp has passed by now)
+            if (lane == 0 && k < NB) sm.tbal[k >> 5] = bal;
+        }
+        if (__syncthreads_count(st[0].done && st[1].done) == NT) break;
+        // the batch ends before its (kTriSlots + 1)-th triangle (every thread
+        // finds the same cut from the ballots)
+        {
+            int run = 0;
+            for (int wd = 0; wd < NB / 32 && wd * 32 < n; ++wd) {
+                uint32_t m = sm.tbal[wd];
+                const int c = __popc(m);
+                if (run + c > kTriSlots) {
+                    for (int j = run; j < kTriSlots; ++j) m &= m - 1u;
+                    n = min(n, wd * 32 + __ffs(m) - 1);
+                    break;
+                }
+                run += c;
+            }
+        }
         const int lbase = (int)(b0 - beg) + 1;  // list position + 1 of the batch's first record
-        for (int k = threadIdx.x; k < n; k += NT) {
-            const uint32_t id = ids[b0 + k];
-            s_id[k] = id;
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            const int k = threadIdx.x + r * NT;
+            if (k >= n) continue;
+            const uint32_t id = rid[r];
+            sm.id[k] = id;
             if (id >= Ng + Nt) {
-                s_wmask[k] = 0u;  // not a record of this frame: no fragment
+                sm.wmask[k] = 0u;  // not a record of this frame: no fragment
             } else if (id < Ng) {
                 float4 a, b, c;
                 if (G16) {  // fp16 record: widen to the fp32 layout
@@ -110,192 +448,116 @@ __device__ __forceinline__ void composite_tile(
                     a = src[0]; b = src[1]; c = src[2];
                 }
                 const uint32_t rx = __float_as_uint(c.y), ry = __float_as_uint(c.z);
-                s_rec[k][0] = a;
-                s_rec[k][1] = make_float4(b.x, b.y, (float)(rx & 0xffff), (float)(rx >> 16));
-                s_rec[k][2] = make_float4((float)(ry & 0xffff), (float)(ry >> 16), b.z, b.w);
-                s_rec[k][3] = make_float4(c.x, c.w, 0.f, 0.f);  // (b, Z)
-                s_wmask[k] = gauss_block_mask<TS>(a.x, a.y, a.z, a.w, b.x, b.y, (int)(rx & 0xffff), (int)(rx >> 16),
-                                                  (int)(ry & 0xffff), (int)(ry >> 16), tile_x0, tile_y0);
+                const int x0 = (int)(rx & 0xffff), x1 = (int)(rx >> 16), y0 = (int)(ry & 0xffff), y1 = (int)(ry >> 16);
+                sm.g[k][0] = a;
+                sm.g[k][1] = b;
+                sm.g[k][2] = make_float4(c.x, c.w, 0.f, 0.f);
+                reinterpret_cast<int4*>(&sm.g[k][3])[0] = make_int4(x0, x1 - x0, y0, y1 - y0);
+                sm.wmask[k] = gauss_block_mask<TS, 8>(a.x, a.y, a.z, a.w, b.x, b.y, x0, x1, y0, y1, tile_x0, tile_y0);
             } else {
-                const float4* src = reinterpret_cast<const float4*>(TR + (id - Ng));
-#pragma unroll
-                for (int q = 0; q < 10; ++q) s_rec[k][q] = src[q];
-                const TRec& tr = *reinterpret_cast<const TRec*>(&s_rec[k][0]);
-                s_wmask[k] = box_block_mask<TS>((int)(tr.rx & 0xffff), (int)(tr.rx >> 16), (int)(tr.ry & 0xffff),
-                                                (int)(tr.ry >> 16), tile_x0, tile_y0);
+                // slot = the triangles of the batch before record k
+                int slot = __popc(sm.tbal[k >> 5] & ((1u << (k & 31)) - 1u));
+                for (int wd = 0; wd < (k >> 5); ++wd) slot += __popc(sm.tbal[wd]);
+                sm.tslot[k] = (uint8_t)slot;
+                sm.wmask[k] = slot < kTriSlots ? stage_triangle<TS>(TR[id - Ng], tile_x0, tile_y0, &sm.t[slot][0])
+                                               : 0u;  // (cannot happen: the batch ends before that triangle)
             }
         }
         __syncthreads();
-        if (__any_sync(0xffffffffu, !done)) {
+        b0 += n;
+        if (__any_sync(0xffffffffu, !(st[0].done && st[1].done))) {
             // this warp's records of the batch, in order
-            uint8_t* lst = s_list + warp * BatchOf<TS>::value;
+            uint16_t* lst = sm.list + warp * NB;
             int cnt = 0;
-            const int lane = threadIdx.x & 31;
+            const uint32_t ng32 = (uint32_t)Ng;
             for (int c0 = 0; c0 < n; c0 += 32) {
-                const bool mine = c0 + lane < n && ((s_wmask[c0 + lane] >> warp) & 1u);
+                const int kk = c0 + lane;
+                const bool mine = kk < n && ((sm.wmask[kk] >> warp) & 1u);
                 const unsigned bal = __ballot_sync(0xffffffffu, mine);
-                if (mine) lst[cnt + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)(c0 + lane);
+                if (mine)
+                    lst[cnt + __popc(bal & ((1u << lane) - 1u))] =
+                        (uint16_t)(sm.id[kk] >= ng32 ? (kk | (sm.tslot[kk] << 8) | 0x8000) : kk);
                 cnt += __popc(bal);
             }
             __syncwarp();
             for (int li = 0; li < cnt; ++li) {
-                const int k = lst[li];
-                if (done) continue;
-                const uint32_t id = s_id[k];
-                if (id < ng32) {
-                    const float4 q1 = s_rec[k][1], q2 = s_rec[k][2];
-                    if (pxf < q1.z || pxf > q1.w || pyf < q2.x || pyf > q2.y) continue;
-                    const float4 q0 = s_rec[k][0];
-                    const float dx = __fsub_rn(qx, q0.x), dy = __fsub_rn(qy, q0.y);
-                    const float p2 = gauss_power2(q0.z, q0.w, q1.x, dx, dy);
-                    const float alpha = fminf(kAlphaMax, __fmul_rn(q1.y, fast_exp2(p2)));
-                    if (alpha < kAlphaMin) continue;
-                    const float w = alpha * st.T;
-                    st.C[0] += w * q2.z; st.C[1] += w * q2.w; st.C[2] += w * s_rec[k][3].x;
-                    if (mode == kModeDepth) { st.D += w * s_rec[k][3].y; st.Wd += w; }
-                    st.T = __fmaf_rn(-alpha, st.T, st.T);  // T (1 - alpha), one rounding
-                    if (mode == UMGS_BLEND_ENTITY_ALL) st.g_since *= (1.f - alpha);
-                    else st.in_ent = false;
+                const int ent = lst[li];
+                const int k = ent & 0xff;
+                if (st[0].done && st[1].done) continue;
+                if (!(ent & 0x8000)) {
+                    const int4 r = reinterpret_cast<const int4*>(&sm.g[k][3])[0];  // (x0, w, y0, h)
+                    const bool in0 = (unsigned)(px - r.x) <= (unsigned)r.y && (unsigned)(py0 - r.z) <= (unsigned)r.w &&
+                                     !st[0].done;
+                    const bool in1 = (unsigned)(px - r.x) <= (unsigned)r.y && (unsigned)(py1 - r.z) <= (unsigned)r.w &&
+                                     !st[1].done;
+                    if (!(in0 || in1)) continue;
+                    const float4 q0 = sm.g[k][0], q1 = sm.g[k][1];
+                    const float dx = __fsub_rn(qx, q0.x);
+                    const float cdx2 = __fmul_rn(q0.z, __fmul_rn(dx, dx));  // ca dx^2, shared by both pixels
+                    const float dy0 = __fsub_rn(qy0, q0.y), dy1 = __fsub_rn(qy1, q0.y);
+                    // (the operation order of gauss_power2)
+                    const float p0 = __fmaf_rn(q1.x, __fmul_rn(dy0, dy0), __fmaf_rn(q0.w, __fmul_rn(dx, dy0), cdx2));
+                    const float p1 = __fmaf_rn(q1.x, __fmul_rn(dy1, dy1), __fmaf_rn(q0.w, __fmul_rn(dx, dy1), cdx2));
+                    const float a0 = fminf(kAlphaMax, __fmul_rn(q1.y, fast_exp2(p0)));
+                    const float a1 = fminf(kAlphaMax, __fmul_rn(q1.y, fast_exp2(p1)));
+                    const bool t0 = in0 && a0 >= kAlphaMin, t1 = in1 && a1 >= kAlphaMin;
+                    if (!(t0 || t1)) continue;
+                    const float2 q2 = *reinterpret_cast<const float2*>(&sm.g[k][2]);
+                    if (t0) blend_gaussian<MODE>(st[0], a0, q1.z, q1.w, q2.x, q2.y, lbase + k, t_eps);
+                    if (t1) blend_gaussian<MODE>(st[1], a1, q1.z, q1.w, q2.x, q2.y, lbase + k, t_eps);
                 } else {
-                    const TRec& t = *reinterpret_cast<const TRec*>(&s_rec[k][0]);
-                    if (px < (int)(t.rx & 0xffff) || px > (int)(t.rx >> 16) || py < (int)(t.ry & 0xffff) ||
-                        py > (int)(t.ry >> 16))
-                        continue;
-                    long long E[3];
-#pragma unroll
-                    for (int e = 0; e < 3; ++e) E[e] = (long long)t.A[e] * scx + (long long)t.B[e] * scy + t.C[e];
-                    int mask = 0;
-                    if (mode == UMGS_BLEND_DIRECT) {
-                        mask = (E[0] >= 0 && E[1] >= 0 && E[2] >= 0) ? 0xf : 0;
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) {
-                            const int sdx = sample_dx(j), sdy = sample_dy(j);
-                            bool in = true;
-#pragma unroll
-                            for (int e = 0; e < 3; ++e) in = in && (E[e] + (long long)(t.A[e] * sdx + t.B[e] * sdy) >= 0);
-                            mask |= in ? (1 << j) : 0;
-                        }
+                    const float4* w = &sm.t[(ent >> 8) & 0x7f][0];
+                    const uint32_t tid = sm.id[k] - (uint32_t)Ng;
+                    if (!st[0].done && blend_triangle<SAVE, MODE>(st[0], w, TR, tid, px, py0, lx, ly0, stack, cap, npix,
+                                                                  pix0, textab)) {
+                        st[0].last = lbase + k;
+                        if (st[0].T < t_eps) st[0].done = true;
                     }
-                    if (mask == 0) continue;
-                    // attributes at the pixel centre: perspective-correct
-                    // barycentrics of the unsnapped triangle, clamped at 0
-                    float lam[3];
-#pragma unroll
-                    for (int e = 0; e < 3; ++e) {
-                        const int a = (e + 1) % 3, b = (e + 2) % 3;
-                        lam[e] = (t.u[a] - qx) * (t.v[b] - qy) - (t.u[b] - qx) * (t.v[a] - qy);
-                    }
-                    const float area = lam[0] + lam[1] + lam[2];
-                    float wv[3];
-                    if (area != 0.f) {
-                        const float ia = __fdividef(1.f, area);  // (fast division: screen areas stay far from 2^126)
-#pragma unroll
-                        for (int e = 0; e < 3; ++e) wv[e] = fmaxf(lam[e] * ia, 0.f) * t.iz[e];
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < 3; ++e) wv[e] = (1.f / 3.f) * t.iz[e];
-                    }
-                    const float ws = wv[0] + wv[1] + wv[2];
-                    float zt = 0.f;  // perspective-correct depth at the pixel centre (depth mode)
-                    if (mode == kModeDepth) {
-                        const float ls = area != 0.f ? fmaxf(lam[0] / area, 0.f) + fmaxf(lam[1] / area, 0.f) +
-                                                           fmaxf(lam[2] / area, 0.f)
-                                                     : 1.f;
-                        zt = ws > 0.f ? ls / ws : 3.f / (t.iz[0] + t.iz[1] + t.iz[2]);
-                    }
-                    if (ws > 0.f) { const float is = __fdividef(1.f, ws); wv[0] *= is; wv[1] *= is; wv[2] *= is; }
-                    else { wv[0] = wv[1] = wv[2] = 1.f / 3.f; }
-                    float col[3];
-                    if (t.tex > 0) {  // textured face: (u, v) interpolated like a colour, then sampled
-                        const float tu = wv[0] * t.col[0] + wv[1] * t.col[2] + wv[2] * t.col[4];
-                        const float tv = wv[0] * t.col[1] + wv[1] * t.col[3] + wv[2] * t.col[5];
-                        sample_texture(textab[t.tex - 1], tu, tv, col);
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < 3; ++c)
-                            col[c] = wv[0] * t.col[c] + wv[1] * t.col[3 + c] + wv[2] * t.col[6 + c];
-                    }
-                    float a = t.const_alpha ? t.alpha[0] : (wv[0] * t.alpha[0] + wv[1] * t.alpha[1] + wv[2] * t.alpha[2]);
-                    a = fminf(fmaxf(a, 0.f), 1.f);
-                    if (mode == UMGS_BLEND_DIRECT) {
-                        const float w = a * st.T;
-                        st.C[0] += w * col[0]; st.C[1] += w * col[1]; st.C[2] += w * col[2];
-                        st.T *= (1.f - a);
-                    } else if (mode == UMGS_BLEND_MSAA_ALL) {
-                        const float O = 0.25f * (float)__popc(mask);
-                        const float w = O * a * st.T;
-                        st.C[0] += w * col[0]; st.C[1] += w * col[1]; st.C[2] += w * col[2];
-                        st.T *= (1.f - O * a);
-                    } else {
-                        if (!st.in_ent) {
-                            st.Tin = st.T;
-                            st.t[0] = st.t[1] = st.t[2] = st.t[3] = 1.f;
-                            st.g_since = 1.f;
-                            st.in_ent = true;
-                        }
-                        if (SAVE && mode == UMGS_BLEND_FULL) {
-                            if (sp < cap) {
-                                const float q = 0.25f * st.Tin;
-                                stack[(int64_t)sp * npix + pix] = make_float4(q * st.t[0], q * st.t[1], q * st.t[2], q * st.t[3]);
-                            }
-                            ++sp;
-                        }
-                        float O = 0.f;
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) O += ((mask >> j) & 1) ? st.t[j] : 0.f;
-                        O *= 0.25f;
-                        const float w = st.Tin * O * a;
-                        st.C[0] += w * col[0]; st.C[1] += w * col[1]; st.C[2] += w * col[2];
-                        if (mode == kModeDepth) { st.D += w * zt; st.Wd += w; }
-#pragma unroll
-                        for (int j = 0; j < 4; ++j)
-                            if ((mask >> j) & 1) st.t[j] *= (1.f - a);
-                        const float tm = 0.25f * ((st.t[0] + st.t[1]) + (st.t[2] + st.t[3]));
-                        if (mode == kModeTProduct) st.T *= (1.f - O * a);
-                        else st.T = (mode == UMGS_BLEND_ENTITY_ALL) ? st.Tin * tm * st.g_since : st.Tin * tm;
+                    if (!st[1].done && blend_triangle<SAVE, MODE>(st[1], w, TR, tid, px, py1, lx, ly1, stack, cap, npix,
+                                                                  pix1, textab)) {
+                        st[1].last = lbase + k;
+                        if (st[1].T < t_eps) st[1].done = true;
                     }
                 }
-                last = lbase + k;
-                if (st.T < t_eps) done = true;
             }
         }
     }
-    if (inside) {
-        out[pix] = make_float4(st.C[0] + st.T * bg0, st.C[1] + st.T * bg1, st.C[2] + st.T * bg2, st.T);
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int py = p ? py1 : py0;
+        if (!(px < W && py < H)) continue;
+        const int64_t pix = p ? pix1 : pix0;
+        const PixelState& s = st[p];
+        out[pix] = make_float4(s.C[0] + s.T * bg0, s.C[1] + s.T * bg1, s.C[2] + s.T * bg2, s.T);
         // bit 31: the pixel stopped at T < t_eps after list position `last`
-        if (out_last) out_last[pix] = last | (st.T < t_eps ? (int)0x80000000u : 0);
+        if (out_last) out_last[pix] = s.last | (s.T < t_eps ? (int)0x80000000u : 0);
         if (SAVE) {
-            out_tfin[pix] = st.T;
-            out_ntri[pix] = sp;
-            if (sp > cap) atomicMax(need, sp);
+            out_tfin[pix] = s.T;
+            out_ntri[pix] = s.sp;
+            if (s.sp > cap) atomicMax(need, s.sp);
         }
-        if (mode == kModeDepth) out_depth[pix] = st.Wd > 0.f ? st.D / st.Wd : __int_as_float(0x7f800000);
+        if (MODE == kModeDepth) out_depth[pix] = s.Wd > 0.f ? s.D / s.Wd : __int_as_float(0x7f800000);
     }
 }
 
 
 // one CTA per tile (grid launch)
 template <int TS, bool SAVE, int MODE>
-__global__ void __launch_bounds__(TS * TS) composite_kernel(
+__global__ void __launch_bounds__(Layout<TS>::NT, MinBlocks<TS>::value) composite_kernel(
     const uint32_t* __restrict__ ids, const int64_t* __restrict__ off, const GRec* __restrict__ grec,
     const GRec16* __restrict__ grec16, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
     int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, float4* __restrict__ out, int32_t* __restrict__ out_last,
     float* __restrict__ out_tfin, int32_t* __restrict__ out_ntri, float4* __restrict__ stack, int cap,
     int64_t npix, int32_t* __restrict__ need, float* __restrict__ out_depth, const DevTex* __restrict__ textab) {
     pdl_enter();
-    constexpr int NB = BatchOf<TS>::value;
-    __shared__ float4 s_rec[NB][10];
-    __shared__ uint32_t s_id[NB];
-    __shared__ uint32_t s_wmask[NB];
-    __shared__ uint8_t s_list[(TS * TS / 32) * NB];
-    composite_tile<TS, SAVE, MODE>(blockIdx.x, s_rec, s_id, s_wmask, s_list, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, out, out_last, out_tfin, out_ntri, stack, cap, npix, need, out_depth, textab);
+    __shared__ CompositeSmem<TS> sm;
+    composite_tile<TS, SAVE, MODE>(blockIdx.x, sm, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, out, out_last, out_tfin, out_ntri, stack, cap, npix, need, out_depth, textab);
 }
 
 // persistent launch: resident CTAs take tiles from an atomic queue in the
 // order `order` (decreasing list length: the heaviest tiles start first)
 template <int TS, bool SAVE, int MODE>
-__global__ void __launch_bounds__(TS * TS) composite_persistent_kernel(
+__global__ void __launch_bounds__(Layout<TS>::NT, MinBlocks<TS>::value) composite_persistent_kernel(
     const uint32_t* __restrict__ order, unsigned* __restrict__ work, int64_t M,
     const uint32_t* __restrict__ ids, const int64_t* __restrict__ off, const GRec* __restrict__ grec,
     const GRec16* __restrict__ grec16, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
@@ -303,11 +565,7 @@ __global__ void __launch_bounds__(TS * TS) composite_persistent_kernel(
     float* __restrict__ out_tfin, int32_t* __restrict__ out_ntri, float4* __restrict__ stack, int cap,
     int64_t npix, int32_t* __restrict__ need, float* __restrict__ out_depth, const DevTex* __restrict__ textab) {
     pdl_enter();
-    constexpr int NB = BatchOf<TS>::value;
-    __shared__ float4 s_rec[NB][10];
-    __shared__ uint32_t s_id[NB];
-    __shared__ uint32_t s_wmask[NB];
-    __shared__ uint8_t s_list[(TS * TS / 32) * NB];
+    __shared__ CompositeSmem<TS> sm;
     __shared__ unsigned s_next;
     while (true) {
         if (threadIdx.x == 0) s_next = atomicAdd(work, 1u);
@@ -315,7 +573,7 @@ __global__ void __launch_bounds__(TS * TS) composite_persistent_kernel(
         const unsigned k = s_next;
         __syncthreads();
         if ((int64_t)k >= M) break;
-        composite_tile<TS, SAVE, MODE>((int)order[k], s_rec, s_id, s_wmask, s_list, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, out, out_last, out_tfin, out_ntri, stack, cap, npix, need, out_depth, textab);
+        composite_tile<TS, SAVE, MODE>((int)order[k], sm, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, out, out_last, out_tfin, out_ntri, stack, cap, npix, need, out_depth, textab);
         __syncthreads();
     }
 }
@@ -367,14 +625,14 @@ cudaError_t launch_composite(umgs_frame* fr, const umgs_render_opts& opts, float
         nblk = opts.sched * fr->ctx->num_sms;
     }
 #define UMGS_LAUNCH(TSV, SV, MV)                                                                                \
-    if (persist) launch_pdl(composite_persistent_kernel<TSV, SV, MV>, nblk, TSV * TSV, 0, stream, order, work, M,      \
+    if (persist) launch_pdl(composite_persistent_kernel<TSV, SV, MV>, nblk, Layout<TSV>::NT, 0, stream, order, work, M,      \
         fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->mixed ? fr->grec.as<GRec16>() : nullptr,  \
         fr->trec.as<TRec>(), fr->ng,                                                                            \
         fr->nt, fr->tiles_x, tpc, fr->W, fr->H, te, opts.bg[0], opts.bg[1], opts.bg[2], out,                      \
         fr->last.as<int32_t>(), save ? fr->tfin.as<float>() : nullptr, save ? fr->ntri.as<int32_t>() : nullptr,   \
         save ? fr->stack.as<float4>() : nullptr, fr->stack_cap, npix, fr->status.as<int32_t>() + 2,             \
         fr->has_depth ? fr->depth.as<float>() : nullptr, fr->textab.as<DevTex>());                                                                                         \
-    else launch_pdl(composite_kernel<TSV, SV, MV>, M, TSV * TSV, 0, stream,                                             \
+    else launch_pdl(composite_kernel<TSV, SV, MV>, M, Layout<TSV>::NT, 0, stream,                                             \
         fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->mixed ? fr->grec.as<GRec16>() : nullptr,  \
         fr->trec.as<TRec>(), fr->ng,                                                                            \
         fr->nt, fr->tiles_x, tpc, fr->W, fr->H, te, opts.bg[0], opts.bg[1], opts.bg[2], out,                      \

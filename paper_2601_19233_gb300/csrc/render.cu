@@ -232,7 +232,7 @@ __global__ void __launch_bounds__(256, 2) project_gaussians_kernel(
             const float id = 1.f / det;
             ia = c * id; ib = -b * id; ic = a * id;
         }
-        if (det < 0.0009765625f * a * c) {  // near-singular: refined in fp64 by refine_conics_kernel
+        if (det < kConicFp64 * a * c) {  // near-singular: refined in fp64 by refine_conics_kernel
             const unsigned slot = atomicAdd(fix_count, 1u);
             if (slot < fix_cap) fix_list[slot] = ri;
         }
