@@ -29,10 +29,9 @@ template <int TS> struct Layout {
     static constexpr int NB = 256;           // records staged per batch
     static constexpr int RPT = (NB + NT - 1) / NT;  // records per thread in the staging
 };
-#ifndef UMGS_COMP_MINB
-#define UMGS_COMP_MINB 6
-#endif
-template <int TS> struct MinBlocks { static constexpr int value = TS == 16 ? UMGS_COMP_MINB : 1; };
+// resident CTAs per SM the 16 x 16 kernels are built for (80 registers, no
+// spills; shared memory allows the same)
+template <int TS> struct MinBlocks { static constexpr int value = TS == 16 ? 6 : 1; };
 constexpr int kSlot = 11;      // 16-byte vectors of shared memory per staged triangle
 constexpr int kTriSlots = 96;  // staged triangles per batch (a batch ends before the 97th)
 
@@ -413,19 +412,18 @@ __device__ __forceinline__ void composite_tile(
         }
         if (__syncthreads_count(st[0].done && st[1].done) == NT) break;
         // the batch ends before its (kTriSlots + 1)-th triangle (every thread
-        // finds the same cut from the ballots)
-        {
-            int run = 0;
-            for (int wd = 0; wd < NB / 32 && wd * 32 < n; ++wd) {
-                uint32_t m = sm.tbal[wd];
-                const int c = __popc(m);
-                if (run + c > kTriSlots) {
-                    for (int j = run; j < kTriSlots; ++j) m &= m - 1u;
-                    n = min(n, wd * 32 + __ffs(m) - 1);
-                    break;
-                }
-                run += c;
+        // finds the same cut, and the number of triangles nT, from the ballots)
+        int nT = 0;
+        for (int wd = 0; wd < NB / 32 && wd * 32 < n; ++wd) {
+            uint32_t m = sm.tbal[wd];
+            const int c = __popc(m);
+            if (nT + c > kTriSlots) {
+                for (int j = nT; j < kTriSlots; ++j) m &= m - 1u;
+                n = min(n, wd * 32 + __ffs(m) - 1);
+                nT = kTriSlots;
+                break;
             }
+            nT += c;
         }
         const int lbase = (int)(b0 - beg) + 1;  // list position + 1 of the batch's first record
 #pragma unroll
@@ -454,14 +452,26 @@ __device__ __forceinline__ void composite_tile(
                 sm.g[k][2] = make_float4(c.x, c.w, 0.f, 0.f);
                 reinterpret_cast<int4*>(&sm.g[k][3])[0] = make_int4(x0, x1 - x0, y0, y1 - y0);
                 sm.wmask[k] = gauss_block_mask<TS, 8>(a.x, a.y, a.z, a.w, b.x, b.y, x0, x1, y0, y1, tile_x0, tile_y0);
-            } else {
-                // slot = the triangles of the batch before record k
-                int slot = __popc(sm.tbal[k >> 5] & ((1u << (k & 31)) - 1u));
-                for (int wd = 0; wd < (k >> 5); ++wd) slot += __popc(sm.tbal[wd]);
-                sm.tslot[k] = (uint8_t)slot;
-                sm.wmask[k] = slot < kTriSlots ? stage_triangle<TS>(TR[id - Ng], tile_x0, tile_y0, &sm.t[slot][0])
-                                               : 0u;  // (cannot happen: the batch ends before that triangle)
             }
+        }
+        // triangles, compacted over the threads: thread t stages the batch's
+        // t-th triangle (slot t), so that the long triangle set-up does not
+        // hold up the Gaussian records of 32 different warps
+        for (int t = threadIdx.x; t < nT; t += NT) {
+            int run = 0, wd = 0;
+            uint32_t m = 0u;
+            for (; wd < NB / 32; ++wd) {
+                m = sm.tbal[wd];
+                const int c = __popc(m);
+                if (run + c > t) break;
+                run += c;
+            }
+            if (wd >= NB / 32) break;  // (cannot happen: nT counts the ballots' bits)
+            for (int j = run; j < t; ++j) m &= m - 1u;
+            const int k = wd * 32 + __ffs(m) - 1;
+            const uint32_t id = ids[b0 + k];
+            sm.tslot[k] = (uint8_t)t;
+            sm.wmask[k] = stage_triangle<TS>(TR[id - Ng], tile_x0, tile_y0, &sm.t[t][0]);
         }
         __syncthreads();
         b0 += n;
@@ -474,9 +484,11 @@ __device__ __forceinline__ void composite_tile(
                 const int kk = c0 + lane;
                 const bool mine = kk < n && ((sm.wmask[kk] >> warp) & 1u);
                 const unsigned bal = __ballot_sync(0xffffffffu, mine);
-                if (mine)
-                    lst[cnt + __popc(bal & ((1u << lane) - 1u))] =
-                        (uint16_t)(sm.id[kk] >= ng32 ? (kk | (sm.tslot[kk] << 8) | 0x8000) : kk);
+                if (mine) {
+                    const int pos = cnt + __popc(bal & ((1u << lane) - 1u));
+                    const bool tri = sm.id[kk] >= ng32;
+                    lst[pos] = (uint16_t)(tri ? (kk | (sm.tslot[kk] << 8) | 0x8000) : kk);
+                }
                 cnt += __popc(bal);
             }
             __syncwarp();
