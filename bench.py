@@ -533,6 +533,16 @@ def run_forms(ctx, dev, steps, crops=None):
     fr = umgs.Frame(ctx)
     t_plain = _time(lambda: umgs.render(ctx, g, ms, sc.cameras, plain, out=out, frame=fr), steps)
     evals_plain = fr.evaluations()
+    # per-stage split of the plain render (a separate profiled pass)
+    umgs.profile_read(ctx)
+    umgs.profile_enable(ctx, True)
+    for _ in range(3):
+        umgs.render(ctx, g, ms, sc.cameras, plain, out=out, frame=fr)
+    torch.cuda.synchronize()
+    st_ms, st_n = umgs.profile_read(ctx)
+    umgs.profile_enable(ctx, False)
+    names = stage_names()
+    mv_stages = {names[k]: round(st_ms[k] / st_n[k], 3) for k in range(16) if st_n[k] > 0}
     best, t_tune = umgs.autotune(ctx, g, ms, sc.cameras, plain, out)
     fr2 = umgs.Frame(ctx)
     # the scene and cameras are the same every replay: pair capacity = the
@@ -544,8 +554,8 @@ def run_forms(ctx, dev, steps, crops=None):
         "workload": "64 orbit views 800x800, 500k Gaussians SH3 (70% in 3 blobs) + 100k-face torus",
         "plain_views_per_s": round(nv * 1e3 / t_plain, 1), "plain_ms": round(t_plain, 3),
         "graph_views_per_s": round(nv * 1e3 / t_graph, 1), "graph_ms": round(t_graph, 3),
-        "autotuned": {"tile_size": best.tile_size, "sched": best.sched, "ms": round(t_tune, 3)},
-        "keys": int(fr.counts()[0]), "evaluations": int(evals_plain)}
+        "autotuned": {"tile_size": best.tile_size, "sched": best.sched, "split": best.split, "ms": round(t_tune, 3)},
+        "keys": int(fr.counts()[0]), "evaluations": int(evals_plain), "plain_stages_ms": mv_stages}
     del gr, fr, fr2, out, g, ms
     torch.cuda.empty_cache()
     # config 3: 8 views of 512x512, forward vs forward+backward (L2 loss to a

@@ -137,6 +137,16 @@ typedef struct {
     int32_t sched;           /* compositor schedule: 0 = one CTA per tile; k > 0 = persistent launch with
                                 k CTAs per SM taking tiles in decreasing order of list length */
     float edge_sigma;        /* UMGS_RENDER_SOFT_EDGE: edge width sigma in pixels (default 0) */
+    int32_t split;           /* per-tile work split for uneven loads: 0 = off; else 256..1048576, a tile
+                                whose list holds more than `split` records is composited as segments of
+                                `split` records on separate CTAs, each from T = 1, merged per pixel front
+                                to back (C = sum_k (prod_{m<k} T_m) C_k).  Cuts only in front of a list's
+                                first triangle record (entity state of Eq. 7-9 never crosses a cut).  The
+                                fp association differs from the whole tile, and a segment stops at its own
+                                T < t_eps: pixels agree with the whole-tile composite within t_eps times the
+                                largest colour plus rounding.  Not with SAVE_BACKWARD, DEPTH or SOFT_EDGE.
+                                Up to 65,535 segments (512 MB of segment buffers) per render; tiles beyond
+                                that are composited whole. */
 } umgs_render_opts;
 
 /* Gradient outputs of umgs_render_backward; every pointer is nullable (not
@@ -174,7 +184,9 @@ umgs_status umgs_ctx_sync(umgs_ctx* ctx, void* stream);
 void umgs_default_render_opts(umgs_render_opts* opts);
 
 /* A frame holds the projected records, sorted tile lists and per-pixel state
- * of one umgs_render call, for umgs_render_backward and for inspection. */
+ * of one umgs_render call, for umgs_render_backward and for inspection.  A
+ * frame is used with its context only while that context lives; destroying
+ * it (umgs_frame_destroy) is allowed after its context was destroyed. */
 umgs_status umgs_frame_create(umgs_ctx* ctx, umgs_frame** out);
 void umgs_frame_destroy(umgs_frame* frame);
 
@@ -353,8 +365,8 @@ umgs_status umgs_bind(umgs_ctx* ctx, const umgs_gaussians* g, const float* proxy
 /* ---- deformation transfer (Sec. 3.3, Eq. 12-13) ---------------------------
  *
  * Per proxy face f: deformation gradient D_f = F'_f F_f^-1 with the frame
- * F = [e1, e2, n/sqrt(|n|)] (e1 = v1-v0, e2 = v2-v0, n = e1 x e2; the inverse
- * is taken in fp64 for sliver faces).  Per proxy vertex: D_v = rest-area-
+ * F = [e1, e2, n/sqrt(|n|)] (e1 = v1-v0, e2 = v2-v0, n = e1 x e2; the frames
+ * and the inverse are computed in fp64 for sliver faces).  Per proxy vertex: D_v = rest-area-
  * weighted mean of the incident D_f, polar D_v = R_v S_v (a proper rotation;
  * for det D_v < 0 the smallest singular direction is flipped), r_v = log R_v
  * (axis-angle, angle in [0, pi]), Delta_v = V'_v - V_v.
@@ -395,7 +407,8 @@ umgs_status umgs_deform_vertex_table(umgs_ctx* ctx, float* out_table, int64_t nv
 
 /* Number of proxy faces of the last umgs_deform / umgs_deform_compact on
  * `ctx` whose rest frame [e1, e2, n/sqrt|n|] was a sliver (|e1 x e2| <
- * 1e-3 |e1||e2|) and was therefore inverted in fp64 (per-face deformation
+ * 1e-3 |e1||e2|), whose deformation gradient (both frames and the inverse)
+ * was therefore computed in fp64 (per-face deformation
  * gradient of the per-vertex transform, Sec. 3.3).  Host output;
  * synchronises `stream`. */
 umgs_status umgs_deform_fp64_faces(umgs_ctx* ctx, int64_t* count, void* stream);
@@ -451,11 +464,13 @@ umgs_status umgs_graph_launch(umgs_graph* graph, void* stream);
 umgs_status umgs_graph_check(umgs_graph* graph, void* stream);
 void umgs_graph_destroy(umgs_graph* graph);
 
-/* Autotuner: renders the given workload with every tile size (8, 16, 32)
- * and compositor schedule (one CTA per tile; persistent with 1, 2 or 4 CTAs
- * per SM; one CTA per tile only with UMGS_RENDER_SOFT_EDGE), 1 warm-up +
- * 3 timed renders each (CUDA events on `stream`), and
- * writes the fastest tile_size and sched into *inout (other fields kept) and
+/* Autotuner: renders the given workload with every tile size (8, 16, 32),
+ * compositor schedule (one CTA per tile; persistent with 1, 2 or 4 CTAs
+ * per SM; one CTA per tile only with UMGS_RENDER_SOFT_EDGE) and per-tile
+ * work split (off, 512, 1024, 2048 records; off with SOFT_EDGE, DEPTH or
+ * SAVE_BACKWARD), 1 warm-up + 3 timed renders each (CUDA events on
+ * `stream`), and writes the fastest tile_size, sched and split into *inout
+ * (other fields kept) and
  * its time in ms per render into *best_ms (nullable).  out_rgbt receives the
  * renders ([ncams,H,W,4]).  Synchronises. */
 umgs_status umgs_autotune(umgs_ctx* ctx, const umgs_gaussians* gaussians, const umgs_mesh* meshes,

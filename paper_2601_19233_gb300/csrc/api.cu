@@ -47,6 +47,7 @@ umgs_status umgs_ctx_create(umgs_ctx** out, int device) {
     }
     c->default_frame = new umgs_frame();
     c->default_frame->ctx = c;
+    c->default_frame->device = device;
     *out = c;
     return UMGS_OK;
 }
@@ -69,6 +70,7 @@ void umgs_ctx_destroy(umgs_ctx* ctx) {
     ctx->bind_cams.release();
     ctx->bind_cnt.release();
     delete ctx;
+    cudaGetLastError();  // leave no error of the teardown behind for the next call
 }
 
 const char* umgs_last_error(const umgs_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
@@ -126,6 +128,7 @@ umgs_status umgs_frame_create(umgs_ctx* ctx, umgs_frame** out) {
     if (!ctx || !out) return UMGS_ERR_INVALID_ARG;
     umgs_frame* f = new umgs_frame();
     f->ctx = ctx;
+    f->device = ctx->device;
     *out = f;
     ctx->err.clear();
     return UMGS_OK;
@@ -133,10 +136,12 @@ umgs_status umgs_frame_create(umgs_ctx* ctx, umgs_frame** out) {
 
 void umgs_frame_destroy(umgs_frame* frame) {
     if (!frame) return;
-    cudaSetDevice(frame->ctx->device);
+    // (the device is the frame's own copy: its context may be gone already)
+    cudaSetDevice(frame->device);
     cudaDeviceSynchronize();
     frame->release();
     delete frame;
+    cudaGetLastError();  // leave no error of the teardown behind for the next call
 }
 
 umgs_status umgs_render(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_mesh* meshes, int32_t nmeshes,
@@ -166,6 +171,11 @@ umgs_status umgs_render(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_mesh*
         return fail(ctx, UMGS_ERR_INVALID_ARG,
                     "UMGS_RENDER_SOFT_EDGE needs FULL mode, 0 < edge_sigma <= 16, sched 0 and none of MIXED, "
                     "T_PRODUCT, DEPTH");
+    if (opts.split != 0 &&
+        (opts.split < 256 || opts.split > (1 << 20) ||
+         (opts.flags & (UMGS_RENDER_SAVE_BACKWARD | UMGS_RENDER_DEPTH | UMGS_RENDER_SOFT_EDGE))))
+        return fail(ctx, UMGS_ERR_INVALID_ARG,
+                    "split must be 0 or 256..1048576, and not with SAVE_BACKWARD, DEPTH or SOFT_EDGE");
     if (!cams || ncams < 1) return fail(ctx, UMGS_ERR_INVALID_ARG, "need at least one camera");
     if (!out_rgbt) return fail(ctx, UMGS_ERR_INVALID_ARG, "out_rgbt is NULL");
     if (nmeshes < 0 || (nmeshes > 0 && !meshes)) return fail(ctx, UMGS_ERR_INVALID_ARG, "bad mesh array");

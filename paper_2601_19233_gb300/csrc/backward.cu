@@ -204,7 +204,9 @@ __global__ void __launch_bounds__(TS * TS, TS == 16 ? (SOFT ? 2 : 4) : 1) compos
                     T = Tk;
                     if (ag <= kAlphaMax) {
                         const float dpow = dalpha * alpha;
-                        const float A = -2.f * kLn2 * q0.z, B = -kLn2 * q0.w, C = -2.f * kLn2 * q1.x;
+                        float ca, cb, cc;
+                            factor_conic(q0.z, q0.w, q1.x, ca, cb, cc);
+                            const float A = -2.f * kLn2 * ca, B = -kLn2 * cb, C = -2.f * kLn2 * cc;
                         v[0] = dpow * (A * dx + B * dy);
                         v[1] = dpow * (B * dx + C * dy);
                         v[2] = -0.5f * dpow * dx * dx;
@@ -354,6 +356,323 @@ __global__ void __launch_bounds__(TS * TS, TS == 16 ? (SOFT ? 2 : 4) : 1) compos
                 for (int e = 0; e < 9; ++e)
                     if (s_acc[k][e] != 0.f) atomicAdd(dst + e, s_acc[k][e]);
             } else {
+                float* dst = tgrad + ((int64_t)cam * Nt + (id - Ng)) * 24;
+#pragma unroll
+                for (int e = 0; e < 21; ++e)
+                    if (s_acc[k][e] != 0.f) atomicAdd(dst + e, s_acc[k][e]);
+            }
+        }
+    }
+}
+
+// ---- two pixels per thread (binary coverage) ---------------------------------
+// The replay of composite_bwd_kernel<TS, false> with the forward compositor's
+// layout: warp w owns the 8 x 8 block (w % (TS/8), w / (TS/8)), lane l the
+// pixels (l % 8, l / 8) and (l % 8, l / 8 + 4).  The arithmetic per pixel is
+// unchanged; the two pixels' derivatives of a record are added in the lane
+// before the warp reduction, so a record costs one reduction per 64 pixels.
+template <int TS> struct Bwd2 {
+    static constexpr int NT = TS * TS / 2;
+    static constexpr int NW = NT / 32;
+    static constexpr int NB = 128;  // records per batch
+    static constexpr int SMEM = NB * (160 + 88 + 4 + 4) + NW * NB + 4 * NW + 16;
+};
+
+template <int TS>
+__global__ void __launch_bounds__(Bwd2<TS>::NT, TS == 16 ? 5 : 1) composite_bwd2_kernel(
+    const uint32_t* __restrict__ ids, const int64_t* __restrict__ off,
+    const GRec* __restrict__ grec, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
+    int tiles_per_cam, int W, int H, float bg0,
+    float bg1, float bg2, const float4* __restrict__ dout, const int32_t* __restrict__ last,
+    const float* __restrict__ tfin, const int32_t* __restrict__ ntri, const float4* __restrict__ stack, int64_t npix,
+    float* __restrict__ ggrad, float* __restrict__ tgrad) {
+    pdl_enter();
+    constexpr int NT = Bwd2<TS>::NT, NW = Bwd2<TS>::NW, kBatchB = Bwd2<TS>::NB;
+    extern __shared__ __align__(16) unsigned char smem[];
+    float4 (*s_rec)[10] = reinterpret_cast<float4 (*)[10]>(smem);
+    float (*s_acc)[22] = reinterpret_cast<float (*)[22]>(smem + kBatchB * 160);  // per record gradient
+    uint32_t* s_id = reinterpret_cast<uint32_t*>(smem + kBatchB * (160 + 88));
+    uint32_t* s_wmask = s_id + kBatchB;
+    int* s_wmax = reinterpret_cast<int*>(s_wmask + kBatchB);
+    int& s_max = s_wmax[NW];
+    uint8_t* s_list = reinterpret_cast<uint8_t*>(s_wmax + NW + 4);
+    const int tile = blockIdx.x;
+    const int cam = tile / tiles_per_cam;
+    const int lt = tile - cam * tiles_per_cam;
+    const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lx = (warp % (TS / 8)) * 8 + (lane & 7);
+    const int ly0 = (warp / (TS / 8)) * 8 + (lane >> 3);
+    const int px = tx * TS + lx;
+    const int64_t beg = off[tile];
+    const GRec* G = grec + (int64_t)cam * Ng;
+    const TRec* TR = trec + (int64_t)cam * Nt;
+    const float qx = px + 0.5f;
+    const long long scx = (long long)px * 256 + 128;
+
+    int nlast[2], sp[2];
+    float T[2], U[2], gr[2], gg[2], gb[2], Uj[2][4], qy[2];
+    bool in_ent[2], inside[2];
+    int64_t pix[2];
+    long long scy[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int py = ty * TS + ly0 + 4 * p;
+        qy[p] = py + 0.5f;
+        scy[p] = (long long)py * 256 + 128;
+        inside[p] = px < W && py < H;
+        pix[p] = ((int64_t)cam * H + py) * W + px;
+        nlast[p] = 0; sp[p] = 0;
+        T[p] = 1.f; U[p] = 0.f; gr[p] = gg[p] = gb[p] = 0.f;
+        if (inside[p]) {
+            nlast[p] = last[pix[p]] & 0x7fffffff;  // bit 31: stopped at T < t_eps
+            sp[p] = ntri[pix[p]];
+            T[p] = tfin[pix[p]];
+            const float4 d = dout[pix[p]];
+            gr[p] = d.x; gg[p] = d.y; gb[p] = d.z;
+            U[p] = d.x * bg0 + d.y * bg1 + d.z * bg2 + d.w;
+        }
+        Uj[p][0] = Uj[p][1] = Uj[p][2] = Uj[p][3] = 0.f;
+        in_ent[p] = false;
+    }
+    if (threadIdx.x == 0) s_max = 0;
+    __syncthreads();
+    const int mylast = max(nlast[0], nlast[1]);
+    atomicMax(&s_max, mylast);
+    {
+        int wm = mylast;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) wm = max(wm, __shfl_xor_sync(0xffffffffu, wm, o));
+        if (lane == 0) s_wmax[warp] = wm;
+    }
+    __syncthreads();
+    const int maxlast = s_max;
+    const int wmaxlast = s_wmax[warp];
+    const int tile_x0 = tx * TS, tile_y0 = ty * TS;
+
+    for (int bend = maxlast; bend > 0; bend -= kBatchB) {
+        const int b0 = max(0, bend - kBatchB);
+        const int n = bend - b0;
+        __syncthreads();
+        for (int k = threadIdx.x; k < n; k += NT) {
+            const uint32_t id = ids[beg + b0 + k];
+            s_id[k] = id;
+            if (id >= Ng + Nt) {
+                s_wmask[k] = 0u;  // not a record of this frame
+            } else if (id < Ng) {
+                const float4* src = reinterpret_cast<const float4*>(G + id);
+                const float4 a = src[0], q1 = src[1], c = src[2];
+                s_rec[k][0] = a; s_rec[k][1] = q1; s_rec[k][2] = c;
+                const uint32_t rx = __float_as_uint(c.y), ry = __float_as_uint(c.z);
+                s_wmask[k] = gauss_block_mask<TS, 8>(a.x, a.y, a.z, a.w, q1.x, q1.y, (int)(rx & 0xffff),
+                                                     (int)(rx >> 16), (int)(ry & 0xffff), (int)(ry >> 16), tile_x0,
+                                                     tile_y0);
+            } else {
+                const float4* src = reinterpret_cast<const float4*>(TR + (id - Ng));
+#pragma unroll
+                for (int q = 0; q < 10; ++q) s_rec[k][q] = src[q];
+                const TRec& tr = *reinterpret_cast<const TRec*>(&s_rec[k][0]);
+                s_wmask[k] = box_block_mask<TS, 8>((int)(tr.rx & 0xffff), (int)(tr.rx >> 16), (int)(tr.ry & 0xffff),
+                                                   (int)(tr.ry >> 16), tile_x0, tile_y0);
+            }
+#pragma unroll
+            for (int e = 0; e < 22; ++e) s_acc[k][e] = 0.f;
+        }
+        __syncthreads();
+        // this warp's records of the batch (in order; replayed back to front)
+        uint8_t* lst = s_list + warp * kBatchB;
+        int cnt = 0;
+        for (int c0 = 0; c0 < n; c0 += 32) {
+            const bool mine = c0 + lane < n && b0 + c0 + lane < wmaxlast && ((s_wmask[c0 + lane] >> warp) & 1u);
+            const unsigned bal = __ballot_sync(0xffffffffu, mine);
+            if (mine) lst[cnt + __popc(bal & ((1u << lane) - 1u))] = (uint8_t)(c0 + lane);
+            cnt += __popc(bal);
+        }
+        __syncwarp();
+        for (int li = cnt - 1; li >= 0; --li) {
+            const int k = lst[li];
+            const int pos = b0 + k;
+            const uint32_t id = s_id[k];
+            if (id < Ng) {
+                // ---- Gaussian fragment
+                const float4 q0 = s_rec[k][0], q1 = s_rec[k][1], q2 = s_rec[k][2];
+                const uint32_t rx = __float_as_uint(q2.y), ry = __float_as_uint(q2.z);
+                const bool inx = px >= (int)(rx & 0xffff) && px <= (int)(rx >> 16);
+                const float dx = __fsub_rn(qx, q0.x);
+                float v[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) v[e] = 0.f;
+                bool any = false;
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    const int py = ty * TS + ly0 + 4 * p;
+                    const bool inrect = inx && py >= (int)(ry & 0xffff) && py <= (int)(ry >> 16);
+                    const float dy = __fsub_rn(qy[p], q0.y);
+                    const float p2 = gauss_power2(q0.z, q0.w, q1.x, dx, dy);
+                    const float Gv = fast_exp2(p2);
+                    const float ag = __fmul_rn(q1.y, Gv);
+                    const float alpha = fminf(kAlphaMax, ag);
+                    const bool contrib = inside[p] && pos < nlast[p] && inrect && alpha >= kAlphaMin;
+                    if (contrib) {
+                        any = true;
+                        if (in_ent[p]) {
+                            U[p] = 0.25f * ((Uj[p][0] + Uj[p][1]) + (Uj[p][2] + Uj[p][3]));
+                            in_ent[p] = false;
+                        }
+                        // (fast division: alpha <= 0.99 keeps the divisor in [0.01, 1])
+                        const float Tk = __fdividef(T[p], 1.f - alpha);
+                        const float gc = gr[p] * q1.z + gg[p] * q1.w + gb[p] * q2.x;
+                        const float dalpha = Tk * (gc - U[p]);
+                        const float w = Tk * alpha;
+                        v[6] += w * gr[p]; v[7] += w * gg[p]; v[8] += w * gb[p];
+                        U[p] = alpha * gc + (1.f - alpha) * U[p];
+                        T[p] = Tk;
+                        if (ag <= kAlphaMax) {
+                            const float dpow = dalpha * alpha;
+                            float ca, cb, cc;
+                            factor_conic(q0.z, q0.w, q1.x, ca, cb, cc);
+                            const float A = -2.f * kLn2 * ca, B = -kLn2 * cb, C = -2.f * kLn2 * cc;
+                            v[0] += dpow * (A * dx + B * dy);
+                            v[1] += dpow * (B * dx + C * dy);
+                            v[2] += -0.5f * dpow * dx * dx;
+                            v[3] += -dpow * dx * dy;
+                            v[4] += -0.5f * dpow * dy * dy;
+                            v[5] += dalpha * Gv;
+                        }
+                    }
+                }
+                if (__any_sync(0xffffffffu, any)) {
+                    warp_sum_transpose<16>(v, lane);
+                    if ((lane & 1) == 0 && lane < 18 && v[0] != 0.f) atomicAdd(&s_acc[k][lane >> 1], v[0]);
+                }
+            } else {
+                // ---- triangle fragment
+                const TRec& t = *reinterpret_cast<const TRec*>(&s_rec[k][0]);
+                float v[32];
+#pragma unroll
+                for (int e = 0; e < 32; ++e) v[e] = 0.f;
+                bool any = false;
+#pragma unroll
+                for (int p = 0; p < 2; ++p) {
+                    int mask = 0;
+                    if (inside[p] && pos < nlast[p]) {
+                        long long E[3];
+#pragma unroll
+                        for (int e = 0; e < 3; ++e)
+                            E[e] = (long long)t.A[e] * scx + (long long)t.B[e] * scy[p] + t.C[e];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const int sdx = sample_dx(j), sdy = sample_dy(j);
+                            bool in = true;
+#pragma unroll
+                            for (int e = 0; e < 3; ++e)
+                                in = in && (E[e] + (long long)(t.A[e] * sdx + t.B[e] * sdy) >= 0);
+                            mask |= in ? (1 << j) : 0;
+                        }
+                    }
+                    if (mask == 0) continue;
+                    any = true;
+                    const float qyp = qy[p];
+                    if (!in_ent[p]) { Uj[p][0] = Uj[p][1] = Uj[p][2] = Uj[p][3] = U[p]; in_ent[p] = true; }
+                    // replayed coverage equals the forward's, so sp > 0 here; the
+                    // guard keeps a mismatch from reading outside the stack
+                    float4 s4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (sp[p] > 0) { --sp[p]; s4 = stack[(int64_t)sp[p] * npix + pix[p]]; }
+                    const float s[4] = {s4.x, s4.y, s4.z, s4.w};
+                    // attributes, as in the forward
+                    float e3[3];
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) {
+                        const int a = (m + 1) % 3, b = (m + 2) % 3;
+                        e3[m] = (t.u[a] - qx) * (t.v[b] - qyp) - (t.u[b] - qx) * (t.v[a] - qyp);
+                    }
+                    const float area = e3[0] + e3[1] + e3[2];
+                    float lam[3], lh[3], wv[3];
+                    const float ia = area != 0.f ? 1.f / area : 0.f;
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) {
+                        lam[m] = area != 0.f ? e3[m] * ia : (1.f / 3.f);
+                        lh[m] = fmaxf(lam[m], 0.f);
+                        wv[m] = lh[m] * t.iz[m];
+                    }
+                    const float ws = wv[0] + wv[1] + wv[2];
+                    float w[3];
+                    if (ws > 0.f) { const float is = 1.f / ws; w[0] = wv[0] * is; w[1] = wv[1] * is; w[2] = wv[2] * is; }
+                    else { w[0] = w[1] = w[2] = 1.f / 3.f; }
+                    float col[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) col[c] = w[0] * t.col[c] + w[1] * t.col[3 + c] + w[2] * t.col[6 + c];
+                    const float araw = t.const_alpha ? t.alpha[0] : (w[0] * t.alpha[0] + w[1] * t.alpha[1] + w[2] * t.alpha[2]);
+                    const float alpha = fminf(fmaxf(araw, 0.f), 1.f);
+                    const float gc = gr[p] * col[0] + gg[p] * col[1] + gb[p] * col[2];
+                    float dalpha = 0.f, wsum = 0.f;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        if ((mask >> j) & 1) {
+                            dalpha += s[j] * (gc - Uj[p][j]);
+                            wsum += s[j] * alpha;
+                            Uj[p][j] = alpha * gc + (1.f - alpha) * Uj[p][j];
+                        }
+                    }
+                    T[p] = (s[0] + s[1]) + (s[2] + s[3]);
+                    const float dc[3] = {wsum * gr[p], wsum * gg[p], wsum * gb[p]};
+                    const float dar = (araw >= 0.f && araw <= 1.f) ? dalpha : 0.f;
+                    // colour and alpha to vertices / weights
+                    float dw[3];
+#pragma unroll
+                    for (int m = 0; m < 3; ++m) {
+                        v[9 + 3 * m] += w[m] * dc[0];
+                        v[10 + 3 * m] += w[m] * dc[1];
+                        v[11 + 3 * m] += w[m] * dc[2];
+                        dw[m] = t.col[3 * m] * dc[0] + t.col[3 * m + 1] * dc[1] + t.col[3 * m + 2] * dc[2];
+                    }
+                    if (t.const_alpha == 0) {
+#pragma unroll
+                        for (int m = 0; m < 3; ++m) { v[18 + m] += w[m] * dar; dw[m] += t.alpha[m] * dar; }
+                    } else if (t.const_alpha == 1) {
+                        v[18] += dar;
+                    }
+                    if (ws > 0.f) {
+                        const float sdw = w[0] * dw[0] + w[1] * dw[1] + w[2] * dw[2];
+                        const float is = 1.f / ws;
+                        float dlam[3];
+#pragma unroll
+                        for (int m = 0; m < 3; ++m) {
+                            const float dwh = (dw[m] - sdw) * is;
+                            const float diz = dwh * lh[m];
+                            v[6 + m] += -diz * t.iz[m] * t.iz[m];
+                            dlam[m] = (area != 0.f && lam[m] >= 0.f) ? dwh * t.iz[m] : 0.f;
+                        }
+                        if (area != 0.f) {
+                            const float sl = dlam[0] * e3[0] + dlam[1] * e3[1] + dlam[2] * e3[2];
+#pragma unroll
+                            for (int m = 0; m < 3; ++m) {
+                                const float de = dlam[m] * ia - sl * ia * ia;
+                                const int a = (m + 1) % 3, b = (m + 2) % 3;
+                                v[a] += de * (t.v[b] - qyp);
+                                v[3 + b] += de * (t.u[a] - qx);
+                                v[b] -= de * (t.v[a] - qyp);
+                                v[3 + a] -= de * (t.u[b] - qx);
+                            }
+                        }
+                    }
+                }
+                if (__any_sync(0xffffffffu, any)) {
+                    warp_sum_transpose<32>(v, lane);
+                    if (lane < 21 && v[0] != 0.f) atomicAdd(&s_acc[k][lane], v[0]);
+                }
+            }
+        }
+        __syncthreads();
+        // one global atomic per (record, component) of this tile's batch
+        for (int k = threadIdx.x; k < n; k += NT) {
+            const uint32_t id = s_id[k];
+            if (id < Ng) {
+                float* dst = ggrad + ((int64_t)cam * Ng + id) * 12;
+#pragma unroll
+                for (int e = 0; e < 9; ++e)
+                    if (s_acc[k][e] != 0.f) atomicAdd(dst + e, s_acc[k][e]);
+            } else if (id < Ng + Nt) {
                 float* dst = tgrad + ((int64_t)cam * Nt + (id - Ng)) * 24;
 #pragma unroll
                 for (int e = 0; e < 21; ++e)
@@ -730,10 +1049,19 @@ umgs_status render_backward(umgs_ctx* ctx, umgs_frame* fr, const umgs_gaussians*
             fr->tiles_x, tpc, fr->W, fr->H, fr->bg[0], fr->bg[1], fr->bg[2], dout, fr->last.as<int32_t>(),         \
             fr->tfin.as<float>(), fr->ntri.as<int32_t>(), fr->stack.as<float4>(), npix, fr->ggrad.as<float>(),     \
             fr->tgrad.as<float>())
+#define UMGS_LAUNCH2(TSV)                                                                                       \
+        UMGS_TRY(cudaFuncSetAttribute(composite_bwd2_kernel<TSV>, cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                                      Bwd2<TSV>::SMEM));                                                          \
+        launch_pdl(composite_bwd2_kernel<TSV>, M, Bwd2<TSV>::NT, Bwd2<TSV>::SMEM, stream,                           \
+            fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->trec.as<TRec>(), Ng, Nt,               \
+            fr->tiles_x, tpc, fr->W, fr->H, fr->bg[0], fr->bg[1], fr->bg[2], dout, fr->last.as<int32_t>(),         \
+            fr->tfin.as<float>(), fr->ntri.as<int32_t>(), fr->stack.as<float4>(), npix, fr->ggrad.as<float>(),     \
+            fr->tgrad.as<float>())
         const bool soft = (fr->opts.flags & UMGS_RENDER_SOFT_EDGE) != 0;
-        if (fr->tile == 16) { if (soft) { UMGS_LAUNCH(16, true); } else { UMGS_LAUNCH(16, false); } }
-        else if (fr->tile == 8) { if (soft) { UMGS_LAUNCH(8, true); } else { UMGS_LAUNCH(8, false); } }
-        else { if (soft) { UMGS_LAUNCH(32, true); } else { UMGS_LAUNCH(32, false); } }
+        if (fr->tile == 16) { if (soft) { UMGS_LAUNCH(16, true); } else { UMGS_LAUNCH2(16); } }
+        else if (fr->tile == 8) { if (soft) { UMGS_LAUNCH(8, true); } else { UMGS_LAUNCH2(8); } }
+        else { if (soft) { UMGS_LAUNCH(32, true); } else { UMGS_LAUNCH2(32); } }
+#undef UMGS_LAUNCH2
 #undef UMGS_LAUNCH
         UMGS_TRY(cudaGetLastError());
     }

@@ -35,9 +35,9 @@ struct DevCam {
 };
 
 // Projected Gaussian record: 48 bytes, three 16-byte vectors.
-//  q0 = (u, v, ca, cb), q1 = (cc, opacity, r, g), q2 = (b, rect_x, rect_y, Z)
+//  q0 = (u, v, l0, l1), q1 = (l2, opacity, r, g), q2 = (b, rect_x, rect_y, Z)
 //  (Z: camera depth of the mean, for the expected-depth output)
-//  power2 = ca*dx^2 + cb*dx*dy + cc*dy^2 is the exponent in base 2:
+//  (l0, l1, l2): the conic's factor of gauss_power2, the exponent in base 2:
 //  alpha = min(0.99, opacity * exp2(power2)); rect_x = x_lo | x_hi << 16.
 struct __align__(16) GRec {
     float4 q0, q1, q2;
@@ -46,7 +46,7 @@ struct __align__(16) GRec {
 // Mixed-precision Gaussian record: 32 bytes, two 16-byte vectors.  The
 // screen position stays fp32 (fp16 loses sub-pixel precision above 2048 px);
 // conic, opacity and colour are fp16; the rect is exact.
-//  v0 = (u, v, half2(ca, cb), half2(cc, opacity)), v1 = (half2(r, g), half2(b, 0), rect_x, rect_y)
+//  v0 = (u, v, half2(l0, l1), half2(l2, opacity)), v1 = (half2(r, g), half2(b, 0), rect_x, rect_y)
 struct __align__(16) GRec16 {
     uint4 v0, v1;
 };
@@ -141,12 +141,29 @@ __device__ __forceinline__ float fast_exp2(float x) {
     return y;
 }
 
-// Gaussian alpha at offset (dx, dy) from the projected mean, with a fixed
-// operation sequence so the forward and the backward replay agree bit for bit:
-// power2 = ca dx^2 + cb dx dy + cc dy^2 (base-2 exponent), alpha = o 2^power2.
-__device__ __forceinline__ float gauss_power2(float ca, float cb, float cc, float dx, float dy) {
-    return __fmaf_rn(cc, __fmul_rn(dy, dy), __fmaf_rn(cb, __fmul_rn(dx, dy), __fmul_rn(ca, __fmul_rn(dx, dx))));
+// Gaussian exponent (base 2) at offset (dx, dy) from the projected mean.
+// The record keeps the factor (l0, l1, l2) of the scaled conic: with
+// Sigma2D = [[a, b], [b, c]], det = a c - b^2, the conic Q = Sigma2D^-1 and
+// k = log2(e) / 2, k Q = L^T L for L = [[l0, l1], [0, l2]], l0 = sqrt(k c /
+// det), l1 = -k b / (det l0), l2 = sqrt(k / c).  Then power2 = -k d^T Q d =
+// -((l0 dx + l1 dy)^2 + (l2 dy)^2), a sum of two squares without the
+// cancellation that A dx^2 + 2 B dx dy + C dy^2 suffers along an elongated
+// footprint; alpha = o 2^power2.  A fixed operation sequence, so the forward
+// and the backward replay agree bit for bit.
+__device__ __forceinline__ float gauss_power2(float l0, float l1, float l2, float dx, float dy) {
+    const float w1 = __fmaf_rn(l1, dy, __fmul_rn(l0, dx));
+    const float w2 = __fmul_rn(l2, dy);
+    return -__fmaf_rn(w1, w1, __fmul_rn(w2, w2));
 }
+// the base-2 conic of a factor: power2 = ca dx^2 + cb dx dy + cc dy^2
+__device__ __forceinline__ void factor_conic(float l0, float l1, float l2, float& ca, float& cb, float& cc) {
+    ca = -l0 * l0;
+    cb = -2.f * l0 * l1;
+    cc = -(l1 * l1 + l2 * l2);
+}
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kHalfLog2e = 0.7213475204444817f;
 
 // A projected covariance [[a, b], [b, c]] with det < kConicFp64 * a * c is
 // near-singular: its conic is inverted in fp64 (the fp32 inverse would lose
@@ -156,7 +173,6 @@ constexpr float kConicFp64 = 1.0f / 128.0f;
 
 constexpr float kAlphaMin = 1.0f / 255.0f;
 constexpr float kAlphaMax = 0.99f;
-constexpr float kLog2e = 1.4426950408889634f;
 
 // ---- warp <-> pixel layout of the compositors -------------------------------
 // Warp w of a TS x TS tile (TS = 8, 16, 32) owns the 8 x 4 pixel block
@@ -188,8 +204,8 @@ __device__ __forceinline__ uint32_t box_block_mask(int x0, int x1, int y0, int y
 
 // Blocks of 8 x BH pixels (as box_block_mask) of the tile with origin (tx0, ty0)
 // whose pixels can hold a fragment of a Gaussian record with projected mean
-// (u, v), base-2 conic (ca, cb, cc) (alpha = o 2^p2, p2 = ca dx^2 + cb dx dy +
-// cc dy^2), opacity o and pixel rect [x0,x1] x [y0,y1].  A fragment needs
+// (u, v), conic factor (l0, l1, l2) (gauss_power2; base-2 conic ca dx^2 +
+// cb dx dy + cc dy^2), opacity o and pixel rect [x0,x1] x [y0,y1].  A fragment needs
 // the pixel in the rect and alpha >= 1/255, i.e. d = (dx, dy) inside the
 // ellipse d^T Q d <= lim with Q = -[[ca, cb/2], [cb/2, cc]], lim =
 // log2(255 o).  The ellipse lies inside the octagon bounded by its support
@@ -199,10 +215,12 @@ __device__ __forceinline__ uint32_t box_block_mask(int x0, int x1, int y0, int y
 // test and of the compositor's own alpha.  o < 1/255: no fragment; a conic
 // that is not positive definite keeps every block of the rect.
 template <int TS, int BH = 4>
-__device__ __forceinline__ uint32_t gauss_block_mask(float u, float v, float ca, float cb, float cc, float o, int x0,
+__device__ __forceinline__ uint32_t gauss_block_mask(float u, float v, float l0, float l1, float l2, float o, int x0,
                                                      int x1, int y0, int y1, int tx0, int ty0) {
     constexpr int LB = BH == 4 ? 2 : 3;
     if (!(o >= kAlphaMin)) return 0u;
+    float ca, cb, cc;
+    factor_conic(l0, l1, l2, ca, cb, cc);
     const float qa = -ca, qb = -0.5f * cb, qc = -cc, det = qa * qc - qb * qb;
     if (!(qa > 0.f && qc > 0.f && det > 0.f)) return box_block_mask<TS, BH>(x0, x1, y0, y1, tx0, ty0);
     const float s = (__log2f(255.f * o) * 1.02f + 1e-4f) / det;  // lim Q^-1 = s [[qc, -qb], [-qb, qa]]

@@ -360,7 +360,8 @@ __device__ __forceinline__ void blend_gaussian(PixelState& st, float al, float r
 
 template <int TS, bool SAVE, int MODE>
 __device__ __forceinline__ void composite_tile(
-    int tile, CompositeSmem<TS>& sm,
+    int tile, int64_t seg_beg, int64_t seg_end, float4* __restrict__ seg_out, int32_t* __restrict__ seg_last,
+    CompositeSmem<TS>& sm,
     const uint32_t* __restrict__ ids, const int64_t* __restrict__ off,
     const GRec* __restrict__ grec,
     const GRec16* __restrict__ grec16, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
@@ -377,7 +378,9 @@ __device__ __forceinline__ void composite_tile(
     const int ly0 = (warp / (TS / 8)) * 8 + (lane >> 3), ly1 = ly0 + 4;
     const int tile_x0 = tx * TS, tile_y0 = ty * TS;
     const int px = tile_x0 + lx, py0 = tile_y0 + ly0, py1 = tile_y0 + ly1;
-    const int64_t beg = off[tile], end = off[tile + 1];
+    // the tile's list, or one segment [seg_beg, seg_end) of it (list
+    // positions stay relative to the start of the tile's list)
+    const int64_t beg = off[tile], end = seg_end >= 0 ? seg_end : off[tile + 1];
     const GRec* G = grec + (int64_t)cam * Ng;
     const GRec16* G16 = grec16 ? grec16 + (int64_t)cam * Ng : nullptr;
     const TRec* TR = trec + (int64_t)cam * Nt;
@@ -398,7 +401,7 @@ __device__ __forceinline__ void composite_tile(
     st[1].done = !(px < W && py1 < H);
     const int64_t pix0 = ((int64_t)cam * H + py0) * W + px, pix1 = ((int64_t)cam * H + py1) * W + px;
 
-    for (int64_t b0 = beg; b0 < end;) {
+    for (int64_t b0 = seg_beg >= 0 ? seg_beg : beg; b0 < end;) {
         int n = (int)min((int64_t)NB, end - b0);
         uint32_t rid[RPT];
 #pragma unroll
@@ -505,11 +508,13 @@ __device__ __forceinline__ void composite_tile(
                     if (!(in0 || in1)) continue;
                     const float4 q0 = sm.g[k][0], q1 = sm.g[k][1];
                     const float dx = __fsub_rn(qx, q0.x);
-                    const float cdx2 = __fmul_rn(q0.z, __fmul_rn(dx, dx));  // ca dx^2, shared by both pixels
+                    const float l0dx = __fmul_rn(q0.z, dx);  // l0 dx, shared by both pixels
                     const float dy0 = __fsub_rn(qy0, q0.y), dy1 = __fsub_rn(qy1, q0.y);
                     // (the operation order of gauss_power2)
-                    const float p0 = __fmaf_rn(q1.x, __fmul_rn(dy0, dy0), __fmaf_rn(q0.w, __fmul_rn(dx, dy0), cdx2));
-                    const float p1 = __fmaf_rn(q1.x, __fmul_rn(dy1, dy1), __fmaf_rn(q0.w, __fmul_rn(dx, dy1), cdx2));
+                    const float w10 = __fmaf_rn(q0.w, dy0, l0dx), w20 = __fmul_rn(q1.x, dy0);
+                    const float w11 = __fmaf_rn(q0.w, dy1, l0dx), w21 = __fmul_rn(q1.x, dy1);
+                    const float p0 = -__fmaf_rn(w10, w10, __fmul_rn(w20, w20));
+                    const float p1 = -__fmaf_rn(w11, w11, __fmul_rn(w21, w21));
                     const float a0 = fminf(kAlphaMax, __fmul_rn(q1.y, fast_exp2(p0)));
                     const float a1 = fminf(kAlphaMax, __fmul_rn(q1.y, fast_exp2(p1)));
                     const bool t0 = in0 && a0 >= kAlphaMin, t1 = in1 && a1 >= kAlphaMin;
@@ -540,6 +545,12 @@ __device__ __forceinline__ void composite_tile(
         if (!(px < W && py < H)) continue;
         const int64_t pix = p ? pix1 : pix0;
         const PixelState& s = st[p];
+        if (seg_out) {  // one segment of a split tile: its own composite, no background (split_merge_kernel)
+            const int q = (p ? ly1 : ly0) * TS + lx;
+            seg_out[q] = make_float4(s.C[0], s.C[1], s.C[2], s.T);
+            seg_last[q] = s.last;
+            continue;
+        }
         out[pix] = make_float4(s.C[0] + s.T * bg0, s.C[1] + s.T * bg1, s.C[2] + s.T * bg2, s.T);
         // bit 31: the pixel stopped at T < t_eps after list position `last`
         if (out_last) out_last[pix] = s.last | (s.T < t_eps ? (int)0x80000000u : 0);
@@ -563,7 +574,7 @@ __global__ void __launch_bounds__(Layout<TS>::NT, MinBlocks<TS>::value) composit
     int64_t npix, int32_t* __restrict__ need, float* __restrict__ out_depth, const DevTex* __restrict__ textab) {
     pdl_enter();
     __shared__ CompositeSmem<TS> sm;
-    composite_tile<TS, SAVE, MODE>(blockIdx.x, sm, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, out, out_last, out_tfin, out_ntri, stack, cap, npix, need, out_depth, textab);
+    composite_tile<TS, SAVE, MODE>(blockIdx.x, -1, -1, nullptr, nullptr, sm, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, out, out_last, out_tfin, out_ntri, stack, cap, npix, need, out_depth, textab);
 }
 
 // persistent launch: resident CTAs take tiles from an atomic queue in the
@@ -585,8 +596,181 @@ __global__ void __launch_bounds__(Layout<TS>::NT, MinBlocks<TS>::value) composit
         const unsigned k = s_next;
         __syncthreads();
         if ((int64_t)k >= M) break;
-        composite_tile<TS, SAVE, MODE>((int)order[k], sm, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, out, out_last, out_tfin, out_ntri, stack, cap, npix, need, out_depth, textab);
+        composite_tile<TS, SAVE, MODE>((int)order[k], -1, -1, nullptr, nullptr, sm, ids, off, grec, grec16, trec, Ng, Nt, tiles_x, tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, out, out_last, out_tfin, out_ntri, stack, cap, npix, need, out_depth, textab);
         __syncthreads();
+    }
+}
+
+// ---- per-tile work split -----------------------------------------------------
+// A tile whose list holds more than `split` records is composited as segments
+// of `split` records on separate CTAs, each from T = 1, and the segments are
+// merged per pixel front to back: C = sum_k (prod_{m<k} T_m) C_k, T = prod_k
+// T_k (the composite of Eq. 1-2 regrouped; fp rounding differs from the whole
+// tile).  Cuts are placed only in front of the list's first triangle record:
+// an entity of depth-adjacent triangles (Eq. 7-9) would carry per-pixel
+// state across a cut, and no entity can be open before a tile's first
+// triangle.  A segment stops at its own T < t_eps, so it may blend a few
+// fragments that the whole tile, already below t_eps, would drop: at most
+// t_eps times the largest colour.
+//
+// Work item: int4 (tile, list begin, list end, meta), meta = slot | seg << 16 |
+// nseg << 24; nseg = 1 is a whole tile (composited into the image).
+constexpr int kMaxSegs = 64;
+
+// one warp per tile: its segments, segment slots and work items
+__global__ void split_plan_kernel(const int64_t* __restrict__ off, const uint32_t* __restrict__ ids, int64_t M,
+                                  uint32_t ng, int split, int4* __restrict__ items, unsigned* __restrict__ nitems,
+                                  unsigned* __restrict__ nslots, unsigned slots_cap) {
+    pdl_enter();
+    const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= M) return;  // (whole warps: M and the block size are warp-aligned per tile)
+    const int64_t beg = off[t], end = off[t + 1], len = end - beg;
+    int nseg = 1;
+    if (len > split) {
+        const int64_t lim = min(len, (int64_t)split * kMaxSegs);
+        int64_t ftri = lim;  // position of the first triangle record (or the scan limit)
+        for (int64_t c = 0; c < lim; c += 32) {
+            const bool tri = c + lane < lim && ids[beg + c + lane] >= ng;
+            const unsigned b = __ballot_sync(0xffffffffu, tri);
+            if (b) { ftri = c + __ffs(b) - 1; break; }
+        }
+        // cuts at split, 2 split, ... that are <= ftri and < len
+        nseg = 1 + (int)min(ftri / split, (len - 1) / split);
+        nseg = min(nseg, kMaxSegs);
+    }
+    if (lane != 0) return;
+    unsigned slot = 0;
+    if (nseg > 1) {
+        slot = atomicAdd(nslots, (unsigned)nseg);
+        if (slot + nseg > slots_cap) nseg = 1;  // no room left: the tile is composited whole
+    }
+    const unsigned base = atomicAdd(nitems, (unsigned)nseg);  // < M + slots_cap: the items buffer's size
+    for (int sg = 0; sg < nseg; ++sg) {
+        const int64_t sb = beg + (int64_t)sg * split, se = sg == nseg - 1 ? end : sb + split;
+        items[base + sg] = make_int4((int)t, (int)(uint32_t)sb, (int)(uint32_t)se,
+                                     (int)(slot | ((unsigned)sg << 16) | ((unsigned)nseg << 24)));
+    }
+}
+
+// order of the work items for the persistent launch (decreasing length)
+__global__ void item_order_keys_kernel(const int4* __restrict__ items, const unsigned* __restrict__ nitems,
+                                       int64_t cap, uint32_t* __restrict__ k, uint32_t* __restrict__ v) {
+    pdl_enter();
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= cap || i >= (int64_t)*nitems) return;
+    const int4 it = items[i];
+    const uint32_t len = (uint32_t)it.z - (uint32_t)it.y;
+    k[i] = 0xffffu - min(len, 0xffffu);
+    v[i] = (uint32_t)i;
+}
+
+// work item -> composite_tile arguments
+template <int TS>
+__device__ __forceinline__ void item_target(const int4 it, float4* segbuf, int32_t* seglast, int64_t& sb, int64_t& se,
+                                            float4*& so, int32_t*& sl) {
+    const unsigned meta = (unsigned)it.w;
+    const unsigned nseg = meta >> 24;
+    sb = (int64_t)(uint32_t)it.y;
+    se = (int64_t)(uint32_t)it.z;
+    if (nseg > 1) {
+        const int64_t q = (int64_t)((meta & 0xffffu) + ((meta >> 16) & 0xffu)) * TS * TS;
+        so = segbuf + q;
+        sl = seglast + q;
+    } else {
+        so = nullptr;
+        sl = nullptr;
+    }
+}
+
+// one CTA per work item (grid sized for the item capacity)
+template <int TS, int MODE>
+__global__ void __launch_bounds__(Layout<TS>::NT, MinBlocks<TS>::value) composite_items_kernel(
+    const int4* __restrict__ items, const unsigned* __restrict__ nitems, float4* __restrict__ segbuf,
+    int32_t* __restrict__ seglast,
+    const uint32_t* __restrict__ ids, const int64_t* __restrict__ off, const GRec* __restrict__ grec,
+    const GRec16* __restrict__ grec16, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
+    int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, float4* __restrict__ out,
+    int32_t* __restrict__ out_last, const DevTex* __restrict__ textab) {
+    pdl_enter();
+    if (blockIdx.x >= *nitems) return;
+    __shared__ CompositeSmem<TS> sm;
+    const int4 it = items[blockIdx.x];
+    int64_t sb, se;
+    float4* so;
+    int32_t* sl;
+    item_target<TS>(it, segbuf, seglast, sb, se, so, sl);
+    composite_tile<TS, false, MODE>(it.x, sb, se, so, sl, sm, ids, off, grec, grec16, trec, Ng, Nt, tiles_x,
+                                    tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, out, out_last, nullptr, nullptr,
+                                    nullptr, 0, 0, nullptr, nullptr, textab);
+}
+
+// persistent launch over the work items in the order `order`
+template <int TS, int MODE>
+__global__ void __launch_bounds__(Layout<TS>::NT, MinBlocks<TS>::value) composite_items_persistent_kernel(
+    const uint32_t* __restrict__ order, unsigned* __restrict__ work, const int4* __restrict__ items,
+    const unsigned* __restrict__ nitems, float4* __restrict__ segbuf, int32_t* __restrict__ seglast,
+    const uint32_t* __restrict__ ids, const int64_t* __restrict__ off, const GRec* __restrict__ grec,
+    const GRec16* __restrict__ grec16, const TRec* __restrict__ trec, int64_t Ng, int64_t Nt, int tiles_x,
+    int tiles_per_cam, int W, int H, float t_eps, float bg0, float bg1, float bg2, float4* __restrict__ out,
+    int32_t* __restrict__ out_last, const DevTex* __restrict__ textab) {
+    pdl_enter();
+    __shared__ CompositeSmem<TS> sm;
+    __shared__ unsigned s_next;
+    const unsigned n = *nitems;
+    while (true) {
+        if (threadIdx.x == 0) s_next = atomicAdd(work, 1u);
+        __syncthreads();
+        const unsigned k = s_next;
+        __syncthreads();
+        if (k >= n) break;
+        const int4 it = items[order[k]];
+        int64_t sb, se;
+        float4* so;
+        int32_t* sl;
+        item_target<TS>(it, segbuf, seglast, sb, se, so, sl);
+        composite_tile<TS, false, MODE>(it.x, sb, se, so, sl, sm, ids, off, grec, grec16, trec, Ng, Nt, tiles_x,
+                                        tiles_per_cam, W, H, t_eps, bg0, bg1, bg2, out, out_last, nullptr, nullptr,
+                                        nullptr, 0, 0, nullptr, nullptr, textab);
+        __syncthreads();
+    }
+}
+
+// merge of the segments of every split tile (one CTA per work item; the
+// tile's first segment does the work)
+template <int TS>
+__global__ void __launch_bounds__(256) split_merge_kernel(
+    const int4* __restrict__ items, const unsigned* __restrict__ nitems, const float4* __restrict__ segbuf,
+    const int32_t* __restrict__ seglast, int tiles_x, int tiles_per_cam, int W, int H, float t_eps, float bg0,
+    float bg1, float bg2, float4* __restrict__ out, int32_t* __restrict__ out_last) {
+    pdl_enter();
+    if (blockIdx.x >= *nitems) return;
+    const int4 it = items[blockIdx.x];
+    const unsigned meta = (unsigned)it.w;
+    const int nseg = (int)(meta >> 24), sg = (int)((meta >> 16) & 0xffu);
+    if (nseg < 2 || sg != 0) return;
+    const unsigned slot = meta & 0xffffu;
+    const int tile = it.x;
+    const int cam = tile / tiles_per_cam;
+    const int lt = tile - cam * tiles_per_cam;
+    const int ty = lt / tiles_x, tx = lt - ty * tiles_x;
+    for (int q = threadIdx.x; q < TS * TS; q += blockDim.x) {
+        const int px = tx * TS + q % TS, py = ty * TS + q / TS;
+        if (px >= W || py >= H) continue;
+        float C0 = 0.f, C1 = 0.f, C2 = 0.f, T = 1.f;
+        int last = 0;
+        for (int k = 0; k < nseg; ++k) {
+            if (T < t_eps) break;  // the whole tile would have stopped before this segment
+            const int64_t i = (int64_t)(slot + k) * TS * TS + q;
+            const float4 r = segbuf[i];
+            C0 += T * r.x; C1 += T * r.y; C2 += T * r.z;
+            T *= r.w;
+            const int l = seglast[i];
+            if (l > 0) last = l;
+        }
+        const int64_t pix = ((int64_t)cam * H + py) * W + px;
+        out[pix] = make_float4(C0 + T * bg0, C1 + T * bg1, C2 + T * bg2, T);
+        if (out_last) out_last[pix] = last | (T < t_eps ? (int)0x80000000u : 0);
     }
 }
 
@@ -603,6 +787,88 @@ __global__ void tile_order_keys_kernel(const int64_t* __restrict__ off, int64_t 
 }
 
 
+// capacities of a split render with `kcap` tile-list entries: segment slots
+// (two or more per split tile, each split tile holds more than `split`
+// entries), at most 65,535 and 512 MB of segment buffers; work items
+static void split_caps(const umgs_frame* fr, int split, int64_t kcap, int64_t* slots_cap, int64_t* items_cap) {
+    const int64_t px = (int64_t)fr->tile * fr->tile;
+    *slots_cap = std::max<int64_t>(1, std::min<int64_t>({65535, 2 * kcap / split + 1, (512LL << 20) / (px * 20)}));
+    *items_cap = fr->num_tiles + *slots_cap;
+}
+
+cudaError_t reserve_split(umgs_frame* fr, int split, int64_t kcap) {
+    int64_t slots_cap, items_cap;
+    split_caps(fr, split, kcap, &slots_cap, &items_cap);
+    const int64_t px = (int64_t)fr->tile * fr->tile;
+    cudaError_t e;
+    if ((e = fr->split_items.reserve(sizeof(int4) * items_cap)) != cudaSuccess) return e;
+    if ((e = fr->segbuf.reserve(sizeof(float4) * slots_cap * px)) != cudaSuccess) return e;
+    if ((e = fr->seglast.reserve(sizeof(int32_t) * slots_cap * px)) != cudaSuccess) return e;
+    for (DevBuf* b : {&fr->ord_k, &fr->ord_v, &fr->ord_k2, &fr->ord_v2})
+        if ((e = b->reserve(sizeof(uint32_t) * items_cap)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+// a render with the per-tile work split (FULL / DIRECT / MSAA_ALL /
+// ENTITY_ALL / T_PRODUCT; no saved state, no depth)
+static cudaError_t launch_split_composite(umgs_frame* fr, const umgs_render_opts& opts, float4* out, float te,
+                                          int mode, cudaStream_t stream) {
+    const int split = opts.split;
+    const int64_t kcap = fr->nosync ? fr->key_capacity : fr->num_keys;
+    int64_t slots_cap, items_cap;
+    split_caps(fr, split, kcap, &slots_cap, &items_cap);
+    cudaError_t e;
+    if (!fr->capture && (e = reserve_split(fr, split, kcap)) != cudaSuccess) return e;
+    const int64_t M = fr->num_tiles;
+    const int tpc = fr->tiles_x * fr->tiles_y;
+    unsigned* nitems = reinterpret_cast<unsigned*>(fr->status.as<int32_t>() + kStatusSplitWords);
+    unsigned* nslots = nitems + 1;
+    unsigned* work = nitems + 2;
+    int4* items = fr->split_items.as<int4>();
+    launch_pdl(split_plan_kernel, (unsigned)((M * 32 + 255) / 256), 256, 0, stream, fr->tile_off.as<int64_t>(),
+               fr->ids, M, (uint32_t)fr->ng, split, items, nitems, nslots, (unsigned)slots_cap);
+    const bool persist = opts.sched > 0;
+    const uint32_t* order = nullptr;
+    if (persist) {
+        launch_pdl(item_order_keys_kernel, (unsigned)((items_cap + 255) / 256), 256, 0, stream, items, nitems,
+                   items_cap, fr->ord_k.as<uint32_t>(), fr->ord_v.as<uint32_t>());
+        uint32_t* rk = nullptr;
+        uint32_t* rv = nullptr;
+        if ((e = radix_sort_pairs(fr, fr->ord_k.as<uint32_t>(), fr->ord_v.as<uint32_t>(), fr->ord_k2.as<uint32_t>(),
+                                  fr->ord_v2.as<uint32_t>(), nitems, items_cap, 16, &rk, &rv, stream)) != cudaSuccess)
+            return e;
+        order = rv;
+    }
+    const int nblk = opts.sched * fr->ctx->num_sms;
+    float4* sb = fr->segbuf.as<float4>();
+    int32_t* sl = fr->seglast.as<int32_t>();
+#define UMGS_SPLIT(TSV, MV)                                                                                     \
+    if (persist) launch_pdl(composite_items_persistent_kernel<TSV, MV>, nblk, Layout<TSV>::NT, 0, stream, order, work, \
+        items, nitems, sb, sl, fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(),                          \
+        fr->mixed ? fr->grec.as<GRec16>() : nullptr, fr->trec.as<TRec>(), fr->ng, fr->nt, fr->tiles_x, tpc,      \
+        fr->W, fr->H, te, opts.bg[0], opts.bg[1], opts.bg[2], out, fr->last.as<int32_t>(),                       \
+        fr->textab.as<DevTex>());                                                                               \
+    else launch_pdl(composite_items_kernel<TSV, MV>, (unsigned)items_cap, Layout<TSV>::NT, 0, stream, items, nitems,  \
+        sb, sl, fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(),                                       \
+        fr->mixed ? fr->grec.as<GRec16>() : nullptr, fr->trec.as<TRec>(), fr->ng, fr->nt, fr->tiles_x, tpc,      \
+        fr->W, fr->H, te, opts.bg[0], opts.bg[1], opts.bg[2], out, fr->last.as<int32_t>(),                       \
+        fr->textab.as<DevTex>());                                                                               \
+    launch_pdl(split_merge_kernel<TSV>, (unsigned)items_cap, 256, 0, stream, items, nitems, sb, sl, fr->tiles_x,  \
+               tpc, fr->W, fr->H, te, opts.bg[0], opts.bg[1], opts.bg[2], out, fr->last.as<int32_t>())
+#define UMGS_SPLIT_MODES(TSV)                                                                                   \
+    if (mode == kModeTProduct) { UMGS_SPLIT(TSV, kModeTProduct); }                                             \
+    else if (mode == UMGS_BLEND_DIRECT) { UMGS_SPLIT(TSV, UMGS_BLEND_DIRECT); }                                \
+    else if (mode == UMGS_BLEND_MSAA_ALL) { UMGS_SPLIT(TSV, UMGS_BLEND_MSAA_ALL); }                            \
+    else if (mode == UMGS_BLEND_ENTITY_ALL) { UMGS_SPLIT(TSV, UMGS_BLEND_ENTITY_ALL); }                        \
+    else { UMGS_SPLIT(TSV, UMGS_BLEND_FULL); }
+    if (fr->tile == 16) { UMGS_SPLIT_MODES(16) }
+    else if (fr->tile == 8) { UMGS_SPLIT_MODES(8) }
+    else { UMGS_SPLIT_MODES(32) }
+#undef UMGS_SPLIT_MODES
+#undef UMGS_SPLIT
+    return cudaGetLastError();
+}
+
 cudaError_t launch_composite(umgs_frame* fr, const umgs_render_opts& opts, float* out_rgbt, cudaStream_t stream) {
     const float te = opts.t_eps > 0.f ? opts.t_eps : -1.f;
     float4* out = reinterpret_cast<float4*>(out_rgbt);
@@ -611,6 +877,11 @@ cudaError_t launch_composite(umgs_frame* fr, const umgs_render_opts& opts, float
     const int tpc = fr->tiles_x * fr->tiles_y;
     const int64_t npix = (int64_t)fr->ncams * fr->W * fr->H;
     const bool save = fr->saved;
+    if (opts.split > 0 && !save && !fr->has_depth) {
+        const int mode = (opts.blend_mode == UMGS_BLEND_FULL && (opts.flags & UMGS_RENDER_T_PRODUCT)) ? kModeTProduct
+                                                                                                   : opts.blend_mode;
+        return launch_split_composite(fr, opts, out, te, mode, stream);
+    }
     if (save) cudaMemsetAsync(fr->status.as<int32_t>() + 2, 0, sizeof(int32_t), stream);
     const bool persist = opts.sched > 0;
     const uint32_t* order = nullptr;

@@ -74,6 +74,38 @@ __device__ bool inv3_fp64(const float Mf[9], float I[9]) {
     return true;
 }
 
+// Deformation gradient D = F' F^-1 of a sliver face entirely in fp64: the
+// frames' cross products (|e1 x e2| is a small difference of large products
+// for a sliver) and the inverse; the fp32 vertex positions are exact in fp64.
+__device__ bool sliver_gradient_fp64(const float P[3][3], const float Q[3][3], float D[9]) {
+    double Fr[9], Fd[9];
+    for (int w = 0; w < 2; ++w) {
+        const float (*X)[3] = w ? Q : P;
+        double* F = w ? Fd : Fr;
+        double e1[3], e2[3], n[3];
+        for (int d = 0; d < 3; ++d) { e1[d] = (double)X[1][d] - X[0][d]; e2[d] = (double)X[2][d] - X[0][d]; }
+        n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+        const double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        if (!(nn > 0.0)) return false;
+        const double sc = 1.0 / sqrt(nn);
+        for (int r = 0; r < 3; ++r) { F[3 * r] = e1[r]; F[3 * r + 1] = e2[r]; F[3 * r + 2] = n[r] * sc; }
+    }
+    const double* M = Fr;
+    const double c00 = M[4] * M[8] - M[5] * M[7], c01 = M[5] * M[6] - M[3] * M[8], c02 = M[3] * M[7] - M[4] * M[6];
+    const double det = M[0] * c00 + M[1] * c01 + M[2] * c02;
+    if (!(fabs(det) > 0.0)) return false;
+    const double id = 1.0 / det;
+    const double I[9] = {c00 * id, (M[2] * M[7] - M[1] * M[8]) * id, (M[1] * M[5] - M[2] * M[4]) * id,
+                         c01 * id, (M[0] * M[8] - M[2] * M[6]) * id, (M[2] * M[3] - M[0] * M[5]) * id,
+                         c02 * id, (M[1] * M[6] - M[0] * M[7]) * id, (M[0] * M[4] - M[1] * M[3]) * id};
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            D[3 * i + j] = (float)(Fd[3 * i] * I[j] + Fd[3 * i + 1] * I[3 + j] + Fd[3 * i + 2] * I[6 + j]);
+    return true;
+}
+
 __device__ __forceinline__ void matmul3(const float A[9], const float B[9], float C[9]) {
     for (int i = 0; i < 3; ++i)
         for (int j = 0; j < 3; ++j) C[3 * i + j] = A[3 * i] * B[j] + A[3 * i + 1] * B[3 + j] + A[3 * i + 2] * B[6 + j];
@@ -97,14 +129,18 @@ __global__ void __launch_bounds__(256) face_gradients_kernel(const float* __rest
     const float nn = face_frame(P[0], P[1], P[2], Fr);
     face_frame(Q[0], Q[1], Q[2], Fd);
     if (!(nn > 0.f)) return;  // degenerate rest face: zero weight
-    // sliver: |n| = |e1||e2| sin(angle); invert in fp64 when sin < 1e-3
+    // sliver: |n| = |e1||e2| sin(angle); its gradient (both frames and the
+    // inverse) in fp64 when sin < 1e-3
     const float l1 = sqrtf(Fr[0] * Fr[0] + Fr[3] * Fr[3] + Fr[6] * Fr[6]);
     const float l2 = sqrtf(Fr[1] * Fr[1] + Fr[4] * Fr[4] + Fr[7] * Fr[7]);
     const bool sliver = nn < 1e-3f * l1 * l2;
-    if (sliver) atomicAdd(status + 1, 1);  // fp64 sliver inverses of this deformation (umgs_deform_fp64_faces)
-    const bool ok = sliver ? inv3_fp64(Fr, Fi) : inv3(Fr, Fi);
-    if (!ok) return;
-    matmul3(Fd, Fi, D);
+    if (sliver) {
+        atomicAdd(status + 1, 1);  // fp64 sliver faces of this deformation (umgs_deform_fp64_faces)
+        if (!sliver_gradient_fp64(P, Q, D)) return;
+    } else {
+        if (!inv3(Fr, Fi)) return;
+        matmul3(Fd, Fi, D);
+    }
     const float area = 0.5f * nn;
     for (int k = 0; k < 3; ++k) {
         float* acc = vacc + 10 * (int64_t)idx[k];

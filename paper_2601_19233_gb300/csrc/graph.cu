@@ -64,6 +64,13 @@ umgs_status umgs_render_graph_create(umgs_ctx* ctx, umgs_frame* frame, const umg
     for (DevBuf* b : {&frame->ord_k, &frame->ord_v, &frame->ord_k2, &frame->ord_v2})
         if (b->reserve(sizeof(uint32_t) * std::max<int64_t>(1, M)) != cudaSuccess)
             return fail(ctx, UMGS_ERR_OUT_OF_MEMORY, "tile order");
+    if (so.split > 0) {
+        if (reserve_split(frame, so.split, Kcap) != cudaSuccess)
+            return fail(ctx, UMGS_ERR_OUT_OF_MEMORY, "work split buffers");
+        if (frame->rs_hist.reserve(sizeof(uint32_t) * 256 *
+                                   std::max(nbmax, radix_blocks(M + 2 * Kcap / so.split + 1))) != cudaSuccess)
+            return fail(ctx, UMGS_ERR_OUT_OF_MEMORY, "histograms");
+    }
     // 3) capture on a private stream
     umgs_graph* gr = new umgs_graph();
     gr->ctx = ctx;
@@ -138,15 +145,20 @@ umgs_status umgs_autotune(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_mes
     cudaEventCreate(&b);
     const int tiles[3] = {8, 16, 32};
     const int scheds[4] = {0, 1, 2, 4};
+    const int splits[4] = {0, 512, 1024, 2048};
     double best = 1e30;
     umgs_render_opts bo = *inout;
-    // the soft-edge compositor has the grid launch only
+    // the soft-edge compositor has the grid launch only; no split with
+    // soft edges or depth (the saved state is not kept while tuning)
     const int nsched = (inout->flags & UMGS_RENDER_SOFT_EDGE) ? 1 : 4;
+    const int nsplit = (inout->flags & (UMGS_RENDER_SOFT_EDGE | UMGS_RENDER_DEPTH)) ? 1 : 4;
     for (int ti = 0; ti < 3 && st == UMGS_OK; ++ti)
-        for (int si = 0; si < nsched && st == UMGS_OK; ++si) {
+        for (int si = 0; si < nsched && st == UMGS_OK; ++si)
+        for (int pi = 0; pi < nsplit && st == UMGS_OK; ++pi) {
             umgs_render_opts o = *inout;
             o.tile_size = tiles[ti];
             o.sched = scheds[si];
+            o.split = splits[pi];
             o.flags &= ~UMGS_RENDER_SAVE_BACKWARD;
             st = umgs_render(ctx, g, meshes, nmeshes, cams, ncams, &o, out_rgbt, fr, stream);  // warm-up
             if (st != UMGS_OK) break;

@@ -35,6 +35,7 @@ struct DevBuf {
 // Everything one umgs_render call produces and umgs_render_backward consumes.
 struct umgs_frame {
     umgs_ctx* ctx = nullptr;
+    int device = 0;  // the context's device (umgs_frame_destroy may outlive the context)
     umgs::DevBuf cams, grec, trec, bin, tile_off;
     // binning: record depth keys/values (+ ping-pong), per-record region
     // counts and offsets, (region, id) pairs (+ ping-pong), radix histograms,
@@ -53,7 +54,8 @@ struct umgs_frame {
     bool has_depth = false;
     umgs::DevBuf ggrad, tgrad, rerun_out;
     umgs::DevBuf fix_list;            // (camera, Gaussian) records whose conic is refined in fp64
-    umgs::DevBuf ord_k, ord_v, ord_k2, ord_v2;  // tile order of the persistent compositor
+    umgs::DevBuf ord_k, ord_v, ord_k2, ord_v2;  // tile (or work item) order of the persistent compositor
+    umgs::DevBuf split_items, segbuf, seglast;  // per-tile work split: work items, segment composites
     int32_t stack_cap = 8;
     bool saved = false;
     bool mixed = false;               // Gaussian records in fp16 (GRec16)
@@ -75,7 +77,7 @@ struct umgs_frame {
                         &rs_hist, &rs_hist2, &rs_bsum, &rg_start, &rg_nchunk, &rg_coff, &rg_ccnt, &rg_cpre, &tl_cnt,
                         &tl_off, &tl_ids,
                         &last, &status, &tfin, &ntri, &stack, &depth, &textab, &ggrad, &tgrad, &rerun_out, &fix_list, &ord_k, &ord_v,
-                        &ord_k2, &ord_v2})
+                        &ord_k2, &ord_v2, &split_items, &segbuf, &seglast})
             b->release();
         cams_host.clear();
         cams_dev = nullptr;
@@ -203,7 +205,11 @@ umgs_status frame_stats(const umgs_frame* fr, umgs_frame_stats* out, cudaStream_
 // first status word past the render's own (16 + the depth sort's key-map
 // slots): two u64 evaluation counters (Gaussian, triangle)
 constexpr int kStatusEvalWords = 16 + 2 * 32;
-constexpr int kStatusWords = kStatusEvalWords + 4;
+// then the work split's counters: work items, segment slots, persistent work counter
+constexpr int kStatusSplitWords = kStatusEvalWords + 4;
+constexpr int kStatusWords = kStatusSplitWords + 4;
+// buffers of a render with the per-tile work split for kcap tile-list entries
+cudaError_t reserve_split(umgs_frame* fr, int split, int64_t kcap);
 umgs_status frame_lists(const umgs_frame* fr, int64_t* tile_ptr, int32_t* ids, uint32_t* dbits,
                         cudaStream_t stream);
 

@@ -109,9 +109,12 @@ __device__ __noinline__ void conic_fp64(const DevCam& C, float mx, float my, flo
     double A2, B2, C2;
     cov2d_fp64(C, mx, my, mz, q, s, cov3d ? c6 : nullptr, A2, B2, C2);
     const double d2 = A2 * C2 - B2 * B2;
-    out[0] = (float)(C2 / d2);
-    out[1] = (float)(-B2 / d2);
-    out[2] = (float)(A2 / d2);
+    // the factor of gauss_power2: l0 = sqrt(k c / det), l1 = -k b / (det l0), l2 = sqrt(k / c)
+    const double k = 0.5 * 1.4426950408889634;
+    const double l0 = sqrt(k * C2 / d2);
+    out[0] = (float)l0;
+    out[1] = (float)(-k * B2 / (d2 * l0));
+    out[2] = (float)sqrt(k / C2);
 }
 
 // fp64 conics of the (camera, Gaussian) records listed by project_gaussians;
@@ -136,13 +139,13 @@ __global__ void refine_conics_kernel(const float* __restrict__ means, const floa
         if (grec16) {
             uint32_t* h = reinterpret_cast<uint32_t*>(grec16 + ri);
             const float o = half_hi(h[3]);
-            h[2] = pack_half2(-0.5f * kLog2e * cq[0], -kLog2e * cq[1]);
-            h[3] = pack_half2(-0.5f * kLog2e * cq[2], o);
+            h[2] = pack_half2(cq[0], cq[1]);
+            h[3] = pack_half2(cq[2], o);
         } else {
             float* g = reinterpret_cast<float*>(grec + ri);
-            g[2] = -0.5f * kLog2e * cq[0];
-            g[3] = -kLog2e * cq[1];
-            g[4] = -0.5f * kLog2e * cq[2];
+            g[2] = cq[0];
+            g[3] = cq[1];
+            g[4] = cq[2];
         }
     }
 }
@@ -225,12 +228,14 @@ __global__ void __launch_bounds__(256, 2) project_gaussians_kernel(
         bi.rx = (uint32_t)ixlo | ((uint32_t)ixhi << 16);
         bi.ry = (uint32_t)iylo | ((uint32_t)iyhi << 16);
         bin[bidx] = bi;
-        // conic (not a decision): fp32, or fp64 when the 2x2 determinant is
-        // small relative to a*c (cancellation would cost > 10 bits)
-        float ia, ib, ic;
+        // conic factor of gauss_power2 (not a decision): fp32, or fp64 when
+        // the 2x2 determinant is small relative to a*c (kConicFp64)
+        float l0, l1, l2;
         {
             const float id = 1.f / det;
-            ia = c * id; ib = -b * id; ic = a * id;
+            l0 = sqrtf(kHalfLog2e * c * id);
+            l1 = -kHalfLog2e * b * id / l0;
+            l2 = sqrtf(kHalfLog2e / c);
         }
         if (det < kConicFp64 * a * c) {  // near-singular: refined in fp64 by refine_conics_kernel
             const unsigned slot = atomicAdd(fix_count, 1u);
@@ -239,13 +244,12 @@ __global__ void __launch_bounds__(256, 2) project_gaussians_kernel(
         // colour is written by shade_gaussians_kernel
         if (grec16) {
             GRec16* hp = grec16 + ri;
-            hp->v0 = make_uint4(__float_as_uint(u), __float_as_uint(v),
-                                pack_half2(-0.5f * kLog2e * ia, -kLog2e * ib), pack_half2(-0.5f * kLog2e * ic, o));
+            hp->v0 = make_uint4(__float_as_uint(u), __float_as_uint(v), pack_half2(l0, l1), pack_half2(l2, o));
             reinterpret_cast<uint2*>(&hp->v1)[1] = make_uint2(bi.rx, bi.ry);
         } else {
             float4* gp = reinterpret_cast<float4*>(grec + ri);
-            gp[0] = make_float4(u, v, -0.5f * kLog2e * ia, -kLog2e * ib);
-            reinterpret_cast<float2*>(gp + 1)[0] = make_float2(-0.5f * kLog2e * ic, o);
+            gp[0] = make_float4(u, v, l0, l1);
+            reinterpret_cast<float2*>(gp + 1)[0] = make_float2(l2, o);
             reinterpret_cast<float2*>(gp + 2)[0] = make_float2(0.f, __uint_as_float(bi.rx));
             reinterpret_cast<float2*>(gp + 2)[1] = make_float2(__uint_as_float(bi.ry), Z);  // Z: expected-depth output
         }
@@ -1154,8 +1158,7 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     }
     // status words cleared by a kernel (not a memset node), so that the
     // programmatic launch chain runs on from the stream's previous kernel
-    launch_pdl(zero_words_kernel, 1, 128, 0, stream, reinterpret_cast<uint32_t*>(fr->status.ptr),
-               16 + 2 * kRadixMapSlots);
+    launch_pdl(zero_words_kernel, 1, 128, 0, stream, reinterpret_cast<uint32_t*>(fr->status.ptr), kStatusWords);
 
     const DevCam* dcams = fr->cams.as<DevCam>();
     const unsigned fix_cap = (unsigned)std::min<int64_t>(std::max<int64_t>(1, Ng * ncams), 1 << 22);

@@ -75,7 +75,7 @@ class CFrameStats(ctypes.Structure):
 class CRenderOpts(ctypes.Structure):
     _fields_ = [("tile_size", ctypes.c_int32), ("blend_mode", ctypes.c_int32), ("t_eps", ctypes.c_float),
                 ("bg", ctypes.c_float * 3), ("flags", ctypes.c_int32), ("sched", ctypes.c_int32),
-                ("edge_sigma", ctypes.c_float)]
+                ("edge_sigma", ctypes.c_float), ("split", ctypes.c_int32)]
 
 
 _lib = None
@@ -326,12 +326,14 @@ def mesh_to_device(m, device="cuda") -> DevMesh:
 
 def render_opts(tile_size=16, blend_mode=BLEND_FULL, t_eps=1e-4, bg=(0.0, 0.0, 0.0), save=False,
                 mixed=False, sched=0, t_product=False, asynchronous=False, depth=False,
-                edge_sigma=None) -> CRenderOpts:
+                edge_sigma=None, split=0) -> CRenderOpts:
     """edge_sigma: soft-edge triangle coverage of that width in pixels
-    (UMGS_RENDER_SOFT_EDGE), or None for the binary sample coverage."""
+    (UMGS_RENDER_SOFT_EDGE), or None for the binary sample coverage.
+    split: per-tile work split (segments of that many records), 0 = off."""
     o = CRenderOpts()
     lib().umgs_default_render_opts(ctypes.byref(o))
     o.sched = int(sched)
+    o.split = int(split)
     o.flags = ((RENDER_SAVE_BACKWARD if save else 0) | (RENDER_MIXED if mixed else 0)
                | (RENDER_T_PRODUCT if t_product else 0) | (RENDER_ASYNC if asynchronous else 0)
                | (RENDER_DEPTH if depth else 0) | (RENDER_SOFT_EDGE if edge_sigma else 0))
