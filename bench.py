@@ -169,9 +169,10 @@ def run_umgs(args, rank, world, local_rank):
     bind_s = time.time() - t0
     bind_info = "umgs_bind BBX k=3, %d cameras, %d fallback targets" % (len(sc.bind_cameras), nfb)
     # the binding regrouped per Gaussian into its distinct proxy vertices and
-    # weights (once, like the binding itself); every step deforms through it
+    # weights, packed (CSR; once, like the binding itself); every step deforms
+    # through it
     t0 = time.time()
-    bcount, bent = umgs.binding_compact(ctx, face, bary, PF, PV.shape[0])
+    boff, bent = umgs.binding_csr(ctx, face, bary, PF, PV.shape[0])
     torch.cuda.synchronize()
     compact_s = time.time() - t0
 
@@ -184,13 +185,13 @@ def run_umgs(args, rank, world, local_rank):
     # one synchronous render sizes the frame; the timed steps render
     # asynchronously (no host read-back) into a pair capacity of 1.25x that
     # count, and umgs_frame_check after the region confirms no step overflowed
-    umgs.deform_compact(ctx, g, bcount, bent, PV, Vd_all[0], PF, out=(mu2, cov2, None))
+    umgs.deform_csr(ctx, g, boff, bent, PV, Vd_all[0], PF, out=(mu2, cov2, None))
     umgs.render(ctx, gdef, [mesh], [cam], umgs.render_opts(16), out=out, frame=frame)
     frame.reserve(int(frame.counts()[0] * 1.25) + 4096)
     opts = umgs.render_opts(16, asynchronous=True)
 
     def step(f, vd=None):
-        umgs.deform_compact(ctx, g, bcount, bent, PV, Vd_all[f % nframes] if vd is None else vd, PF,
+        umgs.deform_csr(ctx, g, boff, bent, PV, Vd_all[f % nframes] if vd is None else vd, PF,
                             out=(mu2, cov2, None))
         umgs.render(ctx, gdef, [mesh], [cam], opts, out=out, frame=frame)
 
@@ -247,7 +248,7 @@ def run_umgs(args, rank, world, local_rank):
         return umgs.render_backward(ctx, frame, gdef, [mesh], dl)
 
     def step_deform(f):
-        umgs.deform_compact(ctx, g, bcount, bent, PV, Vd_all[f % nframes], PF, out=(mu2, cov2, None))
+        umgs.deform_csr(ctx, g, boff, bent, PV, Vd_all[f % nframes], PF, out=(mu2, cov2, None))
 
     for f in range(max(2, Wm)):
         step_fb(f)
@@ -289,7 +290,7 @@ def run_umgs(args, rank, world, local_rank):
         if f >= 2:
             comp.wait_event(copied[b])
         vd_dev.copy_(host_vd[f % nframes], non_blocking=True)
-        umgs.deform_compact(ctx, g, bcount, bent, PV, vd_dev, PF, out=(mu2, cov2, None))
+        umgs.deform_csr(ctx, g, boff, bent, PV, vd_dev, PF, out=(mu2, cov2, None))
         umgs.render(ctx, gdef, [mesh], [cam], opts, out=outs[b], frame=frame)
         rendered[b].record(comp)
         with torch.cuda.stream(copy_s):
@@ -348,8 +349,8 @@ def run_umgs(args, rank, world, local_rank):
     names = stage_names()
     stages = {names[k]: {"ms_per_launch": stage_ms[k] / stage_n[k], "launches": int(stage_n[k])}
               for k in range(16) if stage_n[k] > 0}
-    # algorithmic binding bytes per Gaussian: its count and its used entries
-    bind_bytes = 4.0 + 8.0 * float(bcount.float().mean())
+    # algorithmic binding bytes per Gaussian: its offset and its packed entries
+    bind_bytes = 4.0 + 8.0 * float(bent.shape[0]) / n
     num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
     roof = roofline(stages, nkeys, n, sc, clk, fstats, ms_step, bind_bytes, num_sms)
     comp_ms = stages["composite"]["ms_per_launch"] if "composite" in stages else float("nan")

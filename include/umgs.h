@@ -439,6 +439,28 @@ umgs_status umgs_deform_compact(umgs_ctx* ctx, const umgs_gaussians* rest, const
                                 const int32_t* proxy_f, int64_t nv, int64_t nf, int32_t mode, float* out_means,
                                 float* out_cov3d, float* out_quats, void* stream);
 
+/* The compact binding packed without padding (CSR): Gaussian i's distinct
+ * vertices and weights are entries [offsets[i], offsets[i+1]) of one array,
+ * in order of first appearance, each run padded to an even length with a
+ * zero-weight copy of its first entry (about 11 entries per Gaussian for the
+ * 1080p workload instead of 24 padded rows: the deformation reads 88 bytes
+ * per Gaussian, not 192-byte rows).  A Gaussian with an out-of-range face or
+ * vertex index gets the entries (-1, 0), (-1, 0).
+ *   out_offsets [n+1] int32 device; out_entries [cap,2] int32 device
+ *   (vertex id, weight as float bits), 16-byte aligned, nullable if cap = 0;
+ *   *out_total (host): the entries needed.
+ * Synchronises `stream`.  Errors: INVALID_ARG, CAPACITY when *out_total >
+ * cap (offsets written, entries not: call again with a larger buffer), CUDA.
+ * umgs_deform_csr is umgs_deform_compact over that form (same modes, outputs
+ * and errors). */
+umgs_status umgs_binding_csr(umgs_ctx* ctx, const int32_t* face, const float* bary, int64_t n,
+                             const int32_t* proxy_f, int64_t nv, int64_t nf, int32_t* out_offsets,
+                             int32_t* out_entries, int64_t cap, int64_t* out_total, void* stream);
+umgs_status umgs_deform_csr(umgs_ctx* ctx, const umgs_gaussians* rest, const int32_t* offsets,
+                            const int32_t* entries, const float* proxy_v, const float* proxy_vd,
+                            const int32_t* proxy_f, int64_t nv, int64_t nf, int32_t mode, float* out_means,
+                            float* out_cov3d, float* out_quats, void* stream);
+
 /* ---- multi-view form: CUDA graph and autotuning -----------------------------
  *
  * umgs_render_graph_create renders once (an ordinary umgs_render into

@@ -333,6 +333,46 @@ umgs_status umgs_deform_compact(umgs_ctx* ctx, const umgs_gaussians* rest, const
                                   static_cast<cudaStream_t>(stream));
 }
 
+umgs_status umgs_binding_csr(umgs_ctx* ctx, const int32_t* face, const float* bary, int64_t n,
+                             const int32_t* proxy_f, int64_t nv, int64_t nf, int32_t* out_offsets,
+                             int32_t* out_entries, int64_t cap, int64_t* out_total, void* stream) {
+    if (!ctx) return UMGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, UMGS_ERR_CUDA, "cudaSetDevice");
+    if (n < 0 || nv < 3 || nf < 1 || !proxy_f || cap < 0 || !out_total || !out_offsets)
+        return fail(ctx, UMGS_ERR_INVALID_ARG, "bad sizes, proxy mesh or output");
+    if (n > 0 && (!face || !bary)) return fail(ctx, UMGS_ERR_INVALID_ARG, "NULL array");
+    if (cap > 0 && !out_entries) return fail(ctx, UMGS_ERR_INVALID_ARG, "NULL entries with cap > 0");
+    if ((reinterpret_cast<uintptr_t>(bary) & 7) || (reinterpret_cast<uintptr_t>(out_entries) & 15))
+        return fail(ctx, UMGS_ERR_INVALID_ARG, "bary must be 8-byte and out_entries 16-byte aligned");
+    return binding_csr(ctx, face, bary, n, proxy_f, nv, nf, out_offsets, reinterpret_cast<int2*>(out_entries), cap,
+                       out_total, static_cast<cudaStream_t>(stream));
+}
+
+umgs_status umgs_deform_csr(umgs_ctx* ctx, const umgs_gaussians* rest, const int32_t* offsets,
+                            const int32_t* entries, const float* proxy_v, const float* proxy_vd,
+                            const int32_t* proxy_f, int64_t nv, int64_t nf, int32_t mode, float* out_means,
+                            float* out_cov3d, float* out_quats, void* stream) {
+    if (!ctx) return UMGS_ERR_INVALID_ARG;
+    ctx->err.clear();
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, UMGS_ERR_CUDA, "cudaSetDevice");
+    if (!rest || rest->n < 0) return fail(ctx, UMGS_ERR_INVALID_ARG, "rest Gaussians missing");
+    if ((mode & ~(UMGS_DEFORM_LITERAL | UMGS_DEFORM_ONE_RING)) != 0)
+        return fail(ctx, UMGS_ERR_INVALID_ARG, "bad mode");
+    if (!proxy_v || !proxy_vd || !proxy_f || nv < 3 || nf < 1) return fail(ctx, UMGS_ERR_INVALID_ARG, "bad proxy mesh");
+    if (rest->n > 0) {
+        if (!rest->means || !offsets || !entries || !out_means || !out_cov3d)
+            return fail(ctx, UMGS_ERR_INVALID_ARG, "NULL array");
+        if (!rest->cov3d && (!rest->quats || !rest->scales))
+            return fail(ctx, UMGS_ERR_INVALID_ARG, "need quats+scales or cov3d");
+        if (reinterpret_cast<uintptr_t>(entries) & 15)
+            return fail(ctx, UMGS_ERR_INVALID_ARG, "entries must be 16-byte aligned");
+    }
+    return deform_compact_forward(ctx, rest, offsets, reinterpret_cast<const int2*>(entries), proxy_v, proxy_vd,
+                                  proxy_f, nv, nf, mode, out_means, out_cov3d, out_quats,
+                                  static_cast<cudaStream_t>(stream), true);
+}
+
 umgs_status umgs_bind(umgs_ctx* ctx, const umgs_gaussians* g, const float* proxy_v, const int32_t* proxy_f,
                       int64_t nv, int64_t nf, const umgs_camera* cams, int32_t ncams, int32_t mode, float k_sigma,
                       int32_t* out_face, float* out_bary, float* out_dist, uint8_t* out_flags,

@@ -18,6 +18,9 @@
 #include <cmath>
 #include <mutex>
 
+#include <cstring>
+#include <string>
+
 #include "internal.h"
 
 namespace umgs {
@@ -570,6 +573,106 @@ __global__ void __launch_bounds__(256) binding_compact_kernel(const int32_t* __r
     count[i] = c;
 }
 
+// ---- compact binding as CSR ------------------------------------------------
+// The distinct bound vertices and weights of Gaussian i occupy entries
+// [offsets[i], offsets[i+1]) of one packed array, in order of first
+// appearance, padded to an even count with a zero-weight copy of the first
+// entry (the deformation reads two entries per 16-byte load).  A Gaussian
+// with an out-of-range face or vertex index gets two (-1, 0) entries (the
+// deformation then marks it bad).
+__device__ int csr_distinct(const int32_t* __restrict__ face, const float* __restrict__ bary, int64_t i,
+                            const int32_t* __restrict__ F, int64_t nv, int64_t nf, int2 out[24]) {
+    int c = 0;
+    for (int p = 0; p < 8; ++p) {
+        const int f = face[8 * i + p];
+        const float2 b = reinterpret_cast<const float2*>(bary)[8 * i + p];
+        if (f < 0 || f >= nf) return -1;
+        const float wk[3] = {1.f - b.x - b.y, b.x, b.y};
+        for (int k = 0; k < 3; ++k) {
+            const int v = F[3 * (int64_t)f + k];
+            if (v < 0 || v >= nv) return -1;
+            const float w = 0.125f * wk[k];
+            int j = 0;
+            while (j < c && out[j].x != v) ++j;
+            if (j < c) out[j].y = __float_as_int(__int_as_float(out[j].y) + w);
+            else { out[c] = make_int2(v, __float_as_int(w)); ++c; }
+        }
+    }
+    return c;
+}
+
+__global__ void __launch_bounds__(256) binding_csr_count_kernel(const int32_t* __restrict__ face,
+                                                               const float* __restrict__ bary, int64_t n,
+                                                               const int32_t* __restrict__ F, int64_t nv, int64_t nf,
+                                                               uint32_t* __restrict__ count) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int2 tmp[24];
+    const int c = csr_distinct(face, bary, i, F, nv, nf, tmp);
+    count[i] = c < 0 ? 2u : (uint32_t)((c + 1) & ~1);
+}
+
+// exclusive scan of n counts into offsets[0..n] (offsets[n] = total), in one
+// block of 1024 threads (a one-time step of the binding)
+__global__ void __launch_bounds__(1024) binding_csr_scan_kernel(const uint32_t* __restrict__ count, int64_t n,
+                                                               int32_t* __restrict__ offsets,
+                                                               unsigned long long* __restrict__ total) {
+    __shared__ unsigned long long s_w[32];
+    __shared__ unsigned long long s_base;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t == 0) s_base = 0;
+    __syncthreads();
+    for (int64_t b = 0; b < n; b += 1024) {
+        const int64_t i = b + t;
+        const unsigned long long v = i < n ? count[i] : 0ull;
+        unsigned long long x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_w[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long w = s_w[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            s_w[lane] = w;
+        }
+        __syncthreads();
+        const unsigned long long excl = s_base + (warp ? s_w[warp - 1] : 0ull) + x - v;
+        if (i < n) offsets[i] = (int32_t)min(excl, 0x7fffffffull);
+        __syncthreads();
+        if (t == 1023) s_base += s_w[31];
+        __syncthreads();
+    }
+    if (t == 0) {
+        offsets[n] = (int32_t)min(s_base, 0x7fffffffull);
+        *total = s_base;
+    }
+}
+
+__global__ void __launch_bounds__(256) binding_csr_fill_kernel(const int32_t* __restrict__ face,
+                                                              const float* __restrict__ bary, int64_t n,
+                                                              const int32_t* __restrict__ F, int64_t nv, int64_t nf,
+                                                              const int32_t* __restrict__ offsets,
+                                                              int2* __restrict__ entries) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int2 tmp[24];
+    const int c = csr_distinct(face, bary, i, F, nv, nf, tmp);
+    int2* out = entries + offsets[i];
+    if (c < 0) {
+        out[0] = out[1] = make_int2(-1, 0);
+        return;
+    }
+    for (int j = 0; j < c; ++j) out[j] = tmp[j];
+    if (c & 1) out[c] = make_int2(tmp[0].x, 0);  // zero-weight padding
+}
+
 // Deformation over a compact binding.  A block of 256 threads takes 256
 // Gaussians.  Gather phase, 4 rounds of 64 Gaussians: the four lanes of a
 // Gaussian walk its entries together; for each entry lane p gathers float4 p
@@ -580,6 +683,8 @@ __global__ void __launch_bounds__(256) binding_compact_kernel(const int32_t* __r
 // one Gaussian (Eq. 13 and all three outputs), so that math runs with every
 // lane busy.
 constexpr int kDefBlock = 256;
+// CSR: `count` holds the offsets [n+1] of the packed entries (binding_csr_*)
+template <bool CSR>
 __global__ void __launch_bounds__(kDefBlock) deform_gaussians_compact_kernel(
     const float* __restrict__ means, const float* __restrict__ quats, const float* __restrict__ scales,
     const float* __restrict__ cov3d, int64_t n, const int32_t* __restrict__ count, const int2* __restrict__ entries,
@@ -599,11 +704,18 @@ __global__ void __launch_bounds__(kDefBlock) deform_gaussians_compact_kernel(
         float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
         int bad = 0;
         int c = 0;
+        int64_t start = 24 * i;
         if (i < n) {
-            c = count[i];
-            if (c < 0 || c > 24) { bad = 1; c = 0; }
+            if (CSR) {
+                start = count[i];
+                c = count[i + 1] - count[i];
+                if (c < 0 || c > 24 || (start & 1)) { bad = 1; c = 0; }
+            } else {
+                c = count[i];
+                if (c < 0 || c > 24) { bad = 1; c = 0; }
+            }
         }
-        const int4* row = reinterpret_cast<const int4*>(entries + 24 * i);  // two entries per int4
+        const int4* row = reinterpret_cast<const int4*>(entries + start);  // two entries per int4
         for (int j = 0; j < c; j += 4) {
             const int4 e01 = row[j >> 1];
             const int4 e23 = j + 2 < c ? row[(j >> 1) + 1] : make_int4(0, 0, 0, 0);
@@ -714,18 +826,52 @@ umgs_status binding_compact(umgs_ctx* ctx, const int32_t* face, const float* bar
     return UMGS_OK;
 }
 
+umgs_status binding_csr(umgs_ctx* ctx, const int32_t* face, const float* bary, int64_t n, const int32_t* F,
+                        int64_t nv, int64_t nf, int32_t* out_offsets, int2* out_entries, int64_t cap,
+                        int64_t* out_total, cudaStream_t stream) {
+    cudaError_t e;
+    if ((e = ctx->bind_cnt.reserve(sizeof(uint32_t) * std::max<int64_t>(1, n) + 16)) != cudaSuccess)
+        return fail(ctx, UMGS_ERR_OUT_OF_MEMORY, "CSR counts");
+    uint32_t* cnt = ctx->bind_cnt.as<uint32_t>();
+    unsigned long long* tot = reinterpret_cast<unsigned long long*>(cnt + ((std::max<int64_t>(1, n) + 1) & ~1LL));
+    if (n > 0)
+        binding_csr_count_kernel<<<grid_for(n, 256), 256, 0, stream>>>(face, bary, n, F, nv, nf, cnt), count_launch();
+    binding_csr_scan_kernel<<<1, 1024, 0, stream>>>(cnt, n, out_offsets, tot), count_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "binding_csr kernels");
+    unsigned long long total = 0;
+    if ((e = cudaMemcpyAsync(ctx->pinned, tot, sizeof(total), cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(stream)) != cudaSuccess)
+        return cuda_fail(ctx, e, "reading the CSR size");
+    std::memcpy(&total, ctx->pinned, sizeof(total));
+    *out_total = (int64_t)total;
+    if (total > 0x7fffffffull) return fail(ctx, UMGS_ERR_CAPACITY, "more than 2^31 - 1 binding entries");
+    if ((int64_t)total > cap)
+        return fail(ctx, UMGS_ERR_CAPACITY, "entries capacity " + std::to_string(cap) + " < " + std::to_string(total));
+    if (n > 0)
+        binding_csr_fill_kernel<<<grid_for(n, 256), 256, 0, stream>>>(face, bary, n, F, nv, nf, out_offsets,
+                                                                      out_entries), count_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(ctx, e, "binding_csr_fill_kernel");
+    return UMGS_OK;
+}
+
 umgs_status deform_compact_forward(umgs_ctx* ctx, const umgs_gaussians* g, const int32_t* count, const int2* entries,
                                    const float* V, const float* Vd, const int32_t* F, int64_t nv, int64_t nf,
                                    int32_t mode, float* out_means, float* out_cov, float* out_quats,
-                                   cudaStream_t stream) {
+                                   cudaStream_t stream, bool csr) {
     const umgs_status st = proxy_table(ctx, V, Vd, F, nv, nf, (mode & UMGS_DEFORM_ONE_RING) != 0, stream);
     mode &= 1;  // the mean update: FRAME or LITERAL
     if (st != UMGS_OK) return st;
     StageTimer tm(ctx, UMGS_STAGE_DEFORM_GAUSSIANS, stream);
-    if (g->n > 0)
-        launch_pdl(deform_gaussians_compact_kernel, grid_for(g->n, kDefBlock), kDefBlock, 0, stream, 
-            g->means, g->quats, g->scales, g->cov3d, g->n, count, entries, nv, ctx->vtab.as<float>(), mode,
-            out_means, out_cov, out_quats, ctx->dstatus.as<int32_t>());
+    if (g->n > 0) {
+        if (csr)
+            launch_pdl(deform_gaussians_compact_kernel<true>, grid_for(g->n, kDefBlock), kDefBlock, 0, stream,
+                g->means, g->quats, g->scales, g->cov3d, g->n, count, entries, nv, ctx->vtab.as<float>(), mode,
+                out_means, out_cov, out_quats, ctx->dstatus.as<int32_t>());
+        else
+            launch_pdl(deform_gaussians_compact_kernel<false>, grid_for(g->n, kDefBlock), kDefBlock, 0, stream,
+                g->means, g->quats, g->scales, g->cov3d, g->n, count, entries, nv, ctx->vtab.as<float>(), mode,
+                out_means, out_cov, out_quats, ctx->dstatus.as<int32_t>());
+    }
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(ctx, e, "deform kernels");
     return UMGS_OK;

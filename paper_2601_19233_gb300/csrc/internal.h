@@ -177,7 +177,10 @@ umgs_status binding_compact(umgs_ctx* ctx, const int32_t* face, const float* bar
 umgs_status deform_compact_forward(umgs_ctx* ctx, const umgs_gaussians* g, const int32_t* count, const int2* entries,
                                    const float* V, const float* Vd, const int32_t* F, int64_t nv, int64_t nf,
                                    int32_t mode, float* out_means, float* out_cov, float* out_quats,
-                                   cudaStream_t stream);
+                                   cudaStream_t stream, bool csr = false);
+umgs_status binding_csr(umgs_ctx* ctx, const int32_t* face, const float* bary, int64_t n, const int32_t* F,
+                        int64_t nv, int64_t nf, int32_t* out_offsets, int2* out_entries, int64_t cap,
+                        int64_t* out_total, cudaStream_t stream);
 
 umgs_status bind_forward(umgs_ctx* ctx, const umgs_gaussians* g, const float* V, const int32_t* F, int64_t nv,
                          int64_t nf, const umgs_camera* cams, int32_t ncams, int32_t mode, float k_sigma,

@@ -137,6 +137,11 @@ def lib():
         L.umgs_deform_compact.argtypes = [vp, ctypes.POINTER(CGaussians), vp, vp, vp, vp, vp, i64, i64, i32, vp, vp,
                                           vp, vp]
         L.umgs_deform_compact.restype = ctypes.c_int
+        L.umgs_binding_csr.argtypes = [vp, vp, vp, i64, vp, i64, i64, vp, vp, i64, ctypes.POINTER(i64), vp]
+        L.umgs_binding_csr.restype = ctypes.c_int
+        L.umgs_deform_csr.argtypes = [vp, ctypes.POINTER(CGaussians), vp, vp, vp, vp, vp, i64, i64, i32, vp, vp,
+                                      vp, vp]
+        L.umgs_deform_csr.restype = ctypes.c_int
         L.umgs_frame_reserve.argtypes = [vp, i64]
         L.umgs_frame_reserve.restype = ctypes.c_int
         L.umgs_frame_check.argtypes = [vp, vp]
@@ -409,6 +414,41 @@ def deform_compact(ctx: Context, rest: DevGaussians, count: torch.Tensor, entrie
                                    _ptr(proxy_vd), _ptr(proxy_f), int(proxy_v.shape[0]), int(proxy_f.shape[0]),
                                    int(mode), _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), _stream(stream))
     ctx.check(st, "umgs_deform_compact")
+    return out
+
+
+def binding_csr(ctx: Context, face: torch.Tensor, bary: torch.Tensor, proxy_f: torch.Tensor, nv: int, stream=None):
+    """umgs_binding_csr: (offsets int32 [n+1], entries int32 [total,2]) on the device."""
+    n = int(face.shape[0])
+    dev = torch.device("cuda", ctx.device)
+    offsets = torch.empty((n + 1,), dtype=torch.int32, device=dev)
+    total = ctypes.c_int64(0)
+    st = lib().umgs_binding_csr(ctx._h, _ptr(face), _ptr(bary), n, _ptr(proxy_f), int(nv), int(proxy_f.shape[0]),
+                                _ptr(offsets), None, 0, ctypes.byref(total), _stream(stream))
+    if st not in (OK, 3):  # CAPACITY: the size query
+        ctx.check(st, "umgs_binding_csr")
+    entries = torch.empty((max(1, total.value), 2), dtype=torch.int32, device=dev)
+    ctx.check(lib().umgs_binding_csr(ctx._h, _ptr(face), _ptr(bary), n, _ptr(proxy_f), int(nv),
+                                     int(proxy_f.shape[0]), _ptr(offsets), _ptr(entries), int(entries.shape[0]),
+                                     ctypes.byref(total), _stream(stream)), "umgs_binding_csr")
+    return offsets, entries
+
+
+def deform_csr(ctx: Context, rest: DevGaussians, offsets: torch.Tensor, entries: torch.Tensor,
+               proxy_v: torch.Tensor, proxy_vd: torch.Tensor, proxy_f: torch.Tensor, mode=DEFORM_FRAME,
+               out=None, with_quats=True, stream=None):
+    """umgs_deform_csr: umgs_deform over the CSR binding; returns (means', cov3d', quats' or None)."""
+    n = rest.n
+    dev = torch.device("cuda", ctx.device)
+    if out is None:
+        out = (torch.empty((n, 3), dtype=torch.float32, device=dev),
+               torch.empty((n, 6), dtype=torch.float32, device=dev),
+               torch.empty((n, 4), dtype=torch.float32, device=dev) if with_quats else None)
+    cg = rest.c()
+    st = lib().umgs_deform_csr(ctx._h, ctypes.byref(cg), _ptr(offsets), _ptr(entries), _ptr(proxy_v),
+                               _ptr(proxy_vd), _ptr(proxy_f), int(proxy_v.shape[0]), int(proxy_f.shape[0]),
+                               int(mode), _ptr(out[0]), _ptr(out[1]), _ptr(out[2]), _stream(stream))
+    ctx.check(st, "umgs_deform_csr")
     return out
 
 

@@ -67,16 +67,33 @@ def test_plane_closed_form(ctx):
     assert np.allclose(dist[:, 0], want, rtol=2e-5, atol=1e-6)
 
 
+def _bind_chunk(args):
+    means, quats, scales, V, F, vms = args
+    return B.bind(means, quats, scales, V, F, vms, mode=B.BBX)
+
+
 def test_full_size_sampled(ctx):
     """Bench-size binding (1M Gaussians, 100 cameras, 20,480-face proxy),
-    checked bit-exact on a sample of Gaussians against brute force."""
+    checked bit-exact against brute force on 64 Gaussians (512 targets): 32
+    drawn at random and the 32 whose bound points lie closest to a face edge
+    (smallest barycentric weight), where a wrong face is likeliest.  The brute
+    force runs in a spawned process pool."""
+    import multiprocessing as mp
+    import os
     sc = S.config1()
     g = sc.gaussians
     face, bary, dist, flags, nfb = _gpu_bind(ctx, g, sc.proxy_verts, sc.proxy_faces, sc.bind_cameras, B.BBX)
     assert face.shape == (g.n, 8) and (face >= 0).all()
-    idx = np.random.default_rng(0).choice(g.n, size=4, replace=False)
-    ref = B.bind(g.means, g.quats, g.scales, sc.proxy_verts, sc.proxy_faces, [c.viewmat for c in sc.bind_cameras],
-                 mode=B.BBX, gaussian_ids=idx)
+    rand = np.random.default_rng(0).choice(g.n, size=32, replace=False)
+    w = np.concatenate([bary, 1.0 - bary.sum(-1, keepdims=True)], -1).min(-1).min(-1)
+    w[rand] = np.inf
+    idx = np.sort(np.concatenate([rand, np.argsort(w)[:32]]))
+    vms = [c.viewmat for c in sc.bind_cameras]
+    chunks = [c for c in np.array_split(idx, 16) if len(c)]
+    with mp.get_context("spawn").Pool(min(len(chunks), os.cpu_count() or 1)) as pool:
+        parts = pool.map(_bind_chunk, [(g.means[c], g.quats[c], g.scales[c], sc.proxy_verts, sc.proxy_faces, vms)
+                                       for c in chunks])
+    ref = {k: np.concatenate([p_[k] for p_ in parts]) for k in ("face", "bary", "dist", "flags")}
     assert np.array_equal(face[idx], ref["face"])
     assert np.array_equal(bary[idx].view(np.uint32), ref["bary"].view(np.uint32))
     assert np.array_equal(dist[idx].view(np.uint32), ref["dist"].view(np.uint32))

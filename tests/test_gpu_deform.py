@@ -195,3 +195,45 @@ def test_one_ring_rigid_and_noalloc_rejects(ctx):
     with pytest.raises(umgs.UmgsError):
         umgs.deform_noalloc(dg, t(face), t(b), t(V.astype(np.float32)), t(Vd.astype(np.float32)), t(F), out,
                             mode=umgs.DEFORM_ONE_RING)
+
+
+def test_csr_binding_and_deformation(ctx):
+    """The CSR form holds the padded compact rows packed: the same distinct
+    vertices and weights per Gaussian (runs padded to an even length with a
+    zero weight), and the deformation through it agrees with the padded
+    form's."""
+    from paper_2601_19233_gb300 import umgs
+    V, F, g, face, b = _problem(4)
+    face[7, 3] = len(F) + 5  # an out-of-range face: entries (-1, 0) and a NaN output
+    Vd = S.displace(V, S.sinusoid_params(np.random.default_rng(9)), 31)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a)).cuda()
+    tf = t(F)
+    cnt, ent = umgs.binding_compact(ctx, t(face), t(b), tf, len(V))
+    off, csr = umgs.binding_csr(ctx, t(face), t(b), tf, len(V))
+    cnt, ent, off, csr = cnt.cpu().numpy(), ent.cpu().numpy(), off.cpu().numpy(), csr.cpu().numpy()
+    assert off[0] == 0 and np.all(np.diff(off) % 2 == 0) and off[-1] == len(csr)
+    for i in range(len(cnt)):
+        run = csr[off[i]:off[i + 1]]
+        if cnt[i] < 0:
+            assert i == 7 and np.array_equal(run, [[-1, 0], [-1, 0]])
+            continue
+        assert len(run) == cnt[i] + (cnt[i] & 1)
+        assert np.array_equal(run[:cnt[i]], ent[i, :cnt[i]])
+        if cnt[i] & 1:
+            assert run[-1, 0] == run[0, 0] and run[-1, 1] == 0
+    dg = umgs.gaussians_to_device(g)
+    for mode in (D.FRAME, D.LITERAL):
+        m0, c0, q0 = umgs.deform_compact(ctx, dg, t(cnt), t(ent), t(V.astype(np.float32)),
+                                         t(Vd.astype(np.float32)), tf, mode=mode)
+        m1, c1, q1 = umgs.deform_csr(ctx, dg, t(off), t(csr), t(V.astype(np.float32)),
+                                     t(Vd.astype(np.float32)), tf, mode=mode)
+        m0, m1, c0, c1 = m0.cpu().numpy(), m1.cpu().numpy(), c0.cpu().numpy(), c1.cpu().numpy()
+        ok = np.ones(len(m0), bool)
+        ok[7] = False
+        assert np.isnan(m1[7]).all()
+        # the same sums (the padding adds 0 x a row); the two kernel builds may round apart
+        assert np.abs(m1[ok] - m0[ok]).max() < 2e-6
+        assert (np.abs(c1[ok] - c0[ok]) / np.abs(c0[ok]).max(1, keepdims=True)).max() < 2e-5
+        assert _quat_err(q1.cpu().numpy()[ok], q0.cpu().numpy()[ok]) < 2e-6
+    with pytest.raises(umgs.UmgsError):
+        ctx.sync()  # the bad index is reported

@@ -50,11 +50,21 @@ def _sample_pixels(rng, W, H, n, crop=None):
     return pix
 
 
-def _check_pixels(sc, out_cam, pix, cam_index=0, tol=TOL, cov3d=None, frame=None):
+# Tie pixels (a fragment's fp64 alpha within 1e-6 of 1/255, or T within 0.1%
+# of t_eps) are excluded from the bar.  The 1e-6 window must hold the fp32
+# kernels' alpha error at the threshold, which the rounding of the projected
+# mean dominates (an ulp is 6e-5 px at x = 1000, 2.4e-4 px at x = 3800: up to
+# ~2e-6 in alpha there), and the chance that some fragment of a pixel lands in
+# it grows with the fragments per pixel (about 250 at 1080p, 890 at 4K): the
+# oracle measured 0.7% tie pixels at 1080p and 1.1% on the 4K crops.
+TIE_MAX = {"1080p": 0.02, "4k": 0.03, "multiview": 0.02}
+
+
+def _check_pixels(sc, out_cam, pix, cam_index=0, tol=TOL, cov3d=None, frame=None, tie_max=0.02):
     rgb, T, tie, _ = R.render_pixels(sc, pix, cam_index=cam_index, cov3d=cov3d, frame=frame)
     got = out_cam[pix[:, 1], pix[:, 0]]
     ok = ~tie
-    assert ok.mean() > 0.98
+    assert tie.mean() <= tie_max, ("tie pixels", int(tie.sum()), len(tie))
     e_rgb = np.abs(got[:, :3] - rgb)[ok].max()
     e_T = np.abs(got[:, 3] - T)[ok].max()
     assert e_rgb <= tol and e_T <= tol, (e_rgb, e_T)
@@ -77,7 +87,7 @@ def test_1080p_lists_and_pixels(ctx):
     assert len(gids) > 5_000_000
     assert np.array_equal(gptr, ptr) and np.array_equal(gids, ids) and np.array_equal(gdb, db)
     rng = np.random.default_rng(11)
-    _check_pixels(sc, out, _sample_pixels(rng, 1920, 1080, 192, crop=(760, 340, 400, 400)))
+    _check_pixels(sc, out, _sample_pixels(rng, 1920, 1080, 192, crop=(760, 340, 400, 400)), tie_max=TIE_MAX["1080p"])
 
 
 def test_1080p_deform_then_render(ctx):
@@ -115,7 +125,8 @@ def test_1080p_deform_then_render(ctx):
     ptr, ids, db = cn.sorted_tile_lists([cn.Primitives(sc, 0, cov3d=cov)], 16)
     gptr, gids, gdb = _gpu_lists(fr)
     assert np.array_equal(gptr, ptr) and np.array_equal(gids, ids) and np.array_equal(gdb, db)
-    _check_pixels(sc, out, _sample_pixels(rng, 1920, 1080, 128, crop=(760, 340, 400, 400)), cov3d=cov)
+    _check_pixels(sc, out, _sample_pixels(rng, 1920, 1080, 128, crop=(760, 340, 400, 400)), cov3d=cov,
+                  tie_max=TIE_MAX["1080p"])
 
 
 def test_64_views_graph_autotuned(ctx):
@@ -142,7 +153,8 @@ def test_64_views_graph_autotuned(ctx):
     rng = np.random.default_rng(13)
     outn = ref.cpu().numpy()
     for c in (0, 42):
-        _check_pixels(sc, outn[c], _sample_pixels(rng, 800, 800, 64, crop=(250, 250, 300, 300)), cam_index=c)
+        _check_pixels(sc, outn[c], _sample_pixels(rng, 800, 800, 64, crop=(250, 250, 300, 300)), cam_index=c,
+                      tie_max=TIE_MAX["multiview"])
 
 
 def test_4k_mixed_precision(ctx):
@@ -162,10 +174,18 @@ def test_4k_mixed_precision(ctx):
         got = gids[gptr[t]:gptr[t + 1]]
         assert np.array_equal(got, ref), t
     # colours: the oracle on the bf16-rounded SH, error budget of the fp16 records
-    sc.gaussians.sh = torch.as_tensor(sc.gaussians.sh).to(torch.bfloat16).float().numpy()
     pix = _sample_pixels(rng, 3840, 2160, 128, crop=(1600, 800, 640, 560))
-    rgb, T, tie, _ = R.render_pixels(sc, pix)
     got = out[pix[:, 1], pix[:, 0]]
+    sh32 = sc.gaussians.sh
+    sc.gaussians.sh = torch.as_tensor(sh32).to(torch.bfloat16).float().numpy()
+    rgb, T, tie, _ = R.render_pixels(sc, pix)
     ok = ~tie
+    assert tie.mean() <= TIE_MAX["4k"], ("tie pixels", int(tie.sum()), len(tie))
     assert np.abs(got[:, :3] - rgb)[ok].max() < 2e-2
     assert np.abs(got[:, 3] - T)[ok].max() < 2e-2
+    # and the error of the whole mixed form (bf16 SH and fp16 records) against
+    # the fp64 oracle on the fp32 SH
+    sc.gaussians.sh = sh32
+    rgb, T, tie, _ = R.render_pixels(sc, pix)
+    ok = ~tie
+    assert np.abs(got[:, :3] - rgb)[ok].max() < 3e-2
