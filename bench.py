@@ -44,6 +44,10 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--n-gauss", type=int, default=1_000_000)
     p.add_argument("--no-forms", action="store_true", help="skip the multi-view / differentiable / mixed forms")
+    p.add_argument("--forms", default="all",
+                   help="comma list of the forms to run: multiview, differentiable (with soft edges), mixed, nested")
+    p.add_argument("--forms-only", action="store_true",
+                   help="run the selected forms only (no 1080p frame) and print their JSON")
     return p.parse_args()
 
 
@@ -137,9 +141,10 @@ def run_umgs(args, rank, world, local_rank):
     # mixed-precision form render on the host cores while the GPU works
     pool = crops = None
     workers = max(1, host_cores() - 2)
+    which = FORMS if args.forms == "all" else tuple(x.strip() for x in args.forms.split(","))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         pool = oracle_pool(workers)
-        if not args.no_forms:
+        if not args.no_forms and "mixed" in which:
             crops = CropOracle(pool, bands=max(1, workers // 4))
     import torch
     from paper_2601_19233_gb300 import build, umgs
@@ -149,6 +154,16 @@ def run_umgs(args, rank, world, local_rank):
         dist.init_process_group("nccl")
     build.build()
     K, Wm = args.steps, args.warmup
+    if args.forms_only:
+        dev = torch.device("cuda", local_rank)
+        ctx = umgs.Context(local_rank)
+        res = {"forms": run_forms(ctx, dev, max(3, min(20, K)), crops, which)}
+        if pool is not None:
+            pool.close()
+            pool.join()
+        if rank == 0:
+            print(json.dumps(res), flush=True)
+        return
     nframes = 100
     sc, disp = build_workload(args.n_gauss, nframes)
     dev = torch.device("cuda", local_rank)
@@ -382,7 +397,7 @@ def run_umgs(args, rank, world, local_rank):
         "clocks": clk,
     }
     if not args.no_forms:
-        res["forms"] = run_forms(ctx, dev, min(20, max(3, K // 6)), crops)
+        res["forms"] = run_forms(ctx, dev, min(20, max(3, K // 6)), crops, which)
     if pool is not None:
         res["cpu_baseline"] = cpu_baseline(pool, workers, sc)
         pool.close()
@@ -520,161 +535,186 @@ def _time(fn, steps, warm=2):
     return a.elapsed_time(b) / steps
 
 
-def run_forms(ctx, dev, steps, crops=None):
+FORMS = ("multiview", "differentiable", "mixed", "nested")
+
+
+def run_forms(ctx, dev, steps, crops=None, which=FORMS):
     import torch
     from paper_2601_19233_gb300 import scenes, umgs
     forms = {}
-    # config 2: 64 orbit views of 800x800, clustered Gaussians (uneven tile load)
-    sc = scenes.config2()
-    g = umgs.gaussians_to_device(sc.gaussians, dev)
-    ms = [umgs.mesh_to_device(m, dev) for m in sc.meshes]
-    nv = len(sc.cameras)
-    out = torch.empty((nv, 800, 800, 4), device=dev)
-    plain = umgs.render_opts(16)
-    fr = umgs.Frame(ctx)
-    t_plain = _time(lambda: umgs.render(ctx, g, ms, sc.cameras, plain, out=out, frame=fr), steps)
-    evals_plain = fr.evaluations()
-    # per-stage split of the plain render (a separate profiled pass)
-    umgs.profile_read(ctx)
-    umgs.profile_enable(ctx, True)
-    for _ in range(3):
-        umgs.render(ctx, g, ms, sc.cameras, plain, out=out, frame=fr)
-    torch.cuda.synchronize()
-    st_ms, st_n = umgs.profile_read(ctx)
-    umgs.profile_enable(ctx, False)
-    names = stage_names()
-    mv_stages = {names[k]: round(st_ms[k] / st_n[k], 3) for k in range(16) if st_n[k] > 0}
-    best, t_tune = umgs.autotune(ctx, g, ms, sc.cameras, plain, out)
-    fr2 = umgs.Frame(ctx)
-    # the scene and cameras are the same every replay: pair capacity = the
-    # sizing render's count (+ 4096), no 25% headroom
-    gr = umgs.Graph(ctx, fr2, g, ms, sc.cameras, best, out, key_headroom=1.0)
-    t_graph = _time(lambda: gr.launch(), steps)
-    gr.check()
-    forms["multiview_64x800"] = {
-        "workload": "64 orbit views 800x800, 500k Gaussians SH3 (70% in 3 blobs) + 100k-face torus",
-        "plain_views_per_s": round(nv * 1e3 / t_plain, 1), "plain_ms": round(t_plain, 3),
-        "graph_views_per_s": round(nv * 1e3 / t_graph, 1), "graph_ms": round(t_graph, 3),
-        "autotuned": {"tile_size": best.tile_size, "sched": best.sched, "split": best.split, "ms": round(t_tune, 3)},
-        "keys": int(fr.counts()[0]), "evaluations": int(evals_plain), "plain_stages_ms": mv_stages}
-    del gr, fr, fr2, out, g, ms
-    torch.cuda.empty_cache()
-    # config 3: 8 views of 512x512, forward vs forward+backward (L2 loss to a
-    # render of a perturbed copy of the scene)
-    sc = scenes.config3()
-    rng = np.random.default_rng(7)
-    pert = scenes.config3()
-    pert.gaussians.means = (pert.gaussians.means + rng.normal(0, 0.01, pert.gaussians.means.shape)).astype(np.float32)
-    pert.gaussians.sh = (pert.gaussians.sh + rng.normal(0, 0.05, pert.gaussians.sh.shape)).astype(np.float32)
-    g = umgs.gaussians_to_device(sc.gaussians, dev)
-    ms = [umgs.mesh_to_device(m, dev) for m in sc.meshes]
-    gp = umgs.gaussians_to_device(pert.gaussians, dev)
-    nv = len(sc.cameras)
-    target = umgs.render(ctx, gp, ms, sc.cameras, umgs.render_opts(16)).clone()
-    out = torch.empty_like(target)
-    fr = umgs.Frame(ctx)
-    t_f = _time(lambda: umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(16), out=out, frame=fr), steps)
-    so = umgs.render_opts(16, save=True)
+    if "multiview" in which:
+        # config 2: 64 orbit views of 800x800, clustered Gaussians (uneven tile load)
+        sc = scenes.config2()
+        g = umgs.gaussians_to_device(sc.gaussians, dev)
+        ms = [umgs.mesh_to_device(m, dev) for m in sc.meshes]
+        nv = len(sc.cameras)
+        out = torch.empty((nv, 800, 800, 4), device=dev)
+        plain = umgs.render_opts(16)
+        fr = umgs.Frame(ctx)
+        t_plain = _time(lambda: umgs.render(ctx, g, ms, sc.cameras, plain, out=out, frame=fr), steps)
+        evals_plain = fr.evaluations()
+        # per-stage split of the plain render (a separate profiled pass)
+        umgs.profile_read(ctx)
+        umgs.profile_enable(ctx, True)
+        for _ in range(3):
+            umgs.render(ctx, g, ms, sc.cameras, plain, out=out, frame=fr)
+        torch.cuda.synchronize()
+        st_ms, st_n = umgs.profile_read(ctx)
+        umgs.profile_enable(ctx, False)
+        names = stage_names()
+        mv_stages = {names[k]: round(st_ms[k] / st_n[k], 3) for k in range(16) if st_n[k] > 0}
+        # the per-tile work split alone, at each length the autotuner tries
+        split_ms = {str(sp): round(_time(lambda: umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(16, split=sp),
+                                                             out=out, frame=fr), steps), 3)
+                    for sp in (512, 1024, 2048)}
+        best, t_tune = umgs.autotune(ctx, g, ms, sc.cameras, plain, out)
+        fr2 = umgs.Frame(ctx)
+        # the scene and cameras are the same every replay: pair capacity = the
+        # sizing render's count (+ 4096), no 25% headroom
+        gr = umgs.Graph(ctx, fr2, g, ms, sc.cameras, best, out, key_headroom=1.0)
+        t_graph = _time(lambda: gr.launch(), steps)
+        gr.check()
+        forms["multiview_64x800"] = {
+            "workload": "64 orbit views 800x800, 500k Gaussians SH3 (70% in 3 blobs) + 100k-face torus",
+            "plain_views_per_s": round(nv * 1e3 / t_plain, 1), "plain_ms": round(t_plain, 3),
+            "graph_views_per_s": round(nv * 1e3 / t_graph, 1), "graph_ms": round(t_graph, 3),
+            "split_ms": split_ms,
+            "autotuned": {"tile_size": best.tile_size, "sched": best.sched, "split": best.split, "ms": round(t_tune, 3)},
+            "keys": int(fr.counts()[0]), "evaluations": int(evals_plain), "plain_stages_ms": mv_stages}
+        del gr, fr, fr2, out, g, ms
+        torch.cuda.empty_cache()
+    if "differentiable" in which:
+        # config 3: 8 views of 512x512, forward vs forward+backward (L2 loss to a
+        # render of a perturbed copy of the scene)
+        sc = scenes.config3()
+        rng = np.random.default_rng(7)
+        pert = scenes.config3()
+        pert.gaussians.means = (pert.gaussians.means + rng.normal(0, 0.01, pert.gaussians.means.shape)).astype(np.float32)
+        pert.gaussians.sh = (pert.gaussians.sh + rng.normal(0, 0.05, pert.gaussians.sh.shape)).astype(np.float32)
+        g = umgs.gaussians_to_device(sc.gaussians, dev)
+        ms = [umgs.mesh_to_device(m, dev) for m in sc.meshes]
+        gp = umgs.gaussians_to_device(pert.gaussians, dev)
+        nv = len(sc.cameras)
+        target = umgs.render(ctx, gp, ms, sc.cameras, umgs.render_opts(16)).clone()
+        out = torch.empty_like(target)
+        fr = umgs.Frame(ctx)
+        t_f = _time(lambda: umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(16), out=out, frame=fr), steps)
+        so = umgs.render_opts(16, save=True)
 
-    def fb():
-        umgs.render(ctx, g, ms, sc.cameras, so, out=out, frame=fr)
-        dl = (2.0 / out.numel()) * (out - target)
-        return umgs.render_backward(ctx, fr, g, ms, dl)
-    t_fb = _time(fb, steps)
-    keys_bin = int(fr.counts()[0])
-    forms["differentiable_8x512"] = {
-        "workload": "8 orbit views 512x512, 300k Gaussians SH3 + 50k-face torus, L2 loss to a perturbed-scene render",
-        "fwd_views_per_s": round(nv * 1e3 / t_f, 1), "fwd_ms": round(t_f, 3),
-        "fwd_bwd_views_per_s": round(nv * 1e3 / t_fb, 1), "fwd_bwd_ms": round(t_fb, 3)}
-    # the same step with soft-edge triangle coverage (sigma 0.5 px): the
-    # backward also reaches the vertex positions through coverage
-    sig = 0.5
-    t_sf = _time(lambda: umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(16, edge_sigma=sig), out=out, frame=fr),
-                 steps)
-    keys_soft = int(fr.counts()[0])
-    so_soft = umgs.render_opts(16, save=True, edge_sigma=sig)
+        def fb():
+            umgs.render(ctx, g, ms, sc.cameras, so, out=out, frame=fr)
+            dl = (2.0 / out.numel()) * (out - target)
+            return umgs.render_backward(ctx, fr, g, ms, dl)
+        t_fb = _time(fb, steps)
+        keys_bin = int(fr.counts()[0])
+        forms["differentiable_8x512"] = {
+            "workload": "8 orbit views 512x512, 300k Gaussians SH3 + 50k-face torus, L2 loss to a perturbed-scene render",
+            "fwd_views_per_s": round(nv * 1e3 / t_f, 1), "fwd_ms": round(t_f, 3),
+            "fwd_bwd_views_per_s": round(nv * 1e3 / t_fb, 1), "fwd_bwd_ms": round(t_fb, 3)}
+        # the same step with soft-edge triangle coverage (sigma 0.5 px): the
+        # backward also reaches the vertex positions through coverage
+        sig = 0.5
+        t_sf = _time(lambda: umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(16, edge_sigma=sig), out=out, frame=fr),
+                     steps)
+        keys_soft = int(fr.counts()[0])
+        so_soft = umgs.render_opts(16, save=True, edge_sigma=sig)
 
-    def fb_soft():
-        umgs.render(ctx, g, ms, sc.cameras, so_soft, out=out, frame=fr)
-        dl = (2.0 / out.numel()) * (out - target)
-        return umgs.render_backward(ctx, fr, g, ms, dl)
-    t_sfb = _time(fb_soft, steps)
-    forms["soft_edge_8x512"] = {
-        "workload": "differentiable_8x512 with soft-edge triangle coverage, edge_sigma 0.5 px (rects widened 4 px)",
-        "fwd_views_per_s": round(nv * 1e3 / t_sf, 1), "fwd_ms": round(t_sf, 3),
-        "fwd_bwd_views_per_s": round(nv * 1e3 / t_sfb, 1), "fwd_bwd_ms": round(t_sfb, 3),
-        "keys": keys_soft, "keys_binary_coverage": keys_bin}
-    del g, ms, gp, target, out, fr
-    torch.cuda.empty_cache()
-    # config 4: 4K, 6M Gaussians + 2M triangles, fp32 vs bf16 SH + fp16 records
-    sc = scenes.config4()
-    g32 = umgs.gaussians_to_device(sc.gaussians, dev)
-    g16 = umgs.gaussians_to_device(sc.gaussians, dev, sh_dtype=torch.bfloat16)
-    ms = [umgs.mesh_to_device(m, dev) for m in sc.meshes]
-    out32 = torch.empty((1, 2160, 3840, 4), device=dev)
-    out16 = torch.empty_like(out32)
-    fr = umgs.Frame(ctx)
-    t32 = _time(lambda: umgs.render(ctx, g32, ms, sc.cameras, umgs.render_opts(16), out=out32, frame=fr), steps)
-    keys4 = fr.counts()[0]
-    t16 = _time(lambda: umgs.render(ctx, g16, ms, sc.cameras, umgs.render_opts(16, mixed=True), out=out16, frame=fr),
-                steps)
-    d = (out16[..., :3] - out32[..., :3]).abs().flatten()
-    mse = float(((out16[..., :3] - out32[..., :3]) ** 2).mean())
-    forms["mixed_4k"] = {
-        "workload": "3840x2160, 6M Gaussians SH3 + 2M-face torus (30% transparent)",
-        "fp32_frames_per_s": round(1e3 / t32, 2), "fp32_ms": round(t32, 3),
-        "mixed_frames_per_s": round(1e3 / t16, 2), "mixed_ms": round(t16, 3), "keys": int(keys4),
-        "mixed_vs_fp32": {"max_abs": float(d.max()), "p99_9": float(torch.quantile(d[::7].float(), 0.999)),
-                          "psnr_db": round(10 * math.log10(1.0 / max(mse, 1e-20)), 2)}}
-    if crops is not None:
-        # fp64 oracle (fp32 SH, not rounded to bf16) on 4 crops: the error of
-        # the mixed form against the exact composite, and of the fp32 form
-        img16 = out16[0, ..., :3].cpu().numpy().astype(np.float64)
-        img32 = out32[0, ..., :3].cpu().numpy().astype(np.float64)
-        ref, wall = crops.result()
-        forms["mixed_4k"]["vs_fp64_oracle"] = {
-            "crops": "%d crops of %dx%d (centre + 3 seeded positions)" % (len(ref), CROP, CROP),
-            "mixed": crop_errors(ref, img16), "fp32": crop_errors(ref, img32), "oracle_wall_s": round(wall, 1)}
-    del g32, g16, ms, out32, out16, fr
-    torch.cuda.empty_cache()
-    # nested transparency (Fig. 5b): Gaussians and an opaque ball inside a
-    # transparent sphere, single pass vs the separate-pass baseline (the two
-    # representations rendered apart with their expected depths and
-    # composited per pixel by depth); errors against the single pass, which
-    # the tests hold to the oracle
-    sc, ga, me = scenes.nested_scene(size=1024, n_gauss=400_000, bowl_subdiv=5)
-    bg = (0.05, 0.05, 0.08)
-    g = umgs.gaussians_to_device(sc.gaussians, dev)
-    ms = [umgs.mesh_to_device(m, dev) for m in sc.meshes]
-    one = torch.empty((1, 1024, 1024, 4), device=dev)
-    la, lb = torch.empty_like(one), torch.empty_like(one)
-    fa, fb_, fr = umgs.Frame(ctx), umgs.Frame(ctx), umgs.Frame(ctx)
-    depth_opts = umgs.render_opts(16, depth=True)
-    da = torch.empty((1, 1024, 1024), device=dev)
-    db = torch.empty_like(da)
-    sep = torch.empty_like(one)
+        def fb_soft():
+            umgs.render(ctx, g, ms, sc.cameras, so_soft, out=out, frame=fr)
+            dl = (2.0 / out.numel()) * (out - target)
+            return umgs.render_backward(ctx, fr, g, ms, dl)
+        t_sfb = _time(fb_soft, steps)
+        forms["soft_edge_8x512"] = {
+            "workload": "differentiable_8x512 with soft-edge triangle coverage, edge_sigma 0.5 px (rects widened 4 px)",
+            "fwd_views_per_s": round(nv * 1e3 / t_sf, 1), "fwd_ms": round(t_sf, 3),
+            "fwd_bwd_views_per_s": round(nv * 1e3 / t_sfb, 1), "fwd_bwd_ms": round(t_sfb, 3),
+            "keys": keys_soft, "keys_binary_coverage": keys_bin}
+        del g, ms, gp, target, out, fr
+        torch.cuda.empty_cache()
+    if "mixed" in which:
+        # config 4: 4K, 6M Gaussians + 2M triangles, fp32 vs bf16 SH + fp16 records
+        sc = scenes.config4()
+        g32 = umgs.gaussians_to_device(sc.gaussians, dev)
+        g16 = umgs.gaussians_to_device(sc.gaussians, dev, sh_dtype=torch.bfloat16)
+        ms = [umgs.mesh_to_device(m, dev) for m in sc.meshes]
+        out32 = torch.empty((1, 2160, 3840, 4), device=dev)
+        out16 = torch.empty_like(out32)
+        fr = umgs.Frame(ctx)
+        t32 = _time(lambda: umgs.render(ctx, g32, ms, sc.cameras, umgs.render_opts(16), out=out32, frame=fr), steps)
+        keys4 = fr.counts()[0]
+        t16 = _time(lambda: umgs.render(ctx, g16, ms, sc.cameras, umgs.render_opts(16, mixed=True), out=out16, frame=fr),
+                    steps)
+        # per-stage split of both renders and the frame counters (a separate profiled pass)
+        st4 = {}
+        for name, gg, oo, mixed in (("fp32", g32, out32, False), ("mixed", g16, out16, True)):
+            umgs.profile_read(ctx)
+            umgs.profile_enable(ctx, True)
+            umgs.render(ctx, gg, ms, sc.cameras, umgs.render_opts(16, mixed=mixed), out=oo, frame=fr)
+            torch.cuda.synchronize()
+            st_ms, st_n = umgs.profile_read(ctx)
+            umgs.profile_enable(ctx, False)
+            st4[name] = {stage_names()[k]: round(st_ms[k] / st_n[k], 3) for k in range(16) if st_n[k] > 0}
+        stats4 = fr.stats()
+        d = (out16[..., :3] - out32[..., :3]).abs().flatten()
+        mse = float(((out16[..., :3] - out32[..., :3]) ** 2).mean())
+        forms["mixed_4k"] = {
+            "workload": "3840x2160, 6M Gaussians SH3 + 2M-face torus (30% transparent)",
+            "fp32_frames_per_s": round(1e3 / t32, 2), "fp32_ms": round(t32, 3),
+            "mixed_frames_per_s": round(1e3 / t16, 2), "mixed_ms": round(t16, 3), "keys": int(keys4),
+            "mixed_vs_fp32": {"max_abs": float(d.max()), "p99_9": float(torch.quantile(d[::7].float(), 0.999)),
+                              "psnr_db": round(10 * math.log10(1.0 / max(mse, 1e-20)), 2)},
+            "stages_ms": st4, "fp64_conics": stats4["fp64_conics"],
+            "evaluations": {"gaussian": stats4["gaussian_evals"], "triangle": stats4["triangle_evals"]}}
+        if crops is not None:
+            # fp64 oracle (fp32 SH, not rounded to bf16) on 4 crops: the error of
+            # the mixed form against the exact composite, and of the fp32 form
+            img16 = out16[0, ..., :3].cpu().numpy().astype(np.float64)
+            img32 = out32[0, ..., :3].cpu().numpy().astype(np.float64)
+            ref, wall = crops.result()
+            forms["mixed_4k"]["vs_fp64_oracle"] = {
+                "crops": "%d crops of %dx%d (centre + 3 seeded positions)" % (len(ref), CROP, CROP),
+                "mixed": crop_errors(ref, img16), "fp32": crop_errors(ref, img32), "oracle_wall_s": round(wall, 1)}
+        del g32, g16, ms, out32, out16, fr
+        torch.cuda.empty_cache()
+    if "nested" in which:
+        # nested transparency (Fig. 5b): Gaussians and an opaque ball inside a
+        # transparent sphere, single pass vs the separate-pass baseline (the two
+        # representations rendered apart with their expected depths and
+        # composited per pixel by depth); errors against the single pass, which
+        # the tests hold to the oracle
+        sc, ga, me = scenes.nested_scene(size=1024, n_gauss=400_000, bowl_subdiv=5)
+        bg = (0.05, 0.05, 0.08)
+        g = umgs.gaussians_to_device(sc.gaussians, dev)
+        ms = [umgs.mesh_to_device(m, dev) for m in sc.meshes]
+        one = torch.empty((1, 1024, 1024, 4), device=dev)
+        la, lb = torch.empty_like(one), torch.empty_like(one)
+        fa, fb_, fr = umgs.Frame(ctx), umgs.Frame(ctx), umgs.Frame(ctx)
+        depth_opts = umgs.render_opts(16, depth=True)
+        da = torch.empty((1, 1024, 1024), device=dev)
+        db = torch.empty_like(da)
+        sep = torch.empty_like(one)
 
-    def separate():
-        umgs.render(ctx, g, [], sc.cameras, depth_opts, out=la, frame=fa)
-        umgs.render(ctx, None, ms, sc.cameras, depth_opts, out=lb, frame=fb_)
-        lib = umgs.lib()
-        ctx.check(lib.umgs_frame_depth(fa._h, umgs._ptr(da), umgs._stream()), "umgs_frame_depth")
-        ctx.check(lib.umgs_frame_depth(fb_._h, umgs._ptr(db), umgs._stream()), "umgs_frame_depth")
-        umgs.composite_layers(ctx, la, da, lb, db, bg=bg, out=sep)
-    t_one = _time(lambda: umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(16, bg=bg), out=one, frame=fr), steps)
-    t_sep = _time(separate, steps)
-    d = (sep[..., :3] - one[..., :3]).abs()
-    seen = (one[..., 3] < 0.999)  # pixels where something is blended
-    mse = float(((sep[..., :3] - one[..., :3]) ** 2)[seen].mean())
-    forms["nested_transparency_1024"] = {
-        "workload": "1024x1024, 400k Gaussians (3 boxes) + opaque 320-face ball inside a transparent "
-                    "20,480-face sphere (alpha 0.35)",
-        "single_pass_ms": round(t_one, 3), "separate_pass_ms": round(t_sep, 3),
-        "separate_vs_single": {"max_abs": round(float(d.max()), 4),
-                               "pixels_off_by_0.01": round(float((d.amax(-1) > 0.01).float()[seen].mean()), 4),
-                               "psnr_db_blended_pixels": round(10 * math.log10(1.0 / max(mse, 1e-20)), 2)}}
-    del g, ms, one, la, lb, fa, fb_, fr, da, db, sep
-    torch.cuda.empty_cache()
+        def separate():
+            umgs.render(ctx, g, [], sc.cameras, depth_opts, out=la, frame=fa)
+            umgs.render(ctx, None, ms, sc.cameras, depth_opts, out=lb, frame=fb_)
+            lib = umgs.lib()
+            ctx.check(lib.umgs_frame_depth(fa._h, umgs._ptr(da), umgs._stream()), "umgs_frame_depth")
+            ctx.check(lib.umgs_frame_depth(fb_._h, umgs._ptr(db), umgs._stream()), "umgs_frame_depth")
+            umgs.composite_layers(ctx, la, da, lb, db, bg=bg, out=sep)
+        t_one = _time(lambda: umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(16, bg=bg), out=one, frame=fr), steps)
+        t_sep = _time(separate, steps)
+        d = (sep[..., :3] - one[..., :3]).abs()
+        seen = (one[..., 3] < 0.999)  # pixels where something is blended
+        mse = float(((sep[..., :3] - one[..., :3]) ** 2)[seen].mean())
+        forms["nested_transparency_1024"] = {
+            "workload": "1024x1024, 400k Gaussians (3 boxes) + opaque 320-face ball inside a transparent "
+                        "20,480-face sphere (alpha 0.35)",
+            "single_pass_ms": round(t_one, 3), "separate_pass_ms": round(t_sep, 3),
+            "separate_vs_single": {"max_abs": round(float(d.max()), 4),
+                                   "pixels_off_by_0.01": round(float((d.amax(-1) > 0.01).float()[seen].mean()), 4),
+                                   "psnr_db_blended_pixels": round(10 * math.log10(1.0 / max(mse, 1e-20)), 2)}}
+        del g, ms, one, la, lb, fa, fb_, fr, da, db, sep
+        torch.cuda.empty_cache()
     return forms
 
 

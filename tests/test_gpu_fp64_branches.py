@@ -1,7 +1,7 @@
 """The two fp64 branches of the GPU path, forced and checked against the oracle.
 
 * Near-singular projected covariances (EWA projection, Sec. 3.2): a conic
-  whose 2x2 determinant is below a*c/1024 is inverted in fp64.  Long, thin
+  whose 2x2 determinant is below a*c/128 is inverted in fp64.  Long, thin
   needle Gaussians seen obliquely reach that branch; their keys must stay
   bit-exact and their images within 2e-4 of the fp64 oracle, and the frame's
   fp64 conic counter reports how many (camera, Gaussian) records took it.
