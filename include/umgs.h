@@ -261,9 +261,12 @@ umgs_status umgs_composite_layers(umgs_ctx* ctx, const float* a_rgbt, const floa
                                   void* stream);
 
 /* Synchronises `stream` and reports the device-side conditions of the last
- * asynchronous render into `frame`: CAPACITY if it needed more pairs than
- * the reserved capacity (that render composited no tile: background, T = 1;
- * reserve more and render again), INVALID_ARG for an out-of-range face index. */
+ * render into `frame`: CAPACITY if it needed more pairs than the reserved
+ * capacity (that render composited no tile: background, T = 1; reserve more
+ * and render again), INVALID_ARG for an out-of-range face index, TIMEOUT if
+ * a wait of the binning stage's single-sweep kernels (a block waiting for
+ * the prefix published by the blocks before it, bounded to about 2^20 polls)
+ * gave up; its lists are then not valid. */
 umgs_status umgs_frame_check(umgs_frame* frame, void* stream);
 
 /* Number of (pixel, fragment) evaluations of the last render into `frame`:

@@ -37,6 +37,11 @@ unsnapped projected triangle, so that the composite is differentiable in the
 vertex positions through coverage.  A triangle is a fragment of every pixel
 of its pixel rect widened by ceil(8 sigma) pixels; Eq. 7-9 are unchanged with
 c in place of o (they reduce to the binary form when every c is 0 or 1).
+
+Tie decisions (test reading; pinned in tests/test_oracle_ties.py): a
+Gaussian's alpha within 1e-6 of 1/255, or T within 0.1% of t_eps, is a
+decision the fp32 kernels may take the other way.  The composite flags them,
+and composite_alternatives composites the pixel with each taken either way.
 """
 from __future__ import annotations
 
@@ -305,14 +310,17 @@ class Frame:
 # ----------------------------------------------------------------------------
 # the composite itself
 
-def composite(frags, mode=FULL, t_eps=T_EPS, t_product=False, bg=(0.0, 0.0, 0.0)):
+def composite(frags, mode=FULL, t_eps=T_EPS, t_product=False, bg=(0.0, 0.0, 0.0), choices=None):
     """Composite a depth-ordered fragment list of one pixel.
 
     Returns dict: color (3, background included), T (final transmittance),
     weights (list of (id, weight)), depth (sum_i w_i z_i / sum_i w_i over the
     blended fragments, +inf when none), tie (True when a decision sits within
     rounding distance of a threshold: |alpha - 1/255| < 1e-6 or
-    |T - t_eps| < 1e-3 t_eps), n (fragments consumed).
+    |T - t_eps| < 1e-3 t_eps), n (fragments consumed), decisions (the outcome
+    taken at each such tie decision, in order: True = the Gaussian is blended
+    / the pixel stops).  choices: outcomes to take at the first len(choices)
+    tie decisions instead of the fp64 comparison (composite_alternatives).
     """
     C = np.zeros(3)
     T = 1.0
@@ -323,13 +331,23 @@ def composite(frags, mode=FULL, t_eps=T_EPS, t_product=False, bg=(0.0, 0.0, 0.0)
     weights = []
     tie = False
     n = 0
+    taken = []
+
+    def decide(outcome):
+        if choices is not None and len(taken) < len(choices):
+            outcome = bool(choices[len(taken)])
+        taken.append(outcome)
+        return outcome
+
     for f in frags:
         n += 1
         if f["kind"] == "g":
             a = f["alpha"]
+            keep = a >= ALPHA_MIN
             if abs(a - ALPHA_MIN) < 1e-6:
                 tie = True
-            if a < ALPHA_MIN:
+                keep = decide(keep)
+            if not keep:
                 continue
             w = T * a
             C += w * f["color"]
@@ -383,22 +401,46 @@ def composite(frags, mode=FULL, t_eps=T_EPS, t_product=False, bg=(0.0, 0.0, 0.0)
                 else:
                     T = T_in * float(t.sum()) / 4.0
         if t_eps is not None:
+            stop = T < t_eps
             if abs(T - t_eps) < 1e-3 * t_eps:
                 tie = True
-            if T < t_eps:
+                stop = decide(stop)
+            if stop:
                 break
     C = C + T * np.asarray(bg, np.float64)
     # expected depth of the blended fragments: sum w z / sum w (+inf if none)
     zmap = {f["id"]: f.get("z", np.nan) for f in frags}
     wsum = sum(w for _, w in weights)
     depth = sum(w * zmap[i] for i, w in weights) / wsum if wsum > 0 else np.inf
-    return dict(color=C, T=T, weights=weights, tie=tie, n=n, depth=depth)
+    return dict(color=C, T=T, weights=weights, tie=tie, n=n, depth=depth, decisions=taken)
+
+
+def composite_alternatives(frags, mode=FULL, t_eps=T_EPS, t_product=False, bg=(0.0, 0.0, 0.0), max_runs=64):
+    """Every result the composite of one pixel can have when each tie
+    decision (a fragment's alpha within rounding distance of 1/255, or T of
+    t_eps) may go either way: a decision taken in fp32 by the kernels can land
+    on the other side of the threshold than the fp64 one here.  Depth-first
+    over the decision outcomes (a flipped decision can change which decisions
+    follow it); at most max_runs composites.  Returns [n_alt, 4] (RGB, T),
+    the fp64 outcome first."""
+    out = []
+    stack = [[]]
+    while stack and len(out) < max_runs:
+        c = stack.pop()
+        r = composite(frags, mode, t_eps, t_product, bg, choices=c)
+        out.append(np.r_[r["color"], r["T"]])
+        d = r["decisions"]
+        for i in range(len(c), len(d)):
+            stack.append(d[:i] + [not d[i]])
+    return np.array(out)
 
 
 def render_pixels(scene, pixels, cam_index=0, mode=FULL, t_eps=T_EPS, t_product=False,
-                  bg=(0.0, 0.0, 0.0), cov3d=None, frame=None, soft=None):
+                  bg=(0.0, 0.0, 0.0), cov3d=None, frame=None, soft=None, alts=None):
     """Composite an explicit list of pixels [(x, y), ...] by brute-force gather
-    over all primitives.  Returns (rgb [K,3], T [K], tie [K], wsum [K])."""
+    over all primitives.  Returns (rgb [K,3], T [K], tie [K], wsum [K]).
+    alts: a dict that receives, for every tie pixel k, its
+    composite_alternatives [n_alt, 4]."""
     fr = frame or Frame(scene, cam_index, cov3d, soft)
     K = len(pixels)
     rgb = np.zeros((K, 3))
@@ -406,11 +448,14 @@ def render_pixels(scene, pixels, cam_index=0, mode=FULL, t_eps=T_EPS, t_product=
     tie = np.zeros(K, bool)
     wsum = np.zeros(K)
     for k, (x, y) in enumerate(pixels):
-        r = composite(fr.fragments_at(int(x), int(y)), mode, t_eps, t_product, bg)
+        frags = fr.fragments_at(int(x), int(y))
+        r = composite(frags, mode, t_eps, t_product, bg)
         rgb[k] = r["color"]
         T[k] = r["T"]
         tie[k] = r["tie"]
         wsum[k] = sum(w for _, w in r["weights"])
+        if alts is not None and r["tie"]:
+            alts[k] = composite_alternatives(frags, mode, t_eps, t_product, bg)
     return rgb, T, tie, wsum
 
 
@@ -420,7 +465,8 @@ def render_image(scene, cam_index=0, mode=FULL, t_eps=T_EPS, t_product=False,
     pair is evaluated, pairs are grouped per pixel, ordered by (depth bits,
     id) and composited.  Returns dict rgb [H,W,3], T [H,W], tie [H,W],
     wsum [H,W], nfrag [H,W], depth [H,W] (expected depth, +inf where nothing
-    blends).  soft: soft-edge width sigma in pixels (FULL mode only).
+    blends), alts (for every tie pixel, by flat index y*W + x, its
+    composite_alternatives [n_alt, 4]).  soft: soft-edge width sigma in pixels (FULL mode only).
     window: (x0, x1, y0, y1), inclusive: only the pixels of that rectangle are
     composited (the rect of every primitive is cut to it); the others keep
     the background and T = 1."""
@@ -454,6 +500,7 @@ def render_image(scene, cam_index=0, mode=FULL, t_eps=T_EPS, t_product=False,
     out_n = np.zeros(H * W, np.int64)
     out_d = np.full(H * W, np.inf)
     sig = []
+    alts = {}
     bgv = np.asarray(bg, np.float64)
     out_rgb[:] = bgv
     bounds = np.nonzero(np.diff(np.concatenate([[-1], pix, [-2]])))[0]
@@ -464,6 +511,8 @@ def render_image(scene, cam_index=0, mode=FULL, t_eps=T_EPS, t_product=False,
         out_rgb[p] = res["color"]
         out_T[p] = res["T"]
         out_tie[p] = res["tie"]
+        if res["tie"]:
+            alts[p] = composite_alternatives(frags, mode, t_eps, t_product, bg)
         out_ws[p] = sum(x for _, x in res["weights"])
         out_n[p] = len(frags)
         out_d[p] = res["depth"]
@@ -471,7 +520,7 @@ def render_image(scene, cam_index=0, mode=FULL, t_eps=T_EPS, t_product=False,
                     tuple(f.get("mask", -1) for f in frags[:res["n"]])))
     return dict(rgb=out_rgb.reshape(H, W, 3), T=out_T.reshape(H, W), tie=out_tie.reshape(H, W),
                 wsum=out_ws.reshape(H, W), nfrag=out_n.reshape(H, W), depth=out_d.reshape(H, W),
-                sig=hash(tuple(sig)))
+                sig=hash(tuple(sig)), alts=alts)
 
 
 def evaluation_count(scene, cam_index=0, mode=FULL, t_eps=T_EPS, frame=None):

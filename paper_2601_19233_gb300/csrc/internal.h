@@ -37,12 +37,13 @@ struct umgs_frame {
     umgs_ctx* ctx = nullptr;
     int device = 0;  // the context's device (umgs_frame_destroy may outlive the context)
     umgs::DevBuf cams, grec, trec, bin, tile_off;
-    // binning: record depth keys/values (+ ping-pong), per-record region
-    // counts and offsets, (region, id) pairs (+ ping-pong), radix histograms,
-    // scan sums; per region its first pair, chunk count and first chunk; per
+    // binning: record depth keys/values (+ ping-pong), (region, id) pairs
+    // (+ ping-pong), radix histograms and scan sums (the persistent
+    // compositor's tile-order sort); per region its first pair, chunk count and first chunk; per
     // chunk and region tile the count and the count of earlier chunks; per
     // tile its list length and first entry; the tile lists
-    umgs::DevBuf pk, pv, pk2, pv2, pcnt, poff, tk, tv, tk2, tv2, rs_hist, rs_hist2, rs_bsum;
+    umgs::DevBuf pk, pv, pk2, pv2, tk, tv, tk2, tv2, rs_hist, rs_hist2, rs_bsum;
+    umgs::DevBuf lb_a, lb_b, lb_e, lb_s;  // look-back words: radix passes (alternating), emission, tile scan
     umgs::DevBuf rg_start, rg_nchunk, rg_coff, rg_ccnt, rg_cpre, tl_cnt, tl_off, tl_ids;
     uint32_t* ids = nullptr;    // tile lists: unified ids (tl_ids)
     umgs::DevBuf last, status;
@@ -73,9 +74,9 @@ struct umgs_frame {
     bool valid = false;
     std::vector<int64_t> mesh_offset;  // unified id of each mesh's first face
     void release() {
-        for (auto* b : {&cams, &grec, &trec, &bin, &tile_off, &pk, &pv, &pk2, &pv2, &pcnt, &poff, &tk, &tv, &tk2, &tv2,
+        for (auto* b : {&cams, &grec, &trec, &bin, &tile_off, &pk, &pv, &pk2, &pv2, &tk, &tv, &tk2, &tv2,
                         &rs_hist, &rs_hist2, &rs_bsum, &rg_start, &rg_nchunk, &rg_coff, &rg_ccnt, &rg_cpre, &tl_cnt,
-                        &tl_off, &tl_ids,
+                        &tl_off, &tl_ids, &lb_a, &lb_b, &lb_e, &lb_s,
                         &last, &status, &tfin, &ntri, &stack, &depth, &textab, &ggrad, &tgrad, &rerun_out, &fix_list, &ord_k, &ord_v,
                         &ord_k2, &ord_v2, &split_items, &segbuf, &seglast})
             b->release();
@@ -197,6 +198,11 @@ cudaError_t reserve_binning(umgs_frame* fr, int64_t rcap, int64_t kcap);
 cudaError_t radix_sort_pairs(umgs_frame* fr, uint32_t* k, uint32_t* v, uint32_t* k2, uint32_t* v2,
                              const uint32_t* n_dev, int64_t n_cap, int bits, uint32_t** rk, uint32_t** rv,
                              cudaStream_t s, int lo = 0, const uint32_t* key_mm = nullptr);
+// single-sweep passes of the binning stage's radix sorts (render.cu)
+cudaError_t onesweep_sort(umgs_frame* fr, uint32_t* k, uint32_t* v, uint32_t* k2, uint32_t* v2,
+                          const uint32_t* n_dev, int64_t n_cap, int lo, int npass, uint32_t* ghist,
+                          uint32_t* counters, const uint32_t* mm, const uint32_t* n_culled, uint32_t* err,
+                          cudaStream_t s);
 
 umgs_status render_backward(umgs_ctx* ctx, umgs_frame* fr, const umgs_gaussians* g, const umgs_mesh* meshes,
                             int32_t nmeshes, const float* dL_drgbt, const umgs_gaussian_grads* gg,
@@ -210,7 +216,14 @@ umgs_status frame_stats(const umgs_frame* fr, umgs_frame_stats* out, cudaStream_
 constexpr int kStatusEvalWords = 16 + 2 * 32;
 // then the work split's counters: work items, segment slots, persistent work counter
 constexpr int kStatusSplitWords = kStatusEvalWords + 4;
-constexpr int kStatusWords = kStatusSplitWords + 4;
+// then the binning stage's single-sweep kernels: tile counters (depth-sort
+// passes 0-3, region-sort passes, the pair emission, the tile scan), the
+// depth sort's 4 x 256 and the region sort's 3 x 256 digit counts
+constexpr int kStatusBinWords = kStatusSplitWords + 4;
+constexpr int kBinCounters = 16;
+constexpr int kBinRegionCounters = 4, kBinEmitCounter = 7, kBinScanCounter = 8;
+constexpr int kBinCulledWord = 15;  // (in the counter words) culled records of the depth sort
+constexpr int kStatusWords = kStatusBinWords + kBinCounters + 4 * 256 + 3 * 256;
 // buffers of a render with the per-tile work split for kcap tile-list entries
 cudaError_t reserve_split(umgs_frame* fr, int split, int64_t kcap);
 umgs_status frame_lists(const umgs_frame* fr, int64_t* tile_ptr, int32_t* ids, uint32_t* dbits,

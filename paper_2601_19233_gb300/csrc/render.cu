@@ -469,7 +469,6 @@ __global__ void __launch_bounds__(256) setup_triangles_kernel(
         t.const_alpha = const_alpha;
         t.tex = uv ? tex + 1 : 0;
         t.pad1 = 0;
-#pragma unroll
         t.rx = bi.rx;
         t.ry = bi.ry;
         t.pad2 = isig;  // soft-edge coverage: 1/edge_sigma (0: binary sample coverage)
@@ -477,9 +476,13 @@ __global__ void __launch_bounds__(256) setup_triangles_kernel(
     }
 }
 
-__global__ void zero_words_kernel(uint32_t* __restrict__ p, int n) {
+// The frame's status words (n) and the tile scan's look-back words (nq),
+// cleared at the start of every render.
+__global__ void zero_words_kernel(uint32_t* __restrict__ p, int n, uint64_t* __restrict__ q, int64_t nq) {
     pdl_enter();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = 0u;
+    const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = i0; i < n; i += stride) p[i] = 0u;
+    for (int64_t i = i0; i < nq; i += stride) q[i] = 0ull;
 }
 
 // ---------------------------------------------------------------------------
@@ -508,166 +511,323 @@ constexpr int64_t kMaxRegions = (int64_t)1 << (32 - kRectBits);
 constexpr int kRegionChunk = 2048;           // region pairs per count/fill block
 constexpr int kRegionThreads = 256;
 
-// Depth keys (0xffffffff for culled records) and, for the depth sort's key
-// map, ~min and max of the valid keys: one atomic pair per block into slot
-// blockIdx % kRadixMapSlots of mm (mm[2s] = ~min, mm[2s+1] = max; all start
-// at 0), so that no single address takes every block's update.
-__global__ void __launch_bounds__(256) prim_keys_kernel(const BinInfo* __restrict__ bin, int64_t n,
-                                                        uint32_t* __restrict__ pk, uint32_t* __restrict__ pv,
-                                                        uint32_t* __restrict__ n_dev, uint32_t* __restrict__ mm) {
+// Tiles and regions a record's tile rect meets (both 0 for a culled record).
+struct RecordRects {
+    int tx0, tx1, ty0, ty1;   // tile rect
+    int gx0, gy0, gw, gh;     // region rect
+};
+__device__ __forceinline__ RecordRects record_rects(const BinInfo& b, int ts) {
+    RecordRects r;
+    r.tx0 = (int)(b.rx & 0xffff) / ts; r.tx1 = (int)(b.rx >> 16) / ts;
+    r.ty0 = (int)(b.ry & 0xffff) / ts; r.ty1 = (int)(b.ry >> 16) / ts;
+    r.gx0 = r.tx0 / kRegionTX;
+    r.gy0 = r.ty0 / kRegionTY;
+    r.gw = r.tx1 / kRegionTX - r.gx0 + 1;
+    r.gh = r.ty1 / kRegionTY - r.gy0 + 1;
+    return r;
+}
+
+// Per (camera, primitive) record, in record order (grid-stride, one block
+// of 1024 threads per SM, so that a histogram bin takes one global atomic per
+// SM):
+// * the depth key (0xffffffff for culled records) and the record index,
+//   the inputs of the depth sort;
+// * for the depth sort's high digits (DepthDigits), ~min and max of the valid
+//   keys: one atomic pair per block into slot blockIdx % kRadixMapSlots of
+//   mm (mm[2s] = ~min, mm[2s+1] = max; all start at 0);
+// * the depth sort's digit counts that need no minimum: the low and second
+//   byte of every key (dhist[0..255], dhist[256..511]), the third byte of
+//   the valid keys (dhist[512..767]) and the number of culled records;
+// * the number of tiles and of regions the record's rect meets, summed
+//   (64-bit, one atomic per block) into *ktotal (the length of all tile
+//   lists together) and *rtotal (the number of (region, id) pairs);
+// * and the look-back words of the emission and of the depth sort's first
+//   pass cleared.
+__global__ void __launch_bounds__(1024) prim_keys_kernel(const BinInfo* __restrict__ bin, int64_t n, int64_t ntot,
+                                                         int ts, int regions_x, int regions_per_cam,
+                                                         uint32_t* __restrict__ pk, uint32_t* __restrict__ pv,
+                                                         uint32_t* __restrict__ n_dev, uint32_t* __restrict__ mm,
+                                                         uint32_t* __restrict__ dhist, uint32_t* __restrict__ n_culled,
+                                                         unsigned long long* __restrict__ ktotal,
+                                                         unsigned long long* __restrict__ rtotal,
+                                                         uint64_t* __restrict__ lbe, int64_t lbe_words,
+                                                         uint32_t* __restrict__ lb0, int64_t lb0_words) {
     pdl_enter();
-    __shared__ uint32_t s_mm[2][8];
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i == 0) *n_dev = (uint32_t)n;
-    uint32_t nmin = 0u, kmax = 0u;  // ~min, max over this thread's valid key
-    if (i < n) {
-        const BinInfo b = bin[i];
-        const uint32_t k = b.valid ? b.dbits : 0xffffffffu;
-        pk[i] = k;
-        pv[i] = (uint32_t)i;
-        if (b.valid) { nmin = ~k; kmax = k; }
+    constexpr int U = 4;  // records per thread and round, loaded together
+    __shared__ uint32_t s_mm[2][32];
+    __shared__ unsigned long long s_sum[2][32];
+    __shared__ uint32_t s_cul[32];
+    __shared__ uint32_t s_dh[3 * 256];
+    const int t = threadIdx.x;
+    for (int j = t; j < 3 * 256; j += blockDim.x) s_dh[j] = 0u;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + t;
+    if (i0 == 0) *n_dev = (uint32_t)n;
+    for (int64_t j = i0; j < lbe_words; j += stride) lbe[j] = 0ull;
+    for (int64_t j = i0; j < lb0_words; j += stride) lb0[j] = 0u;
+    __syncthreads();
+    uint32_t nmin = 0u, kmax = 0u, culled = 0u;  // ~min, max over this thread's valid keys
+    unsigned long long tiles = 0, regions = 0;
+    const int lane = t & 31;
+    for (int64_t r0 = i0; r0 - lane < n; r0 += U * stride) {  // (warp-uniform trip count)
+        BinInfo bb[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = r0 + u * stride;
+            if (i < n) bb[u] = bin[i];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t i = r0 + u * stride;
+            const bool live = i < n;
+            const bool valid = live && bb[u].valid;
+            const uint32_t k = valid ? bb[u].dbits : 0xffffffffu;
+            if (live) {
+                pk[i] = k;
+                pv[i] = (uint32_t)i;
+            }
+            // low and second byte: spread, plain atomics (culled records are
+            // counted below); third byte: clustered, one atomic per distinct
+            // value in the warp
+            if (valid) {
+                atomicAdd(&s_dh[k & 255u], 1u);
+                atomicAdd(&s_dh[256 + ((k >> 8) & 255u)], 1u);
+            }
+            const uint32_t d2 = (k >> 16) & 255u;
+            const unsigned peers = match_digit8(d2, valid);
+            if (valid && lane == __ffs(peers) - 1) atomicAdd(&s_dh[512 + d2], (uint32_t)__popc(peers));
+            culled += (live && !valid) ? 1u : 0u;
+            if (!valid) continue;
+            nmin = max(nmin, ~k);
+            kmax = max(kmax, k);
+            const RecordRects r = record_rects(bb[u], ts);
+            tiles += (unsigned long long)((r.tx1 - r.tx0 + 1) * (r.ty1 - r.ty0 + 1));
+            regions += (unsigned long long)(r.gw * r.gh);
+        }
     }
 #pragma unroll
     for (int d = 16; d >= 1; d >>= 1) {
         nmin = max(nmin, __shfl_xor_sync(0xffffffffu, nmin, d));
         kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, d));
+        culled += __shfl_xor_sync(0xffffffffu, culled, d);
+        tiles += __shfl_xor_sync(0xffffffffu, tiles, d);
+        regions += __shfl_xor_sync(0xffffffffu, regions, d);
     }
-    if ((threadIdx.x & 31) == 0) { s_mm[0][threadIdx.x >> 5] = nmin; s_mm[1][threadIdx.x >> 5] = kmax; }
+    if ((t & 31) == 0) {
+        s_mm[0][t >> 5] = nmin; s_mm[1][t >> 5] = kmax;
+        s_sum[0][t >> 5] = tiles; s_sum[1][t >> 5] = regions;
+        s_cul[t >> 5] = culled;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t a = 0u, b = 0u;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a = max(a, s_mm[0][w]); b = max(b, s_mm[1][w]); }
-        if (a | b) {
+    if (t == 0) {
+        uint32_t a = 0u, c = 0u, cu = 0u;
+        unsigned long long st = 0, sr = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a = max(a, s_mm[0][w]); c = max(c, s_mm[1][w]);
+            st += s_sum[0][w]; sr += s_sum[1][w]; cu += s_cul[w];
+        }
+        if (a | c) {
             uint32_t* slot = mm + 2 * (blockIdx.x % kRadixMapSlots);
             atomicMax(slot, a);
-            atomicMax(slot + 1, b);
+            atomicMax(slot + 1, c);
+        }
+        if (st) atomicAdd(ktotal, st);
+        if (sr) atomicAdd(rtotal, sr);
+        if (cu) {  // culled records: key 0xffffffff
+            atomicAdd(n_culled, cu);
+            s_dh[255] += cu;
+            s_dh[256 + 255] += cu;
         }
     }
-}
-
-// Per depth-sorted record: the number of regions its tile rect meets; the
-// number of tiles it meets is summed (64-bit, one atomic per block) into
-// *ktotal, the length of all tile lists together.
-__global__ void __launch_bounds__(256) region_counts_kernel(const BinInfo* __restrict__ bin,
-                                                            const uint32_t* __restrict__ pv, int64_t n, int ts,
-                                                            uint32_t* __restrict__ rcnt,
-                                                            unsigned long long* __restrict__ ktotal) {
-    pdl_enter();
-    __shared__ unsigned long long s_sum[8];
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    unsigned long long tiles = 0;
-    if (i < n) {
-        const BinInfo b = bin[pv[i]];
-        uint32_t regions = 0;
-        if (b.valid) {
-            const int tx0 = (int)(b.rx & 0xffff) / ts, tx1 = (int)(b.rx >> 16) / ts;
-            const int ty0 = (int)(b.ry & 0xffff) / ts, ty1 = (int)(b.ry >> 16) / ts;
-            tiles = (unsigned long long)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
-            regions = (uint32_t)((tx1 / kRegionTX - tx0 / kRegionTX + 1) * (ty1 / kRegionTY - ty0 / kRegionTY + 1));
-        }
-        rcnt[i] = regions;
-    }
-#pragma unroll
-    for (int d = 16; d >= 1; d >>= 1) tiles += __shfl_down_sync(0xffffffffu, tiles, d);
-    if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = tiles;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned long long t = 0;
-#pragma unroll
-        for (int w = 0; w < 8; ++w) t += s_sum[w];
-        if (t) atomicAdd(ktotal, t);
-    }
+    for (int j = t; j < 3 * 256; j += blockDim.x)
+        if (s_dh[j]) atomicAdd(&dhist[j], s_dh[j]);
 }
 
-// (region, id) pairs of the depth-sorted records: record i owns the slots
-// [off[i], off[i] + regions(i)), its regions in row-major order.  Each warp
-// takes 32 consecutive records and fills their (contiguous) slots together:
-// lane l writes slots l, l + 32, ... of the warp's range, finding the owning
-// record by binary search over the warp's exclusive prefix of region counts,
-// so the writes are coalesced and a record with many regions does not hold
-// up its warp.
+// (region, id) pairs of the depth-sorted records (the depth sort's result is
+// in pv_b after an odd number of passes that ran, else in pv_a): record i
+// owns the slots [off(i), off(i) + regions(i)), its regions in row-major
+// order, with off the exclusive prefix of the region counts over the sorted
+// records, found in the same kernel: a block (tile index from *counter)
+// takes kEmitRecords consecutive records, warp w the w-th 256 of them in 8
+// rounds of 32; per-warp scans and a scan over the warps give the block's
+// offsets, and a warp look-back over the blocks before it (one word per
+// block in lbe) the block's first slot.  Then each warp fills the
+// (contiguous) slots of a round's 32 records together: lane l writes slots
+// l, l + 32, ... of the round's range, finding the owning record by binary
+// search over the round's exclusive prefix, so the writes are coalesced and
+// a record with many regions does not hold up its warp.
 // Capacity: when the tile lists would hold more than `kcap` entries (or more
 // than 2^32 - 2), or the pairs more than `rcap`, nothing is emitted, the
-// region-pair count *rn (the sort's count; *rn_scan is the scan's) is set to
-// 0 so that no tile list gets an entry, and the overflow is recorded: status
-// bit 2 for a capacity, status[1] = 0xffffffff for the 32-bit limit.
-// Thread 0 also publishes the number of tile-list entries in status[1].
+// region-pair count *rn (the region sort's count) is set to 0 so that no tile
+// list gets an entry, and the overflow is recorded: status bit 2 for a
+// capacity, status[1] = 0xffffffff for the 32-bit limit.  Thread 0 of block 0
+// also publishes the number of tile-list entries in status[1]; the blocks
+// clear the look-back words of the region sort's first pass (lbr, tiles of
+// `rtile` pairs) and count the digits of the region sort's `rpasses` 8-bit
+// passes over the emitted pairs' region index (rhist[p * 256 + d]: pairs
+// whose region r has (r >> 8p) & 255 == d; in depth order consecutive pairs
+// rarely share a region, so plain shared-memory atomics).
+constexpr int kEmitRounds = 8;
+constexpr int kEmitRecords = 256 * kEmitRounds;
 __global__ void __launch_bounds__(256) emit_region_pairs_kernel(
-    const BinInfo* __restrict__ bin, const uint32_t* __restrict__ pv, const uint32_t* __restrict__ off, int64_t n,
-    int64_t ntot, int ts, int regions_x, int regions_per_cam, const unsigned long long* __restrict__ ktotal,
-    int64_t kcap, uint32_t* __restrict__ rk, uint32_t* __restrict__ rv, int64_t rcap,
-    const uint32_t* __restrict__ rn_scan, uint32_t* __restrict__ rn, int32_t* __restrict__ status) {
+    const BinInfo* __restrict__ bin, const uint32_t* __restrict__ pv_a, const uint32_t* __restrict__ pv_b,
+    const uint32_t* __restrict__ mm, int64_t n, int64_t ntot, int ts, int regions_x, int regions_per_cam,
+    const unsigned long long* __restrict__ ktotal, const unsigned long long* __restrict__ rtotal, int64_t kcap,
+    uint32_t* __restrict__ rk, uint32_t* __restrict__ rv, int64_t rcap, uint32_t* __restrict__ rn,
+    int32_t* __restrict__ status, uint64_t* __restrict__ lbe, uint32_t* __restrict__ counter,
+    PassLookback lbr, int64_t rtile, uint32_t* __restrict__ rhist, int rpasses) {
     pdl_enter();
-    const unsigned long long K = *ktotal;
-    const bool over = K > (unsigned long long)kcap || K >= 0xffffffffull || (int64_t)*rn_scan > rcap;
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    __shared__ uint32_t s_rh[3 * 256];
+    __shared__ uint32_t s_wtot[8];
+    __shared__ uint32_t s_id;
+    __shared__ unsigned long long s_base[8];
+    const unsigned long long K = *ktotal, RT = *rtotal;
+    const bool over = K > (unsigned long long)kcap || K >= 0xffffffffull || RT > (unsigned long long)rcap;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (blockIdx.x == 0 && t == 0) {
         status[1] = (int32_t)(uint32_t)(K >= 0xffffffffull ? 0xffffffffull : K);
         if (over && K < 0xffffffffull) atomicOr(status, 4);
-        *rn = over ? 0u : *rn_scan;
+        *rn = over ? 0u : (uint32_t)RT;
     }
     if (over) return;
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31;
-    if (i - lane >= n) return;  // whole warp past the end
-    int xlo = 0, ylo = 0, w = 1, cnt = 0;
-    int tx0 = 0, tx1 = 0, ty0 = 0, ty1 = 0;  // tile rect
-    uint32_t id = 0, rbase = 0;
-    int64_t start = 0;
-    if (i < n) {
-        const uint32_t rec = pv[i];
-        const BinInfo b = bin[rec];
-        start = off[i];
-        if (b.valid) {
+    {   // the region sort's first look-back words, for its live tiles
+        const int64_t tiles = ((int64_t)RT + rtile - 1) / rtile;
+        const int64_t words = tiles * 256, gwords = lookback_groups(tiles) * 256;
+        const int64_t j0 = blockIdx.x * (int64_t)blockDim.x + t, stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t j = j0; j < words; j += stride) lbr.tiles[j] = 0u;
+        for (int64_t j = j0; j < gwords; j += stride) lbr.groups[j] = 0ull;
+    }
+    for (int j = t; j < 3 * 256; j += blockDim.x) s_rh[j] = 0u;
+    if (t == 0) s_id = atomicAdd(counter, 1u);
+    __syncthreads();
+    const int64_t b = s_id;
+    const uint32_t* __restrict__ pv = (depth_digits(mm).passes_run() & 1) ? pv_b : pv_a;
+    const int64_t wbase = b * kEmitRecords + warp * 256;  // the warp's first record
+    // 1. region counts, exclusive prefix within the warp's 256 records
+    int cnt[kEmitRounds], excl[kEmitRounds];
+    int run = 0;
+#pragma unroll
+    for (int j = 0; j < kEmitRounds; ++j) {
+        const int64_t i = wbase + j * 32 + lane;
+        cnt[j] = 0;
+        if (i < n) {
+            const BinInfo bi = bin[pv[i]];
+            if (bi.valid) {
+                const RecordRects r = record_rects(bi, ts);
+                cnt[j] = r.gw * r.gh;
+            }
+        }
+        int inc = cnt[j];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, d);
+            if (lane >= d) inc += y;
+        }
+        excl[j] = run + inc - cnt[j];
+        run += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (lane == 0) s_wtot[warp] = (uint32_t)run;
+    __syncthreads();
+    // 2. the warps' offsets and the block's first slot (warp 0)
+    if (warp == 0) {
+        const uint32_t wt = lane < 8 ? s_wtot[lane] : 0u;
+        uint32_t winc = wt;
+#pragma unroll
+        for (int d = 1; d < 8; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, winc, d);
+            if (lane >= d) winc += y;
+        }
+        const uint32_t btot = __shfl_sync(0xffffffffu, winc, 7);
+        if (lane == 0) lb_store(lbe + b, (b == 0 ? kLbInc : kLbAgg) | btot);
+        const uint64_t bex = lookback_warp(lbe, b, reinterpret_cast<uint32_t*>(status));
+        if (lane == 0 && b > 0) lb_store(lbe + b, kLbInc | (bex + btot));
+        if (lane < 8) s_base[lane] = bex + (winc - wt);
+    }
+    __syncthreads();
+    const int64_t warp_slot = (int64_t)s_base[warp];
+    // 3. emission, round by round
+#pragma unroll
+    for (int j = 0; j < kEmitRounds; ++j) {
+        if (wbase + j * 32 >= n) break;  // (warp-uniform)
+        const int64_t i = wbase + j * 32 + lane;
+        RecordRects rr{0, 0, 0, 0, 0, 0, 1, 0};
+        uint32_t id = 0, rbase = 0;
+        if (cnt[j] > 0) {
+            const uint32_t rec = pv[i];
             const int cam = (int)(rec / ntot);
             id = (uint32_t)(rec - (int64_t)cam * ntot);
-            tx0 = (int)(b.rx & 0xffff) / ts; tx1 = (int)(b.rx >> 16) / ts;
-            ty0 = (int)(b.ry & 0xffff) / ts; ty1 = (int)(b.ry >> 16) / ts;
-            xlo = tx0 / kRegionTX;
-            ylo = ty0 / kRegionTY;
-            w = tx1 / kRegionTX - xlo + 1;
-            cnt = w * (ty1 / kRegionTY - ylo + 1);
+            rr = record_rects(bin[rec], ts);
             rbase = (uint32_t)cam * (uint32_t)regions_per_cam;
         }
-    }
-    // exclusive prefix of the counts within the warp
-    int incl = cnt;
+        const int e0 = __shfl_sync(0xffffffffu, excl[j], 0);
+        const int ex = excl[j] - e0;  // exclusive prefix within the round
+        const int total = __shfl_sync(0xffffffffu, ex + cnt[j], 31);
+        const int64_t base = warp_slot + e0;
+        for (int s0 = 0; s0 < total; s0 += 32) {
+            const int s = s0 + lane;
+            // owner: the last lane r with ex[r] <= s
+            int r = 0;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += y;
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int c = r + step;
+                const int e = __shfl_sync(0xffffffffu, ex, c & 31);
+                if (c < 32 && e <= s) r = c;
+            }
+            const int re = __shfl_sync(0xffffffffu, ex, r);
+            const int rx = __shfl_sync(0xffffffffu, rr.gx0, r);
+            const int ry = __shfl_sync(0xffffffffu, rr.gy0, r);
+            const int rw = __shfl_sync(0xffffffffu, rr.gw, r);
+            const uint32_t rid = __shfl_sync(0xffffffffu, id, r);
+            const uint32_t rrb = __shfl_sync(0xffffffffu, rbase, r);
+            const int rtx0 = __shfl_sync(0xffffffffu, rr.tx0, r), rtx1 = __shfl_sync(0xffffffffu, rr.tx1, r);
+            const int rty0 = __shfl_sync(0xffffffffu, rr.ty0, r), rty1 = __shfl_sync(0xffffffffu, rr.ty1, r);
+            const int64_t o = base + s;
+            if (s < total && o < rcap) {
+                const int k = s - re;
+                const int gy = ry + k / rw, gx = rx + k % rw;
+                // the record's tiles inside region (gx, gy), region-local
+                const int lx0 = max(rtx0 - gx * kRegionTX, 0), lx1 = min(rtx1 - gx * kRegionTX, kRegionTX - 1);
+                const int ly0 = max(rty0 - gy * kRegionTY, 0), ly1 = min(rty1 - gy * kRegionTY, kRegionTY - 1);
+                const uint32_t lrect = (uint32_t)(lx0 | (lx1 << 3) | (ly0 << 6) | (ly1 << 8));
+                const uint32_t region = rrb + (uint32_t)(gy * regions_x + gx);
+                rk[o] = (region << kRectBits) | lrect;
+                rv[o] = rid;
+                for (int q = 0; q < rpasses; ++q) atomicAdd(&s_rh[q * 256 + ((region >> (8 * q)) & 255u)], 1u);
+            }
+        }
     }
-    const int excl = incl - cnt;
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    const int64_t base = __shfl_sync(0xffffffffu, start, 0);  // offsets are contiguous in record order
-    for (int s0 = 0; s0 < total; s0 += 32) {
-        const int s = s0 + lane;
-        // owner: the last lane r with excl[r] <= s
-        int r = 0;
-#pragma unroll
-        for (int step = 16; step >= 1; step >>= 1) {
-            const int c = r + step;
-            const int e = __shfl_sync(0xffffffffu, excl, c & 31);
-            if (c < 32 && e <= s) r = c;
-        }
-        const int re = __shfl_sync(0xffffffffu, excl, r);
-        const int rx = __shfl_sync(0xffffffffu, xlo, r);
-        const int ry = __shfl_sync(0xffffffffu, ylo, r);
-        const int rw = __shfl_sync(0xffffffffu, w, r);
-        const uint32_t rid = __shfl_sync(0xffffffffu, id, r);
-        const uint32_t rrb = __shfl_sync(0xffffffffu, rbase, r);
-        const int rtx0 = __shfl_sync(0xffffffffu, tx0, r), rtx1 = __shfl_sync(0xffffffffu, tx1, r);
-        const int rty0 = __shfl_sync(0xffffffffu, ty0, r), rty1 = __shfl_sync(0xffffffffu, ty1, r);
-        const int64_t o = base + s;
-        if (s < total && o < rcap) {
-            const int k = s - re;
-            const int gy = ry + k / rw, gx = rx + k % rw;
-            // the record's tiles inside region (gx, gy), region-local
-            const int lx0 = max(rtx0 - gx * kRegionTX, 0), lx1 = min(rtx1 - gx * kRegionTX, kRegionTX - 1);
-            const int ly0 = max(rty0 - gy * kRegionTY, 0), ly1 = min(rty1 - gy * kRegionTY, kRegionTY - 1);
-            const uint32_t lrect = (uint32_t)(lx0 | (lx1 << 3) | (ly0 << 6) | (ly1 << 8));
-            rk[o] = ((rrb + (uint32_t)(gy * regions_x + gx)) << kRectBits) | lrect;
-            rv[o] = rid;
-        }
+    __syncthreads();
+    for (int j = t; j < rpasses * 256; j += blockDim.x)
+        if (s_rh[j]) atomicAdd(&rhist[j], s_rh[j]);
+}
+
+// Region starts and chunk offsets of a render with at most 256 regions (one
+// block), from the region counts of the region sort's histogram (the pairs
+// of region r are rhist[r]; none when the lists overflowed, *rn == 0):
+// rstart[r] = first pair of region r, rstart[R] = pair count; coff[r] =
+// first count/fill chunk of region r, coff[R] = *nblk = chunk count.
+__global__ void __launch_bounds__(256) region_scan_small_kernel(const uint32_t* __restrict__ rhist,
+                                                                const uint32_t* __restrict__ rn, int64_t R,
+                                                                uint32_t* __restrict__ rstart,
+                                                                uint32_t* __restrict__ coff,
+                                                                uint32_t* __restrict__ nblk) {
+    pdl_enter();
+    __shared__ uint32_t s_warp[32];
+    const int t = threadIdx.x;
+    const uint32_t c = (t < R && *rn != 0u) ? rhist[t] : 0u;
+    uint32_t tot, ctot;
+    const uint32_t st = block_exclusive_scan_256(c, s_warp, tot);
+    const uint32_t ch = (c + kRegionChunk - 1) / kRegionChunk;
+    const uint32_t co = block_exclusive_scan_256(ch, s_warp, ctot);
+    if (t < R) {
+        rstart[t] = st;
+        coff[t] = co;
+    }
+    if (t == 0) {
+        rstart[R] = tot;
+        coff[R] = ctot;
+        *nblk = ctot;
     }
 }
 
@@ -1050,6 +1210,49 @@ cudaError_t radix_sort_pairs(umgs_frame* fr, uint32_t* k, uint32_t* v, uint32_t*
     return cudaSuccess;
 }
 
+// Passes [0, npass) of the single-sweep stable LSD radix sort of (k, v) on
+// the 8-bit digits at lo + 8p, or the depth sort's DepthDigits when mm is
+// given (then npass = 4, ghist holds prim_keys_kernel's counts, n_culled the
+// culled records, and pass 2 counts pass 3's digits into ghist[768..]);
+// ghist: 256 digit counts per pass; counters: one zeroed tile counter per
+// pass; the frame's lb_a / lb_b alternate as look-back words
+// (lookback_layout for radix_blocks(n_cap) tiles; lb_a cleared beforehand for
+// the first pass's live tiles).  The element count is
+// read from n_dev (at most n_cap, which sizes the grids); the result is in
+// (k2, v2) after an odd number of passes that ran, else in (k, v).
+cudaError_t onesweep_sort(umgs_frame* fr, uint32_t* k, uint32_t* v, uint32_t* k2, uint32_t* v2,
+                          const uint32_t* n_dev, int64_t n_cap, int lo, int npass, uint32_t* ghist,
+                          uint32_t* counters, const uint32_t* mm, const uint32_t* n_culled, uint32_t* err,
+                          cudaStream_t s) {
+    const int64_t nb = radix_blocks(n_cap);
+    const int items = radix_items(n_cap);
+    const PassLookback lb[2] = {lookback_layout(fr->lb_a.ptr, nb), lookback_layout(fr->lb_b.ptr, nb)};
+    const PassLookback none{nullptr, nullptr};
+    for (int p = 0; p < npass; ++p) {
+        const uint32_t* ki = (p & 1) ? k2 : k;
+        const uint32_t* vi = (p & 1) ? v2 : v;
+        uint32_t* ko = (p & 1) ? k : k2;
+        uint32_t* vo = (p & 1) ? v : v2;
+        const PassLookback nxt = p + 1 < npass ? lb[(p + 1) & 1] : none;
+        const int shift = lo + 8 * p;
+        const uint32_t* gh = ghist + 256 * p;
+#define UMGS_PASS(IT, MP)                                                                                      \
+    launch_pdl(onesweep_pass_kernel<IT, MP>, (unsigned)nb, kRsThreads, 0, s, ki, vi, n_dev, n_cap, shift, gh,  \
+               lb[p & 1], nxt, counters + p, ko, vo, mm, n_culled, mm ? ghist + 3 * 256 : nullptr, err)
+        if (mm) {
+            if (items == 8) UMGS_PASS(8, true);
+            else UMGS_PASS(16, true);
+        } else {
+            if (items == 8) UMGS_PASS(8, false);
+            else UMGS_PASS(16, false);
+        }
+#undef UMGS_PASS
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 // ---------------------------------------------------------------------------
 // host orchestration
 
@@ -1073,6 +1276,9 @@ cudaError_t reserve_binning(umgs_frame* fr, int64_t rcap, int64_t kcap) {
     if ((e = fr->rg_cpre.reserve(sizeof(uint32_t) * 32 * nblk_max)) != cudaSuccess) return e;
     if ((e = fr->tl_cnt.reserve(sizeof(uint32_t) * std::max<int64_t>(1, M))) != cudaSuccess) return e;
     if ((e = fr->tl_off.reserve(sizeof(uint32_t) * std::max<int64_t>(1, M))) != cudaSuccess) return e;
+    // look-back words of the region sort's passes
+    if ((e = fr->lb_a.reserve(lookback_bytes(radix_blocks(rcap)))) != cudaSuccess) return e;
+    if ((e = fr->lb_b.reserve(lookback_bytes(radix_blocks(rcap)))) != cudaSuccess) return e;
     return cudaSuccess;
 }
 
@@ -1117,14 +1323,17 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     UMGS_TRY(fr->trec.reserve(sizeof(TRec) * std::max<int64_t>(1, Nt * ncams)));
     UMGS_TRY(fr->bin.reserve(sizeof(BinInfo) * std::max<int64_t>(1, Ntot * ncams)));
     UMGS_TRY(fr->tile_off.reserve(sizeof(int64_t) * (M + 1)));
+    UMGS_TRY(fr->lb_s.reserve(sizeof(uint64_t) * ((M + 255) / 256)));
     // status words: [0] error bits, [1] number of tile-list entries (32-bit,
     // 0xffffffff when it does not fit), [2] largest saved-stack need, [3] fp64
     // conic list length, [4] tile count for the tile-order sort, [5] record
-    // count for the depth sort, [6..7] evaluation count (u64), [8] persistent
+    // count for the depth sort, [6..7] (region, id) pairs counted (u64), [8] persistent
     // work counter, [9] scan overflow, [10..11] tile-list entries (u64),
     // [12] (region, id) pairs sorted (0 after an overflow), [13] count/fill
-    // chunks, [14] tile-list entries from the tile scan, [15] (region, id)
-    // pairs counted, [16 ..) the depth sort's key-map slots (~min, max)
+    // chunks, [14] tile-list entries from the tile scan, [15] unused,
+    // [16 ..) the depth sort's key-map slots (~min, max); then the
+    // evaluation and work-split counters and, from kStatusBinWords, the
+    // tile counters and digit histograms of the single-sweep binning kernels
     static_assert(kStatusEvalWords == 16 + 2 * kRadixMapSlots, "status word layout");
     UMGS_TRY(fr->status.reserve(sizeof(int32_t) * kStatusWords));
 
@@ -1158,7 +1367,13 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     }
     // status words cleared by a kernel (not a memset node), so that the
     // programmatic launch chain runs on from the stream's previous kernel
-    launch_pdl(zero_words_kernel, 1, 128, 0, stream, reinterpret_cast<uint32_t*>(fr->status.ptr), kStatusWords);
+    {
+        const int64_t nq = (M + 255) / 256;  // the tile scan's look-back words
+        const unsigned zg = (unsigned)std::min<int64_t>((std::max<int64_t>(nq, kStatusWords) + 1023) / 1024,
+                                                        ctx->num_sms);
+        launch_pdl(zero_words_kernel, zg, 256, 0, stream, reinterpret_cast<uint32_t*>(fr->status.ptr), kStatusWords,
+                   fr->lb_s.as<uint64_t>(), nq);
+    }
 
     const DevCam* dcams = fr->cams.as<DevCam>();
     const unsigned fix_cap = (unsigned)std::min<int64_t>(std::max<int64_t>(1, Ng * ncams), 1 << 22);
@@ -1227,31 +1442,37 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     UMGS_TRY(fr->pv.reserve(sizeof(uint32_t) * std::max<int64_t>(1, NR)));
     UMGS_TRY(fr->pk2.reserve(sizeof(uint32_t) * std::max<int64_t>(1, NR)));
     UMGS_TRY(fr->pv2.reserve(sizeof(uint32_t) * std::max<int64_t>(1, NR)));
-    UMGS_TRY(fr->pcnt.reserve(sizeof(uint32_t) * std::max<int64_t>(1, NR)));
-    UMGS_TRY(fr->poff.reserve(sizeof(uint32_t) * std::max<int64_t>(1, NR)));
+    const int64_t nb_depth = radix_blocks(NR);
+    UMGS_TRY(fr->lb_a.reserve(lookback_bytes(nb_depth)));
+    UMGS_TRY(fr->lb_b.reserve(lookback_bytes(nb_depth)));
+    const int64_t nb_emit = (NR + kEmitRecords - 1) / kEmitRecords;
+    UMGS_TRY(fr->lb_e.reserve(sizeof(uint64_t) * std::max<int64_t>(1, nb_emit)));
     uint32_t* pk = fr->pk.as<uint32_t>();
     uint32_t* pv = fr->pv.as<uint32_t>();
     uint32_t* status_u = reinterpret_cast<uint32_t*>(fr->status.as<int32_t>());
     unsigned long long* ktotal = reinterpret_cast<unsigned long long*>(status_u + 10);
+    unsigned long long* rtotal = reinterpret_cast<unsigned long long*>(status_u + 6);
     uint32_t* rn = status_u + 12;    // number of (region, id) pairs sorted
-    uint32_t* rn_scan = status_u + 15;  // number of (region, id) pairs counted
     uint32_t* nblk = status_u + 13;  // number of count/fill chunks
     uint32_t* ktot32 = status_u + 14;
+    uint32_t* mm = status_u + 16;
+    uint32_t* counters = status_u + kStatusBinWords;  // tile counters of the single-sweep kernels
+    uint32_t* dhist = counters + kBinCounters;        // depth sort: 4 x 256 digit counts
+    uint32_t* rhist = dhist + 4 * 256;                // region sort: 3 x 256 digit counts
+    int rbits = 0;
+    while (((int64_t)1 << rbits) < R) ++rbits;
+    const int rpasses = (rbits + 7) / 8;  // region sort passes (none for a single region)
     if (NR > 0) {
         StageTimer tm(ctx, UMGS_STAGE_SCAN, stream);
-        launch_pdl(prim_keys_kernel, grid_for(NR, 256), 256, 0, stream, fr->bin.as<BinInfo>(), NR, pk, pv, status_u + 5,
-                   status_u + 16);
+        // (one block of 1024 threads per SM: a histogram bin takes one global atomic per SM)
+        const unsigned pgrid = (unsigned)std::min<int64_t>(grid_for(NR, kHistThreads), ctx->num_sms);
+        launch_pdl(prim_keys_kernel, pgrid, kHistThreads, 0, stream, fr->bin.as<BinInfo>(), NR, Ntot, ts, regions_x,
+                   regions_per_cam, pk, pv, status_u + 5, mm, dhist, counters + kBinCulledWord, ktotal, rtotal,
+                   fr->lb_e.as<uint64_t>(), nb_emit, fr->lb_a.as<uint32_t>(),
+                   lookback_bytes(nb_depth) / (int64_t)sizeof(uint32_t));
         UMGS_TRY(cudaGetLastError());
-        uint32_t* rk = nullptr;
-        uint32_t* rv = nullptr;
-        UMGS_TRY(radix_sort_pairs(fr, pk, pv, fr->pk2.as<uint32_t>(), fr->pv2.as<uint32_t>(), status_u + 5, NR, 32, &rk,
-                                  &rv, stream, 0, status_u + 16));
-        pk = rk;
-        pv = rv;
-        launch_pdl(region_counts_kernel, grid_for(NR, 256), 256, 0, stream, fr->bin.as<BinInfo>(), pv, NR, ts,
-                                                                    fr->pcnt.as<uint32_t>(), ktotal);
-        UMGS_TRY(cudaGetLastError());
-        UMGS_TRY(scan_u32(fr, fr->pcnt.as<uint32_t>(), fr->poff.as<uint32_t>(), NR, rn_scan, stream));
+        UMGS_TRY(onesweep_sort(fr, pk, pv, fr->pk2.as<uint32_t>(), fr->pv2.as<uint32_t>(), status_u + 5, NR, 0, 4,
+                               dhist, counters, mm, counters + kBinCulledWord, status_u, stream));
     }
     int64_t Kcap, rcap;
     if (!fr->nosync) {
@@ -1260,11 +1481,13 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
         UMGS_TRY(cudaStreamSynchronize(stream));
         const uint32_t* w = reinterpret_cast<const uint32_t*>(ctx->pinned);
         const uint64_t K64 = (uint64_t)w[10] | ((uint64_t)w[11] << 32);
+        const uint64_t R64 = (uint64_t)w[6] | ((uint64_t)w[7] << 32);
         if (w[0] & 1) return fail(ctx, UMGS_ERR_INVALID_ARG, "a face index is out of range");
+        if (w[0] & kStatusLookbackTimeout) return fail(ctx, UMGS_ERR_TIMEOUT, "a binning look-back wait gave up");
         if (K64 >= 0xffffffffull) return fail(ctx, UMGS_ERR_CAPACITY, "more than 4294967294 (tile, primitive) pairs");
         fr->num_keys = (int64_t)K64;
         Kcap = (int64_t)K64;
-        rcap = NR > 0 ? (int64_t)w[15] : 0;
+        rcap = NR > 0 ? (int64_t)R64 : 0;  // (region pairs never outnumber list entries)
     } else {
         // no host read-back: the lists are held to the reserved capacity and
         // an overflow is flagged in the status word (bit 2); inside a capture
@@ -1275,54 +1498,62 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     }
     if (!fr->capture) UMGS_TRY(reserve_binning(fr, rcap, Kcap));
     fr->ids = fr->tl_ids.as<uint32_t>();
+    const int items_r = radix_items(rcap);
     if (NR > 0) {
         StageTimer tm(ctx, UMGS_STAGE_SCATTER, stream);
-        launch_pdl(emit_region_pairs_kernel, grid_for(NR, 256), 256, 0, stream, 
-            fr->bin.as<BinInfo>(), pv, fr->poff.as<uint32_t>(), NR, Ntot, ts, regions_x, regions_per_cam, ktotal,
-            Kcap, fr->tk.as<uint32_t>(), fr->tv.as<uint32_t>(), rcap, rn_scan, rn, fr->status.as<int32_t>());
+        launch_pdl(emit_region_pairs_kernel, (unsigned)nb_emit, 256, 0, stream, fr->bin.as<BinInfo>(),
+                   static_cast<const uint32_t*>(pv), static_cast<const uint32_t*>(fr->pv2.as<uint32_t>()),
+                   static_cast<const uint32_t*>(mm), NR, Ntot, ts, regions_x, regions_per_cam, ktotal, rtotal, Kcap,
+                   fr->tk.as<uint32_t>(), fr->tv.as<uint32_t>(), rcap, rn, fr->status.as<int32_t>(),
+                   fr->lb_e.as<uint64_t>(), counters + kBinEmitCounter,
+                   lookback_layout(fr->lb_a.ptr, radix_blocks(rcap)), (int64_t)kRsThreads * items_r, rhist,
+                   std::max(1, rpasses));
         UMGS_TRY(cudaGetLastError());
     }
     {
         StageTimer tm(ctx, UMGS_STAGE_SORT, stream);
         uint32_t* rk = fr->tk.as<uint32_t>();
         uint32_t* rv = fr->tv.as<uint32_t>();
-        if (NR > 0 && rcap > 0 && R > 1) {
-            int bits = 1;
-            while (((int64_t)1 << bits) < R) ++bits;
-            UMGS_TRY(radix_sort_pairs(fr, fr->tk.as<uint32_t>(), fr->tv.as<uint32_t>(), fr->tk2.as<uint32_t>(),
-                                      fr->tv2.as<uint32_t>(), rn, rcap, bits, &rk, &rv, stream, kRectBits));
+        if (NR > 0 && rcap > 0 && rpasses > 0) {
+            UMGS_TRY(onesweep_sort(fr, fr->tk.as<uint32_t>(), fr->tv.as<uint32_t>(), fr->tk2.as<uint32_t>(),
+                                   fr->tv2.as<uint32_t>(), rn, rcap, kRectBits, rpasses, rhist,
+                                   counters + kBinRegionCounters, nullptr, nullptr, status_u, stream));
+            if (rpasses & 1) {
+                rk = fr->tk2.as<uint32_t>();
+                rv = fr->tv2.as<uint32_t>();
+            }
         }
         const int64_t nblk_max = (rcap + kRegionChunk - 1) / kRegionChunk + R;
         uint32_t* rstart = fr->rg_start.as<uint32_t>();
         uint32_t* coff = fr->rg_coff.as<uint32_t>();
         int64_t* toff64 = fr->tile_off.as<int64_t>();
-        const unsigned sgrid = (unsigned)std::min<int64_t>(grid_for(std::max(rcap, R + 1), 256), 8 * ctx->num_sms);
-        launch_pdl(region_starts_kernel, sgrid, 256, 0, stream, rk, rn, rcap, R, rstart);
-        UMGS_TRY(cudaGetLastError());
-        if (R <= kSmallScanMax) {
-            launch_pdl(scan_small_kernel<ChunksIn, uint32_t>, 1, 1024, 0, stream, ChunksIn{rstart}, R, coff, nblk);
+        if (R <= 256) {
+            // at most one region pass: its digit counts are the region counts
+            launch_pdl(region_scan_small_kernel, 1, 256, 0, stream, static_cast<const uint32_t*>(rhist),
+                       static_cast<const uint32_t*>(rn), R, rstart, coff, nblk);
         } else {
-            launch_pdl(gather_in_kernel<ChunksIn>, grid_for(R, 256), 256, 0, stream, ChunksIn{rstart}, R,
-                                                                             fr->rg_nchunk.as<uint32_t>());
-            UMGS_TRY(scan_u32(fr, fr->rg_nchunk.as<uint32_t>(), coff, R, nblk, stream));
+            const unsigned sgrid = (unsigned)std::min<int64_t>(grid_for(std::max(rcap, R + 1), 256), 8 * ctx->num_sms);
+            launch_pdl(region_starts_kernel, sgrid, 256, 0, stream, rk, rn, rcap, R, rstart);
+            UMGS_TRY(cudaGetLastError());
+            if (R <= kSmallScanMax) {
+                launch_pdl(scan_small_kernel<ChunksIn, uint32_t>, 1, 1024, 0, stream, ChunksIn{rstart}, R, coff, nblk);
+            } else {
+                launch_pdl(gather_in_kernel<ChunksIn>, grid_for(R, 256), 256, 0, stream, ChunksIn{rstart}, R,
+                           fr->rg_nchunk.as<uint32_t>());
+                UMGS_TRY(scan_u32(fr, fr->rg_nchunk.as<uint32_t>(), coff, R, nblk, stream));
+            }
         }
         UMGS_TRY(cudaGetLastError());
-        launch_pdl(region_count_kernel, (unsigned)nblk_max, kRegionThreads, 0, stream, 
+        launch_pdl(region_count_kernel, (unsigned)nblk_max, kRegionThreads, 0, stream,
             rk, coff, rstart, nblk, R, regions_x, regions_per_cam, tiles_x, tiles_per_cam, fr->rg_ccnt.as<uint32_t>());
         UMGS_TRY(cudaGetLastError());
         const TileTotalIn tin{coff, nblk, fr->rg_ccnt.as<uint32_t>(), fr->rg_cpre.as<uint32_t>(), R, tiles_x,
                               tiles_per_cam, regions_x, regions_per_cam};
-        launch_pdl(gather_in_kernel<TileTotalIn>, grid_for(M, 256), 256, 0, stream, tin, M, fr->tl_cnt.as<uint32_t>());
+        // (one tile per thread: a tile's total walks its region's chunks)
+        launch_pdl(scan_lookback_kernel<TileTotalIn, 1>, (unsigned)((M + 255) / 256), kRsThreads, 0, stream, tin, M,
+                   toff64, ktot32, fr->lb_s.as<uint64_t>(), counters + kBinScanCounter, status_u);
         UMGS_TRY(cudaGetLastError());
-        if (M <= kSmallScanMax) {
-            launch_pdl(scan_small_kernel<ArrayIn, int64_t>, 1, 1024, 0, stream, ArrayIn{fr->tl_cnt.as<uint32_t>()}, M, toff64,
-                                                                        ktot32);
-        } else {
-            UMGS_TRY(scan_u32(fr, fr->tl_cnt.as<uint32_t>(), fr->tl_off.as<uint32_t>(), M, ktot32, stream));
-            launch_pdl(tile_off_kernel, grid_for(M + 1, 256), 256, 0, stream, fr->tl_off.as<uint32_t>(), ktot32, M, toff64);
-        }
-        UMGS_TRY(cudaGetLastError());
-        launch_pdl(region_fill_kernel, (unsigned)nblk_max, kRegionThreads, 0, stream, 
+        launch_pdl(region_fill_kernel, (unsigned)nblk_max, kRegionThreads, 0, stream,
             rk, rv, coff, rstart, nblk, R, regions_x, regions_per_cam, tiles_x, tiles_y, tiles_per_cam, toff64,
             fr->rg_ccnt.as<uint32_t>(), fr->rg_cpre.as<uint32_t>(), fr->tl_ids.as<uint32_t>());
         UMGS_TRY(cudaGetLastError());
@@ -1353,6 +1584,7 @@ umgs_status frame_check(umgs_frame* fr, cudaStream_t stream) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_fail(fr->ctx, e, "reading the frame status");
     if (w[0] & 1) return fail(fr->ctx, UMGS_ERR_INVALID_ARG, "a face index is out of range");
+    if (w[0] & kStatusLookbackTimeout) return fail(fr->ctx, UMGS_ERR_TIMEOUT, "a binning look-back wait gave up");
     if ((uint32_t)w[1] == 0xffffffffu)
         return fail(fr->ctx, UMGS_ERR_CAPACITY, "more than 4294967294 (tile, primitive) pairs");
     if (w[0] & 4)

@@ -55,3 +55,25 @@ def single_triangle(camera, pix_pts, z_world, alpha=1.0, colors=None):
 
 def scene(g, meshes, camera, tile=8):
     return S.Scene(g, list(meshes), [camera], tile=tile)
+
+
+def compare_with_ties(got, ref_rgb, ref_T, tie, alts, tol):
+    """GPU RGB+T `got` [..., 4] against the fp64 oracle.  Every pixel is held
+    to `tol` per channel: an ordinary pixel against the oracle's composite, a
+    tie pixel (a decision within rounding distance of its threshold, which the
+    fp32 kernels may take the other way) against the closest of its
+    composite_alternatives (`alts`: flat pixel index -> [n_alt, 4]).
+    Returns (max error of the ordinary pixels, number of tie pixels, tie
+    pixels matching no alternative within tol, max error of the closest
+    alternative over the tie pixels)."""
+    got = np.asarray(got).reshape(-1, 4)
+    ref = np.concatenate([np.asarray(ref_rgb).reshape(-1, 3), np.asarray(ref_T).reshape(-1, 1)], 1)
+    tie = np.asarray(tie).reshape(-1)
+    err = np.abs(got - ref).max(1)
+    e_plain = float(err[~tie].max()) if (~tie).any() else 0.0
+    bad, e_tie = 0, 0.0
+    for k in np.nonzero(tie)[0]:
+        e = float(np.abs(alts[int(k)] - got[k]).max(1).min())
+        e_tie = max(e_tie, e)
+        bad += e > tol
+    return e_plain, int(tie.sum()), bad, e_tie

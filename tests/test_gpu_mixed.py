@@ -7,7 +7,7 @@ import torch
 
 from oracle import render as R
 from paper_2601_19233_gb300 import scenes as S
-from tests.test_gpu_render import check_lists, ctx  # noqa: F401
+from tests.test_gpu_render import check_lists, check_ref, ctx  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
@@ -33,14 +33,14 @@ def test_mixed_precision_error_bounded(ctx, seed):
     out, fr = _render(ctx, sc, True, torch.bfloat16)
     check_lists(sc, fr, 16)
     ref = R.render_image(sc)
+    check_ref(out[0], ref, tol=2e-2)
     ok = ~ref["tie"]
     err = np.abs(out[0, ..., :3] - ref["rgb"])[ok]
-    assert err.max() < 2e-2
     assert np.percentile(err, 99.9) < 1e-2
     assert psnr(out[0, ..., :3][ok], ref["rgb"][ok]) > 45.0
     # fp16 records alone (fp32 SH): smaller error
     out2, _ = _render(ctx, sc, True, torch.float32)
-    assert np.abs(out2[0, ..., :3] - ref["rgb"])[ok].max() < 1e-2
+    check_ref(out2[0], ref, tol=1e-2)
 
 
 def test_bf16_sh_with_fp32_records(ctx):
@@ -49,6 +49,4 @@ def test_bf16_sh_with_fp32_records(ctx):
     # the oracle evaluated on the bf16-rounded coefficients agrees to fp32 tolerance
     sc2 = S.small_scene(93, 40, 40, 800, mesh_subdiv=1, sh_degree=3)
     sc2.gaussians.sh = torch.as_tensor(sc2.gaussians.sh).to(torch.bfloat16).float().numpy()
-    ref = R.render_image(sc2)
-    ok = ~ref["tie"]
-    assert np.abs(out[0, ..., :3] - ref["rgb"])[ok].max() <= 2e-4
+    check_ref(out[0], R.render_image(sc2))

@@ -2,8 +2,10 @@
 
 Bar: tile lists (keys: tile, depth bits, unified id) and their sort order are
 bit-exact; images agree with the fp64 oracle within max-abs 2e-4 per channel
-(fp32 path), excluding "tie" pixels where a fragment's alpha sits within 1e-6
-of the 1/255 cut or T within 0.1% of the termination threshold.
+(fp32 path).  At "tie" pixels, where a fragment's alpha sits within 1e-6 of
+the 1/255 cut or T within 0.1% of the termination threshold, the fp32 kernels
+may take that decision the other way: there the image must match one of the
+oracle's composites with each such decision taken either way.
 """
 import ctypes
 
@@ -52,15 +54,19 @@ def check_lists(sc, fr, tile):
     return len(ids)
 
 
+def check_ref(img, ref, tol=TOL, tie_max=0.01):
+    """One camera's GPU image [H,W,4] against an oracle render_image result:
+    every pixel within tol (tie pixels against their alternatives), and at
+    most tie_max of the pixels ties."""
+    e, nt, bad, et = H.compare_with_ties(img, ref["rgb"], ref["T"], ref["tie"], ref["alts"], tol)
+    assert nt <= tie_max * ref["tie"].size, ("tie pixels", nt, ref["tie"].size)
+    assert e <= tol and bad == 0, (e, nt, bad, et)
+    return e
+
+
 def check_image(sc, out, mode=R.FULL, bg=(0, 0, 0), tol=TOL):
     for c in range(len(sc.cameras)):
-        ref = R.render_image(sc, c, mode=mode, bg=bg)
-        ok = ~ref["tie"]
-        d_rgb = np.abs(out[c, ..., :3] - ref["rgb"])[ok]
-        d_T = np.abs(out[c, ..., 3] - ref["T"])[ok]
-        assert ok.mean() > 0.99
-        assert d_rgb.max() <= tol, (c, d_rgb.max())
-        assert d_T.max() <= tol, (c, d_T.max())
+        check_ref(out[c], R.render_image(sc, c, mode=mode, bg=bg), tol)
 
 
 def test_config0_lists_and_image(ctx):
@@ -95,11 +101,7 @@ def test_t_product_reading(ctx):
     g = umgs.gaussians_to_device(sc.gaussians)
     ms = [umgs.mesh_to_device(m) for m in sc.meshes]
     out = umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(sc.tile, t_product=True)).cpu().numpy()
-    ref = R.render_image(sc, t_product=True)
-    ok = ~ref["tie"]
-    assert ok.mean() > 0.99
-    assert np.abs(out[0, ..., :3] - ref["rgb"])[ok].max() <= TOL
-    assert np.abs(out[0, ..., 3] - ref["T"])[ok].max() <= TOL
+    check_ref(out[0], R.render_image(sc, t_product=True))
     with pytest.raises(umgs.UmgsError):
         umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(sc.tile, t_product=True, save=True))
     with pytest.raises(umgs.UmgsError):
@@ -117,6 +119,27 @@ def test_tile_sizes_bit_identical(ctx):
     check_image(sc, outs[1])
 
 
+def test_wide_depth_range_takes_the_fourth_depth_pass(ctx):
+    # depths from 0.3 to 150: the high halves of the depth keys span more than
+    # 255 values, so the depth sort runs its fourth pass (on the digit counts
+    # its third pass gathers); lists bit-exact, image within the bar
+    rng = np.random.default_rng(77)
+    c = H.cam(64, 48)
+    n = 900
+    Z = np.exp(rng.uniform(np.log(0.3), np.log(150.0), n)).astype(np.float32)
+    u, v = rng.uniform(0, 64, n), rng.uniform(0, 48, n)
+    means = np.c_[(u - c.cx) * Z / c.fx, (v - c.cy) * Z / c.fy, Z - c.viewmat[2, 3]]
+    scales = (np.exp(rng.normal(0.7, 0.4, (n, 3))) * Z[:, None] / c.fx).astype(np.float32)
+    g = H.gaussians(means, scales=scales, opac=rng.uniform(0.2, 0.9, n), colors=rng.uniform(0, 1, (n, 3)))
+    m = H.single_triangle(c, [(5, 4), (60, 10), (30, 44)], 20.0 - c.viewmat[2, 3], 0.6)
+    sc = H.scene(g, [m], c, tile=16)
+    k = cn.Primitives(sc, 0).dbits[cn.Primitives(sc, 0).valid]
+    assert (int(k.max()) >> 16) - (int(k.min()) >> 16) + 1 > 255
+    out, fr = gpu_render(ctx, sc, tile=16)
+    check_lists(sc, fr, 16)
+    check_image(sc, out)
+
+
 def test_multi_camera(ctx):
     sc = S.small_scene(51, 48, 40, 800, mesh_subdiv=2, sh_degree=3, n_cams=3)
     out, fr = gpu_render(ctx, sc)
@@ -130,9 +153,7 @@ def test_background_and_no_early_exit(ctx):
     out, _ = gpu_render(ctx, sc, bg=bg)
     check_image(sc, out, bg=bg)
     out2, _ = gpu_render(ctx, sc, t_eps=0.0)
-    ref = R.render_image(sc, t_eps=None)
-    ok = ~ref["tie"]
-    assert np.abs(out2[0, ..., :3] - ref["rgb"])[ok].max() <= TOL
+    check_ref(out2[0], R.render_image(sc, t_eps=None))
 
 
 def test_empty_and_degenerate_inputs(ctx):
@@ -269,8 +290,5 @@ def test_wide_records_fill_unstaged(ctx):
     out, fr = gpu_render(ctx, sc, tile=8, t_eps=-1.0)
     k = check_lists(sc, fr, 8)
     assert k > 2048 * 20
-    ref = R.render_image(sc, 0, t_eps=None)
-    ok = ~ref["tie"]  # (~2,000 fragments per pixel: 9% of the pixels hold an alpha within 1e-6 of 1/255)
-    assert ok.mean() > 0.85
-    assert np.abs(out[0, ..., :3] - ref["rgb"])[ok].max() <= TOL
-    assert np.abs(out[0, ..., 3] - ref["T"])[ok].max() <= TOL
+    # (~2,000 fragments per pixel: 9% of the pixels hold an alpha within 1e-6 of 1/255)
+    check_ref(out[0], R.render_image(sc, 0, t_eps=None), tie_max=0.15)
