@@ -5,8 +5,9 @@
 // Radix pass = upsweep (per-block digit histograms, digit-major) -> exclusive
 // scan of the histograms -> downsweep (each block re-reads its elements in
 // input order and scatters them; ranks among equal digits come from
-// __match_any_sync inside a warp and per-warp running counts, so the order of
-// equal keys is preserved: the sort is stable).
+// match_digit8 inside a warp and per-warp running counts, so the order of
+// equal keys is preserved: the sort is stable).  The binning stage's own
+// sorts use the single-sweep passes at the end of this file.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -25,6 +26,21 @@ inline int radix_items(int64_t n_cap) { return n_cap <= kRsSmallMax ? 8 : 16; }
 inline int64_t radix_blocks(int64_t n_cap) {
     const int64_t tile = (int64_t)kRsThreads * radix_items(n_cap);
     return n_cap > 0 ? (n_cap + tile - 1) / tile : 1;
+}
+
+// The lanes of the (converged) warp whose 8-bit digit d equals this lane's,
+// among the lanes with `valid` set (0 for an invalid lane): eight ballots,
+// one per digit bit.  Used instead of __match_any_sync, which measured far
+// slower here (about 280 cycles per instruction in a histogram kernel).
+__device__ __forceinline__ unsigned match_digit8(uint32_t d, bool valid) {
+    unsigned peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+    for (int bit = 0; bit < 8; ++bit) {
+        const bool on = (d >> bit) & 1u;
+        const unsigned b = __ballot_sync(0xffffffffu, on);
+        peers &= on ? b : ~b;
+    }
+    return valid ? peers : 0u;
 }
 
 // ---- exclusive scan of uint32 (sum must fit in uint32) ------------------------
@@ -285,7 +301,7 @@ static __global__ void __launch_bounds__(kRsThreads) radix_downsweep_kernel(
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
-        const unsigned peers = __match_any_sync(0xffffffffu, dig[k]);
+        const unsigned peers = match_digit8(dig[k], dig[k] < 256u);
         const uint32_t lr = __popc(peers & lt);
         const uint32_t before = dig[k] < 256u ? wcnt[w][dig[k]] : 0u;
         __syncwarp();
@@ -443,20 +459,6 @@ __device__ __forceinline__ DepthDigits depth_digits(const uint32_t* __restrict__
 
 constexpr int kHistThreads = 1024;  // block size of the binning kernels that count digits
 
-// The lanes of the (converged) warp whose 8-bit digit d equals this lane's,
-// among the lanes with `valid` set (0 for an invalid lane): eight ballots,
-// one per digit bit.  Used instead of __match_any_sync, which measured far
-// slower here (about 280 cycles per instruction in a histogram kernel).
-__device__ __forceinline__ unsigned match_digit8(uint32_t d, bool valid) {
-    unsigned peers = __ballot_sync(0xffffffffu, valid);
-#pragma unroll
-    for (int bit = 0; bit < 8; ++bit) {
-        const bool on = (d >> bit) & 1u;
-        const unsigned b = __ballot_sync(0xffffffffu, on);
-        peers &= on ? b : ~b;
-    }
-    return valid ? peers : 0u;
-}
 
 // Look-back words of one radix pass: per tile one 32-bit word per digit
 // (bit 31 set once written, the tile's count below it), and per group of
