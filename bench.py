@@ -42,6 +42,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="umgs", choices=["umgs", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-spatial-order", action="store_true",
+                   help="keep the Gaussians in the order generated instead of umgs_spatial_order's")
     p.add_argument("--n-gauss", type=int, default=1_000_000)
     p.add_argument("--no-forms", action="store_true", help="skip the multi-view / differentiable / mixed forms")
     p.add_argument("--forms", default="all",
@@ -169,6 +171,16 @@ def run_umgs(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     ctx = umgs.Context(local_rank)
     g = umgs.gaussians_to_device(sc.gaussians, dev)
+    # the model stored in spatial order once, when it is loaded (before the
+    # binding): umgs_spatial_order's Morton order of the means, every
+    # per-Gaussian array gathered by it
+    order = "index order (as generated)"
+    if not args.no_spatial_order:
+        perm = umgs.spatial_order(ctx, g.means).long()
+        g = umgs.DevGaussians(*(x.index_select(0, perm).contiguous() for x in (g.means, g.quats, g.scales,
+                                                                               g.opacities, g.sh)), g.sh_degree)
+        del perm
+        order = "spatial: Morton order of the means (umgs_spatial_order), applied once at load"
     mesh = umgs.mesh_to_device(sc.meshes[0], dev)
     PV = torch.as_tensor(sc.proxy_verts).to(dev)
     PF = torch.as_tensor(sc.proxy_faces).to(dev)
@@ -380,7 +392,7 @@ def run_umgs(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "resolution": [W, H], "gaussians": n, "sh_degree": 3,
                    "triangles": int(sc.meshes[0].nf), "proxy_faces": int(sc.proxy_faces.shape[0]),
-                   "binding": bind_info, "tile": 16, "keys_per_frame": int(nkeys),
+                   "binding": bind_info, "gaussian_order": order, "tile": 16, "keys_per_frame": int(nkeys),
                    "l2": "inputs larger than L2 (Gaussians 236 MB per frame)", "parallelism": "replicas"},
         "e2e": {"value": round(1e3 / e2e_ms * world, 3), "unit": "frames/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},

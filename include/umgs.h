@@ -464,6 +464,22 @@ umgs_status umgs_deform_csr(umgs_ctx* ctx, const umgs_gaussians* rest, const int
                             const int32_t* proxy_f, int64_t nv, int64_t nf, int32_t mode, float* out_means,
                             float* out_cov3d, float* out_quats, void* stream);
 
+/* Spatial order of n Gaussians (a layout tool; no paper counterpart):
+ * out_perm[i] = the index of the Gaussian that comes i-th in the order of the
+ * 30-bit Morton code of its mean (10 bits per axis over the bounding box of
+ * the finite means: q = trunc(clamp((x - lo) * (1024 / (hi - lo)), 0, 1023)),
+ * a non-finite coordinate counts as lo; equal codes in index order).  A
+ * model stored in that order (every per-Gaussian array gathered by out_perm
+ * once, when it is loaded, before the binding) keeps Gaussians that are close
+ * in space close in memory: the deformation's gathers of proxy-vertex rows
+ * then hit the cache.  The renderer's results do not depend on the order
+ * beyond the unified ids that break exact depth ties.
+ *   means [n,3] float device; out_perm [n] int32 device.
+ * Synchronises `stream`; keeps a workspace of 16 n bytes in the context.
+ * Errors: INVALID_ARG (NULL arrays, n < 0 or n >= 2^31 - 1), OUT_OF_MEMORY,
+ * CUDA. */
+umgs_status umgs_spatial_order(umgs_ctx* ctx, const float* means, int64_t n, int32_t* out_perm, void* stream);
+
 /* ---- multi-view form: CUDA graph and autotuning -----------------------------
  *
  * umgs_render_graph_create renders once (an ordinary umgs_render into

@@ -141,6 +141,7 @@ struct umgs_ctx {
     int64_t vtab_rows = 0;
     umgs::DevBuf bind_ws;       // binding workspace (grid header + cell entries)
     umgs::DevBuf bind_cams, bind_cnt;
+    umgs::DevBuf order_ws;      // umgs_spatial_order workspace
 };
 
 namespace umgs {

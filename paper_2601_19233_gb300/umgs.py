@@ -142,6 +142,8 @@ def lib():
         L.umgs_deform_csr.argtypes = [vp, ctypes.POINTER(CGaussians), vp, vp, vp, vp, vp, i64, i64, i32, vp, vp,
                                       vp, vp]
         L.umgs_deform_csr.restype = ctypes.c_int
+        L.umgs_spatial_order.argtypes = [vp, vp, i64, vp, vp]
+        L.umgs_spatial_order.restype = ctypes.c_int
         L.umgs_frame_reserve.argtypes = [vp, i64]
         L.umgs_frame_reserve.restype = ctypes.c_int
         L.umgs_frame_check.argtypes = [vp, vp]
@@ -432,6 +434,15 @@ def binding_csr(ctx: Context, face: torch.Tensor, bary: torch.Tensor, proxy_f: t
                                      int(proxy_f.shape[0]), _ptr(offsets), _ptr(entries), int(entries.shape[0]),
                                      ctypes.byref(total), _stream(stream)), "umgs_binding_csr")
     return offsets, entries
+
+
+def spatial_order(ctx: Context, means: torch.Tensor, stream=None) -> torch.Tensor:
+    """umgs_spatial_order: int32 [n] permutation (Morton order of the means)."""
+    assert means.dtype == torch.float32 and means.dim() == 2 and means.shape[1] == 3, "means must be float32 [n,3]"
+    n = int(means.shape[0])
+    perm = torch.empty((n,), dtype=torch.int32, device=torch.device("cuda", ctx.device))
+    ctx.check(lib().umgs_spatial_order(ctx._h, _ptr(means), n, _ptr(perm), _stream(stream)), "umgs_spatial_order")
+    return perm
 
 
 def deform_csr(ctx: Context, rest: DevGaussians, offsets: torch.Tensor, entries: torch.Tensor,
