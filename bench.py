@@ -47,7 +47,7 @@ def parse():
     p.add_argument("--n-gauss", type=int, default=1_000_000)
     p.add_argument("--no-forms", action="store_true", help="skip the multi-view / differentiable / mixed forms")
     p.add_argument("--forms", default="all",
-                   help="comma list of the forms to run: multiview, differentiable (with soft edges), mixed, nested")
+                   help="comma list of the forms to run: multiview, closeup, differentiable (with soft edges), mixed, nested")
     p.add_argument("--forms-only", action="store_true",
                    help="run the selected forms only (no 1080p frame) and print their JSON")
     return p.parse_args()
@@ -547,7 +547,7 @@ def _time(fn, steps, warm=2):
     return a.elapsed_time(b) / steps
 
 
-FORMS = ("multiview", "differentiable", "mixed", "nested")
+FORMS = ("multiview", "closeup", "differentiable", "mixed", "nested")
 
 
 def run_forms(ctx, dev, steps, crops=None, which=FORMS):
@@ -593,6 +593,31 @@ def run_forms(ctx, dev, steps, crops=None, which=FORMS):
             "split_ms": split_ms,
             "autotuned": {"tile_size": best.tile_size, "sched": best.sched, "split": best.split, "ms": round(t_tune, 3)},
             "keys": int(fr.counts()[0]), "evaluations": int(evals_plain), "plain_stages_ms": mv_stages}
+        del gr, fr, fr2, out, g, ms
+        torch.cuda.empty_cache()
+    if "closeup" in which:
+        # the per-tile work split where it pays: 16 tiles of ~40k records
+        sc = scenes.closeup_scene()
+        g = umgs.gaussians_to_device(sc.gaussians, dev)
+        ms = [umgs.mesh_to_device(m, dev) for m in sc.meshes]
+        out = torch.empty((1, 512, 512, 4), device=dev)
+        fr = umgs.Frame(ctx)
+        t_plain = _time(lambda: umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(16), out=out, frame=fr), steps)
+        nk = int(fr.counts()[0])
+        split_ms = {str(sp): round(_time(lambda: umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(16, split=sp),
+                                                             out=out, frame=fr), steps), 3)
+                    for sp in (512, 1024, 2048)}
+        best, t_tune = umgs.autotune(ctx, g, ms, sc.cameras, umgs.render_opts(16), out)
+        fr2 = umgs.Frame(ctx)
+        gr = umgs.Graph(ctx, fr2, g, ms, sc.cameras, best, out, key_headroom=1.0)
+        t_graph = _time(lambda: gr.launch(), steps)
+        gr.check()
+        forms["split_closeup_512"] = {
+            "workload": "512x512 close-up: 400k faint Gaussians in a 64x64 px square (16 tiles of ~40k records, "
+                        "no early termination) + 320-face icosphere",
+            "plain_ms": round(t_plain, 3), "split_ms": split_ms,
+            "autotuned": {"tile_size": best.tile_size, "sched": best.sched, "split": best.split, "ms": round(t_tune, 3)},
+            "graph_ms": round(t_graph, 3), "graph_vs_plain": round(t_plain / t_graph, 2), "keys": nk}
         del gr, fr, fr2, out, g, ms
         torch.cuda.empty_cache()
     if "differentiable" in which:

@@ -716,6 +716,25 @@ __global__ void __launch_bounds__(kDefBlock) deform_gaussians_compact_kernel(
             }
         }
         const int4* row = reinterpret_cast<const int4*>(entries + start);  // two entries per int4
+        if (CSR) {
+            // runs of even length: one 16-byte load takes two entries, no
+            // tail; an index out of range reads row 0 with weight 0 and marks
+            // the Gaussian bad
+            const float4* tp = tab + part;
+            const uint32_t unv = (uint32_t)min(nv, (int64_t)0xffffffff);
+#pragma unroll 2
+            for (int j = 0; j < c; j += 2) {
+                const int4 e = row[j >> 1];
+                const bool ok0 = (uint32_t)e.x < unv, ok1 = (uint32_t)e.z < unv;
+                bad |= !(ok0 && ok1);
+                const float4 t0 = tp[(uint64_t)(ok0 ? (uint32_t)e.x : 0u) << 2];
+                const float4 t1 = tp[(uint64_t)(ok1 ? (uint32_t)e.z : 0u) << 2];
+                const float w0 = ok0 ? __int_as_float(e.y) : 0.f, w1 = ok1 ? __int_as_float(e.w) : 0.f;
+                a.x += w0 * t0.x; a.y += w0 * t0.y; a.z += w0 * t0.z; a.w += w0 * t0.w;
+                a.x += w1 * t1.x; a.y += w1 * t1.y; a.z += w1 * t1.z; a.w += w1 * t1.w;
+            }
+            c = 0;  // (the padded form's loop below does nothing)
+        }
         for (int j = 0; j < c; j += 4) {
             const int4 e01 = row[j >> 1];
             const int4 e23 = j + 2 < c ? row[(j >> 1) + 1] : make_int4(0, 0, 0, 0);

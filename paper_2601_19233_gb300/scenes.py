@@ -373,6 +373,25 @@ def config4(seed=1004, n_gauss=6_000_000, torus_ab=(1000, 1000), width=3840, hei
     return Scene(g, [Mesh(V, F, vcol, None, falpha)], [cam], tile=16)
 
 
+def closeup_scene(seed=1006, size=512, n_gauss=400_000):
+    """A close-up of a dense, faint cluster (the load imbalance the per-tile
+    work split is for): 400k Gaussians of opacity 0.001-0.003 and projected
+    sigma ~1.3 px packed into a 64 x 64 pixel square at the image centre, so
+    that 16 tiles hold ~40k records each and no pixel reaches T < 1e-4, the
+    rest of the image nearly empty; a small opaque icosphere beside it."""
+    rng = np.random.default_rng(seed)
+    fx = focal_from_fov(size, 60.0)
+    cam = front_camera(size, size, fx, 3.0)
+    half = 32.0 * 3.0 / fx  # 32 px at depth 3
+    means = np.c_[rng.uniform(-half, half, (n_gauss, 2)), rng.uniform(-0.05, 0.05, n_gauss)].astype(np.float32)
+    g = make_gaussians(rng, means, math.log(1.3 * 3.0 / fx), 0)
+    g.opacities[:] = rng.uniform(0.001, 0.003, size=n_gauss).astype(np.float32)
+    Vs, Fs = icosphere(2, 0.1)
+    Vs = (Vs + np.array([0.6, 0.0, 0.0], np.float32)).astype(np.float32)
+    vcol = rng.uniform(0, 1, size=(Vs.shape[0], 3)).astype(np.float32)
+    return Scene(g, [Mesh(Vs, Fs, vcol, None, np.ones(Fs.shape[0], np.float32))], [cam], tile=16)
+
+
 def nested_scene(seed=1005, size=256, n_gauss=30_000, bowl_subdiv=3, bowl_alpha=0.35, n_cams=1):
     """Nested transparency (the setting of Sec. 4.1, Fig. 5b): a Gaussian
     object (three overlapping coloured boxes of points, 0.5 across) and an
