@@ -499,6 +499,11 @@ __global__ void __launch_bounds__(Bwd2<TS>::NT, TS == 16 ? 5 : 1) composite_bwd2
                 const uint32_t rx = __float_as_uint(q2.y), ry = __float_as_uint(q2.z);
                 const bool inx = px >= (int)(rx & 0xffff) && px <= (int)(rx >> 16);
                 const float dx = __fsub_rn(qx, q0.x);
+                // (the conic of the record, once for both pixels)
+                float ca, cb, cc;
+                factor_conic(q0.z, q0.w, q1.x, ca, cb, cc);
+                const float A = -2.f * kLn2 * ca, B = -kLn2 * cb, C = -2.f * kLn2 * cc;
+                const float Adx = A * dx, Bdx = B * dx;
                 float v[16];
 #pragma unroll
                 for (int e = 0; e < 16; ++e) v[e] = 0.f;
@@ -529,11 +534,8 @@ __global__ void __launch_bounds__(Bwd2<TS>::NT, TS == 16 ? 5 : 1) composite_bwd2
                         T[p] = Tk;
                         if (ag <= kAlphaMax) {
                             const float dpow = dalpha * alpha;
-                            float ca, cb, cc;
-                            factor_conic(q0.z, q0.w, q1.x, ca, cb, cc);
-                            const float A = -2.f * kLn2 * ca, B = -kLn2 * cb, C = -2.f * kLn2 * cc;
-                            v[0] += dpow * (A * dx + B * dy);
-                            v[1] += dpow * (B * dx + C * dy);
+                            v[0] += dpow * (Adx + B * dy);
+                            v[1] += dpow * (Bdx + C * dy);
                             v[2] += -0.5f * dpow * dx * dx;
                             v[3] += -dpow * dx * dy;
                             v[4] += -0.5f * dpow * dy * dy;

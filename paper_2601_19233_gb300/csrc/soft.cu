@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(TS * TS) composite_soft_kernel(
     pdl_enter();
     constexpr int NT = TS * TS;
     __shared__ float4 s_rec[kSoftBatch][10];
+    __shared__ SoftEdges s_edges[kSoftBatch];  // per triangle record: its coverage constants
     __shared__ uint32_t s_id[kSoftBatch];
     __shared__ uint32_t s_wmask[kSoftBatch];
     __shared__ uint8_t s_list[(NT / 32) * kSoftBatch];
@@ -75,6 +76,7 @@ __global__ void __launch_bounds__(TS * TS) composite_soft_kernel(
                 const TRec& tr = *reinterpret_cast<const TRec*>(&s_rec[k][0]);
                 wm = box_block_mask<TS>((int)(tr.rx & 0xffff), (int)(tr.rx >> 16), (int)(tr.ry & 0xffff),
                                         (int)(tr.ry >> 16), tile_x0, tile_y0);
+                soft_edges(tr, s_edges[k]);
             }
             s_wmask[k] = wm;
         }
@@ -110,8 +112,8 @@ __global__ void __launch_bounds__(TS * TS) composite_soft_kernel(
                 if (px < (int)(t.rx & 0xffff) || px > (int)(t.rx >> 16) || py < (int)(t.ry & 0xffff) ||
                     py > (int)(t.ry >> 16))
                     continue;
-                float cov[4], sg, il[3], sgm[4][3];
-                soft_coverage(t, qx, qy, cov, sg, il, sgm);
+                float cov[4];
+                soft_coverage_staged(t, s_edges[k], qx, qy, cov);
                 // attributes at the pixel centre: perspective-correct
                 // barycentrics of the unsnapped triangle, clamped at 0
                 float lam[3];

@@ -55,6 +55,52 @@ __device__ __forceinline__ void soft_coverage(const TRec& t, float qx, float qy,
     }
 }
 
+// Per-triangle constants of the forward's coverage, computed once per
+// staged record: the scale of edge e's exponent k[e] = sg log2(e) / (L_e
+// sigma) (k[3] = sg: 0 for a triangle of zero area, which covers nothing),
+// and d[e][j], the change of lambda_e from the pixel centre to sample j
+// (lambda_e is affine in the sample position: d = (v_a - v_b) dx_j +
+// (u_b - u_a) dy_j).
+struct SoftEdges {
+    float k[4];
+    float d[3][4];
+};
+__device__ __forceinline__ void soft_edges(const TRec& t, SoftEdges& se) {
+    const float sg = soft_orientation(t);
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int a = (e + 1) % 3, b = (e + 2) % 3;
+        const float ex = t.u[b] - t.u[a], ey = t.v[b] - t.v[a];
+        const float L = sqrtf(ex * ex + ey * ey);
+        se.k[e] = L > 0.f ? sg * 1.4426950408889634f * t.pad2 / L : 0.f;
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            se.d[e][j] = (t.v[a] - t.v[b]) * ((float)sample_dx(j) * (1.f / 256.f)) +
+                         (t.u[b] - t.u[a]) * ((float)sample_dy(j) * (1.f / 256.f));
+    }
+    se.k[3] = sg;
+}
+// c^j of pixel centre (qx, qy) from the staged constants: lambda_e at the
+// centre (the relative form) plus the sample offsets, and per sample one
+// reciprocal of the product of the three 1 + 2^(-k lambda) (the product of
+// the three logistic terms; an overflow to inf gives 0, the limit)
+__device__ __forceinline__ void soft_coverage_staged(const TRec& t, const SoftEdges& se, float qx, float qy,
+                                                     float c[4]) {
+    float lam[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int a = (e + 1) % 3, b = (e + 2) % 3;
+        lam[e] = (t.u[a] - qx) * (t.v[b] - qy) - (t.u[b] - qx) * (t.v[a] - qy);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float den = 1.f;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) den *= 1.f + fast_exp2(-se.k[e] * (lam[e] + se.d[e][j]));
+        c[j] = se.k[3] != 0.f ? 1.f / den : 0.f;
+    }
+}
+
 // Adds d(sum_j dc[j] c^j) / d(u_k, v_k) to du[k], dv[k] (k = vertex):
 // dc^j/dd_e = c^j (1 - sigmoid_e) / sigma and, with L = |P_b - P_a|,
 // dd/dx = sg (dlambda/dx) / L - d (dL/dx) / L.
