@@ -281,12 +281,17 @@ class Primitives:
         self.dbits = depth_bits(self.depth)
         # triangle edge data concatenated over meshes, indexed by (id - ng)
         if self.tris:
+            # orientation of each triangle: the sign of its snapped integer area
+            self.tri_sign = np.concatenate(
+                [np.sign((t["sx"][:, 1] - t["sx"][:, 0]) * (t["sy"][:, 2] - t["sy"][:, 0])
+                         - (t["sx"][:, 2] - t["sx"][:, 0]) * (t["sy"][:, 1] - t["sy"][:, 0])) for t in self.tris], 0)
             self.A = np.concatenate([t["A"] for t in self.tris], 0)
             self.B = np.concatenate([t["B"] for t in self.tris], 0)
             self.Cb = np.concatenate([t["Cb"] for t in self.tris], 0)
             self.Cu = np.concatenate([t["Cu"] for t in self.tris], 0)
         else:
             self.A = self.B = self.Cb = self.Cu = np.zeros((0, 3), np.int64)
+            self.tri_sign = np.zeros(0, np.int64)
 
     def tile_rects(self, ts):
         r = self.rect

@@ -224,8 +224,10 @@ def composite_torch(scene, p, fr, pixels, table, bg=(0.0, 0.0, 0.0)):
         ta = torch.where(selt, al, ta)
         tc = torch.where(selt[..., None], col, tc)
         if fr.soft:
-            area = (U_[..., 1] - U_[..., 0]) * (V_[..., 2] - V_[..., 0]) - (U_[..., 2] - U_[..., 0]) * (V_[..., 1] - V_[..., 0])
-            sg = torch.sign(area).detach()
+            # the triangle's orientation: the sign of its snapped integer area
+            # (render.soft_coverage), a constant of the decision table
+            tl = np.where(sel, gid - fr.P.ng, 0)
+            sg = torch.as_tensor(np.where(sel, fr.P.tri_sign[tl], 0), dtype=DT)
             cov = []
             for j in range(4):
                 sx = px + float(cn_offsets[j, 0]) / 256.0

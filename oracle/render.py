@@ -131,18 +131,22 @@ def soft_dilation(sigma):
     return int(np.ceil(8.0 * float(np.float32(sigma)))) if sigma else 0
 
 
-def soft_coverage(tu, tv, px, py, sigma):
+def soft_coverage(tu, tv, px, py, sigma, sg=None):
     """Soft coverage c^j (j = 0..3, the samples of canonical.SAMPLE_OFFSETS)
     of pixel (px, py) by triangles with unsnapped screen vertices tu, tv
     ([K,3] fp64, original vertex order): c^j = prod_e sigmoid(d_e / sigma),
     d_e = s * lambda_e / |P_b - P_a| for the edge (a, b) = (e+1, e+2) opposite
     vertex e, lambda_e(x) = (u_a - x)(v_b - y) - (u_b - x)(v_a - y) twice the
-    signed area of (x, P_a, P_b) and s the sign of the triangle's signed
-    area.  A triangle of zero area covers nothing.  Returns [K,4]."""
+    signed area of (x, P_a, P_b) and s the triangle's orientation: `sg` [K],
+    the sign of its snapped integer area (canonical.Primitives.tri_sign, the
+    orientation the setup uses), or, when not given, the sign of the
+    unsnapped area.  A triangle of zero area covers nothing.  Returns [K,4]."""
     tu = np.asarray(tu, np.float64).reshape(-1, 3)
     tv = np.asarray(tv, np.float64).reshape(-1, 3)
-    area = (tu[:, 1] - tu[:, 0]) * (tv[:, 2] - tv[:, 0]) - (tu[:, 2] - tu[:, 0]) * (tv[:, 1] - tv[:, 0])
-    sg = np.sign(area)
+    if sg is None:
+        area = (tu[:, 1] - tu[:, 0]) * (tv[:, 2] - tv[:, 0]) - (tu[:, 2] - tu[:, 0]) * (tv[:, 1] - tv[:, 0])
+        sg = np.sign(area)
+    sg = np.asarray(sg, np.float64).reshape(-1)
     out = np.ones((tu.shape[0], 4))
     for j in range(4):
         sx = px + 0.5 + cn.SAMPLE_OFFSETS[j, 0] / 256.0
@@ -301,7 +305,7 @@ class Frame:
                          mask=int(mask[k]), centre=bool(cen[k]))
                 if self.soft:
                     fv = np.asarray(self.scene.meshes[mi].faces, np.int64)[fi]
-                    f["cov"] = soft_coverage(vu[fv], vv[fv], px, py, self.soft)[0]
+                    f["cov"] = soft_coverage(vu[fv], vv[fv], px, py, self.soft, P.tri_sign[loc[k]:loc[k] + 1])[0]
                 frags.append(f)
         frags.sort(key=lambda f: (int(P.dbits[f["id"]]), f["id"]))
         return frags

@@ -73,7 +73,7 @@ struct __align__(16) TRec {
     int32_t const_alpha;
     int32_t tex;
     long long C[3];
-    long long pad1;
+    long long orient;  // sign of the snapped integer area (+1 / -1): the setup's orientation
     float u[3], v[3];
     float iz[3];
     float col[9];

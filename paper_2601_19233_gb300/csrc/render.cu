@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(256) setup_triangles_kernel(
         for (int k = 0; k < 9; ++k) t.col[k] = col[k];
         t.const_alpha = const_alpha;
         t.tex = uv ? tex + 1 : 0;
-        t.pad1 = 0;
+        t.orient = area > 0 ? 1 : -1;
         t.rx = bi.rx;
         t.ry = bi.ry;
         t.pad2 = isig;  // soft-edge coverage: 1/edge_sigma (0: binary sample coverage)

@@ -7,7 +7,7 @@
 //   lambda_e(s) = (u_a - s_x)(v_b - s_y) - (u_b - s_x)(v_a - s_y)
 //     (twice the signed area of (s, P_a, P_b), the stable relative form),
 //   d_e = sg lambda_e / |P_b - P_a|   (signed distance, positive inside;
-//     sg = sign of the triangle's signed area),
+//     sg = sign of the snapped integer area, TRec::orient),
 //   c^j = prod_e sigmoid(d_e / sigma),  sigma = 1 / t.pad2.
 // A triangle of zero area covers nothing.
 #pragma once
@@ -16,9 +16,11 @@
 
 namespace umgs {
 
+// sg: the orientation the setup found from the snapped integer area (the
+// one that orders the edge functions and culls zero-area triangles), not the
+// fp32 area of the unsnapped vertices, whose sign can differ on a sliver
 __device__ __forceinline__ float soft_orientation(const TRec& t) {
-    const float area = (t.u[1] - t.u[0]) * (t.v[2] - t.v[0]) - (t.u[2] - t.u[0]) * (t.v[1] - t.v[0]);
-    return area > 0.f ? 1.f : (area < 0.f ? -1.f : 0.f);
+    return t.orient > 0 ? 1.f : (t.orient < 0 ? -1.f : 0.f);
 }
 
 // sigmoid(x) with the hardware exponential __expf (relative error ~2^-21 over

@@ -14,6 +14,7 @@ from oracle import canonical as cn
 from oracle import grad as OG
 from oracle import render as R
 from paper_2601_19233_gb300 import scenes as S
+from tests import helpers as H
 from tests.test_gpu_render import check_ref
 
 pytestmark = pytest.mark.gpu
@@ -94,6 +95,34 @@ def test_soft_gradients(ctx, seed, W, H, n, sigma, valpha):
         assert np.abs(gk - r).max() <= 1e-3 * scale + 1e-6, (k, np.abs(gk - r).max(), scale)
     # coverage carries gradient to the vertex positions that the binary form has not
     assert np.abs(ref["verts0"] - hard_ref["verts0"]).max() > 0.1 * np.abs(ref["verts0"]).max()
+
+
+def test_soft_sliver_takes_the_setup_orientation(ctx):
+    """A sliver whose snapped integer area and unsnapped area have opposite
+    signs: the kernels take the soft coverage's orientation from the triangle
+    record (the setup's integer sign), as the oracle does: image and vertex
+    gradients match it."""
+    from paper_2601_19233_gb300 import umgs
+    from tests.test_oracle_soft import SLIVER
+    c = H.cam(48, 32)
+    g = H.gaussians(np.array([[0.1, 0.05, 0.3]]), scales=np.full((1, 3), 0.08, np.float32), opac=[0.5],
+                    colors=[[0.2, 0.8, 0.4]])
+    sc = H.scene(g, [H.single_triangle(c, SLIVER, 0.2, 0.7)], c, tile=8)
+    out, fr, gd, ms = _render(ctx, sc, 0.5, 8, save=True)
+    _check_lists(sc, fr, 8, 0.5)
+    ref = R.render_image(sc, soft=0.5)
+    check_ref(out.cpu().numpy()[0], ref)
+    rng = np.random.default_rng(3)
+    gC = rng.normal(size=(32, 48, 3))
+    gT = rng.normal(size=(32, 48))
+    gC[ref["tie"]] = 0
+    gT[ref["tie"]] = 0
+    r, _, _ = OG.image_grad(sc, gC, gT, soft=0.5)
+    dl = torch.as_tensor(np.concatenate([gC, gT[..., None]], -1)[None].astype(np.float32)).cuda()
+    got = umgs.render_backward(ctx, fr, gd, ms, dl)
+    torch.cuda.synchronize()
+    gk = got["verts0"].cpu().numpy().reshape(r["verts0"].shape)
+    assert np.abs(gk - r["verts0"]).max() <= 1e-3 * np.abs(r["verts0"]).max() + 1e-6
 
 
 def test_soft_invalid_options_rejected(ctx):

@@ -19,6 +19,7 @@ from oracle import canonical as cn
 from oracle import grad as G
 from oracle import render as R
 from paper_2601_19233_gb300 import scenes as S
+from tests import helpers as H
 
 
 def _samples(px, py):
@@ -192,3 +193,41 @@ def test_widened_rects_are_the_binary_rects_plus_the_dilation():
         assert np.array_equal(s[:, 3], np.minimum(h[:, 3] + R_, cam.height - 1))
         # widening only adds triangles (those whose sample rect was empty)
         assert np.all(soft["valid"][hard["valid"]])
+
+
+# a sliver whose snapped integer area (the setup's orientation) has the
+# opposite sign of its unsnapped area
+SLIVER = [(5.027790005723492, 10.736210131921993), (14.411724373399148, 12.507311622341327),
+          (41.61529358247677, 17.643240721287356)]
+
+
+def _sliver_scene(pts=SLIVER):
+    c = H.cam(48, 32)
+    return H.scene(H.no_gaussians(), [H.single_triangle(c, pts, 0.2, 0.7)], c, tile=8)
+
+
+def test_soft_orientation_is_the_setup_orientation():
+    """The orientation sg of the soft coverage is the sign of the snapped
+    integer area (the one the setup orders the edges by and the kernels store
+    in the triangle record), not the sign of the unsnapped area: exact on both
+    sides.  On this sliver (its middle vertex almost on the segment between
+    the other two) the two signs disagree, and the coverage along it differs
+    with the choice."""
+    sc = _sliver_scene()
+    P = cn.Primitives(sc, 0, dilate=R.soft_dilation(0.5))
+    t = P.tris[0]
+    sx, sy = t["sx"][0], t["sy"][0]
+    snapped = (sx[1] - sx[0]) * (sy[2] - sy[0]) - (sx[2] - sx[0]) * (sy[1] - sy[0])
+    fr = R.Frame(sc, 0, soft=0.5)
+    vu, vv, _ = fr.V[0]
+    f = np.asarray(sc.meshes[0].faces[0], np.int64)
+    tu, tv = vu[f][None], vv[f][None]
+    unsnapped = (tu[0, 1] - tu[0, 0]) * (tv[0, 2] - tv[0, 0]) - (tu[0, 2] - tu[0, 0]) * (tv[0, 1] - tv[0, 0])
+    assert P.tri_sign[0] == np.sign(snapped) and np.sign(snapped) != np.sign(unsnapped)
+    px, py = 4, 10  # a pixel on the sliver
+    c_setup = R.soft_coverage(tu, tv, px, py, 0.5, P.tri_sign[:1])[0]
+    c_fp = R.soft_coverage(tu, tv, px, py, 0.5, np.sign([unsnapped]))[0]
+    assert np.abs(c_setup - c_fp).max() > 0.02
+    # the fragments the oracle composites take the setup's sign
+    frag = [g for g in fr.fragments_at(px, py) if g["kind"] == "t"][0]
+    assert np.allclose(frag["cov"], c_setup, rtol=0, atol=1e-15)
