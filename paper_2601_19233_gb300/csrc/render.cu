@@ -679,6 +679,8 @@ __global__ void __launch_bounds__(256) emit_region_pairs_kernel(
     PassLookback lbr, int64_t rtile, uint32_t* __restrict__ rhist, int rpasses) {
     pdl_enter();
     __shared__ uint32_t s_rh[3 * 256];
+    __shared__ uint2 s_rect[kEmitRecords];  // per record of the block: tile rect (x0 | x1 << 16, y0 | y1 << 16)
+    __shared__ uint32_t s_rec[kEmitRecords];  // ... and its record index
     __shared__ uint32_t s_wtot[8];
     __shared__ uint32_t s_id;
     __shared__ unsigned long long s_base[8];
@@ -710,12 +712,17 @@ __global__ void __launch_bounds__(256) emit_region_pairs_kernel(
 #pragma unroll
     for (int j = 0; j < kEmitRounds; ++j) {
         const int64_t i = wbase + j * 32 + lane;
+        const int local = warp * 256 + j * 32 + lane;
         cnt[j] = 0;
         if (i < n) {
-            const BinInfo bi = bin[pv[i]];
+            const uint32_t rec = pv[i];
+            const BinInfo bi = bin[rec];
             if (bi.valid) {
                 const RecordRects r = record_rects(bi, ts);
                 cnt[j] = r.gw * r.gh;
+                s_rect[local] = make_uint2((uint32_t)r.tx0 | ((uint32_t)r.tx1 << 16),
+                                           (uint32_t)r.ty0 | ((uint32_t)r.ty1 << 16));
+                s_rec[local] = rec;
             }
         }
         int inc = cnt[j];
@@ -750,14 +757,20 @@ __global__ void __launch_bounds__(256) emit_region_pairs_kernel(
 #pragma unroll
     for (int j = 0; j < kEmitRounds; ++j) {
         if (wbase + j * 32 >= n) break;  // (warp-uniform)
-        const int64_t i = wbase + j * 32 + lane;
+        const int local = warp * 256 + j * 32 + lane;
         RecordRects rr{0, 0, 0, 0, 0, 0, 1, 0};
         uint32_t id = 0, rbase = 0;
-        if (cnt[j] > 0) {
-            const uint32_t rec = pv[i];
+        if (cnt[j] > 0) {  // (the rect and record staged in step 1, no second gather)
+            const uint32_t rec = s_rec[local];
+            const uint2 q = s_rect[local];
             const int cam = (int)(rec / ntot);
             id = (uint32_t)(rec - (int64_t)cam * ntot);
-            rr = record_rects(bin[rec], ts);
+            rr.tx0 = (int)(q.x & 0xffffu); rr.tx1 = (int)(q.x >> 16);
+            rr.ty0 = (int)(q.y & 0xffffu); rr.ty1 = (int)(q.y >> 16);
+            rr.gx0 = rr.tx0 / kRegionTX;
+            rr.gy0 = rr.ty0 / kRegionTY;
+            rr.gw = rr.tx1 / kRegionTX - rr.gx0 + 1;
+            rr.gh = rr.ty1 / kRegionTY - rr.gy0 + 1;
             rbase = (uint32_t)cam * (uint32_t)regions_per_cam;
         }
         const int e0 = __shfl_sync(0xffffffffu, excl[j], 0);
