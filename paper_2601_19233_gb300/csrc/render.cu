@@ -1056,8 +1056,10 @@ __global__ void __launch_bounds__(kRegionThreads) region_count_kernel(
 // are staged in shared memory, tile by
 // tile (the chunk's tile counts are known from the counting pass), and then
 // written out as contiguous runs; a chunk with more than kFillStage entries
-// writes them directly.  Ballots and warp prefixes alternate between two
-// buffers, so one barrier per round orders their reuse.
+// writes them directly.  Every warp keeps the per-tile running slots itself
+// (lane t: tile t), so one barrier per round suffices, and ballots alternate
+// between two buffers: a warp writes round q + 2's ballots only after the
+// barrier of round q + 1, which every warp passes after its reads of round q.
 constexpr int kFillStage = 10240;  // staged ids per chunk (40 KB)
 __global__ void __launch_bounds__(kRegionThreads) region_fill_kernel(
     const uint32_t* __restrict__ rk, const uint32_t* __restrict__ rv, const uint32_t* __restrict__ coff,
@@ -1068,7 +1070,6 @@ __global__ void __launch_bounds__(kRegionThreads) region_fill_kernel(
     constexpr int NW = kRegionThreads / 32;
     __shared__ uint32_t s_bal[2][NW][32];
     __shared__ uint32_t s_pre[2][NW][32];
-    __shared__ uint32_t s_run[32];    // next slot of each tile (staged or global)
     __shared__ uint32_t s_cst[33];    // staged start of each tile
     __shared__ uint32_t s_base[32];   // global first slot of each tile's run
     __shared__ uint32_t s_stage[kFillStage];
@@ -1094,7 +1095,9 @@ __global__ void __launch_bounds__(kRegionThreads) region_fill_kernel(
     }
     __syncthreads();
     const bool staged = s_cst[32] <= (uint32_t)kFillStage;  // block-uniform
-    if (threadIdx.x < 32) s_run[threadIdx.x] = staged ? s_cst[threadIdx.x] : s_base[threadIdx.x];
+    // lane t of every warp: the next slot of tile t (staged or global),
+    // advanced by every round's count of the whole block
+    uint32_t run = staged ? s_cst[lane] : s_base[lane];
     uint32_t id[kRegionItems], m[kRegionItems];
 #pragma unroll
     for (int q = 0; q < kRegionItems; ++q) {
@@ -1110,23 +1113,26 @@ __global__ void __launch_bounds__(kRegionThreads) region_fill_kernel(
         if (c.e0 + q * kRegionThreads >= c.e1) break;  // block-uniform
         const int buf = q & 1;
         s_bal[buf][warp][lane] = warp_transpose32(m[q]);  // lane t: the warp's ballot of tile t
-        __syncthreads();  // (also orders s_run's first write before its use)
-        if (threadIdx.x < 32) {
-            uint32_t run = s_run[threadIdx.x];
-#pragma unroll
-            for (int w = 0; w < NW; ++w) {
-                s_pre[buf][w][threadIdx.x] = run;
-                run += __popc(s_bal[buf][w][threadIdx.x]);
-            }
-            s_run[threadIdx.x] = run;
-        }
         __syncthreads();
+        // lane t: this warp's first slot of tile t in this round (the counts of
+        // the warps before it), and every warp advances its own running slots
+        // by the round's total: no second barrier, no serial warp
+        uint32_t pre = run;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t cw = __popc(s_bal[buf][w][lane]);
+            pre += w < warp ? cw : 0u;
+            run += cw;
+        }
+        s_pre[buf][warp][lane] = pre;  // (a row of this warp's own)
+        __syncwarp();
         uint32_t mm = m[q];
         while (mm) {
             const int t = __ffs(mm) - 1;
             mm &= mm - 1u;
             dst[s_pre[buf][warp][t] + __popc(s_bal[buf][warp][t] & lt_mask)] = id[q];
         }
+        __syncwarp();
     }
     if (!staged) return;
     __syncthreads();
