@@ -628,11 +628,18 @@ def run_forms(ctx, dev, steps, crops=None, which=FORMS):
         pert = scenes.config3()
         pert.gaussians.means = (pert.gaussians.means + rng.normal(0, 0.01, pert.gaussians.means.shape)).astype(np.float32)
         pert.gaussians.sh = (pert.gaussians.sh + rng.normal(0, 0.05, pert.gaussians.sh.shape)).astype(np.float32)
+        o = np.clip(pert.gaussians.opacities.astype(np.float64), 1e-6, 1 - 1e-6)
+        logit = np.log(o / (1 - o)) + rng.normal(0, 0.2, o.shape)
+        pert.gaussians.opacities = (1 / (1 + np.exp(-logit))).astype(np.float32)
+        for m in pert.meshes:
+            m.verts = (m.verts + rng.normal(0, 0.005, m.verts.shape)).astype(np.float32)
+            m.vcolor = np.clip(m.vcolor + rng.normal(0, 0.05, m.vcolor.shape), 0, 1).astype(np.float32)
+        mp = [umgs.mesh_to_device(m, dev) for m in pert.meshes]
         g = umgs.gaussians_to_device(sc.gaussians, dev)
         ms = [umgs.mesh_to_device(m, dev) for m in sc.meshes]
         gp = umgs.gaussians_to_device(pert.gaussians, dev)
         nv = len(sc.cameras)
-        target = umgs.render(ctx, gp, ms, sc.cameras, umgs.render_opts(16)).clone()
+        target = umgs.render(ctx, gp, mp, sc.cameras, umgs.render_opts(16)).clone()
         out = torch.empty_like(target)
         fr = umgs.Frame(ctx)
         t_f = _time(lambda: umgs.render(ctx, g, ms, sc.cameras, umgs.render_opts(16), out=out, frame=fr), steps)
@@ -645,7 +652,8 @@ def run_forms(ctx, dev, steps, crops=None, which=FORMS):
         t_fb = _time(fb, steps)
         keys_bin = int(fr.counts()[0])
         forms["differentiable_8x512"] = {
-            "workload": "8 orbit views 512x512, 300k Gaussians SH3 + 50k-face torus, L2 loss to a perturbed-scene render",
+            "workload": "8 orbit views 512x512, 300k Gaussians SH3 + 50k-face torus, L2 loss to the render of a "
+                        "perturbed copy (means, SH, opacity logits, vertices, colours)",
             "fwd_views_per_s": round(nv * 1e3 / t_f, 1), "fwd_ms": round(t_f, 3),
             "fwd_bwd_views_per_s": round(nv * 1e3 / t_fb, 1), "fwd_bwd_ms": round(t_fb, 3)}
         # the same step with soft-edge triangle coverage (sigma 0.5 px): the
@@ -666,7 +674,7 @@ def run_forms(ctx, dev, steps, crops=None, which=FORMS):
             "fwd_views_per_s": round(nv * 1e3 / t_sf, 1), "fwd_ms": round(t_sf, 3),
             "fwd_bwd_views_per_s": round(nv * 1e3 / t_sfb, 1), "fwd_bwd_ms": round(t_sfb, 3),
             "keys": keys_soft, "keys_binary_coverage": keys_bin}
-        del g, ms, gp, target, out, fr
+        del g, ms, gp, mp, target, out, fr
         torch.cuda.empty_cache()
     if "mixed" in which:
         # config 4: 4K, 6M Gaussians + 2M triangles, fp32 vs bf16 SH + fp16 records

@@ -41,6 +41,11 @@ template <int TS> struct BwdBatch { static constexpr int value = TS == 16 ? 192 
 template <int TS> constexpr int bwd_smem_bytes() {
     return BwdBatch<TS>::value * (160 + 88 + 4 + 4 + TS * TS / 32) + 4 * (TS * TS / 32) + 16;
 }
+// (soft-edge replays: then the records' coverage constants, SoftEdges, 16-byte aligned)
+template <int TS> constexpr int bwd_soft_edges_offset() { return (bwd_smem_bytes<TS>() + 15) & ~15; }
+template <int TS, bool SOFT> constexpr int bwd_smem_bytes_for() {
+    return SOFT ? bwd_soft_edges_offset<TS>() + BwdBatch<TS>::value * (int)sizeof(SoftEdges) : bwd_smem_bytes<TS>();
+}
 constexpr float kLn2 = 0.6931471805599453f;
 
 // Warp sum of V values per lane (V = 16 or 32) by recursive halving: at each
@@ -91,6 +96,7 @@ __global__ void __launch_bounds__(TS * TS, TS == 16 ? (SOFT ? 2 : 4) : 1) compos
     int* s_wmax = reinterpret_cast<int*>(s_wmask + kBatchB);
     int& s_max = s_wmax[NW];
     uint8_t* s_list = reinterpret_cast<uint8_t*>(s_wmax + NW + 4);
+    SoftEdges* s_edges = reinterpret_cast<SoftEdges*>(smem + bwd_soft_edges_offset<TS>());  // (SOFT only)
     const int tile = blockIdx.x;
     const int cam = tile / tiles_per_cam;
     const int lt = tile - cam * tiles_per_cam;
@@ -157,6 +163,7 @@ __global__ void __launch_bounds__(TS * TS, TS == 16 ? (SOFT ? 2 : 4) : 1) compos
                 const TRec& tr = *reinterpret_cast<const TRec*>(&s_rec[k][0]);
                 s_wmask[k] = box_block_mask<TS>((int)(tr.rx & 0xffff), (int)(tr.rx >> 16), (int)(tr.ry & 0xffff),
                                                 (int)(tr.ry >> 16), tile_x0, tile_y0);
+                if (SOFT) soft_edges(tr, s_edges[k]);
             }
 #pragma unroll
             for (int e = 0; e < 22; ++e) s_acc[k][e] = 0.f;
@@ -228,7 +235,7 @@ __global__ void __launch_bounds__(TS * TS, TS == 16 ? (SOFT ? 2 : 4) : 1) compos
                     if (active && px >= (int)(t.rx & 0xffff) && px <= (int)(t.rx >> 16) &&
                         py >= (int)(t.ry & 0xffff) && py <= (int)(t.ry >> 16)) {
                         mask = 0xf;  // a fragment of this pixel
-                        soft_coverage(t, qx, qy, cov, sg, il, sgm);
+                        soft_coverage_staged_bwd(t, s_edges[k], qx, qy, cov, sg, il, sgm);
                     }
                 } else if (active) {
                     long long E[3];
@@ -1045,8 +1052,8 @@ umgs_status render_backward(umgs_ctx* ctx, umgs_frame* fr, const umgs_gaussians*
 #define UMGS_LAUNCH(TSV, SOFTV)                                                                                  \
         /* per call: the attribute belongs to the current device */                                         \
         UMGS_TRY(cudaFuncSetAttribute(composite_bwd_kernel<TSV, SOFTV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                      bwd_smem_bytes<TSV>()));                                                   \
-        launch_pdl(composite_bwd_kernel<TSV, SOFTV>, M, TSV * TSV, bwd_smem_bytes<TSV>(), stream,                        \
+                                      (bwd_smem_bytes_for<TSV, SOFTV>())));                                      \
+        launch_pdl(composite_bwd_kernel<TSV, SOFTV>, M, TSV * TSV, (bwd_smem_bytes_for<TSV, SOFTV>()), stream,           \
             fr->ids, fr->tile_off.as<int64_t>(), fr->grec.as<GRec>(), fr->trec.as<TRec>(), Ng, Nt,               \
             fr->tiles_x, tpc, fr->W, fr->H, fr->bg[0], fr->bg[1], fr->bg[2], dout, fr->last.as<int32_t>(),         \
             fr->tfin.as<float>(), fr->ntri.as<int32_t>(), fr->stack.as<float4>(), npix, fr->ggrad.as<float>(),     \

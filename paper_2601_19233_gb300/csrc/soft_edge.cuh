@@ -66,6 +66,7 @@ __device__ __forceinline__ void soft_coverage(const TRec& t, float qx, float qy,
 struct SoftEdges {
     float k[4];
     float d[3][4];
+    float il[4];  // 1 / L_e (0 for an edge of zero length; il[3] unused), for the backward
 };
 __device__ __forceinline__ void soft_edges(const TRec& t, SoftEdges& se) {
     const float sg = soft_orientation(t);
@@ -75,12 +76,14 @@ __device__ __forceinline__ void soft_edges(const TRec& t, SoftEdges& se) {
         const float ex = t.u[b] - t.u[a], ey = t.v[b] - t.v[a];
         const float L = sqrtf(ex * ex + ey * ey);
         se.k[e] = L > 0.f ? sg * 1.4426950408889634f * t.pad2 / L : 0.f;
+        se.il[e] = L > 0.f ? 1.f / L : 0.f;
 #pragma unroll
         for (int j = 0; j < 4; ++j)
             se.d[e][j] = (t.v[a] - t.v[b]) * ((float)sample_dx(j) * (1.f / 256.f)) +
                          (t.u[b] - t.u[a]) * ((float)sample_dy(j) * (1.f / 256.f));
     }
     se.k[3] = sg;
+    se.il[3] = 0.f;
 }
 // c^j of pixel centre (qx, qy) from the staged constants: lambda_e at the
 // centre (the relative form) plus the sample offsets, and per sample one
@@ -100,6 +103,31 @@ __device__ __forceinline__ void soft_coverage_staged(const TRec& t, const SoftEd
 #pragma unroll
         for (int e = 0; e < 3; ++e) den *= 1.f + fast_exp2(-se.k[e] * (lam[e] + se.d[e][j]));
         c[j] = se.k[3] != 0.f ? 1.f / den : 0.f;
+    }
+}
+
+// The backward's form of soft_coverage from the staged constants: c^j and
+// the per-(sample, edge) logistic terms the gradient needs, sg and 1/L_e
+__device__ __forceinline__ void soft_coverage_staged_bwd(const TRec& t, const SoftEdges& se, float qx, float qy,
+                                                         float c[4], float& sg, float il[3], float sgm[4][3]) {
+    float lam[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int a = (e + 1) % 3, b = (e + 2) % 3;
+        lam[e] = (t.u[a] - qx) * (t.v[b] - qy) - (t.u[b] - qx) * (t.v[a] - qy);
+        il[e] = se.il[e];
+    }
+    sg = se.k[3];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        float cj = sg != 0.f ? 1.f : 0.f;
+#pragma unroll
+        for (int e = 0; e < 3; ++e) {
+            const float sj = 1.f / (1.f + fast_exp2(-se.k[e] * (lam[e] + se.d[e][j])));
+            sgm[j][e] = sj;
+            cj *= sj;
+        }
+        c[j] = cj;
     }
 }
 
