@@ -17,11 +17,13 @@ namespace umgs {
 constexpr int kRsThreads = 256;
 constexpr int kRsItems = 16;
 constexpr int kRsTile = kRsThreads * kRsItems;  // elements per block of the scan
-// Radix sorts of up to kRsSmallMax elements (the count that sizes the grid)
-// take 8 elements per thread, longer ones 16 (measured at 1080p: the 4 depth
-// passes over 1.2M records and the region pass over 1.85M pairs gain from
-// more blocks in flight; 4 per thread was slower again).
-constexpr int64_t kRsSmallMax = (int64_t)1 << 24;
+// Radix passes take 8 elements per thread at every size (measured on the
+// 64-view 800^2 workload: 38M depth keys and the region pairs sorted with 8
+// per thread instead of 16 took the render from 15.4 to 14.7 ms, the
+// 16-element pass kernel holding 128 registers at two CTAs per SM; at 1080p
+// the passes already used 8).  kRsSmallMax keeps the 16-element kernels
+// selectable (above it) without a size in practice reaching it.
+constexpr int64_t kRsSmallMax = (int64_t)1 << 62;
 inline int radix_items(int64_t n_cap) { return n_cap <= kRsSmallMax ? 8 : 16; }
 inline int64_t radix_blocks(int64_t n_cap) {
     const int64_t tile = (int64_t)kRsThreads * radix_items(n_cap);
