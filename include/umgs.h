@@ -475,7 +475,10 @@ umgs_status umgs_deform_csr(umgs_ctx* ctx, const umgs_gaussians* rest, const int
  * then hit the cache.  The renderer's results do not depend on the order
  * beyond the unified ids that break exact depth ties.
  *   means [n,3] float device; out_perm [n] int32 device.
- * Synchronises `stream`; keeps a workspace of 16 n bytes in the context.
+ * Synchronises `stream`; keeps a workspace of 16 n bytes in the context and
+ * sorts with the sort workspace of the context's default frame (the one
+ * umgs_render uses when given no frame), so it must not run while a render
+ * into that frame is in flight on another stream.
  * Errors: INVALID_ARG (NULL arrays, n < 0 or n >= 2^31 - 1), OUT_OF_MEMORY,
  * CUDA. */
 umgs_status umgs_spatial_order(umgs_ctx* ctx, const float* means, int64_t n, int32_t* out_perm, void* stream);
