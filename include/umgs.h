@@ -65,7 +65,9 @@ typedef struct {
     const float* quats;      /* [n,4] (w,x,y,z); normalised inside; ignored when cov3d != NULL */
     const float* scales;     /* [n,3] activated standard deviations; ignored when cov3d != NULL */
     const float* opacities;  /* [n] activated opacity in [0,1] */
-    const void* sh;          /* [n,(sh_degree+1)^2,3] float32 or bfloat16 (sh_dtype) */
+    const void* sh;          /* [n,(sh_degree+1)^2,3] float32 or bfloat16 (sh_dtype); 16-byte aligned
+                                when a row's bytes are a multiple of 16 (float32 degree 1 and 3,
+                                bfloat16 degree 3), 8-byte aligned for bfloat16 degree 1 */
     const float* cov3d;      /* nullable [n,6] (xx,xy,xz,yy,yz,zz), e.g. the output of umgs_deform */
     int64_t n;
     int32_t sh_degree;       /* 0..3 */
@@ -208,8 +210,8 @@ void umgs_frame_destroy(umgs_frame* frame);
  * meshes     host array of nmeshes umgs_mesh (may be NULL when nmeshes == 0)
  * cams       host array of ncams cameras; all must have the same width/height
  * opts       host pointer; NULL = defaults
- * out_rgbt   [ncams,H,W,4] device float: RGB (background included) and the
- *            final transmittance T
+ * out_rgbt   [ncams,H,W,4] device float, 16-byte aligned: RGB (background
+ *            included) and the final transmittance T
  * frame      nullable; when given, the frame keeps everything
  *            umgs_render_backward needs (and the call uses its buffers)
  * Synchronises once per call on `stream` to read the number of keys, except
@@ -217,7 +219,8 @@ void umgs_frame_destroy(umgs_frame* frame);
  * a pair capacity from umgs_frame_reserve, the number of keys is not known
  * on the host afterwards, and a render that needs more pairs composites no
  * tile and is reported by umgs_frame_check).
- * Errors: INVALID_ARG (NULL arrays with n > 0, ncams < 1, mixed image sizes,
+ * Errors: INVALID_ARG (NULL arrays with n > 0, misaligned out_rgbt or sh,
+ * ncams < 1, mixed image sizes,
  * image sides above 32768, tile_size not 8/16/32, sh_degree > 3, more than
  * 4294967294 primitives, more than 2^22 regions of 8 x 4 tiles over the
  * cameras, ASYNC without a frame or capacity), CAPACITY (more than
@@ -254,7 +257,7 @@ umgs_status umgs_frame_depth(const umgs_frame* frame, float* out_depth, void* st
  * their expected depths (the nearer layer over the farther, layer a first
  * on equal depths), then the background bg:
  *   C = C_f + T_f C_b + T_f T_b bg,  T = T_f T_b.
- * a_rgbt, b_rgbt, out_rgbt [npix,4] and a_depth, b_depth [npix] float device;
+ * a_rgbt, b_rgbt, out_rgbt [npix,4] (16-byte aligned) and a_depth, b_depth [npix] float device;
  * bg host float[3].  Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA. */
 umgs_status umgs_composite_layers(umgs_ctx* ctx, const float* a_rgbt, const float* a_depth, const float* b_rgbt,
                                   const float* b_depth, int64_t npix, const float* bg, float* out_rgbt,
@@ -321,12 +324,14 @@ umgs_status umgs_frame_lists(const umgs_frame* frame, int64_t* tile_ptr, int32_t
  *
  * frame      the frame of the forward call (same ctx)
  * g, meshes  the SAME inputs as the forward call
- * dL_drgbt   [ncams,H,W,4] device float: dL/dR, dL/dG, dL/dB, dL/dT
+ * dL_drgbt   [ncams,H,W,4] device float, 16-byte aligned: dL/dR, dL/dG, dL/dB, dL/dT
+ *            (g->quats, when used, and gg->quats are read and written as
+ *            16-byte rows: both 16-byte aligned)
  * gg, mg     host structs of device output pointers (mg: nmeshes entries);
  *            outputs are overwritten (zero-filled first)
  * Synchronises once (checks the saved-state capacity; if a pixel had more
  * triangle fragments than the stack held, the forward composite is re-run
- * with a larger stack first).  Errors: INVALID_ARG (no saved frame, sizes),
+ * with a larger stack first).  Errors: INVALID_ARG (no saved frame, sizes, alignment),
  * NOT_IMPLEMENTED (blend modes other than FULL), OUT_OF_MEMORY, CUDA.
  */
 umgs_status umgs_render_backward(umgs_ctx* ctx, umgs_frame* frame, const umgs_gaussians* g,

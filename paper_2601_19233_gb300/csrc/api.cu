@@ -18,6 +18,14 @@ umgs_status cuda_fail(umgs_ctx* ctx, cudaError_t e, const char* where) {
     return fail(ctx, UMGS_ERR_CUDA, m);
 }
 
+// Alignment of the SH array that the colour kernel's vector loads need: a
+// row of (degree + 1)^2 x 3 coefficients read as 16-byte words when its bytes
+// are a multiple of 16, as 8-byte words when a multiple of 8.
+static uintptr_t sh_alignment(int degree, int dtype) {
+    const int row = (degree + 1) * (degree + 1) * 3 * (dtype == UMGS_BF16 ? 2 : 4);
+    return row % 16 == 0 ? 16 : row % 8 == 0 ? 8 : 1;
+}
+
 }  // namespace umgs
 
 using namespace umgs;
@@ -178,6 +186,8 @@ umgs_status umgs_render(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_mesh*
                     "split must be 0 or 256..1048576, and not with SAVE_BACKWARD, DEPTH or SOFT_EDGE");
     if (!cams || ncams < 1) return fail(ctx, UMGS_ERR_INVALID_ARG, "need at least one camera");
     if (!out_rgbt) return fail(ctx, UMGS_ERR_INVALID_ARG, "out_rgbt is NULL");
+    if (reinterpret_cast<uintptr_t>(out_rgbt) & 15)
+        return fail(ctx, UMGS_ERR_INVALID_ARG, "out_rgbt must be 16-byte aligned");
     if (nmeshes < 0 || (nmeshes > 0 && !meshes)) return fail(ctx, UMGS_ERR_INVALID_ARG, "bad mesh array");
     for (int c = 0; c < ncams; ++c) {
         if (cams[c].width != cams[0].width || cams[c].height != cams[0].height)
@@ -194,6 +204,9 @@ umgs_status umgs_render(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_mesh*
         if (g->sh_degree < 0 || g->sh_degree > 3) return fail(ctx, UMGS_ERR_INVALID_ARG, "sh_degree must be 0..3");
         if (g->sh_dtype != UMGS_F32 && g->sh_dtype != UMGS_BF16)
             return fail(ctx, UMGS_ERR_INVALID_ARG, "sh_dtype must be UMGS_F32 or UMGS_BF16");
+        if (reinterpret_cast<uintptr_t>(g->sh) & (sh_alignment(g->sh_degree, g->sh_dtype) - 1))
+            return fail(ctx, UMGS_ERR_INVALID_ARG,
+                        "sh must be 16-byte aligned (8-byte for bfloat16 degree 1; see umgs_gaussians)");
     }
     if (g && g->n < 0) return fail(ctx, UMGS_ERR_INVALID_ARG, "negative Gaussian count");
     for (int m = 0; m < nmeshes; ++m) {
@@ -255,6 +268,12 @@ umgs_status umgs_render_backward(umgs_ctx* ctx, umgs_frame* frame, const umgs_ga
     if (!frame->saved) return fail(ctx, UMGS_ERR_INVALID_ARG, "render without UMGS_RENDER_SAVE_BACKWARD");
     if (frame->mixed) return fail(ctx, UMGS_ERR_NOT_IMPLEMENTED, "backward of a mixed-precision render");
     if (!dL_drgbt) return fail(ctx, UMGS_ERR_INVALID_ARG, "dL_drgbt is NULL");
+    if (reinterpret_cast<uintptr_t>(dL_drgbt) & 15)
+        return fail(ctx, UMGS_ERR_INVALID_ARG, "dL_drgbt must be 16-byte aligned");
+    if (g && g->n > 0 && !g->cov3d && (reinterpret_cast<uintptr_t>(g->quats) & 15))
+        return fail(ctx, UMGS_ERR_INVALID_ARG, "quats must be 16-byte aligned for the backward");
+    if (gg && (reinterpret_cast<uintptr_t>(gg->quats) & 15))
+        return fail(ctx, UMGS_ERR_INVALID_ARG, "the quats gradient must be 16-byte aligned");
     const int64_t ng = g ? g->n : 0;
     if (ng != frame->ng) return fail(ctx, UMGS_ERR_INVALID_ARG, "Gaussian count differs from the forward call");
     if (nmeshes != (int32_t)frame->mesh_offset.size() || (nmeshes > 0 && !meshes))

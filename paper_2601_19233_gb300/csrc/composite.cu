@@ -33,12 +33,13 @@ template <int TS> struct Layout {
 // spills; shared memory allows the same)
 template <int TS> struct MinBlocks { static constexpr int value = TS == 16 ? 6 : 1; };
 constexpr int kSlot = 11;      // 16-byte vectors of shared memory per staged triangle
-constexpr int kTriSlots = 96;  // staged triangles per batch (a batch ends before the 97th)
+constexpr int kTriSlots = 64;  // staged triangles per batch (a batch ends before the 65th)
 
+// Per-pixel state of the blend.  The colour, the transmittance and the
+// expected-depth sums of a thread's two pixels are held as (pixel 0, pixel 1)
+// pairs in PairAcc, so that a Gaussian fragment updates both with one packed
+// fp32 instruction each (fma.rn.f32x2: the same rounding as two scalar fmas).
 struct PixelState {
-    float C[3];
-    float T;
-    float D, Wd;  // expected-depth mode: sum w z, sum w
     float Tin;
     float t[4];
     float g_since;
@@ -47,10 +48,17 @@ struct PixelState {
     int last;
     int sp;
 };
+struct PairAcc {
+    float2 C[3];
+    float2 T;
+    float2 D, Wd;  // expected-depth mode: sum w z, sum w
+};
 
 // Shared memory of the forward compositor: per batch the staged Gaussians
-// ((u, v, ca, cb), (cc, o, r, g), (b, Z, -, -), pixel rect (x0, x1 - x0,
-// y0, y1 - y0) as integers), up to kTriSlots staged triangles (kSlot x 16
+// as five 16-byte vectors, the pairs that the packed exponent of a thread's
+// two pixels reads ((-u, -u, -v, -v), (l0, l0, l1, l1), (l2, l2, o, o)),
+// then (r, g, b, Z) and the pixel rect (x0, x1 - x0, y0, y1 - y0) as
+// integers; up to kTriSlots staged triangles (kSlot x 16
 // bytes, stage_triangle), the ids and warp-block masks of the batch's
 // records, one ballot of "is a triangle" per 32 records, each triangle
 // record's slot, and per warp its list of entries (record | slot << 8 |
@@ -58,7 +66,7 @@ struct PixelState {
 template <int TS>
 struct CompositeSmem {
     static constexpr int NB = Layout<TS>::NB;
-    float4 g[NB][4];
+    float4 g[NB][5];
     float4 t[kTriSlots][kSlot];
     uint32_t id[NB];
     uint32_t wmask[NB];
@@ -231,7 +239,8 @@ __device__ __forceinline__ int record_coverage(const TRec& t, int px, int py, bo
 // One triangle record at one pixel: coverage, attributes, and the blend of
 // the blend mode (Eq. 7-9 for FULL).  Returns true when it was a fragment.
 template <bool SAVE, int MODE>
-__device__ __forceinline__ bool blend_triangle(PixelState& st, const float4* __restrict__ w, const TRec* __restrict__ TR,
+__device__ __forceinline__ bool blend_triangle(PixelState& st, float (&C)[3], float& T, float& D, float& Wd,
+                                               const float4* __restrict__ w, const TRec* __restrict__ TR,
                                                uint32_t tid, int px, int py, int lx, int ly,
                                                float4* __restrict__ stack, int cap, int64_t npix, int64_t pix,
                                                const DevTex* __restrict__ textab) {
@@ -305,17 +314,17 @@ __device__ __forceinline__ bool blend_triangle(PixelState& st, const float4* __r
     float a = (flags & kTriConstAlpha) ? v0.w : (wv[0] * v0.w + wv[1] * v1.w + wv[2] * v2.w);
     a = fminf(fmaxf(a, 0.f), 1.f);
     if (mode == UMGS_BLEND_DIRECT) {
-        const float wt = a * st.T;
-        st.C[0] += wt * col[0]; st.C[1] += wt * col[1]; st.C[2] += wt * col[2];
-        st.T *= (1.f - a);
+        const float wt = a * T;
+        C[0] += wt * col[0]; C[1] += wt * col[1]; C[2] += wt * col[2];
+        T *= (1.f - a);
     } else if (mode == UMGS_BLEND_MSAA_ALL) {
         const float O = 0.25f * (float)__popc(mask);
-        const float wt = O * a * st.T;
-        st.C[0] += wt * col[0]; st.C[1] += wt * col[1]; st.C[2] += wt * col[2];
-        st.T *= (1.f - O * a);
+        const float wt = O * a * T;
+        C[0] += wt * col[0]; C[1] += wt * col[1]; C[2] += wt * col[2];
+        T *= (1.f - O * a);
     } else {
         if (!st.in_ent) {
-            st.Tin = st.T;
+            st.Tin = T;
             st.t[0] = st.t[1] = st.t[2] = st.t[3] = 1.f;
             st.g_since = 1.f;
             st.in_ent = true;
@@ -332,30 +341,45 @@ __device__ __forceinline__ bool blend_triangle(PixelState& st, const float4* __r
         for (int j = 0; j < 4; ++j) O += ((mask >> j) & 1) ? st.t[j] : 0.f;
         O *= 0.25f;
         const float wt = st.Tin * O * a;
-        st.C[0] += wt * col[0]; st.C[1] += wt * col[1]; st.C[2] += wt * col[2];
-        if (mode == kModeDepth) { st.D += wt * zt; st.Wd += wt; }
+        C[0] += wt * col[0]; C[1] += wt * col[1]; C[2] += wt * col[2];
+        if (mode == kModeDepth) { D += wt * zt; Wd += wt; }
 #pragma unroll
         for (int j = 0; j < 4; ++j)
             if ((mask >> j) & 1) st.t[j] *= (1.f - a);
         const float tm = 0.25f * ((st.t[0] + st.t[1]) + (st.t[2] + st.t[3]));
-        if (mode == kModeTProduct) st.T *= (1.f - O * a);
-        else st.T = (mode == UMGS_BLEND_ENTITY_ALL) ? st.Tin * tm * st.g_since : st.Tin * tm;
+        if (mode == kModeTProduct) T *= (1.f - O * a);
+        else T = (mode == UMGS_BLEND_ENTITY_ALL) ? st.Tin * tm * st.g_since : st.Tin * tm;
     }
     return true;
 }
 
-// Blend of a Gaussian fragment of alpha `al` (Eq. 1-2).
+// Blend of a Gaussian fragment into both pixels of a thread (Eq. 1-2):
+// alpha (a0, a1), where a pixel the fragment does not reach takes alpha 0,
+// which leaves its colour, T and sums exactly as they were.
 template <int MODE>
-__device__ __forceinline__ void blend_gaussian(PixelState& st, float al, float r, float g, float b, float z, int pos,
-                                               float t_eps) {
-    const float w = al * st.T;
-    st.C[0] += w * r; st.C[1] += w * g; st.C[2] += w * b;
-    if (MODE == kModeDepth) { st.D += w * z; st.Wd += w; }
-    st.T = __fmaf_rn(-al, st.T, st.T);  // T (1 - alpha), one rounding
-    if (MODE == UMGS_BLEND_ENTITY_ALL) st.g_since *= (1.f - al);
-    else st.in_ent = false;
-    st.last = pos;
-    if (st.T < t_eps) st.done = true;
+__device__ __forceinline__ void blend_gaussian2(PixelState (&st)[2], PairAcc& acc, bool t0, bool t1, float a0, float a1,
+                                                float r, float g, float b, float z, int pos, float t_eps) {
+    const float2 al = make_float2(t0 ? a0 : 0.f, t1 ? a1 : 0.f);
+    const float2 w = __fmul2_rn(al, acc.T);
+    acc.C[0] = __ffma2_rn(w, make_float2(r, r), acc.C[0]);
+    acc.C[1] = __ffma2_rn(w, make_float2(g, g), acc.C[1]);
+    acc.C[2] = __ffma2_rn(w, make_float2(b, b), acc.C[2]);
+    if (MODE == kModeDepth) {
+        acc.D = __ffma2_rn(w, make_float2(z, z), acc.D);
+        acc.Wd = __fadd2_rn(acc.Wd, w);
+    }
+    acc.T = __ffma2_rn(make_float2(-al.x, -al.y), acc.T, acc.T);  // T (1 - alpha), one rounding
+    if (MODE == UMGS_BLEND_ENTITY_ALL) {
+        st[0].g_since *= (1.f - al.x);
+        st[1].g_since *= (1.f - al.y);
+    } else {
+        st[0].in_ent = st[0].in_ent && !t0;
+        st[1].in_ent = st[1].in_ent && !t1;
+    }
+    if (t0) st[0].last = pos;
+    if (t1) st[1].last = pos;
+    st[0].done = st[0].done || acc.T.x < t_eps;
+    st[1].done = st[1].done || acc.T.y < t_eps;
 }
 
 template <int TS, bool SAVE, int MODE>
@@ -387,11 +411,14 @@ __device__ __forceinline__ void composite_tile(
     const float qx = px + 0.5f, qy0 = py0 + 0.5f, qy1 = py1 + 0.5f;
 
     PixelState st[2];
+    PairAcc acc;
+    acc.C[0] = acc.C[1] = acc.C[2] = make_float2(0.f, 0.f);
+    acc.T = make_float2(1.f, 1.f);
+    acc.D = acc.Wd = make_float2(0.f, 0.f);
+    const float2 qxx = make_float2(qx, qx), qyy = make_float2(qy0, qy1);
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
-        st[p].C[0] = st[p].C[1] = st[p].C[2] = 0.f;
-        st[p].T = 1.f; st[p].Tin = 1.f; st[p].g_since = 1.f;
-        st[p].D = 0.f; st[p].Wd = 0.f;
+        st[p].Tin = 1.f; st[p].g_since = 1.f;
         st[p].t[0] = st[p].t[1] = st[p].t[2] = st[p].t[3] = 1.f;
         st[p].in_ent = false;
         st[p].last = 0;
@@ -450,10 +477,11 @@ __device__ __forceinline__ void composite_tile(
                 }
                 const uint32_t rx = __float_as_uint(c.y), ry = __float_as_uint(c.z);
                 const int x0 = (int)(rx & 0xffff), x1 = (int)(rx >> 16), y0 = (int)(ry & 0xffff), y1 = (int)(ry >> 16);
-                sm.g[k][0] = a;
-                sm.g[k][1] = b;
-                sm.g[k][2] = make_float4(c.x, c.w, 0.f, 0.f);
-                reinterpret_cast<int4*>(&sm.g[k][3])[0] = make_int4(x0, x1 - x0, y0, y1 - y0);
+                sm.g[k][0] = make_float4(-a.x, -a.x, -a.y, -a.y);
+                sm.g[k][1] = make_float4(a.z, a.z, a.w, a.w);
+                sm.g[k][2] = make_float4(b.x, b.x, b.y, b.y);
+                sm.g[k][3] = make_float4(b.z, b.w, c.x, c.w);
+                reinterpret_cast<int4*>(&sm.g[k][4])[0] = make_int4(x0, x1 - x0, y0, y1 - y0);
                 sm.wmask[k] = gauss_block_mask<TS, 8>(a.x, a.y, a.z, a.w, b.x, b.y, x0, x1, y0, y1, tile_x0, tile_y0);
             }
         }
@@ -500,40 +528,49 @@ __device__ __forceinline__ void composite_tile(
                 const int k = ent & 0xff;
                 if (st[0].done && st[1].done) continue;
                 if (!(ent & 0x8000)) {
-                    const int4 r = reinterpret_cast<const int4*>(&sm.g[k][3])[0];  // (x0, w, y0, h)
-                    const bool in0 = (unsigned)(px - r.x) <= (unsigned)r.y && (unsigned)(py0 - r.z) <= (unsigned)r.w &&
-                                     !st[0].done;
-                    const bool in1 = (unsigned)(px - r.x) <= (unsigned)r.y && (unsigned)(py1 - r.z) <= (unsigned)r.w &&
-                                     !st[1].done;
+                    const int4 r = reinterpret_cast<const int4*>(&sm.g[k][4])[0];  // (x0, w, y0, h)
+                    const bool inx = (unsigned)(px - r.x) <= (unsigned)r.y;
+                    const bool in0 = inx && (unsigned)(py0 - r.z) <= (unsigned)r.w && !st[0].done;
+                    const bool in1 = inx && (unsigned)(py1 - r.z) <= (unsigned)r.w && !st[1].done;
                     if (!(in0 || in1)) continue;
-                    const float4 q0 = sm.g[k][0], q1 = sm.g[k][1];
-                    const float dx = __fsub_rn(qx, q0.x);
-                    const float l0dx = __fmul_rn(q0.z, dx);  // l0 dx, shared by both pixels
-                    const float dy0 = __fsub_rn(qy0, q0.y), dy1 = __fsub_rn(qy1, q0.y);
-                    // (the operation order of gauss_power2)
-                    const float w10 = __fmaf_rn(q0.w, dy0, l0dx), w20 = __fmul_rn(q1.x, dy0);
-                    const float w11 = __fmaf_rn(q0.w, dy1, l0dx), w21 = __fmul_rn(q1.x, dy1);
-                    const float p0 = -__fmaf_rn(w10, w10, __fmul_rn(w20, w20));
-                    const float p1 = -__fmaf_rn(w11, w11, __fmul_rn(w21, w21));
-                    const float a0 = fminf(kAlphaMax, __fmul_rn(q1.y, fast_exp2(p0)));
-                    const float a1 = fminf(kAlphaMax, __fmul_rn(q1.y, fast_exp2(p1)));
+                    // the exponent of both pixels in packed fp32 (the operation
+                    // order and roundings of gauss_power2)
+                    const float4 g0 = sm.g[k][0], g1 = sm.g[k][1], g2 = sm.g[k][2];
+                    const float2 dx = __fadd2_rn(qxx, make_float2(g0.x, g0.y));
+                    const float2 dy = __fadd2_rn(qyy, make_float2(g0.z, g0.w));
+                    const float2 w1 = __ffma2_rn(make_float2(g1.z, g1.w), dy, __fmul2_rn(make_float2(g1.x, g1.y), dx));
+                    const float2 w2 = __fmul2_rn(make_float2(g2.x, g2.y), dy);
+                    const float2 pw = __ffma2_rn(w1, w1, __fmul2_rn(w2, w2));
+                    const float2 e = __fmul2_rn(make_float2(g2.z, g2.w), make_float2(fast_exp2(-pw.x), fast_exp2(-pw.y)));
+                    const float a0 = fminf(kAlphaMax, e.x), a1 = fminf(kAlphaMax, e.y);
                     const bool t0 = in0 && a0 >= kAlphaMin, t1 = in1 && a1 >= kAlphaMin;
                     if (!(t0 || t1)) continue;
-                    const float2 q2 = *reinterpret_cast<const float2*>(&sm.g[k][2]);
-                    if (t0) blend_gaussian<MODE>(st[0], a0, q1.z, q1.w, q2.x, q2.y, lbase + k, t_eps);
-                    if (t1) blend_gaussian<MODE>(st[1], a1, q1.z, q1.w, q2.x, q2.y, lbase + k, t_eps);
+                    const float4 g3 = sm.g[k][3];  // (r, g, b, Z)
+                    blend_gaussian2<MODE>(st, acc, t0, t1, a0, a1, g3.x, g3.y, g3.z, g3.w, lbase + k, t_eps);
                 } else {
                     const float4* w = &sm.t[(ent >> 8) & 0x7f][0];
                     const uint32_t tid = sm.id[k] - (uint32_t)Ng;
-                    if (!st[0].done && blend_triangle<SAVE, MODE>(st[0], w, TR, tid, px, py0, lx, ly0, stack, cap, npix,
-                                                                  pix0, textab)) {
-                        st[0].last = lbase + k;
-                        if (st[0].T < t_eps) st[0].done = true;
+                    if (!st[0].done) {
+                        float C[3] = {acc.C[0].x, acc.C[1].x, acc.C[2].x};
+                        float T = acc.T.x, D = acc.D.x, Wd = acc.Wd.x;
+                        if (blend_triangle<SAVE, MODE>(st[0], C, T, D, Wd, w, TR, tid, px, py0, lx, ly0, stack, cap,
+                                                       npix, pix0, textab)) {
+                            st[0].last = lbase + k;
+                            if (T < t_eps) st[0].done = true;
+                        }
+                        acc.C[0].x = C[0]; acc.C[1].x = C[1]; acc.C[2].x = C[2];
+                        acc.T.x = T; acc.D.x = D; acc.Wd.x = Wd;
                     }
-                    if (!st[1].done && blend_triangle<SAVE, MODE>(st[1], w, TR, tid, px, py1, lx, ly1, stack, cap, npix,
-                                                                  pix1, textab)) {
-                        st[1].last = lbase + k;
-                        if (st[1].T < t_eps) st[1].done = true;
+                    if (!st[1].done) {
+                        float C[3] = {acc.C[0].y, acc.C[1].y, acc.C[2].y};
+                        float T = acc.T.y, D = acc.D.y, Wd = acc.Wd.y;
+                        if (blend_triangle<SAVE, MODE>(st[1], C, T, D, Wd, w, TR, tid, px, py1, lx, ly1, stack, cap,
+                                                       npix, pix1, textab)) {
+                            st[1].last = lbase + k;
+                            if (T < t_eps) st[1].done = true;
+                        }
+                        acc.C[0].y = C[0]; acc.C[1].y = C[1]; acc.C[2].y = C[2];
+                        acc.T.y = T; acc.D.y = D; acc.Wd.y = Wd;
                     }
                 }
             }
@@ -545,21 +582,24 @@ __device__ __forceinline__ void composite_tile(
         if (!(px < W && py < H)) continue;
         const int64_t pix = p ? pix1 : pix0;
         const PixelState& s = st[p];
+        const float C0 = p ? acc.C[0].y : acc.C[0].x, C1 = p ? acc.C[1].y : acc.C[1].x,
+                    C2 = p ? acc.C[2].y : acc.C[2].x, T = p ? acc.T.y : acc.T.x;
+        const float D = p ? acc.D.y : acc.D.x, Wd = p ? acc.Wd.y : acc.Wd.x;
         if (seg_out) {  // one segment of a split tile: its own composite, no background (split_merge_kernel)
             const int q = (p ? ly1 : ly0) * TS + lx;
-            seg_out[q] = make_float4(s.C[0], s.C[1], s.C[2], s.T);
+            seg_out[q] = make_float4(C0, C1, C2, T);
             seg_last[q] = s.last;
             continue;
         }
-        out[pix] = make_float4(s.C[0] + s.T * bg0, s.C[1] + s.T * bg1, s.C[2] + s.T * bg2, s.T);
+        out[pix] = make_float4(C0 + T * bg0, C1 + T * bg1, C2 + T * bg2, T);
         // bit 31: the pixel stopped at T < t_eps after list position `last`
-        if (out_last) out_last[pix] = s.last | (s.T < t_eps ? (int)0x80000000u : 0);
+        if (out_last) out_last[pix] = s.last | (T < t_eps ? (int)0x80000000u : 0);
         if (SAVE) {
-            out_tfin[pix] = s.T;
+            out_tfin[pix] = T;
             out_ntri[pix] = s.sp;
             if (s.sp > cap) atomicMax(need, s.sp);
         }
-        if (MODE == kModeDepth) out_depth[pix] = s.Wd > 0.f ? s.D / s.Wd : __int_as_float(0x7f800000);
+        if (MODE == kModeDepth) out_depth[pix] = Wd > 0.f ? D / Wd : __int_as_float(0x7f800000);
     }
 }
 

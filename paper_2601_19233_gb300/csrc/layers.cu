@@ -32,6 +32,9 @@ extern "C" umgs_status umgs_composite_layers(umgs_ctx* ctx, const float* a_rgbt,
     ctx->err.clear();
     if (npix < 0 || (npix > 0 && (!a_rgbt || !a_depth || !b_rgbt || !b_depth || !out_rgbt)) || !bg)
         return fail(ctx, UMGS_ERR_INVALID_ARG, "NULL array or negative size");
+    if ((reinterpret_cast<uintptr_t>(a_rgbt) | reinterpret_cast<uintptr_t>(b_rgbt) |
+         reinterpret_cast<uintptr_t>(out_rgbt)) & 15)
+        return fail(ctx, UMGS_ERR_INVALID_ARG, "the rgbt arrays must be 16-byte aligned");
     if (npix == 0) return UMGS_OK;
     if (cudaSetDevice(ctx->device) != cudaSuccess) return fail(ctx, UMGS_ERR_CUDA, "cudaSetDevice");
     composite_layers_kernel<<<(unsigned)((npix + 255) / 256), 256, 0, static_cast<cudaStream_t>(stream)>>>(

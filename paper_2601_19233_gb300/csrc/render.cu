@@ -257,25 +257,55 @@ __global__ void __launch_bounds__(256, 2) project_gaussians_kernel(
 }
 
 // View-dependent colour of every visible (camera, Gaussian): one thread per
-// Gaussian keeps its SH coefficients in registers across the cameras.
+// Gaussian keeps its SH coefficients in registers across the cameras.  Rows
+// whose bytes are a multiple of 16 (fp32 degree 1 and 3, bf16 degree 3) are
+// first copied for the whole block with coalesced 16-byte loads into shared
+// memory, at a pitch of an odd number of 16-byte words so that the threads'
+// reads of their own rows meet no bank conflict.  The coefficients and the
+// means are read before the wait on the preceding kernel: they are inputs
+// of the frame that no kernel of it writes (the set-up kernels before this
+// one write the records and the visibility, which are read after the wait).
+constexpr int kShadeThreads = 128;
+template <int WR>
+__device__ __forceinline__ void shade_stage_rows(const void* sh, int64_t base, int nb, uint4* __restrict__ rows) {
+    if constexpr (WR > 0) {
+        const uint4* src = reinterpret_cast<const uint4*>(static_cast<const unsigned char*>(sh) + base * (16 * WR));
+        for (int q = threadIdx.x; q < nb * WR; q += kShadeThreads) {
+            const int r = q / WR;
+            rows[r * (WR | 1) + (q - r * WR)] = src[q];
+        }
+    }
+}
+
 template <int DEG>
-__global__ void __launch_bounds__(256) shade_gaussians_kernel(const float* __restrict__ means, const void* __restrict__ sh,
+__global__ void __launch_bounds__(kShadeThreads) shade_gaussians_kernel(const float* __restrict__ means, const void* __restrict__ sh,
                                                               int sh_dtype, int64_t N, const DevCam* __restrict__ cams,
                                                               int ncams, const BinInfo* __restrict__ bin, int64_t ntot,
                                                               GRec* __restrict__ grec, GRec16* __restrict__ grec16) {
-    pdl_enter();
     constexpr int K = (DEG + 1) * (DEG + 1);
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    // 16-byte words per staged row (0: the rows are read in place)
+    constexpr int W32 = (12 * K) % 16 == 0 ? 12 * K / 16 : 0, W16 = (6 * K) % 16 == 0 ? 6 * K / 16 : 0;
+    constexpr int WMAX = W32 > W16 ? W32 : W16;
+    __shared__ uint4 s_rows[kShadeThreads * (WMAX | 1)];
+    const bool bf = sh_dtype == UMGS_BF16;
+    const int64_t base = (int64_t)blockIdx.x * kShadeThreads;
+    const int64_t i = base + threadIdx.x;
+    const int nb = (int)min((int64_t)kShadeThreads, N - base);
+    if (bf) shade_stage_rows<W16>(sh, base, nb, s_rows);
+    else shade_stage_rows<W32>(sh, base, nb, s_rows);
+    float mx = 0.f, my = 0.f, mz = 0.f;
+    if (i < N) { mx = means[3 * i]; my = means[3 * i + 1]; mz = means[3 * i + 2]; }
+    pdl_enter();
+    if ((bf ? W16 : W32) > 0) __syncthreads();
     if (i >= N) return;
     float c[3 * K];
-    if (sh_dtype == UMGS_BF16) {
-        // 3K bf16 values per Gaussian: widest aligned vector loads (16 B for SH3)
-        constexpr int NB = 3 * K * 2;
-        const unsigned char* p = static_cast<const unsigned char*>(sh) + i * NB;
-        if (NB % 16 == 0) {
+    bool done_rows = false;
+    if constexpr (W16 > 0) {
+        if (bf) {
+            const uint4* row = s_rows + threadIdx.x * (W16 | 1);
 #pragma unroll
-            for (int q = 0; q < NB / 16; ++q) {
-                const uint4 u = reinterpret_cast<const uint4*>(p)[q];
+            for (int q = 0; q < W16; ++q) {
+                const uint4 u = row[q];
                 const uint32_t w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
                 for (int h = 0; h < 4; ++h) {
@@ -283,7 +313,25 @@ __global__ void __launch_bounds__(256) shade_gaussians_kernel(const float* __res
                     c[8 * q + 2 * h + 1] = __uint_as_float(w[h] & 0xffff0000u);
                 }
             }
-        } else if (NB % 8 == 0) {
+            done_rows = true;
+        }
+    }
+    if constexpr (W32 > 0) {
+        if (!bf) {
+            const float4* row = reinterpret_cast<const float4*>(s_rows + threadIdx.x * (W32 | 1));
+#pragma unroll
+            for (int k = 0; k < W32; ++k) {
+                const float4 t = row[k];
+                c[4 * k] = t.x; c[4 * k + 1] = t.y; c[4 * k + 2] = t.z; c[4 * k + 3] = t.w;
+            }
+            done_rows = true;
+        }
+    }
+    if (!done_rows && bf) {
+        // 3K bf16 values per Gaussian: 8-byte loads where a row allows them
+        constexpr int NB = 3 * K * 2;
+        const unsigned char* p = static_cast<const unsigned char*>(sh) + i * NB;
+        if (NB % 8 == 0) {
 #pragma unroll
             for (int q = 0; q < NB / 8; ++q) {
                 const uint2 u = reinterpret_cast<const uint2*>(p)[q];
@@ -295,19 +343,11 @@ __global__ void __launch_bounds__(256) shade_gaussians_kernel(const float* __res
 #pragma unroll
             for (int k = 0; k < 3 * K; ++k) c[k] = __uint_as_float(((unsigned int)q[k]) << 16);
         }
-    } else if ((3 * K) % 4 == 0) {
-        const float4* p = reinterpret_cast<const float4*>(static_cast<const float*>(sh) + i * 3 * K);
-#pragma unroll
-        for (int k = 0; k < 3 * K / 4; ++k) {
-            const float4 t = p[k];
-            c[4 * k] = t.x; c[4 * k + 1] = t.y; c[4 * k + 2] = t.z; c[4 * k + 3] = t.w;
-        }
-    } else {
+    } else if (!done_rows) {
         const float* p = static_cast<const float*>(sh) + i * 3 * K;
 #pragma unroll
         for (int k = 0; k < 3 * K; ++k) c[k] = p[k];
     }
-    const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
     for (int cam = 0; cam < ncams; ++cam) {
         if (!bin[(int64_t)cam * ntot + i].valid) continue;
         const DevCam& C = cams[cam];
@@ -1413,13 +1453,13 @@ umgs_status render_forward(umgs_ctx* ctx, const umgs_gaussians* g, const umgs_me
     }
     if (Ng > 0) {
         StageTimer tm(ctx, UMGS_STAGE_SHADE_GAUSSIANS, stream);
-        const unsigned gb = grid_for(Ng, 256);
+        const unsigned gb = grid_for(Ng, kShadeThreads);
         GRec16* g16 = mixed ? fr->grec.as<GRec16>() : nullptr;
         switch (g->sh_degree) {
-            case 0: launch_pdl(shade_gaussians_kernel<0>, gb, 256, 0, stream, g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16); break;
-            case 1: launch_pdl(shade_gaussians_kernel<1>, gb, 256, 0, stream, g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16); break;
-            case 2: launch_pdl(shade_gaussians_kernel<2>, gb, 256, 0, stream, g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16); break;
-            default: launch_pdl(shade_gaussians_kernel<3>, gb, 256, 0, stream, g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16); break;
+            case 0: launch_pdl(shade_gaussians_kernel<0>, gb, kShadeThreads, 0, stream, g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16); break;
+            case 1: launch_pdl(shade_gaussians_kernel<1>, gb, kShadeThreads, 0, stream, g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16); break;
+            case 2: launch_pdl(shade_gaussians_kernel<2>, gb, kShadeThreads, 0, stream, g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16); break;
+            default: launch_pdl(shade_gaussians_kernel<3>, gb, kShadeThreads, 0, stream, g->means, g->sh, g->sh_dtype, Ng, dcams, ncams, fr->bin.as<BinInfo>(), Ntot, fr->grec.as<GRec>(), g16); break;
         }
         UMGS_TRY(cudaGetLastError());
     }

@@ -194,6 +194,58 @@ def test_invalid_arguments_rejected(ctx):
     assert e.value.status == 1
 
 
+def _offset_view(t):
+    """A float32 copy of t whose data starts 4 bytes past a 16-byte boundary."""
+    buf = torch.empty(t.numel() + 1, dtype=torch.float32, device=t.device)
+    v = buf[1:].view(t.shape)
+    v.copy_(t)
+    assert v.data_ptr() % 16 == 4
+    return v
+
+
+def test_misaligned_arrays_rejected_on_the_host(ctx):
+    """The kernels move the image, the SH rows of degree 1 and 3, the upstream
+    gradient and the backward's quaternions as 16-byte words: a pointer off
+    that boundary is refused before anything is launched."""
+    from paper_2601_19233_gb300 import umgs
+    sc = S.config0()
+    cam = sc.cameras[0]
+    g = umgs.gaussians_to_device(sc.gaussians)
+    n = g.n
+    sh3 = torch.zeros((n, 16, 3), device="cuda")
+    n0 = umgs.kernel_launches()
+    with pytest.raises(umgs.UmgsError) as e:
+        umgs.render(ctx, g, [], sc.cameras, out=_offset_view(torch.zeros((1, cam.height, cam.width, 4), device="cuda")))
+    assert e.value.status == 1 and "out_rgbt" in str(e.value)
+    for sh, deg in ((sh3, 3), (sh3[:, :4].contiguous(), 1)):
+        g3 = umgs.DevGaussians(g.means, g.quats, g.scales, g.opacities, _offset_view(sh), deg)
+        with pytest.raises(umgs.UmgsError) as e:
+            umgs.render(ctx, g3, [], sc.cameras)
+        assert e.value.status == 1 and "sh" in str(e.value)
+    assert umgs.kernel_launches() == n0
+    # rows of degree 0 and 2 are read as single values: any float boundary does
+    for deg in (0, 2):
+        K = (deg + 1) ** 2
+        sh = torch.zeros((n, K, 3), device="cuda")
+        sh[:, 0] = g.sh[:, 0]
+        g0 = umgs.DevGaussians(g.means, g.quats, g.scales, g.opacities, _offset_view(sh), deg)
+        out = umgs.render(ctx, g0, [], sc.cameras)
+        ref = umgs.render(ctx, umgs.DevGaussians(g.means, g.quats, g.scales, g.opacities, sh, deg), [], sc.cameras)
+        assert torch.equal(out, ref)
+    fr = umgs.Frame(ctx)
+    out = umgs.render(ctx, g, [], sc.cameras, umgs.render_opts(sc.tile, save=True), frame=fr)
+    dl_bad, q_bad, dl = _offset_view(torch.zeros_like(out)), _offset_view(g.quats), torch.zeros_like(out)
+    n0 = umgs.kernel_launches()
+    with pytest.raises(umgs.UmgsError) as e:
+        umgs.render_backward(ctx, fr, g, [], dl_bad)
+    assert e.value.status == 1 and "dL_drgbt" in str(e.value)
+    gq = umgs.DevGaussians(g.means, q_bad, g.scales, g.opacities, g.sh, g.sh_degree)
+    with pytest.raises(umgs.UmgsError) as e:
+        umgs.render_backward(ctx, fr, gq, [], dl)
+    assert e.value.status == 1 and "quats" in str(e.value)
+    assert umgs.kernel_launches() == n0
+
+
 def test_evaluation_count_matches_oracle(ctx):
     sc = S.config0()
     out, fr = gpu_render(ctx, sc)
