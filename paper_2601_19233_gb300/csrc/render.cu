@@ -262,9 +262,14 @@ __global__ void __launch_bounds__(256, 2) project_gaussians_kernel(
 // first copied for the whole block with coalesced 16-byte loads into shared
 // memory, at a pitch of an odd number of 16-byte words so that the threads'
 // reads of their own rows meet no bank conflict.  The coefficients and the
-// means are read before the wait on the preceding kernel: they are inputs
-// of the frame that no kernel of it writes (the set-up kernels before this
-// one write the records and the visibility, which are read after the wait).
+// means are read before the wait on the preceding kernel.  That is safe:
+// every kernel of the chain waits before it lets the next one start, so when
+// this one starts, everything launched before its predecessor has finished
+// (the render's status clearing and projection, and whatever the caller ran
+// on the stream before the render, a deformation that wrote these means
+// included), and the predecessor, the fp64 conic refinement, writes neither
+// array.  The records and the visibility it and the projection write are
+// read after the wait.
 constexpr int kShadeThreads = 128;
 template <int WR>
 __device__ __forceinline__ void shade_stage_rows(const void* sh, int64_t base, int nb, uint4* __restrict__ rows) {
